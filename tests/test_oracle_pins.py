@@ -1,0 +1,371 @@
+"""Pins for the CPU oracle: each check ties an oracle function to something
+other than itself (a closed form, an independent equation, a high-precision
+brute force, finite differences, an exact invariance or a hand-derived
+fixture). CPU only."""
+import json
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_03541_b300 import workloads as W
+
+
+def _rand_problem(K=4, Nk=(3, 5, 2, 4), seed=0, scale=2.0):
+    g = np.random.default_rng(seed)
+    N_k = np.asarray(Nk[:K], dtype=np.int64)
+    u = scale * g.standard_normal((K, int(N_k.sum()))) + g.uniform(-3, 3, size=(K, 1))
+    return u, N_k
+
+
+# ---------------------------------------------------------------------------
+# closed forms
+# ---------------------------------------------------------------------------
+
+def test_two_samples_two_states_closed_form():
+    """K = 2, one sample per state. With f_0 = 0 the state-0 equation reads
+    1/(1+A) + 1/(1+B) = 1 with A = e^{f-da}, B = e^{f-db} (da, db the energy
+    differences u_1n - u_0n), i.e. AB = 1, so f_1 = (da + db) / 2."""
+    g = np.random.default_rng(3)
+    for _ in range(5):
+        u = g.normal(size=(2, 2)) * 3
+        f = O.solve_mbar(u, np.array([1, 1]))
+        da, db = u[1] - u[0]
+        assert abs(f[1] - 0.5 * (da + db)) < 1e-12
+
+
+def test_constant_offset_states_closed_form():
+    """If u_k = u_0 + c_k for every sample, then f_k = c_k - c_0 for any data."""
+    g = np.random.default_rng(4)
+    u0 = g.normal(size=50) * 2
+    c = g.uniform(-5, 5, size=6)
+    u = u0[None, :] + c[:, None]
+    N_k = np.array([10, 5, 5, 10, 15, 5])
+    f = O.solve_mbar(u, N_k)
+    assert np.max(np.abs(f - (c - c[0]))) < 1e-12
+    # one Eq. 1 step from f = 0 already lands there
+    f1 = O.gauge(O.sci_step(u, np.zeros(6), N_k))
+    assert np.max(np.abs(f1 - (c - c[0]))) < 1e-12
+
+
+def test_bar_equivalence_for_two_states():
+    """MBAR with K = 2 is Bennett's acceptance ratio. Solve Bennett's
+    implicit equation (which uses the sample labels, unlike MBAR) by
+    bisection and compare. N_0 != N_1 catches a transposed N_k."""
+    g = np.random.default_rng(5)
+    N0, N1 = 300, 170
+    x0 = g.normal(0.0, 1.0, N0)
+    x1 = g.normal(0.7, 1.2, N1)
+    x = np.concatenate([x0, x1])
+    u = np.stack([0.5 * x**2, 0.5 * ((x - 0.7) / 1.2) ** 2 + math.log(1.2)])
+    du = u[1] - u[0]
+
+    def bennett(df):
+        lhs = np.sum(1.0 / (1.0 + (N0 / N1) * np.exp(du[:N0] - df)))
+        rhs = np.sum(1.0 / (1.0 + (N1 / N0) * np.exp(-du[N0:] + df)))
+        return lhs - rhs          # increasing in df
+
+    lo, hi = -50.0, 50.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if bennett(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    f = O.solve_mbar(u, np.array([N0, N1]))
+    assert abs(f[1] - 0.5 * (lo + hi)) < 1e-10
+
+
+def _mp_solve(u, N_k, dps=40):
+    mp.mp.dps = dps
+    K, N = u.shape
+    U = [[mp.mpf(float(u[k, n])) for n in range(N)] for k in range(K)]
+    Nk = [mp.mpf(int(v)) for v in N_k]
+
+    def eqs(*fs):
+        f = [mp.mpf(0)] + list(fs)
+        out = []
+        for i in range(1, K):
+            tot = mp.mpf(0)
+            for n in range(N):
+                den = mp.fsum(Nk[j] * mp.exp(f[j] - U[j][n]) for j in range(K))
+                tot += mp.exp(f[i] - U[i][n]) / den
+            out.append(tot - 1)
+        return out
+
+    sol = mp.findroot(eqs, [mp.mpf(0)] * (K - 1))
+    sol = [sol] if K == 2 else list(sol)
+    return np.array([0.0] + [float(s) for s in sol])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bruteforce_40_digits(seed):
+    """Root of sum_n W_kn = 1 found by mpmath at 40 digits, directly from the
+    definition (plain sums, no log-sum-exp), K = 3, N = 6."""
+    u, N_k = _rand_problem(K=3, Nk=(2, 3, 1), seed=seed, scale=1.5)
+    f_mp = _mp_solve(u, N_k)
+    f = O.solve_mbar(u, N_k)
+    assert np.max(np.abs(f - f_mp)) < 1e-12
+
+
+def test_sci_step_against_direct_eq1_in_high_precision():
+    """Eq. 1 evaluated literally with 40-digit sums, binned (H_p > 1)."""
+    u, N_k = _rand_problem(K=3, Nk=(2, 3, 2), seed=7, scale=3.0)
+    H = np.array([1, 3, 2, 1, 4, 1, 2])
+    f = np.array([0.0, 0.4, -1.3])
+    mp.mp.dps = 40
+    K, n = u.shape
+    expect = []
+    for i in range(K):
+        tot = mp.mpf(0)
+        for p in range(n):
+            den = mp.fsum(int(N_k[j]) * mp.exp(mp.mpf(f[j]) - mp.mpf(float(u[j, p]))) for j in range(K))
+            tot += int(H[p]) * mp.exp(-mp.mpf(float(u[i, p]))) / den
+        expect.append(float(-mp.log(tot)))
+    got = O.sci_step(u, f, N_k, H)
+    assert np.max(np.abs(got - np.array(expect))) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# derivatives
+# ---------------------------------------------------------------------------
+
+def test_gradient_is_derivative_of_objective():
+    u, N_k = _rand_problem(K=4, seed=11)
+    H = np.array([1, 2, 1, 3, 1, 1, 2, 1, 1, 1, 2, 1, 1, 1])
+    f = np.array([0.0, 0.3, -0.2, 1.1])
+    g = O.mbar_gradient(u, f, N_k, H)
+    h = 1e-5
+    fd = np.array([(O.mbar_objective(u, f + h * e, N_k, H) - O.mbar_objective(u, f - h * e, N_k, H)) / (2 * h)
+                   for e in np.eye(4)])
+    assert np.max(np.abs(g - fd)) < 1e-7 * max(1.0, np.max(np.abs(g)))
+
+
+def test_hessian_is_derivative_of_gradient_and_has_gauge_null_vector():
+    u, N_k = _rand_problem(K=4, seed=12)
+    f = np.array([0.0, -0.4, 0.2, 0.9])
+    Hs = O.mbar_hessian(u, f, N_k)
+    h = 1e-5
+    fd = np.stack([(O.mbar_gradient(u, f + h * e, N_k) - O.mbar_gradient(u, f - h * e, N_k)) / (2 * h)
+                   for e in np.eye(4)], axis=1)
+    assert np.max(np.abs(Hs - fd)) < 1e-7
+    assert np.max(np.abs(Hs - Hs.T)) < 1e-14
+    assert np.max(np.abs(Hs @ np.ones(4))) < 1e-12
+    assert np.min(np.linalg.eigvalsh(Hs)) > -1e-12
+    # binned form, counts H_n as weights
+    Hn = np.array([1, 2, 1, 3, 1, 1, 2, 1, 1, 1, 2, 1, 1, 1])
+    Hb = O.mbar_hessian(u, f, N_k, Hn)
+    fd = np.stack([(O.mbar_gradient(u, f + h * e, N_k, Hn) - O.mbar_gradient(u, f - h * e, N_k, Hn)) / (2 * h)
+                   for e in np.eye(4)], axis=1)
+    assert np.max(np.abs(Hb - fd)) < 1e-7
+
+
+# ---------------------------------------------------------------------------
+# solution properties and invariances
+# ---------------------------------------------------------------------------
+
+def test_fixed_point_and_weight_sums():
+    p = W.harmonic(K=5, N_k=200, seed=2)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    Wkn = O.mbar_weights(p.u_kn, f, p.N_k)
+    assert np.max(np.abs(Wkn.sum(axis=1) - 1.0)) < 1e-12          # each state's weights sum to 1
+    assert np.max(np.abs((p.N_k[:, None] * Wkn).sum(axis=0) - 1.0)) < 1e-12   # each sample's
+    assert f[0] == 0.0                                             # gauge
+    f_sci = O.gauge(O.sci_step(p.u_kn, f, p.N_k))                   # Eq. 1 fixed point
+    assert np.max(np.abs(f_sci - f)) < 1e-11
+
+
+def test_exact_invariances():
+    p = W.harmonic(K=4, N_k=100, seed=9)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    g = np.random.default_rng(0)
+    c_k = g.normal(size=4) * 3
+    c_n = g.normal(size=p.N) * 50
+    f_state = O.solve_mbar(p.u_kn + c_k[:, None], p.N_k)
+    assert np.max(np.abs(f_state - (f + c_k - c_k[0]))) < 1e-10
+    f_sample = O.solve_mbar(p.u_kn + c_n[None, :], p.N_k)
+    assert np.max(np.abs(f_sample - f)) < 1e-10
+    perm = g.permutation(p.N)
+    f_perm = O.solve_mbar(p.u_kn[:, perm], p.N_k)
+    assert np.max(np.abs(f_perm - f)) < 1e-10
+
+
+def test_duplicate_sample_equals_count_two():
+    u, N_k = _rand_problem(K=3, Nk=(2, 2, 2), seed=21)
+    f = np.array([0.0, 0.5, -0.5])
+    H = np.array([1, 2, 1, 1, 1, 1])
+    dup = np.concatenate([u, u[:, 1:2]], axis=1)
+    a = O.sci_step(u, f, N_k, H)
+    b = O.sci_step(dup, f, N_k)
+    assert np.max(np.abs(a - b)) < 1e-14
+    ga = O.mbar_gradient(u, f, N_k, H)
+    gb = O.mbar_gradient(dup, f, N_k)
+    assert np.max(np.abs(ga - gb)) < 1e-13
+
+
+def test_one_sample_per_bin_is_the_unbinned_step():
+    p = W.umbrella(K=6, N_k=40, seed=1, grid_points=1 << 12)
+    phi = p.phi
+    w = np.min(np.diff(np.unique(phi))) / 4
+    hist = O.histogram(phi, w)
+    assert np.all(hist.H == 1) and hist.H.shape[0] == p.N
+    ub = O.binned_u(p.u_kn, hist)
+    f = np.linspace(0, 1, 6)
+    a = O.sci_step(ub, f, p.N_k, hist.H)
+    b = O.sci_step(p.u_kn, f, p.N_k)
+    assert np.max(np.abs(a - b)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# binning fixtures (hand-derived) and the width rule
+# ---------------------------------------------------------------------------
+
+def test_binning_golden(golden_dir):
+    spec = json.load(open(os.path.join(golden_dir, "binning_cases.json")))
+    for case in spec["cases"]:
+        phi = np.array(case["phi"])
+        keys = O.bin_keys(phi, phi.min(), case["w"])
+        assert keys.tolist() == case["keys"], case["name"]
+        h = O.histogram(phi, case["w"])
+        assert h.keys.tolist() == case["nonempty_keys"], case["name"]
+        assert h.H.tolist() == case["H"], case["name"]
+        assert O.nonempty_bins(phi, case["w"]) == len(case["H"])
+    for case in spec["width_cases"]:
+        phi = np.arange(float(case["phi_range"]))
+        assert O.width_for_bins(phi, case["n"]) == case["w_star"], case["name"]
+
+
+def test_width_rule_properties():
+    """w* has g(w*) >= n and the next binary64 number above it has fewer."""
+    g = np.random.default_rng(8)
+    phi = np.concatenate([g.normal(size=3000), 5 + 0.1 * g.standard_t(3, size=500)])
+    for n in (10, 100, 1000):
+        w = O.width_for_bins(phi, n)
+        assert O.nonempty_bins(phi, w) >= n
+        assert O.nonempty_bins(phi, np.nextafter(w, np.inf)) < n
+    assert O.width_for_bins(phi, 10**6) is None          # more bins than distinct values
+
+
+def test_binned_u_is_member_mean():
+    g = np.random.default_rng(2)
+    phi = np.round(g.normal(size=200), 1)
+    u = g.normal(size=(3, 200))
+    hist = O.histogram(phi, 0.25)
+    ub = O.binned_u(u, hist)
+    for p, m in enumerate(hist.members):
+        assert np.allclose(ub[:, p], u[:, m].mean(axis=1), rtol=0, atol=1e-14)
+    assert hist.H.sum() == 200
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1
+# ---------------------------------------------------------------------------
+
+def test_algorithm1_defaults(golden_dir):
+    spec = json.load(open(os.path.join(golden_dir, "algorithm1_hyperparameters.json")))
+    o = O.BUOptions()
+    assert (o.n0, o.eps, o.inc, o.n_intermediate) == (spec["n0"], spec["eps"], spec["inc"], spec["n_intermediate"])
+
+
+def test_algorithm1_reaches_the_mbar_solution():
+    p = W.gaussian_overlap(M=8, N_0=3000, seed=3)
+    tr = []
+    f_bu = O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, trace=tr)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    assert np.max(np.abs(f_bu - f)) < 1e-10
+    ns = [t[1] for t in tr if t[0] in ("phase1", "phase2")]
+    assert ns[0] == 100
+    assert all(b >= a for a, b in zip(ns, ns[1:]))              # bins only ever refine
+    assert set(ns) <= {100, 1000, 10000}
+
+
+def test_algorithm1_width_schedule():
+    p = W.umbrella(K=8, N_k=400, seed=4, grid_points=1 << 12)
+    o = O.BUOptions(h0=0.1)
+    f_bu = O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, opts=o)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    assert np.max(np.abs(f_bu - f)) < 1e-10
+
+
+def test_relative_step_reading():
+    assert O.relative_step(np.array([0.0, 1.0]), np.zeros(2)) == math.inf
+    assert O.relative_step(np.array([0.0, 1.5, -2.0]), np.array([0.0, 1.0, -1.0])) == 1.0
+
+
+# ---------------------------------------------------------------------------
+# statistical pins against analytic free energies
+# ---------------------------------------------------------------------------
+
+def _sigma(u, f, N_k):
+    Hs = O.mbar_hessian(u, f, N_k)
+    cov = np.linalg.inv(Hs[1:, 1:])
+    return np.concatenate([[0.0], np.sqrt(np.diag(cov))])
+
+
+def test_harmonic_analytic():
+    """f_k - f_0 = (d/2) ln(kappa_k/kappa_0) for u_k = kappa_k |x - mu_k|^2 / 2."""
+    p = W.harmonic(K=8, d=3, N_k=1000, seed=0)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    kap = p.meta["kappa"]
+    exact = 1.5 * np.log(kap / kap[0])
+    sig = _sigma(p.u_kn, f, p.N_k)
+    assert np.all(np.abs(f - exact)[1:] < 5 * sig[1:] + 1e-3)
+    assert np.max(sig) < 0.2
+
+
+def test_gaussian_overlap_analytic():
+    """Unit-variance Gaussian density of states: f(beta) = -beta^2/2 + const."""
+    p = W.gaussian_overlap(M=10, N_0=2000, seed=1)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    b = p.meta["beta"]
+    exact = -(b**2 - b[0] ** 2) / 2
+    sig = _sigma(p.u_kn, f, p.N_k)
+    assert np.all(np.abs(f - exact)[1:] < 5 * sig[1:] + 1e-3)
+
+
+def test_umbrella_quadrature():
+    from scipy.integrate import quad
+    p = W.umbrella(K=12, N_k=800, seed=2, grid_points=1 << 14)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    c = p.meta["centres"]
+    kap = p.meta["kappa"]
+    Z = [quad(lambda x: math.exp(-W.double_well(x) - 0.5 * kap * (x - ck) ** 2), ck - 2, ck + 2,
+              epsabs=0, epsrel=1e-12, limit=200)[0] for ck in c]
+    exact = -np.log(Z)
+    exact -= exact[0]
+    sig = _sigma(p.u_kn, f, p.N_k)
+    assert np.all(np.abs(f - exact)[1:] < 5 * sig[1:] + 1e-3)
+
+
+# ---------------------------------------------------------------------------
+# Eqs. 5-7
+# ---------------------------------------------------------------------------
+
+def test_reweight_to_a_sampled_state_gives_its_mbar_weights():
+    p = W.harmonic(K=4, N_k=150, seed=6)
+    f = O.solve_mbar(p.u_kn, p.N_k)
+    pw = O.reweight(p.u_kn[2], p.u_kn, f, p.N_k)
+    assert abs(pw.sum() - 1.0) < 1e-13
+    Wkn = O.mbar_weights(p.u_kn, f, p.N_k)
+    assert np.max(np.abs(pw - Wkn[2])) < 1e-14
+
+
+def test_reweight_high_precision():
+    u, N_k = _rand_problem(K=3, Nk=(2, 2, 1), seed=31)
+    f = np.array([0.0, 0.2, -0.7])
+    u0 = np.array([0.1, -0.3, 1.2, 0.0, 0.5])
+    mp.mp.dps = 40
+    raw = []
+    for n in range(5):
+        den = mp.fsum(int(N_k[m]) * mp.exp(mp.mpf(f[m]) - mp.mpf(float(u[m, n]))) for m in range(3))
+        raw.append(mp.exp(-mp.mpf(float(u0[n]))) / den)
+    C = mp.fsum(raw)
+    expect = np.array([float(r / C) for r in raw])
+    assert np.max(np.abs(O.reweight(u0, u, f, N_k) - expect)) < 1e-15
+
+
+def test_mae():
+    assert O.mae(np.array([0.0, 1.0, 2.0]), np.array([0.0, 1.5, 1.0])) == pytest.approx(0.5)
