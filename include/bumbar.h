@@ -1,0 +1,237 @@
+/*
+ * bumbar.h -- C ABI of the B300-native BU-MBAR hot path.
+ *
+ * BU-MBAR (binned-to-unbinned MBAR; Mueller, Alesiani, Christiansen) solves
+ * the MBAR / UWHAM equations for K thermodynamic states and N samples by
+ * iterating the WHAM self-consistent update (Eq. 1) on histograms with a
+ * growing number of nonempty bins (Algorithm 1, heuristic Eq. 3), and ends
+ * with derivative-based (Newton) iterations on the unbinned data (Sec. II,
+ * Sec. III). The data are the reduced potentials
+ *
+ *     u_kn  =  reduced potential of sample n evaluated in state k
+ *              (the paper's beta_i E_p; row-major, K rows of N samples),
+ *     N_k   =  number of samples drawn from state k, sum_k N_k = N,
+ *
+ * and the result is the dimensionless free-energy vector f (gauge f_0 = 0).
+ *
+ * Conventions of every entry point:
+ *   - return an mbar_status; nothing aborts, throws or exits;
+ *   - pointers documented "host" are read or written synchronously before
+ *     the call returns; "device" pointers must be CUDA device memory of the
+ *     current device; the library never keeps a caller pointer after a call;
+ *   - a context owns all device memory it allocates; mbar_destroy frees it;
+ *   - calls on one context are not thread safe; distinct contexts on
+ *     distinct streams are independent;
+ *   - on error, mbar_last_error() returns a message for the calling thread.
+ */
+#ifndef BUMBAR_H
+#define BUMBAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BUMBAR_API __attribute__((visibility("default")))
+#else
+#define BUMBAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbar_ctx mbar_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  MBAR_OK = 0,
+  MBAR_EINVAL = 1,      /* bad argument: K < 1, N_k sum != N, non-finite u, ... */
+  MBAR_ENOMEM = 2,      /* device or host allocation failed */
+  MBAR_ECUDA = 3,       /* a CUDA runtime/driver call failed */
+  MBAR_ENOTCONV = 4,    /* iteration limit reached; the current f is readable */
+  MBAR_ESTATE = 5,      /* call not valid in the context's current state */
+  MBAR_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  MBAR_EUNSUPPORTED = 7 /* size outside what this build supports */
+} mbar_status;
+
+typedef enum {
+  MBAR_FP64 = 0,  /* u_kn stored in FP64, exp/LSE/accumulation in FP64 */
+  MBAR_MIXED = 1  /* u_kn shifted per sample and stored in FP32, exp/LSE in
+                     FP32, row sums accumulated in FP64, FP64 Newton solve */
+} mbar_precision;
+
+/* Options. mbar_opts_default fills the paper's hyperparameters (Sec. II,
+ * after Algorithm 1): n0 = 100, eps = 1e-3, inc = 10, n_intermediate = 20. */
+typedef struct {
+  int32_t precision;      /* mbar_precision */
+  int32_t n0;             /* initial number of nonempty bins */
+  double eps;             /* first-loop threshold on the relative step (Eq. 2) */
+  int32_t inc;            /* bin-count increase factor */
+  int32_t n_intermediate; /* SCI steps between checks of Eq. 3 */
+  double h0;              /* > 0: explicit width schedule h0, h0/inc, ...
+                             instead of the width rule w*(n) of Sec. II */
+  int32_t use_binning;    /* 0: skip Algorithm 1 (plain MBAR: unbinned SCI
+                             warm-up, then Newton) */
+  double f_tol;           /* Newton stops when max|delta f| < f_tol */
+  double warm_tol;        /* plain-MBAR warm-up: SCI until max_k|g_k|/N_k < warm_tol */
+  int32_t max_newton;     /* Newton iteration limit */
+  int32_t max_sci;        /* limit on SCI steps per loop of Algorithm 1 */
+} mbar_opts;
+
+typedef struct {
+  int64_t iters_first_loop;  /* SCI steps of Algorithm 1's first loop */
+  int64_t iters_second_loop; /* SCI steps (including probes) of its second loop */
+  int64_t iters_newton;      /* Newton iterations on unbinned data */
+  int64_t newton_fallbacks;  /* Newton steps replaced by an SCI step */
+  int64_t n_rebins;          /* histograms built */
+  int64_t final_bins;        /* nonempty bins of the last binned level */
+  double max_abs_grad;       /* max_k |g_k| at the returned f */
+  double last_step;          /* max |delta f| of the last Newton step */
+} mbar_report;
+
+/* Fills *opts with the defaults above (f_tol 1e-10 for MBAR_FP64, 1e-6 for
+ * MBAR_MIXED, chosen by `precision`; warm_tol 1e-3;
+ * max_newton 50; max_sci 200000; use_binning 1; h0 0). */
+BUMBAR_API mbar_status mbar_opts_default(mbar_opts* opts, int32_t precision);
+
+/* Creates a context for one problem (the paper's input list of Algorithm 1:
+ * per-state sample counts and energies, generalised to u_kn).
+ *   K, N         number of states (1 <= K <= 1024) and samples (N >= 1);
+ *   N_k          host[K], positive, sum == N;
+ *   u_kn         K x N row-major FP64, host or device (u_on_device != 0);
+ *                every entry must be finite;
+ *   opts         NULL for defaults of MBAR_MIXED;
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream).
+ * The library copies u_kn into its own device buffer (FP64, or FP32 after
+ * subtracting c_n = min_k u_kn from each column in mixed precision) and
+ * sets the bin coordinate to row 0 of u_kn.
+ * Errors: EINVAL (sizes, counts, non-finite u), ENOMEM, ECUDA, EUNSUPPORTED. */
+BUMBAR_API mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
+                        int32_t u_on_device, const mbar_opts* opts, void* cuda_stream);
+
+/* Sets the 1-D bin coordinate phi_n (Sec. II bins the energies E_p; here any
+ * per-sample coordinate). phi: N finite FP64 values, host or device.
+ * Sorts the samples by phi once (stable LSD radix sort) and reorders the
+ * stored columns, so every later histogram is a scan over contiguous runs. */
+BUMBAR_API mbar_status mbar_set_coordinate(mbar_ctx* ctx, const double* phi, int32_t phi_on_device);
+
+/* Builds the histogram of nonempty bins of uniform width h anchored at
+ * min(phi) (Sec. II): bin index floor((phi_n - min phi)/h) with the
+ * subtraction and division each rounded to nearest in binary64, counts
+ * H_p >= 1, and the binned reduced potential u_kp = mean of u_kn over the
+ * bin's members. h == 0 selects the unbinned data. The histogram becomes the
+ * context's current level for mbar_sci_step / mbar_hessian.
+ * n_bins_out (host, nullable) receives the number of nonempty bins.
+ * EINVAL if h < 0 or (max phi - min phi)/h > 2^52. */
+BUMBAR_API mbar_status mbar_bin(mbar_ctx* ctx, double h, int64_t* n_bins_out);
+
+/* Width rule of Sec. II, w*(n) = max{w : n <= g(w)}, by the deterministic
+ * search: R = range of phi; w_hi = 2R, w_lo = R/n; halve w_lo (w_hi takes
+ * its old value) until g(w_lo) >= n, giving up once R/w_lo > 2^52; then up
+ * to 64 geometric bisections mid = sqrt(w_lo*w_hi) (each operation rounded
+ * to nearest), keeping w_lo with g(w_lo) >= n. On success bins at w* like
+ * mbar_bin and returns w* in *w_out; if n cannot be reached, selects the
+ * unbinned data and returns *w_out = 0. n <= 1 or R == 0 gives one bin. */
+BUMBAR_API mbar_status mbar_bin_count(mbar_ctx* ctx, int64_t n, double* w_out, int64_t* n_bins_out);
+
+/* Reads the current histogram back. keys (host int64[n_bins], nullable):
+ * bin indices in increasing order; H (host int64[n_bins], nullable): counts;
+ * u_kp (host FP64 K x n_bins row-major, nullable): binned reduced potential
+ * as stored -- in MBAR_MIXED column p is lowered by the constant
+ * mean_{n in p} c_n of its members (differences between states are exact
+ * up to FP32 storage). ESTATE if the current level is unbinned. */
+BUMBAR_API mbar_status mbar_get_bins(mbar_ctx* ctx, int64_t* keys, int64_t* H, double* u_kp);
+
+/* One self-consistent step, Eq. 1, on the current level (bins with counts
+ * H_p, or the unbinned samples with H = 1), from f_in (host[K]):
+ *   logden_p = log sum_j N_j exp(f_j - u_jp)           (paired LSE, part 1)
+ *   Q_i      = sum_p H_p N_i exp(f_i - u_ip - logden_p) (paired LSE, part 2)
+ *   f_out_i  = f_i - log(Q_i / N_i), then gauge f_out_0 = 0
+ *   grad_i   = Q_i - N_i (gradient of the convex MBAR objective)
+ *   s        = max over i with f_in_i != 0 of |f_out_i/f_in_i - 1| (Eq. 2),
+ *              +inf if f_in is all zero.
+ * f_out, grad (host[K]), s_out (host scalar), logden (host FP64[n_cols] in
+ * the caller's original sample order when unbinned, bin order otherwise)
+ * are all nullable. */
+BUMBAR_API mbar_status mbar_sci_step(mbar_ctx* ctx, const double* f_in, double* f_out, double* grad, double* s_out,
+                          double* logden);
+
+/* Hessian of the MBAR objective on the current level at f_in (host[K]):
+ *   H_ij = delta_ij sum_p H_p P_ip - sum_p H_p P_ip P_jp,  P_ip = N_i W_ip,
+ * evaluated as the overlap matrix G_ij = sum_p H_p P_ip P_jp (off-diagonal,
+ * tensor cores, FP16 operands / FP32 accumulation) with the diagonal taken
+ * from the zero row sums, H_ii = sum_{j != i} G_ij.
+ * hess (host FP64 K x K row-major). */
+BUMBAR_API mbar_status mbar_hessian(mbar_ctx* ctx, const double* f_in, double* hess);
+
+/* One gauge-fixed Newton step from f_in on the current level: gradient,
+ * Hessian, FP64 Cholesky of the (K-1)x(K-1) block without state 0, and
+ * f_out = f_in + delta (delta_0 = 0). step_max_abs (nullable) = max|delta|.
+ * ENOTCONV if the reduced Hessian is not numerically positive definite. */
+BUMBAR_API mbar_status mbar_newton_step(mbar_ctx* ctx, const double* f_in, double* f_out, double* step_max_abs);
+
+/* Full solve: Algorithm 1 on the binned data (unless opts.use_binning == 0)
+ * followed by Newton iterations on the unbinned data until
+ * max|delta f| < f_tol. f_init (host[K], nullable => 0) warm-starts; with a
+ * warm start the first loop of Algorithm 1 runs from f_init.
+ * report (host, nullable). ENOTCONV: limit reached, f still readable. */
+BUMBAR_API mbar_status mbar_solve(mbar_ctx* ctx, const double* f_init, mbar_report* report);
+
+/* Copies the current free energies (gauge f_0 = 0) to f_out (host[K]). */
+BUMBAR_API mbar_status mbar_free_energies(mbar_ctx* ctx, double* f_out);
+
+/* Frees everything the context owns. mbar_destroy(NULL) is MBAR_OK. */
+BUMBAR_API mbar_status mbar_destroy(mbar_ctx* ctx);
+
+/* Static description of a status code. */
+BUMBAR_API const char* mbar_status_string(mbar_status status);
+
+/* Message of the last failed call on this thread ("" if none). */
+BUMBAR_API const char* mbar_last_error(void);
+
+/* Opt-in timing of the context's large launches with CUDA events on its
+ * stream (for profiling; adds two event records per timed launch).
+ * mbar_set_timing(ctx, 1) clears earlier records and starts recording,
+ * 0 stops. mbar_get_timing sums the records of one kind:
+ *   0 = unbinned fused LSE passes, 1 = Hessian, 2 = FP64 Newton solve;
+ * launches, total_ms (device time) and bytes (K x n x element size of the
+ * data each launch streams; K x K x 8 for the solve) are all nullable. */
+BUMBAR_API mbar_status mbar_set_timing(mbar_ctx* ctx, int32_t enable);
+BUMBAR_API mbar_status mbar_get_timing(mbar_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms,
+                                       double* bytes);
+
+/* Number of CUDA kernels this library has launched in this process. */
+BUMBAR_API mbar_status mbar_kernel_launches(int64_t* count);
+
+/* Bytes of device memory the context currently holds. */
+BUMBAR_API mbar_status mbar_device_bytes(mbar_ctx* ctx, int64_t* bytes);
+
+/* ---------------------------------------------------------------------
+ * Stateless device-level entry point: one fused paired-LSE pass.
+ *
+ * The Eq. 1 evaluation over a K x n matrix that is already resident in
+ * device memory. v: device, K rows of n columns, row pitch ld elements
+ * (ld >= n, ld * elem_bytes a multiple of 16, v 16-byte aligned);
+ * dtype_bytes 4 (FP32) or 8 (FP64). Columns may carry any per-column
+ * shift (f does not depend on it).
+ *   f (device FP64[K]) current free energies; log_N (device FP64[K]);
+ *   H (device int32[n], nullable => all ones) column counts;
+ *   Q (device FP64[K], out) Q_i = sum_p H_p exp(f_i + log N_i - v_ip - logden_p);
+ *   logden (device, nullable, same dtype as v, [n], out)
+ *          logden_p = log sum_j exp(f_j + log N_j - v_jp);
+ *   scratch (device) of at least mbar_lse_scratch_bytes(K, n, dtype_bytes)
+ *          bytes, 16-byte aligned, owned by the caller; it holds per-CTA
+ *          partial row sums and a completion counter, which must be zero
+ *          before the first call (the pass leaves it zero again).
+ * Runs asynchronously on `stream`. EINVAL on bad sizes or alignment,
+ * EUNSUPPORTED for K > 1024.
+ * ------------------------------------------------------------------- */
+BUMBAR_API size_t mbar_lse_scratch_bytes(int64_t K, int64_t n, int32_t dtype_bytes);
+BUMBAR_API mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t K, int64_t n, int64_t ld,
+                          const double* f, const double* log_N, const int32_t* H, double* Q, void* logden,
+                          void* scratch, size_t scratch_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BUMBAR_H */

@@ -1,0 +1,1169 @@
+// C ABI and the solver driver: Algorithm 1 (binned-to-unbinned SCI with the
+// bin-refinement heuristic of Eq. 3) followed by Newton iterations on the
+// unbinned data. All arithmetic runs in the kernels of this library; the
+// host only sequences launches and takes the scalar decisions of
+// Algorithm 1 (s < eps, 2 s_next > inc s_n, the break rule) and of the
+// Newton safeguard from values the kernels leave in device memory.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bumbar {
+const char* last_error();
+}
+
+using namespace bumbar;
+
+namespace {
+
+constexpr double kMaxIndex = 4503599627370496.0;  // 2^52
+constexpr int kPhase1Batch = 16;                  // guarded SCI launches per host check
+
+struct Level {
+  bool binned = false;
+  int64_t n = 0;         // columns
+  int64_t ld = 0;        // row pitch (elements)
+  void* v = nullptr;     // K x ld, owned if binned
+  int32_t* H = nullptr;  // counts (binned)
+  int64_t* keys = nullptr;
+  double w = 0.0;
+  int64_t n_sched = 0;  // n used by Algorithm 1's break rule
+  CUtensorMap tmap;
+};
+
+}  // namespace
+
+struct mbar_ctx {
+  int64_t K = 0, N = 0;
+  int dtype = 4;
+  mbar_opts opts{};
+  cudaStream_t st = nullptr;
+  std::vector<double> Nk_h;
+  double* Nk_d = nullptr;
+  double* logN_d = nullptr;
+  // unbinned data in the current column order
+  void* v = nullptr;
+  int64_t ld = 0;
+  double* cshift = nullptr;  // mixed: per-column shift (current order)
+  int32_t* perm = nullptr;   // current column -> original sample
+  double* phi0 = nullptr;    // default bin coordinate (row 0 of u, original order)
+  double* phi_sorted = nullptr;
+  bool sorted = false;
+  double phi_lo = 0.0, phi_hi = 0.0;
+  Level full;  // unbinned level view (not owning)
+  Level cur;   // level selected through mbar_bin / mbar_bin_count
+  // iteration state
+  double *f = nullptr, *fs = nullptr, *ft = nullptr, *fts = nullptr;
+  double *g = nullptr, *gt = nullptr, *Q = nullptr, *s = nullptr, *s2 = nullptr;
+  double *hess = nullptr, *delta = nullptr;
+  int* info = nullptr;
+  int* bad = nullptr;
+  Ctrl* ctrl = nullptr;
+  void* logden = nullptr;  // N entries, dtype
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int32_t* seg = nullptr;  // N, bin ordinal of each sorted sample
+  int32_t* start = nullptr;
+  unsigned long long* count = nullptr;
+  int32_t* nb_dev = nullptr;
+  std::vector<double> f_h;
+  std::unordered_map<void*, size_t> live;  // device allocations -> bytes
+  int64_t bytes = 0;
+  // opt-in kernel timing (CUDA events on the context's stream)
+  struct Rec {
+    cudaEvent_t a, b;
+    int kind;
+    double bytes;
+  };
+  bool timing = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+mbar_status dalloc(mbar_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, c->st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_status(e, "cudaMallocAsync");
+  }
+  c->bytes += static_cast<int64_t>(bytes);
+  c->live[*p] = bytes;
+  return MBAR_OK;
+}
+
+template <typename T>
+mbar_status dalloc_t(mbar_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  BUMBAR_TRY(dalloc(c, &q, count * sizeof(T)));
+  *p = static_cast<T*>(q);
+  return MBAR_OK;
+}
+
+void dfree(mbar_ctx* c, void* p) {
+  if (!p) return;
+  auto it = c->live.find(p);
+  if (it != c->live.end()) {
+    c->bytes -= static_cast<int64_t>(it->second);
+    c->live.erase(it);
+  }
+  cudaFreeAsync(p, c->st);
+}
+
+void level_free(mbar_ctx* c, Level* L) {
+  if (L->binned) {
+    dfree(c, L->v);
+    dfree(c, L->H);
+    dfree(c, L->keys);
+  }
+  *L = Level{};
+}
+
+mbar_status level_tmap(mbar_ctx* c, Level* L) {
+  const int C = 128 / c->dtype;
+  const int box_rows = static_cast<int>(std::min<int64_t>(256, round_up(c->K, 8)));
+  return make_tmap_2d(&L->tmap, L->v, c->dtype == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                      c->dtype, c->K, L->n, L->ld, C, box_rows);
+}
+
+cudaEvent_t take_event(mbar_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one timed launch: call with begin=true before and false after.
+void time_mark(mbar_ctx* c, bool begin, int kind, double bytes) {
+  if (!c->timing) return;
+  if (begin) {
+    mbar_ctx::Rec r{take_event(c), take_event(c), kind, bytes};
+    cudaEventRecord(r.a, c->st);
+    c->recs.push_back(r);
+  } else {
+    cudaEventRecord(c->recs.back().b, c->st);
+  }
+}
+
+// One pass of the fused LSE kernel over a level.
+mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, double* f_out, double* g_out,
+                    double* s_out, double eps, int skip_if_done, void* logden_out) {
+  const LsePlan pl = lse_plan(c->K, L.n, c->dtype);
+  LseParams p{};
+  p.K = static_cast<int>(c->K);
+  p.n = static_cast<int>(L.n);
+  p.f = f_in;
+  p.logN = c->logN_d;
+  p.H = L.H;
+  unsigned char* sc = static_cast<unsigned char*>(c->scratch);
+  p.counter = reinterpret_cast<unsigned*>(sc);
+  p.err = reinterpret_cast<unsigned*>(sc + 4);
+  p.partials = reinterpret_cast<double*>(sc + 256);
+  p.Q = c->Q;
+  p.logden = logden_out;
+  p.mode = mode;
+  p.Nk = c->Nk_d;
+  p.f_out = f_out;
+  p.g_out = g_out;
+  p.s_out = s_out;
+  p.ctrl = c->ctrl;
+  p.eps = eps;
+  p.skip_if_done = skip_if_done;
+  const bool timed = !L.binned;
+  if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
+  mbar_status s = lse_launch(L.tmap, pl, p, c->dtype, c->st);
+  if (timed) time_mark(c, false, 0, 0);
+  return s;
+}
+
+mbar_status check_device_errors(mbar_ctx* c) {
+  unsigned err = 0;
+  int nonfinite = 0;
+  BUMBAR_CUDA(cudaMemcpyAsync(&err, static_cast<unsigned char*>(c->scratch) + 4, sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, c->st));
+  BUMBAR_CUDA(cudaMemcpyAsync(&nonfinite, &c->ctrl->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  if (err) {
+    set_error("a bounded device-side wait gave up (%u CTAs)", err);
+    BUMBAR_CUDA(cudaMemsetAsync(static_cast<unsigned char*>(c->scratch) + 4, 0, sizeof(unsigned), c->st));
+    return MBAR_ETIMEOUT;
+  }
+  if (nonfinite) {
+    set_error("non-finite free energies (a state lost all weight)");
+    BUMBAR_CUDA(cudaMemsetAsync(&c->ctrl->nonfinite, 0, sizeof(int), c->st));
+    return MBAR_ENOTCONV;
+  }
+  return MBAR_OK;
+}
+
+mbar_status ensure_sorted(mbar_ctx* c);
+
+// Histogram at width w over the sorted coordinate -> a binned level.
+mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
+  *L = Level{};
+  BUMBAR_TRY(ensure_sorted(c));
+  const size_t htmp = hist_tmp_bytes(c->N);
+  const size_t mtmp = bin_means_tmp_bytes(c->K, c->N);
+  void* tmp = nullptr;
+  BUMBAR_TRY(dalloc(c, &tmp, std::max(htmp, mtmp)));
+  int64_t* keys_full = nullptr;
+  int32_t* H_full = nullptr;
+  mbar_status s = dalloc_t(c, &keys_full, c->N);
+  if (s == MBAR_OK) s = dalloc_t(c, &H_full, c->N);
+  if (s == MBAR_OK)
+    s = build_histogram(c->phi_sorted, c->N, w, c->seg, c->start, H_full, keys_full, c->nb_dev, tmp, htmp, c->st);
+  int32_t nb = 0;
+  if (s == MBAR_OK) {
+    cudaError_t e = cudaMemcpyAsync(&nb, c->nb_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) s = cuda_status(e, "histogram size");
+  }
+  if (s == MBAR_OK) {
+    L->binned = true;
+    L->n = nb;
+    L->ld = round_up(nb, 32);
+    L->w = w;
+    L->n_sched = nb;
+    s = dalloc(c, &L->v, static_cast<size_t>(c->K) * L->ld * c->dtype);
+  }
+  if (s == MBAR_OK) s = dalloc_t(c, &L->H, nb);
+  if (s == MBAR_OK) s = dalloc_t(c, &L->keys, nb);
+  if (s == MBAR_OK) {
+    cudaError_t e = cudaMemcpyAsync(L->H, H_full, nb * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L->keys, keys_full, nb * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st);
+    if (e != cudaSuccess) s = cuda_status(e, "histogram copy");
+  }
+  if (s == MBAR_OK)
+    s = bin_means(c->v, c->dtype, c->K, c->N, c->ld, c->seg, c->start, nb, L->v, L->ld, tmp, mtmp, c->st);
+  if (s == MBAR_OK) s = level_tmap(c, L);
+  dfree(c, tmp);
+  dfree(c, keys_full);
+  dfree(c, H_full);
+  if (s != MBAR_OK) level_free(c, L);
+  return s;
+}
+
+mbar_status count_at(mbar_ctx* c, double w, int64_t* g) {
+  BUMBAR_TRY(count_bins(c->phi_sorted, c->N, w, c->count, c->st));
+  unsigned long long h = 0;
+  BUMBAR_CUDA(cudaMemcpyAsync(&h, c->count, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  *g = static_cast<int64_t>(h);
+  return MBAR_OK;
+}
+
+// Width rule w*(n) by the deterministic search; *found = false when n cannot
+// be reached (the caller then uses the unbinned data).
+mbar_status width_search(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
+  BUMBAR_TRY(ensure_sorted(c));
+  const double R = c->phi_hi - c->phi_lo;
+  *found = true;
+  if (n <= 1 || R == 0.0) {
+    *w_out = R > 0.0 ? 2.0 * R : 1.0;
+    return MBAR_OK;
+  }
+  double w_hi = 2.0 * R;
+  double w_lo = R / static_cast<double>(n);
+  for (;;) {
+    if (R / w_lo > kMaxIndex) {
+      *found = false;
+      return MBAR_OK;
+    }
+    int64_t g = 0;
+    BUMBAR_TRY(count_at(c, w_lo, &g));
+    if (g >= n) break;
+    w_hi = w_lo;
+    w_lo = w_lo * 0.5;
+  }
+  for (int it = 0; it < 64; ++it) {
+    const double mid = std::sqrt(w_lo * w_hi);
+    if (!(w_lo < mid && mid < w_hi)) break;
+    int64_t g = 0;
+    BUMBAR_TRY(count_at(c, mid, &g));
+    if (g >= n)
+      w_lo = mid;
+    else
+      w_hi = mid;
+  }
+  *w_out = w_lo;
+  return MBAR_OK;
+}
+
+// Level `idx` of the schedule of Algorithm 1 (n0 * inc^idx bins, or width
+// h0 / inc^idx); unbinned when the schedule runs past the data.
+mbar_status schedule_level(mbar_ctx* c, int idx, Level* L) {
+  *L = Level{};
+  const mbar_opts& o = c->opts;
+  BUMBAR_TRY(ensure_sorted(c));
+  const double R = c->phi_hi - c->phi_lo;
+  if (o.h0 > 0.0) {
+    const double w = o.h0 / std::pow(static_cast<double>(o.inc), idx);
+    if (R / w > kMaxIndex) {
+      *L = c->full;
+      return MBAR_OK;
+    }
+    return make_level_w(c, w, L);
+  }
+  double nt = static_cast<double>(o.n0) * std::pow(static_cast<double>(o.inc), idx);
+  if (nt > static_cast<double>(c->N) * 4.0) {  // far past the data: unbinned
+    *L = c->full;
+    return MBAR_OK;
+  }
+  const int64_t n_target = static_cast<int64_t>(nt);
+  double w = 0.0;
+  bool found = false;
+  BUMBAR_TRY(width_search(c, n_target, &w, &found));
+  if (!found) {
+    *L = c->full;
+    return MBAR_OK;
+  }
+  BUMBAR_TRY(make_level_w(c, w, L));
+  L->n_sched = n_target;
+  return MBAR_OK;
+}
+
+mbar_status set_coordinate_dev(mbar_ctx* c, const double* phi_orig) {
+  // phi in the caller's original order -> current column order
+  const int64_t N = c->N;
+  double* phi_cur = nullptr;
+  int32_t* perm_rel = nullptr;
+  void* tmp = nullptr;
+  const size_t stmp = sort_tmp_bytes(N);
+  BUMBAR_TRY(dalloc_t(c, &phi_cur, N));
+  mbar_status s = dalloc_t(c, &perm_rel, N);
+  if (s == MBAR_OK) s = dalloc(c, &tmp, std::max<size_t>(stmp, static_cast<size_t>(c->K) * c->ld * c->dtype));
+  // phi_cur[i] = phi[perm[i]]
+  if (s == MBAR_OK) s = gather_columns(phi_orig, phi_cur, 8, 1, N, N, c->perm, c->st);
+  if (s == MBAR_OK) s = sort_coordinate(phi_cur, N, c->phi_sorted, perm_rel, tmp, stmp, c->st);
+  // reorder the data columns and the bookkeeping by perm_rel
+  if (s == MBAR_OK) s = gather_columns(c->v, tmp, c->dtype, c->K, N, c->ld, perm_rel, c->st);
+  if (s == MBAR_OK) {
+    std::swap(c->v, tmp);
+    c->full.v = c->v;
+  }
+  if (s == MBAR_OK) s = level_tmap(c, &c->full);
+  if (s == MBAR_OK && c->cshift) {
+    s = gather_columns(c->cshift, phi_cur, 8, 1, N, N, perm_rel, c->st);  // phi_cur reused as scratch
+    if (s == MBAR_OK) {
+      cudaError_t e = cudaMemcpyAsync(c->cshift, phi_cur, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      if (e != cudaSuccess) s = cuda_status(e, "shift reorder");
+    }
+  }
+  if (s == MBAR_OK) {
+    // perm_new[i] = perm[perm_rel[i]]
+    int32_t* pn = reinterpret_cast<int32_t*>(phi_cur);
+    s = gather_columns(c->perm, pn, 4, 1, N, N, perm_rel, c->st);
+    if (s == MBAR_OK) {
+      cudaError_t e = cudaMemcpyAsync(c->perm, pn, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st);
+      if (e != cudaSuccess) s = cuda_status(e, "perm update");
+    }
+  }
+  if (s == MBAR_OK) {
+    cudaError_t e = cudaMemcpyAsync(&c->phi_lo, c->phi_sorted, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&c->phi_hi, c->phi_sorted + N - 1, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) s = cuda_status(e, "coordinate range");
+  }
+  dfree(c, tmp);
+  dfree(c, phi_cur);
+  dfree(c, perm_rel);
+  if (s == MBAR_OK) {
+    c->sorted = true;
+    level_free(c, &c->cur);
+    c->cur = c->full;
+  }
+  return s;
+}
+
+mbar_status ensure_sorted(mbar_ctx* c) {
+  if (c->sorted) return MBAR_OK;
+  return set_coordinate_dev(c, c->phi0);
+}
+
+mbar_status h2d(mbar_ctx* c, double* dst, const double* src, int64_t n) {
+  BUMBAR_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  return MBAR_OK;
+}
+
+mbar_status d2h(mbar_ctx* c, double* dst, const double* src, int64_t n) {
+  BUMBAR_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  return MBAR_OK;
+}
+
+double max_abs(const std::vector<double>& x) {
+  double m = 0.0;
+  for (double v : x) m = std::max(m, std::fabs(v));
+  return m;
+}
+
+mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
+  const int64_t K = c->K;
+  const Level& L = c->full;
+  std::vector<double> gh(K), dh(K);
+  // evaluate at f: SCI step (fs), gradient (g), logden
+  BUMBAR_TRY(run_lse(c, L, c->f, kLseModeSci, c->fs, c->g, c->s, 0.0, 0, c->logden));
+  BUMBAR_TRY(check_device_errors(c));
+  BUMBAR_TRY(d2h(c, gh.data(), c->g, K));
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  double gmax = max_abs(gh);
+  const size_t htmp = hessian_tmp_bytes(K, L.n);
+  const size_t ntmp = newton_tmp_bytes(K);
+  void* tmp = nullptr;
+  BUMBAR_TRY(dalloc(c, &tmp, std::max(htmp, ntmp)));
+  mbar_status st = MBAR_ENOTCONV;
+  int rejects = 0;
+  for (int it = 0; it < c->opts.max_newton; ++it) {
+    if (gmax == 0.0 || K == 1) {
+      st = MBAR_OK;
+      break;
+    }
+    rep->iters_newton++;
+    time_mark(c, true, 1, static_cast<double>(K) * L.n * c->dtype);
+    mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->f, c->logN_d, c->logden, nullptr, c->hess, tmp, htmp, c->st);
+    time_mark(c, false, 1, 0);
+    if (s == MBAR_OK) s = cudaMemsetAsync(c->info, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
+    time_mark(c, true, 2, static_cast<double>(K) * K * 8);
+    if (s == MBAR_OK) s = newton_solve(c->hess, K, c->g, c->delta, c->info, tmp, ntmp, c->st);
+    time_mark(c, false, 2, 0);
+    int info = 0;
+    if (s == MBAR_OK) {
+      cudaError_t e = cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dh.data(), c->delta, K * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+      if (e != cudaSuccess) s = cuda_status(e, "newton readback");
+    }
+    if (s != MBAR_OK) {
+      dfree(c, tmp);
+      return s;
+    }
+    const double step = max_abs(dh);
+    bool accepted = false;
+    if (info == 0 && std::isfinite(step)) {
+      s = vec_add_gauge(c->f, c->delta, c->ft, K, c->st);
+      if (s == MBAR_OK) s = run_lse(c, L, c->ft, kLseModeSci, c->fts, c->gt, c->s2, 0.0, 0, c->logden);
+      if (s == MBAR_OK) s = check_device_errors(c);
+      if (s == MBAR_OK) s = d2h(c, gh.data(), c->gt, K);
+      if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+      if (s != MBAR_OK && s != MBAR_ENOTCONV) {
+        dfree(c, tmp);
+        return s;
+      }
+      const double gmax_t = (s == MBAR_OK) ? max_abs(gh) : INFINITY;
+      if (gmax_t <= gmax) {
+        std::swap(c->f, c->ft);
+        std::swap(c->fs, c->fts);
+        std::swap(c->g, c->gt);
+        gmax = gmax_t;
+        accepted = true;
+        rejects = 0;
+        rep->last_step = step;
+        if (step < c->opts.f_tol) {
+          st = MBAR_OK;
+          break;
+        }
+      }
+    }
+    if (!accepted) {
+      // Newton step did not lower max|g|: take the SCI step from f instead
+      rep->newton_fallbacks++;
+      rejects++;
+      if (rejects >= 3 && step < 1e3 * c->opts.f_tol) {  // at the noise floor of the gradient
+        st = MBAR_OK;
+        break;
+      }
+      std::swap(c->f, c->fs);
+      s = run_lse(c, L, c->f, kLseModeSci, c->fs, c->g, c->s, 0.0, 0, c->logden);
+      if (s == MBAR_OK) s = check_device_errors(c);
+      if (s == MBAR_OK) s = d2h(c, gh.data(), c->g, K);
+      if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+      if (s != MBAR_OK) {
+        dfree(c, tmp);
+        return s;
+      }
+      gmax = max_abs(gh);
+    }
+  }
+  dfree(c, tmp);
+  rep->max_abs_grad = gmax;
+  return st;
+}
+
+// Phase-1 loop of Algorithm 1 on level L: guarded in-place SCI steps until
+// s < eps (the guard turns later launches of a batch into no-ops).
+mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
+  BUMBAR_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st));
+  int64_t done_iters = 0;
+  for (;;) {
+    for (int b = 0; b < kPhase1Batch; ++b)
+      BUMBAR_TRY(run_lse(c, L, c->f, kLseModeSci, c->f, nullptr, c->s, c->opts.eps, 1, nullptr));
+    Ctrl h{};
+    BUMBAR_CUDA(cudaMemcpyAsync(&h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
+    BUMBAR_TRY(check_device_errors(c));
+    done_iters = h.iters;
+    if (h.done) break;
+    if (done_iters >= c->opts.max_sci) break;
+  }
+  rep->iters_first_loop += done_iters;
+  return MBAR_OK;
+}
+
+mbar_status read_scalar(mbar_ctx* c, const double* d, double* h) {
+  BUMBAR_CUDA(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  return MBAR_OK;
+}
+
+mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
+  const mbar_opts& o = c->opts;
+  Level L0;
+  BUMBAR_TRY(schedule_level(c, 0, &L0));
+  rep->n_rebins += L0.binned ? 1 : 0;
+  mbar_status s = first_loop(c, L0, rep);
+  level_free(c, &L0);
+  BUMBAR_TRY(s);
+  int idx = 1;
+  Level cur, nxt;
+  BUMBAR_TRY(schedule_level(c, idx, &cur));
+  rep->n_rebins += cur.binned ? 1 : 0;
+  if (!cur.binned) return MBAR_OK;
+  s = schedule_level(c, idx + 1, &nxt);
+  if (s != MBAR_OK) {
+    level_free(c, &cur);
+    return s;
+  }
+  rep->n_rebins += nxt.binned ? 1 : 0;
+  const int64_t N = c->N;
+  for (int64_t round = 0; s == MBAR_OK; ++round) {
+    if (rep->iters_second_loop >= o.max_sci) break;
+    for (int i = 0; i < o.n_intermediate && s == MBAR_OK; ++i)
+      s = run_lse(c, cur, c->f, kLseModeSci, c->f, nullptr, nullptr, 0.0, 0, nullptr);
+    if (s == MBAR_OK) s = run_lse(c, cur, c->f, kLseModeSci, c->ft, nullptr, c->s, 0.0, 0, nullptr);
+    if (s == MBAR_OK) s = run_lse(c, nxt, c->f, kLseModeSci, c->fts, nullptr, c->s2, 0.0, 0, nullptr);
+    double s_n = 0, s_next = 0;
+    if (s == MBAR_OK) s = read_scalar(c, c->s, &s_n);
+    if (s == MBAR_OK) s = read_scalar(c, c->s2, &s_next);
+    if (s == MBAR_OK) s = check_device_errors(c);
+    if (s != MBAR_OK) break;
+    rep->iters_second_loop += o.n_intermediate + 2;
+    if (2.0 * s_next > static_cast<double>(o.inc) * s_n) {
+      std::swap(c->f, c->fts);
+      level_free(c, &cur);
+      cur = nxt;
+      nxt = Level{};
+      idx++;
+      if (!cur.binned || 2.0 * o.inc * static_cast<double>(cur.n_sched) > static_cast<double>(N)) break;
+      s = schedule_level(c, idx + 1, &nxt);
+      if (s == MBAR_OK) rep->n_rebins += nxt.binned ? 1 : 0;
+    } else {
+      std::swap(c->f, c->ft);
+    }
+  }
+  rep->final_bins = cur.binned ? cur.n : 0;
+  level_free(c, &cur);
+  level_free(c, &nxt);
+  return s;
+}
+
+// plain MBAR warm-up: unbinned SCI until max_k |g_k|/N_k < warm_tol
+mbar_status plain_warmup(mbar_ctx* c, mbar_report* rep) {
+  std::vector<double> gh(c->K);
+  for (int64_t it = 0; it < c->opts.max_sci; ++it) {
+    BUMBAR_TRY(run_lse(c, c->full, c->f, kLseModeSci, c->fs, c->g, c->s, 0.0, 0, nullptr));
+    BUMBAR_TRY(check_device_errors(c));
+    BUMBAR_TRY(d2h(c, gh.data(), c->g, c->K));
+    BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+    double r = 0.0;
+    for (int64_t k = 0; k < c->K; ++k) r = std::max(r, std::fabs(gh[k]) / c->Nk_h[k]);
+    if (r < c->opts.warm_tol) break;
+    std::swap(c->f, c->fs);
+    rep->iters_first_loop++;
+  }
+  return MBAR_OK;
+}
+
+mbar_status upload_f(mbar_ctx* c, const double* f_host, double* dst) {
+  std::vector<double> g(f_host, f_host + c->K);
+  BUMBAR_TRY(h2d(c, dst, g.data(), c->K));
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  return MBAR_OK;
+}
+
+#define CHECK_CTX(c)                         \
+  do {                                       \
+    if (!(c)) {                              \
+      set_error("null context");             \
+      return MBAR_EINVAL;                    \
+    }                                        \
+  } while (0)
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* mbar_status_string(mbar_status s) {
+  switch (s) {
+    case MBAR_OK: return "ok";
+    case MBAR_EINVAL: return "invalid argument";
+    case MBAR_ENOMEM: return "out of memory";
+    case MBAR_ECUDA: return "CUDA error";
+    case MBAR_ENOTCONV: return "not converged";
+    case MBAR_ESTATE: return "invalid state";
+    case MBAR_ETIMEOUT: return "device wait timed out";
+    case MBAR_EUNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}
+
+const char* mbar_last_error(void) { return bumbar::last_error(); }
+
+mbar_status mbar_opts_default(mbar_opts* o, int32_t precision) {
+  if (!o) {
+    set_error("opts is NULL");
+    return MBAR_EINVAL;
+  }
+  if (precision != MBAR_FP64 && precision != MBAR_MIXED) {
+    set_error("unknown precision %d", precision);
+    return MBAR_EINVAL;
+  }
+  std::memset(o, 0, sizeof(*o));
+  o->precision = precision;
+  o->n0 = 100;
+  o->eps = 1e-3;
+  o->inc = 10;
+  o->n_intermediate = 20;
+  o->h0 = 0.0;
+  o->use_binning = 1;
+  o->f_tol = precision == MBAR_FP64 ? 1e-10 : 1e-6;
+  o->warm_tol = 1e-3;
+  o->max_newton = 50;
+  o->max_sci = 200000;
+  return MBAR_OK;
+}
+
+mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
+                        int32_t u_on_device, const mbar_opts* opts, void* cuda_stream) {
+  if (!out || !N_k || !u_kn) {
+    set_error("mbar_create: null pointer argument");
+    return MBAR_EINVAL;
+  }
+  *out = nullptr;
+  if (K < 1 || N < 1) {
+    set_error("mbar_create: need K >= 1 and N >= 1 (got K=%lld N=%lld)", (long long)K, (long long)N);
+    return MBAR_EINVAL;
+  }
+  if (K > 1024) {
+    set_error("mbar_create: K=%lld exceeds the supported maximum of 1024 states", (long long)K);
+    return MBAR_EUNSUPPORTED;
+  }
+  if (N > 2000000000LL) {
+    set_error("mbar_create: N=%lld exceeds the supported maximum of 2e9 samples", (long long)N);
+    return MBAR_EUNSUPPORTED;
+  }
+  int64_t sum = 0;
+  for (int64_t k = 0; k < K; ++k) {
+    if (N_k[k] < 1) {
+      set_error("mbar_create: N_k[%lld] = %lld must be positive", (long long)k, (long long)N_k[k]);
+      return MBAR_EINVAL;
+    }
+    sum += N_k[k];
+  }
+  if (sum != N) {
+    set_error("mbar_create: sum of N_k (%lld) != N (%lld)", (long long)sum, (long long)N);
+    return MBAR_EINVAL;
+  }
+  mbar_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    mbar_opts_default(&o, MBAR_MIXED);
+  }
+  if ((o.precision != MBAR_FP64 && o.precision != MBAR_MIXED) || o.n0 < 1 || o.inc < 2 || !(o.eps > 0) ||
+      o.n_intermediate < 0 || o.h0 < 0 || !(o.f_tol > 0) || o.max_newton < 1 || o.max_sci < 1) {
+    set_error("mbar_create: invalid options");
+    return MBAR_EINVAL;
+  }
+  auto* c = new (std::nothrow) mbar_ctx();
+  if (!c) {
+    set_error("mbar_create: host allocation failed");
+    return MBAR_ENOMEM;
+  }
+  c->K = K;
+  c->N = N;
+  c->opts = o;
+  c->dtype = o.precision == MBAR_MIXED ? 4 : 8;
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  c->ld = round_up(N, 32);
+  c->Nk_h.resize(K);
+  c->f_h.assign(K, 0.0);
+  std::vector<double> logN(K);
+  for (int64_t k = 0; k < K; ++k) {
+    c->Nk_h[k] = static_cast<double>(N_k[k]);
+    logN[k] = std::log(c->Nk_h[k]);
+  }
+  auto fail = [&](mbar_status s) {
+    mbar_destroy(c);
+    return s;
+  };
+  mbar_status s = MBAR_OK;
+#define TRYC(x)               \
+  do {                        \
+    s = (x);                  \
+    if (s != MBAR_OK) return fail(s); \
+  } while (0)
+  TRYC(dalloc_t(c, &c->Nk_d, K));
+  TRYC(dalloc_t(c, &c->logN_d, K));
+  TRYC(h2d(c, c->Nk_d, c->Nk_h.data(), K));
+  TRYC(h2d(c, c->logN_d, logN.data(), K));
+  for (double** p : {&c->f, &c->fs, &c->ft, &c->fts, &c->g, &c->gt, &c->Q, &c->delta}) TRYC(dalloc_t(c, p, K));
+  TRYC(dalloc_t(c, &c->s, 1));
+  TRYC(dalloc_t(c, &c->s2, 1));
+  TRYC(dalloc_t(c, &c->hess, K * K));
+  TRYC(dalloc_t(c, &c->info, 1));
+  TRYC(dalloc_t(c, &c->bad, 1));
+  TRYC(dalloc_t(c, &c->count, 1));
+  TRYC(dalloc_t(c, &c->nb_dev, 1));
+  void* ctrl = nullptr;
+  TRYC(dalloc(c, &ctrl, sizeof(Ctrl)));
+  c->ctrl = static_cast<Ctrl*>(ctrl);
+  if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+  if (cudaMemsetAsync(c->bad, 0, sizeof(int), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+  if (cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+  TRYC(dalloc(c, &c->v, static_cast<size_t>(K) * c->ld * c->dtype));
+  TRYC(dalloc(c, &c->logden, static_cast<size_t>(N) * c->dtype));
+  TRYC(dalloc_t(c, &c->perm, N));
+  TRYC(dalloc_t(c, &c->seg, N));
+  TRYC(dalloc_t(c, &c->start, N + 1));
+  TRYC(dalloc_t(c, &c->phi0, N));
+  TRYC(dalloc_t(c, &c->phi_sorted, N));
+  // the samples of u_kn on the device in FP64
+  const double* u_dev = u_kn;
+  double* u_tmp = nullptr;
+  if (!u_on_device) {
+    TRYC(dalloc_t(c, &u_tmp, K * N));
+    if (cudaMemcpyAsync(u_tmp, u_kn, K * N * sizeof(double), cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
+      dfree(c, u_tmp);
+      return fail(cuda_status(cudaGetLastError(), "u_kn upload"));
+    }
+    u_dev = u_tmp;
+  }
+  if (c->dtype == 4) {
+    s = dalloc_t(c, &c->cshift, N);
+    if (s == MBAR_OK) s = shift_to_fp32(u_dev, K, N, N, c->cshift, static_cast<float*>(c->v), c->ld, c->bad, c->st);
+  } else {
+    s = copy_fp64_checked(u_dev, K, N, N, static_cast<double*>(c->v), c->ld, c->bad, c->st);
+  }
+  if (s == MBAR_OK && cudaMemcpyAsync(c->phi0, u_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+    s = MBAR_ECUDA;
+  {
+    // identity permutation
+    std::vector<int32_t> id(N);
+    std::iota(id.begin(), id.end(), 0);
+    if (s == MBAR_OK && cudaMemcpyAsync(c->perm, id.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      s = MBAR_ECUDA;
+    int bad = 0;
+    if (s == MBAR_OK && cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+      s = MBAR_ECUDA;
+    if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+    if (s == MBAR_OK && bad) {
+      set_error("mbar_create: u_kn has non-finite entries");
+      s = MBAR_EINVAL;
+    }
+  }
+  dfree(c, u_tmp);
+  if (s == MBAR_ECUDA) set_error("mbar_create: %s", cudaGetErrorString(cudaGetLastError()));
+  if (s != MBAR_OK) return fail(s);
+  // LSE scratch sized for the widest grid of this K
+  {
+    const LsePlan pl = lse_plan(K, N, c->dtype);
+    c->scratch_bytes = static_cast<size_t>(pl.grid) * K * sizeof(double) + 256;
+    TRYC(dalloc(c, &c->scratch, c->scratch_bytes));
+    if (cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+  }
+  c->full.binned = false;
+  c->full.n = N;
+  c->full.ld = c->ld;
+  c->full.v = c->v;
+  c->full.n_sched = N;
+  TRYC(level_tmap(c, &c->full));
+  c->cur = c->full;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "mbar_create"));
+#undef TRYC
+  *out = c;
+  return MBAR_OK;
+}
+
+mbar_status mbar_set_coordinate(mbar_ctx* c, const double* phi, int32_t phi_on_device) {
+  CHECK_CTX(c);
+  if (!phi) {
+    set_error("mbar_set_coordinate: phi is NULL");
+    return MBAR_EINVAL;
+  }
+  double* pd = nullptr;
+  BUMBAR_TRY(dalloc_t(c, &pd, c->N));
+  cudaError_t e = cudaMemcpyAsync(pd, phi, c->N * sizeof(double),
+                                  phi_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st);
+  int bad = 0;
+  mbar_status s = e == cudaSuccess ? MBAR_OK : cuda_status(e, "phi upload");
+  if (s == MBAR_OK) s = cudaMemsetAsync(c->bad, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
+  if (s == MBAR_OK) s = check_finite(pd, c->N, c->bad, c->st);
+  if (s == MBAR_OK && cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    s = MBAR_ECUDA;
+  if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+  if (s == MBAR_OK && bad) {
+    set_error("mbar_set_coordinate: phi has non-finite entries");
+    s = MBAR_EINVAL;
+  }
+  if (s == MBAR_OK) s = set_coordinate_dev(c, pd);
+  dfree(c, pd);
+  return s;
+}
+
+mbar_status mbar_bin(mbar_ctx* c, double h, int64_t* n_bins_out) {
+  CHECK_CTX(c);
+  if (!(h >= 0.0) || !std::isfinite(h)) {
+    set_error("mbar_bin: h must be finite and >= 0");
+    return MBAR_EINVAL;
+  }
+  BUMBAR_TRY(ensure_sorted(c));
+  if (h == 0.0) {
+    level_free(c, &c->cur);
+    c->cur = c->full;
+  } else {
+    if ((c->phi_hi - c->phi_lo) / h > kMaxIndex) {
+      set_error("mbar_bin: width too small for exact bin indices (range/h > 2^52)");
+      return MBAR_EINVAL;
+    }
+    Level L;
+    BUMBAR_TRY(make_level_w(c, h, &L));
+    level_free(c, &c->cur);
+    c->cur = L;
+  }
+  if (n_bins_out) *n_bins_out = c->cur.n;
+  return MBAR_OK;
+}
+
+mbar_status mbar_bin_count(mbar_ctx* c, int64_t n, double* w_out, int64_t* n_bins_out) {
+  CHECK_CTX(c);
+  if (n < 1) {
+    set_error("mbar_bin_count: n must be >= 1");
+    return MBAR_EINVAL;
+  }
+  double w = 0.0;
+  bool found = false;
+  BUMBAR_TRY(width_search(c, n, &w, &found));
+  if (!found) {
+    level_free(c, &c->cur);
+    c->cur = c->full;
+    if (w_out) *w_out = 0.0;
+  } else {
+    Level L;
+    BUMBAR_TRY(make_level_w(c, w, &L));
+    level_free(c, &c->cur);
+    c->cur = L;
+    if (w_out) *w_out = w;
+  }
+  if (n_bins_out) *n_bins_out = c->cur.n;
+  return MBAR_OK;
+}
+
+mbar_status mbar_get_bins(mbar_ctx* c, int64_t* keys, int64_t* H, double* u_kp) {
+  CHECK_CTX(c);
+  if (!c->cur.binned) {
+    set_error("mbar_get_bins: the current level is unbinned");
+    return MBAR_ESTATE;
+  }
+  const int64_t nb = c->cur.n;
+  if (keys) BUMBAR_CUDA(cudaMemcpyAsync(keys, c->cur.keys, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, c->st));
+  std::vector<int32_t> h32;
+  if (H) {
+    h32.resize(nb);
+    BUMBAR_CUDA(cudaMemcpyAsync(h32.data(), c->cur.H, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+  }
+  std::vector<unsigned char> raw;
+  if (u_kp) {
+    raw.resize(static_cast<size_t>(c->K) * c->cur.ld * c->dtype);
+    BUMBAR_CUDA(cudaMemcpyAsync(raw.data(), c->cur.v, raw.size(), cudaMemcpyDeviceToHost, c->st));
+  }
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  if (H)
+    for (int64_t b = 0; b < nb; ++b) H[b] = h32[b];
+  if (u_kp) {
+    for (int64_t k = 0; k < c->K; ++k)
+      for (int64_t b = 0; b < nb; ++b) {
+        const size_t idx = static_cast<size_t>(k) * c->cur.ld + b;
+        u_kp[k * nb + b] = c->dtype == 4 ? static_cast<double>(reinterpret_cast<float*>(raw.data())[idx])
+                                         : reinterpret_cast<double*>(raw.data())[idx];
+      }
+  }
+  return MBAR_OK;
+}
+
+mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double* grad, double* s_out,
+                          double* logden) {
+  CHECK_CTX(c);
+  if (!f_in) {
+    set_error("mbar_sci_step: f_in is NULL");
+    return MBAR_EINVAL;
+  }
+  const int64_t K = c->K;
+  BUMBAR_TRY(upload_f(c, f_in, c->ft));
+  BUMBAR_TRY(run_lse(c, c->cur, c->ft, kLseModeSci, c->fts, c->gt, c->s2, 0.0, 0, logden ? c->logden : nullptr));
+  BUMBAR_TRY(check_device_errors(c));
+  if (f_out) BUMBAR_TRY(d2h(c, f_out, c->fts, K));
+  if (grad) BUMBAR_TRY(d2h(c, grad, c->gt, K));
+  if (s_out) BUMBAR_TRY(d2h(c, s_out, c->s2, 1));
+  const int64_t n = c->cur.n;
+  std::vector<unsigned char> raw;
+  std::vector<int32_t> perm;
+  std::vector<double> shift;
+  if (logden) {
+    raw.resize(static_cast<size_t>(n) * c->dtype);
+    BUMBAR_CUDA(cudaMemcpyAsync(raw.data(), c->logden, raw.size(), cudaMemcpyDeviceToHost, c->st));
+    if (!c->cur.binned) {
+      perm.resize(n);
+      BUMBAR_CUDA(cudaMemcpyAsync(perm.data(), c->perm, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+      if (c->cshift) {
+        shift.resize(n);
+        BUMBAR_CUDA(cudaMemcpyAsync(shift.data(), c->cshift, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      }
+    }
+  }
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  if (logden) {
+    for (int64_t i = 0; i < n; ++i) {
+      double v = c->dtype == 4 ? static_cast<double>(reinterpret_cast<float*>(raw.data())[i])
+                               : reinterpret_cast<double*>(raw.data())[i];
+      if (!c->cur.binned) {
+        if (c->cshift) v -= shift[i];  // v_kn = u_kn - c_n  =>  logden(u) = logden(v) - c_n
+        logden[perm[i]] = v;
+      } else {
+        logden[i] = v;
+      }
+    }
+  }
+  return MBAR_OK;
+}
+
+mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
+  CHECK_CTX(c);
+  if (!f_in || !hess_out) {
+    set_error("mbar_hessian: null pointer argument");
+    return MBAR_EINVAL;
+  }
+  const int64_t K = c->K;
+  const Level& L = c->cur;
+  BUMBAR_TRY(upload_f(c, f_in, c->ft));
+  BUMBAR_TRY(run_lse(c, L, c->ft, kLseModePass, nullptr, nullptr, nullptr, 0.0, 0, c->logden));
+  const size_t htmp = hessian_tmp_bytes(K, L.n);
+  void* tmp = nullptr;
+  BUMBAR_TRY(dalloc(c, &tmp, htmp));
+  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, tmp, htmp, c->st);
+  if (s == MBAR_OK) s = check_device_errors(c);
+  if (s == MBAR_OK) s = d2h(c, hess_out, c->hess, K * K);
+  if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+  dfree(c, tmp);
+  return s;
+}
+
+mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, double* step_max_abs) {
+  CHECK_CTX(c);
+  if (!f_in) {
+    set_error("mbar_newton_step: f_in is NULL");
+    return MBAR_EINVAL;
+  }
+  const int64_t K = c->K;
+  const Level& L = c->cur;
+  BUMBAR_TRY(upload_f(c, f_in, c->ft));
+  BUMBAR_TRY(run_lse(c, L, c->ft, kLseModeSci, c->fts, c->gt, c->s2, 0.0, 0, c->logden));
+  const size_t htmp = hessian_tmp_bytes(K, L.n), ntmp = newton_tmp_bytes(K);
+  void* tmp = nullptr;
+  BUMBAR_TRY(dalloc(c, &tmp, std::max(htmp, ntmp)));
+  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, tmp, htmp, c->st);
+  if (s == MBAR_OK) s = cudaMemsetAsync(c->info, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
+  if (s == MBAR_OK) s = newton_solve(c->hess, K, c->gt, c->delta, c->info, tmp, ntmp, c->st);
+  if (s == MBAR_OK) s = vec_add_gauge(c->ft, c->delta, c->fts, K, c->st);
+  std::vector<double> d(K);
+  int info = 0;
+  if (s == MBAR_OK) s = check_device_errors(c);
+  if (s == MBAR_OK) s = d2h(c, d.data(), c->delta, K);
+  if (s == MBAR_OK && f_out) s = d2h(c, f_out, c->fts, K);
+  if (s == MBAR_OK && cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    s = MBAR_ECUDA;
+  if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+  dfree(c, tmp);
+  BUMBAR_TRY(s);
+  if (step_max_abs) *step_max_abs = max_abs(d);
+  if (info) {
+    set_error("mbar_newton_step: reduced Hessian not positive definite");
+    return MBAR_ENOTCONV;
+  }
+  return MBAR_OK;
+}
+
+mbar_status mbar_solve(mbar_ctx* c, const double* f_init, mbar_report* report) {
+  CHECK_CTX(c);
+  mbar_report rep{};
+  const int64_t K = c->K;
+  if (f_init) {
+    std::vector<double> f0(f_init, f_init + K);
+    for (int64_t k = K - 1; k >= 0; --k) f0[k] -= f0[0];
+    BUMBAR_TRY(h2d(c, c->f, f0.data(), K));
+  } else {
+    BUMBAR_CUDA(cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st));
+  }
+  mbar_status s = MBAR_OK;
+  if (K > 1) {
+    if (c->opts.use_binning)
+      s = algorithm1(c, &rep);
+    else
+      s = plain_warmup(c, &rep);
+    if (s == MBAR_OK) s = newton_phase(c, &rep);
+  }
+  mbar_status s2 = d2h(c, c->f_h.data(), c->f, K);
+  if (s2 == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s2 = MBAR_ECUDA;
+  if (report) *report = rep;
+  if (s != MBAR_OK) return s;
+  return s2;
+}
+
+mbar_status mbar_free_energies(mbar_ctx* c, double* f_out) {
+  CHECK_CTX(c);
+  if (!f_out) {
+    set_error("mbar_free_energies: f_out is NULL");
+    return MBAR_EINVAL;
+  }
+  std::copy(c->f_h.begin(), c->f_h.end(), f_out);
+  return MBAR_OK;
+}
+
+mbar_status mbar_device_bytes(mbar_ctx* c, int64_t* bytes) {
+  CHECK_CTX(c);
+  if (bytes) *bytes = c->bytes;
+  return MBAR_OK;
+}
+
+mbar_status mbar_set_timing(mbar_ctx* c, int32_t enable) {
+  CHECK_CTX(c);
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  for (auto& r : c->recs) {
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  c->timing = enable != 0;
+  return MBAR_OK;
+}
+
+mbar_status mbar_get_timing(mbar_ctx* c, int32_t kind, int64_t* launches, double* total_ms, double* bytes) {
+  CHECK_CTX(c);
+  BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+  int64_t n = 0;
+  double ms = 0.0, by = 0.0;
+  for (auto& r : c->recs) {
+    if (r.kind != kind) continue;
+    float t = 0.f;
+    BUMBAR_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    ++n;
+    ms += t;
+    by += r.bytes;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  if (bytes) *bytes = by;
+  return MBAR_OK;
+}
+
+mbar_status mbar_kernel_launches(int64_t* count) {
+  if (!count) {
+    set_error("mbar_kernel_launches: count is NULL");
+    return MBAR_EINVAL;
+  }
+  *count = launches_so_far();
+  return MBAR_OK;
+}
+
+mbar_status mbar_destroy(mbar_ctx* c) {
+  if (!c) return MBAR_OK;
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  level_free(c, &c->cur);
+  void* ptrs[] = {c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->f,
+                  c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->s,          c->s2,
+                  c->hess, c->delta,  c->info,  c->bad,    c->ctrl,  c->logden,  c->scratch,    c->seg,
+                  c->start, c->count, c->nb_dev};
+  for (void* p : ptrs) dfree(c, p);
+  cudaStreamSynchronize(c->st);
+  delete c;
+  return MBAR_OK;
+}
+
+size_t mbar_lse_scratch_bytes(int64_t K, int64_t n, int32_t dtype_bytes) {
+  if (K < 1 || K > 1024 || n < 1 || (dtype_bytes != 4 && dtype_bytes != 8)) return 0;
+  return lse_scratch_bytes(K, n, dtype_bytes) + 256;
+}
+
+mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
+                          const double* log_N, const int32_t* H, double* Q, void* logden, void* scratch,
+                          size_t scratch_bytes, void* stream) {
+  if (!v || !f || !log_N || !Q || !scratch) {
+    set_error("mbar_lse_pass: null pointer argument");
+    return MBAR_EINVAL;
+  }
+  if (dtype_bytes != 4 && dtype_bytes != 8) {
+    set_error("mbar_lse_pass: dtype_bytes must be 4 or 8");
+    return MBAR_EINVAL;
+  }
+  if (K < 1 || n < 1 || ld < n || n > 2000000000LL) {
+    set_error("mbar_lse_pass: bad sizes K=%lld n=%lld ld=%lld", (long long)K, (long long)n, (long long)ld);
+    return MBAR_EINVAL;
+  }
+  if (K > 1024) {
+    set_error("mbar_lse_pass: K=%lld exceeds 1024", (long long)K);
+    return MBAR_EUNSUPPORTED;
+  }
+  if ((reinterpret_cast<uintptr_t>(scratch) & 15) != 0 || scratch_bytes < mbar_lse_scratch_bytes(K, n, dtype_bytes)) {
+    set_error("mbar_lse_pass: scratch must be 16-byte aligned and at least mbar_lse_scratch_bytes()");
+    return MBAR_EINVAL;
+  }
+  CUtensorMap map;
+  const int C = 128 / dtype_bytes;
+  const int box_rows = static_cast<int>(std::min<int64_t>(256, round_up(K, 8)));
+  BUMBAR_TRY(make_tmap_2d(&map, v, dtype_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                          dtype_bytes, K, n, ld, C, box_rows));
+  const LsePlan pl = lse_plan(K, n, dtype_bytes);
+  LseParams p{};
+  p.K = static_cast<int>(K);
+  p.n = static_cast<int>(n);
+  p.f = f;
+  p.logN = log_N;
+  p.H = H;
+  unsigned char* sc = static_cast<unsigned char*>(scratch);
+  p.counter = reinterpret_cast<unsigned*>(sc);
+  p.err = reinterpret_cast<unsigned*>(sc + 4);
+  p.partials = reinterpret_cast<double*>(sc + 256);
+  p.Q = Q;
+  p.logden = logden;
+  p.mode = kLseModePass;
+  return lse_launch(map, pl, p, dtype_bytes, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

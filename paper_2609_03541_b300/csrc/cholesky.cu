@@ -1,0 +1,148 @@
+// Gauge-fixed Newton solve in FP64 on the device: the Hessian annihilates
+// the all-ones vector (f is defined up to a constant), so state 0 is held
+// fixed (delta_0 = 0) and the remaining (K-1) x (K-1) block, symmetric
+// positive definite for connected data, is factored by a blocked
+// right-looking Cholesky (32-wide panels: diagonal block in shared memory,
+// panel triangular solve, trailing symmetric update) followed by forward
+// and backward substitution.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bumbar {
+
+namespace {
+
+constexpr int NB = 32;
+
+__global__ void copy_reduced(const double* __restrict__ hess, int64_t K, const double* __restrict__ g,
+                             double* __restrict__ A, double* __restrict__ b) {
+  const int64_t m = K - 1;
+  const int64_t i = blockIdx.x;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) A[i * m + j] = hess[(i + 1) * K + (j + 1)];
+  if (threadIdx.x == 0) b[i] = -g[i + 1];
+}
+
+__global__ void potrf_block(double* __restrict__ A, int64_t m, int64_t kb, int nb, int* info) {
+  __shared__ double L[NB][NB + 1];
+  const int t = threadIdx.x;
+  const int r = t / NB, c = t % NB;
+  if (r < nb && c < nb) L[r][c] = A[(kb + r) * m + kb + c];
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (t == 0) {
+      const double d = L[j][j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        atomicOr(info, 1);
+        L[j][j] = 1.0;
+      } else {
+        L[j][j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (t > j && t < nb) L[t][j] /= L[j][j];
+    __syncthreads();
+    if (r > j && r < nb && c > j && c <= r) L[r][c] -= L[r][j] * L[c][j];
+    __syncthreads();
+  }
+  if (r < nb && c < nb && c <= r) A[(kb + r) * m + kb + c] = L[r][c];
+}
+
+__global__ void trsm_panel(double* __restrict__ A, int64_t m, int64_t kb, int nb) {
+  __shared__ double L[NB][NB + 1];
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    L[r][c] = (r < nb && c < nb && c <= r) ? A[(kb + r) * m + kb + c] : 0.0;
+  }
+  __syncthreads();
+  const int64_t i = kb + nb + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double y[NB];
+  for (int j = 0; j < nb; ++j) {
+    double s = A[i * m + kb + j];
+    for (int l = 0; l < j; ++l) s -= y[l] * L[j][l];
+    y[j] = s / L[j][j];
+  }
+  for (int j = 0; j < nb; ++j) A[i * m + kb + j] = y[j];
+}
+
+__global__ void syrk_update(double* __restrict__ A, int64_t m, int64_t kb, int nb) {
+  const int64_t base = kb + nb;
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (tj > ti) return;
+  __shared__ double Pi[NB][NB + 1];
+  __shared__ double Pj[NB][NB + 1];
+  const int r = threadIdx.x / NB, c = threadIdx.x % NB;  // 1024 threads
+  const int64_t i = base + ti * NB + r, jr = base + tj * NB + r;
+  Pi[r][c] = (i < m && c < nb) ? A[i * m + kb + c] : 0.0;
+  Pj[r][c] = (jr < m && c < nb) ? A[jr * m + kb + c] : 0.0;
+  __syncthreads();
+  const int64_t j = base + tj * NB + c;
+  if (i < m && j < m && j <= i) {
+    double s = 0.0;
+    for (int l = 0; l < nb; ++l) s += Pi[r][l] * Pj[c][l];
+    A[i * m + j] -= s;
+  }
+}
+
+// Single-block forward then backward substitution with the lower factor.
+__global__ void chol_solve(const double* __restrict__ A, int64_t m, double* __restrict__ b, double* __restrict__ delta) {
+  for (int64_t j = 0; j < m; ++j) {
+    __syncthreads();
+    const double yj = b[j] / A[j * m + j];
+    __syncthreads();
+    if (threadIdx.x == 0) b[j] = yj;
+    for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) b[i] -= A[i * m + j] * yj;
+  }
+  for (int64_t j = m - 1; j >= 0; --j) {
+    __syncthreads();
+    const double xj = b[j] / A[j * m + j];
+    __syncthreads();
+    if (threadIdx.x == 0) b[j] = xj;
+    for (int64_t i = threadIdx.x; i < j; i += blockDim.x) b[i] -= A[j * m + i] * xj;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) delta[i + 1] = b[i];
+  if (threadIdx.x == 0) delta[0] = 0.0;
+}
+
+}  // namespace
+
+size_t newton_tmp_bytes(int64_t K) { return round_up((K - 1) * (K - 1) * 8, 256) + round_up(K * 8, 256) + 256; }
+
+mbar_status newton_solve(double* hess, int64_t K, const double* g, double* delta, int* info, void* tmp,
+                         size_t tmp_bytes, cudaStream_t st) {
+  if (K == 1) {
+    BUMBAR_CUDA(cudaMemsetAsync(delta, 0, sizeof(double), st));
+    return MBAR_OK;
+  }
+  if (tmp_bytes < newton_tmp_bytes(K)) {
+    set_error("newton_solve: scratch too small");
+    return MBAR_EINVAL;
+  }
+  const int64_t m = K - 1;
+  double* A = static_cast<double*>(tmp);
+  double* b = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + round_up(m * m * 8, 256));
+  copy_reduced<<<static_cast<unsigned>(m), kThreads, 0, st>>>(hess, K, g, A, b);
+  count_launches(1);
+  for (int64_t kb = 0; kb < m; kb += NB) {
+    const int nb = static_cast<int>(std::min<int64_t>(NB, m - kb));
+    potrf_block<<<1, NB * NB, 0, st>>>(A, m, kb, nb, info);
+    count_launches(1);
+    const int64_t rest = m - kb - nb;
+    if (rest > 0) {
+      trsm_panel<<<static_cast<unsigned>(ceil_div(rest, 128)), 128, 0, st>>>(A, m, kb, nb);
+      count_launches(1);
+      const unsigned nt = static_cast<unsigned>(ceil_div(rest, NB));
+      syrk_update<<<dim3(nt, nt), NB * NB, 0, st>>>(A, m, kb, nb);
+      count_launches(1);
+    }
+  }
+  chol_solve<<<1, 1024, 0, st>>>(A, m, b, delta);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+}  // namespace bumbar

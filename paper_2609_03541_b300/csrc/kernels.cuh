@@ -1,0 +1,118 @@
+// Internal kernel interfaces of the BU-MBAR library (not part of the C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace bumbar {
+
+// Device control block of the iteration driver (one per context).
+struct Ctrl {
+  int done;       // first loop of Algorithm 1: set when s < eps
+  int nonfinite;  // an update produced a non-finite f
+  int iters;      // SCI steps executed by the guarded kernels
+  int pad;
+  double last_s;  // relative step (Eq. 2) of the last SCI step
+};
+
+constexpr int kLseModePass = 0;  // Q (and logden) only
+constexpr int kLseModeSci = 1;   // + Eq. 1 update, gauge, gradient, Eq. 2
+
+struct LseParams {
+  int K, n;
+  int num_strips, box_rows, nbox, stages;  // filled by lse_launch from the plan
+  const double* f;                         // [K] current f
+  const double* logN;                      // [K]
+  const int32_t* H;                        // [n] counts or nullptr (all ones)
+  double* partials;                        // [grid x K] scratch
+  unsigned* counter;                       // scratch: completion counter (zero between passes)
+  unsigned* err;                           // scratch: timeout count
+  double* Q;                               // [K] out
+  void* logden;                            // [n] out (dtype of v) or nullptr
+  int mode;
+  // SCI epilogue
+  const double* Nk;  // [K] sample counts as doubles
+  double* f_out;     // [K]
+  double* g_out;     // [K] or nullptr
+  double* s_out;     // scalar or nullptr
+  Ctrl* ctrl;        // or nullptr
+  double eps;        // > 0: set ctrl->done when s < eps
+  int skip_if_done;  // return at once if ctrl->done
+};
+
+struct LsePlan {
+  int C, num_strips, box_rows, nbox, stages, grid;
+  size_t smem;
+};
+
+LsePlan lse_plan(int64_t K, int64_t n, int dtype_bytes);
+size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes);
+mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm, int dtype_bytes,
+                       cudaStream_t stream);
+
+// ---- binning (binning.cu) ----
+// Stable LSD radix sort of phi (binary64, order-preserving key transform);
+// writes phi_sorted[N] and perm[N] (sorted position -> original sample).
+mbar_status sort_coordinate(const double* phi, int64_t N, double* phi_sorted, int32_t* perm, void* tmp,
+                            size_t tmp_bytes, cudaStream_t stream);
+size_t sort_tmp_bytes(int64_t N);
+
+// Count of nonempty bins g(w) over sorted phi (anchor phi_sorted[0]);
+// result left in *count_dev (int64). tmp: >= 8 bytes.
+mbar_status count_bins(const double* phi_sorted, int64_t N, double w, unsigned long long* count_dev,
+                       cudaStream_t stream);
+
+// Histogram at width w over sorted phi: per sorted sample its bin ordinal
+// seg[N] (0..nb-1), bin start offsets start[nb+1], counts H[nb] (int32),
+// keys[nb] (int64). nb is returned through *nb_dev. tmp sized by
+// hist_tmp_bytes.
+mbar_status build_histogram(const double* phi_sorted, int64_t N, double w, int32_t* seg, int32_t* start,
+                            int32_t* H, int64_t* keys, int32_t* nb_dev, void* tmp, size_t tmp_bytes,
+                            cudaStream_t stream);
+size_t hist_tmp_bytes(int64_t N);
+
+// Binned matrix: out[k][b] = mean over the bin's members of v[k][i]
+// (members are the contiguous sorted columns start[b]..start[b+1]-1).
+mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int64_t ld, const int32_t* seg,
+                      const int32_t* start, int64_t nb, void* out, int64_t ld_out, void* tmp, size_t tmp_bytes,
+                      cudaStream_t stream);
+size_t bin_means_tmp_bytes(int64_t K, int64_t N);
+
+// Column gather: out[k][i] = in[k][perm[i]] (row pitch ld for both).
+mbar_status gather_columns(const void* in, void* out, int dtype_bytes, int64_t K, int64_t N, int64_t ld,
+                           const int32_t* perm, cudaStream_t stream);
+
+// ---- data preparation (prep.cu) ----
+// Per-column minimum c[n] over the K rows of FP64 u (row pitch ldu), then
+// v[k][n] = float(u[k][n] - c[n]) with row pitch ldv. Also flags non-finite
+// entries in *bad.
+mbar_status shift_to_fp32(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, float* v, int64_t ldv,
+                          int* bad, cudaStream_t stream);
+mbar_status copy_fp64_checked(const double* u, int64_t K, int64_t N, int64_t ldu, double* v, int64_t ldv, int* bad,
+                              cudaStream_t stream);
+mbar_status check_finite(const double* x, int64_t n, int* bad, cudaStream_t stream);
+
+// ---- Hessian (hessian.cu) ----
+// G = sum_p H_p P_ip P_jp with P_ip = exp(a_i - v_ip - logden_p) (a = f + log N);
+// writes the FP64 Hessian hess[K x K] = Laplacian of G (off-diagonal -G_ij,
+// diagonal sum_{j != i} G_ij).
+mbar_status hessian(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
+                    const double* logN, const void* logden, const int32_t* H, double* hess, void* tmp,
+                    size_t tmp_bytes, cudaStream_t stream);
+size_t hessian_tmp_bytes(int64_t K, int64_t n);
+
+// ---- dense FP64 (cholesky.cu) ----
+// Solves A x = b for the (m x m) symmetric positive definite block
+// A = hess[1:,1:] (row pitch K) and b = -g[1:]; x written to delta[1:],
+// delta[0] = 0. Sets *info != 0 if a pivot is not positive.
+mbar_status newton_solve(double* hess, int64_t K, const double* g, double* delta, int* info, void* tmp,
+                         size_t tmp_bytes, cudaStream_t stream);
+size_t newton_tmp_bytes(int64_t K);
+
+// small helpers (prep.cu)
+mbar_status vec_add_gauge(const double* f, const double* d, double* out, int64_t K, cudaStream_t stream);
+
+}  // namespace bumbar

@@ -1,0 +1,90 @@
+// Data preparation on the device: validation of u_kn, the per-sample shift
+// of the mixed-precision store, and small vector updates.
+//
+// Mixed precision keeps v_kn = fl32(u_kn - c_n) with c_n = min_k u_kn: the
+// free energies are unchanged by any per-sample shift (the shift cancels
+// between numerator and denominator of Eq. 1), the stored magnitudes stay
+// small for the entries that carry weight, and every v_kn >= 0.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bumbar {
+
+namespace {
+
+__global__ void shift_fp32_kernel(const double* __restrict__ u, int64_t K, int64_t N, int64_t ldu,
+                                  double* __restrict__ c, float* __restrict__ v, int64_t ldv, int* bad) {
+  const int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double m = INFINITY;
+  bool ok = true;
+  for (int64_t k = 0; k < K; ++k) {
+    const double x = u[k * ldu + n];
+    ok &= static_cast<bool>(isfinite(x));
+    m = fmin(m, x);
+  }
+  if (!ok) {
+    atomicOr(bad, 1);
+    m = 0.0;
+  }
+  c[n] = m;
+  for (int64_t k = 0; k < K; ++k) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - m);
+}
+
+__global__ void copy_checked_kernel(const double* __restrict__ u, int64_t K, int64_t N, int64_t ldu,
+                                    double* __restrict__ v, int64_t ldv, int* bad) {
+  const int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t k = blockIdx.y;
+  if (n >= N) return;
+  const double x = u[k * ldu + n];
+  if (!isfinite(x)) atomicOr(bad, 1);
+  v[k * ldv + n] = x;
+}
+
+__global__ void finite_kernel(const double* __restrict__ x, int64_t n, int* bad) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(x[i])) atomicOr(bad, 1);
+}
+
+__global__ void add_gauge_kernel(const double* __restrict__ f, const double* __restrict__ d, double* __restrict__ out,
+                                 int64_t K) {
+  __shared__ double base;
+  if (threadIdx.x == 0) base = f[0] + d[0];
+  __syncthreads();
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) out[k] = (f[k] + d[k]) - base;
+}
+
+}  // namespace
+
+mbar_status shift_to_fp32(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, float* v, int64_t ldv,
+                          int* bad, cudaStream_t st) {
+  shift_fp32_kernel<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(u, K, N, ldu, c, v, ldv, bad);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+mbar_status copy_fp64_checked(const double* u, int64_t K, int64_t N, int64_t ldu, double* v, int64_t ldv, int* bad,
+                              cudaStream_t st) {
+  const dim3 g(static_cast<unsigned>(ceil_div(N, kThreads)), static_cast<unsigned>(K));
+  copy_checked_kernel<<<g, kThreads, 0, st>>>(u, K, N, ldu, v, ldv, bad);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+mbar_status check_finite(const double* x, int64_t n, int* bad, cudaStream_t st) {
+  finite_kernel<<<static_cast<unsigned>(ceil_div(n, kThreads)), kThreads, 0, st>>>(x, n, bad);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+mbar_status vec_add_gauge(const double* f, const double* d, double* out, int64_t K, cudaStream_t st) {
+  add_gauge_kernel<<<1, kThreads, 0, st>>>(f, d, out, K);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+}  // namespace bumbar

@@ -1,0 +1,302 @@
+"""ctypes binding of ``libbumbar.so`` (argument marshalling only).
+
+Every computation happens inside the library's CUDA kernels. The names
+follow the C ABI in ``include/bumbar.h``: ``Context`` wraps an ``mbar_ctx``
+and its methods call ``mbar_create / mbar_set_coordinate / mbar_bin /
+mbar_bin_count / mbar_get_bins / mbar_sci_step / mbar_hessian /
+mbar_newton_step / mbar_solve / mbar_free_energies / mbar_destroy``;
+``lse_pass`` calls the stateless ``mbar_lse_pass``.
+
+Loading fails loudly (``LibraryMissing``) when the library has not been
+built; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbumbar.so")
+
+MBAR_FP64 = 0
+MBAR_MIXED = 1
+
+STATUS = {
+    0: "MBAR_OK", 1: "MBAR_EINVAL", 2: "MBAR_ENOMEM", 3: "MBAR_ECUDA", 4: "MBAR_ENOTCONV",
+    5: "MBAR_ESTATE", 6: "MBAR_ETIMEOUT", 7: "MBAR_EUNSUPPORTED",
+}
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class MbarError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("n0", ctypes.c_int32),
+        ("eps", ctypes.c_double),
+        ("inc", ctypes.c_int32),
+        ("n_intermediate", ctypes.c_int32),
+        ("h0", ctypes.c_double),
+        ("use_binning", ctypes.c_int32),
+        ("f_tol", ctypes.c_double),
+        ("warm_tol", ctypes.c_double),
+        ("max_newton", ctypes.c_int32),
+        ("max_sci", ctypes.c_int32),
+    ]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [
+        ("iters_first_loop", ctypes.c_int64),
+        ("iters_second_loop", ctypes.c_int64),
+        ("iters_newton", ctypes.c_int64),
+        ("newton_fallbacks", ctypes.c_int64),
+        ("n_rebins", ctypes.c_int64),
+        ("final_bins", ctypes.c_int64),
+        ("max_abs_grad", ctypes.c_double),
+        ("last_step", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+_SIGNATURES = {
+    "mbar_opts_default": ([ctypes.POINTER(Opts), ctypes.c_int32], ctypes.c_int),
+    "mbar_create": ([ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int64, _i64p, _vp, ctypes.c_int32,
+                     ctypes.POINTER(Opts), _vp], ctypes.c_int),
+    "mbar_set_coordinate": ([_vp, _vp, ctypes.c_int32], ctypes.c_int),
+    "mbar_bin": ([_vp, ctypes.c_double, _i64p], ctypes.c_int),
+    "mbar_bin_count": ([_vp, ctypes.c_int64, _dp, _i64p], ctypes.c_int),
+    "mbar_get_bins": ([_vp, _i64p, _i64p, _dp], ctypes.c_int),
+    "mbar_sci_step": ([_vp, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
+    "mbar_hessian": ([_vp, _dp, _dp], ctypes.c_int),
+    "mbar_newton_step": ([_vp, _dp, _dp, _dp], ctypes.c_int),
+    "mbar_solve": ([_vp, _dp, ctypes.POINTER(Report)], ctypes.c_int),
+    "mbar_free_energies": ([_vp, _dp], ctypes.c_int),
+    "mbar_destroy": ([_vp], ctypes.c_int),
+    "mbar_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "mbar_last_error": ([], ctypes.c_char_p),
+    "mbar_device_bytes": ([_vp, _i64p], ctypes.c_int),
+    "mbar_set_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "mbar_get_timing": ([_vp, ctypes.c_int32, _i64p, _dp, _dp], ctypes.c_int),
+    "mbar_kernel_launches": ([_i64p], ctypes.c_int),
+    "mbar_lse_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32], ctypes.c_size_t),
+    "mbar_lse_pass": ([_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
+                       _vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
+}
+
+
+def lib():
+    """The loaded library (loads it on first use)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LibraryMissing(
+                f"{LIB_PATH} is not built; run `python -m paper_2609_03541_b300.build` (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().mbar_last_error().decode(errors="replace")
+        raise MbarError(status, msg)
+
+
+def default_opts(precision: int = MBAR_MIXED, **overrides) -> Opts:
+    o = Opts()
+    _check(lib().mbar_opts_default(ctypes.byref(o), int(precision)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _device_ptr(x):
+    """(pointer, on_device) for a numpy array or a CUDA torch tensor."""
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        return ctypes.c_void_p(x.data_ptr()), 1
+    return None, 0
+
+
+class Context:
+    """One MBAR problem resident on the device (``mbar_ctx``)."""
+
+    def __init__(self, u_kn, N_k, precision: int = MBAR_MIXED, opts: Opts | None = None, stream=None):
+        self._h = ctypes.c_void_p()
+        Nk = np.ascontiguousarray(np.asarray(N_k, dtype=np.int64))
+        K = int(Nk.shape[0])
+        dptr, on_dev = _device_ptr(u_kn)
+        if on_dev:
+            if u_kn.dtype.__repr__() != "torch.float64" or not u_kn.is_contiguous():
+                raise ValueError("device u_kn must be a contiguous float64 CUDA tensor")
+            N = int(u_kn.shape[1])
+            uptr = dptr
+            self._keep = u_kn
+        else:
+            u = _f64(u_kn)
+            N = int(u.shape[1])
+            uptr = ctypes.c_void_p(u.ctypes.data)
+            self._keep = u
+        if opts is None:
+            opts = default_opts(precision)
+        else:
+            opts.precision = precision
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else 0))
+        _check(lib().mbar_create(ctypes.byref(self._h), K, N, Nk.ctypes.data_as(_i64p), uptr, on_dev,
+                                 ctypes.byref(opts), st))
+        self._keep = None
+        self.K, self.N, self.precision = K, N, precision
+
+    # -- binning ---------------------------------------------------------
+    def set_coordinate(self, phi):
+        dptr, on_dev = _device_ptr(phi)
+        if on_dev:
+            _check(lib().mbar_set_coordinate(self._h, dptr, 1))
+        else:
+            p = _f64(phi)
+            _check(lib().mbar_set_coordinate(self._h, ctypes.c_void_p(p.ctypes.data), 0))
+
+    def bin(self, h: float) -> int:
+        nb = ctypes.c_int64()
+        _check(lib().mbar_bin(self._h, float(h), ctypes.byref(nb)))
+        return nb.value
+
+    def bin_count(self, n: int):
+        w = ctypes.c_double()
+        nb = ctypes.c_int64()
+        _check(lib().mbar_bin_count(self._h, int(n), ctypes.byref(w), ctypes.byref(nb)))
+        return w.value, nb.value
+
+    def get_bins(self, n_bins: int):
+        keys = np.empty(n_bins, dtype=np.int64)
+        H = np.empty(n_bins, dtype=np.int64)
+        u = np.empty((self.K, n_bins), dtype=np.float64)
+        _check(lib().mbar_get_bins(self._h, keys.ctypes.data_as(_i64p), H.ctypes.data_as(_i64p), _ptr(u)))
+        return keys, H, u
+
+    # -- evaluation ----------------------------------------------------------
+    def sci_step(self, f, n_cols: int | None = None, want_logden: bool = False):
+        f = _f64(f)
+        fo = np.empty(self.K)
+        g = np.empty(self.K)
+        s = np.empty(1)
+        ld = np.empty(n_cols if n_cols is not None else self.N) if want_logden else None
+        _check(lib().mbar_sci_step(self._h, _ptr(f), _ptr(fo), _ptr(g), _ptr(s),
+                                   _ptr(ld) if ld is not None else None))
+        return (fo, g, float(s[0]), ld) if want_logden else (fo, g, float(s[0]))
+
+    def hessian(self, f):
+        f = _f64(f)
+        H = np.empty((self.K, self.K))
+        _check(lib().mbar_hessian(self._h, _ptr(f), _ptr(H)))
+        return H
+
+    def newton_step(self, f):
+        f = _f64(f)
+        fo = np.empty(self.K)
+        st = ctypes.c_double()
+        _check(lib().mbar_newton_step(self._h, _ptr(f), _ptr(fo), ctypes.byref(st)))
+        return fo, st.value
+
+    def solve(self, f_init=None) -> Report:
+        rep = Report()
+        fi = _f64(f_init) if f_init is not None else None
+        _check(lib().mbar_solve(self._h, _ptr(fi) if fi is not None else None, ctypes.byref(rep)))
+        return rep
+
+    def free_energies(self) -> np.ndarray:
+        f = np.empty(self.K)
+        _check(lib().mbar_free_energies(self._h, _ptr(f)))
+        return f
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        _check(lib().mbar_device_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def set_timing(self, enable: bool):
+        _check(lib().mbar_set_timing(self._h, int(bool(enable))))
+
+    def timing(self, kind: int):
+        """(launches, total device ms, streamed bytes) of one launch kind:
+        0 unbinned LSE pass, 1 Hessian, 2 Newton solve."""
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        _check(lib().mbar_get_timing(self._h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+        return n.value, ms.value, by.value
+
+    def close(self):
+        if self._h:
+            _check(lib().mbar_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    n = ctypes.c_int64()
+    _check(lib().mbar_kernel_launches(ctypes.byref(n)))
+    return n.value
+
+
+def lse_scratch_bytes(K: int, n: int, dtype_bytes: int) -> int:
+    return int(lib().mbar_lse_scratch_bytes(int(K), int(n), int(dtype_bytes)))
+
+
+def lse_pass(v, f, log_N, Q, H=None, logden=None, scratch=None, stream=None):
+    """Stateless fused LSE pass over a resident K x n CUDA tensor ``v``
+    (float32 or float64, row pitch = v.stride(0)). All arguments are CUDA
+    tensors; ``scratch`` is a uint8 tensor of ``lse_scratch_bytes`` bytes,
+    zero before its first use."""
+    K, n = int(v.shape[0]), int(v.shape[1])
+    eb = int(v.element_size())
+    st = stream.cuda_stream if stream is not None else 0
+    _check(lib().mbar_lse_pass(
+        ctypes.c_void_p(v.data_ptr()), eb, K, n, int(v.stride(0)),
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(log_N.data_ptr()),
+        ctypes.c_void_p(H.data_ptr()) if H is not None else None,
+        ctypes.c_void_p(Q.data_ptr()),
+        ctypes.c_void_p(logden.data_ptr()) if logden is not None else None,
+        ctypes.c_void_p(scratch.data_ptr()), int(scratch.numel()), ctypes.c_void_p(st)))

@@ -1,0 +1,96 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+symbol the header declares, its structs match the binding, and the host-side
+argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_2609_03541_b300 import build as B
+from paper_2609_03541_b300 import mbar as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bumbar.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return M.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mbar_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["mbar_create", "mbar_bin", "mbar_solve", "mbar_free_energies", "mbar_destroy",
+                     "mbar_sci_step", "mbar_hessian", "mbar_newton_step", "mbar_lse_pass"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", M.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(mbar_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    assert set(M._SIGNATURES) <= exported
+
+
+def test_struct_layout_matches_binding():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "bumbar.h"
+int main(void){
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mbar_opts), offsetof(mbar_opts, f_tol), offsetof(mbar_opts, max_sci),
+         sizeof(mbar_report), offsetof(mbar_report, max_abs_grad), offsetof(mbar_report, last_step));
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
+    assert vals == [ctypes.sizeof(M.Opts), M.Opts.f_tol.offset, M.Opts.max_sci.offset,
+                    ctypes.sizeof(M.Report), M.Report.max_abs_grad.offset, M.Report.last_step.offset]
+
+
+def test_opts_default_are_the_papers(L):
+    o = M.default_opts(M.MBAR_MIXED)
+    assert (o.n0, o.eps, o.inc, o.n_intermediate) == (100, 1e-3, 10, 20)
+    assert o.use_binning == 1 and o.h0 == 0.0
+    with pytest.raises(M.MbarError):
+        M.default_opts(7)
+
+
+def test_status_strings(L):
+    for code in range(8):
+        assert L.mbar_status_string(code)
+
+
+@pytest.mark.parametrize("K,N,Nk,code", [
+    (0, 4, [], "MBAR_EINVAL"),
+    (2, 4, [1, 2], "MBAR_EINVAL"),           # counts do not sum to N
+    (2, 4, [0, 4], "MBAR_EINVAL"),           # empty state
+    (2000, 4000, [2] * 2000, "MBAR_EUNSUPPORTED"),
+])
+def test_create_rejects_bad_sizes_before_any_device_work(L, K, N, Nk, code):
+    u = np.zeros((max(K, 1), N))
+    Nk = np.asarray(Nk if Nk else [1], dtype=np.int64)
+    h = ctypes.c_void_p()
+    st = L.mbar_create(ctypes.byref(h), K, N, Nk.ctypes.data_as(M._i64p), ctypes.c_void_p(u.ctypes.data), 0, None, None)
+    assert M.STATUS[st] == code
+    assert not h.value
+
+
+def test_destroy_null_is_ok(L):
+    assert L.mbar_destroy(None) == 0

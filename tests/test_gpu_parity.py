@@ -1,0 +1,325 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (from the arithmetic of each path):
+  * bin keys / counts / width search: bit-exact (integer work, binary64
+    bin index with the same rounding on both sides);
+  * FP64 path: 1e-9 kT per step and 1e-8 kT for the solve (sums of a few
+    thousand binary64 terms in another order differ by ~1e-14 relative);
+  * MIXED path: 1e-4 kT (FP32 exp with row sums accumulated in FP64);
+  * Hessian: 1e-4 of max|H| on the CUDA-core path (FP32 products,
+    FP64 reduction across slices).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_03541_b300 import mbar as M
+from paper_2609_03541_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"fp64": M.MBAR_FP64, "mixed": M.MBAR_MIXED}
+F_TOL = {"fp64": 1e-9, "mixed": 1e-4}
+SOLVE_TOL = {"fp64": 1e-8, "mixed": 1e-4}
+
+
+def rand_problem(K, N, seed=0, spread=3.0, offset=0.0):
+    g = np.random.default_rng(seed)
+    base = np.full(K, N // K, dtype=np.int64)
+    base[: N - base.sum()] += 1
+    u = spread * g.standard_normal((K, N)) + g.uniform(-2, 2, size=(K, 1)) + offset * g.standard_normal((1, N))
+    return u, base
+
+
+def rand_f(K, seed=1):
+    g = np.random.default_rng(seed)
+    f = g.uniform(-1.0, 1.0, size=K)
+    f[0] = 0.0
+    return f
+
+
+# ---------------------------------------------------------------------------
+# b1/b2: one SCI step, gradient and logden, unbinned
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,N", [(1, 50), (2, 33), (3, 1000), (8, 8013), (64, 4099), (257, 3001), (500, 2053),
+                                 (1000, 1031)])
+def test_sci_step_unbinned(prec, K, N):
+    u, Nk = rand_problem(K, N, seed=K + N, offset=200.0)
+    f = rand_f(K)
+    ctx = M.Context(u, Nk, PREC[prec])
+    fo, g, s, ld = ctx.sci_step(f, want_logden=True)
+    ctx.close()
+    fo_ref = O.gauge(O.sci_step(u, f, Nk))
+    g_ref = O.mbar_gradient(u, f, Nk)
+    ld_ref = O.log_denominator(u, f, Nk)
+    s_ref = O.relative_step(fo_ref, f)
+    tol = F_TOL[prec]
+    assert np.max(np.abs(fo - fo_ref)) < tol
+    assert np.max(np.abs(g - g_ref) / Nk) < tol
+    assert np.max(np.abs(ld - ld_ref)) < tol * 10
+    if K > 1:
+        assert abs(s - s_ref) <= tol * max(1.0, abs(s_ref)) * 10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sci_step_first_step_from_zero(prec):
+    p = W.harmonic(K=8, N_k=1000, seed=0)
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    fo, g, s = ctx.sci_step(np.zeros(8))
+    ctx.close()
+    assert s == np.inf
+    assert np.max(np.abs(fo - O.gauge(O.sci_step(p.u_kn, np.zeros(8), p.N_k)))) < F_TOL[prec]
+
+
+# ---------------------------------------------------------------------------
+# a1-a4: binning
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("h", [0.5, 0.1, 0.013, 1e-3, 1e-6])
+def test_histogram_bit_exact(prec, h):
+    p = W.umbrella(K=6, N_k=700, seed=3, grid_points=1 << 12)
+    phi = p.phi.copy()
+    phi[::97] = np.round(phi[::97], 1)        # ties and values on bin edges
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    ctx.set_coordinate(phi)
+    nb = ctx.bin(h)
+    keys, H, ub = ctx.get_bins(nb)
+    hist = O.histogram(phi, h)
+    assert nb == hist.H.shape[0]
+    assert np.array_equal(keys, hist.keys)
+    assert np.array_equal(H, hist.H)
+    ub_ref = O.binned_u(p.u_kn, hist)
+    if prec == "fp64":
+        assert np.max(np.abs(ub - ub_ref)) < 1e-11
+    else:  # stored with a per-bin shift; state differences are exact up to FP32
+        d = (ub - ub[0]) - (ub_ref - ub_ref[0])
+        assert np.max(np.abs(d)) < 1e-4 * max(1.0, np.max(np.abs(ub_ref - ub_ref[0])))
+    ctx.close()
+
+
+def test_histogram_golden_edges(golden_dir):
+    import json, os
+    spec = json.load(open(os.path.join(golden_dir, "binning_cases.json")))
+    for case in spec["cases"]:
+        phi = np.array(case["phi"])
+        N = phi.shape[0]
+        u = np.vstack([phi, 2 * phi])
+        ctx = M.Context(u, np.array([N - N // 2, N // 2]) if N > 1 else np.array([1, 0]), M.MBAR_FP64) if N > 1 else None
+        if ctx is None:
+            continue
+        ctx.set_coordinate(phi)
+        nb = ctx.bin(case["w"])
+        keys, H, _ = ctx.get_bins(nb)
+        assert keys.tolist() == case["nonempty_keys"], case["name"]
+        assert H.tolist() == case["H"], case["name"]
+        ctx.close()
+
+
+@pytest.mark.parametrize("n", [2, 10, 100, 1000, 5000])
+def test_width_search_bit_exact(n):
+    p = W.gaussian_overlap(M=6, N_0=1500, seed=2)
+    ctx = M.Context(p.u_kn, p.N_k, M.MBAR_FP64)
+    ctx.set_coordinate(p.phi)
+    w, nb = ctx.bin_count(n)
+    w_ref = O.width_for_bins(p.phi, n)
+    assert w == w_ref
+    assert nb == O.nonempty_bins(p.phi, w_ref)
+    ctx.close()
+
+
+def test_width_search_unreachable_gives_unbinned():
+    p = W.harmonic(K=3, N_k=50, seed=1)
+    ctx = M.Context(p.u_kn, p.N_k, M.MBAR_FP64)
+    w, nb = ctx.bin_count(10**6)
+    assert w == 0.0 and nb == p.N
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_binned_sci_step(prec):
+    p = W.umbrella(K=10, N_k=900, seed=5, grid_points=1 << 12)
+    f = rand_f(10, seed=4)
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    ctx.set_coordinate(p.phi)
+    for h in (0.2, 0.02, 0.002):
+        nb = ctx.bin(h)
+        fo, g, s = ctx.sci_step(f)
+        hist = O.histogram(p.phi, h)
+        ub = O.binned_u(p.u_kn, hist)
+        fo_ref = O.gauge(O.sci_step(ub, f, p.N_k, hist.H))
+        g_ref = O.mbar_gradient(ub, f, p.N_k, hist.H)
+        assert nb == hist.H.shape[0]
+        assert np.max(np.abs(fo - fo_ref)) < F_TOL[prec]
+        assert np.max(np.abs(g - g_ref) / p.N_k) < F_TOL[prec]
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# c1/c2: Hessian and Newton step
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,N", [(2, 500), (8, 8000), (70, 3001), (200, 2500)])
+def test_hessian(prec, K, N):
+    u, Nk = rand_problem(K, N, seed=3 * K, spread=1.5)
+    f = O.solve_mbar(u, Nk, tol=1e-10) if K <= 8 else rand_f(K, seed=2) * 0.1
+    ctx = M.Context(u, Nk, PREC[prec])
+    Hs = ctx.hessian(f)
+    ctx.close()
+    H_ref = O.mbar_hessian(u, f, Nk)
+    scale = np.max(np.abs(H_ref))
+    assert np.max(np.abs(Hs - H_ref)) < 1e-4 * scale
+    assert np.max(np.abs(Hs - Hs.T)) < 1e-9 * scale
+    assert np.max(np.abs(Hs.sum(axis=1))) < 1e-9 * scale
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_newton_step(prec):
+    p = W.harmonic(K=8, N_k=1000, seed=0)
+    f0 = O.gauge(O.sci_step(p.u_kn, np.zeros(8), p.N_k))
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    fo, step = ctx.newton_step(f0)
+    ctx.close()
+    d = O.newton_direction(O.mbar_hessian(p.u_kn, f0, p.N_k), O.mbar_gradient(p.u_kn, f0, p.N_k))
+    assert np.max(np.abs(fo - (f0 + d))) < (1e-6 if prec == "fp64" else 1e-3) * max(1, np.max(np.abs(d)))
+    assert abs(step - np.max(np.abs(d))) < 1e-3 * np.max(np.abs(d))
+
+
+# ---------------------------------------------------------------------------
+# full solves
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_harmonic_plain_and_binned(prec):
+    p = W.harmonic(K=8, d=3, N_k=1000, seed=0)
+    f_ref = O.solve_mbar(p.u_kn, p.N_k)
+    for use_binning in (0, 1):
+        o = M.default_opts(PREC[prec], use_binning=use_binning)
+        ctx = M.Context(p.u_kn, p.N_k, PREC[prec], opts=o)
+        rep = ctx.solve()
+        f = ctx.free_energies()
+        ctx.close()
+        assert np.max(np.abs(f - f_ref)) < SOLVE_TOL[prec], (use_binning, rep.as_dict())
+        assert f[0] == 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_umbrella_width_schedule(prec):
+    p = W.umbrella(K=16, N_k=1000, seed=1, grid_points=1 << 13)
+    opts = O.BUOptions(h0=0.1)
+    tr = []
+    f_ref = O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, opts=opts, trace=tr)
+    o = M.default_opts(PREC[prec], h0=0.1)
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec], opts=o)
+    ctx.set_coordinate(p.phi)
+    rep = ctx.solve()
+    f = ctx.free_energies()
+    ctx.close()
+    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL[prec], rep.as_dict()
+    n_first = sum(1 for t in tr if t[0] == "phase1")
+    if prec == "fp64":
+        assert rep.iters_first_loop == n_first
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_gaussian_overlap_count_schedule(prec):
+    p = W.gaussian_overlap(M=12, N_0=2000, seed=4)
+    f_ref = O.solve_mbar(p.u_kn, p.N_k)
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    ctx.set_coordinate(p.phi)
+    rep = ctx.solve()
+    f = ctx.free_energies()
+    ctx.close()
+    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL[prec], rep.as_dict()
+    assert rep.n_rebins >= 2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_alchemical_small(prec):
+    p = W.alchemical(K=20, N_k=300, seed=2)
+    f_ref = O.bu_mbar(p.u_kn, p.N_k, phi=p.phi)
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    ctx.set_coordinate(p.phi)
+    rep = ctx.solve()
+    f = ctx.free_energies()
+    ctx.close()
+    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL[prec], rep.as_dict()
+
+
+def test_solve_invariances_on_device():
+    p = W.harmonic(K=5, N_k=400, seed=7)
+    g = np.random.default_rng(0)
+    c_n = g.normal(size=p.N) * 100
+    perm = g.permutation(p.N)
+    out = []
+    for u in (p.u_kn, p.u_kn + c_n[None, :], p.u_kn[:, perm]):
+        ctx = M.Context(u, p.N_k, M.MBAR_FP64)
+        ctx.solve()
+        out.append(ctx.free_energies())
+        ctx.close()
+    assert np.max(np.abs(out[1] - out[0])) < 1e-9
+    assert np.max(np.abs(out[2] - out[0])) < 1e-9
+
+
+def test_single_state_and_two_sample_closed_form():
+    ctx = M.Context(np.array([[0.3, -1.0, 2.0]]), np.array([3]), M.MBAR_FP64)
+    ctx.solve()
+    assert ctx.free_energies().tolist() == [0.0]
+    ctx.close()
+    u = np.array([[0.0, 0.0], [1.3, -0.4]])
+    ctx = M.Context(u, np.array([1, 1]), M.MBAR_FP64, opts=M.default_opts(M.MBAR_FP64, use_binning=0))
+    ctx.solve()
+    f = ctx.free_energies()
+    ctx.close()
+    assert abs(f[1] - 0.5 * (1.3 - 0.4)) < 1e-10
+
+
+def test_bad_inputs_are_rejected():
+    u = np.ones((2, 4))
+    u[1, 2] = np.nan
+    with pytest.raises(M.MbarError) as e:
+        M.Context(u, np.array([2, 2]), M.MBAR_MIXED)
+    assert e.value.name == "MBAR_EINVAL"
+    ctx = M.Context(np.ones((2, 4)), np.array([2, 2]), M.MBAR_FP64)
+    with pytest.raises(M.MbarError):
+        ctx.bin(-1.0)
+    with pytest.raises(M.MbarError):
+        ctx.get_bins(1)          # unbinned level
+    with pytest.raises(M.MbarError):
+        ctx.set_coordinate(np.array([0.0, np.inf, 1.0, 2.0]))
+    ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# stateless device-level pass
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_lse_pass_stateless(dtype):
+    import torch
+    K, N = 37, 5001
+    u, Nk = rand_problem(K, N, seed=9)
+    f = rand_f(K, seed=3)
+    dev = torch.device("cuda")
+    tdt = torch.float32 if dtype == "float32" else torch.float64
+    ld = (N + 31) // 32 * 32
+    v = torch.zeros((K, ld), dtype=tdt, device=dev)
+    v[:, :N] = torch.from_numpy(u).to(dev, tdt)
+    vv = v[:, :N]
+    ft = torch.from_numpy(f).to(dev)
+    lN = torch.from_numpy(np.log(Nk.astype(np.float64))).to(dev)
+    Q = torch.empty(K, dtype=torch.float64, device=dev)
+    logden = torch.empty(N, dtype=tdt, device=dev)
+    nbytes = M.lse_scratch_bytes(K, N, v.element_size())
+    scratch = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        M.lse_pass(vv, ft, lN, Q, logden=logden, scratch=scratch)
+    torch.cuda.synchronize()
+    Wk = O.mbar_weights(u, f, Nk)
+    Q_ref = Nk * Wk.sum(axis=1)
+    tol = 1e-10 if dtype == "float64" else 1e-5
+    assert np.max(np.abs(Q.cpu().numpy() - Q_ref) / Q_ref) < tol
+    assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - O.log_denominator(u, f, Nk))) < tol * 100
