@@ -179,6 +179,52 @@ def oracle_sample(name: str, target_seconds: float = 20.0):
 
 
 # ---------------------------------------------------------------------------
+# kernel-only timing of the fused LSE pass
+# ---------------------------------------------------------------------------
+
+def lse_only(args):
+    """Times mbar_lse_pass on a resident K x n matrix (random reduced
+    potentials) with CUDA events on the launching stream; prints one JSON
+    line with the achieved bandwidth against the measured HBM peak."""
+    import torch
+    from paper_2609_03541_b300 import mbar as M
+    dev = torch.device("cuda", 0)
+    K, n = args.lse_K, args.lse_n
+    dt = torch.float32 if args.lse_dtype == "float32" else torch.float64
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    ld = (n + 31) // 32 * 32
+    v = torch.empty((K, ld), dtype=dt, device=dev)
+    v[:, :n] = (3.0 * torch.randn((K, n), generator=g, device=dev, dtype=torch.float32)).abs().to(dt)
+    vv = v[:, :n]
+    f = torch.linspace(-1, 1, K, device=dev, dtype=torch.float64)
+    logN = torch.full((K,), float(np.log(n / K)), device=dev, dtype=torch.float64)
+    Q = torch.empty(K, device=dev, dtype=torch.float64)
+    logden = torch.empty(n, device=dev, dtype=dt)
+    scratch = torch.zeros(M.lse_scratch_bytes(K, n, v.element_size()), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        M.lse_pass(vv, f, logN, Q, logden=logden, scratch=scratch, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        M.lse_pass(vv, f, logN, Q, logden=logden, scratch=scratch, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks, src = load_peaks()
+    algo = K * n * v.element_size()
+    gbs = algo / (ms / 1e3) / 1e9
+    print(json.dumps({"kernel": f"lse_pass_kernel<{args.lse_dtype}>", "K": K, "n": n, "ms_per_launch": ms,
+                      "algorithmic_bytes": algo, "achieved_GBps": gbs, "peak_GBps": peaks["hbm_gbs"],
+                      "frac": gbs / peaks["hbm_gbs"], "peak_source": src,
+                      "entries_per_s": K * n / (ms / 1e3)}), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # main
 # ---------------------------------------------------------------------------
 
@@ -191,12 +237,24 @@ def main():
     ap.add_argument("--workload", default="alchemical", choices=list(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--precision", default=None, choices=["mixed", "fp64"],
+                    help="override the workload's precision")
+    ap.add_argument("--lse-only", action="store_true",
+                    help="time only the stateless fused LSE pass (mbar_lse_pass) on a resident K x n matrix")
+    ap.add_argument("--lse-K", type=int, default=500)
+    ap.add_argument("--lse-n", type=int, default=2_000_000)
+    ap.add_argument("--lse-dtype", default="float32", choices=["float32", "float64"])
     args = ap.parse_args()
+    if args.lse_only:
+        return lse_only(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    cfg = WORKLOADS[args.workload]
+    cfg = dict(WORKLOADS[args.workload])
+    if args.precision:
+        cfg["precision"] = args.precision
     metric = "MBAR solves/sec"
     config = {"workload": cfg["desc"], "K": cfg["K"], "N": cfg["K"] * cfg["N_k"], "precision": cfg["precision"],
               "tolerance_kT": 1e-4 if cfg["precision"] == "mixed" else 1e-8,
@@ -247,6 +305,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     opts = M.default_opts(prec, h0=cfg["h0"])
 
+    traces = []
+
     def step(u, phi, timing=False, acc=None):
         ctx = M.Context(u, Nk, prec, opts=opts, stream=stream.cuda_stream)
         if timing:
@@ -255,6 +315,7 @@ def main():
             ctx.set_coordinate(phi)
         rep = ctx.solve()
         f = ctx.free_energies()
+        traces.append(ctx.trace())
         if timing and acc is not None:
             for kind in (0, 1, 2):
                 n, ms, by = ctx.timing(kind)
@@ -268,6 +329,11 @@ def main():
     for i in range(args.warmup):
         f_w, rep_w = step(u_dev, phi_dev)
         log(f"[bench] warmup {i}: report {rep_w.as_dict()}")
+    if traces:
+        tr = traces[-1]
+        log(f"[bench] solve trace ({len(tr)} rows: phase, n, a, b):")
+        for row in tr[:40]:
+            log("   " + " ".join(f"{x:.6g}" for x in row))
 
     def barrier():
         if dist is not None:
@@ -318,7 +384,7 @@ def main():
 
     # ---- accuracy of the timed solve against the FP64 GPU path (outside timing) ----
     accuracy = None
-    if prec == M.MBAR_MIXED and rank == 0:
+    if prec == M.MBAR_MIXED and rank == 0 and not args.no_accuracy:
         o64 = M.default_opts(M.MBAR_FP64, h0=cfg["h0"])
         ctx = M.Context(u_dev, Nk, M.MBAR_FP64, opts=o64, stream=stream.cuda_stream)
         if phi_dev is not None:

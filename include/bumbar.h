@@ -71,10 +71,16 @@ typedef struct {
                              instead of the width rule w*(n) of Sec. II */
   int32_t use_binning;    /* 0: skip Algorithm 1 (plain MBAR: unbinned SCI
                              warm-up, then Newton) */
-  double f_tol;           /* Newton stops when max|delta f| < f_tol */
+  double f_tol;           /* Newton stops when max|delta f| < f_tol; Newton
+                             steps below 10 f_tol are always accepted */
   double warm_tol;        /* plain-MBAR warm-up: SCI until max_k|g_k|/N_k < warm_tol */
   int32_t max_newton;     /* Newton iteration limit */
   int32_t max_sci;        /* limit on SCI steps per loop of Algorithm 1 */
+  double noise_floor;     /* > 0: an SCI step with max_k |delta f_k| below this
+                             many kT is under the rounding floor of the
+                             evaluation; Algorithm 1 then treats the level as
+                             converged (first loop: stop; second loop: raise
+                             n). 0 = Eq. 2/3 exactly as printed. */
 } mbar_opts;
 
 typedef struct {
@@ -88,9 +94,11 @@ typedef struct {
   double last_step;          /* max |delta f| of the last Newton step */
 } mbar_report;
 
-/* Fills *opts with the defaults above (f_tol 1e-10 for MBAR_FP64, 1e-6 for
- * MBAR_MIXED, chosen by `precision`; warm_tol 1e-3;
- * max_newton 50; max_sci 200000; use_binning 1; h0 0). */
+/* Fills *opts with the defaults above (f_tol 1e-10 for MBAR_FP64, 1e-5 for
+ * MBAR_MIXED, chosen by `precision`; warm_tol 1e-3; max_newton 50;
+ * max_sci 200000; use_binning 1; h0 0; noise_floor 0 for MBAR_FP64 and
+ * 2e-6 kT for MBAR_MIXED, whose FP32 evaluation moves f by ~1e-7..1e-6 kT
+ * from rounding alone). */
 BUMBAR_API mbar_status mbar_opts_default(mbar_opts* opts, int32_t precision);
 
 /* Creates a context for one problem (the paper's input list of Algorithm 1:
@@ -198,6 +206,21 @@ BUMBAR_API const char* mbar_last_error(void);
 BUMBAR_API mbar_status mbar_set_timing(mbar_ctx* ctx, int32_t enable);
 BUMBAR_API mbar_status mbar_get_timing(mbar_ctx* ctx, int32_t kind, int64_t* launches, double* total_ms,
                                        double* bytes);
+
+/* Trace of the last mbar_solve, one row of 4 doubles per event:
+ *   (1, n, s, iterations)      end of Algorithm 1's first loop at n bins;
+ *   (2, n, s_n, s_next)        one check of Eq. 3 in the second loop;
+ *   (3, iteration, |delta f|max, max|g|)  accepted Newton step;
+ *   (4, iteration, |delta f|max, max|g|)  rejected Newton step (SCI instead).
+ * *rows receives the number of rows; out (host, nullable) receives up to
+ * `capacity` rows. */
+BUMBAR_API mbar_status mbar_get_trace(mbar_ctx* ctx, int64_t* rows, double* out, int64_t capacity);
+
+/* Process-wide choice of the Hessian contraction: 0 = by size (tensor
+ * cores, FP16 operands / FP32 accumulation, for K >= 64; CUDA cores, FP32,
+ * below), 1 = always CUDA cores, 2 = always tensor cores. For testing and
+ * tuning; EINVAL for other values. */
+BUMBAR_API mbar_status mbar_set_hessian_path(int32_t path);
 
 /* Number of CUDA kernels this library has launched in this process. */
 BUMBAR_API mbar_status mbar_kernel_launches(int64_t* count);

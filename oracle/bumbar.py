@@ -322,7 +322,10 @@ def width_for_bins(phi: np.ndarray, n: int) -> float | None:
 class BUOptions:
     """Hyperparameters of Algorithm 1, defaults from Sec. II (n0 = 100,
     eps = 1e-3, inc = 10, N_intermediate = 20). ``h0`` > 0 switches to an
-    explicit width schedule h0, h0/inc, h0/inc^2, ... instead of w*(n)."""
+    explicit width schedule h0, h0/inc, h0/inc^2, ... instead of w*(n).
+    ``noise_floor`` > 0 treats an SCI step with max|delta f| below it as
+    converged at its level (first loop stops, second loop raises n); 0 runs
+    Eqs. 2-3 exactly as printed."""
     n0: int = 100
     eps: float = 1e-3
     inc: int = 10
@@ -331,6 +334,7 @@ class BUOptions:
     newton_tol: float = 1e-12
     max_phase1: int = 100000
     max_rounds: int = 100000
+    noise_floor: float = 0.0
 
 
 @dataclass
@@ -388,10 +392,10 @@ def bu_mbar(u_kn, N_k, phi=None, opts: BUOptions | None = None, trace: list | No
     for _ in range(opts.max_phase1):
         f_new = gauge(sci_step(cur.u, f, Nk, cur.H))
         s = relative_step(f_new, f)
-        f = f_new
+        f_prev, f = f, f_new
         if trace is not None:
             trace.append(("phase1", cur.n, s, None))
-        if s < opts.eps:
+        if s < opts.eps or (opts.noise_floor > 0 and np.max(np.abs(f - f_prev)) < opts.noise_floor):
             break
     lvl_idx += 1
     cur = level(lvl_idx)
@@ -406,7 +410,8 @@ def bu_mbar(u_kn, N_k, phi=None, opts: BUOptions | None = None, trace: list | No
             s_next = relative_step(f_next, f)
             if trace is not None:
                 trace.append(("phase2", cur.n, s_n, s_next))
-            if 2.0 * s_next > inc * s_n:
+            floor_hit = opts.noise_floor > 0 and np.max(np.abs(f_new - f)) < opts.noise_floor
+            if 2.0 * s_next > inc * s_n or floor_hit:
                 f = f_next
                 lvl_idx += 1
                 cur = nxt

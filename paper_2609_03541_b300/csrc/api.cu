@@ -61,7 +61,7 @@ struct mbar_ctx {
   Level cur;   // level selected through mbar_bin / mbar_bin_count
   // iteration state
   double *f = nullptr, *fs = nullptr, *ft = nullptr, *fts = nullptr;
-  double *g = nullptr, *gt = nullptr, *Q = nullptr, *s = nullptr, *s2 = nullptr;
+  double *g = nullptr, *gt = nullptr, *Q = nullptr, *s = nullptr, *s2 = nullptr, *d = nullptr;
   double *hess = nullptr, *delta = nullptr;
   int* info = nullptr;
   int* bad = nullptr;
@@ -85,6 +85,8 @@ struct mbar_ctx {
   bool timing = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
+  // solver trace: (phase, n, a, b) rows, see mbar_get_trace
+  std::vector<double> trace;
 };
 
 namespace {
@@ -158,9 +160,14 @@ void time_mark(mbar_ctx* c, bool begin, int kind, double bytes) {
   }
 }
 
+void trace_row(mbar_ctx* c, double phase, double n, double a, double b) {
+  c->trace.insert(c->trace.end(), {phase, n, a, b});
+}
+
 // One pass of the fused LSE kernel over a level.
 mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, double* f_out, double* g_out,
-                    double* s_out, double eps, int skip_if_done, void* logden_out) {
+                    double* s_out, double eps, int skip_if_done, void* logden_out, double* d_out = nullptr,
+                    double noise = 0.0) {
   const LsePlan pl = lse_plan(c->K, L.n, c->dtype);
   LseParams p{};
   p.K = static_cast<int>(c->K);
@@ -181,6 +188,8 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   p.s_out = s_out;
   p.ctrl = c->ctrl;
   p.eps = eps;
+  p.noise = noise;
+  p.d_out = d_out;
   p.skip_if_done = skip_if_done;
   const bool timed = !L.binned;
   if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
@@ -188,6 +197,8 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   if (timed) time_mark(c, false, 0, 0);
   return s;
 }
+
+unsigned* err_word(mbar_ctx* c) { return reinterpret_cast<unsigned*>(static_cast<unsigned char*>(c->scratch) + 4); }
 
 mbar_status check_device_errors(mbar_ctx* c) {
   unsigned err = 0;
@@ -433,7 +444,8 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
     }
     rep->iters_newton++;
     time_mark(c, true, 1, static_cast<double>(K) * L.n * c->dtype);
-    mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->f, c->logN_d, c->logden, nullptr, c->hess, tmp, htmp, c->st);
+    mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->f, c->logN_d, c->logden, nullptr, c->hess, err_word(c),
+                            tmp, htmp, c->st);
     time_mark(c, false, 1, 0);
     if (s == MBAR_OK) s = cudaMemsetAsync(c->info, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
     time_mark(c, true, 2, static_cast<double>(K) * K * 8);
@@ -463,7 +475,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
         return s;
       }
       const double gmax_t = (s == MBAR_OK) ? max_abs(gh) : INFINITY;
-      if (gmax_t <= gmax) {
+      if (std::isfinite(gmax_t) && (gmax_t <= gmax || step <= 10.0 * c->opts.f_tol)) {
         std::swap(c->f, c->ft);
         std::swap(c->fs, c->fts);
         std::swap(c->g, c->gt);
@@ -471,6 +483,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
         accepted = true;
         rejects = 0;
         rep->last_step = step;
+        trace_row(c, 3, it, step, gmax);
         if (step < c->opts.f_tol) {
           st = MBAR_OK;
           break;
@@ -480,6 +493,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
     if (!accepted) {
       // Newton step did not lower max|g|: take the SCI step from f instead
       rep->newton_fallbacks++;
+      trace_row(c, 4, it, step, gmax);
       rejects++;
       if (rejects >= 3 && step < 1e3 * c->opts.f_tol) {  // at the noise floor of the gradient
         st = MBAR_OK;
@@ -509,13 +523,16 @@ mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
   int64_t done_iters = 0;
   for (;;) {
     for (int b = 0; b < kPhase1Batch; ++b)
-      BUMBAR_TRY(run_lse(c, L, c->f, kLseModeSci, c->f, nullptr, c->s, c->opts.eps, 1, nullptr));
+      BUMBAR_TRY(run_lse(c, L, c->f, kLseModeSci, c->f, nullptr, c->s, c->opts.eps, 1, nullptr, nullptr,
+                         c->opts.noise_floor));
     Ctrl h{};
     BUMBAR_CUDA(cudaMemcpyAsync(&h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
     BUMBAR_TRY(check_device_errors(c));
     done_iters = h.iters;
-    if (h.done) break;
-    if (done_iters >= c->opts.max_sci) break;
+    if (h.done || done_iters >= c->opts.max_sci) {
+      trace_row(c, 1, static_cast<double>(L.n_sched), h.last_s, static_cast<double>(done_iters));
+      break;
+    }
   }
   rep->iters_first_loop += done_iters;
   return MBAR_OK;
@@ -550,15 +567,19 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
     if (rep->iters_second_loop >= o.max_sci) break;
     for (int i = 0; i < o.n_intermediate && s == MBAR_OK; ++i)
       s = run_lse(c, cur, c->f, kLseModeSci, c->f, nullptr, nullptr, 0.0, 0, nullptr);
-    if (s == MBAR_OK) s = run_lse(c, cur, c->f, kLseModeSci, c->ft, nullptr, c->s, 0.0, 0, nullptr);
+    if (s == MBAR_OK) s = run_lse(c, cur, c->f, kLseModeSci, c->ft, nullptr, c->s, 0.0, 0, nullptr, c->d);
     if (s == MBAR_OK) s = run_lse(c, nxt, c->f, kLseModeSci, c->fts, nullptr, c->s2, 0.0, 0, nullptr);
-    double s_n = 0, s_next = 0;
+    double s_n = 0, s_next = 0, d_n = 0;
     if (s == MBAR_OK) s = read_scalar(c, c->s, &s_n);
     if (s == MBAR_OK) s = read_scalar(c, c->s2, &s_next);
+    if (s == MBAR_OK) s = read_scalar(c, c->d, &d_n);
     if (s == MBAR_OK) s = check_device_errors(c);
     if (s != MBAR_OK) break;
     rep->iters_second_loop += o.n_intermediate + 2;
-    if (2.0 * s_next > static_cast<double>(o.inc) * s_n) {
+    trace_row(c, 2, static_cast<double>(cur.n_sched), s_n, s_next);
+    // Eq. 3, plus: a step under the evaluation's rounding floor means the
+    // level has converged as far as this arithmetic can tell
+    if (2.0 * s_next > static_cast<double>(o.inc) * s_n || (o.noise_floor > 0.0 && d_n < o.noise_floor)) {
       std::swap(c->f, c->fts);
       level_free(c, &cur);
       cur = nxt;
@@ -649,15 +670,17 @@ mbar_status mbar_opts_default(mbar_opts* o, int32_t precision) {
   o->n_intermediate = 20;
   o->h0 = 0.0;
   o->use_binning = 1;
-  o->f_tol = precision == MBAR_FP64 ? 1e-10 : 1e-6;
+  o->f_tol = precision == MBAR_FP64 ? 1e-10 : 1e-5;
   o->warm_tol = 1e-3;
   o->max_newton = 50;
   o->max_sci = 200000;
+  o->noise_floor = precision == MBAR_FP64 ? 0.0 : 2e-6;
   return MBAR_OK;
 }
 
 mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
                         int32_t u_on_device, const mbar_opts* opts, void* cuda_stream) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   if (!out || !N_k || !u_kn) {
     set_error("mbar_create: null pointer argument");
     return MBAR_EINVAL;
@@ -694,7 +717,8 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
     mbar_opts_default(&o, MBAR_MIXED);
   }
   if ((o.precision != MBAR_FP64 && o.precision != MBAR_MIXED) || o.n0 < 1 || o.inc < 2 || !(o.eps > 0) ||
-      o.n_intermediate < 0 || o.h0 < 0 || !(o.f_tol > 0) || o.max_newton < 1 || o.max_sci < 1) {
+      o.n_intermediate < 0 || o.h0 < 0 || !(o.f_tol > 0) || o.max_newton < 1 || o.max_sci < 1 ||
+      !(o.noise_floor >= 0)) {
     set_error("mbar_create: invalid options");
     return MBAR_EINVAL;
   }
@@ -733,6 +757,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   for (double** p : {&c->f, &c->fs, &c->ft, &c->fts, &c->g, &c->gt, &c->Q, &c->delta}) TRYC(dalloc_t(c, p, K));
   TRYC(dalloc_t(c, &c->s, 1));
   TRYC(dalloc_t(c, &c->s2, 1));
+  TRYC(dalloc_t(c, &c->d, 1));
   TRYC(dalloc_t(c, &c->hess, K * K));
   TRYC(dalloc_t(c, &c->info, 1));
   TRYC(dalloc_t(c, &c->bad, 1));
@@ -809,6 +834,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
 }
 
 mbar_status mbar_set_coordinate(mbar_ctx* c, const double* phi, int32_t phi_on_device) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   if (!phi) {
     set_error("mbar_set_coordinate: phi is NULL");
@@ -835,6 +861,7 @@ mbar_status mbar_set_coordinate(mbar_ctx* c, const double* phi, int32_t phi_on_d
 }
 
 mbar_status mbar_bin(mbar_ctx* c, double h, int64_t* n_bins_out) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   if (!(h >= 0.0) || !std::isfinite(h)) {
     set_error("mbar_bin: h must be finite and >= 0");
@@ -859,6 +886,7 @@ mbar_status mbar_bin(mbar_ctx* c, double h, int64_t* n_bins_out) {
 }
 
 mbar_status mbar_bin_count(mbar_ctx* c, int64_t n, double* w_out, int64_t* n_bins_out) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   if (n < 1) {
     set_error("mbar_bin_count: n must be >= 1");
@@ -916,6 +944,7 @@ mbar_status mbar_get_bins(mbar_ctx* c, int64_t* keys, int64_t* H, double* u_kp) 
 
 mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double* grad, double* s_out,
                           double* logden) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   if (!f_in) {
     set_error("mbar_sci_step: f_in is NULL");
@@ -961,6 +990,7 @@ mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double
 }
 
 mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   if (!f_in || !hess_out) {
     set_error("mbar_hessian: null pointer argument");
@@ -973,7 +1003,8 @@ mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
   const size_t htmp = hessian_tmp_bytes(K, L.n);
   void* tmp = nullptr;
   BUMBAR_TRY(dalloc(c, &tmp, htmp));
-  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, tmp, htmp, c->st);
+  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, err_word(c), tmp,
+                          htmp, c->st);
   if (s == MBAR_OK) s = check_device_errors(c);
   if (s == MBAR_OK) s = d2h(c, hess_out, c->hess, K * K);
   if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
@@ -982,6 +1013,7 @@ mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
 }
 
 mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, double* step_max_abs) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   if (!f_in) {
     set_error("mbar_newton_step: f_in is NULL");
@@ -994,7 +1026,8 @@ mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, dou
   const size_t htmp = hessian_tmp_bytes(K, L.n), ntmp = newton_tmp_bytes(K);
   void* tmp = nullptr;
   BUMBAR_TRY(dalloc(c, &tmp, std::max(htmp, ntmp)));
-  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, tmp, htmp, c->st);
+  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, err_word(c), tmp,
+                          htmp, c->st);
   if (s == MBAR_OK) s = cudaMemsetAsync(c->info, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
   if (s == MBAR_OK) s = newton_solve(c->hess, K, c->gt, c->delta, c->info, tmp, ntmp, c->st);
   if (s == MBAR_OK) s = vec_add_gauge(c->ft, c->delta, c->fts, K, c->st);
@@ -1017,6 +1050,7 @@ mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, dou
 }
 
 mbar_status mbar_solve(mbar_ctx* c, const double* f_init, mbar_report* report) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   mbar_report rep{};
   const int64_t K = c->K;
@@ -1027,6 +1061,7 @@ mbar_status mbar_solve(mbar_ctx* c, const double* f_init, mbar_report* report) {
   } else {
     BUMBAR_CUDA(cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st));
   }
+  c->trace.clear();
   mbar_status s = MBAR_OK;
   if (K > 1) {
     if (c->opts.use_binning)
@@ -1089,6 +1124,23 @@ mbar_status mbar_get_timing(mbar_ctx* c, int32_t kind, int64_t* launches, double
   return MBAR_OK;
 }
 
+mbar_status mbar_get_trace(mbar_ctx* c, int64_t* rows, double* out, int64_t capacity) {
+  CHECK_CTX(c);
+  const int64_t n = static_cast<int64_t>(c->trace.size() / 4);
+  if (rows) *rows = n;
+  if (out) std::copy(c->trace.begin(), c->trace.begin() + 4 * std::min(n, std::max<int64_t>(capacity, 0)), out);
+  return MBAR_OK;
+}
+
+mbar_status mbar_set_hessian_path(int32_t path) {
+  if (path < 0 || path > 2) {
+    set_error("mbar_set_hessian_path: path must be 0, 1 or 2");
+    return MBAR_EINVAL;
+  }
+  set_hessian_path(path);
+  return MBAR_OK;
+}
+
 mbar_status mbar_kernel_launches(int64_t* count) {
   if (!count) {
     set_error("mbar_kernel_launches: count is NULL");
@@ -1108,7 +1160,7 @@ mbar_status mbar_destroy(mbar_ctx* c) {
   level_free(c, &c->cur);
   void* ptrs[] = {c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->f,
                   c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->s,          c->s2,
-                  c->hess, c->delta,  c->info,  c->bad,    c->ctrl,  c->logden,  c->scratch,    c->seg,
+                  c->hess, c->delta,  c->info,  c->bad,    c->ctrl,  c->logden,  c->scratch,    c->seg, c->d,
                   c->start, c->count, c->nb_dev};
   for (void* p : ptrs) dfree(c, p);
   cudaStreamSynchronize(c->st);
@@ -1124,6 +1176,7 @@ size_t mbar_lse_scratch_bytes(int64_t K, int64_t n, int32_t dtype_bytes) {
 mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
                           const double* log_N, const int32_t* H, double* Q, void* logden, void* scratch,
                           size_t scratch_bytes, void* stream) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   if (!v || !f || !log_N || !Q || !scratch) {
     set_error("mbar_lse_pass: null pointer argument");
     return MBAR_EINVAL;

@@ -9,6 +9,7 @@
 // gauge null vector exact. G is the contraction; this file holds the
 // CUDA-core path (used for small K) and the shared reduction/assembly; the
 // tensor-core path for larger K lives in hessian_tc.cu.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -137,6 +138,20 @@ __global__ void laplacian_from_overlap(const double* __restrict__ G, int64_t K, 
   }
 }
 
+// a_k = f_k + log N_k for the tensor-core path
+__global__ void add_vectors(const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ out,
+                            int64_t K) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < K) out[k] = x[k] + y[k];
+}
+
+static int g_hessian_path = 0;
+void set_hessian_path(int path) { g_hessian_path = path; }
+int hessian_path_for(int64_t K) {
+  if (g_hessian_path == 1 || g_hessian_path == 2) return g_hessian_path;
+  return K >= 64 ? 2 : 1;
+}
+
 struct SimtPlan {
   int nt, npairs, nslices;
   int64_t cols_per_slice;
@@ -156,20 +171,34 @@ static SimtPlan simt_plan(int64_t K, int64_t n) {
 
 size_t hessian_tmp_bytes(int64_t K, int64_t n) {
   const SimtPlan p = simt_plan(K, n);
-  return round_up(static_cast<int64_t>(p.nslices) * p.npairs * kTile * kTile * 4, 256) + round_up(K * K * 8, 256);
+  const size_t simt = round_up(static_cast<int64_t>(p.nslices) * p.npairs * kTile * kTile * 4, 256);
+  const size_t tc = overlap_tc_tmp_bytes(K, n) + round_up(K * 8, 256);
+  return std::max(simt, tc) + round_up(K * K * 8, 256);
 }
 
 mbar_status hessian(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
-                    const double* logN, const void* logden, const int32_t* H, double* hess, void* tmp,
-                    size_t tmp_bytes, cudaStream_t st) {
+                    const double* logN, const void* logden, const int32_t* H, double* hess, unsigned* err,
+                    void* tmp, size_t tmp_bytes, cudaStream_t st) {
   if (tmp_bytes < hessian_tmp_bytes(K, n)) {
     set_error("hessian: scratch too small");
     return MBAR_EINVAL;
   }
   const SimtPlan p = simt_plan(K, n);
+  const size_t simt = round_up(static_cast<int64_t>(p.nslices) * p.npairs * kTile * kTile * 4, 256);
+  const size_t tc = overlap_tc_tmp_bytes(K, n) + round_up(K * 8, 256);
+  double* G = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + std::max(simt, tc));
+  if (hessian_path_for(K) == 2) {
+    double* a = static_cast<double*>(tmp);
+    unsigned char* rest = static_cast<unsigned char*>(tmp) + round_up(K * 8, 256);
+    add_vectors<<<static_cast<unsigned>(ceil_div(K, 256)), 256, 0, st>>>(f, logN, a, K);
+    count_launches(1);
+    BUMBAR_TRY(overlap_tc(v, dtype_bytes, K, n, ld, a, logden, H, G, err, rest, overlap_tc_tmp_bytes(K, n), st));
+    laplacian_from_overlap<<<static_cast<unsigned>(K), kThreads, 0, st>>>(G, K, hess);
+    count_launches(1);
+    BUMBAR_CUDA(cudaGetLastError());
+    return MBAR_OK;
+  }
   float* part = static_cast<float*>(tmp);
-  double* G = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) +
-                                        round_up(static_cast<int64_t>(p.nslices) * p.npairs * kTile * kTile * 4, 256));
   const dim3 grid(p.npairs, p.nslices);
   if (dtype_bytes == 4) {
     overlap_simt<float><<<grid, kThreads, 0, st>>>(static_cast<const float*>(v), K, n, ld, f, logN,

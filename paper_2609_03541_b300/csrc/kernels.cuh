@@ -38,14 +38,17 @@ struct LseParams {
   double* f_out;     // [K]
   double* g_out;     // [K] or nullptr
   double* s_out;     // scalar or nullptr
+  double* d_out;     // scalar or nullptr: max_k |f_out_k - (f_k - f_0)|
   Ctrl* ctrl;        // or nullptr
   double eps;        // > 0: set ctrl->done when s < eps
+  double noise;      // > 0: set ctrl->done when max|f_out - f| < noise
   int skip_if_done;  // return at once if ctrl->done
 };
 
 struct LsePlan {
-  int C, num_strips, box_rows, nbox, stages, grid;
+  int C, num_strips, box_rows, nbox, stages, grid, threads;
   size_t smem;
+  bool ok;  // fits the device's shared-memory limit
 };
 
 LsePlan lse_plan(int64_t K, int64_t n, int dtype_bytes);
@@ -100,9 +103,22 @@ mbar_status check_finite(const double* x, int64_t n, int* bad, cudaStream_t stre
 // writes the FP64 Hessian hess[K x K] = Laplacian of G (off-diagonal -G_ij,
 // diagonal sum_{j != i} G_ij).
 mbar_status hessian(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
-                    const double* logN, const void* logden, const int32_t* H, double* hess, void* tmp,
-                    size_t tmp_bytes, cudaStream_t stream);
+                    const double* logN, const void* logden, const int32_t* H, double* hess, unsigned* err,
+                    void* tmp, size_t tmp_bytes, cudaStream_t stream);
 size_t hessian_tmp_bytes(int64_t K, int64_t n);
+
+// Tensor-core overlap matrix (hessian_tc.cu): G[K x K] (FP64, symmetric) =
+// sum_p H_p P_ip P_jp with FP16 operands and FP32 accumulation in TMEM.
+// a = f + log N (device, K). err counts bounded waits that gave up.
+mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* a,
+                       const void* logden, const int32_t* H, double* G, unsigned* err, void* tmp, size_t tmp_bytes,
+                       cudaStream_t st);
+size_t overlap_tc_tmp_bytes(int64_t K, int64_t n);
+
+// Which contraction hessian() uses: 0 = by size (tensor cores for K >= 64),
+// 1 = CUDA cores, 2 = tensor cores.
+void set_hessian_path(int path);
+int hessian_path_for(int64_t K);
 
 // ---- dense FP64 (cholesky.cu) ----
 // Solves A x = b for the (m x m) symmetric positive definite block

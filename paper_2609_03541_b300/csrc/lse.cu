@@ -2,19 +2,25 @@
 // matrix v (samples or bins),
 //     logden_p = log sum_j exp(a_j - v_jp),          a_j = f_j + log N_j,
 //     Q_i      = sum_p H_p exp(a_i - v_ip - logden_p),
-// in ONE read of v from HBM. Columns are streamed in strips of 128 bytes
-// (32 FP32 or 16 FP64 columns) x all K rows; each strip is brought into
-// shared memory by 2-D TMA boxes (128-byte swizzle) through a multi-stage
-// mbarrier pipeline. Per strip:
-//   A1  column maxima over k (8 or 16 lanes per column, shuffle merge);
-//   A2  e_kp = exp(a_k - v_kp - max_p), written back in place, column sums;
-//   B   each thread owns whole rows and accumulates sum_p e_kp * H_p / s_p
-//       from 16-byte chunks of the swizzled tile (conflict-free).
-// Row sums are kept per thread (FP32 for MIXED, flushed to FP64 every few
-// strips; FP64 throughout for the FP64 path) and written once per CTA to
+// in ONE read of v from HBM.
+//
+// Layout and schedule (persistent CTAs, one per SM or more):
+//   * columns are streamed in strips of 128 bytes (32 FP32 or 16 FP64
+//     columns) x all K rows; each strip is fetched into shared memory by 2-D
+//     TMA boxes (<= 256 rows each, 128-byte swizzle) through a multi-stage
+//     mbarrier pipeline, so HBM reads of later strips overlap the arithmetic;
+//   * A1: column maxima of x = a_k - v_kp. A warp covers one 16-byte chunk
+//     of the swizzled row (4 FP32 / 2 FP64 columns) and 8 / 16 row residues,
+//     so its shared-memory reads are conflict-free; G warps split the rows
+//     and merge through shared memory;
+//   * A2: e_kp = exp(x - max_p) written back in place, column sums;
+//   * B: each thread owns whole rows and accumulates sum_p e_kp H_p / s_p
+//     from 16-byte chunks of the swizzled tile.
+// Row sums are kept per thread (FP32 partial sums flushed to FP64 every few
+// strips for MIXED; FP64 throughout for FP64) and written once per CTA to
 // scratch; the last CTA to finish reduces the per-CTA partials in a fixed
-// order (deterministic) and, for an SCI step, applies the update, the
-// gauge, the gradient and the relative step of Eq. 2.
+// order (deterministic) and, for an SCI step, applies the update, the gauge,
+// the gradient and the relative step of Eq. 2.
 #include <cmath>
 #include <cstdio>
 
@@ -25,76 +31,84 @@ namespace bumbar {
 
 namespace {
 
-constexpr int kMaxRowsPerThread = 4;      // K <= 1024 with 256 threads
 constexpr int kFlushStrips = 4;           // FP32 row sums flushed to FP64 every 4 strips
 constexpr uint32_t kMaxSpins = 1u << 28;  // bounded mbarrier wait
 
-template <typename T>
-struct Lane;
-
-template <>
-struct Lane<float> {
-  static constexpr int C = 32;  // columns per strip (128 bytes)
-  static constexpr int R = 8;   // lanes (row groups) per column
-};
-template <>
-struct Lane<double> {
-  static constexpr int C = 16;
-  static constexpr int R = 16;
+template <typename T, int G>
+struct Cfg {
+  static constexpr int THREADS = 256 * G;
+  static constexpr int C = 128 / static_cast<int>(sizeof(T));  // columns per strip
+  static constexpr int CPW = C / 8;                             // columns per 16-byte chunk
+  static constexpr int LW = 32 / CPW;                           // lanes per column inside a warp
+  static constexpr int R = LW * G;                              // row groups per column
+  static constexpr int ROWS_PT = (1024 + THREADS - 1) / THREADS;  // phase-B rows per thread
 };
 
-__device__ __forceinline__ float lse_exp(float x) { return ex2_approx(x); }     // x in log2 units
-__device__ __forceinline__ double lse_exp(double x) { return exp(x); }         // x in natural units
-__device__ __forceinline__ float lse_scale() { return kLog2e; }
+__device__ __forceinline__ float lse_exp(float x) { return ex2_approx(x); }  // x in log2 units
+__device__ __forceinline__ double lse_exp(double x) { return exp(x); }      // x in natural units
 __device__ __forceinline__ float lse_log(float s) { return __log2f(s); }
 __device__ __forceinline__ double lse_log(double s) { return log(s); }
-
 __device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+
+// x = a - v in the kernel's exponent units (log2 for FP32, natural for FP64)
+__device__ __forceinline__ float expo(float a, float v) { return fmaf(-v, kLog2e, a); }
+__device__ __forceinline__ double expo(double a, double v) { return a - v; }
 
 template <typename T>
 __device__ __forceinline__ T shfl_xor(T v, int m) {
   return __shfl_xor_sync(0xffffffffu, v, m);
 }
 
+__host__ __device__ inline size_t rup(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
 }  // namespace
 
-// Shared-memory carve-up of one CTA (dynamic smem, 1024-aligned base).
-template <typename T>
+// Shared-memory carve-up (dynamic, base aligned up to 1024 in the kernel):
+//   stages x stage bytes | a_k [K] | w_c [32] | column partials [2][G][32] |
+//   mbarriers [8] | epilogue doubles [K]
+template <typename T, int G>
 struct LseSmem {
   static __host__ __device__ size_t stage_bytes(int nbox, int box_rows) {
     return static_cast<size_t>(nbox) * box_rows * 128;
   }
+  static __host__ __device__ size_t a_bytes(int K) { return rup(static_cast<size_t>(K) * sizeof(T), 16); }
+  static constexpr size_t kW = 32 * sizeof(T);
+  static constexpr size_t kParts = 2 * G * 32 * sizeof(T);
+  static constexpr size_t kBars = 64;
   static __host__ __device__ size_t extra_bytes(int K) {
-    // a_k (Kpad of T), w_c (C of T), mbarriers (4), epilogue scratch (K doubles + 64)
-    return round_up_dev(static_cast<size_t>(K) * sizeof(T), 16) + 128 * sizeof(T) + 64 +
-           round_up_dev(static_cast<size_t>(K) * sizeof(double), 16) + 512;
+    return a_bytes(K) + kW + kParts + kBars + rup(static_cast<size_t>(K) * sizeof(double), 16);
   }
-  static __host__ __device__ size_t round_up_dev(size_t x, size_t m) { return (x + m - 1) / m * m; }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                            LseParams p) {
-  constexpr int C = Lane<T>::C;
-  constexpr int R = Lane<T>::R;
+template <typename T, int G>
+__global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                     LseParams p) {
+  using CF = Cfg<T, G>;
+  constexpr int THREADS = CF::THREADS, C = CF::C, CPW = CF::CPW, LW = CF::LW, R = CF::R;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // align base to 1024 for the 128-byte swizzle atoms
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
 
   const int K = p.K;
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
 
   if (p.ctrl != nullptr && p.skip_if_done && p.ctrl->done) return;
 
-  const size_t sbytes = LseSmem<T>::stage_bytes(p.nbox, p.box_rows);
+  const size_t sbytes = LseSmem<T, G>::stage_bytes(p.nbox, p.box_rows);
   unsigned char* stage_base = smem;
-  T* a_s = reinterpret_cast<T*>(smem + p.stages * sbytes);
-  T* w_s = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(a_s) +
-                                LseSmem<T>::round_up_dev(static_cast<size_t>(K) * sizeof(T), 16));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(w_s) + 128 * sizeof(T));
-  double* red_s = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(bars) + 64);
+  unsigned char* cur = smem + p.stages * sbytes;
+  T* a_s = reinterpret_cast<T*>(cur);
+  cur += LseSmem<T, G>::a_bytes(K);
+  T* w_s = reinterpret_cast<T*>(cur);
+  cur += LseSmem<T, G>::kW;
+  T* colm = reinterpret_cast<T*>(cur);         // [G][32] partial maxima
+  T* cols = colm + G * 32;                     // [G][32] partial sums
+  cur += LseSmem<T, G>::kParts;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cur);
+  cur += LseSmem<T, G>::kBars;
+  double* red_s = reinterpret_cast<double*>(cur);
 
   const int num_strips = p.num_strips;
   const int my_first = blockIdx.x;
@@ -106,9 +120,8 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
     for (int s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
   }
-  // a_k = f_k + log N_k (FP32 path: in log2 units)
-  for (int k = tid; k < K; k += kThreads) {
-    double a = p.f[k] + p.logN[k];
+  for (int k = tid; k < K; k += THREADS) {
+    const double a = p.f[k] + p.logN[k];
     if constexpr (sizeof(T) == 4) {
       a_s[k] = static_cast<T>(a * 1.4426950408889634);
     } else {
@@ -118,7 +131,6 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
   __syncthreads();
 
   const uint32_t tx_bytes = static_cast<uint32_t>(sbytes);
-  // prologue: fill the pipeline
   if (tid == 0) {
     for (int s = 0; s < p.stages && s < my_count; ++s) {
       const int strip = my_first + s * stride;
@@ -129,17 +141,24 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
     }
   }
 
-  // Per-thread row ownership for phase B.
-  double acc64[kMaxRowsPerThread];
-  float acc32[kMaxRowsPerThread];
+  double acc64[CF::ROWS_PT];
+  float acc32[CF::ROWS_PT];
 #pragma unroll
-  for (int j = 0; j < kMaxRowsPerThread; ++j) {
+  for (int j = 0; j < CF::ROWS_PT; ++j) {
     acc64[j] = 0.0;
     acc32[j] = 0.f;
   }
 
-  const int col = tid / R;  // phase-A column within the strip
-  const int rg = tid % R;   // phase-A row group
+  // phase-A geometry of this thread
+  const int q = warp & 7;                    // 16-byte chunk (column group) of the strip
+  const int h = warp >> 3;                   // row half (0..G-1)
+  const int col = q * CPW + lane / LW;       // column within the strip
+  const int r0 = h * LW + (lane % LW);       // first row; rows r0, r0 + R, ...
+  // byte offset of (row r0, col) inside the swizzled tile; rows r0 + R*j keep
+  // the same swizzle phase (R is a multiple of 8), so the stride is R*128 bytes
+  const uint32_t off0 = static_cast<uint32_t>(r0) * 128u + ((static_cast<uint32_t>(q) ^ (r0 & 7u)) << 4) +
+                        static_cast<uint32_t>((col % CPW) * sizeof(T));
+  constexpr uint32_t kRowStep = R * 128u;
   int it_fail = -1;
 
   for (int it = 0; it < my_count; ++it) {
@@ -148,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
     const int strip = my_first + it * stride;
     unsigned char* tile = stage_base + s * sbytes;
     const bool ok = mbar_wait_bounded(&bars[s], parity, kMaxSpins);
-    if (__syncthreads_or(!ok)) {  // uniform decision across the CTA
+    if (__syncthreads_or(!ok)) {
       it_fail = it;
       break;
     }
@@ -156,43 +175,67 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
     const bool valid = gcol < p.n;
 
     // ---- A1: column maximum of x = a_k - v_kp ----
-    T m = -INFINITY;
-    for (int k = rg; k < K; k += R) {
-      const uint32_t off = swz128(k, (col * sizeof(T)) / 16) + (col * sizeof(T)) % 16;
-      const T v = *reinterpret_cast<const T*>(tile + off);
-      T x;
-      if constexpr (sizeof(T) == 4) {
-        x = fmaf(-v, lse_scale(), a_s[k]);
-      } else {
-        x = a_s[k] - v;
+    T m0 = -INFINITY, m1 = -INFINITY;
+    {
+      int k = r0;
+      uint32_t off = off0;
+      for (; k + R < K; k += 2 * R, off += 2 * kRowStep) {
+        const T v0 = *reinterpret_cast<const T*>(tile + off);
+        const T v1 = *reinterpret_cast<const T*>(tile + off + kRowStep);
+        m0 = tmax(m0, expo(a_s[k], v0));
+        m1 = tmax(m1, expo(a_s[k + R], v1));
       }
-      m = tmax(m, x);
+      if (k < K) m0 = tmax(m0, expo(a_s[k], *reinterpret_cast<const T*>(tile + off)));
     }
+    T m = tmax(m0, m1);
 #pragma unroll
-    for (int o = R / 2; o >= 1; o >>= 1) m = tmax(m, shfl_xor(m, o));
+    for (int o = LW / 2; o >= 1; o >>= 1) m = tmax(m, shfl_xor(m, o));
+    if constexpr (G > 1) {
+      if ((lane % LW) == 0) colm[h * 32 + col] = m;
+      __syncthreads();
+#pragma unroll
+      for (int g = 0; g < G; ++g) m = tmax(m, colm[g * 32 + col]);
+    }
 
     // ---- A2: e = exp(x - m) in place, column sum ----
-    T ssum = T(0);
-    for (int k = rg; k < K; k += R) {
-      const uint32_t off = swz128(k, (col * sizeof(T)) / 16) + (col * sizeof(T)) % 16;
-      T* ptr = reinterpret_cast<T*>(tile + off);
-      T x;
-      if constexpr (sizeof(T) == 4) {
-        x = fmaf(-*ptr, lse_scale(), a_s[k]);
-      } else {
-        x = a_s[k] - *ptr;
+    T s0 = T(0), s1 = T(0);
+    {
+      int k = r0;
+      uint32_t off = off0;
+      for (; k + R < K; k += 2 * R, off += 2 * kRowStep) {
+        T* p0 = reinterpret_cast<T*>(tile + off);
+        T* p1 = reinterpret_cast<T*>(tile + off + kRowStep);
+        const T e0 = lse_exp(expo(a_s[k], *p0) - m);
+        const T e1 = lse_exp(expo(a_s[k + R], *p1) - m);
+        *p0 = e0;
+        *p1 = e1;
+        s0 += e0;
+        s1 += e1;
       }
-      const T e = lse_exp(x - m);
-      *ptr = e;
-      ssum += e;
+      if (k < K) {
+        T* p0 = reinterpret_cast<T*>(tile + off);
+        const T e0 = lse_exp(expo(a_s[k], *p0) - m);
+        *p0 = e0;
+        s0 += e0;
+      }
     }
+    T ssum = s0 + s1;
 #pragma unroll
-    for (int o = R / 2; o >= 1; o >>= 1) ssum += shfl_xor(ssum, o);
-    if (rg == 0) {
+    for (int o = LW / 2; o >= 1; o >>= 1) ssum += shfl_xor(ssum, o);
+    if constexpr (G > 1) {
+      if ((lane % LW) == 0) cols[h * 32 + col] = ssum;
+      __syncthreads();
+    }
+    if (h == 0 && (lane % LW) == 0) {
+      if constexpr (G > 1) {
+        ssum = T(0);
+#pragma unroll
+        for (int g = 0; g < G; ++g) ssum += cols[g * 32 + col];
+      }
       T w = T(0);
       if (valid) {
-        const T h = p.H ? static_cast<T>(p.H[gcol]) : T(1);
-        w = h / ssum;
+        const T hc = p.H ? static_cast<T>(p.H[gcol]) : T(1);
+        w = hc / ssum;
         if (p.logden != nullptr) {
           T ld;
           if constexpr (sizeof(T) == 4) {
@@ -209,38 +252,48 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
 
     // ---- B: row sums over the strip ----
 #pragma unroll
-    for (int j = 0; j < kMaxRowsPerThread; ++j) {
-      const int k = tid + j * kThreads;
+    for (int j = 0; j < CF::ROWS_PT; ++j) {
+      const int k = tid + j * THREADS;
       if (k < K) {
         if constexpr (sizeof(T) == 4) {
-          float part = 0.f;
+          float pa = 0.f, pb = 0.f;
 #pragma unroll
-          for (int ch = 0; ch < 8; ++ch) {
-            const float4 e4 = *reinterpret_cast<const float4*>(tile + swz128(k, ch));
-            const float4 w4 = *reinterpret_cast<const float4*>(w_s + ch * 4);
-            part = fmaf(e4.x, w4.x, part);
-            part = fmaf(e4.y, w4.y, part);
-            part = fmaf(e4.z, w4.z, part);
-            part = fmaf(e4.w, w4.w, part);
+          for (int ch = 0; ch < 8; ch += 2) {
+            const float4 ea = *reinterpret_cast<const float4*>(tile + swz128(k, ch));
+            const float4 wa = *reinterpret_cast<const float4*>(w_s + ch * 4);
+            const float4 eb = *reinterpret_cast<const float4*>(tile + swz128(k, ch + 1));
+            const float4 wb = *reinterpret_cast<const float4*>(w_s + ch * 4 + 4);
+            pa = fmaf(ea.x, wa.x, pa);
+            pb = fmaf(eb.x, wb.x, pb);
+            pa = fmaf(ea.y, wa.y, pa);
+            pb = fmaf(eb.y, wb.y, pb);
+            pa = fmaf(ea.z, wa.z, pa);
+            pb = fmaf(eb.z, wb.z, pb);
+            pa = fmaf(ea.w, wa.w, pa);
+            pb = fmaf(eb.w, wb.w, pb);
           }
-          acc32[j] += part;
+          acc32[j] += pa + pb;
         } else {
-          double part = 0.0;
+          double pa = 0.0, pb = 0.0;
 #pragma unroll
-          for (int ch = 0; ch < 8; ++ch) {
-            const double2 e2 = *reinterpret_cast<const double2*>(tile + swz128(k, ch));
-            const double2 w2 = *reinterpret_cast<const double2*>(w_s + ch * 2);
-            part = fma(e2.x, w2.x, part);
-            part = fma(e2.y, w2.y, part);
+          for (int ch = 0; ch < 8; ch += 2) {
+            const double2 ea = *reinterpret_cast<const double2*>(tile + swz128(k, ch));
+            const double2 wa = *reinterpret_cast<const double2*>(w_s + ch * 2);
+            const double2 eb = *reinterpret_cast<const double2*>(tile + swz128(k, ch + 1));
+            const double2 wb = *reinterpret_cast<const double2*>(w_s + ch * 2 + 2);
+            pa = fma(ea.x, wa.x, pa);
+            pb = fma(eb.x, wb.x, pb);
+            pa = fma(ea.y, wa.y, pa);
+            pb = fma(eb.y, wb.y, pb);
           }
-          acc64[j] += part;
+          acc64[j] += pa + pb;
         }
       }
     }
     if constexpr (sizeof(T) == 4) {
       if ((it + 1) % kFlushStrips == 0) {
 #pragma unroll
-        for (int j = 0; j < kMaxRowsPerThread; ++j) {
+        for (int j = 0; j < CF::ROWS_PT; ++j) {
           acc64[j] += static_cast<double>(acc32[j]);
           acc32[j] = 0.f;
         }
@@ -271,8 +324,8 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
   // ---- per-CTA partials ----
   double* part = p.partials + static_cast<size_t>(blockIdx.x) * K;
 #pragma unroll
-  for (int j = 0; j < kMaxRowsPerThread; ++j) {
-    const int k = tid + j * kThreads;
+  for (int j = 0; j < CF::ROWS_PT; ++j) {
+    const int k = tid + j * THREADS;
     if (k < K) {
       double v = acc64[j];
       if constexpr (sizeof(T) == 4) v += static_cast<double>(acc32[j]);
@@ -292,51 +345,58 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
 
   // ---- last CTA: fixed-order reduction and the SCI epilogue ----
   double* fnew_s = red_s;  // K doubles
-  for (int k = tid; k < K; k += kThreads) {
-    double q = 0.0;
-    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) q += p.partials[static_cast<size_t>(b) * K + k];
-    p.Q[k] = q;
-    fnew_s[k] = p.f[k] + p.logN[k] - log(q);
+  for (int k = tid; k < K; k += THREADS) {
+    double qk = 0.0;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) qk += p.partials[static_cast<size_t>(b) * K + k];
+    p.Q[k] = qk;
+    fnew_s[k] = p.f[k] + p.logN[k] - log(qk);
   }
   __syncthreads();
   if (p.mode == kLseModeSci) {
     const double f0 = fnew_s[0];
+    const double fin0 = p.f[0];
     double smax = -1.0;  // -1 = no f_k != 0 seen
+    double dmax = 0.0;
     bool finite = true;
-    for (int k = tid; k < K; k += kThreads) {
+    for (int k = tid; k < K; k += THREADS) {
       const double fo = fnew_s[k] - f0;
       const double fi = p.f[k];
       if (p.f_out) p.f_out[k] = fo;
       if (p.g_out) p.g_out[k] = p.Q[k] - p.Nk[k];
       if (!isfinite(fo)) finite = false;
       if (fi != 0.0) smax = fmax(smax, fabs(fo / fi - 1.0));
+      dmax = fmax(dmax, fabs(fo - (fi - fin0)));
     }
-    // block max
-    __shared__ double red[kThreads / 32];
-    __shared__ int fin[kThreads / 32];
+    __shared__ double red[THREADS / 32];
+    __shared__ double redd[THREADS / 32];
+    __shared__ int fin[THREADS / 32];
     for (int o = 16; o >= 1; o >>= 1) {
       smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     }
     const int allfin = __all_sync(0xffffffffu, finite);
-    if ((tid & 31) == 0) {
-      red[tid >> 5] = smax;
-      fin[tid >> 5] = allfin;
+    if (lane == 0) {
+      red[warp] = smax;
+      redd[warp] = dmax;
+      fin[warp] = allfin;
     }
     __syncthreads();
     if (tid == 0) {
-      double sm = -1.0;
-      int ok = 1;
-      for (int w = 0; w < kThreads / 32; ++w) {
+      double sm = -1.0, dm = 0.0;
+      int okf = 1;
+      for (int w = 0; w < THREADS / 32; ++w) {
         sm = fmax(sm, red[w]);
-        ok &= fin[w];
+        dm = fmax(dm, redd[w]);
+        okf &= fin[w];
       }
       const double s = (sm < 0.0) ? INFINITY : sm;
       if (p.s_out) *p.s_out = s;
+      if (p.d_out) *p.d_out = dm;
       if (p.ctrl) {
         p.ctrl->iters += 1;
         p.ctrl->last_s = s;
-        if (!ok) p.ctrl->nonfinite = 1;
-        if (p.eps > 0.0 && s < p.eps) p.ctrl->done = 1;
+        if (!okf) p.ctrl->nonfinite = 1;
+        if ((p.eps > 0.0 && s < p.eps) || (p.noise > 0.0 && dm < p.noise)) p.ctrl->done = 1;
       }
     }
   }
@@ -347,33 +407,57 @@ __global__ void __launch_bounds__(kThreads) lse_pass_kernel(const __grid_constan
 // host side
 // ---------------------------------------------------------------------------
 
+namespace {
+
+// CTA width per element type: FP32 runs 512 threads (G = 2), FP64 256 (G = 1).
+constexpr int kGf32 = 2;
+constexpr int kGf64 = 1;
+
+template <typename T, int G>
+int lse_occupancy(size_t smem) {
+  static size_t max_dyn = 0;
+  if (max_dyn == 0) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, lse_pass_kernel<T, G>);
+    max_dyn = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+    cudaFuncSetAttribute(lse_pass_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(max_dyn));
+  }
+  if (smem > max_dyn) return 0;
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, lse_pass_kernel<T, G>, Cfg<T, G>::THREADS, smem) !=
+      cudaSuccess)
+    blocks = 0;
+  return blocks;
+}
+
+}  // namespace
+
 LsePlan lse_plan(int64_t K, int64_t n, int dtype_bytes) {
   LsePlan pl{};
   const int C = 128 / dtype_bytes;
   pl.C = C;
+  pl.threads = dtype_bytes == 4 ? Cfg<float, kGf32>::THREADS : Cfg<double, kGf64>::THREADS;
   pl.num_strips = static_cast<int>(ceil_div(n, C));
   pl.box_rows = static_cast<int>(std::min<int64_t>(256, round_up(K, 8)));
   pl.nbox = static_cast<int>(ceil_div(K, pl.box_rows));
   const size_t sb = static_cast<size_t>(pl.nbox) * pl.box_rows * 128;
   pl.stages = sb <= 48 * 1024 ? 4 : (sb <= 64 * 1024 ? 3 : (sb <= 96 * 1024 ? 2 : 1));
-  const size_t extra = (dtype_bytes == 4) ? LseSmem<float>::extra_bytes(static_cast<int>(K))
-                                          : LseSmem<double>::extra_bytes(static_cast<int>(K));
+  const size_t extra = (dtype_bytes == 4) ? LseSmem<float, kGf32>::extra_bytes(static_cast<int>(K))
+                                          : LseSmem<double, kGf64>::extra_bytes(static_cast<int>(K));
   pl.smem = pl.stages * sb + extra + 1024;  // + alignment slack
   static int occ_cache[2][1025] = {};
   int* occ = &occ_cache[dtype_bytes == 4 ? 0 : 1][std::min<int64_t>(K, 1024)];
   if (*occ == 0) {
-    int blocks = 1;
-    if (dtype_bytes == 4) {
-      cudaFuncSetAttribute(lse_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, lse_pass_kernel<float>, kThreads, pl.smem);
-    } else {
-      cudaFuncSetAttribute(lse_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, lse_pass_kernel<double>, kThreads, pl.smem);
-    }
-    *occ = std::max(1, blocks);
+    *occ = (dtype_bytes == 4) ? lse_occupancy<float, kGf32>(pl.smem) : lse_occupancy<double, kGf64>(pl.smem);
+    cudaGetLastError();  // the probes above report through their return values
   }
-  pl.grid = static_cast<int>(std::min<int64_t>(pl.num_strips, static_cast<int64_t>(*occ) * num_sms()));
+  pl.grid = static_cast<int>(std::min<int64_t>(pl.num_strips, static_cast<int64_t>(std::max(*occ, 1)) * num_sms()));
   pl.grid = std::max(pl.grid, 1);
+  pl.ok = *occ > 0;
   return pl;
 }
 
@@ -384,17 +468,20 @@ size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes) {
 
 mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm, int dtype_bytes,
                        cudaStream_t stream) {
+  if (!pl.ok) {
+    set_error("lse pass: %zu bytes of shared memory per CTA exceed the device limit", pl.smem);
+    return MBAR_EUNSUPPORTED;
+  }
   prm.num_strips = pl.num_strips;
   prm.box_rows = pl.box_rows;
   prm.nbox = pl.nbox;
   prm.stages = pl.stages;
   if (dtype_bytes == 4) {
-    lse_pass_kernel<float><<<pl.grid, kThreads, pl.smem, stream>>>(tmap, prm);
-    count_launches(1);
+    lse_pass_kernel<float, kGf32><<<pl.grid, pl.threads, pl.smem, stream>>>(tmap, prm);
   } else {
-    lse_pass_kernel<double><<<pl.grid, kThreads, pl.smem, stream>>>(tmap, prm);
-    count_launches(1);
+    lse_pass_kernel<double, kGf64><<<pl.grid, pl.threads, pl.smem, stream>>>(tmap, prm);
   }
+  count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
 }

@@ -53,6 +53,7 @@ class Opts(ctypes.Structure):
         ("warm_tol", ctypes.c_double),
         ("max_newton", ctypes.c_int32),
         ("max_sci", ctypes.c_int32),
+        ("noise_floor", ctypes.c_double),
     ]
 
 
@@ -97,6 +98,8 @@ _SIGNATURES = {
     "mbar_set_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
     "mbar_get_timing": ([_vp, ctypes.c_int32, _i64p, _dp, _dp], ctypes.c_int),
     "mbar_kernel_launches": ([_i64p], ctypes.c_int),
+    "mbar_get_trace": ([_vp, _i64p, _dp, ctypes.c_int64], ctypes.c_int),
+    "mbar_set_hessian_path": ([ctypes.c_int32], ctypes.c_int),
     "mbar_lse_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32], ctypes.c_size_t),
     "mbar_lse_pass": ([_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
                        _vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
@@ -256,6 +259,14 @@ class Context:
         _check(lib().mbar_get_timing(self._h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
         return n.value, ms.value, by.value
 
+    def trace(self) -> np.ndarray:
+        """Rows (phase, n, a, b) of the last solve (see mbar_get_trace)."""
+        n = ctypes.c_int64()
+        _check(lib().mbar_get_trace(self._h, ctypes.byref(n), None, 0))
+        out = np.empty((n.value, 4))
+        _check(lib().mbar_get_trace(self._h, ctypes.byref(n), _ptr(out), n.value))
+        return out
+
     def close(self):
         if self._h:
             _check(lib().mbar_destroy(self._h))
@@ -272,6 +283,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def set_hessian_path(path: int):
+    """0 = by size (tensor cores for K >= 64), 1 = CUDA cores, 2 = tensor cores."""
+    _check(lib().mbar_set_hessian_path(int(path)))
 
 
 def kernel_launches() -> int:

@@ -50,7 +50,8 @@ def test_struct_layout_matches_binding():
 #include <stddef.h>
 #include "bumbar.h"
 int main(void){
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mbar_opts), offsetof(mbar_opts, f_tol), offsetof(mbar_opts, max_sci),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(mbar_opts), offsetof(mbar_opts, f_tol), offsetof(mbar_opts, max_sci),
+         offsetof(mbar_opts, noise_floor),
          sizeof(mbar_report), offsetof(mbar_report, max_abs_grad), offsetof(mbar_report, last_step));
   return 0;
 }'''
@@ -60,7 +61,7 @@ int main(void){
         exe = os.path.join(d, "t")
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
-    assert vals == [ctypes.sizeof(M.Opts), M.Opts.f_tol.offset, M.Opts.max_sci.offset,
+    assert vals == [ctypes.sizeof(M.Opts), M.Opts.f_tol.offset, M.Opts.max_sci.offset, M.Opts.noise_floor.offset,
                     ctypes.sizeof(M.Report), M.Report.max_abs_grad.offset, M.Report.last_step.offset]
 
 
