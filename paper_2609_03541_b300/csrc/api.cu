@@ -267,17 +267,20 @@ mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
   return s;
 }
 
-mbar_status count_at(mbar_ctx* c, double w, int64_t* g) {
-  BUMBAR_TRY(count_bins(c->phi_sorted, c->N, w, c->count, c->st));
-  unsigned long long h = 0;
-  BUMBAR_CUDA(cudaMemcpyAsync(&h, c->count, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+mbar_status count_at(mbar_ctx* c, const double* ws, int nw, int64_t* g) {
+  BUMBAR_TRY(count_bins(c->phi_sorted, c->N, ws, nw, c->count, c->st));
+  unsigned long long h[kWidthsPerPass];
+  BUMBAR_CUDA(cudaMemcpyAsync(h, c->count, nw * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
   BUMBAR_CUDA(cudaStreamSynchronize(c->st));
-  *g = static_cast<int64_t>(h);
+  for (int i = 0; i < nw; ++i) g[i] = static_cast<int64_t>(h[i]);
   return MBAR_OK;
 }
 
 // Width rule w*(n) by the deterministic search; *found = false when n cannot
-// be reached (the caller then uses the unbinned data).
+// be reached (the caller then uses the unbinned data). The bisection is the
+// sequential one, evaluated four levels at a time: one counting pass gets
+// g at all 15 midpoints of the next four levels of the bisection tree, then
+// the host walks the path the sequential search would take.
 mbar_status width_search(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
   BUMBAR_TRY(ensure_sorted(c));
   const double R = c->phi_hi - c->phi_lo;
@@ -294,20 +297,45 @@ mbar_status width_search(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
       return MBAR_OK;
     }
     int64_t g = 0;
-    BUMBAR_TRY(count_at(c, w_lo, &g));
+    BUMBAR_TRY(count_at(c, &w_lo, 1, &g));
     if (g >= n) break;
     w_hi = w_lo;
     w_lo = w_lo * 0.5;
   }
-  for (int it = 0; it < 64; ++it) {
-    const double mid = std::sqrt(w_lo * w_hi);
-    if (!(w_lo < mid && mid < w_hi)) break;
-    int64_t g = 0;
-    BUMBAR_TRY(count_at(c, mid, &g));
-    if (g >= n)
-      w_lo = mid;
-    else
-      w_hi = mid;
+  constexpr int kLevels = 4;  // 2^4 - 1 = 15 midpoints per pass
+  int steps = 0;
+  bool stop = false;
+  while (!stop && steps < 64) {
+    double mid[16], a[16], b[16];
+    a[1] = w_lo;
+    b[1] = w_hi;
+    for (int node = 1; node < 16; ++node) {
+      mid[node] = std::sqrt(a[node] * b[node]);
+      if (2 * node < 16) {
+        a[2 * node] = a[node];
+        b[2 * node] = mid[node];
+        a[2 * node + 1] = mid[node];
+        b[2 * node + 1] = b[node];
+      }
+    }
+    int64_t g[16];
+    BUMBAR_TRY(count_at(c, mid + 1, 15, g + 1));
+    int node = 1;
+    for (int d = 0; d < kLevels && steps < 64; ++d) {
+      const double m = mid[node];
+      if (!(w_lo < m && m < w_hi)) {
+        stop = true;
+        break;
+      }
+      ++steps;
+      if (g[node] >= n) {
+        w_lo = m;
+        node = 2 * node + 1;
+      } else {
+        w_hi = m;
+        node = 2 * node;
+      }
+    }
   }
   *w_out = w_lo;
   return MBAR_OK;
@@ -761,7 +789,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   TRYC(dalloc_t(c, &c->hess, K * K));
   TRYC(dalloc_t(c, &c->info, 1));
   TRYC(dalloc_t(c, &c->bad, 1));
-  TRYC(dalloc_t(c, &c->count, 1));
+  TRYC(dalloc_t(c, &c->count, kWidthsPerPass));
   TRYC(dalloc_t(c, &c->nb_dev, 1));
   void* ctrl = nullptr;
   TRYC(dalloc(c, &ctrl, sizeof(Ctrl)));

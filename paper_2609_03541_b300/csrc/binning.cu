@@ -21,6 +21,7 @@ namespace {
 
 constexpr int kSortTile = 1024;  // elements per warp tile
 constexpr int kScanBlock = 1024; // elements per block in the scan (256 threads x 4)
+constexpr int kMaxWidths = 15;   // candidate widths per counting pass
 
 __device__ __forceinline__ unsigned long long order_key(double x) {
   unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -30,6 +31,20 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
 __device__ __forceinline__ long long bin_index(double phi, double lo, double w) {
   const double q = __ddiv_rn(__dsub_rn(phi, lo), w);
   return static_cast<long long>(floor(q));
+}
+
+// Same value as bin_index, mostly without the division: with rw = RN(1/w),
+// q = RN(d * rw) lies within (d/w) 2^-52 of d/w, as does RN(d/w), so their
+// floors can only differ when q is that close to an integer; those rare
+// cases take the correctly rounded division.
+__device__ __forceinline__ long long bin_index_fast(double phi, double lo, double w, double rw) {
+  const double d = __dsub_rn(phi, lo);
+  const double q = __dmul_rn(d, rw);
+  const double fq = floor(q);
+  const double r = q - fq;
+  const double tol = q * 0x1p-49;
+  if (r <= tol || 1.0 - r <= tol) return static_cast<long long>(floor(__ddiv_rn(d, w)));
+  return static_cast<long long>(fq);
 }
 
 // ---------------------------------------------------------------------------
@@ -196,26 +211,45 @@ __global__ void gather_phi(const double* __restrict__ phi, const int32_t* __rest
 // ---------------------------------------------------------------------------
 // histogram over sorted phi
 // ---------------------------------------------------------------------------
-__global__ void count_heads(const double* __restrict__ phi, int64_t N, double w,
-                            unsigned long long* __restrict__ count) {
+// Number of nonempty bins for up to kMaxWidths widths in one pass over the
+// sorted coordinate (head flags counted by warp ballots).
+struct WidthSet {
+  double w[kMaxWidths];
+  double rw[kMaxWidths];
+  int n;
+};
+
+__global__ void count_heads_multi(const double* __restrict__ phi, int64_t N, WidthSet ws,
+                                  unsigned long long* __restrict__ counts) {
+  __shared__ unsigned int cnt[kMaxWidths];
+  if (threadIdx.x < kMaxWidths) cnt[threadIdx.x] = 0u;
+  __syncthreads();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const double lo = phi[0];
-  long long key = 0;
-  if (i < N) key = bin_index(phi[i], lo, w);
-  long long prev = __shfl_up_sync(0xffffffffu, key, 1);
-  if ((threadIdx.x & 31) == 0 && i > 0 && i < N) prev = bin_index(phi[i - 1], lo, w);
-  const int head = (i < N) && (i == 0 || key != prev);
-  const int n = __syncthreads_count(head);
-  if (threadIdx.x == 0 && n) atomicAdd(count, static_cast<unsigned long long>(n));
+  const bool in = i < N;
+  const double x = in ? phi[i] : lo;
+  const double xp = (in && i > 0) ? phi[i - 1] : lo;
+  for (int c = 0; c < ws.n; ++c) {
+    bool head = false;
+    if (in) {
+      const long long key = bin_index_fast(x, lo, ws.w[c], ws.rw[c]);
+      head = (i == 0) || key != bin_index_fast(xp, lo, ws.w[c], ws.rw[c]);
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, head);
+    if (lane == 0 && b) atomicAdd(&cnt[c], static_cast<unsigned>(__popc(b)));
+  }
+  __syncthreads();
+  if (threadIdx.x < ws.n && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], static_cast<unsigned long long>(cnt[threadIdx.x]));
 }
 
-__global__ void head_flags(const double* __restrict__ phi, int64_t N, double w, int* __restrict__ flags) {
+__global__ void head_flags(const double* __restrict__ phi, int64_t N, double w, double rw, int* __restrict__ flags) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const double lo = phi[0];
   long long key = 0;
-  if (i < N) key = bin_index(phi[i], lo, w);
+  if (i < N) key = bin_index_fast(phi[i], lo, w, rw);
   long long prev = __shfl_up_sync(0xffffffffu, key, 1);
-  if ((threadIdx.x & 31) == 0 && i > 0 && i < N) prev = bin_index(phi[i - 1], lo, w);
+  if ((threadIdx.x & 31) == 0 && i > 0 && i < N) prev = bin_index_fast(phi[i - 1], lo, w, rw);
   if (i < N) flags[i] = (i == 0 || key != prev) ? 1 : 0;
 }
 
@@ -244,76 +278,186 @@ __global__ void counts_from_starts(const int32_t* __restrict__ start, int64_t nb
 }
 
 // ---------------------------------------------------------------------------
-// binned means: each thread walks one (row, tile of TW sorted columns)
+// binned means: segmented sums over contiguous sorted columns
 // ---------------------------------------------------------------------------
-template <typename T, int TW>
-__global__ void bin_means_tiles(const T* __restrict__ v, int64_t K, int64_t N, int64_t ld,
-                                const int32_t* __restrict__ seg, const int32_t* __restrict__ start,
-                                T* __restrict__ out, int64_t ld_out, double* __restrict__ part0,
-                                double* __restrict__ part1, int64_t ntiles) {
-  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t k = blockIdx.y;
-  if (t >= ntiles) return;
-  const int64_t c0 = t * TW;
-  const int64_t c1 = (c0 + TW < N) ? c0 + TW : N;
-  const T* row = v + k * ld;
-  int cur = seg[c0];
-  double sum = 0.0;
-  bool first_run = true;
-  double p0 = 0.0, p1 = 0.0;
-  for (int64_t c = c0; c < c1; ++c) {
-    const int s = seg[c];
-    if (s != cur) {
-      // run of bin `cur` ends at column c-1 inside this tile
-      const bool starts_here = start[cur] >= c0;
-      if (starts_here) {
-        out[k * ld_out + cur] = static_cast<T>(sum / static_cast<double>(start[cur + 1] - start[cur]));
-      } else {
-        p0 = sum;  // first run, bin began in an earlier tile
-      }
-      first_run = false;
-      cur = s;
-      sum = 0.0;
+// A block owns a tile of 2048 sorted columns (256 threads x 8 consecutive
+// columns) for kRowsPerBlock rows. Per row, each thread splits its 8 values
+// into runs of equal bin ordinal; runs that start and end inside the thread
+// are written at once; the last run of each thread enters a block-wide
+// segmented inclusive scan (FP64) that carries it across thread boundaries.
+// A bin whose run ends in a thread is finished there: written if the bin
+// started in this tile, else its partial goes to carry0[tile] (a bin that
+// began in an earlier tile). The last thread's still-open run goes to
+// carry1[tile] (a bin that starts in this tile and continues) or, if it
+// began before the tile, to carry0[tile]. A fix-up kernel finishes bins that
+// span tiles: sum = carry1[first tile] + carry0[later tiles], in order.
+constexpr int kBmCols = 8;
+constexpr int kBmTile = kThreads * kBmCols;  // 2048
+constexpr int kRowsPerBlock = 4;
+
+template <typename T>
+__device__ __forceinline__ void load8(const T* src, int nvalid, double* x) {
+  if constexpr (sizeof(T) == 4) {
+    if (nvalid == 8) {
+      const float4 a = *reinterpret_cast<const float4*>(src);
+      const float4 b = *reinterpret_cast<const float4*>(src + 4);
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+      x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+      return;
     }
-    sum += static_cast<double>(row[c]);
-  }
-  // last run of the tile
-  const bool starts_here = start[cur] >= c0;
-  const bool ends_here = start[cur + 1] <= c1;
-  if (starts_here && ends_here) {
-    out[k * ld_out + cur] = static_cast<T>(sum / static_cast<double>(start[cur + 1] - start[cur]));
-  } else if (first_run) {
-    p0 = sum;  // the only run of the tile, cut on at least one side
   } else {
-    p1 = sum;  // last run, continues into the next tile
+    if (nvalid == 8) {
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        const double2 a = *reinterpret_cast<const double2*>(src + j);
+        x[j] = a.x;
+        x[j + 1] = a.y;
+      }
+      return;
+    }
   }
-  part0[k * ntiles + t] = p0;
-  part1[k * ntiles + t] = p1;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (j < nvalid) ? static_cast<double>(src[j]) : 0.0;
 }
 
-template <typename T, int TW>
-__global__ void bin_means_fixup(int64_t K, int64_t nb, const int32_t* __restrict__ start, T* __restrict__ out,
-                                int64_t ld_out, const double* __restrict__ part0, const double* __restrict__ part1,
-                                int64_t ntiles) {
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__ v, int64_t K, int64_t N, int64_t ld,
+                                                           const int32_t* __restrict__ seg,
+                                                           const int32_t* __restrict__ start, T* __restrict__ out,
+                                                           int64_t ld_out, double* __restrict__ carry0,
+                                                           double* __restrict__ carry1, int64_t ntiles) {
+  __shared__ double wv[kThreads / 32];
+  __shared__ int wf[kThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t tile = blockIdx.x;
+  const int64_t tile0 = tile * kBmTile;
+  const int64_t tile_end = (tile0 + kBmTile < N) ? tile0 + kBmTile : N;
+  const int64_t c0 = tile0 + static_cast<int64_t>(tid) * kBmCols;
+  const int nvalid = static_cast<int>(c0 < N ? ((N - c0) < kBmCols ? (N - c0) : kBmCols) : 0);
+  const bool last_thread = nvalid > 0 && c0 + nvalid == tile_end;
+
+  // run structure of this thread's columns (identical for every row)
+  int sg[kBmCols];
+#pragma unroll
+  for (int j = 0; j < kBmCols; ++j) sg[j] = (j < nvalid) ? seg[c0 + j] : -1;
+  const int b0 = sg[0];
+  const int bl = nvalid > 0 ? sg[nvalid - 1] : -1;
+  int nruns = 0;
+#pragma unroll
+  for (int j = 1; j < kBmCols; ++j)
+    if (j < nvalid && sg[j] != sg[j - 1]) ++nruns;
+  const int64_t st_b0 = nvalid > 0 ? start[b0] : 0;
+  const int64_t st_bl = nvalid > 0 ? start[bl] : 0;
+  const int64_t en_bl = nvalid > 0 ? start[bl + 1] : 0;
+  const bool flag = nvalid <= 0 || nruns > 0 || st_bl >= c0;  // last run starts in this thread
+  const bool cont = nvalid > 0 && st_b0 < c0;                 // first run continues from the left
+  const bool last_ends_here = nvalid > 0 && en_bl <= c0 + nvalid;
+
+  const int64_t k_begin = static_cast<int64_t>(blockIdx.y) * kRowsPerBlock;
+  for (int64_t k = k_begin; k < K && k < k_begin + kRowsPerBlock; ++k) {
+    double x[kBmCols];
+    load8<T>(v + k * ld + c0, nvalid, x);
+    // local runs
+    double head = 0.0, run = 0.0;
+    int cur = b0;
+    bool first = true;
+#pragma unroll
+    for (int j = 0; j < kBmCols; ++j) {
+      if (j < nvalid) {
+        if (sg[j] != cur) {
+          if (first) {
+            head = run;
+            first = false;
+          } else {  // interior run: starts and ends inside this thread
+            out[k * ld_out + cur] = static_cast<T>(run / static_cast<double>(start[cur + 1] - start[cur]));
+          }
+          cur = sg[j];
+          run = 0.0;
+        }
+        run += x[j];
+      }
+    }
+    // block-wide segmented inclusive scan of the last-run sums
+    double sv = nvalid > 0 ? run : 0.0;
+    int sf = flag ? 1 : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double uv = __shfl_up_sync(0xffffffffu, sv, o);
+      const int uf = __shfl_up_sync(0xffffffffu, sf, o);
+      if (lane >= o) {
+        if (!sf) sv += uv;
+        sf |= uf;
+      }
+    }
+    if (lane == 31) {
+      wv[warp] = sv;
+      wf[warp] = sf;
+    }
+    __syncthreads();
+    double pv = 0.0;  // segmented prefix of all earlier warps
+    for (int w = 0; w < warp; ++w) pv = wf[w] ? wv[w] : pv + wv[w];
+    if (!sf) sv += pv;
+    double prev = __shfl_up_sync(0xffffffffu, sv, 1);
+    if (lane == 0) prev = pv;
+    if (tid == 0) prev = 0.0;
+    __syncthreads();
+    if (nvalid > 0) {
+      const double carry_in = cont ? prev : 0.0;
+      if (nruns > 0) {  // the first run ends inside this thread
+        const double tot = carry_in + head;
+        if (st_b0 >= tile0)
+          out[k * ld_out + b0] = static_cast<T>(tot / static_cast<double>(start[b0 + 1] - st_b0));
+        else
+          carry0[k * ntiles + tile] = tot;
+      }
+      if (last_ends_here) {
+        if (st_bl >= tile0)
+          out[k * ld_out + bl] = static_cast<T>(sv / static_cast<double>(en_bl - st_bl));
+        else
+          carry0[k * ntiles + tile] = sv;
+      } else if (last_thread) {
+        if (st_bl >= tile0)
+          carry1[k * ntiles + tile] = sv;
+        else
+          carry0[k * ntiles + tile] = sv;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void bin_sums_fixup(int64_t K, int64_t nb, const int32_t* __restrict__ start, T* __restrict__ out,
+                               int64_t ld_out, const double* __restrict__ carry0, const double* __restrict__ carry1,
+                               int64_t ntiles) {
   const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t k = blockIdx.y;
   if (b >= nb) return;
   const int64_t s = start[b], e = start[b + 1];
-  const int64_t ts = s / TW, te = (e - 1) / TW;
-  if (ts == te) return;  // complete inside one tile, written by the tile pass
-  const double* p0 = part0 + k * ntiles;
-  const double* p1 = part1 + k * ntiles;
-  double sum = (s == ts * TW) ? p0[ts] : p1[ts];
-  for (int64_t t = ts + 1; t <= te; ++t) sum += p0[t];
+  const int64_t ts = s / kBmTile, te = (e - 1) / kBmTile;
+  if (ts == te) return;  // finished inside one tile
+  double sum = carry1[k * ntiles + ts];
+  for (int64_t t = ts + 1; t <= te; ++t) sum += carry0[k * ntiles + t];
   out[k * ld_out + b] = static_cast<T>(sum / static_cast<double>(e - s));
 }
 
+// out[k][i] = in[k][perm[i]]: each thread loads perm[i] once and moves it
+// for 8 rows; blocks run row-group major so the 8 input rows being gathered
+// stay in L2.
+constexpr int kGatherRows = 8;
 template <typename T>
-__global__ void gather_cols_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t N, int64_t ld,
+__global__ void gather_cols_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t K, int64_t N, int64_t ld,
                                    const int32_t* __restrict__ perm) {
-  const int64_t k = blockIdx.y;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * kGatherRows;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < N) out[k * ld + i] = in[k * ld + perm[i]];
+  if (i >= N) return;
+  const int64_t src = perm[i];
+  T vals[kGatherRows];
+#pragma unroll
+  for (int r = 0; r < kGatherRows; ++r)
+    if (k0 + r < K) vals[r] = in[(k0 + r) * ld + src];
+#pragma unroll
+  for (int r = 0; r < kGatherRows; ++r)
+    if (k0 + r < K) out[(k0 + r) * ld + i] = vals[r];
 }
 
 }  // namespace
@@ -376,10 +520,20 @@ mbar_status sort_coordinate(const double* phi, int64_t N, double* phi_sorted, in
   return MBAR_OK;
 }
 
-mbar_status count_bins(const double* phi_sorted, int64_t N, double w, unsigned long long* count_dev,
-                       cudaStream_t st) {
-  BUMBAR_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long), st));
-  count_heads<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(phi_sorted, N, w, count_dev);
+mbar_status count_bins(const double* phi_sorted, int64_t N, const double* widths, int nw,
+                       unsigned long long* counts_dev, cudaStream_t st) {
+  if (nw < 1 || nw > kMaxWidths) {
+    set_error("count_bins: 1..%d widths per pass", kMaxWidths);
+    return MBAR_EINVAL;
+  }
+  WidthSet ws{};
+  ws.n = nw;
+  for (int c = 0; c < nw; ++c) {
+    ws.w[c] = widths[c];
+    ws.rw[c] = 1.0 / widths[c];
+  }
+  BUMBAR_CUDA(cudaMemsetAsync(counts_dev, 0, kMaxWidths * sizeof(unsigned long long), st));
+  count_heads_multi<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(phi_sorted, N, ws, counts_dev);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
@@ -399,7 +553,7 @@ mbar_status build_histogram(const double* phi_sorted, int64_t N, double w, int32
   int* excl = reinterpret_cast<int*>(p);
   p += round_up(N * 4, 256);
   const unsigned gN = static_cast<unsigned>(ceil_div(N, kThreads));
-  head_flags<<<gN, kThreads, 0, st>>>(phi_sorted, N, w, flags);
+  head_flags<<<gN, kThreads, 0, st>>>(phi_sorted, N, w, 1.0 / w, flags);
   count_launches(1);
   BUMBAR_TRY(excl_scan(flags, N, excl, nullptr, p, st));
   finish_histogram<<<gN, kThreads, 0, st>>>(phi_sorted, N, w, flags, excl, seg, start, keys, nb_dev);
@@ -414,11 +568,8 @@ mbar_status build_histogram(const double* phi_sorted, int64_t N, double w, int32
   return MBAR_OK;
 }
 
-static constexpr int kTileF32 = 64;
-static constexpr int kTileF64 = 32;
-
 size_t bin_means_tmp_bytes(int64_t K, int64_t N) {
-  const int64_t ntiles = ceil_div(N, kTileF64);  // the larger tile count of the two
+  const int64_t ntiles = ceil_div(N, kBmTile);
   return round_up(K * ntiles * 8, 256) * 2;
 }
 
@@ -429,26 +580,24 @@ mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int6
     set_error("bin_means: scratch too small");
     return MBAR_EINVAL;
   }
-  const int TW = dtype_bytes == 4 ? kTileF32 : kTileF64;
-  const int64_t ntiles = ceil_div(N, TW);
-  double* part0 = static_cast<double*>(tmp);
-  double* part1 = part0 + round_up(K * ntiles, 32);
-  const dim3 g1(static_cast<unsigned>(ceil_div(ntiles, kThreads)), static_cast<unsigned>(K));
+  const int64_t ntiles = ceil_div(N, kBmTile);
+  double* carry0 = static_cast<double*>(tmp);
+  double* carry1 = carry0 + round_up(K * ntiles, 32);
+  const dim3 g1(static_cast<unsigned>(ntiles), static_cast<unsigned>(ceil_div(K, kRowsPerBlock)));
   const dim3 g2(static_cast<unsigned>(ceil_div(nb, kThreads)), static_cast<unsigned>(K));
   if (dtype_bytes == 4) {
-    bin_means_tiles<float, kTileF32><<<g1, kThreads, 0, st>>>(static_cast<const float*>(v), K, N, ld, seg, start,
-                                                              static_cast<float*>(out), ld_out, part0, part1, ntiles);
+    bin_sums_block<float><<<g1, kThreads, 0, st>>>(static_cast<const float*>(v), K, N, ld, seg, start,
+                                                   static_cast<float*>(out), ld_out, carry0, carry1, ntiles);
     count_launches(1);
-    bin_means_fixup<float, kTileF32><<<g2, kThreads, 0, st>>>(K, nb, start, static_cast<float*>(out), ld_out, part0,
-                                                              part1, ntiles);
+    bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, nb, start, static_cast<float*>(out), ld_out, carry0, carry1,
+                                                   ntiles);
     count_launches(1);
   } else {
-    bin_means_tiles<double, kTileF64><<<g1, kThreads, 0, st>>>(static_cast<const double*>(v), K, N, ld, seg, start,
-                                                               static_cast<double*>(out), ld_out, part0, part1,
-                                                               ntiles);
+    bin_sums_block<double><<<g1, kThreads, 0, st>>>(static_cast<const double*>(v), K, N, ld, seg, start,
+                                                    static_cast<double*>(out), ld_out, carry0, carry1, ntiles);
     count_launches(1);
-    bin_means_fixup<double, kTileF64><<<g2, kThreads, 0, st>>>(K, nb, start, static_cast<double*>(out), ld_out, part0,
-                                                               part1, ntiles);
+    bin_sums_fixup<double><<<g2, kThreads, 0, st>>>(K, nb, start, static_cast<double*>(out), ld_out, carry0, carry1,
+                                                    ntiles);
     count_launches(1);
   }
   BUMBAR_CUDA(cudaGetLastError());
@@ -457,14 +606,14 @@ mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int6
 
 mbar_status gather_columns(const void* in, void* out, int dtype_bytes, int64_t K, int64_t N, int64_t ld,
                            const int32_t* perm, cudaStream_t st) {
-  const dim3 g(static_cast<unsigned>(ceil_div(N, kThreads)), static_cast<unsigned>(K));
+  const dim3 g(static_cast<unsigned>(ceil_div(N, kThreads)), static_cast<unsigned>(ceil_div(K, kGatherRows)));
   if (dtype_bytes == 4) {
-    gather_cols_kernel<float><<<g, kThreads, 0, st>>>(static_cast<const float*>(in), static_cast<float*>(out), N, ld,
-                                                      perm);
+    gather_cols_kernel<float><<<g, kThreads, 0, st>>>(static_cast<const float*>(in), static_cast<float*>(out), K, N,
+                                                      ld, perm);
     count_launches(1);
   } else {
-    gather_cols_kernel<double><<<g, kThreads, 0, st>>>(static_cast<const double*>(in), static_cast<double*>(out), N,
-                                                       ld, perm);
+    gather_cols_kernel<double><<<g, kThreads, 0, st>>>(static_cast<const double*>(in), static_cast<double*>(out), K,
+                                                       N, ld, perm);
     count_launches(1);
   }
   BUMBAR_CUDA(cudaGetLastError());

@@ -86,25 +86,66 @@ __global__ void syrk_update(double* __restrict__ A, int64_t m, int64_t kb, int n
   }
 }
 
-// Single-block forward then backward substitution with the lower factor.
-__global__ void chol_solve(const double* __restrict__ A, int64_t m, double* __restrict__ b, double* __restrict__ delta) {
-  for (int64_t j = 0; j < m; ++j) {
+// Single-block forward then backward substitution with the lower factor L,
+// by 32-row panels: warp 0 solves the 32 x 32 triangle of a panel in
+// registers (one row per lane, shuffles), then all threads apply the panel
+// to the remaining right-hand side (a matrix-vector product).
+__global__ void __launch_bounds__(1024) chol_solve(const double* __restrict__ A, int64_t m, double* __restrict__ b,
+                                                   double* __restrict__ delta) {
+  __shared__ double xs[NB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // forward: L y = b
+  for (int64_t j0 = 0; j0 < m; j0 += NB) {
+    const int nb = static_cast<int>(m - j0 < NB ? m - j0 : NB);
     __syncthreads();
-    const double yj = b[j] / A[j * m + j];
+    if (warp == 0) {
+      double rhs = lane < nb ? b[j0 + lane] : 0.0;
+      double y = 0.0;
+      for (int j = 0; j < nb; ++j) {
+        const double yj = __shfl_sync(0xffffffffu, rhs, j) / A[(j0 + j) * m + j0 + j];
+        if (lane == j) y = yj;
+        if (lane > j && lane < nb) rhs -= A[(j0 + lane) * m + j0 + j] * yj;
+      }
+      if (lane < nb) {
+        xs[lane] = y;
+        b[j0 + lane] = y;
+      }
+    }
     __syncthreads();
-    if (threadIdx.x == 0) b[j] = yj;
-    for (int64_t i = j + 1 + threadIdx.x; i < m; i += blockDim.x) b[i] -= A[i * m + j] * yj;
+    for (int64_t i = j0 + nb + tid; i < m; i += blockDim.x) {
+      double s = 0.0;
+      for (int j = 0; j < nb; ++j) s += A[i * m + j0 + j] * xs[j];
+      b[i] -= s;
+    }
   }
-  for (int64_t j = m - 1; j >= 0; --j) {
+  // backward: L^T x = y
+  for (int64_t j1 = m; j1 > 0; j1 -= NB) {
+    const int64_t j0 = j1 - NB > 0 ? j1 - NB : 0;
+    const int nb = static_cast<int>(j1 - j0);
     __syncthreads();
-    const double xj = b[j] / A[j * m + j];
+    if (warp == 0) {
+      double rhs = lane < nb ? b[j0 + lane] : 0.0;
+      double x = 0.0;
+      for (int j = nb - 1; j >= 0; --j) {
+        const double xj = __shfl_sync(0xffffffffu, rhs, j) / A[(j0 + j) * m + j0 + j];
+        if (lane == j) x = xj;
+        if (lane < j) rhs -= A[(j0 + j) * m + j0 + lane] * xj;
+      }
+      if (lane < nb) {
+        xs[lane] = x;
+        b[j0 + lane] = x;
+      }
+    }
     __syncthreads();
-    if (threadIdx.x == 0) b[j] = xj;
-    for (int64_t i = threadIdx.x; i < j; i += blockDim.x) b[i] -= A[j * m + i] * xj;
+    for (int64_t i = tid; i < j0; i += blockDim.x) {
+      double s = 0.0;
+      for (int j = 0; j < nb; ++j) s += A[(j0 + j) * m + i] * xs[j];
+      b[i] -= s;
+    }
   }
   __syncthreads();
-  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) delta[i + 1] = b[i];
-  if (threadIdx.x == 0) delta[0] = 0.0;
+  for (int64_t i = tid; i < m; i += blockDim.x) delta[i + 1] = b[i];
+  if (tid == 0) delta[0] = 0.0;
 }
 
 }  // namespace

@@ -197,42 +197,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
       }
     }
     const bool full8 = col0 + 8 <= job.c_end;
-    for (int lr = rsub; lr < rows; lr += 32) {
-      const int row = lr < rowsA ? job.bi * 128 + lr : job.bj0 * 128 + (lr - rowsA);
-      float x[8];
-      if (row < p.K) {
-        const T* src = vv + static_cast<int64_t>(row) * p.ld + col0;
-        if constexpr (sizeof(T) == 4) {
-          if (full8 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
-            const float4 v0 = *reinterpret_cast<const float4*>(src);
-            const float4 v1 = *reinterpret_cast<const float4*>(src + 4);
-            x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
-            x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+    // four rows per round: issue all loads first, then the SFU work
+    for (int lr0 = rsub; lr0 < rows; lr0 += 128) {
+      float x[4][8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int lr = lr0 + 32 * u;
+        const int row = lr < rowsA ? job.bi * 128 + lr : job.bj0 * 128 + (lr - rowsA);
+        if (lr < rows && row < p.K) {
+          const T* src = vv + static_cast<int64_t>(row) * p.ld + col0;
+          if constexpr (sizeof(T) == 4) {
+            if (full8) {
+              const float4 v0 = *reinterpret_cast<const float4*>(src);
+              const float4 v1 = *reinterpret_cast<const float4*>(src + 4);
+              x[u][0] = v0.x; x[u][1] = v0.y; x[u][2] = v0.z; x[u][3] = v0.w;
+              x[u][4] = v1.x; x[u][5] = v1.y; x[u][6] = v1.z; x[u][7] = v1.w;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) x[u][j] = (col0 + j < job.c_end) ? src[j] : 0.f;
+            }
           } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = (col0 + j < job.c_end) ? src[j] : 0.f;
+            for (int j = 0; j < 8; ++j) x[u][j] = (col0 + j < job.c_end) ? static_cast<float>(src[j]) : 0.f;
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) x[j] = (col0 + j < job.c_end) ? static_cast<float>(src[j]) : 0.f;
+          for (int j = 0; j < 8; ++j) x[u][j] = 0.f;
         }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = 0.f;
       }
-      const float a2 = a2_s[lr];
-      float pv[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float e = fmaf(-x[j], kLog2e, a2) - l2[j];
-        pv[j] = ex2_approx(e) * sh[j];
+      for (int u = 0; u < 4; ++u) {
+        const int lr = lr0 + 32 * u;
+        if (lr < rows) {
+          const float a2 = a2_s[lr];
+          float pv[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) pv[j] = ex2_approx(fmaf(-x[u][j], kLog2e, a2) - l2[j]) * sh[j];
+          uint4 packed;
+          packed.x = pack_half2(pv[0], pv[1]);
+          packed.y = pack_half2(pv[2], pv[3]);
+          packed.z = pack_half2(pv[4], pv[5]);
+          packed.w = pack_half2(pv[6], pv[7]);
+          *reinterpret_cast<uint4*>(buf + lr * 128 + ((g ^ (lr & 7)) << 4)) = packed;
+        }
       }
-      uint4 packed;
-      packed.x = pack_half2(pv[0], pv[1]);
-      packed.y = pack_half2(pv[2], pv[3]);
-      packed.z = pack_half2(pv[4], pv[5]);
-      packed.w = pack_half2(pv[6], pv[7]);
-      *reinterpret_cast<uint4*>(buf + lr * 128 + ((g ^ (lr & 7)) << 4)) = packed;
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
 
 // Fixed-order FP64 reduction of the slices of each item into G (upper
 // triangle computed, mirrored into the lower one).
-__global__ void reduce_tc(const float* __restrict__ part, const TcCta* __restrict__ ctas, int nctas,
+__global__ void reduce_tc(const float* __restrict__ part, const TcCta* __restrict__ ctas, int stride,
                           const int* __restrict__ item_first, const int* __restrict__ item_count, int K,
                           double* __restrict__ G) {
   const int item = blockIdx.y;
@@ -302,7 +310,8 @@ __global__ void reduce_tc(const float* __restrict__ part, const TcCta* __restric
   if (e >= static_cast<int64_t>(128) * used) return;
   const int rl = static_cast<int>(e / used), cl = static_cast<int>(e % used);
   double s = 0.0;
-  for (int i = 0; i < count; ++i) s += part[static_cast<int64_t>(first + i) * 128 * 512 + rl * 512 + cl];
+  for (int i = 0; i < count; ++i)
+    s += part[static_cast<int64_t>(first + i * stride) * 128 * 512 + rl * 512 + cl];
   const int row = job.bi * 128 + rl;
   const int col = job.bj0 * 128 + cl;
   if (row >= K || col >= K) return;
@@ -313,7 +322,8 @@ __global__ void reduce_tc(const float* __restrict__ part, const TcCta* __restric
 
 struct TcPlan {
   std::vector<TcCta> ctas;
-  std::vector<int> first, count;
+  std::vector<int> first, count;  // CTAs of item i: first[i] + j * stride, j < count[i]
+  int stride = 1;
 };
 
 TcPlan tc_plan(int64_t K, int64_t n) {
@@ -323,27 +333,29 @@ TcPlan tc_plan(int64_t K, int64_t n) {
   std::vector<Item> items;
   for (int bi = 0; bi < MT; ++bi)
     for (int bj0 = bi; bj0 < MT; bj0 += 4) items.push_back({bi, bj0, std::min(4, MT - bj0)});
-  // work of an item ~ rows of P~ it builds + MMA tiles
-  double total = 0;
-  std::vector<double> wk(items.size());
-  for (size_t i = 0; i < items.size(); ++i) {
-    wk[i] = (items[i].bj0 != items[i].bi ? 1 : 0) + items[i].nt + 0.5 * items[i].nt;
-    total += wk[i];
-  }
-  const int target = std::min(kMaxCtas, std::max(static_cast<int>(items.size()), num_sms()));
+  const int W = static_cast<int>(items.size());
+  // equal slices for every item, CTAs ordered slice-major so the CTAs that
+  // read the same columns of v run together and share them through L2;
+  // about four CTAs per SM even out the unequal item sizes
   const int64_t nch = ceil_div(n, kChunkCols);
-  for (size_t i = 0; i < items.size(); ++i) {
-    int64_t s = std::max<int64_t>(1, static_cast<int64_t>(std::floor(target * wk[i] / total)));
-    s = std::min<int64_t>(s, nch);
-    const int64_t per = ceil_div(nch, s) * kChunkCols;
-    pl.first.push_back(static_cast<int>(pl.ctas.size()));
-    int cnt = 0;
-    for (int64_t c0 = 0; c0 < n; c0 += per) {
-      pl.ctas.push_back({static_cast<int>(i), items[i].bi, items[i].bj0, items[i].nt, c0, std::min<int64_t>(n, c0 + per)});
-      ++cnt;
+  int64_t S = std::max<int64_t>(1, (4 * static_cast<int64_t>(num_sms()) + W - 1) / W);
+  S = std::min<int64_t>(S, std::max<int64_t>(1, kMaxCtas / W));
+  S = std::min<int64_t>(S, nch);
+  const int64_t per = ceil_div(nch, S) * kChunkCols;
+  S = ceil_div(n, per);
+  pl.first.assign(W, 0);
+  pl.count.assign(W, 0);
+  // item i's CTAs are i, i + W, i + 2W, ... : record them as a strided run
+  for (int64_t sl = 0; sl < S; ++sl)
+    for (int i = 0; i < W; ++i) {
+      const int64_t c0 = sl * per;
+      pl.ctas.push_back({i, items[i].bi, items[i].bj0, items[i].nt, c0, std::min<int64_t>(n, c0 + per)});
     }
-    pl.count.push_back(cnt);
+  for (int i = 0; i < W; ++i) {
+    pl.first[i] = i;
+    pl.count[i] = static_cast<int>(S);
   }
+  pl.stride = W;
   return pl;
 }
 
@@ -414,7 +426,7 @@ mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   const unsigned gx = static_cast<unsigned>(ceil_div(128 * 512, 256));
-  reduce_tc<<<dim3(gx, ni), 256, 0, st>>>(part, ctas_d, nc, first_d, count_d, static_cast<int>(K), G);
+  reduce_tc<<<dim3(gx, ni), 256, 0, st>>>(part, ctas_d, pl.stride, first_d, count_d, static_cast<int>(K), G);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;

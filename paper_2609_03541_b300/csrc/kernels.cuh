@@ -47,11 +47,16 @@ struct LseParams {
 
 struct LsePlan {
   int C, num_strips, box_rows, nbox, stages, grid, threads;
+  int variant;  // 0 = tiled (lse.cu), 1 = register-resident (lse_regs.cu)
+  int J;        // rows per thread of the register-resident variant
   size_t smem;
   bool ok;  // fits the device's shared-memory limit
 };
 
 LsePlan lse_plan(int64_t K, int64_t n, int dtype_bytes);
+bool lse_regs_supported(int64_t K, int dtype_bytes);
+LsePlan lse_regs_plan(int64_t K, int64_t n);
+mbar_status lse_regs_launch(const CUtensorMap& tmap, const LsePlan& pl, const LseParams& prm, cudaStream_t st);
 size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes);
 mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm, int dtype_bytes,
                        cudaStream_t stream);
@@ -63,10 +68,11 @@ mbar_status sort_coordinate(const double* phi, int64_t N, double* phi_sorted, in
                             size_t tmp_bytes, cudaStream_t stream);
 size_t sort_tmp_bytes(int64_t N);
 
-// Count of nonempty bins g(w) over sorted phi (anchor phi_sorted[0]);
-// result left in *count_dev (int64). tmp: >= 8 bytes.
-mbar_status count_bins(const double* phi_sorted, int64_t N, double w, unsigned long long* count_dev,
-                       cudaStream_t stream);
+// Counts of nonempty bins g(w) over sorted phi (anchor phi_sorted[0]) for
+// nw <= 15 widths in one pass; counts_dev holds 15 entries.
+constexpr int kWidthsPerPass = 15;
+mbar_status count_bins(const double* phi_sorted, int64_t N, const double* widths, int nw,
+                       unsigned long long* counts_dev, cudaStream_t stream);
 
 // Histogram at width w over sorted phi: per sorted sample its bin ordinal
 // seg[N] (0..nb-1), bin start offsets start[nb+1], counts H[nb] (int32),

@@ -26,6 +26,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "lse_common.cuh"
 
 namespace bumbar {
 
@@ -321,86 +322,14 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
     __syncthreads();
   }
 
-  // ---- per-CTA partials ----
-  double* part = p.partials + static_cast<size_t>(blockIdx.x) * K;
+  // ---- per-CTA partials, then the last CTA's reduction and SCI epilogue ----
+  double rowsum[CF::ROWS_PT];
 #pragma unroll
   for (int j = 0; j < CF::ROWS_PT; ++j) {
-    const int k = tid + j * THREADS;
-    if (k < K) {
-      double v = acc64[j];
-      if constexpr (sizeof(T) == 4) v += static_cast<double>(acc32[j]);
-      part[k] = v;
-    }
+    rowsum[j] = acc64[j];
+    if constexpr (sizeof(T) == 4) rowsum[j] += static_cast<double>(acc32[j]);
   }
-  __threadfence();
-  __syncthreads();
-  __shared__ unsigned int is_last;
-  if (tid == 0) {
-    const unsigned int ticket = atomicAdd(p.counter, 1u);
-    is_last = (ticket == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-
-  // ---- last CTA: fixed-order reduction and the SCI epilogue ----
-  double* fnew_s = red_s;  // K doubles
-  for (int k = tid; k < K; k += THREADS) {
-    double qk = 0.0;
-    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) qk += p.partials[static_cast<size_t>(b) * K + k];
-    p.Q[k] = qk;
-    fnew_s[k] = p.f[k] + p.logN[k] - log(qk);
-  }
-  __syncthreads();
-  if (p.mode == kLseModeSci) {
-    const double f0 = fnew_s[0];
-    const double fin0 = p.f[0];
-    double smax = -1.0;  // -1 = no f_k != 0 seen
-    double dmax = 0.0;
-    bool finite = true;
-    for (int k = tid; k < K; k += THREADS) {
-      const double fo = fnew_s[k] - f0;
-      const double fi = p.f[k];
-      if (p.f_out) p.f_out[k] = fo;
-      if (p.g_out) p.g_out[k] = p.Q[k] - p.Nk[k];
-      if (!isfinite(fo)) finite = false;
-      if (fi != 0.0) smax = fmax(smax, fabs(fo / fi - 1.0));
-      dmax = fmax(dmax, fabs(fo - (fi - fin0)));
-    }
-    __shared__ double red[THREADS / 32];
-    __shared__ double redd[THREADS / 32];
-    __shared__ int fin[THREADS / 32];
-    for (int o = 16; o >= 1; o >>= 1) {
-      smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-    }
-    const int allfin = __all_sync(0xffffffffu, finite);
-    if (lane == 0) {
-      red[warp] = smax;
-      redd[warp] = dmax;
-      fin[warp] = allfin;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double sm = -1.0, dm = 0.0;
-      int okf = 1;
-      for (int w = 0; w < THREADS / 32; ++w) {
-        sm = fmax(sm, red[w]);
-        dm = fmax(dm, redd[w]);
-        okf &= fin[w];
-      }
-      const double s = (sm < 0.0) ? INFINITY : sm;
-      if (p.s_out) *p.s_out = s;
-      if (p.d_out) *p.d_out = dm;
-      if (p.ctrl) {
-        p.ctrl->iters += 1;
-        p.ctrl->last_s = s;
-        if (!okf) p.ctrl->nonfinite = 1;
-        if ((p.eps > 0.0 && s < p.eps) || (p.noise > 0.0 && dm < p.noise)) p.ctrl->done = 1;
-      }
-    }
-  }
-  if (tid == 0) *p.counter = 0u;  // leave the scratch counter zeroed
+  lse_finish<THREADS, CF::ROWS_PT>(p, rowsum, red_s);
 }
 
 // ---------------------------------------------------------------------------
@@ -437,6 +366,7 @@ int lse_occupancy(size_t smem) {
 }  // namespace
 
 LsePlan lse_plan(int64_t K, int64_t n, int dtype_bytes) {
+  if (lse_regs_supported(K, dtype_bytes)) return lse_regs_plan(K, n);
   LsePlan pl{};
   const int C = 128 / dtype_bytes;
   pl.C = C;
@@ -476,6 +406,7 @@ mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm
   prm.box_rows = pl.box_rows;
   prm.nbox = pl.nbox;
   prm.stages = pl.stages;
+  if (pl.variant == 1) return lse_regs_launch(tmap, pl, prm, stream);
   if (dtype_bytes == 4) {
     lse_pass_kernel<float, kGf32><<<pl.grid, pl.threads, pl.smem, stream>>>(tmap, prm);
   } else {

@@ -12,23 +12,43 @@ namespace bumbar {
 
 namespace {
 
-__global__ void shift_fp32_kernel(const double* __restrict__ u, int64_t K, int64_t N, int64_t ldu,
-                                  double* __restrict__ c, float* __restrict__ v, int64_t ldv, int* bad) {
-  const int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+// One block per 32 columns: 8 row groups x 32 columns. Pass 1 takes the
+// column minimum (warp-coalesced 256-byte row segments), pass 2 re-reads the
+// same 32 x K FP64 block -- small enough to still be in L2 -- and writes the
+// shifted FP32 values.
+__global__ void __launch_bounds__(256) shift_fp32_kernel(const double* __restrict__ u, int64_t K, int64_t N,
+                                                         int64_t ldu, double* __restrict__ c, float* __restrict__ v,
+                                                         int64_t ldv, int* bad) {
+  __shared__ double part[8][32];
+  __shared__ int okp[8][32];
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const int64_t n = static_cast<int64_t>(blockIdx.x) * 32 + lane;
   double m = INFINITY;
   bool ok = true;
-  for (int64_t k = 0; k < K; ++k) {
-    const double x = u[k * ldu + n];
-    ok &= static_cast<bool>(isfinite(x));
-    m = fmin(m, x);
+  if (n < N) {
+    for (int64_t k = rg; k < K; k += 8) {
+      const double x = u[k * ldu + n];
+      ok &= static_cast<bool>(isfinite(x));
+      m = fmin(m, x);
+    }
   }
-  if (!ok) {
-    atomicOr(bad, 1);
-    m = 0.0;
+  part[rg][lane] = m;
+  okp[rg][lane] = ok ? 1 : 0;
+  __syncthreads();
+  double mm = part[0][lane];
+  int allok = okp[0][lane];
+#pragma unroll
+  for (int g = 1; g < 8; ++g) {
+    mm = fmin(mm, part[g][lane]);
+    allok &= okp[g][lane];
   }
-  c[n] = m;
-  for (int64_t k = 0; k < K; ++k) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - m);
+  if (n >= N) return;
+  if (!allok) {
+    if (rg == 0) atomicOr(bad, 1);
+    mm = 0.0;
+  }
+  if (rg == 0) c[n] = mm;
+  for (int64_t k = rg; k < K; k += 8) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - mm);
 }
 
 __global__ void copy_checked_kernel(const double* __restrict__ u, int64_t K, int64_t N, int64_t ldu,
@@ -58,7 +78,7 @@ __global__ void add_gauge_kernel(const double* __restrict__ f, const double* __r
 
 mbar_status shift_to_fp32(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, float* v, int64_t ldv,
                           int* bad, cudaStream_t st) {
-  shift_fp32_kernel<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(u, K, N, ldu, c, v, ldv, bad);
+  shift_fp32_kernel<<<static_cast<unsigned>(ceil_div(N, 32)), 256, 0, st>>>(u, K, N, ldu, c, v, ldv, bad);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
