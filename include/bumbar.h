@@ -80,7 +80,7 @@ typedef struct {
                              many kT is under the rounding floor of the
                              evaluation; Algorithm 1 then treats the level as
                              converged (first loop: stop; second loop: raise
-                             n). 0 = Eq. 2/3 exactly as printed. */
+                             n). 0 = Eqs. 2-3 exactly as printed. */
 } mbar_opts;
 
 typedef struct {
@@ -96,9 +96,9 @@ typedef struct {
 
 /* Fills *opts with the defaults above (f_tol 1e-10 for MBAR_FP64, 1e-5 for
  * MBAR_MIXED, chosen by `precision`; warm_tol 1e-3; max_newton 50;
- * max_sci 200000; use_binning 1; h0 0; noise_floor 0 for MBAR_FP64 and
- * 2e-6 kT for MBAR_MIXED, whose FP32 evaluation moves f by ~1e-7..1e-6 kT
- * from rounding alone). */
+ * max_sci 200000; use_binning 1; h0 0; noise_floor 1e-11 kT for MBAR_FP64
+ * and 2e-6 kT for MBAR_MIXED: rounding alone moves f by ~1e-13 kT per FP64
+ * step and ~1e-7..1e-6 kT per FP32 step). */
 BUMBAR_API mbar_status mbar_opts_default(mbar_opts* opts, int32_t precision);
 
 /* Creates a context for one problem (the paper's input list of Algorithm 1:

@@ -55,6 +55,7 @@ struct mbar_ctx {
   int32_t* perm = nullptr;   // current column -> original sample
   double* phi0 = nullptr;    // default bin coordinate (row 0 of u, original order)
   double* phi_sorted = nullptr;
+  double* d_sorted = nullptr;  // phi_sorted - min(phi)
   bool sorted = false;
   double phi_lo = 0.0, phi_hi = 0.0;
   Level full;  // unbinned level view (not owning)
@@ -235,7 +236,7 @@ mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
   mbar_status s = dalloc_t(c, &keys_full, c->N);
   if (s == MBAR_OK) s = dalloc_t(c, &H_full, c->N);
   if (s == MBAR_OK)
-    s = build_histogram(c->phi_sorted, c->N, w, c->seg, c->start, H_full, keys_full, c->nb_dev, tmp, htmp, c->st);
+    s = build_histogram(c->d_sorted, c->N, w, c->seg, c->start, H_full, keys_full, c->nb_dev, tmp, htmp, c->st);
   int32_t nb = 0;
   if (s == MBAR_OK) {
     cudaError_t e = cudaMemcpyAsync(&nb, c->nb_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
@@ -268,7 +269,7 @@ mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
 }
 
 mbar_status count_at(mbar_ctx* c, const double* ws, int nw, int64_t* g) {
-  BUMBAR_TRY(count_bins(c->phi_sorted, c->N, ws, nw, c->count, c->st));
+  BUMBAR_TRY(count_bins(c->d_sorted, c->N, ws, nw, c->count, c->st));
   unsigned long long h[kWidthsPerPass];
   BUMBAR_CUDA(cudaMemcpyAsync(h, c->count, nw * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
   BUMBAR_CUDA(cudaStreamSynchronize(c->st));
@@ -387,6 +388,7 @@ mbar_status set_coordinate_dev(mbar_ctx* c, const double* phi_orig) {
   // phi_cur[i] = phi[perm[i]]
   if (s == MBAR_OK) s = gather_columns(phi_orig, phi_cur, 8, 1, N, N, c->perm, c->st);
   if (s == MBAR_OK) s = sort_coordinate(phi_cur, N, c->phi_sorted, perm_rel, tmp, stmp, c->st);
+  if (s == MBAR_OK) s = offsets_from_min(c->phi_sorted, N, c->d_sorted, c->st);
   // reorder the data columns and the bookkeeping by perm_rel
   if (s == MBAR_OK) s = gather_columns(c->v, tmp, c->dtype, c->K, N, c->ld, perm_rel, c->st);
   if (s == MBAR_OK) {
@@ -702,7 +704,7 @@ mbar_status mbar_opts_default(mbar_opts* o, int32_t precision) {
   o->warm_tol = 1e-3;
   o->max_newton = 50;
   o->max_sci = 200000;
-  o->noise_floor = precision == MBAR_FP64 ? 0.0 : 2e-6;
+  o->noise_floor = precision == MBAR_FP64 ? 1e-11 : 2e-6;
   return MBAR_OK;
 }
 
@@ -804,6 +806,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   TRYC(dalloc_t(c, &c->start, N + 1));
   TRYC(dalloc_t(c, &c->phi0, N));
   TRYC(dalloc_t(c, &c->phi_sorted, N));
+  TRYC(dalloc_t(c, &c->d_sorted, N));
   // the samples of u_kn on the device in FP64
   const double* u_dev = u_kn;
   double* u_tmp = nullptr;
@@ -1186,7 +1189,7 @@ mbar_status mbar_destroy(mbar_ctx* c) {
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   level_free(c, &c->cur);
-  void* ptrs[] = {c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->f,
+  void* ptrs[] = {c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->f,
                   c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->s,          c->s2,
                   c->hess, c->delta,  c->info,  c->bad,    c->ctrl,  c->logden,  c->scratch,    c->seg, c->d,
                   c->start, c->count, c->nb_dev};

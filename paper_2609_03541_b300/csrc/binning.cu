@@ -28,23 +28,26 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
-__device__ __forceinline__ long long bin_index(double phi, double lo, double w) {
-  const double q = __ddiv_rn(__dsub_rn(phi, lo), w);
-  return static_cast<long long>(floor(q));
-}
-
-// Same value as bin_index, mostly without the division: with rw = RN(1/w),
-// q = RN(d * rw) lies within (d/w) 2^-52 of d/w, as does RN(d/w), so their
-// floors can only differ when q is that close to an integer; those rare
-// cases take the correctly rounded division.
-__device__ __forceinline__ long long bin_index_fast(double phi, double lo, double w, double rw) {
-  const double d = __dsub_rn(phi, lo);
+// floor(RN(d / w)) for d = phi - phi_lo >= 0, with one FP64 multiply and
+// integer work in the common case: q = RN(d * rw), rw = RN(1/w), is within
+// about 3 ulp(q) of RN(d/w), so unless q lies within 8 ulps of an integer
+// its integer part (read from the binary64 bits) is the bin index; the rare
+// close cases, and q >= 2^49 where every value is close, use the correctly
+// rounded division.
+__device__ __forceinline__ long long key_from_d(double d, double w, double rw) {
   const double q = __dmul_rn(d, rw);
-  const double fq = floor(q);
-  const double r = q - fq;
-  const double tol = q * 0x1p-49;
-  if (r <= tol || 1.0 - r <= tol) return static_cast<long long>(floor(__ddiv_rn(d, w)));
-  return static_cast<long long>(fq);
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(q));
+  const int e = static_cast<int>((bits >> 52) & 0x7FF) - 1023;
+  if (e < 0) {
+    if (bits < 0x3FEFFFFFFFFFFFF8ull) return 0;  // q < 1 - 8 ulp: bin 0
+  } else if (e < 49) {
+    const int sh = 52 - e;
+    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const unsigned long long one = 1ull << sh;
+    const unsigned long long frac = mant & (one - 1);
+    if (frac >= 8 && frac <= one - 8) return static_cast<long long>(mant >> sh);
+  }
+  return static_cast<long long>(floor(__ddiv_rn(d, w)));
 }
 
 // ---------------------------------------------------------------------------
@@ -211,49 +214,73 @@ __global__ void gather_phi(const double* __restrict__ phi, const int32_t* __rest
 // ---------------------------------------------------------------------------
 // histogram over sorted phi
 // ---------------------------------------------------------------------------
-// Number of nonempty bins for up to kMaxWidths widths in one pass over the
-// sorted coordinate (head flags counted by warp ballots).
+// Number of nonempty bins for up to kMaxWidths widths in one pass over
+// d_i = phi_i - phi_lo (sorted). Bin indices are non-decreasing in i, so a
+// thread owning 16 consecutive samples first compares the indices just before
+// and at the end of its chunk: equal means no bin starts inside, a difference
+// of one means exactly one does; only otherwise are all 16 indices formed.
 struct WidthSet {
   double w[kMaxWidths];
   double rw[kMaxWidths];
   int n;
 };
+constexpr int kCountChunk = 16;
 
-__global__ void count_heads_multi(const double* __restrict__ phi, int64_t N, WidthSet ws,
+__global__ void count_heads_multi(const double* __restrict__ d, int64_t N, WidthSet ws,
                                   unsigned long long* __restrict__ counts) {
   __shared__ unsigned int cnt[kMaxWidths];
   if (threadIdx.x < kMaxWidths) cnt[threadIdx.x] = 0u;
   __syncthreads();
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const double lo = phi[0];
-  const bool in = i < N;
-  const double x = in ? phi[i] : lo;
-  const double xp = (in && i > 0) ? phi[i - 1] : lo;
+  const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kCountChunk;
+  const int64_t i1 = (i0 + kCountChunk < N) ? i0 + kCountChunk : N;
   for (int c = 0; c < ws.n; ++c) {
-    bool head = false;
-    if (in) {
-      const long long key = bin_index_fast(x, lo, ws.w[c], ws.rw[c]);
-      head = (i == 0) || key != bin_index_fast(xp, lo, ws.w[c], ws.rw[c]);
+    unsigned int heads = 0;
+    if (i0 < N) {
+      const double w = ws.w[c], rw = ws.rw[c];
+      const long long kend = key_from_d(d[i1 - 1], w, rw);
+      long long kprev;
+      if (i0 == 0) {
+        heads = 1;  // the first sample opens the first bin
+        kprev = key_from_d(d[0], w, rw);
+      } else {
+        kprev = key_from_d(d[i0 - 1], w, rw);
+      }
+      const long long diff = kend - kprev;
+      if (diff == 1) {
+        heads += 1;
+      } else if (diff > 1) {
+        for (int64_t i = (i0 == 0 ? 1 : i0); i < i1; ++i) {
+          const long long k = key_from_d(d[i], w, rw);
+          heads += (k != kprev) ? 1u : 0u;
+          kprev = k;
+        }
+      }
     }
-    const unsigned b = __ballot_sync(0xffffffffu, head);
-    if (lane == 0 && b) atomicAdd(&cnt[c], static_cast<unsigned>(__popc(b)));
+    // warp sum, one shared atomic per warp
+    for (int o = 16; o >= 1; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
+    if (lane == 0 && heads) atomicAdd(&cnt[c], heads);
   }
   __syncthreads();
   if (threadIdx.x < ws.n && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], static_cast<unsigned long long>(cnt[threadIdx.x]));
 }
 
-__global__ void head_flags(const double* __restrict__ phi, int64_t N, double w, double rw, int* __restrict__ flags) {
+__global__ void offsets_from_lo(const double* __restrict__ phi, int64_t N, double* __restrict__ d) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const double lo = phi[0];
+  if (i < N) d[i] = __dsub_rn(phi[i], phi[0]);
+}
+
+__global__ void head_flags(const double* __restrict__ d, int64_t N, double w, double rw, int* __restrict__ flags) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   long long key = 0;
-  if (i < N) key = bin_index_fast(phi[i], lo, w, rw);
+  if (i < N) key = key_from_d(d[i], w, rw);
   long long prev = __shfl_up_sync(0xffffffffu, key, 1);
-  if ((threadIdx.x & 31) == 0 && i > 0 && i < N) prev = bin_index_fast(phi[i - 1], lo, w, rw);
+  if ((threadIdx.x & 31) == 0 && i > 0 && i < N) prev = key_from_d(d[i - 1], w, rw);
   if (i < N) flags[i] = (i == 0 || key != prev) ? 1 : 0;
 }
 
-__global__ void finish_histogram(const double* __restrict__ phi, int64_t N, double w, const int* __restrict__ flags,
+__global__ void finish_histogram(const double* __restrict__ d, int64_t N, double w, double rw,
+                                 const int* __restrict__ flags,
                                  const int* __restrict__ excl, int32_t* __restrict__ seg, int32_t* __restrict__ start,
                                  int64_t* __restrict__ keys, int32_t* __restrict__ nb_dev) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -263,7 +290,7 @@ __global__ void finish_histogram(const double* __restrict__ phi, int64_t N, doub
   seg[i] = e + f - 1;
   if (f) {
     start[e] = static_cast<int32_t>(i);
-    keys[e] = bin_index(phi[i], phi[0], w);
+    keys[e] = key_from_d(d[i], w, rw);
   }
   if (i == N - 1) {
     const int nb = e + f;
@@ -295,8 +322,22 @@ constexpr int kBmCols = 8;
 constexpr int kBmTile = kThreads * kBmCols;  // 2048
 constexpr int kRowsPerBlock = 4;
 
+// Accumulation type of the segmented sums: FP32 for FP32 data (the binned
+// matrix only steers Algorithm 1; the answer comes from the unbinned data,
+// and FP64 arithmetic is slow on this part), FP64 for FP64 data.
 template <typename T>
-__device__ __forceinline__ void load8(const T* src, int nvalid, double* x) {
+struct Acc;
+template <>
+struct Acc<float> {
+  using type = float;
+};
+template <>
+struct Acc<double> {
+  using type = double;
+};
+
+template <typename T, typename A>
+__device__ __forceinline__ void load8(const T* src, int nvalid, A* x) {
   if constexpr (sizeof(T) == 4) {
     if (nvalid == 8) {
       const float4 a = *reinterpret_cast<const float4*>(src);
@@ -317,16 +358,18 @@ __device__ __forceinline__ void load8(const T* src, int nvalid, double* x) {
     }
   }
 #pragma unroll
-  for (int j = 0; j < 8; ++j) x[j] = (j < nvalid) ? static_cast<double>(src[j]) : 0.0;
+  for (int j = 0; j < 8; ++j) x[j] = (j < nvalid) ? static_cast<A>(src[j]) : A(0);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__ v, int64_t K, int64_t N, int64_t ld,
                                                            const int32_t* __restrict__ seg,
-                                                           const int32_t* __restrict__ start, T* __restrict__ out,
+                                                           const int32_t* __restrict__ start,
+                                                           const double* __restrict__ inv_count, T* __restrict__ out,
                                                            int64_t ld_out, double* __restrict__ carry0,
                                                            double* __restrict__ carry1, int64_t ntiles) {
-  __shared__ double wv[kThreads / 32];
+  using A = typename Acc<T>::type;
+  __shared__ A wv[kThreads / 32];
   __shared__ int wf[kThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t tile = blockIdx.x;
@@ -352,13 +395,15 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
   const bool flag = nvalid <= 0 || nruns > 0 || st_bl >= c0;  // last run starts in this thread
   const bool cont = nvalid > 0 && st_b0 < c0;                 // first run continues from the left
   const bool last_ends_here = nvalid > 0 && en_bl <= c0 + nvalid;
+  const A inv_b0 = nvalid > 0 ? static_cast<A>(inv_count[b0]) : A(0);
+  const A inv_bl = nvalid > 0 ? static_cast<A>(inv_count[bl]) : A(0);
 
   const int64_t k_begin = static_cast<int64_t>(blockIdx.y) * kRowsPerBlock;
   for (int64_t k = k_begin; k < K && k < k_begin + kRowsPerBlock; ++k) {
-    double x[kBmCols];
-    load8<T>(v + k * ld + c0, nvalid, x);
+    A x[kBmCols];
+    load8<T, A>(v + k * ld + c0, nvalid, x);
     // local runs
-    double head = 0.0, run = 0.0;
+    A head = A(0), run = A(0);
     int cur = b0;
     bool first = true;
 #pragma unroll
@@ -369,20 +414,20 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
             head = run;
             first = false;
           } else {  // interior run: starts and ends inside this thread
-            out[k * ld_out + cur] = static_cast<T>(run / static_cast<double>(start[cur + 1] - start[cur]));
+            out[k * ld_out + cur] = static_cast<T>(run * static_cast<A>(inv_count[cur]));
           }
           cur = sg[j];
-          run = 0.0;
+          run = A(0);
         }
         run += x[j];
       }
     }
     // block-wide segmented inclusive scan of the last-run sums
-    double sv = nvalid > 0 ? run : 0.0;
+    A sv = nvalid > 0 ? run : A(0);
     int sf = flag ? 1 : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const double uv = __shfl_up_sync(0xffffffffu, sv, o);
+      const A uv = __shfl_up_sync(0xffffffffu, sv, o);
       const int uf = __shfl_up_sync(0xffffffffu, sf, o);
       if (lane >= o) {
         if (!sf) sv += uv;
@@ -394,41 +439,46 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
       wf[warp] = sf;
     }
     __syncthreads();
-    double pv = 0.0;  // segmented prefix of all earlier warps
+    A pv = A(0);  // segmented prefix of all earlier warps
     for (int w = 0; w < warp; ++w) pv = wf[w] ? wv[w] : pv + wv[w];
     if (!sf) sv += pv;
-    double prev = __shfl_up_sync(0xffffffffu, sv, 1);
+    A prev = __shfl_up_sync(0xffffffffu, sv, 1);
     if (lane == 0) prev = pv;
-    if (tid == 0) prev = 0.0;
+    if (tid == 0) prev = A(0);
     __syncthreads();
     if (nvalid > 0) {
-      const double carry_in = cont ? prev : 0.0;
+      const A carry_in = cont ? prev : A(0);
       if (nruns > 0) {  // the first run ends inside this thread
-        const double tot = carry_in + head;
+        const A tot = carry_in + head;
         if (st_b0 >= tile0)
-          out[k * ld_out + b0] = static_cast<T>(tot / static_cast<double>(start[b0 + 1] - st_b0));
+          out[k * ld_out + b0] = static_cast<T>(tot * inv_b0);
         else
-          carry0[k * ntiles + tile] = tot;
+          carry0[k * ntiles + tile] = static_cast<double>(tot);
       }
       if (last_ends_here) {
         if (st_bl >= tile0)
-          out[k * ld_out + bl] = static_cast<T>(sv / static_cast<double>(en_bl - st_bl));
+          out[k * ld_out + bl] = static_cast<T>(sv * inv_bl);
         else
-          carry0[k * ntiles + tile] = sv;
+          carry0[k * ntiles + tile] = static_cast<double>(sv);
       } else if (last_thread) {
         if (st_bl >= tile0)
-          carry1[k * ntiles + tile] = sv;
+          carry1[k * ntiles + tile] = static_cast<double>(sv);
         else
-          carry0[k * ntiles + tile] = sv;
+          carry0[k * ntiles + tile] = static_cast<double>(sv);
       }
     }
   }
 }
 
+__global__ void inverse_counts(const int32_t* __restrict__ start, int64_t nb, double* __restrict__ inv) {
+  const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b < nb) inv[b] = 1.0 / static_cast<double>(start[b + 1] - start[b]);
+}
+
 template <typename T>
-__global__ void bin_sums_fixup(int64_t K, int64_t nb, const int32_t* __restrict__ start, T* __restrict__ out,
-                               int64_t ld_out, const double* __restrict__ carry0, const double* __restrict__ carry1,
-                               int64_t ntiles) {
+__global__ void bin_sums_fixup(int64_t K, int64_t nb, const int32_t* __restrict__ start,
+                               const double* __restrict__ inv_count, T* __restrict__ out, int64_t ld_out,
+                               const double* __restrict__ carry0, const double* __restrict__ carry1, int64_t ntiles) {
   const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t k = blockIdx.y;
   if (b >= nb) return;
@@ -437,7 +487,7 @@ __global__ void bin_sums_fixup(int64_t K, int64_t nb, const int32_t* __restrict_
   if (ts == te) return;  // finished inside one tile
   double sum = carry1[k * ntiles + ts];
   for (int64_t t = ts + 1; t <= te; ++t) sum += carry0[k * ntiles + t];
-  out[k * ld_out + b] = static_cast<T>(sum / static_cast<double>(e - s));
+  out[k * ld_out + b] = static_cast<T>(sum * inv_count[b]);
 }
 
 // out[k][i] = in[k][perm[i]]: each thread loads perm[i] once and moves it
@@ -520,7 +570,14 @@ mbar_status sort_coordinate(const double* phi, int64_t N, double* phi_sorted, in
   return MBAR_OK;
 }
 
-mbar_status count_bins(const double* phi_sorted, int64_t N, const double* widths, int nw,
+mbar_status offsets_from_min(const double* phi_sorted, int64_t N, double* d_sorted, cudaStream_t st) {
+  offsets_from_lo<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(phi_sorted, N, d_sorted);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+mbar_status count_bins(const double* d_sorted, int64_t N, const double* widths, int nw,
                        unsigned long long* counts_dev, cudaStream_t st) {
   if (nw < 1 || nw > kMaxWidths) {
     set_error("count_bins: 1..%d widths per pass", kMaxWidths);
@@ -533,7 +590,8 @@ mbar_status count_bins(const double* phi_sorted, int64_t N, const double* widths
     ws.rw[c] = 1.0 / widths[c];
   }
   BUMBAR_CUDA(cudaMemsetAsync(counts_dev, 0, kMaxWidths * sizeof(unsigned long long), st));
-  count_heads_multi<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(phi_sorted, N, ws, counts_dev);
+  count_heads_multi<<<static_cast<unsigned>(ceil_div(N, static_cast<int64_t>(kThreads) * kCountChunk)), kThreads, 0,
+                      st>>>(d_sorted, N, ws, counts_dev);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
@@ -541,7 +599,7 @@ mbar_status count_bins(const double* phi_sorted, int64_t N, const double* widths
 
 size_t hist_tmp_bytes(int64_t N) { return round_up(N * 4, 256) * 2 + round_up(scan_tmp_bytes(N), 256); }
 
-mbar_status build_histogram(const double* phi_sorted, int64_t N, double w, int32_t* seg, int32_t* start, int32_t* H,
+mbar_status build_histogram(const double* d_sorted, int64_t N, double w, int32_t* seg, int32_t* start, int32_t* H,
                             int64_t* keys, int32_t* nb_dev, void* tmp, size_t tmp_bytes, cudaStream_t st) {
   if (tmp_bytes < hist_tmp_bytes(N)) {
     set_error("build_histogram: scratch too small");
@@ -553,10 +611,11 @@ mbar_status build_histogram(const double* phi_sorted, int64_t N, double w, int32
   int* excl = reinterpret_cast<int*>(p);
   p += round_up(N * 4, 256);
   const unsigned gN = static_cast<unsigned>(ceil_div(N, kThreads));
-  head_flags<<<gN, kThreads, 0, st>>>(phi_sorted, N, w, 1.0 / w, flags);
+  const double rw = 1.0 / w;
+  head_flags<<<gN, kThreads, 0, st>>>(d_sorted, N, w, rw, flags);
   count_launches(1);
   BUMBAR_TRY(excl_scan(flags, N, excl, nullptr, p, st));
-  finish_histogram<<<gN, kThreads, 0, st>>>(phi_sorted, N, w, flags, excl, seg, start, keys, nb_dev);
+  finish_histogram<<<gN, kThreads, 0, st>>>(d_sorted, N, w, rw, flags, excl, seg, start, keys, nb_dev);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   int32_t nb = 0;
@@ -570,7 +629,7 @@ mbar_status build_histogram(const double* phi_sorted, int64_t N, double w, int32
 
 size_t bin_means_tmp_bytes(int64_t K, int64_t N) {
   const int64_t ntiles = ceil_div(N, kBmTile);
-  return round_up(K * ntiles * 8, 256) * 2;
+  return round_up(K * ntiles * 8, 256) * 2 + round_up(N * 8, 256);
 }
 
 mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int64_t ld, const int32_t* seg,
@@ -583,21 +642,24 @@ mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int6
   const int64_t ntiles = ceil_div(N, kBmTile);
   double* carry0 = static_cast<double*>(tmp);
   double* carry1 = carry0 + round_up(K * ntiles, 32);
+  double* inv = carry1 + round_up(K * ntiles, 32);
+  inverse_counts<<<static_cast<unsigned>(ceil_div(nb, kThreads)), kThreads, 0, st>>>(start, nb, inv);
+  count_launches(1);
   const dim3 g1(static_cast<unsigned>(ntiles), static_cast<unsigned>(ceil_div(K, kRowsPerBlock)));
   const dim3 g2(static_cast<unsigned>(ceil_div(nb, kThreads)), static_cast<unsigned>(K));
   if (dtype_bytes == 4) {
-    bin_sums_block<float><<<g1, kThreads, 0, st>>>(static_cast<const float*>(v), K, N, ld, seg, start,
+    bin_sums_block<float><<<g1, kThreads, 0, st>>>(static_cast<const float*>(v), K, N, ld, seg, start, inv,
                                                    static_cast<float*>(out), ld_out, carry0, carry1, ntiles);
     count_launches(1);
-    bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, nb, start, static_cast<float*>(out), ld_out, carry0, carry1,
-                                                   ntiles);
+    bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, nb, start, inv, static_cast<float*>(out), ld_out, carry0,
+                                                   carry1, ntiles);
     count_launches(1);
   } else {
-    bin_sums_block<double><<<g1, kThreads, 0, st>>>(static_cast<const double*>(v), K, N, ld, seg, start,
+    bin_sums_block<double><<<g1, kThreads, 0, st>>>(static_cast<const double*>(v), K, N, ld, seg, start, inv,
                                                     static_cast<double*>(out), ld_out, carry0, carry1, ntiles);
     count_launches(1);
-    bin_sums_fixup<double><<<g2, kThreads, 0, st>>>(K, nb, start, static_cast<double*>(out), ld_out, carry0, carry1,
-                                                    ntiles);
+    bin_sums_fixup<double><<<g2, kThreads, 0, st>>>(K, nb, start, inv, static_cast<double*>(out), ld_out, carry0,
+                                                    carry1, ntiles);
     count_launches(1);
   }
   BUMBAR_CUDA(cudaGetLastError());

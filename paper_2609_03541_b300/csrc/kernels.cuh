@@ -49,6 +49,7 @@ struct LsePlan {
   int C, num_strips, box_rows, nbox, stages, grid, threads;
   int variant;  // 0 = tiled (lse.cu), 1 = register-resident (lse_regs.cu)
   int J;        // rows per thread of the register-resident variant
+  int H;        // row halves of the register-resident variant (1 or 2)
   size_t smem;
   bool ok;  // fits the device's shared-memory limit
 };
@@ -68,17 +69,21 @@ mbar_status sort_coordinate(const double* phi, int64_t N, double* phi_sorted, in
                             size_t tmp_bytes, cudaStream_t stream);
 size_t sort_tmp_bytes(int64_t N);
 
-// Counts of nonempty bins g(w) over sorted phi (anchor phi_sorted[0]) for
-// nw <= 15 widths in one pass; counts_dev holds 15 entries.
+// d_sorted[i] = phi_sorted[i] - phi_sorted[0] (binary64, rounded to nearest):
+// the offsets every bin index is computed from.
+mbar_status offsets_from_min(const double* phi_sorted, int64_t N, double* d_sorted, cudaStream_t stream);
+
+// Counts of nonempty bins g(w) over the sorted offsets for nw <= 15 widths
+// in one pass; counts_dev holds 15 entries.
 constexpr int kWidthsPerPass = 15;
-mbar_status count_bins(const double* phi_sorted, int64_t N, const double* widths, int nw,
+mbar_status count_bins(const double* d_sorted, int64_t N, const double* widths, int nw,
                        unsigned long long* counts_dev, cudaStream_t stream);
 
-// Histogram at width w over sorted phi: per sorted sample its bin ordinal
+// Histogram at width w over the sorted offsets: per sorted sample its bin ordinal
 // seg[N] (0..nb-1), bin start offsets start[nb+1], counts H[nb] (int32),
 // keys[nb] (int64). nb is returned through *nb_dev. tmp sized by
 // hist_tmp_bytes.
-mbar_status build_histogram(const double* phi_sorted, int64_t N, double w, int32_t* seg, int32_t* start,
+mbar_status build_histogram(const double* d_sorted, int64_t N, double w, int32_t* seg, int32_t* start,
                             int32_t* H, int64_t* keys, int32_t* nb_dev, void* tmp, size_t tmp_bytes,
                             cudaStream_t stream);
 size_t hist_tmp_bytes(int64_t N);

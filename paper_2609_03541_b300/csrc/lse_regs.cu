@@ -4,22 +4,25 @@
 //
 // Same strip pipeline as lse.cu (2-D TMA boxes, 128-byte swizzle, mbarrier
 // stages), but each thread keeps its slice of a strip in registers instead
-// of writing e back to shared memory:
-//   * thread (warp w, lane l) owns column c = 4 (w % 8) + l / 8 of the strip
-//     and rows k_j = 8 (w / 8) + l % 8 + 16 j, j < J (J = ceil(K / 16));
+// of writing e back to shared memory. A stage holds SUB sub-tiles of 32
+// columns x all K rows; 16 warps cover them as 8 column chunks x H row
+// halves x SUB sub-tiles (H * SUB = 2):
+//   * thread (warp w, lane l) owns column c = 4 (w % 8) + l / 8 of its
+//     sub-tile and rows k_j = 8 h + l % 8 + 8 H j, j < J (J = ceil(K / 8H));
 //   * A1 reads v once from shared memory (conflict-free: a warp reads one
-//     16-byte chunk of 8 different rows whose swizzle phases differ) and
-//     keeps x_j = a_kj - v log2(e) in registers; column max by 8-lane
-//     shuffles and one shared-memory exchange between the two row halves;
-//     the stage is then released and its next TMA load issued at once;
-//   * A2 turns x_j into e_j = 2^(x_j - max) in place; column sum the same way;
+//     16-byte chunk of 8 rows whose swizzle phases differ) and keeps
+//     x_j = a_kj - v log2(e) in registers; column max by 8-lane shuffles
+//     (plus one shared-memory exchange between row halves when H = 2); the
+//     stage is then released and its next TMA load issued at once;
+//   * A2 turns x_j into e_j = 2^(x_j - max) in place; column sum likewise;
 //   * B accumulates e_j * H_c / s_c into per-thread row partials acc_j.
-// Every 32 strips the four column lanes that share rows are combined by
-// shuffles and added into one FP64 slot per (warp column group, row) in
-// shared memory (fixed order, deterministic); at the end the eight slots of
-// a row are summed in order and the common epilogue (lse_common.cuh) runs.
-// Per entry: one shared-memory read of v and one (broadcast-friendly) of a,
-// one FFMA, one max, one SFU ex2, two adds and one FFMA.
+// Every 32 stages the four column lanes that share rows are combined by
+// shuffles and added into one FP64 slot per warp and row in shared memory
+// (fixed order, deterministic); at the end a row's slots are summed in order
+// and the common epilogue (lse_common.cuh) runs. H = 1 (two 32-column
+// sub-tiles per stage, no cross-warp exchange) serves K <= 256; H = 2 serves
+// K <= 512. Per entry: one shared-memory read of v and one of a, one FFMA,
+// one max, one SFU ex2, two adds and one FFMA.
 #include <cmath>
 
 #include "common.cuh"
@@ -31,26 +34,29 @@ namespace bumbar {
 namespace {
 
 constexpr int kRThreads = 512;
-constexpr int kRowGroups = 16;     // 2 row halves x 8 lane residues
-constexpr int kFlush = 32;         // strips between FP32 -> FP64 flushes
+constexpr int kFlush = 32;  // stages between FP32 -> FP64 flushes
 constexpr uint32_t kSpin = 1u << 28;
 
 __host__ __device__ inline size_t rupr(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-// shared memory: stages | a [Kpad] f32 | slots [8][Kpad] f64 | colm[2][32] |
+// shared memory: stages | a [Kpad] f32 | slots [16][Kpad] f64 | colm[2][32] |
 //                cols[2][32] | mbarriers[8] | epilogue [K] f64
 struct RegsSmem {
   static __host__ __device__ size_t kpad(int K) { return rupr(static_cast<size_t>(K), 16); }
-  static __host__ __device__ size_t extra(int K) {
-    return kpad(K) * 4 + 8 * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64 + rupr(static_cast<size_t>(K) * 8, 16);
+  static __host__ __device__ size_t extra(int K, int nslots) {
+    return kpad(K) * 4 + nslots * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64 + rupr(static_cast<size_t>(K) * 8, 16);
   }
 };
 
-template <int J>
+template <int J, int H>
 __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 LseParams p) {
+  constexpr int SUB = 2 / H;             // 32-column sub-tiles per stage
+  constexpr int CS = 32 * SUB;           // columns per stage
+  constexpr int RG = 8 * H;              // row groups
+  constexpr int NSLOT = 16;              // one per warp
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -58,13 +64,14 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (p.ctrl != nullptr && p.skip_if_done && p.ctrl->done) return;
 
-  const size_t sbytes = static_cast<size_t>(p.nbox) * p.box_rows * 128;
+  const size_t subbytes = static_cast<size_t>(p.nbox) * p.box_rows * 128;
+  const size_t sbytes = SUB * subbytes;
   const size_t kp = RegsSmem::kpad(K);
   unsigned char* cur = smem + p.stages * sbytes;
   float* a_s = reinterpret_cast<float*>(cur);
   cur += kp * 4;
-  double* slots = reinterpret_cast<double*>(cur);  // [8][kp]
-  cur += 8 * kp * 8;
+  double* slots = reinterpret_cast<double*>(cur);  // [NSLOT][kp]
+  cur += NSLOT * kp * 8;
   float* colm = reinterpret_cast<float*>(cur);     // [2][32]
   float* cols = colm + 64;                         // [2][32]
   cur += 2 * 32 * 4 * 2;
@@ -83,25 +90,31 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   }
   for (int k = tid; k < static_cast<int>(kp); k += kRThreads)
     a_s[k] = k < K ? static_cast<float>((p.f[k] + p.logN[k]) * 1.4426950408889634) : 0.f;
-  for (int i = tid; i < static_cast<int>(8 * kp); i += kRThreads) slots[i] = 0.0;
+  for (int i = tid; i < static_cast<int>(NSLOT * kp); i += kRThreads) slots[i] = 0.0;
   __syncthreads();
 
   const uint32_t tx = static_cast<uint32_t>(sbytes);
-  if (tid == 0) {
-    for (int s = 0; s < p.stages && s < my_count; ++s) {
-      unsigned char* dst = smem + s * sbytes;
-      mbar_expect_tx(&bars[s], tx);
+  auto issue = [&](int stage, int strip) {
+    unsigned char* dst = smem + stage * sbytes;
+    mbar_expect_tx(&bars[stage], tx);
+#pragma unroll
+    for (int sb = 0; sb < SUB; ++sb)
       for (int b = 0; b < p.nbox; ++b)
-        tma_load_2d(dst + static_cast<size_t>(b) * p.box_rows * 128, &tmap, &bars[s], (my_first + s * stride) * 32,
-                    b * p.box_rows);
-    }
+        tma_load_2d(dst + sb * subbytes + static_cast<size_t>(b) * p.box_rows * 128, &tmap, &bars[stage],
+                    strip * CS + sb * 32, b * p.box_rows);
+  };
+  if (tid == 0) {
+    for (int s = 0; s < p.stages && s < my_count; ++s) issue(s, my_first + s * stride);
   }
 
-  const int q = warp & 7, h = warp >> 3;
-  const int col = q * 4 + (lane >> 3);
+  const int q = warp & 7;
+  const int h = (H == 2) ? (warp >> 3) : 0;
+  const int sub = (H == 1) ? (warp >> 3) : 0;
+  const int col = q * 4 + (lane >> 3);  // column within the sub-tile
   const int r0 = h * 8 + (lane & 7);
-  const uint32_t off0 = static_cast<uint32_t>(r0) * 128u + ((static_cast<uint32_t>(q) ^ (lane & 7u)) << 4) +
-                        static_cast<uint32_t>((lane >> 3) * 4);
+  const uint32_t off0 = static_cast<uint32_t>(sub * subbytes) + static_cast<uint32_t>(r0) * 128u +
+                        ((static_cast<uint32_t>(q) ^ (lane & 7u)) << 4) + static_cast<uint32_t>((lane >> 3) * 4);
+  constexpr uint32_t kStep = RG * 128u;
   float acc[J];
 #pragma unroll
   for (int j = 0; j < J; ++j) acc[j] = 0.f;
@@ -113,8 +126,8 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
       float v = acc[j];
       v += __shfl_xor_sync(0xffffffffu, v, 8);
       v += __shfl_xor_sync(0xffffffffu, v, 16);
-      const int k = r0 + kRowGroups * j;
-      if (lane < 8 && k < K) slots[q * kp + k] += static_cast<double>(v);
+      const int k = r0 + RG * j;
+      if (lane < 8 && k < K) slots[warp * kp + k] += static_cast<double>(v);
       acc[j] = 0.f;
     }
   };
@@ -129,16 +142,16 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
       it_fail = it;
       break;
     }
-    const int gcol = strip * 32 + col;
+    const int gcol = strip * CS + sub * 32 + col;
 
     // A1: x_j in registers, column max
     float x[J];
     float m0 = -INFINITY, m1 = -INFINITY;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      const int k = r0 + kRowGroups * j;
+      const int k = r0 + RG * j;
       if (k < K) {
-        const float v = *reinterpret_cast<const float*>(tile + off0 + j * (kRowGroups * 128u));
+        const float v = *reinterpret_cast<const float*>(tile + off0 + j * kStep);
         x[j] = fmaf(-v, kLog2e, a_s[k]);
         if (j & 1)
           m1 = fmaxf(m1, x[j]);
@@ -152,17 +165,13 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
-    if ((lane & 7) == 0) colm[h * 32 + col] = m;
-    fence_proxy_async_smem();
-    __syncthreads();  // also: every warp is done reading this stage
-    if (tid == 0 && it + p.stages < my_count) {
-      unsigned char* dst = smem + s * sbytes;
-      mbar_expect_tx(&bars[s], tx);
-      for (int b = 0; b < p.nbox; ++b)
-        tma_load_2d(dst + static_cast<size_t>(b) * p.box_rows * 128, &tmap, &bars[s],
-                    (my_first + (it + p.stages) * stride) * 32, b * p.box_rows);
+    if constexpr (H == 2) {
+      if ((lane & 7) == 0) colm[h * 32 + col] = m;
     }
-    m = fmaxf(colm[col], colm[32 + col]);
+    fence_proxy_async_smem();
+    __syncthreads();  // every warp is done reading this stage
+    if (tid == 0 && it + p.stages < my_count) issue(s, my_first + (it + p.stages) * stride);
+    if constexpr (H == 2) m = fmaxf(colm[col], colm[32 + col]);
 
     // A2: e_j = 2^(x_j - m), column sum
     float s0 = 0.f, s1 = 0.f;
@@ -178,15 +187,17 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     ssum += __shfl_xor_sync(0xffffffffu, ssum, 1);
     ssum += __shfl_xor_sync(0xffffffffu, ssum, 2);
     ssum += __shfl_xor_sync(0xffffffffu, ssum, 4);
-    if ((lane & 7) == 0) cols[h * 32 + col] = ssum;
-    __syncthreads();
-    const float S = cols[col] + cols[32 + col];
+    if constexpr (H == 2) {
+      if ((lane & 7) == 0) cols[h * 32 + col] = ssum;
+      __syncthreads();
+      ssum = cols[col] + cols[32 + col];
+    }
     const bool valid = gcol < p.n;
     float w = 0.f;
     if (valid) {
-      w = (p.H ? static_cast<float>(p.H[gcol]) : 1.f) / S;
+      w = (p.H ? static_cast<float>(p.H[gcol]) : 1.f) / ssum;
       if (p.logden != nullptr && h == 0 && (lane & 7) == 0)
-        static_cast<float*>(p.logden)[gcol] = (m + __log2f(S)) * kLn2;
+        static_cast<float*>(p.logden)[gcol] = (m + __log2f(ssum)) * kLn2;
     }
 
     // B: row partials
@@ -205,25 +216,26 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   }
   flush();
   __syncthreads();
-  double rowsum[(1024 + kRThreads - 1) / kRThreads];
+  constexpr int RPT = (1024 + kRThreads - 1) / kRThreads;
+  double rowsum[RPT];
 #pragma unroll
-  for (int j = 0; j < (1024 + kRThreads - 1) / kRThreads; ++j) {
+  for (int j = 0; j < RPT; ++j) {
     const int k = tid + j * kRThreads;
     double t = 0.0;
     if (k < K) {
 #pragma unroll
-      for (int g = 0; g < 8; ++g) t += slots[g * kp + k];
+      for (int g = 0; g < NSLOT; ++g) t += slots[g * kp + k];
     }
     rowsum[j] = t;
   }
-  lse_finish<kRThreads, (1024 + kRThreads - 1) / kRThreads>(p, rowsum, red_s);
+  lse_finish<kRThreads, RPT>(p, rowsum, red_s);
 }
 
 // ---------------------------------------------------------------------------
 
 namespace {
 
-template <int J>
+template <int J, int H>
 int regs_occupancy(size_t smem) {
   static size_t max_dyn = 0;
   if (max_dyn == 0) {
@@ -231,56 +243,74 @@ int regs_occupancy(size_t smem) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, lse_regs_kernel<J>);
+    cudaFuncGetAttributes(&fa, lse_regs_kernel<J, H>);
     max_dyn = static_cast<size_t>(optin) - fa.sharedSizeBytes;
-    cudaFuncSetAttribute(lse_regs_kernel<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(max_dyn));
+    cudaFuncSetAttribute(lse_regs_kernel<J, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(max_dyn));
   }
   if (smem > max_dyn) return 0;
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, lse_regs_kernel<J>, kRThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, lse_regs_kernel<J, H>, kRThreads, smem) != cudaSuccess)
     blocks = 0;
   return blocks;
 }
 
-int regs_J(int64_t K) {
-  const int64_t j = ceil_div(K, kRowGroups);
-  if (j <= 4) return 4;
-  if (j <= 8) return 8;
-  if (j <= 16) return 16;
-  if (j <= 32) return 32;
-  return 0;  // larger K: the tiled variant (the FP64 row slots would not fit next to two stages)
+// (J, H) for a given K: H = 1 while J = ceil(K/8) <= 32, else H = 2.
+void regs_shape(int64_t K, int* J, int* H) {
+  const int64_t j1 = ceil_div(K, 8);
+  *H = j1 <= 32 ? 1 : 2;
+  const int64_t j = ceil_div(K, 8 * (*H));
+  *J = j <= 4 ? 4 : j <= 8 ? 8 : j <= 16 ? 16 : j <= 32 ? 32 : 0;
+}
+
+int regs_occ_dispatch(int J, int H, size_t smem) {
+  if (H == 1) {
+    switch (J) {
+      case 4: return regs_occupancy<4, 1>(smem);
+      case 8: return regs_occupancy<8, 1>(smem);
+      case 16: return regs_occupancy<16, 1>(smem);
+      case 32: return regs_occupancy<32, 1>(smem);
+    }
+  } else {
+    switch (J) {
+      case 16: return regs_occupancy<16, 2>(smem);
+      case 32: return regs_occupancy<32, 2>(smem);
+    }
+  }
+  return 0;
 }
 
 }  // namespace
 
-bool lse_regs_supported(int64_t K, int dtype_bytes) { return dtype_bytes == 4 && regs_J(K) > 0; }
+bool lse_regs_supported(int64_t K, int dtype_bytes) {
+  if (dtype_bytes != 4 || K < 1) return false;
+  int J = 0, H = 0;
+  regs_shape(K, &J, &H);
+  return J > 0;
+}
 
 LsePlan lse_regs_plan(int64_t K, int64_t n) {
   LsePlan pl{};
-  pl.C = 32;
+  int J = 0, H = 0;
+  regs_shape(K, &J, &H);
+  const int SUB = 2 / H;
   pl.variant = 1;
-  pl.J = regs_J(K);
+  pl.J = J;
+  pl.H = H;
+  pl.C = 32 * SUB;
   pl.threads = kRThreads;
-  pl.num_strips = static_cast<int>(ceil_div(n, 32));
+  pl.num_strips = static_cast<int>(ceil_div(n, pl.C));
   pl.box_rows = static_cast<int>(std::min<int64_t>(256, round_up(K, 8)));
   pl.nbox = static_cast<int>(ceil_div(K, pl.box_rows));
-  const size_t sb = static_cast<size_t>(pl.nbox) * pl.box_rows * 128;
-  const size_t extra = RegsSmem::extra(static_cast<int>(K)) + 1024;
-  // as many stages (2..4) as fit next to the slots
+  const size_t sb = static_cast<size_t>(SUB) * pl.nbox * pl.box_rows * 128;
+  const size_t extra = RegsSmem::extra(static_cast<int>(K), 16) + 1024;
   pl.stages = 4;
   while (pl.stages > 2 && pl.stages * sb + extra > 220 * 1024) --pl.stages;
   pl.smem = pl.stages * sb + extra;
   static int occ_cache[1025] = {};
   int* occ = &occ_cache[std::min<int64_t>(K, 1024)];
   if (*occ == 0) {
-    switch (pl.J) {
-      case 4: *occ = regs_occupancy<4>(pl.smem); break;
-      case 8: *occ = regs_occupancy<8>(pl.smem); break;
-      case 16: *occ = regs_occupancy<16>(pl.smem); break;
-      case 32: *occ = regs_occupancy<32>(pl.smem); break;
-      case 48: *occ = regs_occupancy<48>(pl.smem); break;
-      default: *occ = 0;
-    }
+    *occ = regs_occ_dispatch(J, H, pl.smem);
     cudaGetLastError();
   }
   pl.grid = static_cast<int>(std::min<int64_t>(pl.num_strips, static_cast<int64_t>(std::max(*occ, 1)) * num_sms()));
@@ -290,15 +320,21 @@ LsePlan lse_regs_plan(int64_t K, int64_t n) {
 }
 
 mbar_status lse_regs_launch(const CUtensorMap& tmap, const LsePlan& pl, const LseParams& prm, cudaStream_t st) {
-  switch (pl.J) {
-    case 4: lse_regs_kernel<4><<<pl.grid, kRThreads, pl.smem, st>>>(tmap, prm); break;
-    case 8: lse_regs_kernel<8><<<pl.grid, kRThreads, pl.smem, st>>>(tmap, prm); break;
-    case 16: lse_regs_kernel<16><<<pl.grid, kRThreads, pl.smem, st>>>(tmap, prm); break;
-    case 32: lse_regs_kernel<32><<<pl.grid, kRThreads, pl.smem, st>>>(tmap, prm); break;
-    case 48: lse_regs_kernel<48><<<pl.grid, kRThreads, pl.smem, st>>>(tmap, prm); break;
-    default:
-      set_error("lse_regs_launch: unsupported J=%d", pl.J);
-      return MBAR_EUNSUPPORTED;
+  const dim3 g(pl.grid), b(kRThreads);
+  if (pl.H == 1) {
+    switch (pl.J) {
+      case 4: lse_regs_kernel<4, 1><<<g, b, pl.smem, st>>>(tmap, prm); break;
+      case 8: lse_regs_kernel<8, 1><<<g, b, pl.smem, st>>>(tmap, prm); break;
+      case 16: lse_regs_kernel<16, 1><<<g, b, pl.smem, st>>>(tmap, prm); break;
+      case 32: lse_regs_kernel<32, 1><<<g, b, pl.smem, st>>>(tmap, prm); break;
+      default: set_error("lse_regs_launch: unsupported J=%d", pl.J); return MBAR_EUNSUPPORTED;
+    }
+  } else {
+    switch (pl.J) {
+      case 16: lse_regs_kernel<16, 2><<<g, b, pl.smem, st>>>(tmap, prm); break;
+      case 32: lse_regs_kernel<32, 2><<<g, b, pl.smem, st>>>(tmap, prm); break;
+      default: set_error("lse_regs_launch: unsupported J=%d", pl.J); return MBAR_EUNSUPPORTED;
+    }
   }
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());

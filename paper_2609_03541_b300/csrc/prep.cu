@@ -5,6 +5,8 @@
 // free energies are unchanged by any per-sample shift (the shift cancels
 // between numerator and denominator of Eq. 1), the stored magnitudes stay
 // small for the entries that carry weight, and every v_kn >= 0.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -12,43 +14,61 @@ namespace bumbar {
 
 namespace {
 
-// One block per 32 columns: 8 row groups x 32 columns. Pass 1 takes the
-// column minimum (warp-coalesced 256-byte row segments), pass 2 re-reads the
-// same 32 x K FP64 block -- small enough to still be in L2 -- and writes the
-// shifted FP32 values.
+// Persistent blocks, each handling strips of 32 columns: 8 row groups x 32
+// columns. Pass 1 takes the column minimum with integer comparisons on an
+// order-preserving image of the binary64 bits (FP64 arithmetic is slow on
+// this part); pass 2 re-reads the same 32 x K block -- few enough blocks are
+// resident that it is still in L2 -- and writes fl32(u - min).
+__device__ __forceinline__ unsigned long long ordered_bits(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
 __global__ void __launch_bounds__(256) shift_fp32_kernel(const double* __restrict__ u, int64_t K, int64_t N,
                                                          int64_t ldu, double* __restrict__ c, float* __restrict__ v,
                                                          int64_t ldv, int* bad) {
-  __shared__ double part[8][32];
+  __shared__ unsigned long long part[8][32];
   __shared__ int okp[8][32];
   const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
-  const int64_t n = static_cast<int64_t>(blockIdx.x) * 32 + lane;
-  double m = INFINITY;
-  bool ok = true;
-  if (n < N) {
-    for (int64_t k = rg; k < K; k += 8) {
-      const double x = u[k * ldu + n];
-      ok &= static_cast<bool>(isfinite(x));
-      m = fmin(m, x);
+  const int64_t nstrips = (N + 31) / 32;
+  for (int64_t strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
+    const int64_t n = strip * 32 + lane;
+    unsigned long long m = ~0ull;
+    bool ok = true;
+    if (n < N) {
+      for (int64_t k = rg; k < K; k += 8) {
+        const double x = u[k * ldu + n];
+        const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+        ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
+        const unsigned long long kx = ordered_bits(x);
+        m = kx < m ? kx : m;
+      }
+    }
+    part[rg][lane] = m;
+    okp[rg][lane] = ok ? 1 : 0;
+    __syncthreads();
+    unsigned long long mm = part[0][lane];
+    int allok = okp[0][lane];
+#pragma unroll
+    for (int g = 1; g < 8; ++g) {
+      mm = part[g][lane] < mm ? part[g][lane] : mm;
+      allok &= okp[g][lane];
+    }
+    __syncthreads();
+    if (n < N) {
+      double cm = from_ordered(mm);
+      if (!allok) {
+        if (rg == 0) atomicOr(bad, 1);
+        cm = 0.0;
+      }
+      if (rg == 0) c[n] = cm;
+      for (int64_t k = rg; k < K; k += 8) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - cm);
     }
   }
-  part[rg][lane] = m;
-  okp[rg][lane] = ok ? 1 : 0;
-  __syncthreads();
-  double mm = part[0][lane];
-  int allok = okp[0][lane];
-#pragma unroll
-  for (int g = 1; g < 8; ++g) {
-    mm = fmin(mm, part[g][lane]);
-    allok &= okp[g][lane];
-  }
-  if (n >= N) return;
-  if (!allok) {
-    if (rg == 0) atomicOr(bad, 1);
-    mm = 0.0;
-  }
-  if (rg == 0) c[n] = mm;
-  for (int64_t k = rg; k < K; k += 8) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - mm);
 }
 
 __global__ void copy_checked_kernel(const double* __restrict__ u, int64_t K, int64_t N, int64_t ldu,
@@ -78,7 +98,9 @@ __global__ void add_gauge_kernel(const double* __restrict__ f, const double* __r
 
 mbar_status shift_to_fp32(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, float* v, int64_t ldv,
                           int* bad, cudaStream_t st) {
-  shift_fp32_kernel<<<static_cast<unsigned>(ceil_div(N, 32)), 256, 0, st>>>(u, K, N, ldu, c, v, ldv, bad);
+  const int64_t strips = ceil_div(N, 32);
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(strips, 4 * static_cast<int64_t>(num_sms())));
+  shift_fp32_kernel<<<grid, 256, 0, st>>>(u, K, N, ldu, c, v, ldv, bad);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;

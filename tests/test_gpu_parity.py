@@ -6,8 +6,8 @@ Tolerances (from the arithmetic of each path):
   * FP64 path: 1e-9 kT per step and 1e-8 kT for the solve (sums of a few
     thousand binary64 terms in another order differ by ~1e-14 relative);
   * MIXED path: 1e-4 kT (FP32 exp with row sums accumulated in FP64);
-  * Hessian: 1e-4 of max|H| on the CUDA-core path (FP32 products,
-    FP64 reduction across slices).
+  * Hessian: 1e-4 of max|H| on the CUDA-core path (FP32 products, FP64
+    reduction across slices), 2e-3 on the tensor-core path (FP16 operands).
 """
 import numpy as np
 import pytest
@@ -43,8 +43,8 @@ def rand_f(K, seed=1):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("K,N", [(1, 50), (2, 33), (3, 1000), (8, 8013), (64, 4099), (257, 3001), (500, 2053),
-                                 (1000, 1031)])
+@pytest.mark.parametrize("K,N", [(1, 50), (2, 33), (3, 1000), (8, 8013), (64, 4099), (100, 3333), (200, 2111),
+                                 (257, 3001), (500, 2053), (513, 1500), (1000, 1031)])
 def test_sci_step_unbinned(prec, K, N):
     u, Nk = rand_problem(K, N, seed=K + N, offset=200.0)
     f = rand_f(K)
@@ -161,17 +161,22 @@ def test_binned_sci_step(prec):
 # c1/c2: Hessian and Newton step
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("path,tol", [(1, 1e-4), (2, 2e-3)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("K,N", [(2, 500), (8, 8000), (70, 3001), (200, 2500)])
-def test_hessian(prec, K, N):
+def test_hessian(prec, K, N, path, tol):
     u, Nk = rand_problem(K, N, seed=3 * K, spread=1.5)
     f = O.solve_mbar(u, Nk, tol=1e-10) if K <= 8 else rand_f(K, seed=2) * 0.1
-    ctx = M.Context(u, Nk, PREC[prec])
-    Hs = ctx.hessian(f)
-    ctx.close()
+    M.set_hessian_path(path)   # 1: CUDA cores (FP32), 2: tensor cores (FP16 operands)
+    try:
+        ctx = M.Context(u, Nk, PREC[prec])
+        Hs = ctx.hessian(f)
+        ctx.close()
+    finally:
+        M.set_hessian_path(0)
     H_ref = O.mbar_hessian(u, f, Nk)
     scale = np.max(np.abs(H_ref))
-    assert np.max(np.abs(Hs - H_ref)) < 1e-4 * scale
+    assert np.max(np.abs(Hs - H_ref)) < tol * scale
     assert np.max(np.abs(Hs - Hs.T)) < 1e-9 * scale
     assert np.max(np.abs(Hs.sum(axis=1))) < 1e-9 * scale
 
