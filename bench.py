@@ -225,6 +225,37 @@ def lse_only(args):
     return 0
 
 
+def hess_only(args):
+    """Times mbar_hessian on a random mixed-precision K x n problem (host
+    f in, host K x K out); reports the library-timed Hessian launches."""
+    import torch
+    from paper_2609_03541_b300 import mbar as M
+    K, n = args.lse_K, args.lse_n
+    g = np.random.default_rng(0)
+    x = g.uniform(0, 1, size=n)
+    centres = np.linspace(0, 1, K)
+    u = torch.empty((K, n), dtype=torch.float64, device="cuda")
+    for k0 in range(0, K, 64):
+        k1 = min(K, k0 + 64)
+        u[k0:k1] = torch.from_numpy(0.5 * (K * 0.8) ** 2 * (x[None, :] - centres[k0:k1, None]) ** 2).cuda()
+    Nk = np.full(K, n // K, dtype=np.int64)
+    Nk[: n - Nk.sum()] += 1
+    ctx = M.Context(u, Nk, M.MBAR_MIXED)
+    f = np.zeros(K)
+    for _ in range(max(args.warmup, 1)):
+        ctx.hessian(f)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.hessian(f)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    print(json.dumps({"kernel": "mbar_hessian (LSE pass + overlap_tc + Laplacian)", "K": K, "n": n,
+                      "ms_per_call_wall": ms, "flops_upper_triangle": 2.0 * K * K * n * 0.5}), flush=True)
+    ctx.close()
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # main
 # ---------------------------------------------------------------------------
@@ -246,9 +277,13 @@ def main():
     ap.add_argument("--lse-K", type=int, default=500)
     ap.add_argument("--lse-n", type=int, default=2_000_000)
     ap.add_argument("--lse-dtype", default="float32", choices=["float32", "float64"])
+    ap.add_argument("--hess-only", action="store_true",
+                    help="time mbar_hessian (one fused LSE pass + the tensor-core Hessian) on a random K x n problem")
     args = ap.parse_args()
     if args.lse_only:
         return lse_only(args)
+    if args.hess_only:
+        return hess_only(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

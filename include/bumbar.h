@@ -92,6 +92,10 @@ typedef struct {
   int64_t final_bins;        /* nonempty bins of the last binned level */
   double max_abs_grad;       /* max_k |g_k| at the returned f */
   double last_step;          /* max |delta f| of the last Newton step */
+  double seconds_width;      /* host wall time in the width search w*(n) */
+  double seconds_levels;     /* ... building histograms and binned matrices */
+  double seconds_sci;        /* ... in the SCI loops of Algorithm 1 */
+  double seconds_newton;     /* ... in the unbinned Newton phase */
 } mbar_report;
 
 /* Fills *opts with the defaults above (f_tol 1e-10 for MBAR_FP64, 1e-5 for
@@ -111,7 +115,8 @@ BUMBAR_API mbar_status mbar_opts_default(mbar_opts* opts, int32_t precision);
  *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream).
  * The library copies u_kn into its own device buffer (FP64, or FP32 after
  * subtracting c_n = min_k u_kn from each column in mixed precision) and
- * sets the bin coordinate to row 0 of u_kn.
+ * sets the bin coordinate to row 0 of u_kn. Freed stream-ordered allocations
+ * stay cached in the device's default memory pool (rebins reuse them).
  * Errors: EINVAL (sizes, counts, non-finite u), ENOMEM, ECUDA, EUNSUPPORTED. */
 BUMBAR_API mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
                         int32_t u_on_device, const mbar_opts* opts, void* cuda_stream);

@@ -5,6 +5,7 @@
 // Algorithm 1 (s < eps, 2 s_next > inc s_n, the break rule) and of the
 // Newton safeguard from values the kernels leave in device memory.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,7 +25,20 @@ using namespace bumbar;
 namespace {
 
 constexpr double kMaxIndex = 4503599627370496.0;  // 2^52
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 constexpr int kPhase1Batch = 16;                  // guarded SCI launches per host check
+
+// Scalars the kernels leave for the host, contiguous so one pinned copy
+// brings them all back.
+struct DevStatus {
+  Ctrl ctrl;
+  double s, s2, d;  // relative steps (Eq. 2) of the last probes, max |delta f|
+  unsigned err;     // bounded waits that gave up
+  unsigned pad;
+};
 
 struct Level {
   bool binned = false;
@@ -56,6 +70,7 @@ struct mbar_ctx {
   double* phi0 = nullptr;    // default bin coordinate (row 0 of u, original order)
   double* phi_sorted = nullptr;
   double* d_sorted = nullptr;  // phi_sorted - min(phi)
+  float2* d_pairs = nullptr;   // FP32 (hi, lo) split of d_sorted
   bool sorted = false;
   double phi_lo = 0.0, phi_hi = 0.0;
   Level full;  // unbinned level view (not owning)
@@ -67,6 +82,8 @@ struct mbar_ctx {
   int* info = nullptr;
   int* bad = nullptr;
   Ctrl* ctrl = nullptr;
+  DevStatus* stat = nullptr;   // device
+  DevStatus* hstat = nullptr;  // pinned host mirror
   void* logden = nullptr;  // N entries, dtype
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -88,6 +105,9 @@ struct mbar_ctx {
   std::vector<cudaEvent_t> pool;
   // solver trace: (phase, n, a, b) rows, see mbar_get_trace
   std::vector<double> trace;
+  double t_width = 0.0, t_levels = 0.0;  // host seconds, accumulated during a solve
+  cudaStream_t ust = nullptr;            // the caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -178,7 +198,7 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   p.H = L.H;
   unsigned char* sc = static_cast<unsigned char*>(c->scratch);
   p.counter = reinterpret_cast<unsigned*>(sc);
-  p.err = reinterpret_cast<unsigned*>(sc + 4);
+  p.err = &c->stat->err;
   p.partials = reinterpret_cast<double*>(sc + 256);
   p.Q = c->Q;
   p.logden = logden_out;
@@ -199,21 +219,18 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   return s;
 }
 
-unsigned* err_word(mbar_ctx* c) { return reinterpret_cast<unsigned*>(static_cast<unsigned char*>(c->scratch) + 4); }
+unsigned* err_word(mbar_ctx* c) { return &c->stat->err; }
 
-mbar_status check_device_errors(mbar_ctx* c) {
-  unsigned err = 0;
-  int nonfinite = 0;
-  BUMBAR_CUDA(cudaMemcpyAsync(&err, static_cast<unsigned char*>(c->scratch) + 4, sizeof(unsigned),
-                              cudaMemcpyDeviceToHost, c->st));
-  BUMBAR_CUDA(cudaMemcpyAsync(&nonfinite, &c->ctrl->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+// One pinned copy of the status block, one sync; then the error checks.
+mbar_status read_status(mbar_ctx* c) {
+  BUMBAR_CUDA(cudaMemcpyAsync(c->hstat, c->stat, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->st));
   BUMBAR_CUDA(cudaStreamSynchronize(c->st));
-  if (err) {
-    set_error("a bounded device-side wait gave up (%u CTAs)", err);
-    BUMBAR_CUDA(cudaMemsetAsync(static_cast<unsigned char*>(c->scratch) + 4, 0, sizeof(unsigned), c->st));
+  if (c->hstat->err) {
+    set_error("a bounded device-side wait gave up (%u CTAs)", c->hstat->err);
+    BUMBAR_CUDA(cudaMemsetAsync(&c->stat->err, 0, sizeof(unsigned), c->st));
     return MBAR_ETIMEOUT;
   }
-  if (nonfinite) {
+  if (c->hstat->ctrl.nonfinite) {
     set_error("non-finite free energies (a state lost all weight)");
     BUMBAR_CUDA(cudaMemsetAsync(&c->ctrl->nonfinite, 0, sizeof(int), c->st));
     return MBAR_ENOTCONV;
@@ -221,10 +238,21 @@ mbar_status check_device_errors(mbar_ctx* c) {
   return MBAR_OK;
 }
 
+mbar_status check_device_errors(mbar_ctx* c) { return read_status(c); }
+
 mbar_status ensure_sorted(mbar_ctx* c);
 
 // Histogram at width w over the sorted coordinate -> a binned level.
+mbar_status make_level_w_impl(mbar_ctx* c, double w, Level* L);
+
 mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
+  const double t0 = now_s();
+  const mbar_status s = make_level_w_impl(c, w, L);
+  c->t_levels += now_s() - t0;
+  return s;
+}
+
+mbar_status make_level_w_impl(mbar_ctx* c, double w, Level* L) {
   *L = Level{};
   BUMBAR_TRY(ensure_sorted(c));
   const size_t htmp = hist_tmp_bytes(c->N);
@@ -236,7 +264,8 @@ mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
   mbar_status s = dalloc_t(c, &keys_full, c->N);
   if (s == MBAR_OK) s = dalloc_t(c, &H_full, c->N);
   if (s == MBAR_OK)
-    s = build_histogram(c->d_sorted, c->N, w, c->seg, c->start, H_full, keys_full, c->nb_dev, tmp, htmp, c->st);
+    s = build_histogram(c->d_pairs, c->d_sorted, c->N, w, c->seg, c->start, H_full, keys_full, c->nb_dev, tmp, htmp,
+                        c->st);
   int32_t nb = 0;
   if (s == MBAR_OK) {
     cudaError_t e = cudaMemcpyAsync(&nb, c->nb_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
@@ -269,7 +298,7 @@ mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
 }
 
 mbar_status count_at(mbar_ctx* c, const double* ws, int nw, int64_t* g) {
-  BUMBAR_TRY(count_bins(c->d_sorted, c->N, ws, nw, c->count, c->st));
+  BUMBAR_TRY(count_bins(c->d_pairs, c->d_sorted, c->N, ws, nw, c->count, c->st));
   unsigned long long h[kWidthsPerPass];
   BUMBAR_CUDA(cudaMemcpyAsync(h, c->count, nw * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
   BUMBAR_CUDA(cudaStreamSynchronize(c->st));
@@ -282,7 +311,16 @@ mbar_status count_at(mbar_ctx* c, const double* ws, int nw, int64_t* g) {
 // sequential one, evaluated four levels at a time: one counting pass gets
 // g at all 15 midpoints of the next four levels of the bisection tree, then
 // the host walks the path the sequential search would take.
+mbar_status width_search_impl(mbar_ctx* c, int64_t n, double* w_out, bool* found);
+
 mbar_status width_search(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
+  const double t0 = now_s();
+  const mbar_status s = width_search_impl(c, n, w_out, found);
+  c->t_width += now_s() - t0;
+  return s;
+}
+
+mbar_status width_search_impl(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
   BUMBAR_TRY(ensure_sorted(c));
   const double R = c->phi_hi - c->phi_lo;
   *found = true;
@@ -388,7 +426,7 @@ mbar_status set_coordinate_dev(mbar_ctx* c, const double* phi_orig) {
   // phi_cur[i] = phi[perm[i]]
   if (s == MBAR_OK) s = gather_columns(phi_orig, phi_cur, 8, 1, N, N, c->perm, c->st);
   if (s == MBAR_OK) s = sort_coordinate(phi_cur, N, c->phi_sorted, perm_rel, tmp, stmp, c->st);
-  if (s == MBAR_OK) s = offsets_from_min(c->phi_sorted, N, c->d_sorted, c->st);
+  if (s == MBAR_OK) s = offsets_from_min(c->phi_sorted, N, c->d_sorted, c->d_pairs, c->st);
   // reorder the data columns and the bookkeeping by perm_rel
   if (s == MBAR_OK) s = gather_columns(c->v, tmp, c->dtype, c->K, N, c->ld, perm_rel, c->st);
   if (s == MBAR_OK) {
@@ -548,16 +586,60 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
 
 // Phase-1 loop of Algorithm 1 on level L: guarded in-place SCI steps until
 // s < eps (the guard turns later launches of a batch into no-ops).
+// A captured sequence of launches on the context's stream, replayed with
+// one cudaGraphLaunch (the binned loops of Algorithm 1 launch the same
+// kernels with the same arguments many times).
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  ~Graph() { reset(); }
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+};
+
+template <typename F>
+mbar_status capture(mbar_ctx* c, Graph* g, F&& body) {
+  g->reset();
+  BUMBAR_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  const mbar_status s = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+  if (s != MBAR_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+  const cudaError_t e2 = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return cuda_status(e2, "cudaGraphInstantiate");
+  return MBAR_OK;
+}
+
+// Phase-1 loop of Algorithm 1 on level L: guarded in-place SCI steps until
+// s < eps (the guard turns later launches of a batch into no-ops). A binned
+// level replays a captured batch of kPhase1Batch launches.
 mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
   BUMBAR_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st));
-  int64_t done_iters = 0;
-  for (;;) {
+  auto batch = [&]() -> mbar_status {
     for (int b = 0; b < kPhase1Batch; ++b)
       BUMBAR_TRY(run_lse(c, L, c->f, kLseModeSci, c->f, nullptr, c->s, c->opts.eps, 1, nullptr, nullptr,
                          c->opts.noise_floor));
-    Ctrl h{};
-    BUMBAR_CUDA(cudaMemcpyAsync(&h, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
-    BUMBAR_TRY(check_device_errors(c));
+    return MBAR_OK;
+  };
+  Graph g;
+  const bool use_graph = L.binned;  // unbinned launches carry timing events
+  if (use_graph) BUMBAR_TRY(capture(c, &g, batch));
+  int64_t done_iters = 0;
+  for (;;) {
+    if (use_graph) {
+      BUMBAR_CUDA(cudaGraphLaunch(g.exec, c->st));
+      count_launches(kPhase1Batch);
+    } else {
+      BUMBAR_TRY(batch());
+    }
+    BUMBAR_TRY(read_status(c));
+    const Ctrl h = c->hstat->ctrl;
     done_iters = h.iters;
     if (h.done || done_iters >= c->opts.max_sci) {
       trace_row(c, 1, static_cast<double>(L.n_sched), h.last_s, static_cast<double>(done_iters));
@@ -565,11 +647,6 @@ mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
     }
   }
   rep->iters_first_loop += done_iters;
-  return MBAR_OK;
-}
-
-mbar_status read_scalar(mbar_ctx* c, const double* d, double* h) {
-  BUMBAR_CUDA(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   return MBAR_OK;
 }
 
@@ -593,24 +670,51 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   }
   rep->n_rebins += nxt.binned ? 1 : 0;
   const int64_t N = c->N;
+  const int64_t K = c->K;
+  // one round: N_intermediate in-place steps on cur, the probe at n (-> ft)
+  // and the probe at n * inc (-> fts); the f buffers keep their addresses so
+  // the captured round stays valid until the level pair changes
+  auto round_body = [&]() -> mbar_status {
+    for (int i = 0; i < o.n_intermediate; ++i)
+      BUMBAR_TRY(run_lse(c, cur, c->f, kLseModeSci, c->f, nullptr, nullptr, 0.0, 0, nullptr));
+    BUMBAR_TRY(run_lse(c, cur, c->f, kLseModeSci, c->ft, nullptr, c->s, 0.0, 0, nullptr, c->d));
+    BUMBAR_TRY(run_lse(c, nxt, c->f, kLseModeSci, c->fts, nullptr, c->s2, 0.0, 0, nullptr));
+    return MBAR_OK;
+  };
+  Graph g;
+  bool captured = false;
   for (int64_t round = 0; s == MBAR_OK; ++round) {
     if (rep->iters_second_loop >= o.max_sci) break;
-    for (int i = 0; i < o.n_intermediate && s == MBAR_OK; ++i)
-      s = run_lse(c, cur, c->f, kLseModeSci, c->f, nullptr, nullptr, 0.0, 0, nullptr);
-    if (s == MBAR_OK) s = run_lse(c, cur, c->f, kLseModeSci, c->ft, nullptr, c->s, 0.0, 0, nullptr, c->d);
-    if (s == MBAR_OK) s = run_lse(c, nxt, c->f, kLseModeSci, c->fts, nullptr, c->s2, 0.0, 0, nullptr);
-    double s_n = 0, s_next = 0, d_n = 0;
-    if (s == MBAR_OK) s = read_scalar(c, c->s, &s_n);
-    if (s == MBAR_OK) s = read_scalar(c, c->s2, &s_next);
-    if (s == MBAR_OK) s = read_scalar(c, c->d, &d_n);
-    if (s == MBAR_OK) s = check_device_errors(c);
+    const bool use_graph = cur.binned && nxt.binned;
+    if (use_graph && !captured) {
+      s = capture(c, &g, round_body);
+      if (s != MBAR_OK) break;
+      captured = true;
+    }
+    if (use_graph) {
+      cudaError_t e = cudaGraphLaunch(g.exec, c->st);
+      if (e != cudaSuccess) {
+        s = cuda_status(e, "cudaGraphLaunch");
+        break;
+      }
+      count_launches(o.n_intermediate + 2);
+    } else {
+      s = round_body();
+    }
+    if (s == MBAR_OK) s = read_status(c);
     if (s != MBAR_OK) break;
+    const double s_n = c->hstat->s, s_next = c->hstat->s2, d_n = c->hstat->d;
     rep->iters_second_loop += o.n_intermediate + 2;
     trace_row(c, 2, static_cast<double>(cur.n_sched), s_n, s_next);
     // Eq. 3, plus: a step under the evaluation's rounding floor means the
     // level has converged as far as this arithmetic can tell
     if (2.0 * s_next > static_cast<double>(o.inc) * s_n || (o.noise_floor > 0.0 && d_n < o.noise_floor)) {
-      std::swap(c->f, c->fts);
+      if (cudaMemcpyAsync(c->f, c->fts, K * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess) {
+        s = MBAR_ECUDA;
+        break;
+      }
+      g.reset();
+      captured = false;
       level_free(c, &cur);
       cur = nxt;
       nxt = Level{};
@@ -619,9 +723,13 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
       s = schedule_level(c, idx + 1, &nxt);
       if (s == MBAR_OK) rep->n_rebins += nxt.binned ? 1 : 0;
     } else {
-      std::swap(c->f, c->ft);
+      if (cudaMemcpyAsync(c->f, c->ft, K * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess) {
+        s = MBAR_ECUDA;
+        break;
+      }
     }
   }
+  g.reset();
   rep->final_bins = cur.binned ? cur.n : 0;
   level_free(c, &cur);
   level_free(c, &nxt);
@@ -659,6 +767,20 @@ mbar_status upload_f(mbar_ctx* c, const double* f_host, double* dst) {
       return MBAR_EINVAL;                    \
     }                                        \
   } while (0)
+
+// Orders the context's internal stream after the caller's stream on entry
+// and the caller's stream after the internal one on exit.
+struct StreamFence {
+  mbar_ctx* c;
+  explicit StreamFence(mbar_ctx* ctx) : c(ctx) {
+    cudaEventRecord(c->ev_in, c->ust);
+    cudaStreamWaitEvent(c->st, c->ev_in, 0);
+  }
+  ~StreamFence() {
+    cudaEventRecord(c->ev_out, c->st);
+    cudaStreamWaitEvent(c->ust, c->ev_out, 0);
+  }
+};
 
 }  // namespace
 
@@ -757,11 +879,32 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
     set_error("mbar_create: host allocation failed");
     return MBAR_ENOMEM;
   }
+  {
+    // keep freed stream-ordered allocations cached in the device's default
+    // pool (level buffers are allocated and released on every rebin)
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
   c->K = K;
   c->N = N;
   c->opts = o;
   c->dtype = o.precision == MBAR_MIXED ? 4 : 8;
-  c->st = static_cast<cudaStream_t>(cuda_stream);
+  c->ust = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    mbar_status st = cuda_status(cudaGetLastError(), "stream/event creation");
+    mbar_destroy(c);
+    return st;
+  }
+  // u_kn may have been produced on the caller's stream
+  cudaEventRecord(c->ev_in, c->ust);
+  cudaStreamWaitEvent(c->st, c->ev_in, 0);
   c->ld = round_up(N, 32);
   c->Nk_h.resize(K);
   c->f_h.assign(K, 0.0);
@@ -785,18 +928,24 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   TRYC(h2d(c, c->Nk_d, c->Nk_h.data(), K));
   TRYC(h2d(c, c->logN_d, logN.data(), K));
   for (double** p : {&c->f, &c->fs, &c->ft, &c->fts, &c->g, &c->gt, &c->Q, &c->delta}) TRYC(dalloc_t(c, p, K));
-  TRYC(dalloc_t(c, &c->s, 1));
-  TRYC(dalloc_t(c, &c->s2, 1));
-  TRYC(dalloc_t(c, &c->d, 1));
+  {
+    void* st = nullptr;
+    TRYC(dalloc(c, &st, sizeof(DevStatus)));
+    c->stat = static_cast<DevStatus*>(st);
+    if (cudaMemsetAsync(c->stat, 0, sizeof(DevStatus), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+    if (cudaMallocHost(reinterpret_cast<void**>(&c->hstat), sizeof(DevStatus)) != cudaSuccess)
+      return fail(cuda_status(cudaGetLastError(), "cudaMallocHost"));
+    c->s = &c->stat->s;
+    c->s2 = &c->stat->s2;
+    c->d = &c->stat->d;
+    c->ctrl = &c->stat->ctrl;
+  }
   TRYC(dalloc_t(c, &c->hess, K * K));
   TRYC(dalloc_t(c, &c->info, 1));
   TRYC(dalloc_t(c, &c->bad, 1));
   TRYC(dalloc_t(c, &c->count, kWidthsPerPass));
   TRYC(dalloc_t(c, &c->nb_dev, 1));
-  void* ctrl = nullptr;
-  TRYC(dalloc(c, &ctrl, sizeof(Ctrl)));
-  c->ctrl = static_cast<Ctrl*>(ctrl);
-  if (cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+
   if (cudaMemsetAsync(c->bad, 0, sizeof(int), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   if (cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   TRYC(dalloc(c, &c->v, static_cast<size_t>(K) * c->ld * c->dtype));
@@ -807,6 +956,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   TRYC(dalloc_t(c, &c->phi0, N));
   TRYC(dalloc_t(c, &c->phi_sorted, N));
   TRYC(dalloc_t(c, &c->d_sorted, N));
+  TRYC(dalloc_t(c, &c->d_pairs, N));
   // the samples of u_kn on the device in FP64
   const double* u_dev = u_kn;
   double* u_tmp = nullptr;
@@ -867,6 +1017,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
 mbar_status mbar_set_coordinate(mbar_ctx* c, const double* phi, int32_t phi_on_device) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  StreamFence fence(c);
   if (!phi) {
     set_error("mbar_set_coordinate: phi is NULL");
     return MBAR_EINVAL;
@@ -894,6 +1045,7 @@ mbar_status mbar_set_coordinate(mbar_ctx* c, const double* phi, int32_t phi_on_d
 mbar_status mbar_bin(mbar_ctx* c, double h, int64_t* n_bins_out) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  StreamFence fence(c);
   if (!(h >= 0.0) || !std::isfinite(h)) {
     set_error("mbar_bin: h must be finite and >= 0");
     return MBAR_EINVAL;
@@ -919,6 +1071,7 @@ mbar_status mbar_bin(mbar_ctx* c, double h, int64_t* n_bins_out) {
 mbar_status mbar_bin_count(mbar_ctx* c, int64_t n, double* w_out, int64_t* n_bins_out) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  StreamFence fence(c);
   if (n < 1) {
     set_error("mbar_bin_count: n must be >= 1");
     return MBAR_EINVAL;
@@ -943,6 +1096,7 @@ mbar_status mbar_bin_count(mbar_ctx* c, int64_t n, double* w_out, int64_t* n_bin
 
 mbar_status mbar_get_bins(mbar_ctx* c, int64_t* keys, int64_t* H, double* u_kp) {
   CHECK_CTX(c);
+  StreamFence fence(c);
   if (!c->cur.binned) {
     set_error("mbar_get_bins: the current level is unbinned");
     return MBAR_ESTATE;
@@ -977,6 +1131,7 @@ mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double
                           double* logden) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  StreamFence fence(c);
   if (!f_in) {
     set_error("mbar_sci_step: f_in is NULL");
     return MBAR_EINVAL;
@@ -1023,6 +1178,7 @@ mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double
 mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  StreamFence fence(c);
   if (!f_in || !hess_out) {
     set_error("mbar_hessian: null pointer argument");
     return MBAR_EINVAL;
@@ -1046,6 +1202,7 @@ mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
 mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, double* step_max_abs) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  StreamFence fence(c);
   if (!f_in) {
     set_error("mbar_newton_step: f_in is NULL");
     return MBAR_EINVAL;
@@ -1083,6 +1240,7 @@ mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, dou
 mbar_status mbar_solve(mbar_ctx* c, const double* f_init, mbar_report* report) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  StreamFence fence(c);
   mbar_report rep{};
   const int64_t K = c->K;
   if (f_init) {
@@ -1093,13 +1251,20 @@ mbar_status mbar_solve(mbar_ctx* c, const double* f_init, mbar_report* report) {
     BUMBAR_CUDA(cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st));
   }
   c->trace.clear();
+  c->t_width = c->t_levels = 0.0;
   mbar_status s = MBAR_OK;
   if (K > 1) {
+    const double t0 = now_s();
     if (c->opts.use_binning)
       s = algorithm1(c, &rep);
     else
       s = plain_warmup(c, &rep);
+    const double t1 = now_s();
     if (s == MBAR_OK) s = newton_phase(c, &rep);
+    rep.seconds_newton = now_s() - t1;
+    rep.seconds_width = c->t_width;
+    rep.seconds_levels = c->t_levels;
+    rep.seconds_sci = (t1 - t0) - c->t_width - c->t_levels;
   }
   mbar_status s2 = d2h(c, c->f_h.data(), c->f, K);
   if (s2 == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s2 = MBAR_ECUDA;
@@ -1189,12 +1354,18 @@ mbar_status mbar_destroy(mbar_ctx* c) {
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   level_free(c, &c->cur);
-  void* ptrs[] = {c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->f,
-                  c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->s,          c->s2,
-                  c->hess, c->delta,  c->info,  c->bad,    c->ctrl,  c->logden,  c->scratch,    c->seg, c->d,
+  void* ptrs[] = {c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->d_pairs, c->f,
+                  c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->stat,
+                  c->hess, c->delta,  c->info,  c->bad,    c->logden,  c->scratch,    c->seg,
                   c->start, c->count, c->nb_dev};
-  for (void* p : ptrs) dfree(c, p);
-  cudaStreamSynchronize(c->st);
+  if (c->st) {
+    for (void* p : ptrs) dfree(c, p);
+    cudaStreamSynchronize(c->st);
+    cudaStreamDestroy(c->st);
+  }
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->hstat) cudaFreeHost(c->hstat);
   delete c;
   return MBAR_OK;
 }

@@ -28,26 +28,38 @@ __device__ __forceinline__ unsigned long long order_key(double x) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
-// floor(RN(d / w)) for d = phi - phi_lo >= 0, with one FP64 multiply and
-// integer work in the common case: q = RN(d * rw), rw = RN(1/w), is within
-// about 3 ulp(q) of RN(d/w), so unless q lies within 8 ulps of an integer
-// its integer part (read from the binary64 bits) is the bin index; the rare
-// close cases, and q >= 2^49 where every value is close, use the correctly
-// rounded division.
-__device__ __forceinline__ long long key_from_d(double d, double w, double rw) {
-  const double q = __dmul_rn(d, rw);
-  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(q));
-  const int e = static_cast<int>((bits >> 52) & 0x7FF) - 1023;
-  if (e < 0) {
-    if (bits < 0x3FEFFFFFFFFFFFF8ull) return 0;  // q < 1 - 8 ulp: bin 0
-  } else if (e < 49) {
-    const int sh = 52 - e;
-    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
-    const unsigned long long one = 1ull << sh;
-    const unsigned long long frac = mant & (one - 1);
-    if (frac >= 8 && frac <= one - 8) return static_cast<long long>(mant >> sh);
-  }
-  return static_cast<long long>(floor(__ddiv_rn(d, w)));
+// floor(RN(d / w)) from a double-float FP32 pair (d_hi + d_lo ~ d to
+// 2^-48 relative) and rw_hi + rw_lo ~ RN(1/w): the product is formed with an
+// exact FP32 FMA error term, so q = d/w is known to ~|q| 2^-44; its integer
+// part is returned when the fractional part is farther than
+// 2^-20 + |q| 2^-42 from an integer, which also covers the rounding of RN(d/w)
+// itself. Otherwise (about 2e-5 of random inputs) the correctly rounded FP64
+// division decides. FP32 arithmetic only in the common case.
+struct RecipW {
+  double w;
+  float hi, lo;
+};
+
+__host__ __device__ inline RecipW make_recip(double w) {
+  RecipW r;
+  r.w = w;
+  const double rw = 1.0 / w;
+  r.hi = static_cast<float>(rw);
+  r.lo = static_cast<float>(rw - static_cast<double>(r.hi));
+  return r;
+}
+
+__device__ __forceinline__ long long key_df(float dh, float dl, const RecipW& r, const double* d_exact) {
+  const float p_hi = __fmul_rn(dh, r.hi);
+  const float p_err = __fmaf_rn(dh, r.hi, -p_hi);
+  const float t = __fadd_rn(__fadd_rn(__fmul_rn(dh, r.lo), __fmul_rn(dl, r.hi)), p_err);
+  const float fl = floorf(p_hi);
+  const float rr = __fadd_rn(__fsub_rn(p_hi, fl), t);
+  const float fr = floorf(rr);
+  const float frac = __fsub_rn(rr, fr);
+  const float delta = 9.5367431640625e-07f + fabsf(p_hi) * 2.2737367544323206e-13f;  // 2^-20 + |q| 2^-42
+  if (frac > delta && frac < 1.0f - delta) return static_cast<long long>(fl) + static_cast<long long>(fr);
+  return static_cast<long long>(floor(__ddiv_rn(*d_exact, r.w)));
 }
 
 // ---------------------------------------------------------------------------
@@ -220,14 +232,13 @@ __global__ void gather_phi(const double* __restrict__ phi, const int32_t* __rest
 // and at the end of its chunk: equal means no bin starts inside, a difference
 // of one means exactly one does; only otherwise are all 16 indices formed.
 struct WidthSet {
-  double w[kMaxWidths];
-  double rw[kMaxWidths];
+  RecipW r[kMaxWidths];
   int n;
 };
 constexpr int kCountChunk = 16;
 
-__global__ void count_heads_multi(const double* __restrict__ d, int64_t N, WidthSet ws,
-                                  unsigned long long* __restrict__ counts) {
+__global__ void count_heads_multi(const float2* __restrict__ dhl, const double* __restrict__ d, int64_t N,
+                                  WidthSet ws, unsigned long long* __restrict__ counts) {
   __shared__ unsigned int cnt[kMaxWidths];
   if (threadIdx.x < kMaxWidths) cnt[threadIdx.x] = 0u;
   __syncthreads();
@@ -237,27 +248,30 @@ __global__ void count_heads_multi(const double* __restrict__ d, int64_t N, Width
   for (int c = 0; c < ws.n; ++c) {
     unsigned int heads = 0;
     if (i0 < N) {
-      const double w = ws.w[c], rw = ws.rw[c];
-      const long long kend = key_from_d(d[i1 - 1], w, rw);
+      const RecipW r = ws.r[c];
+      const float2 e = dhl[i1 - 1];
+      const long long kend = key_df(e.x, e.y, r, d + i1 - 1);
       long long kprev;
       if (i0 == 0) {
         heads = 1;  // the first sample opens the first bin
-        kprev = key_from_d(d[0], w, rw);
+        const float2 s0 = dhl[0];
+        kprev = key_df(s0.x, s0.y, r, d);
       } else {
-        kprev = key_from_d(d[i0 - 1], w, rw);
+        const float2 sp = dhl[i0 - 1];
+        kprev = key_df(sp.x, sp.y, r, d + i0 - 1);
       }
       const long long diff = kend - kprev;
       if (diff == 1) {
         heads += 1;
       } else if (diff > 1) {
         for (int64_t i = (i0 == 0 ? 1 : i0); i < i1; ++i) {
-          const long long k = key_from_d(d[i], w, rw);
+          const float2 x = dhl[i];
+          const long long k = key_df(x.x, x.y, r, d + i);
           heads += (k != kprev) ? 1u : 0u;
           kprev = k;
         }
       }
     }
-    // warp sum, one shared atomic per warp
     for (int o = 16; o >= 1; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
     if (lane == 0 && heads) atomicAdd(&cnt[c], heads);
   }
@@ -265,21 +279,34 @@ __global__ void count_heads_multi(const double* __restrict__ d, int64_t N, Width
   if (threadIdx.x < ws.n && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], static_cast<unsigned long long>(cnt[threadIdx.x]));
 }
 
-__global__ void offsets_from_lo(const double* __restrict__ phi, int64_t N, double* __restrict__ d) {
+__global__ void offsets_from_lo(const double* __restrict__ phi, int64_t N, double* __restrict__ d,
+                                float2* __restrict__ dhl) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < N) d[i] = __dsub_rn(phi[i], phi[0]);
+  if (i < N) {
+    const double x = __dsub_rn(phi[i], phi[0]);
+    d[i] = x;
+    const float hi = __double2float_rn(x);
+    dhl[i] = make_float2(hi, __double2float_rn(__dsub_rn(x, static_cast<double>(hi))));
+  }
 }
 
-__global__ void head_flags(const double* __restrict__ d, int64_t N, double w, double rw, int* __restrict__ flags) {
+__global__ void head_flags(const float2* __restrict__ dhl, const double* __restrict__ d, int64_t N, RecipW r,
+                           int* __restrict__ flags) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   long long key = 0;
-  if (i < N) key = key_from_d(d[i], w, rw);
+  if (i < N) {
+    const float2 x = dhl[i];
+    key = key_df(x.x, x.y, r, d + i);
+  }
   long long prev = __shfl_up_sync(0xffffffffu, key, 1);
-  if ((threadIdx.x & 31) == 0 && i > 0 && i < N) prev = key_from_d(d[i - 1], w, rw);
+  if ((threadIdx.x & 31) == 0 && i > 0 && i < N) {
+    const float2 x = dhl[i - 1];
+    prev = key_df(x.x, x.y, r, d + i - 1);
+  }
   if (i < N) flags[i] = (i == 0 || key != prev) ? 1 : 0;
 }
 
-__global__ void finish_histogram(const double* __restrict__ d, int64_t N, double w, double rw,
+__global__ void finish_histogram(const float2* __restrict__ dhl, const double* __restrict__ d, int64_t N, RecipW r,
                                  const int* __restrict__ flags,
                                  const int* __restrict__ excl, int32_t* __restrict__ seg, int32_t* __restrict__ start,
                                  int64_t* __restrict__ keys, int32_t* __restrict__ nb_dev) {
@@ -290,7 +317,8 @@ __global__ void finish_histogram(const double* __restrict__ d, int64_t N, double
   seg[i] = e + f - 1;
   if (f) {
     start[e] = static_cast<int32_t>(i);
-    keys[e] = key_from_d(d[i], w, rw);
+    const float2 x = dhl[i];
+    keys[e] = key_df(x.x, x.y, r, d + i);
   }
   if (i == N - 1) {
     const int nb = e + f;
@@ -570,14 +598,16 @@ mbar_status sort_coordinate(const double* phi, int64_t N, double* phi_sorted, in
   return MBAR_OK;
 }
 
-mbar_status offsets_from_min(const double* phi_sorted, int64_t N, double* d_sorted, cudaStream_t st) {
-  offsets_from_lo<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(phi_sorted, N, d_sorted);
+mbar_status offsets_from_min(const double* phi_sorted, int64_t N, double* d_sorted, float2* d_pairs,
+                             cudaStream_t st) {
+  offsets_from_lo<<<static_cast<unsigned>(ceil_div(N, kThreads)), kThreads, 0, st>>>(phi_sorted, N, d_sorted,
+                                                                                     d_pairs);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
 }
 
-mbar_status count_bins(const double* d_sorted, int64_t N, const double* widths, int nw,
+mbar_status count_bins(const float2* d_pairs, const double* d_sorted, int64_t N, const double* widths, int nw,
                        unsigned long long* counts_dev, cudaStream_t st) {
   if (nw < 1 || nw > kMaxWidths) {
     set_error("count_bins: 1..%d widths per pass", kMaxWidths);
@@ -585,13 +615,10 @@ mbar_status count_bins(const double* d_sorted, int64_t N, const double* widths, 
   }
   WidthSet ws{};
   ws.n = nw;
-  for (int c = 0; c < nw; ++c) {
-    ws.w[c] = widths[c];
-    ws.rw[c] = 1.0 / widths[c];
-  }
+  for (int c = 0; c < nw; ++c) ws.r[c] = make_recip(widths[c]);
   BUMBAR_CUDA(cudaMemsetAsync(counts_dev, 0, kMaxWidths * sizeof(unsigned long long), st));
   count_heads_multi<<<static_cast<unsigned>(ceil_div(N, static_cast<int64_t>(kThreads) * kCountChunk)), kThreads, 0,
-                      st>>>(d_sorted, N, ws, counts_dev);
+                      st>>>(d_pairs, d_sorted, N, ws, counts_dev);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
@@ -599,8 +626,9 @@ mbar_status count_bins(const double* d_sorted, int64_t N, const double* widths, 
 
 size_t hist_tmp_bytes(int64_t N) { return round_up(N * 4, 256) * 2 + round_up(scan_tmp_bytes(N), 256); }
 
-mbar_status build_histogram(const double* d_sorted, int64_t N, double w, int32_t* seg, int32_t* start, int32_t* H,
-                            int64_t* keys, int32_t* nb_dev, void* tmp, size_t tmp_bytes, cudaStream_t st) {
+mbar_status build_histogram(const float2* d_pairs, const double* d_sorted, int64_t N, double w, int32_t* seg,
+                            int32_t* start, int32_t* H, int64_t* keys, int32_t* nb_dev, void* tmp, size_t tmp_bytes,
+                            cudaStream_t st) {
   if (tmp_bytes < hist_tmp_bytes(N)) {
     set_error("build_histogram: scratch too small");
     return MBAR_EINVAL;
@@ -611,11 +639,11 @@ mbar_status build_histogram(const double* d_sorted, int64_t N, double w, int32_t
   int* excl = reinterpret_cast<int*>(p);
   p += round_up(N * 4, 256);
   const unsigned gN = static_cast<unsigned>(ceil_div(N, kThreads));
-  const double rw = 1.0 / w;
-  head_flags<<<gN, kThreads, 0, st>>>(d_sorted, N, w, rw, flags);
+  const RecipW rw = make_recip(w);
+  head_flags<<<gN, kThreads, 0, st>>>(d_pairs, d_sorted, N, rw, flags);
   count_launches(1);
   BUMBAR_TRY(excl_scan(flags, N, excl, nullptr, p, st));
-  finish_histogram<<<gN, kThreads, 0, st>>>(d_sorted, N, w, rw, flags, excl, seg, start, keys, nb_dev);
+  finish_histogram<<<gN, kThreads, 0, st>>>(d_pairs, d_sorted, N, rw, flags, excl, seg, start, keys, nb_dev);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   int32_t nb = 0;

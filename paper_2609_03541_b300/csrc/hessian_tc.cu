@@ -33,7 +33,8 @@ namespace bumbar {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
+constexpr int kRowStride = kTcThreads / 8;  // threads per 8-sample group column
 constexpr int kChunkCols = 64;                 // samples per chunk = one 128-byte FP16 row
 constexpr int kMaxRows = 640;                  // A tile + 4 B tiles
 constexpr int kStageBytes = kMaxRows * 128;    // 80 KB per buffer
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
 
   const int64_t nchunks = (job.c_end - job.c_begin + kChunkCols - 1) / kChunkCols;
   const int g = tid & 7;         // 8-sample group of the chunk
-  const int rsub = tid >> 3;     // first local row; rows rsub, rsub + 32, ...
+  const int rsub = tid >> 3;     // first local row; rows rsub, rsub + kRowStride, ...
   constexpr uint32_t idesc = idesc_f16(128, 128);
   const T* vv = static_cast<const T*>(p.v);
   const T* ld_in = static_cast<const T*>(p.logden);
@@ -198,11 +199,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
     }
     const bool full8 = col0 + 8 <= job.c_end;
     // four rows per round: issue all loads first, then the SFU work
-    for (int lr0 = rsub; lr0 < rows; lr0 += 128) {
-      float x[4][8];
+    constexpr int kRowsPerRound = 4;
+    for (int lr0 = rsub; lr0 < rows; lr0 += kRowStride * kRowsPerRound) {
+      float x[kRowsPerRound][8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int lr = lr0 + 32 * u;
+      for (int u = 0; u < kRowsPerRound; ++u) {
+        const int lr = lr0 + kRowStride * u;
         const int row = lr < rowsA ? job.bi * 128 + lr : job.bj0 * 128 + (lr - rowsA);
         if (lr < rows && row < p.K) {
           const T* src = vv + static_cast<int64_t>(row) * p.ld + col0;
@@ -226,8 +228,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int lr = lr0 + 32 * u;
+      for (int u = 0; u < kRowsPerRound; ++u) {
+        const int lr = lr0 + kRowStride * u;
         if (lr < rows) {
           const float a2 = a2_s[lr];
           float pv[8];
@@ -271,13 +273,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
   if (failed && tid == 0) atomicAdd(p.err, 1u);
   tc_fence_after();
 
-  // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31; warps w and w+4 split the columns
+  // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31; the four warps of a
+  // lane quarter split the columns
   float* out = p.out + static_cast<int64_t>(blockIdx.x) * 128 * 512;
   const int sub = warp & 3;
-  const int half = warp >> 2;
+  const int quarter = warp >> 2;  // 0..3
   const int used = job.nt * 128;
   const int row_local = sub * 32 + lane;
-  for (int c0 = half * 32; c0 < used; c0 += 64) {
+  for (int c0 = quarter * 32; c0 < used; c0 += 128) {
     float r[32];
     if (nchunks > 0 && !failed) {
       tmem_ld32(tmem + (static_cast<uint32_t>(sub * 32) << 16) + static_cast<uint32_t>(c0), r);

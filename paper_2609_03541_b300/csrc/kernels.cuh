@@ -71,19 +71,22 @@ size_t sort_tmp_bytes(int64_t N);
 
 // d_sorted[i] = phi_sorted[i] - phi_sorted[0] (binary64, rounded to nearest):
 // the offsets every bin index is computed from.
-mbar_status offsets_from_min(const double* phi_sorted, int64_t N, double* d_sorted, cudaStream_t stream);
+// d_pairs[i] = (hi, lo) FP32 split of d_sorted[i] for the FP32 bin-index path.
+mbar_status offsets_from_min(const double* phi_sorted, int64_t N, double* d_sorted, float2* d_pairs,
+                             cudaStream_t stream);
 
 // Counts of nonempty bins g(w) over the sorted offsets for nw <= 15 widths
 // in one pass; counts_dev holds 15 entries.
 constexpr int kWidthsPerPass = 15;
-mbar_status count_bins(const double* d_sorted, int64_t N, const double* widths, int nw,
+mbar_status count_bins(const float2* d_pairs, const double* d_sorted, int64_t N, const double* widths, int nw,
                        unsigned long long* counts_dev, cudaStream_t stream);
 
 // Histogram at width w over the sorted offsets: per sorted sample its bin ordinal
 // seg[N] (0..nb-1), bin start offsets start[nb+1], counts H[nb] (int32),
 // keys[nb] (int64). nb is returned through *nb_dev. tmp sized by
 // hist_tmp_bytes.
-mbar_status build_histogram(const double* d_sorted, int64_t N, double w, int32_t* seg, int32_t* start,
+mbar_status build_histogram(const float2* d_pairs, const double* d_sorted, int64_t N, double w, int32_t* seg,
+                            int32_t* start,
                             int32_t* H, int64_t* keys, int32_t* nb_dev, void* tmp, size_t tmp_bytes,
                             cudaStream_t stream);
 size_t hist_tmp_bytes(int64_t N);

@@ -67,6 +67,10 @@ class Report(ctypes.Structure):
         ("final_bins", ctypes.c_int64),
         ("max_abs_grad", ctypes.c_double),
         ("last_step", ctypes.c_double),
+        ("seconds_width", ctypes.c_double),
+        ("seconds_levels", ctypes.c_double),
+        ("seconds_sci", ctypes.c_double),
+        ("seconds_newton", ctypes.c_double),
     ]
 
     def as_dict(self):
