@@ -258,6 +258,34 @@ BUMBAR_API mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t
                           const double* f, const double* log_N, const int32_t* H, double* Q, void* logden,
                           void* scratch, size_t scratch_bytes, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free variant of mbar_lse_pass (no counterpart in the paper;
+ * an interface for callers that cannot allocate device memory: for example
+ * a host framework whose caching allocator already owns nearly all of the
+ * GPU's memory, or a latency-critical loop where cudaMalloc's implicit
+ * device synchronisation is not acceptable).
+ *
+ * Same arguments, layout and results as mbar_lse_pass, minus the scratch
+ * buffer: the pass uses a fixed, 256-byte-aligned array of
+ * mbar_lse_static_scratch_bytes() bytes (1 MiB) compiled into this library,
+ * which every GPU that loads the library holds until the process exits.
+ * The call allocates nothing (no cudaMalloc/cudaFree, no allocating library
+ * routine); it zeroes the array's counter on `stream` before launching.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make this first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls that overlap on the GPU (concurrent streams, several host
+ *     threads) race and give wrong results; order them.
+ *   - Sizes whose scratch need (mbar_lse_scratch_bytes) exceeds the array
+ *     are rejected with MBAR_EUNSUPPORTED and a message naming both sizes;
+ *     use mbar_lse_pass with a caller buffer for those.
+ * ------------------------------------------------------------------- */
+BUMBAR_API size_t mbar_lse_static_scratch_bytes(void);
+BUMBAR_API mbar_status mbar_lse_pass_static(const void* v, int32_t dtype_bytes, int64_t K, int64_t n, int64_t ld,
+                                            const double* f, const double* log_N, const int32_t* H, double* Q,
+                                            void* logden, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,9 @@ _SIGNATURES = {
     "mbar_kernel_launches": ([_i64p], ctypes.c_int),
     "mbar_get_trace": ([_vp, _i64p, _dp, ctypes.c_int64], ctypes.c_int),
     "mbar_set_hessian_path": ([ctypes.c_int32], ctypes.c_int),
+    "mbar_lse_static_scratch_bytes": ([], ctypes.c_size_t),
+    "mbar_lse_pass_static": ([_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
+                              _vp, _vp, _vp], ctypes.c_int),
     "mbar_lse_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32], ctypes.c_size_t),
     "mbar_lse_pass": ([_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
                        _vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
@@ -320,3 +323,18 @@ def lse_pass(v, f, log_N, Q, H=None, logden=None, scratch=None, stream=None):
         ctypes.c_void_p(Q.data_ptr()),
         ctypes.c_void_p(logden.data_ptr()) if logden is not None else None,
         ctypes.c_void_p(scratch.data_ptr()), int(scratch.numel()), ctypes.c_void_p(st)))
+
+
+def lse_pass_static(v, f, log_N, Q, H=None, logden=None, stream=None):
+    """``mbar_lse_pass_static``: the fused LSE pass with the library's built-in
+    scratch array (no device allocation by the call). Arguments as in
+    ``lse_pass`` minus ``scratch``."""
+    K, n = int(v.shape[0]), int(v.shape[1])
+    st = stream.cuda_stream if stream is not None else 0
+    _check(lib().mbar_lse_pass_static(
+        ctypes.c_void_p(v.data_ptr()), int(v.element_size()), K, n, int(v.stride(0)),
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(log_N.data_ptr()),
+        ctypes.c_void_p(H.data_ptr()) if H is not None else None,
+        ctypes.c_void_p(Q.data_ptr()),
+        ctypes.c_void_p(logden.data_ptr()) if logden is not None else None,
+        ctypes.c_void_p(st)))
