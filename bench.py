@@ -260,13 +260,198 @@ def hess_only(args):
 # main
 # ---------------------------------------------------------------------------
 
+def _gen_device(kind: str, K: int, Nk: int, seed: int):
+    from paper_2609_03541_b300 import workloads as W
+    if kind == "harmonic":
+        return W.harmonic_device(K, Nk, seed)
+    return W.umbrella_device(K, Nk, seed)
+
+
+def batch_bench(args):
+    """512 uneven problems (K ~ U{4..256}, N_k ~ U{100..10000} per problem,
+    alternating harmonic d=3 / umbrella), mixed precision, solved by
+    mbar_batch_solve in footprint waves: each wave's FP64 inputs are drawn on
+    the device (untimed), then the wave's batch solve is timed (wall clock,
+    device synchronised on both sides). The first wave is also solved on the
+    plain FP64 path for the accuracy and speed comparison."""
+    import torch
+    from paper_2609_03541_b300 import mbar as M
+    rng = np.random.default_rng(args.seed)
+    P = args.problems
+    specs = [("harmonic" if i % 2 == 0 else "umbrella", int(rng.integers(4, 257)), int(rng.integers(100, 10001)),
+              1000 + i) for i in range(P)]
+    wave_cap = int(args.wave_gb * (1 << 30))
+    waves, cur, cur_b = [], [], 0
+    for sp in specs:
+        b = sp[1] * sp[1] * sp[2] * 8
+        if cur and cur_b + b > wave_cap:
+            waves.append(cur)
+            cur, cur_b = [], 0
+        cur.append(sp)
+        cur_b += b
+    if cur:
+        waves.append(cur)
+    cfg = M.server_config(workers=args.workers, hbm_budget_bytes=int(args.budget_gb * (1 << 30)),
+                          precision=M.MBAR_MIXED)
+    total_s, entries, wave_info = 0.0, 0, []
+    acc = None
+    for wi, wave in enumerate(waves):
+        probs = []
+        for kind, K, Nk, seed in wave:
+            u, nk, phi = _gen_device(kind, K, Nk, seed)
+            probs.append((u, nk, phi))
+            entries += K * K * Nk
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fs, reps, sts = M.batch_solve(probs, cfg)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        total_s += dt
+        bad = [i for i, st in enumerate(sts) if st != 0]
+        wave_info.append({"problems": len(wave), "seconds": dt, "failed": len(bad)})
+        log(f"[bench] batch wave {wi}: {len(wave)} problems in {dt:.3f} s, failed {len(bad)}")
+        if wi == 0 and not args.no_accuracy:
+            cfg64 = M.server_config(workers=args.workers, hbm_budget_bytes=int(args.budget_gb * (1 << 30)),
+                                    precision=M.MBAR_FP64)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            f64, _, st64 = M.batch_solve(probs, cfg64)
+            torch.cuda.synchronize()
+            dt64 = time.perf_counter() - t1
+            err = max(float(np.max(np.abs(a - b))) for a, b, s1, s2 in zip(fs, f64, sts, st64) if s1 == 0 and s2 == 0)
+            acc = {"wave0_problems": len(wave), "max_abs_df_vs_fp64_gpu_kT": err, "fp64_wave0_s": dt64,
+                   "mixed_wave0_s": dt, "mixed_speedup_vs_fp64_gpu": dt64 / dt}
+        del probs, fs
+        torch.cuda.empty_cache()
+    line = {"metric": "MBAR solves/sec (batched)", "value": P / total_s, "unit": "solves/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": total_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: 512 problems, K~U{4..256}, N_k~U{100..10000} per problem, harmonic d=3 / "
+                                   "umbrella alternating, mixed precision, mbar_batch_solve in footprint waves",
+                       "problems": P, "entries": entries, "workers": args.workers, "budget_gb": args.budget_gb,
+                       "wave_input_gb": args.wave_gb},
+            "waves": wave_info, "accuracy": acc}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_bench(args):
+    """Serving stream: requests with K log-uniform in [4, 1024] and N_k ~
+    U{100..20000} (harmonic / umbrella alternating), drawn on the device at
+    their arrival (timed separately), submitted to one mbar_server (mixed
+    precision, memory budget); first at saturation (all submitted as soon as
+    drawn) for the capacity, then with Poisson arrivals at the given fractions
+    of that capacity for p50/p99 latency from arrival to completion."""
+    import torch
+    from paper_2609_03541_b300 import mbar as M
+    rng = np.random.default_rng(args.seed)
+    R = args.requests
+    Ks = np.exp(rng.uniform(np.log(4), np.log(1024), size=R)).astype(int)
+    Nks = rng.integers(100, 20001, size=R)
+    specs = [("harmonic" if i % 2 == 0 else "umbrella", int(Ks[i]), int(Nks[i]), 5000 + i) for i in range(R)]
+    budget = int(args.budget_gb * (1 << 30))
+    input_cap = int(args.wave_gb * (1 << 30))
+
+    def run(rate):
+        cfg = M.server_config(workers=args.workers, hbm_budget_bytes=budget, precision=M.MBAR_MIXED)
+        srv = M.Server(cfg)
+        pending = {}   # id -> (arrival time, input bytes, K)
+        lat, rejected, gen_s = [], 0, 0.0
+        held = 0
+        t_start = time.perf_counter()
+        t_next = t_start
+        done = 0
+
+        def reap(block):
+            nonlocal held, done
+            for rid in list(pending):
+                if block or srv.poll(rid) == 2:
+                    t_arr, b = pending.pop(rid)
+                    try:
+                        srv.wait(rid)
+                    except M.MbarError:
+                        pass
+                    lat.append(time.perf_counter() - t_arr)
+                    held -= b
+                    done += 1
+                    if block:
+                        return
+
+        for kind, K, Nk, seed in specs:
+            if rate:
+                t_next += rng.exponential(1.0 / rate)
+                while time.perf_counter() < t_next:
+                    reap(False)
+                    time.sleep(0.0005)
+            b = K * K * Nk * 8
+            if K * K * Nk * 12 > budget or b > input_cap:
+                rejected += 1
+                continue
+            while held + b > input_cap and pending:
+                reap(True)
+            t_arr = max(t_next, time.perf_counter()) if rate else time.perf_counter()
+            tg = time.perf_counter()
+            u, nk, phi = _gen_device(kind, K, Nk, seed)
+            torch.cuda.synchronize()
+            gen_s += time.perf_counter() - tg
+            try:
+                rid = srv.submit(u, nk, phi)
+            except M.MbarError:
+                rejected += 1
+                continue
+            pending[rid] = (t_arr if rate else tg, b)
+            held += b
+            del u, phi
+        while pending:
+            reap(True)
+        elapsed = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        return {"completed": done, "rejected": rejected, "elapsed_s": elapsed, "gen_s": gen_s,
+                "solves_per_s": done / elapsed, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "peak_running": st["peak_running"],
+                "peak_bytes": st["peak_bytes"]}
+
+    sat = run(None)
+    log(f"[bench] serve saturation: {sat}")
+    loads = {}
+    for frac in args.loads:
+        loads[str(frac)] = run(frac * sat["solves_per_s"])
+        log(f"[bench] serve load {frac}: {loads[str(frac)]}")
+    line = {"metric": "MBAR solves/sec (served); p50/p99 latency", "value": sat["solves_per_s"], "unit": "solves/s",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": sat["elapsed_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: K log-uniform [4,1024], N_k~U{100..20000}, harmonic/umbrella, inputs drawn "
+                                   "on the device at arrival, mixed precision", "requests": R,
+                       "workers": args.workers, "budget_gb": args.budget_gb, "input_window_gb": args.wave_gb},
+            "saturation": sat, "poisson": loads}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """Largest per-rank time (ms): the job's time is set by its slowest rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, ms_total: float) -> float:
+    """Solves per second of the whole job: every rank solves `steps` problems
+    of its own (replicas), all within the max-over-ranks time."""
+    return world * steps / (ms_total / 1e3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="alchemical", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="alchemical", choices=list(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -279,7 +464,19 @@ def main():
     ap.add_argument("--lse-dtype", default="float32", choices=["float32", "float64"])
     ap.add_argument("--hess-only", action="store_true",
                     help="time mbar_hessian (one fused LSE pass + the tensor-core Hessian) on a random K x n problem")
+    ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
+    ap.add_argument("--loads", type=lambda t: [float(x) for x in t.split(",")], default=[0.5, 0.9],
+                    help="serve: Poisson arrival rates as fractions of the measured capacity")
+    ap.add_argument("--workers", type=int, default=16, help="batch/serve: concurrent solves")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="batch/serve: device memory budget of the server")
+    ap.add_argument("--wave-gb", type=float, default=90.0, help="batch/serve: FP64 input memory held at once")
+    ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
+    if args.workload == "batch":
+        return batch_bench(args)
+    if args.workload == "serve":
+        return serve_bench(args)
     if args.lse_only:
         return lse_only(args)
     if args.hess_only:
@@ -392,16 +589,12 @@ def main():
         e1.record(stream)
         barrier()
     launches = M.kernel_launches() - launches0
-    ms_total = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_per_step = ms_total / args.steps
     lat = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps))
     latency = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                "min_ms": lat[0], "max_ms": lat[-1], "samples": len(lat)}
-    value = world * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(world, args.steps, ms_total)
     clocks = clk.summary()
 
     # ---- end to end: host buffers through the C ABI ----
@@ -416,12 +609,8 @@ def main():
             step(host.numpy(), phi_host.numpy() if phi_host is not None else None)
         e1.record(stream)
         barrier()
-        ms_e2e = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": world * args.steps / (ms_e2e / 1e3), "unit": "solves/s",
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        e2e = {"value": whole_job_rate(world, args.steps, ms_e2e), "unit": "solves/s",
                "h2d_bytes_per_step": hbytes, "d2h_bytes_per_step": prob["K"] * 8}
 
     # ---- accuracy of the timed solve against the FP64 GPU path (outside timing) ----

@@ -223,8 +223,9 @@ BUMBAR_API mbar_status mbar_get_trace(mbar_ctx* ctx, int64_t* rows, double* out,
 
 /* Process-wide choice of the Hessian contraction: 0 = by size (tensor
  * cores, FP16 operands / FP32 accumulation, for K >= 64; CUDA cores, FP32,
- * below), 1 = always CUDA cores, 2 = always tensor cores. For testing and
- * tuning; EINVAL for other values. */
+ * below), 1 = always CUDA cores, 2 = always tensor cores, 3 = tensor cores
+ * without the thread-block-cluster kernel (which otherwise serves FP32 data
+ * with K <= 512). For testing and tuning; EINVAL for other values. */
 BUMBAR_API mbar_status mbar_set_hessian_path(int32_t path);
 
 /* Number of CUDA kernels this library has launched in this process. */
@@ -285,6 +286,82 @@ BUMBAR_API size_t mbar_lse_static_scratch_bytes(void);
 BUMBAR_API mbar_status mbar_lse_pass_static(const void* v, int32_t dtype_bytes, int64_t K, int64_t n, int64_t ld,
                                             const double* f, const double* log_N, const int32_t* H, double* Q,
                                             void* logden, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Serving and batching. These layer on mbar_ctx: every request is solved by
+ * its own context (mbar_create, mbar_set_coordinate, mbar_solve,
+ * mbar_free_energies, mbar_destroy) on one of the server's worker threads,
+ * each with its own CUDA stream, so requests that are admitted together
+ * run concurrently on the GPU. A request's kernels, launch shapes and
+ * reduction orders depend only on its own K, N and options: its result is
+ * the same alone and in any mix.
+ *
+ * Admission (continuous batching): queued requests are admitted in arrival
+ * order while a worker is free and the request's device footprint
+ * (mbar_footprint_bytes) fits in what the admitted requests leave of
+ * hbm_budget_bytes; a request that does not fit yet is passed over by later
+ * ones, at most 4 x workers times, after which admission waits for it.
+ * ------------------------------------------------------------------- */
+typedef struct mbar_server mbar_server;
+
+typedef struct {
+  int32_t workers;           /* concurrent solves, 1..256 */
+  int32_t pad;
+  uint64_t hbm_budget_bytes; /* device memory the admitted requests may hold together */
+  mbar_opts opts;            /* options of every solve */
+} mbar_server_config;
+
+/* Estimated peak device memory of one solve from host u (creation with an
+ * FP64 staging copy of u, the stored data, Algorithm 1's binned levels,
+ * reorder buffer, per-sample vectors and the Hessian). 0 for K < 1 or N < 1.
+ * The server charges requests whose u is in device memory without the
+ * staging copy. */
+BUMBAR_API uint64_t mbar_footprint_bytes(int64_t K, int64_t N, int32_t precision, int32_t use_binning);
+
+/* Starts `cfg->workers` worker threads on the current device.
+ * EINVAL for a bad configuration, ENOMEM if the threads cannot start. */
+BUMBAR_API mbar_status mbar_server_create(mbar_server** out, const mbar_server_config* cfg);
+
+/* Queues one solve (arguments as mbar_create / mbar_set_coordinate; phi
+ * nullable => row 0 of u). N_k is copied now; u_kn and phi (host or
+ * device) are read when the request is admitted and must stay valid until
+ * mbar_server_wait has returned for it. *id receives the request id.
+ * EUNSUPPORTED if the footprint exceeds the whole budget (it could never be
+ * admitted) or K > 1024; ESTATE while the server shuts down. */
+BUMBAR_API mbar_status mbar_server_submit(mbar_server* server, int64_t K, int64_t N, const int64_t* N_k,
+                                          const double* u_kn, int32_t u_on_device, const double* phi,
+                                          int32_t phi_on_device, int64_t* id);
+
+/* Non-blocking state of a request: 0 queued, 1 admitted/running, 2 done. */
+BUMBAR_API mbar_status mbar_server_poll(mbar_server* server, int64_t id, int32_t* state);
+
+/* Blocks until request `id` is done and releases its record. f_out
+ * (host[K], nullable) receives the free energies (f_0 = 0), report
+ * (nullable) the solve's report, latency_s (nullable) the seconds from
+ * submit to completion, run_s (nullable) from admission to completion.
+ * Returns the request's own status (e.g. ENOTCONV, with f still copied). */
+BUMBAR_API mbar_status mbar_server_wait(mbar_server* server, int64_t id, double* f_out, mbar_report* report,
+                                        double* latency_s, double* run_s);
+
+/* Counters since creation: completed requests, the largest number of
+ * requests admitted at once, and the largest sum of their footprints. */
+BUMBAR_API mbar_status mbar_server_stats(mbar_server* server, int64_t* completed, int32_t* peak_running,
+                                         uint64_t* peak_bytes);
+
+/* Stops the server: running requests finish, queued ones are dropped (their
+ * waiters get ESTATE). mbar_server_destroy(NULL) is MBAR_OK. */
+BUMBAR_API mbar_status mbar_server_destroy(mbar_server* server);
+
+/* P independent solves through a temporary server with configuration cfg:
+ * problem p has K[p] states, N[p] samples, counts N_k[p], energies u_kn[p]
+ * (all host, or all device with u_on_device) and coordinate phi[p] (phi
+ * nullable, or entries nullable). f_out[p] (host[K[p]]) receives its free
+ * energies, reports[p] / statuses[p] (nullable arrays) its report and
+ * status. Returns the first failing status, MBAR_OK if all succeeded. */
+BUMBAR_API mbar_status mbar_batch_solve(int32_t P, const int64_t* K, const int64_t* N, const int64_t* const* N_k,
+                                        const double* const* u_kn, int32_t u_on_device, const double* const* phi,
+                                        int32_t phi_on_device, const mbar_server_config* cfg, double* const* f_out,
+                                        mbar_report* reports, mbar_status* statuses);
 
 #ifdef __cplusplus
 }

@@ -5,10 +5,12 @@
 // Algorithm 1 (s < eps, 2 s_next > inc s_n, the break rule) and of the
 // Newton safeguard from values the kernels leave in device memory.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <unordered_map>
 #include <vector>
@@ -306,111 +308,13 @@ mbar_status count_at(mbar_ctx* c, const double* ws, int nw, int64_t* g) {
   return MBAR_OK;
 }
 
-// Width rule w*(n) by the deterministic search; *found = false when n cannot
-// be reached (the caller then uses the unbinned data). The bisection is the
-// sequential one, evaluated four levels at a time: one counting pass gets
-// g at all 15 midpoints of the next four levels of the bisection tree, then
-// the host walks the path the sequential search would take.
-mbar_status width_search_impl(mbar_ctx* c, int64_t n, double* w_out, bool* found);
+mbar_status width_search_multi(mbar_ctx* c, const int64_t* n, int count, double* w_out, bool* found);
 
+// Width rule w*(n) by the deterministic search (width_search_multi with one
+// target); *found = false when n cannot be reached (the caller then uses the
+// unbinned data).
 mbar_status width_search(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
-  const double t0 = now_s();
-  const mbar_status s = width_search_impl(c, n, w_out, found);
-  c->t_width += now_s() - t0;
-  return s;
-}
-
-mbar_status width_search_impl(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
-  BUMBAR_TRY(ensure_sorted(c));
-  const double R = c->phi_hi - c->phi_lo;
-  *found = true;
-  if (n <= 1 || R == 0.0) {
-    *w_out = R > 0.0 ? 2.0 * R : 1.0;
-    return MBAR_OK;
-  }
-  double w_hi = 2.0 * R;
-  double w_lo = R / static_cast<double>(n);
-  for (;;) {
-    if (R / w_lo > kMaxIndex) {
-      *found = false;
-      return MBAR_OK;
-    }
-    int64_t g = 0;
-    BUMBAR_TRY(count_at(c, &w_lo, 1, &g));
-    if (g >= n) break;
-    w_hi = w_lo;
-    w_lo = w_lo * 0.5;
-  }
-  constexpr int kLevels = 4;  // 2^4 - 1 = 15 midpoints per pass
-  int steps = 0;
-  bool stop = false;
-  while (!stop && steps < 64) {
-    double mid[16], a[16], b[16];
-    a[1] = w_lo;
-    b[1] = w_hi;
-    for (int node = 1; node < 16; ++node) {
-      mid[node] = std::sqrt(a[node] * b[node]);
-      if (2 * node < 16) {
-        a[2 * node] = a[node];
-        b[2 * node] = mid[node];
-        a[2 * node + 1] = mid[node];
-        b[2 * node + 1] = b[node];
-      }
-    }
-    int64_t g[16];
-    BUMBAR_TRY(count_at(c, mid + 1, 15, g + 1));
-    int node = 1;
-    for (int d = 0; d < kLevels && steps < 64; ++d) {
-      const double m = mid[node];
-      if (!(w_lo < m && m < w_hi)) {
-        stop = true;
-        break;
-      }
-      ++steps;
-      if (g[node] >= n) {
-        w_lo = m;
-        node = 2 * node + 1;
-      } else {
-        w_hi = m;
-        node = 2 * node;
-      }
-    }
-  }
-  *w_out = w_lo;
-  return MBAR_OK;
-}
-
-// Level `idx` of the schedule of Algorithm 1 (n0 * inc^idx bins, or width
-// h0 / inc^idx); unbinned when the schedule runs past the data.
-mbar_status schedule_level(mbar_ctx* c, int idx, Level* L) {
-  *L = Level{};
-  const mbar_opts& o = c->opts;
-  BUMBAR_TRY(ensure_sorted(c));
-  const double R = c->phi_hi - c->phi_lo;
-  if (o.h0 > 0.0) {
-    const double w = o.h0 / std::pow(static_cast<double>(o.inc), idx);
-    if (R / w > kMaxIndex) {
-      *L = c->full;
-      return MBAR_OK;
-    }
-    return make_level_w(c, w, L);
-  }
-  double nt = static_cast<double>(o.n0) * std::pow(static_cast<double>(o.inc), idx);
-  if (nt > static_cast<double>(c->N) * 4.0) {  // far past the data: unbinned
-    *L = c->full;
-    return MBAR_OK;
-  }
-  const int64_t n_target = static_cast<int64_t>(nt);
-  double w = 0.0;
-  bool found = false;
-  BUMBAR_TRY(width_search(c, n_target, &w, &found));
-  if (!found) {
-    *L = c->full;
-    return MBAR_OK;
-  }
-  BUMBAR_TRY(make_level_w(c, w, L));
-  L->n_sched = n_target;
-  return MBAR_OK;
+  return width_search_multi(c, &n, 1, w_out, found);
 }
 
 mbar_status set_coordinate_dev(mbar_ctx* c, const double* phi_orig) {
@@ -650,24 +554,328 @@ mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
   return MBAR_OK;
 }
 
+// The width rule for several bin counts at once. Each search is the
+// sequential procedure of width_search (halving, then at most 64 geometric
+// bisections); one counting pass serves all of them: a halving search
+// contributes its current width, a bisecting one the midpoints of the next
+// d levels of its bisection tree, the 15 widths of a pass shared out so that
+// d is as large as the share allows. Results are those of the sequential
+// searches, one by one.
+struct WidthSearch {
+  int64_t n = 0;
+  double w_lo = 0.0, w_hi = 0.0;
+  int phase = 0;  // 0 halving, 1 bisecting, 2 done
+  bool found = true;
+  int steps = 0;
+};
+
+mbar_status width_search_multi(mbar_ctx* c, const int64_t* n, int count, double* w_out, bool* found) {
+  const double t0 = now_s();
+  BUMBAR_TRY(ensure_sorted(c));
+  const double R = c->phi_hi - c->phi_lo;
+  std::vector<WidthSearch> ss(count);
+  for (int i = 0; i < count; ++i) {
+    WidthSearch& q = ss[i];
+    q.n = n[i];
+    if (n[i] <= 1 || R == 0.0) {
+      q.phase = 2;
+      q.w_lo = R > 0.0 ? 2.0 * R : 1.0;
+      continue;
+    }
+    q.w_hi = 2.0 * R;
+    q.w_lo = R / static_cast<double>(n[i]);
+  }
+  for (;;) {
+    // halving searches first: one width each (or done when out of range)
+    std::vector<int> halving, bisecting;
+    for (int i = 0; i < count; ++i) {
+      WidthSearch& q = ss[i];
+      if (q.phase == 0 && R / q.w_lo > kMaxIndex) {
+        q.phase = 2;
+        q.found = false;
+      }
+      if (q.phase == 0) halving.push_back(i);
+      if (q.phase == 1) bisecting.push_back(i);
+    }
+    if (halving.empty() && bisecting.empty()) break;
+    double ws[kWidthsPerPass];
+    int nw = 0;
+    std::vector<int> first(count, 0), depth(count, 0);
+    for (int i : halving) {
+      if (nw == kWidthsPerPass) break;
+      first[i] = nw;
+      depth[i] = 1;
+      ws[nw++] = ss[i].w_lo;
+    }
+    // bisection trees: the deepest d with 2^d - 1 widths within the share
+    const int left = kWidthsPerPass - nw;
+    const int nb = static_cast<int>(bisecting.size());
+    std::vector<std::array<double, 16>> mids(count);
+    for (int j = 0; j < nb && nw < kWidthsPerPass; ++j) {
+      const int i = bisecting[j];
+      const int share = left / nb + (j < left % nb ? 1 : 0);
+      int d = 0;
+      while (d < 4 && (1 << (d + 1)) - 1 <= share) ++d;
+      if (d == 0) continue;  // no room this pass
+      double a[16], b[16];
+      auto& mid = mids[i];
+      a[1] = ss[i].w_lo;
+      b[1] = ss[i].w_hi;
+      const int nodes = (1 << d) - 1;
+      for (int node = 1; node <= nodes; ++node) {
+        mid[node] = std::sqrt(a[node] * b[node]);
+        if (2 * node <= nodes) {
+          a[2 * node] = a[node];
+          b[2 * node] = mid[node];
+          a[2 * node + 1] = mid[node];
+          b[2 * node + 1] = b[node];
+        }
+      }
+      first[i] = nw;
+      depth[i] = d;
+      for (int node = 1; node <= nodes; ++node) ws[nw++] = mid[node];
+    }
+    int64_t g[kWidthsPerPass];
+    BUMBAR_TRY(count_at(c, ws, nw, g));
+    for (int i : halving) {
+      if (depth[i] == 0) continue;
+      WidthSearch& q = ss[i];
+      if (g[first[i]] >= q.n) {
+        q.phase = 1;
+      } else {
+        q.w_hi = q.w_lo;
+        q.w_lo = q.w_lo * 0.5;
+      }
+    }
+    for (int i : bisecting) {
+      if (depth[i] == 0) continue;
+      WidthSearch& q = ss[i];
+      const auto& mid = mids[i];
+      int node = 1;
+      for (int lev = 0; lev < depth[i] && q.steps < 64; ++lev) {
+        const double m = mid[node];
+        if (!(q.w_lo < m && m < q.w_hi)) {
+          q.phase = 2;
+          break;
+        }
+        ++q.steps;
+        if (g[first[i] + node - 1] >= q.n) {
+          q.w_lo = m;
+          node = 2 * node + 1;
+        } else {
+          q.w_hi = m;
+          node = 2 * node;
+        }
+      }
+      if (q.steps >= 64) q.phase = 2;
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    w_out[i] = ss[i].w_lo;
+    found[i] = ss[i].found;
+  }
+  c->t_width += now_s() - t0;
+  return MBAR_OK;
+}
+
+// Width (or unbinned) of level `idx` of Algorithm 1's schedule without
+// building it: n0 * inc^idx bins by the width rule, or width h0 / inc^idx.
+mbar_status plan_level(mbar_ctx* c, int idx, bool* binned, double* w, int64_t* n_sched) {
+  const mbar_opts& o = c->opts;
+  *binned = false;
+  BUMBAR_TRY(ensure_sorted(c));
+  const double R = c->phi_hi - c->phi_lo;
+  if (o.h0 > 0.0) {
+    const double ww = o.h0 / std::pow(static_cast<double>(o.inc), idx);
+    if (R / ww > kMaxIndex) return MBAR_OK;
+    *binned = true;
+    *w = ww;
+    *n_sched = -1;  // the histogram's size
+    return MBAR_OK;
+  }
+  const double nt = static_cast<double>(o.n0) * std::pow(static_cast<double>(o.inc), idx);
+  if (nt > static_cast<double>(c->N) * 4.0) return MBAR_OK;  // far past the data: unbinned
+  const int64_t n_target = static_cast<int64_t>(nt);
+  bool found = false;
+  BUMBAR_TRY(width_search(c, n_target, w, &found));
+  if (!found) return MBAR_OK;
+  *binned = true;
+  *n_sched = n_target;
+  return MBAR_OK;
+}
+
+// Every level Algorithm 1 can visit, built up front: the histograms one by
+// one (each needs only the sorted coordinate), then all bin means in one read
+// of the data. Level 0 and 1 always; level 2 when level 1 is binned; level
+// j + 1 (j >= 2) when level j is binned and 2 inc n_j <= N -- the levels the
+// second loop would build as it goes. An unbinned entry ends the list.
+mbar_status prebuild_levels(mbar_ctx* c, std::vector<Level>* levels) {
+  const mbar_opts& o = c->opts;
+  const int64_t N = c->N, K = c->K;
+  std::vector<int32_t*> segs, starts;
+  void* tmp = nullptr;
+  int64_t* keys_full = nullptr;
+  int32_t* H_full = nullptr;
+  const size_t htmp = hist_tmp_bytes(N);
+  auto cleanup = [&]() {
+    for (auto* q : segs) dfree(c, q);
+    for (auto* q : starts) dfree(c, q);
+    dfree(c, tmp);
+    dfree(c, keys_full);
+    dfree(c, H_full);
+  };
+  auto fail = [&](mbar_status s) {
+    cleanup();
+    for (auto& L : *levels) level_free(c, &L);
+    levels->clear();
+    return s;
+  };
+  mbar_status s = dalloc(c, &tmp, htmp);
+  if (s == MBAR_OK) s = dalloc_t(c, &keys_full, N);
+  if (s == MBAR_OK) s = dalloc_t(c, &H_full, N);
+  if (s != MBAR_OK) return fail(s);
+  // bin-count schedule: the targets are known, so all width searches run
+  // together; the list stops where the second loop would stop building
+  std::vector<double> wpre;
+  std::vector<bool> fpre;
+  std::vector<int64_t> npre;
+  if (o.h0 <= 0.0) {
+    s = ensure_sorted(c);
+    if (s != MBAR_OK) return fail(s);
+    for (int idx = 0; idx < kMaxBinLevels; ++idx) {
+      const double nt = static_cast<double>(o.n0) * std::pow(static_cast<double>(o.inc), idx);
+      if (nt > static_cast<double>(N) * 4.0) break;
+      npre.push_back(static_cast<int64_t>(nt));
+      if (!(idx < 2 || 2.0 * o.inc * nt <= static_cast<double>(N))) break;
+    }
+    wpre.resize(npre.size());
+    std::unique_ptr<bool[]> fb(new bool[npre.size() + 1]);
+    if (!npre.empty()) {
+      s = width_search_multi(c, npre.data(), static_cast<int>(npre.size()), wpre.data(), fb.get());
+      if (s != MBAR_OK) return fail(s);
+    }
+    for (size_t i = 0; i < npre.size(); ++i) fpre.push_back(fb[i]);
+  }
+  for (int idx = 0; idx < kMaxBinLevels; ++idx) {
+    bool binned = false;
+    double w = 0.0;
+    int64_t n_sched = 0;
+    if (o.h0 > 0.0) {
+      s = plan_level(c, idx, &binned, &w, &n_sched);
+      if (s != MBAR_OK) return fail(s);
+    } else if (idx < static_cast<int>(npre.size())) {
+      binned = fpre[idx];
+      w = wpre[idx];
+      n_sched = npre[idx];
+    }
+    if (!binned) {
+      levels->push_back(c->full);
+      break;
+    }
+    const double t0 = now_s();
+    int32_t *seg = nullptr, *start = nullptr;
+    s = dalloc_t(c, &seg, N);
+    if (s == MBAR_OK) {
+      segs.push_back(seg);
+      s = dalloc_t(c, &start, N + 1);
+    }
+    if (s == MBAR_OK) {
+      starts.push_back(start);
+      s = build_histogram(c->d_pairs, c->d_sorted, N, w, seg, start, H_full, keys_full, c->nb_dev, tmp, htmp, c->st);
+    }
+    int32_t nb = 0;
+    if (s == MBAR_OK) {
+      cudaError_t e = cudaMemcpyAsync(&nb, c->nb_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+      if (e != cudaSuccess) s = cuda_status(e, "histogram size");
+    }
+    Level L;
+    if (s == MBAR_OK) {
+      L.binned = true;
+      L.n = nb;
+      L.ld = round_up(nb, 32);
+      L.w = w;
+      L.n_sched = n_sched >= 0 ? n_sched : nb;
+      s = dalloc(c, &L.v, static_cast<size_t>(K) * L.ld * c->dtype);
+    }
+    if (s == MBAR_OK) s = dalloc_t(c, &L.H, nb);
+    if (s == MBAR_OK) s = dalloc_t(c, &L.keys, nb);
+    if (s == MBAR_OK) {
+      cudaError_t e = cudaMemcpyAsync(L.H, H_full, nb * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(L.keys, keys_full, nb * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st);
+      if (e != cudaSuccess) s = cuda_status(e, "histogram copy");
+    }
+    if (s == MBAR_OK) s = level_tmap(c, &L);
+    c->t_levels += now_s() - t0;
+    if (s != MBAR_OK) {
+      level_free(c, &L);
+      return fail(s);
+    }
+    levels->push_back(L);
+    const bool more = idx < 2 || 2.0 * o.inc * static_cast<double>(L.n_sched) <= static_cast<double>(N);
+    if (!more) break;
+  }
+  // all bin means in one read of the data (up to kMaxBinLevels per call)
+  const double t0 = now_s();
+  std::vector<const int32_t*> sg, stt;
+  std::vector<int64_t> nbs, lds;
+  std::vector<void*> outs;
+  for (size_t i = 0; i < segs.size(); ++i) {
+    sg.push_back(segs[i]);
+    stt.push_back(starts[i]);
+    nbs.push_back((*levels)[i].n);
+    outs.push_back((*levels)[i].v);
+    lds.push_back((*levels)[i].ld);
+  }
+  const int L = static_cast<int>(sg.size());
+  if (L > 0) {
+    void* mt = nullptr;
+    const size_t mbytes = bin_means_multi_tmp_bytes(K, N, L, nbs.data());
+    s = dalloc(c, &mt, mbytes);
+    if (s == MBAR_OK)
+      s = bin_means_multi(c->v, c->dtype, K, N, c->ld, L, sg.data(), stt.data(), nbs.data(), outs.data(), lds.data(),
+                          mt, mbytes, c->st);
+    dfree(c, mt);
+    if (s != MBAR_OK) return fail(s);
+  }
+  c->t_levels += now_s() - t0;
+  cleanup();
+  return MBAR_OK;
+}
+
 mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   const mbar_opts& o = c->opts;
-  Level L0;
-  BUMBAR_TRY(schedule_level(c, 0, &L0));
+  std::vector<Level> levels;
+  BUMBAR_TRY(prebuild_levels(c, &levels));
+  // level idx of the schedule; ownership passes to the caller
+  auto take = [&](int idx) -> Level {
+    if (idx < static_cast<int>(levels.size())) {
+      Level L = levels[idx];
+      levels[idx] = c->full;
+      return L;
+    }
+    return c->full;
+  };
+  auto free_rest = [&]() {
+    for (auto& L : levels) level_free(c, &L);
+  };
+  Level L0 = take(0);
   rep->n_rebins += L0.binned ? 1 : 0;
   mbar_status s = first_loop(c, L0, rep);
   level_free(c, &L0);
-  BUMBAR_TRY(s);
-  int idx = 1;
-  Level cur, nxt;
-  BUMBAR_TRY(schedule_level(c, idx, &cur));
-  rep->n_rebins += cur.binned ? 1 : 0;
-  if (!cur.binned) return MBAR_OK;
-  s = schedule_level(c, idx + 1, &nxt);
   if (s != MBAR_OK) {
-    level_free(c, &cur);
+    free_rest();
     return s;
   }
+  int idx = 1;
+  Level cur = take(idx), nxt;
+  rep->n_rebins += cur.binned ? 1 : 0;
+  if (!cur.binned) {
+    free_rest();
+    return MBAR_OK;
+  }
+  nxt = take(idx + 1);
   rep->n_rebins += nxt.binned ? 1 : 0;
   const int64_t N = c->N;
   const int64_t K = c->K;
@@ -720,8 +928,8 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
       nxt = Level{};
       idx++;
       if (!cur.binned || 2.0 * o.inc * static_cast<double>(cur.n_sched) > static_cast<double>(N)) break;
-      s = schedule_level(c, idx + 1, &nxt);
-      if (s == MBAR_OK) rep->n_rebins += nxt.binned ? 1 : 0;
+      nxt = take(idx + 1);
+      rep->n_rebins += nxt.binned ? 1 : 0;
     } else {
       if (cudaMemcpyAsync(c->f, c->ft, K * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess) {
         s = MBAR_ECUDA;
@@ -733,6 +941,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   rep->final_bins = cur.binned ? cur.n : 0;
   level_free(c, &cur);
   level_free(c, &nxt);
+  free_rest();
   return s;
 }
 
@@ -997,7 +1206,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   // LSE scratch sized for the widest grid of this K
   {
     const LsePlan pl = lse_plan(K, N, c->dtype);
-    c->scratch_bytes = static_cast<size_t>(pl.grid) * K * sizeof(double) + 256;
+    c->scratch_bytes = lse_scratch_for_grid(K, pl.grid);
     TRYC(dalloc(c, &c->scratch, c->scratch_bytes));
     if (cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   }
@@ -1329,8 +1538,8 @@ mbar_status mbar_get_trace(mbar_ctx* c, int64_t* rows, double* out, int64_t capa
 }
 
 mbar_status mbar_set_hessian_path(int32_t path) {
-  if (path < 0 || path > 2) {
-    set_error("mbar_set_hessian_path: path must be 0, 1 or 2");
+  if (path < 0 || path > 3) {
+    set_error("mbar_set_hessian_path: path must be 0, 1, 2 or 3");
     return MBAR_EINVAL;
   }
   set_hessian_path(path);

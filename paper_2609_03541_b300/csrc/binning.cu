@@ -10,6 +10,7 @@
 // ordinals, run starts and counts. All integer work is exact; the bin index
 // uses the binary64 subtraction and division, each rounded to nearest
 // (__dsub_rn/__ddiv_rn; no contraction into FMA).
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -58,8 +59,31 @@ __device__ __forceinline__ long long key_df(float dh, float dl, const RecipW& r,
   const float fr = floorf(rr);
   const float frac = __fsub_rn(rr, fr);
   const float delta = 9.5367431640625e-07f + fabsf(p_hi) * 2.2737367544323206e-13f;  // 2^-20 + |q| 2^-42
-  if (frac > delta && frac < 1.0f - delta) return static_cast<long long>(fl) + static_cast<long long>(fr);
+  if (frac > delta && frac < 1.0f - delta) {
+    if (p_hi < 16777216.0f) return static_cast<long long>(__float2int_rz(__fadd_rn(fl, fr)));  // exact below 2^24
+    return static_cast<long long>(fl) + static_cast<long long>(fr);
+  }
   return static_cast<long long>(floor(__ddiv_rn(*d_exact, r.w)));
+}
+
+// key_df for q = d/w < 2^22 with no conversion instructions: adding 2^23
+// with rounding towards -inf leaves 2^23 + floor(p_hi) (float spacing is 1
+// in [2^23, 2^24)), whose low mantissa bits are the integer part; the
+// remainder (p_hi - floor(p_hi)) + t lies in (-1, 2), so its floor is one of
+// -1, 0, 1. Same decisions and the same fallback as key_df.
+__device__ __forceinline__ int key_small(float dh, float dl, const RecipW& r, const double* d_exact) {
+  const float p_hi = __fmul_rn(dh, r.hi);
+  const float p_err = __fmaf_rn(dh, r.hi, -p_hi);
+  const float t = __fadd_rn(__fadd_rn(__fmul_rn(dh, r.lo), __fmul_rn(dl, r.hi)), p_err);
+  const float m = __fadd_rd(p_hi, 8388608.0f);
+  const float fl = __fsub_rn(m, 8388608.0f);
+  const int ip = __float_as_int(m) - 0x4B000000;
+  const float rr = __fadd_rn(__fsub_rn(p_hi, fl), t);
+  const bool neg = rr < 0.f, big = rr >= 1.f;
+  const float frac = neg ? __fadd_rn(rr, 1.f) : (big ? __fsub_rn(rr, 1.f) : rr);
+  const float delta = 9.5367431640625e-07f + p_hi * 2.2737367544323206e-13f;  // 2^-20 + |q| 2^-42
+  if (frac > delta && frac < 1.0f - delta) return ip + (neg ? -1 : (big ? 1 : 0));
+  return static_cast<int>(floor(__ddiv_rn(*d_exact, r.w)));
 }
 
 // ---------------------------------------------------------------------------
@@ -237,40 +261,58 @@ struct WidthSet {
 };
 constexpr int kCountChunk = 16;
 
-__global__ void count_heads_multi(const float2* __restrict__ dhl, const double* __restrict__ d, int64_t N,
-                                  WidthSet ws, unsigned long long* __restrict__ counts) {
+__global__ void __launch_bounds__(kThreads) count_heads_multi(const float2* __restrict__ dhl,
+                                                               const double* __restrict__ d, int64_t N, WidthSet ws,
+                                                               unsigned long long* __restrict__ counts) {
   __shared__ unsigned int cnt[kMaxWidths];
   if (threadIdx.x < kMaxWidths) cnt[threadIdx.x] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kCountChunk;
   const int64_t i1 = (i0 + kCountChunk < N) ? i0 + kCountChunk : N;
-  for (int c = 0; c < ws.n; ++c) {
+  const int nv = i0 < N ? static_cast<int>(i1 - i0) : 0;
+  // the chunk (and the sample before it) in registers, loaded once for all widths
+  float2 x[kCountChunk];
+#pragma unroll
+  for (int j = 0; j < kCountChunk; ++j) x[j] = (j < nv) ? dhl[i0 + j] : make_float2(0.f, 0.f);
+  const float2 xp = (nv > 0 && i0 > 0) ? dhl[i0 - 1] : make_float2(0.f, 0.f);
+  const float2 xl = (nv > 0) ? dhl[i1 - 1] : make_float2(0.f, 0.f);
+  const float dmax = N > 0 ? dhl[N - 1].x : 0.f;  // largest offset (sorted)
+  // heads of one chunk under width r, keys of type Key from key_fn
+  auto chunk_heads = [&](const RecipW& r, auto key_fn) -> unsigned int {
     unsigned int heads = 0;
-    if (i0 < N) {
-      const RecipW r = ws.r[c];
-      const float2 e = dhl[i1 - 1];
-      const long long kend = key_df(e.x, e.y, r, d + i1 - 1);
-      long long kprev;
-      if (i0 == 0) {
-        heads = 1;  // the first sample opens the first bin
-        const float2 s0 = dhl[0];
-        kprev = key_df(s0.x, s0.y, r, d);
-      } else {
-        const float2 sp = dhl[i0 - 1];
-        kprev = key_df(sp.x, sp.y, r, d + i0 - 1);
-      }
-      const long long diff = kend - kprev;
-      if (diff == 1) {
-        heads += 1;
-      } else if (diff > 1) {
-        for (int64_t i = (i0 == 0 ? 1 : i0); i < i1; ++i) {
-          const float2 x = dhl[i];
-          const long long k = key_df(x.x, x.y, r, d + i);
+    const auto kend = key_fn(xl, r, d + i1 - 1);
+    auto kprev = kend;
+    if (i0 == 0) {
+      heads = 1;  // the first sample opens the first bin
+      kprev = key_fn(x[0], r, d);
+    } else {
+      kprev = key_fn(xp, r, d + i0 - 1);
+    }
+    const auto diff = kend - kprev;
+    if (diff == 1) {
+      heads += 1;
+    } else if (diff > 1) {
+#pragma unroll
+      for (int j = 0; j < kCountChunk; ++j) {
+        if (j < nv && !(i0 == 0 && j == 0)) {
+          const auto k = key_fn(x[j], r, d + i0 + j);
           heads += (k != kprev) ? 1u : 0u;
           kprev = k;
         }
       }
+    }
+    return heads;
+  };
+  for (int c = 0; c < ws.n; ++c) {
+    unsigned int heads = 0;
+    if (nv > 0) {
+      const RecipW r = ws.r[c];
+      // every key of this width below 4e6 < 2^22 (margin for the rounding of dmax * hi)
+      if (__fmul_ru(dmax, r.hi) < 4.0e6f)
+        heads = chunk_heads(r, [](float2 v, const RecipW& rw, const double* de) { return key_small(v.x, v.y, rw, de); });
+      else
+        heads = chunk_heads(r, [](float2 v, const RecipW& rw, const double* de) { return key_df(v.x, v.y, rw, de); });
     }
     for (int o = 16; o >= 1; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
     if (lane == 0 && heads) atomicAdd(&cnt[c], heads);
@@ -335,20 +377,20 @@ __global__ void counts_from_starts(const int32_t* __restrict__ start, int64_t nb
 // ---------------------------------------------------------------------------
 // binned means: segmented sums over contiguous sorted columns
 // ---------------------------------------------------------------------------
-// A block owns a tile of 2048 sorted columns (256 threads x 8 consecutive
-// columns) for kRowsPerBlock rows. Per row, each thread splits its 8 values
-// into runs of equal bin ordinal; runs that start and end inside the thread
-// are written at once; the last run of each thread enters a block-wide
-// segmented inclusive scan (FP64) that carries it across thread boundaries.
-// A bin whose run ends in a thread is finished there: written if the bin
-// started in this tile, else its partial goes to carry0[tile] (a bin that
-// began in an earlier tile). The last thread's still-open run goes to
+// Each warp owns a tile of 256 sorted columns (32 lanes x 8 consecutive
+// columns) and walks a range of rows, with no block-level synchronisation.
+// Per row, a lane splits its 8 values into runs of equal bin ordinal; runs
+// that start and end inside the lane are written at once; the last run of
+// each lane enters a warp-wide segmented inclusive scan that carries it
+// across lanes. A bin whose run ends in a lane is finished there: written if
+// the bin started in this tile, else its partial goes to carry0[tile] (a bin
+// that began in an earlier tile). The last lane's still-open run goes to
 // carry1[tile] (a bin that starts in this tile and continues) or, if it
 // began before the tile, to carry0[tile]. A fix-up kernel finishes bins that
 // span tiles: sum = carry1[first tile] + carry0[later tiles], in order.
 constexpr int kBmCols = 8;
-constexpr int kBmTile = kThreads * kBmCols;  // 2048
-constexpr int kRowsPerBlock = 4;
+constexpr int kBmTile = 32 * kBmCols;  // columns per warp tile (256)
+constexpr int kBmRowsPerBlock = 64;    // rows a block walks for its eight warp tiles
 
 // Accumulation type of the segmented sums: FP32 for FP32 data (the binned
 // matrix only steers Algorithm 1; the answer comes from the unbinned data,
@@ -363,6 +405,14 @@ template <>
 struct Acc<double> {
   using type = double;
 };
+
+// Mean of a run of `len` (1..7) columns that lies inside one lane: FP32
+// division, or for FP64 the product with 1/len (as 1 / count elsewhere).
+__device__ __forceinline__ float run_mean(float sum, int len) { return sum / static_cast<float>(len); }
+__device__ __forceinline__ double run_mean(double sum, int len) {
+  const double r = len == 1 ? 1.0 : len == 2 ? 0.5 : len == 4 ? 0.25 : 1.0 / static_cast<double>(len);
+  return sum * r;
+}
 
 template <typename T, typename A>
 __device__ __forceinline__ void load8(const T* src, int nvalid, A* x) {
@@ -397,17 +447,16 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
                                                            int64_t ld_out, double* __restrict__ carry0,
                                                            double* __restrict__ carry1, int64_t ntiles) {
   using A = typename Acc<T>::type;
-  __shared__ A wv[kThreads / 32];
-  __shared__ int wf[kThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + warp;
+  if (tile >= ntiles) return;  // whole warp
   const int64_t tile0 = tile * kBmTile;
   const int64_t tile_end = (tile0 + kBmTile < N) ? tile0 + kBmTile : N;
-  const int64_t c0 = tile0 + static_cast<int64_t>(tid) * kBmCols;
+  const int64_t c0 = tile0 + static_cast<int64_t>(lane) * kBmCols;
   const int nvalid = static_cast<int>(c0 < N ? ((N - c0) < kBmCols ? (N - c0) : kBmCols) : 0);
-  const bool last_thread = nvalid > 0 && c0 + nvalid == tile_end;
+  const bool last_lane = nvalid > 0 && c0 + nvalid == tile_end;
 
-  // run structure of this thread's columns (identical for every row)
+  // run structure of this lane's columns (identical for every row)
   int sg[kBmCols];
 #pragma unroll
   for (int j = 0; j < kBmCols; ++j) sg[j] = (j < nvalid) ? seg[c0 + j] : -1;
@@ -420,19 +469,24 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
   const int64_t st_b0 = nvalid > 0 ? start[b0] : 0;
   const int64_t st_bl = nvalid > 0 ? start[bl] : 0;
   const int64_t en_bl = nvalid > 0 ? start[bl + 1] : 0;
-  const bool flag = nvalid <= 0 || nruns > 0 || st_bl >= c0;  // last run starts in this thread
+  const bool flag = nvalid <= 0 || nruns > 0 || st_bl >= c0;  // last run starts in this lane
   const bool cont = nvalid > 0 && st_b0 < c0;                 // first run continues from the left
   const bool last_ends_here = nvalid > 0 && en_bl <= c0 + nvalid;
   const A inv_b0 = nvalid > 0 ? static_cast<A>(inv_count[b0]) : A(0);
   const A inv_bl = nvalid > 0 ? static_cast<A>(inv_count[bl]) : A(0);
 
-  const int64_t k_begin = static_cast<int64_t>(blockIdx.y) * kRowsPerBlock;
-  for (int64_t k = k_begin; k < K && k < k_begin + kRowsPerBlock; ++k) {
+  const int64_t k_begin = static_cast<int64_t>(blockIdx.y) * kBmRowsPerBlock;
+  const int64_t k_end = (k_begin + kBmRowsPerBlock < K) ? k_begin + kBmRowsPerBlock : K;
+  A xn[kBmCols];  // next row, loaded one row ahead
+  if (k_begin < k_end) load8<T, A>(v + k_begin * ld + c0, nvalid, xn);
+  for (int64_t k = k_begin; k < k_end; ++k) {
     A x[kBmCols];
-    load8<T, A>(v + k * ld + c0, nvalid, x);
-    // local runs
+#pragma unroll
+    for (int j = 0; j < kBmCols; ++j) x[j] = xn[j];
+    if (k + 1 < k_end) load8<T, A>(v + (k + 1) * ld + c0, nvalid, xn);
     A head = A(0), run = A(0);
     int cur = b0;
+    int rs = 0;  // column where the current run starts
     bool first = true;
 #pragma unroll
     for (int j = 0; j < kBmCols; ++j) {
@@ -441,16 +495,17 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
           if (first) {
             head = run;
             first = false;
-          } else {  // interior run: starts and ends inside this thread
-            out[k * ld_out + cur] = static_cast<T>(run * static_cast<A>(inv_count[cur]));
+          } else {  // interior run: the whole bin lies in this lane, its count is the run length
+            out[k * ld_out + cur] = static_cast<T>(run_mean(run, j - rs));
           }
           cur = sg[j];
+          rs = j;
           run = A(0);
         }
         run += x[j];
       }
     }
-    // block-wide segmented inclusive scan of the last-run sums
+    // warp-wide segmented inclusive scan of the last-run sums
     A sv = nvalid > 0 ? run : A(0);
     int sf = flag ? 1 : 0;
 #pragma unroll
@@ -462,37 +517,181 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
         sf |= uf;
       }
     }
-    if (lane == 31) {
-      wv[warp] = sv;
-      wf[warp] = sf;
-    }
-    __syncthreads();
-    A pv = A(0);  // segmented prefix of all earlier warps
-    for (int w = 0; w < warp; ++w) pv = wf[w] ? wv[w] : pv + wv[w];
-    if (!sf) sv += pv;
     A prev = __shfl_up_sync(0xffffffffu, sv, 1);
-    if (lane == 0) prev = pv;
-    if (tid == 0) prev = A(0);
-    __syncthreads();
+    if (lane == 0) prev = A(0);
     if (nvalid > 0) {
       const A carry_in = cont ? prev : A(0);
-      if (nruns > 0) {  // the first run ends inside this thread
+      if (nruns > 0) {  // the first run ends inside this lane
         const A tot = carry_in + head;
         if (st_b0 >= tile0)
           out[k * ld_out + b0] = static_cast<T>(tot * inv_b0);
         else
-          carry0[k * ntiles + tile] = static_cast<double>(tot);
+          carry0[tile * K + k] = static_cast<double>(tot);
       }
       if (last_ends_here) {
         if (st_bl >= tile0)
           out[k * ld_out + bl] = static_cast<T>(sv * inv_bl);
         else
-          carry0[k * ntiles + tile] = static_cast<double>(sv);
-      } else if (last_thread) {
+          carry0[tile * K + k] = static_cast<double>(sv);
+      } else if (last_lane) {
         if (st_bl >= tile0)
-          carry1[k * ntiles + tile] = static_cast<double>(sv);
+          carry1[tile * K + k] = static_cast<double>(sv);
         else
-          carry0[k * ntiles + tile] = static_cast<double>(sv);
+          carry0[tile * K + k] = static_cast<double>(sv);
+      }
+    }
+  }
+}
+
+// All levels of a schedule in one read of v: the warp-tile scheme of
+// bin_sums_block, repeated per level on the same eight values of each lane.
+// Bins are consecutive along the sorted columns, so a lane's runs are bins
+// b0, b0 + 1, ...; per level a lane keeps only b0, a bit set of run starts
+// and a few flags (row independent), and the inverse counts of its first
+// and last bin.
+constexpr int kMaxLevels = 8;
+struct LevelOut {
+  const int32_t* seg;
+  const int32_t* start;
+  const double* inv;
+  void* out;
+  int64_t ld_out;
+  double* carry0;
+  double* carry1;
+};
+struct MultiLevel {
+  LevelOut l[kMaxLevels];
+  int L;
+};
+
+// descriptor bits: 0..7 run starts at column j (j >= 1); 8 last run starts in
+// this lane; 9 first run continues from the left; 10 last run ends in this
+// lane; 11 first bin starts in this tile; 12 last bin starts in this tile;
+// 16..19 number of run starts
+template <typename T, int NL>
+__global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__ v, int64_t K, int64_t N, int64_t ld,
+                                                           MultiLevel ml, int64_t ntiles) {
+  using A = typename Acc<T>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + warp;
+  if (tile >= ntiles) return;  // whole warp
+  const int64_t tile0 = tile * kBmTile;
+  const int64_t tile_end = (tile0 + kBmTile < N) ? tile0 + kBmTile : N;
+  const int64_t c0 = tile0 + static_cast<int64_t>(lane) * kBmCols;
+  const int nvalid = static_cast<int>(c0 < N ? ((N - c0) < kBmCols ? (N - c0) : kBmCols) : 0);
+  const bool last_lane = nvalid > 0 && c0 + nvalid == tile_end;
+
+  int b0[NL];
+  unsigned bits[NL];
+  A inv0[NL], invl[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    b0[l] = 0;
+    bits[l] = 0;
+    inv0[l] = invl[l] = A(0);
+    if (nvalid > 0) {
+      const int32_t* seg = ml.l[l].seg;
+      const int32_t* start = ml.l[l].start;
+      const int first = seg[c0];
+      int prev = first, nr = 0;
+      unsigned b = 0;
+#pragma unroll
+      for (int j = 1; j < kBmCols; ++j) {
+        if (j < nvalid) {
+          const int sj = seg[c0 + j];
+          if (sj != prev) {
+            b |= 1u << j;
+            ++nr;
+          }
+          prev = sj;
+        }
+      }
+      const int last = prev;
+      const int64_t st0 = start[first], stl = start[last], enl = start[last + 1];
+      if (nr > 0 || stl >= c0) b |= 1u << 8;
+      if (st0 < c0) b |= 1u << 9;
+      if (enl <= c0 + nvalid) b |= 1u << 10;
+      if (st0 >= tile0) b |= 1u << 11;
+      if (stl >= tile0) b |= 1u << 12;
+      b |= static_cast<unsigned>(nr) << 16;
+      b0[l] = first;
+      bits[l] = b;
+      inv0[l] = static_cast<A>(ml.l[l].inv[first]);
+      invl[l] = static_cast<A>(ml.l[l].inv[last]);
+    } else {
+      bits[l] = 1u << 8;  // past the end: empty segment head
+    }
+  }
+
+  const int64_t k_begin = static_cast<int64_t>(blockIdx.y) * kBmRowsPerBlock;
+  const int64_t k_end = (k_begin + kBmRowsPerBlock < K) ? k_begin + kBmRowsPerBlock : K;
+  A xn[kBmCols];
+  if (k_begin < k_end) load8<T, A>(v + k_begin * ld + c0, nvalid, xn);
+  for (int64_t k = k_begin; k < k_end; ++k) {
+    A x[kBmCols];
+#pragma unroll
+    for (int j = 0; j < kBmCols; ++j) x[j] = xn[j];
+    if (k + 1 < k_end) load8<T, A>(v + (k + 1) * ld + c0, nvalid, xn);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const unsigned b = bits[l];
+      T* out = static_cast<T*>(ml.l[l].out) + k * ml.l[l].ld_out;
+      A head = A(0), run = A(0);
+      int cur = b0[l];
+      int rs = 0;  // column where the current run starts
+      bool first = true;
+#pragma unroll
+      for (int j = 0; j < kBmCols; ++j) {
+        if (j < nvalid) {
+          if (b & (1u << j)) {
+            if (first) {
+              head = run;
+              first = false;
+            } else {  // interior run: the whole bin lies in this lane, its count is the run length
+              out[cur] = static_cast<T>(run_mean(run, j - rs));
+            }
+            ++cur;
+            rs = j;
+            run = A(0);
+          }
+          run += x[j];
+        }
+      }
+      A sv = nvalid > 0 ? run : A(0);
+      int sf = (b >> 8) & 1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const A uv = __shfl_up_sync(0xffffffffu, sv, o);
+        const int uf = __shfl_up_sync(0xffffffffu, sf, o);
+        if (lane >= o) {
+          if (!sf) sv += uv;
+          sf |= uf;
+        }
+      }
+      A prev = __shfl_up_sync(0xffffffffu, sv, 1);
+      if (lane == 0) prev = A(0);
+      if (nvalid > 0) {
+        const int nruns = static_cast<int>((b >> 16) & 15u);
+        double* carry0 = ml.l[l].carry0 + tile * K + k;
+        if (nruns > 0) {  // the first run ends inside this lane
+          const A tot = (((b >> 9) & 1) ? prev : A(0)) + head;
+          if ((b >> 11) & 1)
+            out[b0[l]] = static_cast<T>(tot * inv0[l]);
+          else
+            *carry0 = static_cast<double>(tot);
+        }
+        const int bl = b0[l] + nruns;
+        if ((b >> 10) & 1) {
+          if ((b >> 12) & 1)
+            out[bl] = static_cast<T>(sv * invl[l]);
+          else
+            *carry0 = static_cast<double>(sv);
+        } else if (last_lane) {
+          if ((b >> 12) & 1)
+            ml.l[l].carry1[tile * K + k] = static_cast<double>(sv);
+          else
+            *carry0 = static_cast<double>(sv);
+        }
       }
     }
   }
@@ -503,18 +702,36 @@ __global__ void inverse_counts(const int32_t* __restrict__ start, int64_t nb, do
   if (b < nb) inv[b] = 1.0 / static_cast<double>(start[b + 1] - start[b]);
 }
 
+// Bins that span tiles. A bin crosses the first column of tile t (t >= 1)
+// and began in tile t - 1 for exactly the spanning bins, each once. One warp
+// per (such t, chunk of 32 rows), one row per lane: carry1[t - 1] plus the
+// carry0 of every later tile the bin covers, in tile order. Carries are
+// stored tile-major ([tile][K]), so each step reads 32 consecutive rows.
+constexpr int kFixWarps = kThreads / 32;
 template <typename T>
-__global__ void bin_sums_fixup(int64_t K, int64_t nb, const int32_t* __restrict__ start,
+__global__ void bin_sums_fixup(int64_t K, const int32_t* __restrict__ seg, const int32_t* __restrict__ start,
                                const double* __restrict__ inv_count, T* __restrict__ out, int64_t ld_out,
                                const double* __restrict__ carry0, const double* __restrict__ carry1, int64_t ntiles) {
-  const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t k = blockIdx.y;
-  if (b >= nb) return;
-  const int64_t s = start[b], e = start[b + 1];
-  const int64_t ts = s / kBmTile, te = (e - 1) / kBmTile;
-  if (ts == te) return;  // finished inside one tile
-  double sum = carry1[k * ntiles + ts];
-  for (int64_t t = ts + 1; t <= te; ++t) sum += carry0[k * ntiles + t];
+  const int lane = threadIdx.x & 31;
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * kFixWarps + (threadIdx.x >> 5) + 1;
+  if (t >= ntiles) return;
+  const int64_t c = t * kBmTile;
+  const int b = seg[c];
+  const int64_t s = start[b];
+  if (s >= c || s < c - kBmTile) return;
+  const int64_t k = static_cast<int64_t>(blockIdx.y) * 32 + lane;
+  if (k >= K) return;
+  const int64_t te = (static_cast<int64_t>(start[b + 1]) - 1) / kBmTile;
+  double sum = carry1[(t - 1) * K + k];
+  int64_t u = t;
+  for (; u + 8 <= te + 1; u += 8) {  // eight loads in flight, added in order
+    double x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = carry0[(u + j) * K + k];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sum += x[j];
+  }
+  for (; u <= te; ++u) sum += carry0[u * K + k];
   out[k * ld_out + b] = static_cast<T>(sum * inv_count[b]);
 }
 
@@ -655,6 +872,81 @@ mbar_status build_histogram(const float2* d_pairs, const double* d_sorted, int64
   return MBAR_OK;
 }
 
+size_t bin_means_multi_tmp_bytes(int64_t K, int64_t N, int L, const int64_t* nb) {
+  const int64_t ntiles = ceil_div(N, kBmTile);
+  size_t b = 0;
+  for (int l = 0; l < L; ++l) b += round_up(K * ntiles * 8, 256) * 2 + round_up(nb[l] * 8, 256);
+  return b;
+}
+
+mbar_status bin_means_multi(const void* v, int dtype_bytes, int64_t K, int64_t N, int64_t ld, int L,
+                            const int32_t* const* seg, const int32_t* const* start, const int64_t* nb,
+                            void* const* out, const int64_t* ld_out, void* tmp, size_t tmp_bytes, cudaStream_t st) {
+  if (L < 1 || L > kMaxLevels) {
+    set_error("bin_means_multi: 1..%d levels", kMaxLevels);
+    return MBAR_EINVAL;
+  }
+  if (tmp_bytes < bin_means_multi_tmp_bytes(K, N, L, nb)) {
+    set_error("bin_means_multi: scratch too small");
+    return MBAR_EINVAL;
+  }
+  const int64_t ntiles = ceil_div(N, kBmTile);
+  MultiLevel ml{};
+  ml.L = L;
+  unsigned char* q = static_cast<unsigned char*>(tmp);
+  for (int l = 0; l < L; ++l) {
+    LevelOut& o = ml.l[l];
+    o.seg = seg[l];
+    o.start = start[l];
+    o.out = out[l];
+    o.ld_out = ld_out[l];
+    o.carry0 = reinterpret_cast<double*>(q);
+    q += round_up(K * ntiles * 8, 256);
+    o.carry1 = reinterpret_cast<double*>(q);
+    q += round_up(K * ntiles * 8, 256);
+    double* inv = reinterpret_cast<double*>(q);
+    q += round_up(nb[l] * 8, 256);
+    o.inv = inv;
+    inverse_counts<<<static_cast<unsigned>(ceil_div(nb[l], kThreads)), kThreads, 0, st>>>(start[l], nb[l], inv);
+    count_launches(1);
+  }
+  const dim3 g1(static_cast<unsigned>(ceil_div(ntiles, kThreads / 32)),
+                static_cast<unsigned>(ceil_div(K, kBmRowsPerBlock)));
+  const dim3 g2(static_cast<unsigned>(std::max<int64_t>(1, ceil_div(ntiles - 1, kFixWarps))),
+                static_cast<unsigned>(ceil_div(K, 32)));
+  auto launch = [&](auto tag) {
+    using T = decltype(tag);
+    const T* vv = static_cast<const T*>(v);
+    switch (L) {
+      case 1: bin_sums_multi<T, 1><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+      case 2: bin_sums_multi<T, 2><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+      case 3: bin_sums_multi<T, 3><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+      case 4: bin_sums_multi<T, 4><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+      case 5: bin_sums_multi<T, 5><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+      case 6: bin_sums_multi<T, 6><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+      case 7: bin_sums_multi<T, 7><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+      default: bin_sums_multi<T, 8><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
+    }
+  };
+  if (dtype_bytes == 4)
+    launch(float{});
+  else
+    launch(double{});
+  count_launches(1);
+  for (int l = 0; l < L; ++l) {
+    const LevelOut& o = ml.l[l];
+    if (dtype_bytes == 4)
+      bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, o.seg, o.start, o.inv, static_cast<float*>(o.out), o.ld_out,
+                                                     o.carry0, o.carry1, ntiles);
+    else
+      bin_sums_fixup<double><<<g2, kThreads, 0, st>>>(K, o.seg, o.start, o.inv, static_cast<double*>(o.out),
+                                                      o.ld_out, o.carry0, o.carry1, ntiles);
+    count_launches(1);
+  }
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
 size_t bin_means_tmp_bytes(int64_t K, int64_t N) {
   const int64_t ntiles = ceil_div(N, kBmTile);
   return round_up(K * ntiles * 8, 256) * 2 + round_up(N * 8, 256);
@@ -673,20 +965,21 @@ mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int6
   double* inv = carry1 + round_up(K * ntiles, 32);
   inverse_counts<<<static_cast<unsigned>(ceil_div(nb, kThreads)), kThreads, 0, st>>>(start, nb, inv);
   count_launches(1);
-  const dim3 g1(static_cast<unsigned>(ntiles), static_cast<unsigned>(ceil_div(K, kRowsPerBlock)));
-  const dim3 g2(static_cast<unsigned>(ceil_div(nb, kThreads)), static_cast<unsigned>(K));
+  const dim3 g1(static_cast<unsigned>(ceil_div(ntiles, kThreads / 32)), static_cast<unsigned>(ceil_div(K, kBmRowsPerBlock)));
+  const dim3 g2(static_cast<unsigned>(std::max<int64_t>(1, ceil_div(ntiles - 1, kFixWarps))),
+                static_cast<unsigned>(ceil_div(K, 32)));
   if (dtype_bytes == 4) {
     bin_sums_block<float><<<g1, kThreads, 0, st>>>(static_cast<const float*>(v), K, N, ld, seg, start, inv,
                                                    static_cast<float*>(out), ld_out, carry0, carry1, ntiles);
     count_launches(1);
-    bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, nb, start, inv, static_cast<float*>(out), ld_out, carry0,
+    bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, seg, start, inv, static_cast<float*>(out), ld_out, carry0,
                                                    carry1, ntiles);
     count_launches(1);
   } else {
     bin_sums_block<double><<<g1, kThreads, 0, st>>>(static_cast<const double*>(v), K, N, ld, seg, start, inv,
                                                     static_cast<double*>(out), ld_out, carry0, carry1, ntiles);
     count_launches(1);
-    bin_sums_fixup<double><<<g2, kThreads, 0, st>>>(K, nb, start, inv, static_cast<double*>(out), ld_out, carry0,
+    bin_sums_fixup<double><<<g2, kThreads, 0, st>>>(K, seg, start, inv, static_cast<double*>(out), ld_out, carry0,
                                                     carry1, ntiles);
     count_launches(1);
   }

@@ -57,14 +57,24 @@ __global__ void trsm_panel(double* __restrict__ A, int64_t m, int64_t kb, int nb
   }
   __syncthreads();
   const int64_t i = kb + nb + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  __shared__ double rdiag[NB];
+  if (threadIdx.x < NB) rdiag[threadIdx.x] = threadIdx.x < nb ? 1.0 / L[threadIdx.x][threadIdx.x] : 0.0;
+  __syncthreads();
   if (i >= m) return;
   double y[NB];
-  for (int j = 0; j < nb; ++j) {
-    double s = A[i * m + kb + j];
-    for (int l = 0; l < j; ++l) s -= y[l] * L[j][l];
-    y[j] = s / L[j][j];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) y[j] = j < nb ? A[i * m + kb + j] : 0.0;  // independent loads first
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < nb) {
+      double s = y[j];
+      for (int l = 0; l < j; ++l) s -= y[l] * L[j][l];
+      y[j] = s * rdiag[j];
+    }
   }
-  for (int j = 0; j < nb; ++j) A[i * m + kb + j] = y[j];
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    if (j < nb) A[i * m + kb + j] = y[j];
 }
 
 __global__ void syrk_update(double* __restrict__ A, int64_t m, int64_t kb, int nb) {
@@ -93,18 +103,27 @@ __global__ void syrk_update(double* __restrict__ A, int64_t m, int64_t kb, int n
 __global__ void __launch_bounds__(1024) chol_solve(const double* __restrict__ A, int64_t m, double* __restrict__ b,
                                                    double* __restrict__ delta) {
   __shared__ double xs[NB];
+  __shared__ double D[NB][NB + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // forward: L y = b
   for (int64_t j0 = 0; j0 < m; j0 += NB) {
     const int nb = static_cast<int>(m - j0 < NB ? m - j0 : NB);
     __syncthreads();
+    // the diagonal block, loaded by all threads (no load latency in the
+    // recurrence below)
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      const int r = e / NB, cc = e % NB;
+      D[r][cc] = (r < nb && cc < nb) ? A[(j0 + r) * m + j0 + cc] : 0.0;
+    }
+    __syncthreads();
     if (warp == 0) {
       double rhs = lane < nb ? b[j0 + lane] : 0.0;
       double y = 0.0;
+      const double rd = lane < nb ? 1.0 / D[lane][lane] : 0.0;
       for (int j = 0; j < nb; ++j) {
-        const double yj = __shfl_sync(0xffffffffu, rhs, j) / A[(j0 + j) * m + j0 + j];
+        const double yj = __shfl_sync(0xffffffffu, rhs * rd, j);
         if (lane == j) y = yj;
-        if (lane > j && lane < nb) rhs -= A[(j0 + lane) * m + j0 + j] * yj;
+        if (lane > j && lane < nb) rhs -= D[lane][j] * yj;
       }
       if (lane < nb) {
         xs[lane] = y;
@@ -123,13 +142,19 @@ __global__ void __launch_bounds__(1024) chol_solve(const double* __restrict__ A,
     const int64_t j0 = j1 - NB > 0 ? j1 - NB : 0;
     const int nb = static_cast<int>(j1 - j0);
     __syncthreads();
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      const int r = e / NB, cc = e % NB;
+      D[r][cc] = (r < nb && cc < nb) ? A[(j0 + r) * m + j0 + cc] : 0.0;
+    }
+    __syncthreads();
     if (warp == 0) {
       double rhs = lane < nb ? b[j0 + lane] : 0.0;
       double x = 0.0;
+      const double rd = lane < nb ? 1.0 / D[lane][lane] : 0.0;
       for (int j = nb - 1; j >= 0; --j) {
-        const double xj = __shfl_sync(0xffffffffu, rhs, j) / A[(j0 + j) * m + j0 + j];
+        const double xj = __shfl_sync(0xffffffffu, rhs * rd, j);
         if (lane == j) x = xj;
-        if (lane < j) rhs -= A[(j0 + j) * m + j0 + lane] * xj;
+        if (lane < j) rhs -= D[j][lane] * xj;
       }
       if (lane < nb) {
         xs[lane] = x;

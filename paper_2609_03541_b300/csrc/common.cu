@@ -32,14 +32,18 @@ void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed);
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 int num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   return sms;
+}
+
+std::recursive_mutex& init_mutex() {
+  static std::recursive_mutex m;
+  return m;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {

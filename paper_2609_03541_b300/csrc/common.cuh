@@ -1,6 +1,8 @@
 // Shared device/host helpers of the BU-MBAR library (sm_103a).
 #pragma once
 
+#include <mutex>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -37,6 +39,9 @@ inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
 int num_sms();
 
 // Process-wide count of kernels launched by this library.
+// Guards the one-time caches (occupancy, shared-memory limits, plans) that
+// concurrent solves on several host threads may fill at the same time.
+std::recursive_mutex& init_mutex();
 void count_launches(int n);
 int64_t launches_so_far();
 

@@ -149,8 +149,10 @@ static int g_hessian_path = 0;
 void set_hessian_path(int path) { g_hessian_path = path; }
 int hessian_path_for(int64_t K) {
   if (g_hessian_path == 1 || g_hessian_path == 2) return g_hessian_path;
+  if (g_hessian_path == 3) return 2;
   return K >= 64 ? 2 : 1;
 }
+bool tc_cluster_enabled() { return g_hessian_path != 3; }
 
 struct SimtPlan {
   int nt, npairs, nslices;

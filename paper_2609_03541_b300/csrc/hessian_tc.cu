@@ -40,6 +40,9 @@ constexpr int kMaxRows = 640;                  // A tile + 4 B tiles
 constexpr int kStageBytes = kMaxRows * 128;    // 80 KB per buffer
 constexpr int kMaxCtas = 1024;
 constexpr uint32_t kMaxSpins = 1u << 28;
+#ifndef TC_ROWS_PER_ROUND
+#define TC_ROWS_PER_ROUND 4
+#endif
 
 struct TcCta {
   int item;     // work item index
@@ -173,6 +176,60 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
   const T* ld_in = static_cast<const T*>(p.logden);
   bool failed = false;
 
+  // Each thread handles rows rsub + kRowStride * m, m = 0, 1, ..., in rounds
+  // of kRowsPerRound rows; the loads of the next round (next chunk after
+  // the last round) are issued before the exponentials of the current one.
+  constexpr int kRowsPerRound = TC_ROWS_PER_ROUND;
+  const int nrounds = (rows + kRowStride * kRowsPerRound - 1) / (kRowStride * kRowsPerRound);
+  auto load_cols = [&](int64_t c, float* l2, float* sh) {
+    const int64_t col0 = job.c_begin + c * kChunkCols + g * 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t col = col0 + j;
+      if (col < job.c_end) {
+        l2[j] = static_cast<float>(ld_in[col]) * kLog2e;
+        sh[j] = p.H ? sqrtf(static_cast<float>(p.H[col])) : 1.f;
+      } else {
+        l2[j] = INFINITY;  // exp2(-inf) = 0: padding samples contribute nothing
+        sh[j] = 0.f;
+      }
+    }
+  };
+  auto load_round = [&](int64_t c, int r, float (*x)[8]) {
+    const int64_t col0 = job.c_begin + c * kChunkCols + g * 8;
+    const bool full8 = col0 + 8 <= job.c_end;
+#pragma unroll
+    for (int u = 0; u < kRowsPerRound; ++u) {
+      const int lr = rsub + kRowStride * (r * kRowsPerRound + u);
+      const int row = lr < rowsA ? job.bi * 128 + lr : job.bj0 * 128 + (lr - rowsA);
+      if (lr < rows && row < p.K) {
+        const T* src = vv + static_cast<int64_t>(row) * p.ld + col0;
+        if constexpr (sizeof(T) == 4) {
+          if (full8) {
+            const float4 v0 = *reinterpret_cast<const float4*>(src);
+            const float4 v1 = *reinterpret_cast<const float4*>(src + 4);
+            x[u][0] = v0.x; x[u][1] = v0.y; x[u][2] = v0.z; x[u][3] = v0.w;
+            x[u][4] = v1.x; x[u][5] = v1.y; x[u][6] = v1.z; x[u][7] = v1.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[u][j] = (col0 + j < job.c_end) ? src[j] : 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[u][j] = (col0 + j < job.c_end) ? static_cast<float>(src[j]) : 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[u][j] = 0.f;
+      }
+    }
+  };
+
+  float xn[kRowsPerRound][8], l2n[8], shn[8];
+  if (nchunks > 0) {
+    load_cols(0, l2n, shn);
+    load_round(0, 0, xn);
+  }
   for (int64_t c = 0; c < nchunks; ++c) {
     const int b = static_cast<int>(c & 1);
     unsigned char* buf = buf0 + b * kStageBytes;
@@ -183,53 +240,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) overlap_tc_kernel(TcParams p) {
         break;
       }
     }
-    // per-thread column parameters (8 consecutive samples)
-    const int64_t col0 = job.c_begin + c * kChunkCols + g * 8;
     float l2[8], sh[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int64_t col = col0 + j;
-      if (col < job.c_end) {
-        l2[j] = static_cast<float>(static_cast<double>(ld_in[col]) * 1.4426950408889634);
-        sh[j] = p.H ? sqrtf(static_cast<float>(p.H[col])) : 1.f;
-      } else {
-        l2[j] = INFINITY;  // exp2(-inf) = 0: padding samples contribute nothing
-        sh[j] = 0.f;
-      }
+      l2[j] = l2n[j];
+      sh[j] = shn[j];
     }
-    const bool full8 = col0 + 8 <= job.c_end;
-    // four rows per round: issue all loads first, then the SFU work
-    constexpr int kRowsPerRound = 4;
-    for (int lr0 = rsub; lr0 < rows; lr0 += kRowStride * kRowsPerRound) {
+    for (int r = 0; r < nrounds; ++r) {
       float x[kRowsPerRound][8];
 #pragma unroll
-      for (int u = 0; u < kRowsPerRound; ++u) {
-        const int lr = lr0 + kRowStride * u;
-        const int row = lr < rowsA ? job.bi * 128 + lr : job.bj0 * 128 + (lr - rowsA);
-        if (lr < rows && row < p.K) {
-          const T* src = vv + static_cast<int64_t>(row) * p.ld + col0;
-          if constexpr (sizeof(T) == 4) {
-            if (full8) {
-              const float4 v0 = *reinterpret_cast<const float4*>(src);
-              const float4 v1 = *reinterpret_cast<const float4*>(src + 4);
-              x[u][0] = v0.x; x[u][1] = v0.y; x[u][2] = v0.z; x[u][3] = v0.w;
-              x[u][4] = v1.x; x[u][5] = v1.y; x[u][6] = v1.z; x[u][7] = v1.w;
-            } else {
+      for (int u = 0; u < kRowsPerRound; ++u)
 #pragma unroll
-              for (int j = 0; j < 8; ++j) x[u][j] = (col0 + j < job.c_end) ? src[j] : 0.f;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[u][j] = (col0 + j < job.c_end) ? static_cast<float>(src[j]) : 0.f;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) x[u][j] = 0.f;
-        }
+        for (int j = 0; j < 8; ++j) x[u][j] = xn[u][j];
+      if (r + 1 < nrounds) {
+        load_round(c, r + 1, xn);
+      } else if (c + 1 < nchunks) {
+        load_cols(c + 1, l2n, shn);
+        load_round(c + 1, 0, xn);
       }
 #pragma unroll
       for (int u = 0; u < kRowsPerRound; ++u) {
-        const int lr = lr0 + kRowStride * u;
+        const int lr = rsub + kRowStride * (r * kRowsPerRound + u);
         if (lr < rows) {
           const float a2 = a2_s[lr];
           float pv[8];
@@ -323,6 +354,355 @@ __global__ void reduce_tc(const float* __restrict__ part, const TcCta* __restric
   G[static_cast<int64_t>(col) * K + row] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Cluster variant for K <= 512 (FP32 data): one cluster of MT = ceil(K/128)
+// CTAs per slice of samples. CTA r of a cluster builds P~ only for its own
+// 128-row tile r -- every exponential is evaluated once -- and stores the
+// FP16 tile into its own shared memory and into the shared memory of the
+// peer CTAs that use it as a B operand (distributed shared memory). CTA r
+// accumulates the tiles (r, (r + d) mod MT), d = 0 .. dmax(r), which cover
+// the upper triangle of G exactly once (a circulant assignment: at most
+// three 128 x 128 FP32 accumulators per CTA, within the 512 TMEM columns).
+//
+// Per 64-sample chunk: TMA brings the CTA's 128 x 64 FP32 block of v into a
+// three-stage ring (vfull barriers); all threads wait until every reader of
+// the previous use of the P~ stage has finished its MMAs (pempty, arrived
+// by tcgen05.commit multicast to the writers), build and distribute P~, and
+// thread 0 then signals the readers' pfull barriers (remote arrive,
+// release at cluster scope), waits for its own pfull (all writers done) and
+// issues the MMAs. Every wait is bounded; a CTA that gives up records an
+// error and still reaches the final cluster barrier.
+constexpr int kClThreads = 512;
+constexpr int kClVStages = 3;
+constexpr int kClVStageBytes = 128 * 64 * 4;  // two 32-column 128B-swizzled boxes
+constexpr int kClPSlots = 3;
+constexpr int kClPSlotBytes = 128 * 128;      // one FP16 128 x 64 tile
+constexpr int kClPStageBytes = kClPSlots * kClPSlotBytes;
+constexpr int kClMaxTiles = 4;                // MT <= 4, i.e. K <= 512
+
+__host__ __device__ inline int cl_dmax(int q, int MT) {
+  return (MT - 1) / 2 + ((MT % 2 == 0 && q < MT / 2) ? 1 : 0);
+}
+__host__ __device__ inline int cl_tile_base(int q, int MT) {
+  int t = 0;
+  for (int i = 0; i < q; ++i) t += cl_dmax(i, MT) + 1;
+  return t;
+}
+
+struct ClParams {
+  int K;
+  int MT;
+  int T;          // accumulator tiles per cluster
+  int64_t n;
+  int64_t per;    // samples per slice (multiple of 64)
+  const double* a;
+  const float* logden;
+  const int32_t* H;
+  float* out;     // [slices][T][128][128]
+  unsigned* err;
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t o;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(o) : "r"(addr), "r"(rank));
+  return o;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits bounded in time as well as in polls: gives up after about one second
+// (every legitimate wait of this kernel lasts microseconds).
+constexpr uint64_t kClWaitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, uint32_t max_spins) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < max_spins; ++i) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if ((i & 255u) == 255u && global_ns() - t0 > kClWaitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, uint32_t parity, uint32_t max_spins) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < max_spins; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u && global_ns() - t0 > kClWaitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void umma_commit_multicast(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kClThreads, 1)
+    overlap_tc_cluster_kernel(const __grid_constant__ CUtensorMap tmap, ClParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* vbuf = smem;
+  unsigned char* pbuf = smem + kClVStages * kClVStageBytes;
+  uint64_t* vfull = reinterpret_cast<uint64_t*>(pbuf + 2 * kClPStageBytes);  // [3]
+  uint64_t* pfull = vfull + kClVStages;                                        // [2]
+  uint64_t* pempty = pfull + 2;                                                // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pempty + 2);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int MT = p.MT;
+  const int r = static_cast<int>(cluster_ctarank());
+  const int64_t slice = blockIdx.x / MT;
+  const int dm = cl_dmax(r, MT);
+  const int ntl = dm + 1;
+  const uint32_t ncols = ntl == 1 ? 128u : (ntl == 2 ? 256u : 512u);
+  // readers of tile r: CTAs q that use it (slot (r - q) mod MT there)
+  uint32_t reader_mask = 0;
+  for (int q = 0; q < MT; ++q)
+    if ((r - q + MT) % MT <= cl_dmax(q, MT)) reader_mask |= 1u << q;
+  const int nreaders = __popc(reader_mask);
+  uint16_t writer_mask = 0;  // CTAs whose tiles this CTA uses
+  for (int d = 0; d <= dm; ++d) writer_mask |= static_cast<uint16_t>(1u << ((r + d) % MT));
+  const int64_t c_begin = slice * p.per;
+  const int64_t c_end = (c_begin + p.per < p.n) ? c_begin + p.per : p.n;
+  const int64_t nchunks = c_end > c_begin ? (c_end - c_begin + 63) / 64 : 0;
+
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  if (tid == 0) {
+    for (int s = 0; s < kClVStages; ++s) mbar_init(&vfull[s], 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&pfull[b], static_cast<uint32_t>(dm + 1));
+      mbar_init(&pempty[b], static_cast<uint32_t>(nreaders));
+    }
+    fence_barrier_init();
+    prefetch_tmap(&tmap);
+  }
+  // this thread's rows (lr0, lr0 + 64) of tile r and 8-sample group g
+  const int g = tid & 7;
+  const int lr0 = tid >> 3;
+  float a2r[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int row = r * 128 + lr0 + 64 * u;
+    a2r[u] = row < p.K ? static_cast<float>(p.a[row] * 1.4426950408889634) : -INFINITY;
+  }
+  tc_fence_before();
+  cluster_sync_all();  // barrier initialisation visible to the peers
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto issue_v = [&](int64_t c) {
+    const int s = static_cast<int>(c % kClVStages);
+    unsigned char* dst = vbuf + s * kClVStageBytes;
+    const int col = static_cast<int>(c_begin + c * 64);
+    mbar_expect_tx(&vfull[s], kClVStageBytes);
+    tma_load_2d(dst, &tmap, &vfull[s], col, r * 128);
+    tma_load_2d(dst + kClVStageBytes / 2, &tmap, &vfull[s], col + 32, r * 128);
+  };
+  int64_t issued = 0;
+  if (tid == 0) {
+    for (int64_t c = 0; c < nchunks && c < kClVStages; ++c) issue_v(c);
+  }
+  issued = nchunks < kClVStages ? nchunks : kClVStages;
+
+  auto load_cols = [&](int64_t c, float* l2, float* sh) {
+    const int64_t col0 = c_begin + c * 64 + g * 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t col = col0 + j;
+      if (col < c_end) {
+        l2[j] = p.logden[col] * kLog2e;
+        sh[j] = p.H ? sqrtf(static_cast<float>(p.H[col])) : 1.f;
+      } else {
+        l2[j] = INFINITY;  // padding samples contribute nothing
+        sh[j] = 0.f;
+      }
+    }
+  };
+  float l2n[8], shn[8];
+  if (nchunks > 0) load_cols(0, l2n, shn);
+  constexpr uint32_t idesc = idesc_f16(128, 128);
+  bool failed = false;
+  bool t0_failed = false;  // thread 0 gave up on a pfull wait
+  int64_t c = 0;
+  for (; c < nchunks; ++c) {
+    const int s = static_cast<int>(c % kClVStages);
+    const int b = static_cast<int>(c & 1);
+    bool ok = mbar_wait_timed(&vfull[s], static_cast<uint32_t>((c / kClVStages) & 1), kMaxSpins);
+    if (ok && c >= 2) ok = mbar_wait_cluster_bounded(&pempty[b], static_cast<uint32_t>(((c - 2) >> 1) & 1), kMaxSpins);
+    if (__syncthreads_or(!ok || t0_failed)) {
+      failed = true;
+      break;
+    }
+    float l2[8], sh[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      l2[j] = l2n[j];
+      sh[j] = shn[j];
+    }
+    if (c + 1 < nchunks) load_cols(c + 1, l2n, shn);
+    const unsigned char* vb = vbuf + s * kClVStageBytes + (g >> 2) * (kClVStageBytes / 2);
+    unsigned char* pst = pbuf + b * kClPStageBytes;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int lr = lr0 + 64 * u;
+      const float4 x0 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2));
+      const float4 x1 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2 + 1));
+      const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      float pv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pv[j] = ex2_approx(fmaf(-x[j], kLog2e, a2r[u]) - l2[j]) * sh[j];
+      uint4 packed;
+      packed.x = pack_half2(pv[0], pv[1]);
+      packed.y = pack_half2(pv[2], pv[3]);
+      packed.z = pack_half2(pv[4], pv[5]);
+      packed.w = pack_half2(pv[6], pv[7]);
+      const uint32_t off = static_cast<uint32_t>(lr * 128 + ((g ^ (lr & 7)) << 4));
+#pragma unroll
+      for (int q = 0; q < kClMaxTiles; ++q) {
+        if (reader_mask & (1u << q)) {
+          const int slot = (r - q + MT) % MT;
+          if (q == r)
+            *reinterpret_cast<uint4*>(pst + off) = packed;  // own tile: slot 0
+          else
+            st_cluster_v4(mapa_shared(smem_u32(pst + slot * kClPSlotBytes) + off, static_cast<uint32_t>(q)),
+                          packed);
+        }
+      }
+    }
+    fence_proxy_async_all();
+    __syncthreads();
+    if (tid == 0) {
+      if (c + kClVStages < nchunks) {
+        issue_v(c + kClVStages);  // every thread is past its reads of this stage
+      }
+      for (int q = 0; q < MT; ++q)
+        if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
+      if (mbar_wait_cluster_bounded(&pfull[b], static_cast<uint32_t>((c >> 1) & 1), kMaxSpins)) {
+        tc_fence_after();
+        const uint32_t base = smem_u32(pst);
+        for (int t = 0; t < ntl; ++t) {
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)
+            umma_f16(tmem + static_cast<uint32_t>(t * 128), sdesc_sw128(base + k4 * 32),
+                     sdesc_sw128(base + static_cast<uint32_t>(t * kClPSlotBytes) + k4 * 32), idesc,
+                     (c > 0 || k4 > 0) ? 1u : 0u);
+        }
+        umma_commit_multicast(&pempty[b], writer_mask);
+      } else {
+        t0_failed = true;
+      }
+    }
+    if (c + kClVStages < nchunks) ++issued;
+  }
+  if (__syncthreads_or(t0_failed)) failed = true;
+  if (!failed && nchunks > 0) {
+    // the last commits of every reader of this tile (they include this CTA's)
+    bool ok = true;
+    for (int64_t last = nchunks - 1; last >= 0 && last >= nchunks - 2; --last)
+      ok = ok && mbar_wait_cluster_bounded(&pempty[last & 1], static_cast<uint32_t>((last >> 1) & 1), kMaxSpins);
+    if (__syncthreads_or(!ok)) failed = true;
+  }
+  if (failed) {
+    // let this CTA's own tensor copies in flight land before leaving
+    if (tid == 0) {
+      for (int64_t cc = c; cc < issued; ++cc)
+        mbar_wait_timed(&vfull[cc % kClVStages], static_cast<uint32_t>((cc / kClVStages) & 1), kMaxSpins);
+      atomicAdd(p.err, 1u);
+    }
+  }
+  tc_fence_after();
+
+  // epilogue: warp w reads TMEM lanes 32*(w%4) .. +31, the four warps of a
+  // lane quarter split the columns
+  float* out = p.out + (slice * p.T + cl_tile_base(r, MT)) * 128 * 128;
+  const int sub = warp & 3;
+  const int quarter = warp >> 2;
+  const int row_local = sub * 32 + lane;
+  for (int c0 = quarter * 32; c0 < ntl * 128; c0 += 128) {
+    float rr[32];
+    if (nchunks > 0 && !failed) {
+      tmem_ld32(tmem + (static_cast<uint32_t>(sub * 32) << 16) + static_cast<uint32_t>(c0), rr);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) rr[i] = 0.f;
+    }
+    float4* dst = reinterpret_cast<float4*>(out + (c0 >> 7) * 128 * 128 + row_local * 128 + (c0 & 127));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[i] = make_float4(rr[4 * i], rr[4 * i + 1], rr[4 * i + 2], rr[4 * i + 3]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // no peer touches this CTA's shared memory after this point
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+// Fixed-order FP64 sum of the slices of each accumulator tile; tile
+// (q, d) is G's block (q, (q + d) mod MT), mirrored into its transpose.
+__global__ void reduce_tc_cluster(const float* __restrict__ part, int S, int T, int MT, int K,
+                                  double* __restrict__ G) {
+  const int tile = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 128 * 128) return;
+  int q = 0, base = 0;
+  while (q + 1 < MT && base + cl_dmax(q, MT) + 1 <= tile) {
+    base += cl_dmax(q, MT) + 1;
+    ++q;
+  }
+  const int d = tile - base;
+  double s = 0.0;
+  for (int sl = 0; sl < S; ++sl) s += part[(static_cast<int64_t>(sl) * T + tile) * 128 * 128 + e];
+  const int row = q * 128 + e / 128;
+  const int col = ((q + d) % MT) * 128 + e % 128;
+  if (row >= K || col >= K) return;
+  if (d == 0 && col < row) return;  // diagonal tile: keep one of each pair
+  G[static_cast<int64_t>(row) * K + col] = s;
+  G[static_cast<int64_t>(col) * K + row] = s;
+}
+
+size_t tc_cluster_smem() {
+  return static_cast<size_t>(kClVStages) * kClVStageBytes + 2 * static_cast<size_t>(kClPStageBytes) + 64 + 1024;
+}
+
+struct ClPlan {
+  int MT = 0, T = 0, S = 0;
+  int64_t per = 0;
+};
+
 struct TcPlan {
   std::vector<TcCta> ctas;
   std::vector<int> first, count;  // CTAs of item i: first[i] + j * stride, j < count[i]
@@ -369,21 +749,128 @@ size_t tc_smem() {
 
 }  // namespace
 
+namespace {
+
+// Clusters of MT CTAs that can be resident at once (queried once per MT,
+// after the kernel's shared-memory limit is raised).
+int max_active_clusters(int MT) {
+  std::lock_guard<std::recursive_mutex> lock(init_mutex());
+  static int cache[kClMaxTiles + 1] = {0, 0, 0, 0, 0};
+  if (cache[MT] == 0) {
+    if (cudaFuncSetAttribute(overlap_tc_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(tc_cluster_smem())) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(MT * num_sms()));
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = tc_cluster_smem();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(MT);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, overlap_tc_cluster_kernel, &cfg) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = std::max(1, num_sms() / MT / 2);
+    }
+    cache[MT] = n;
+  }
+  return cache[MT];
+}
+
+bool cl_eligible(int dtype_bytes, int64_t K) { return dtype_bytes == 4 && K <= 128 * kClMaxTiles && tc_cluster_enabled(); }
+
+// Upper bound of the slices (clusters) of any cluster plan: no more
+// clusters than SMs / MT can be resident.
+ClPlan cl_plan(int64_t K, int64_t n, int clusters) {
+  ClPlan pl;
+  pl.MT = static_cast<int>(ceil_div(K, 128));
+  pl.T = cl_tile_base(pl.MT, pl.MT);
+  const int64_t nch = ceil_div(n, 64);
+  const int64_t S = std::max<int64_t>(1, std::min<int64_t>(clusters, nch));
+  pl.per = ceil_div(nch, S) * 64;
+  pl.S = static_cast<int>(ceil_div(n, pl.per));
+  return pl;
+}
+
+size_t cl_tmp_bytes(int64_t K) {
+  const int MT = static_cast<int>(ceil_div(K, 128));
+  const int T = cl_tile_base(MT, MT);
+  const int64_t Smax = std::max(1, num_sms() / MT);
+  return round_up(Smax * T * 128 * 128 * 4, 256);
+}
+
+}  // namespace
+
 size_t overlap_tc_tmp_bytes(int64_t K, int64_t n) {
   const TcPlan pl = tc_plan(K, n);
   const size_t nc = pl.ctas.size(), ni = pl.first.size();
-  return round_up(static_cast<int64_t>(nc) * 128 * 512 * 4, 256) + round_up(nc * sizeof(TcCta), 256) +
-         round_up(2 * ni * sizeof(int), 256) + 256;
+  const size_t items = round_up(static_cast<int64_t>(nc) * 128 * 512 * 4, 256) + round_up(nc * sizeof(TcCta), 256) +
+                       round_up(2 * ni * sizeof(int), 256) + 256;
+  return K <= 128 * kClMaxTiles ? std::max(items, cl_tmp_bytes(K)) : items;
+}
+
+static mbar_status overlap_tc_cluster(const void* v, int64_t K, int64_t n, int64_t ld, const double* a,
+                                      const void* logden, const int32_t* H, double* G, unsigned* err, void* tmp,
+                                      cudaStream_t st) {
+  const int MT = static_cast<int>(ceil_div(K, 128));
+  const int resident = max_active_clusters(MT);
+  if (resident <= 0) {
+    set_error("overlap_tc: cannot raise the shared-memory limit of the cluster kernel");
+    return MBAR_ECUDA;
+  }
+  const int clusters = std::min(resident, std::max(1, num_sms() / MT));
+  const ClPlan pl = cl_plan(K, n, clusters);
+  CUtensorMap map;
+  BUMBAR_TRY(make_tmap_2d(&map, v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, K, n, ld, 32, 128));
+  BUMBAR_CUDA(cudaMemsetAsync(G, 0, static_cast<size_t>(K) * K * sizeof(double), st));
+  ClParams prm{};
+  prm.K = static_cast<int>(K);
+  prm.MT = pl.MT;
+  prm.T = pl.T;
+  prm.n = n;
+  prm.per = pl.per;
+  prm.a = a;
+  prm.logden = static_cast<const float*>(logden);
+  prm.H = H;
+  prm.out = static_cast<float*>(tmp);
+  prm.err = err;
+  const size_t smem = tc_cluster_smem();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(pl.S * pl.MT));
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(pl.MT);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BUMBAR_CUDA(cudaLaunchKernelEx(&cfg, overlap_tc_cluster_kernel, map, prm));
+  count_launches(1);
+  reduce_tc_cluster<<<dim3(128 * 128 / 256, static_cast<unsigned>(pl.T)), 256, 0, st>>>(prm.out, pl.S, pl.T, pl.MT,
+                                                                                       static_cast<int>(K), G);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
 }
 
 mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* a,
                        const void* logden, const int32_t* H, double* G, unsigned* err, void* tmp, size_t tmp_bytes,
                        cudaStream_t st) {
-  const TcPlan pl = tc_plan(K, n);
   if (tmp_bytes < overlap_tc_tmp_bytes(K, n)) {
     set_error("overlap_tc: scratch too small");
     return MBAR_EINVAL;
   }
+  if (cl_eligible(dtype_bytes, K)) return overlap_tc_cluster(v, K, n, ld, a, logden, H, G, err, tmp, st);
+  const TcPlan pl = tc_plan(K, n);
   const int nc = static_cast<int>(pl.ctas.size()), ni = static_cast<int>(pl.first.size());
   unsigned char* q = static_cast<unsigned char*>(tmp);
   float* part = reinterpret_cast<float*>(q);
@@ -411,18 +898,24 @@ mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int
   const size_t smem = dtype_bytes == 4 ? tc_smem<float>() : tc_smem<double>();
   if (dtype_bytes == 4) {
     static bool attr = false;
-    if (!attr) {
-      BUMBAR_CUDA(cudaFuncSetAttribute(overlap_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem)));
-      attr = true;
+    {
+      std::lock_guard<std::recursive_mutex> lock(init_mutex());
+      if (!attr) {
+        BUMBAR_CUDA(cudaFuncSetAttribute(overlap_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+        attr = true;
+      }
     }
     overlap_tc_kernel<float><<<nc, kTcThreads, smem, st>>>(prm);
   } else {
     static bool attr = false;
-    if (!attr) {
-      BUMBAR_CUDA(cudaFuncSetAttribute(overlap_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem)));
-      attr = true;
+    {
+      std::lock_guard<std::recursive_mutex> lock(init_mutex());
+      if (!attr) {
+        BUMBAR_CUDA(cudaFuncSetAttribute(overlap_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+        attr = true;
+      }
     }
     overlap_tc_kernel<double><<<nc, kTcThreads, smem, st>>>(prm);
   }

@@ -28,7 +28,9 @@ struct LseParams {
   const double* logN;                      // [K]
   const int32_t* H;                        // [n] counts or nullptr (all ones)
   double* partials;                        // [grid x K] scratch
-  unsigned* counter;                       // scratch: completion counter (zero between passes)
+  double* epi;                             // scratch after the partials: new f [K], then per-CTA (s, d, finite)
+  int nparts;                              // CTAs of the pass (rows of partials); set by lse_launch
+  unsigned* counter;                       // scratch: completion counter of the epilogue (zero between passes)
   unsigned* err;                           // scratch: timeout count
   double* Q;                               // [K] out
   void* logden;                            // [n] out (dtype of v) or nullptr
@@ -59,6 +61,9 @@ bool lse_regs_supported(int64_t K, int dtype_bytes);
 LsePlan lse_regs_plan(int64_t K, int64_t n);
 mbar_status lse_regs_launch(const CUtensorMap& tmap, const LsePlan& pl, const LseParams& prm, cudaStream_t st);
 size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes);
+// Scratch of a pass whose plan has `grid` CTAs: 256 bytes (counter, error
+// word), grid x K FP64 partials, then the epilogue's new f and per-CTA slots.
+size_t lse_scratch_for_grid(int64_t K, int grid);
 mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm, int dtype_bytes,
                        cudaStream_t stream);
 
@@ -97,6 +102,14 @@ mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int6
                       const int32_t* start, int64_t nb, void* out, int64_t ld_out, void* tmp, size_t tmp_bytes,
                       cudaStream_t stream);
 size_t bin_means_tmp_bytes(int64_t K, int64_t N);
+// The bin means of up to 8 histograms of the same sorted data in one read of
+// v (level l: segment ids seg[l], bin starts start[l], nb[l] bins, output
+// out[l] with row pitch ld_out[l]).
+constexpr int kMaxBinLevels = 8;
+mbar_status bin_means_multi(const void* v, int dtype_bytes, int64_t K, int64_t N, int64_t ld, int L,
+                            const int32_t* const* seg, const int32_t* const* start, const int64_t* nb,
+                            void* const* out, const int64_t* ld_out, void* tmp, size_t tmp_bytes, cudaStream_t st);
+size_t bin_means_multi_tmp_bytes(int64_t K, int64_t N, int L, const int64_t* nb);
 
 // Column gather: out[k][i] = in[k][perm[i]] (row pitch ld for both).
 mbar_status gather_columns(const void* in, void* out, int dtype_bytes, int64_t K, int64_t N, int64_t ld,
@@ -133,6 +146,7 @@ size_t overlap_tc_tmp_bytes(int64_t K, int64_t n);
 // 1 = CUDA cores, 2 = tensor cores.
 void set_hessian_path(int path);
 int hessian_path_for(int64_t K);
+bool tc_cluster_enabled();  // false: tensor-core path without the cluster variant
 
 // ---- dense FP64 (cholesky.cu) ----
 // Solves A x = b for the (m x m) symmetric positive definite block

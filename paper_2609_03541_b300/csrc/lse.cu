@@ -67,7 +67,7 @@ __host__ __device__ inline size_t rup(size_t x, size_t m) { return (x + m - 1) /
 
 // Shared-memory carve-up (dynamic, base aligned up to 1024 in the kernel):
 //   stages x stage bytes | a_k [K] | w_c [32] | column partials [2][G][32] |
-//   mbarriers [8] | epilogue doubles [K]
+//   mbarriers [8]
 template <typename T, int G>
 struct LseSmem {
   static __host__ __device__ size_t stage_bytes(int nbox, int box_rows) {
@@ -78,7 +78,7 @@ struct LseSmem {
   static constexpr size_t kParts = 2 * G * 32 * sizeof(T);
   static constexpr size_t kBars = 64;
   static __host__ __device__ size_t extra_bytes(int K) {
-    return a_bytes(K) + kW + kParts + kBars + rup(static_cast<size_t>(K) * sizeof(double), 16);
+    return a_bytes(K) + kW + kParts + kBars;
   }
 };
 
@@ -108,8 +108,6 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
   T* cols = colm + G * 32;                     // [G][32] partial sums
   cur += LseSmem<T, G>::kParts;
   uint64_t* bars = reinterpret_cast<uint64_t*>(cur);
-  cur += LseSmem<T, G>::kBars;
-  double* red_s = reinterpret_cast<double*>(cur);
 
   const int num_strips = p.num_strips;
   const int my_first = blockIdx.x;
@@ -329,7 +327,7 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
     rowsum[j] = acc64[j];
     if constexpr (sizeof(T) == 4) rowsum[j] += static_cast<double>(acc32[j]);
   }
-  lse_finish<THREADS, CF::ROWS_PT>(p, rowsum, red_s);
+  lse_write_partials<THREADS, CF::ROWS_PT>(p, rowsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,6 +342,7 @@ constexpr int kGf64 = 1;
 
 template <typename T, int G>
 int lse_occupancy(size_t smem) {
+  std::lock_guard<std::recursive_mutex> lock(init_mutex());
   static size_t max_dyn = 0;
   if (max_dyn == 0) {
     int dev = 0, optin = 0;
@@ -380,20 +379,164 @@ LsePlan lse_plan(int64_t K, int64_t n, int dtype_bytes) {
                                           : LseSmem<double, kGf64>::extra_bytes(static_cast<int>(K));
   pl.smem = pl.stages * sb + extra + 1024;  // + alignment slack
   static int occ_cache[2][1025] = {};
-  int* occ = &occ_cache[dtype_bytes == 4 ? 0 : 1][std::min<int64_t>(K, 1024)];
-  if (*occ == 0) {
-    *occ = (dtype_bytes == 4) ? lse_occupancy<float, kGf32>(pl.smem) : lse_occupancy<double, kGf64>(pl.smem);
-    cudaGetLastError();  // the probes above report through their return values
+  int occ = 0;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    int* slot = &occ_cache[dtype_bytes == 4 ? 0 : 1][std::min<int64_t>(K, 1024)];
+    if (*slot == 0) {
+      *slot = (dtype_bytes == 4) ? lse_occupancy<float, kGf32>(pl.smem) : lse_occupancy<double, kGf64>(pl.smem);
+      cudaGetLastError();  // the probes above report through their return values
+    }
+    occ = *slot;
   }
-  pl.grid = static_cast<int>(std::min<int64_t>(pl.num_strips, static_cast<int64_t>(std::max(*occ, 1)) * num_sms()));
+  pl.grid = static_cast<int>(std::min<int64_t>(pl.num_strips, static_cast<int64_t>(std::max(occ, 1)) * num_sms()));
   pl.grid = std::max(pl.grid, 1);
-  pl.ok = *occ > 0;
+  pl.ok = occ > 0;
   return pl;
+}
+
+namespace {
+
+constexpr int kEpiWarps = 4;  // states per epilogue CTA (one warp each)
+
+// Reduction over the CTAs of the pass and the SCI epilogue, one warp per
+// state k: the lanes add the partials of CTAs lane, lane + 32, ... in order,
+// a shuffle tree combines them (a fixed order); lane 0 finishes the state.
+// Each CTA also evaluates state 0's update for the gauge. The new f goes to
+// a scratch vector first (f_out may be f itself, which other CTAs are still
+// reading). Per-CTA maxima of the step sizes go to scratch slots, and the
+// last CTA to finish combines them with all its threads (shuffle trees, no
+// long dependent FP64 chains), updates the loop control and copies the new
+// f out.
+__global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams p) {
+  if (p.ctrl != nullptr && p.skip_if_done && p.ctrl->done) return;  // same guard as the pass
+  const int K = p.K;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blockIdx.x * kEpiWarps + warp;
+  const bool sci = p.mode == kLseModeSci;
+  auto rowsum = [&](int row) {
+    double q = 0.0;
+    for (int b = lane; b < p.nparts; b += 32) q += p.partials[static_cast<size_t>(b) * K + row];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    return q;
+  };
+  __shared__ double f0new_s;
+  __shared__ double smax_s[kEpiWarps], dmax_s[kEpiWarps];
+  __shared__ int fin_s[kEpiWarps];
+  if (sci && warp == 0) {
+    const double q0 = rowsum(0);
+    if (lane == 0) f0new_s = p.f[0] + p.logN[0] - log(q0);
+  }
+  double qk = 0.0, fnew = 0.0;
+  if (k < K) {
+    qk = rowsum(k);
+    if (lane == 0) {
+      p.Q[k] = qk;
+      if (sci) fnew = p.f[k] + p.logN[k] - log(qk);
+    }
+  }
+  if (!sci) return;
+  __syncthreads();
+  double smax = -1.0, dmax = 0.0;  // smax -1: no f_k != 0 seen
+  int finite = 1;
+  if (k < K && lane == 0) {
+    const double fo = fnew - f0new_s;
+    const double fi = p.f[k];
+    p.epi[k] = fo;
+    if (p.g_out) p.g_out[k] = qk - p.Nk[k];
+    if (!isfinite(fo)) finite = 0;
+    if (fi != 0.0) smax = fabs(fo / fi - 1.0);
+    dmax = fabs(fo - (fi - p.f[0]));
+  }
+  if (lane == 0) {
+    smax_s[warp] = smax;
+    dmax_s[warp] = dmax;
+    fin_s[warp] = finite;
+  }
+  __syncthreads();
+  __shared__ unsigned int is_last;
+  if (threadIdx.x == 0) {
+    double sm = -1.0, dm = 0.0;
+    int ok = 1;
+#pragma unroll
+    for (int w = 0; w < kEpiWarps; ++w) {
+      sm = fmax(sm, smax_s[w]);
+      dm = fmax(dm, dmax_s[w]);
+      ok &= fin_s[w];
+    }
+    double* slot = p.epi + K + 3 * static_cast<size_t>(blockIdx.x);
+    slot[0] = sm;
+    slot[1] = dm;
+    slot[2] = ok ? 1.0 : 0.0;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(p.counter, 1u);
+    is_last = (ticket == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (p.f_out)
+    for (int j = threadIdx.x; j < K; j += blockDim.x) p.f_out[j] = p.epi[j];
+  double sm = -1.0, dm = 0.0;
+  int okm = 1;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    const double* slot = p.epi + K + 3 * static_cast<size_t>(b);
+    sm = fmax(sm, slot[0]);
+    dm = fmax(dm, slot[1]);
+    okm &= slot[2] != 0.0 ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+    dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    okm &= __shfl_xor_sync(0xffffffffu, okm, o);
+  }
+  if (lane == 0) {
+    smax_s[warp] = sm;
+    dmax_s[warp] = dm;
+    fin_s[warp] = okm;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double smf = -1.0, dmf = 0.0;
+  int okf = 1;
+#pragma unroll
+  for (int w = 0; w < kEpiWarps; ++w) {
+    smf = fmax(smf, smax_s[w]);
+    dmf = fmax(dmf, dmax_s[w]);
+    okf &= fin_s[w];
+  }
+  const double sv = (smf < 0.0) ? INFINITY : smf;
+  const double dv = dmf;
+  if (p.s_out) *p.s_out = sv;
+  if (p.d_out) *p.d_out = dv;
+  if (p.ctrl) {
+    p.ctrl->iters += 1;
+    p.ctrl->last_s = sv;
+    if (!okf) p.ctrl->nonfinite = 1;
+    if ((p.eps > 0.0 && sv < p.eps) || (p.noise > 0.0 && dv < p.noise)) p.ctrl->done = 1;
+  }
+  *p.counter = 0u;  // leave the scratch counter zeroed
+}
+
+}  // namespace
+
+size_t lse_scratch_for_grid(int64_t K, int grid) {
+  return 256 + static_cast<size_t>(grid) * K * sizeof(double) + sizeof(double) * K +
+         3 * sizeof(double) * ceil_div(K, kEpiWarps);
 }
 
 size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes) {
   LsePlan pl = lse_plan(K, n, dtype_bytes);
-  return static_cast<size_t>(pl.grid) * K * sizeof(double) + 256;
+  return lse_scratch_for_grid(K, pl.grid);
+}
+
+mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream) {
+  lse_epilogue_kernel<<<static_cast<unsigned>(ceil_div(prm.K, kEpiWarps)), 32 * kEpiWarps, 0, stream>>>(prm);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
 }
 
 mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm, int dtype_bytes,
@@ -406,7 +549,12 @@ mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm
   prm.box_rows = pl.box_rows;
   prm.nbox = pl.nbox;
   prm.stages = pl.stages;
-  if (pl.variant == 1) return lse_regs_launch(tmap, pl, prm, stream);
+  prm.nparts = pl.grid;
+  prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
+  if (pl.variant == 1) {
+    BUMBAR_TRY(lse_regs_launch(tmap, pl, prm, stream));
+    return lse_epilogue_launch(prm, stream);
+  }
   if (dtype_bytes == 4) {
     lse_pass_kernel<float, kGf32><<<pl.grid, pl.threads, pl.smem, stream>>>(tmap, prm);
   } else {
@@ -414,7 +562,7 @@ mbar_status lse_launch(const CUtensorMap& tmap, const LsePlan& pl, LseParams prm
   }
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
-  return MBAR_OK;
+  return lse_epilogue_launch(prm, stream);
 }
 
 }  // namespace bumbar

@@ -42,11 +42,11 @@ __host__ __device__ inline size_t rupr(size_t x, size_t m) { return (x + m - 1) 
 }  // namespace
 
 // shared memory: stages | a [Kpad] f32 | slots [16][Kpad] f64 | colm[2][32] |
-//                cols[2][32] | mbarriers[8] | epilogue [K] f64
+//                cols[2][32] | mbarriers[8]
 struct RegsSmem {
   static __host__ __device__ size_t kpad(int K) { return rupr(static_cast<size_t>(K), 16); }
   static __host__ __device__ size_t extra(int K, int nslots) {
-    return kpad(K) * 4 + nslots * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64 + rupr(static_cast<size_t>(K) * 8, 16);
+    return kpad(K) * 4 + nslots * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64;
   }
 };
 
@@ -76,8 +76,6 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   float* cols = colm + 64;                         // [2][32]
   cur += 2 * 32 * 4 * 2;
   uint64_t* bars = reinterpret_cast<uint64_t*>(cur);
-  cur += 64;
-  double* red_s = reinterpret_cast<double*>(cur);
 
   const int num_strips = p.num_strips;
   const int my_first = blockIdx.x, stride = gridDim.x;
@@ -228,7 +226,7 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     }
     rowsum[j] = t;
   }
-  lse_finish<kRThreads, RPT>(p, rowsum, red_s);
+  lse_write_partials<kRThreads, RPT>(p, rowsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -237,6 +235,7 @@ namespace {
 
 template <int J, int H>
 int regs_occupancy(size_t smem) {
+  std::lock_guard<std::recursive_mutex> lock(init_mutex());
   static size_t max_dyn = 0;
   if (max_dyn == 0) {
     int dev = 0, optin = 0;
@@ -308,14 +307,19 @@ LsePlan lse_regs_plan(int64_t K, int64_t n) {
   while (pl.stages > 2 && pl.stages * sb + extra > 220 * 1024) --pl.stages;
   pl.smem = pl.stages * sb + extra;
   static int occ_cache[1025] = {};
-  int* occ = &occ_cache[std::min<int64_t>(K, 1024)];
-  if (*occ == 0) {
-    *occ = regs_occ_dispatch(J, H, pl.smem);
-    cudaGetLastError();
+  int occ = 0;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    int* slot = &occ_cache[std::min<int64_t>(K, 1024)];
+    if (*slot == 0) {
+      *slot = regs_occ_dispatch(J, H, pl.smem);
+      cudaGetLastError();
+    }
+    occ = *slot;
   }
-  pl.grid = static_cast<int>(std::min<int64_t>(pl.num_strips, static_cast<int64_t>(std::max(*occ, 1)) * num_sms()));
+  pl.grid = static_cast<int>(std::min<int64_t>(pl.num_strips, static_cast<int64_t>(std::max(occ, 1)) * num_sms()));
   pl.grid = std::max(pl.grid, 1);
-  pl.ok = *occ > 0;
+  pl.ok = occ > 0;
   return pl;
 }
 

@@ -15,7 +15,7 @@ namespace bumbar {
 namespace {
 
 // Persistent blocks, each handling strips of 32 columns: 8 row groups x 32
-// columns. Pass 1 takes the column minimum with integer comparisons on an
+// columns, eight rows in flight per thread. Pass 1 takes the column minimum with integer comparisons on an
 // order-preserving image of the binary64 bits (FP64 arithmetic is slow on
 // this part); pass 2 re-reads the same 32 x K block -- few enough blocks are
 // resident that it is still in L2 -- and writes fl32(u - min).
@@ -40,7 +40,21 @@ __global__ void __launch_bounds__(256) shift_fp32_kernel(const double* __restric
     unsigned long long m = ~0ull;
     bool ok = true;
     if (n < N) {
-      for (int64_t k = rg; k < K; k += 8) {
+      // eight independent loads in flight per thread
+      int64_t k = rg;
+      for (; k + 56 < K; k += 64) {
+        double x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = u[(k + 8 * j) * ldu + n];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x[j]));
+          ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
+          const unsigned long long kx = ordered_bits(x[j]);
+          m = kx < m ? kx : m;
+        }
+      }
+      for (; k < K; k += 8) {
         const double x = u[k * ldu + n];
         const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
         ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
@@ -66,7 +80,15 @@ __global__ void __launch_bounds__(256) shift_fp32_kernel(const double* __restric
         cm = 0.0;
       }
       if (rg == 0) c[n] = cm;
-      for (int64_t k = rg; k < K; k += 8) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - cm);
+      int64_t k = rg;
+      for (; k + 56 < K; k += 64) {
+        double x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = u[(k + 8 * j) * ldu + n];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[(k + 8 * j) * ldv + n] = static_cast<float>(x[j] - cm);
+      }
+      for (; k < K; k += 8) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - cm);
     }
   }
 }

@@ -77,6 +77,15 @@ class Report(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("workers", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_uint64),
+        ("opts", Opts),
+    ]
+
+
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -104,6 +113,18 @@ _SIGNATURES = {
     "mbar_kernel_launches": ([_i64p], ctypes.c_int),
     "mbar_get_trace": ([_vp, _i64p, _dp, ctypes.c_int64], ctypes.c_int),
     "mbar_set_hessian_path": ([ctypes.c_int32], ctypes.c_int),
+    "mbar_footprint_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32], ctypes.c_uint64),
+    "mbar_server_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ServerConfig)], ctypes.c_int),
+    "mbar_server_submit": ([_vp, ctypes.c_int64, ctypes.c_int64, _i64p, _vp, ctypes.c_int32, _vp, ctypes.c_int32,
+                            _i64p], ctypes.c_int),
+    "mbar_server_poll": ([_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "mbar_server_wait": ([_vp, ctypes.c_int64, _dp, ctypes.POINTER(Report), _dp, _dp], ctypes.c_int),
+    "mbar_server_stats": ([_vp, _i64p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)],
+                          ctypes.c_int),
+    "mbar_server_destroy": ([_vp], ctypes.c_int),
+    "mbar_batch_solve": ([ctypes.c_int32, _i64p, _i64p, ctypes.POINTER(_i64p), ctypes.POINTER(_vp), ctypes.c_int32,
+                          ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(ServerConfig), ctypes.POINTER(_dp),
+                          ctypes.POINTER(Report), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "mbar_lse_static_scratch_bytes": ([], ctypes.c_size_t),
     "mbar_lse_pass_static": ([_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
                               _vp, _vp, _vp], ctypes.c_int),
@@ -338,3 +359,139 @@ def lse_pass_static(v, f, log_N, Q, H=None, logden=None, stream=None):
         ctypes.c_void_p(Q.data_ptr()),
         ctypes.c_void_p(logden.data_ptr()) if logden is not None else None,
         ctypes.c_void_p(st)))
+
+
+# ---------------------------------------------------------------------------
+# serving and batching (mbar_server_* / mbar_batch_solve)
+# ---------------------------------------------------------------------------
+
+def footprint_bytes(K: int, N: int, precision: int = MBAR_MIXED, use_binning: int = 1) -> int:
+    """``mbar_footprint_bytes``: estimated peak device memory of one solve."""
+    return int(lib().mbar_footprint_bytes(int(K), int(N), int(precision), int(use_binning)))
+
+
+def server_config(workers: int = 8, hbm_budget_bytes: int = 160 << 30, precision: int = MBAR_MIXED,
+                  opts: Opts | None = None) -> ServerConfig:
+    cfg = ServerConfig()
+    cfg.workers = int(workers)
+    cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+    cfg.opts = opts if opts is not None else default_opts(precision)
+    cfg.opts.precision = int(precision)
+    return cfg
+
+
+def _u_arg(u_kn):
+    """(pointer, on_device, keep-alive object, N) for a host array or a CUDA tensor."""
+    dptr, on_dev = _device_ptr(u_kn)
+    if on_dev:
+        if u_kn.dtype.__repr__() != "torch.float64" or not u_kn.is_contiguous():
+            raise ValueError("device u_kn must be a contiguous float64 CUDA tensor")
+        return dptr, 1, u_kn, int(u_kn.shape[1])
+    u = _f64(u_kn)
+    return ctypes.c_void_p(u.ctypes.data), 0, u, int(u.shape[1])
+
+
+def _phi_arg(phi):
+    if phi is None:
+        return None, 0, None
+    dptr, on_dev = _device_ptr(phi)
+    if on_dev:
+        return dptr, 1, phi
+    p = _f64(phi)
+    return ctypes.c_void_p(p.ctypes.data), 0, p
+
+
+class Server:
+    """``mbar_server``: worker threads, each with its own CUDA stream, solve
+    admitted requests concurrently; admission keeps the sum of the requests'
+    footprints within the memory budget."""
+
+    def __init__(self, cfg: ServerConfig):
+        self._h = ctypes.c_void_p()
+        _check(lib().mbar_server_create(ctypes.byref(self._h), ctypes.byref(cfg)))
+        self._keep = {}
+        self._K = {}
+
+    def submit(self, u_kn, N_k, phi=None) -> int:
+        Nk = np.ascontiguousarray(np.asarray(N_k, dtype=np.int64))
+        uptr, u_dev, ukeep, N = _u_arg(u_kn)
+        pptr, p_dev, pkeep = _phi_arg(phi)
+        rid = ctypes.c_int64()
+        _check(lib().mbar_server_submit(self._h, int(Nk.shape[0]), N, Nk.ctypes.data_as(_i64p), uptr, u_dev, pptr,
+                                        p_dev, ctypes.byref(rid)))
+        self._keep[rid.value] = (ukeep, pkeep)   # read at admission: alive until wait
+        self._K[rid.value] = int(Nk.shape[0])
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        st = ctypes.c_int32()
+        _check(lib().mbar_server_poll(self._h, int(rid), ctypes.byref(st)))
+        return st.value
+
+    def wait(self, rid: int):
+        """(f, report, latency_s, run_s) of request ``rid``; raises on a failed solve."""
+        f = np.zeros(self._K[rid])
+        rep = Report()
+        lat = ctypes.c_double()
+        run = ctypes.c_double()
+        status = lib().mbar_server_wait(self._h, int(rid), _ptr(f), ctypes.byref(rep), ctypes.byref(lat),
+                                        ctypes.byref(run))
+        self._keep.pop(rid, None)
+        self._K.pop(rid, None)
+        _check(status)
+        return f, rep, lat.value, run.value
+
+    def stats(self):
+        c = ctypes.c_int64()
+        pr = ctypes.c_int32()
+        pb = ctypes.c_uint64()
+        _check(lib().mbar_server_stats(self._h, ctypes.byref(c), ctypes.byref(pr), ctypes.byref(pb)))
+        return {"completed": c.value, "peak_running": pr.value, "peak_bytes": pb.value}
+
+    def close(self):
+        if self._h:
+            _check(lib().mbar_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def batch_solve(problems, cfg: ServerConfig):
+    """``mbar_batch_solve`` over ``problems`` = [(u_kn, N_k, phi or None), ...]
+    (all host arrays or all CUDA tensors). Returns ([f_p], [report_p], [status_p])."""
+    P = len(problems)
+    Ks, Ns, nk_arrs, uptrs, pptrs, keep = [], [], [], [], [], []
+    on_dev = None
+    p_dev = 0
+    for u, Nk, phi in problems:
+        uptr, ud, ukeep, N = _u_arg(u)
+        on_dev = ud if on_dev is None else on_dev
+        if ud != on_dev:
+            raise ValueError("batch_solve: all u_kn on the host or all on the device")
+        pptr, pd, pkeep = _phi_arg(phi)
+        if phi is not None:
+            p_dev = pd
+        nk = np.ascontiguousarray(np.asarray(Nk, dtype=np.int64))
+        Ks.append(int(nk.shape[0]))
+        Ns.append(N)
+        nk_arrs.append(nk)
+        uptrs.append(uptr)
+        pptrs.append(pptr)
+        keep.append((ukeep, pkeep))
+    K_a = np.asarray(Ks, dtype=np.int64)
+    N_a = np.asarray(Ns, dtype=np.int64)
+    nk_ptrs = (_i64p * P)(*[a.ctypes.data_as(_i64p) for a in nk_arrs])
+    u_ptrs = (_vp * P)(*[p.value for p in uptrs])
+    phi_ptrs = (_vp * P)(*[(p.value if p is not None else None) for p in pptrs])
+    fs = [np.zeros(k) for k in Ks]
+    f_ptrs = (_dp * P)(*[_ptr(f) for f in fs])
+    reps = (Report * P)()
+    sts = (ctypes.c_int * P)()
+    lib().mbar_batch_solve(P, K_a.ctypes.data_as(_i64p), N_a.ctypes.data_as(_i64p), nk_ptrs, u_ptrs, int(on_dev or 0),
+                           phi_ptrs, int(p_dev), ctypes.byref(cfg), f_ptrs, reps, sts)
+    return fs, [reps[i] for i in range(P)], [int(sts[i]) for i in range(P)]

@@ -198,3 +198,64 @@ def batch_of_problems(count: int = 512, K_range=(4, 256), N_k_range=(100, 10000)
         else:
             out.append(umbrella(K=K, N_k=Nk, seed=s, grid_points=1 << 14))
     return out
+
+
+# ---------------------------------------------------------------------------
+# device-side generators (torch on the GPU): the batched and served workloads
+# are too large to draw on the host. Same models as harmonic / umbrella above,
+# drawn with torch's counter-based Philox generator from (kind, K, N_k, seed).
+# ---------------------------------------------------------------------------
+
+def harmonic_device(K: int, N_k: int, seed: int, d: int = 3, device="cuda"):
+    """(u_kn float64 K x N on `device`, N_k array, phi=None): harmonic wells,
+    kappa_k ~ U[1,4], mu_k ~ U[0,2]^d, N_k exact Gaussian samples per state.
+    u_kn = 0.5 kappa_k (|x|^2 - 2 mu_k.x + |mu_k|^2), formed by one small
+    matrix product (no K x N x d intermediate)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    kappa = 1.0 + 3.0 * torch.rand(K, generator=g, device=device, dtype=torch.float64)
+    mu = 2.0 * torch.rand(K, d, generator=g, device=device, dtype=torch.float64)
+    x = torch.empty(K * N_k, d, device=device, dtype=torch.float64)
+    step = max(1, (1 << 24) // max(1, N_k * d))        # states per chunk of draws
+    for k0 in range(0, K, step):
+        k1 = min(K, k0 + step)
+        z = torch.randn(k1 - k0, N_k, d, generator=g, device=device, dtype=torch.float64)
+        z.div_(torch.sqrt(kappa[k0:k1])[:, None, None]).add_(mu[k0:k1, None, :])
+        x[k0 * N_k:k1 * N_k] = z.reshape(-1, d)
+    x2 = (x * x).sum(dim=1)
+    mu2 = (mu * mu).sum(dim=1)
+    u = mu @ x.T                                        # K x N, formed in place from here on
+    u.mul_(-2.0).add_(x2[None, :]).add_(mu2[:, None]).mul_(0.5 * kappa[:, None]).clamp_(min=0.0)
+    return u.contiguous(), np.full(K, N_k, dtype=np.int64), None
+
+
+def umbrella_device(K: int, N_k: int, seed: int, kappa: float = 50.0, grid_points: int = 4096, device="cuda"):
+    """(u_kn float64 K x N, N_k array, phi = x): the umbrella windows of
+    `umbrella`, sampled by inverse CDF of each window's density tabulated on
+    `grid_points` points over [x_k - 1.5, x_k + 1.5] (trapezoid CDF, linear
+    interpolation)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    xc = torch.linspace(-1.5, 1.5, K, device=device, dtype=torch.float64)
+    t = torch.linspace(-1.5, 1.5, grid_points, device=device, dtype=torch.float64)
+    grid = xc[:, None] + t[None, :]                                    # K x G
+    logp = -5.0 * (grid * grid - 1.0) ** 2 - 0.5 * kappa * (grid - xc[:, None]) ** 2
+    p = torch.exp(logp - logp.max(dim=1, keepdim=True).values)
+    cdf = torch.zeros_like(p)
+    cdf[:, 1:] = torch.cumsum(0.5 * (p[:, 1:] + p[:, :-1]), dim=1)
+    cdf /= cdf[:, -1:].clone()
+    r = torch.rand(K, N_k, generator=g, device=device, dtype=torch.float64)
+    j = torch.searchsorted(cdf, r).clamp_(1, grid_points - 1)
+    c0 = torch.gather(cdf, 1, j - 1)
+    c1 = torch.gather(cdf, 1, j)
+    x0 = torch.gather(grid, 1, j - 1)
+    x1 = torch.gather(grid, 1, j)
+    w = torch.where(c1 > c0, (r - c0) / (c1 - c0), torch.zeros_like(r))
+    x = (x0 + w * (x1 - x0)).reshape(-1)                               # N, state-major
+    del r, j, c0, c1, x0, x1, w
+    well = 5.0 * (x * x - 1.0) ** 2
+    u = x[None, :].repeat(K, 1)                          # K x N, formed in place from here on
+    u.sub_(xc[:, None]).square_().mul_(0.5 * kappa).add_(well[None, :])
+    return u.contiguous(), np.full(K, N_k, dtype=np.int64), x.contiguous()

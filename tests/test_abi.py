@@ -50,9 +50,11 @@ def test_struct_layout_matches_binding():
 #include <stddef.h>
 #include "bumbar.h"
 int main(void){
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(mbar_opts), offsetof(mbar_opts, f_tol), offsetof(mbar_opts, max_sci),
-         offsetof(mbar_opts, noise_floor),
-         sizeof(mbar_report), offsetof(mbar_report, max_abs_grad), offsetof(mbar_report, last_step));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mbar_opts), offsetof(mbar_opts, f_tol),
+         offsetof(mbar_opts, max_sci), offsetof(mbar_opts, noise_floor),
+         sizeof(mbar_report), offsetof(mbar_report, max_abs_grad), offsetof(mbar_report, last_step),
+         sizeof(mbar_server_config), offsetof(mbar_server_config, hbm_budget_bytes),
+         offsetof(mbar_server_config, opts));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -62,7 +64,9 @@ int main(void){
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = list(map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()))
     assert vals == [ctypes.sizeof(M.Opts), M.Opts.f_tol.offset, M.Opts.max_sci.offset, M.Opts.noise_floor.offset,
-                    ctypes.sizeof(M.Report), M.Report.max_abs_grad.offset, M.Report.last_step.offset]
+                    ctypes.sizeof(M.Report), M.Report.max_abs_grad.offset, M.Report.last_step.offset,
+                    ctypes.sizeof(M.ServerConfig), M.ServerConfig.hbm_budget_bytes.offset,
+                    M.ServerConfig.opts.offset]
 
 
 def test_opts_default_are_the_papers(L):
@@ -95,3 +99,22 @@ def test_create_rejects_bad_sizes_before_any_device_work(L, K, N, Nk, code):
 
 def test_destroy_null_is_ok(L):
     assert L.mbar_destroy(None) == 0
+
+
+def test_footprint_estimate_grows_with_the_problem(L):
+    small = M.footprint_bytes(8, 8000)
+    big = M.footprint_bytes(500, 2_000_000)
+    assert 0 < small < big
+    assert big >= 500 * 2_000_000 * 12          # FP64 staging + FP32 data at creation
+    assert M.footprint_bytes(500, 2_000_000, M.MBAR_FP64) > big
+    assert M.footprint_bytes(0, 10) == 0
+
+
+def test_server_rejects_bad_configuration_without_a_gpu(L):
+    cfg = M.server_config(workers=0, hbm_budget_bytes=1 << 30)
+    with pytest.raises(M.MbarError) as e:
+        M.Server(cfg)
+    assert e.value.name == "MBAR_EINVAL"
+    cfg = M.server_config(workers=2, hbm_budget_bytes=0)
+    with pytest.raises(M.MbarError):
+        M.Server(cfg)

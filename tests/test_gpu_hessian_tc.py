@@ -33,9 +33,15 @@ def _tensor_cores():
     M.set_hessian_path(0)
 
 
+# path 2: tensor cores (thread-block-cluster kernel for FP32 data with
+# K <= 512, one cluster CTA per 128-row tile); path 3: tensor cores with the
+# per-item kernel only
+@pytest.mark.parametrize("path", [2, 3])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-@pytest.mark.parametrize("K,N", [(64, 3000), (128, 4099), (200, 5001), (500, 6000), (1000, 9001)])
-def test_tc_hessian_matches_oracle(prec, K, N):
+@pytest.mark.parametrize("K,N", [(64, 3000), (128, 4099), (200, 5001), (300, 70001), (500, 6000), (512, 20000),
+                                 (1000, 9001)])
+def test_tc_hessian_matches_oracle(prec, K, N, path):
+    M.set_hessian_path(path)
     u, Nk = _problem(K, N, seed=K)
     f = O.gauge(O.sci_step(u, np.zeros(K), Nk))
     ctx = M.Context(u, Nk, M.MBAR_MIXED if prec == "mixed" else M.MBAR_FP64)
@@ -71,3 +77,35 @@ def test_tc_and_cuda_core_paths_agree():
     H_cc = ctx.hessian(f)
     ctx.close()
     assert np.max(np.abs(H_tc - H_cc)) < 2e-3 * np.max(np.abs(H_cc))
+
+
+@pytest.mark.parametrize("K", [90, 260, 500])
+def test_tc_cluster_hessian_binned_counts_mixed(K):
+    """Binned counts H_p (sqrt(H_p) scaling of P~) on the cluster kernel."""
+    p = W.umbrella(K=K, N_k=200, seed=K, grid_points=1 << 12)
+    f = O.gauge(O.sci_step(p.u_kn, np.zeros(K), p.N_k))
+    ctx = M.Context(p.u_kn, p.N_k, M.MBAR_MIXED)
+    ctx.set_coordinate(p.phi)
+    ctx.bin(0.003)
+    Hs = ctx.hessian(f)
+    ctx.close()
+    hist = O.histogram(p.phi, 0.003)
+    ub = O.binned_u(p.u_kn, hist)
+    H_ref = O.mbar_hessian(ub, f, p.N_k, hist.H)
+    assert np.max(np.abs(Hs - H_ref)) < 2e-3 * np.max(np.abs(H_ref))
+
+
+@pytest.mark.parametrize("K,N", [(64, 64), (100, 100), (257, 300), (400, 450)])
+def test_tc_cluster_and_item_kernels_agree_on_few_samples(K, N):
+    """One to seven 64-sample chunks in all, the last one partial."""
+    u, Nk = _problem(K, N, seed=N)
+    f = np.zeros(K)
+    ctx = M.Context(u, Nk, M.MBAR_MIXED)
+    H2 = ctx.hessian(f)
+    M.set_hessian_path(3)
+    H3 = ctx.hessian(f)
+    ctx.close()
+    H_ref = O.mbar_hessian(u, f, Nk)
+    scale = np.max(np.abs(H_ref))
+    assert np.max(np.abs(H2 - H_ref)) < 2e-3 * scale
+    assert np.max(np.abs(H2 - H3)) < 2e-3 * scale

@@ -328,3 +328,37 @@ def test_lse_pass_stateless(dtype):
     tol = 1e-10 if dtype == "float64" else 1e-5
     assert np.max(np.abs(Q.cpu().numpy() - Q_ref) / Q_ref) < tol
     assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - O.log_denominator(u, f, Nk))) < tol * 100
+
+
+@pytest.mark.parametrize("case", ["gaussian", "umbrella_h0"])
+def test_algorithm1_trajectory_matches_oracle_fp64(case):
+    """Every Eq. 3 check of the second loop (level size, s_n, s_next) and the
+    end of the first loop agree with the oracle's run: the binned levels,
+    built up front from one read of the data, carry the same bin means as the
+    oracle's level-by-level histograms."""
+    if case == "gaussian":
+        p = W.gaussian_overlap(M=12, N_0=2000, seed=4)
+        opts = O.BUOptions()
+        o = M.default_opts(M.MBAR_FP64)
+    else:
+        p = W.umbrella(K=16, N_k=1000, seed=1, grid_points=1 << 13)
+        opts = O.BUOptions(h0=0.1)
+        o = M.default_opts(M.MBAR_FP64, h0=0.1)
+    tr = []
+    O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, opts=opts, trace=tr)
+    ctx = M.Context(p.u_kn, p.N_k, M.MBAR_FP64, opts=o)
+    ctx.set_coordinate(p.phi)
+    ctx.solve()
+    gt = ctx.trace()
+    ctx.close()
+    ph1 = [t for t in tr if t[0] == "phase1"]
+    ph2 = [t for t in tr if t[0] == "phase2"]
+    g1 = [r for r in gt if r[0] == 1]
+    g2 = [r for r in gt if r[0] == 2]
+    assert len(g1) == 1 and int(g1[0][3]) == len(ph1)
+    assert g1[0][2] == pytest.approx(ph1[-1][2], rel=1e-6)
+    assert len(g2) == len(ph2) and len(g2) >= 2
+    for r, t in zip(g2, ph2):
+        assert int(r[1]) == t[1]
+        assert r[2] == pytest.approx(t[2], rel=1e-6, abs=1e-15)
+        assert r[3] == pytest.approx(t[3], rel=1e-6, abs=1e-15)
