@@ -352,6 +352,8 @@ def serve_bench(args):
     budget = int(args.budget_gb * (1 << 30))
     input_cap = int(args.wave_gb * (1 << 30))
 
+    gen_stream = torch.cuda.Stream()
+
     def run(rate):
         cfg = M.server_config(workers=args.workers, hbm_budget_bytes=budget, precision=M.MBAR_MIXED)
         srv = M.Server(cfg)
@@ -391,8 +393,11 @@ def serve_bench(args):
                 reap(True)
             t_arr = max(t_next, time.perf_counter()) if rate else time.perf_counter()
             tg = time.perf_counter()
-            u, nk, phi = _gen_device(kind, K, Nk, seed)
-            torch.cuda.synchronize()
+            if torch.cuda.memory_reserved() > input_cap + (8 << 30):
+                torch.cuda.empty_cache()   # freed inputs of other sizes: hand the memory back
+            with torch.cuda.stream(gen_stream):
+                u, nk, phi = _gen_device(kind, K, Nk, seed)
+            gen_stream.synchronize()       # this stream only: solves keep running meanwhile
             gen_s += time.perf_counter() - tg
             try:
                 rid = srv.submit(u, nk, phi)
@@ -469,8 +474,8 @@ def main():
     ap.add_argument("--loads", type=lambda t: [float(x) for x in t.split(",")], default=[0.5, 0.9],
                     help="serve: Poisson arrival rates as fractions of the measured capacity")
     ap.add_argument("--workers", type=int, default=16, help="batch/serve: concurrent solves")
-    ap.add_argument("--budget-gb", type=float, default=150.0, help="batch/serve: device memory budget of the server")
-    ap.add_argument("--wave-gb", type=float, default=90.0, help="batch/serve: FP64 input memory held at once")
+    ap.add_argument("--budget-gb", type=float, default=140.0, help="batch/serve: device memory budget of the server")
+    ap.add_argument("--wave-gb", type=float, default=80.0, help="batch/serve: FP64 input memory held at once")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     if args.workload == "batch":

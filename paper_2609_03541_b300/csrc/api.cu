@@ -109,6 +109,7 @@ struct mbar_ctx {
   std::vector<double> trace;
   double t_width = 0.0, t_levels = 0.0;  // host seconds, accumulated during a solve
   cudaStream_t ust = nullptr;            // the caller's stream
+  bool graphs = true;                    // capture the binned loops into CUDA graphs
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
@@ -532,7 +533,7 @@ mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
     return MBAR_OK;
   };
   Graph g;
-  const bool use_graph = L.binned;  // unbinned launches carry timing events
+  const bool use_graph = L.binned && c->graphs;  // unbinned launches carry timing events
   if (use_graph) BUMBAR_TRY(capture(c, &g, batch));
   int64_t done_iters = 0;
   for (;;) {
@@ -893,7 +894,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   bool captured = false;
   for (int64_t round = 0; s == MBAR_OK; ++round) {
     if (rep->iters_second_loop >= o.max_sci) break;
-    const bool use_graph = cur.binned && nxt.binned;
+    const bool use_graph = cur.binned && nxt.binned && c->graphs;
     if (use_graph && !captured) {
       s = capture(c, &g, round_body);
       if (s != MBAR_OK) break;
@@ -996,6 +997,12 @@ struct StreamFence {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace bumbar {
+void ctx_set_graphs(mbar_ctx* c, bool on) {
+  if (c) c->graphs = on;
+}
+}  // namespace bumbar
+
 extern "C" {
 
 const char* mbar_status_string(mbar_status s) {

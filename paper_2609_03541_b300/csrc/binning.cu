@@ -12,6 +12,7 @@
 // (__dsub_rn/__ddiv_rn; no contraction into FMA).
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -614,6 +615,8 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
       if (st0 >= tile0) b |= 1u << 11;
       if (stl >= tile0) b |= 1u << 12;
       b |= static_cast<unsigned>(nr) << 16;
+      // the whole tile is one bin (row independent, uniform over the warp)
+      if (seg[tile0] == seg[tile_end - 1]) b |= 1u << 13;
       b0[l] = first;
       bits[l] = b;
       inv0[l] = static_cast<A>(ml.l[l].inv[first]);
@@ -636,6 +639,27 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
     for (int l = 0; l < NL; ++l) {
       const unsigned b = bits[l];
       T* out = static_cast<T*>(ml.l[l].out) + k * ml.l[l].ld_out;
+      if (__shfl_sync(0xffffffffu, b, 0) & (1u << 13)) {
+        // one bin covers the tile: a plain warp sum, written by lane 0 as
+        // the bin's mean (bin inside the tile), its opening part (carry1) or
+        // a continuation (carry0)
+        A t = A(0);
+#pragma unroll
+        for (int j = 0; j < kBmCols; ++j) t += x[j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) {
+          const int bin = b0[l];
+          const int64_t st = ml.l[l].start[bin], en = ml.l[l].start[bin + 1];
+          if (st < tile0)
+            ml.l[l].carry0[tile * K + k] = static_cast<double>(t);
+          else if (en <= tile_end)
+            out[bin] = static_cast<T>(t * inv0[l]);
+          else
+            ml.l[l].carry1[tile * K + k] = static_cast<double>(t);
+        }
+        continue;
+      }
       A head = A(0), run = A(0);
       int cur = b0[l];
       int rs = 0;  // column where the current run starts
@@ -694,6 +718,39 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
         }
       }
     }
+  }
+}
+
+// Bin means of a level with small bins (a few samples each): one thread per
+// bin and chunk of rows, summing the bin's columns in order; the bins of a
+// warp are consecutive, so its loads of one row cover consecutive columns.
+constexpr int kFineRows = 64;
+constexpr double kFineMaxMean = 32.0;  // levels with at most this many samples per bin on average
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bin_means_fine(const T* __restrict__ v, int64_t K, int64_t ld,
+                                                           const int32_t* __restrict__ start, int64_t nb,
+                                                           T* __restrict__ out, int64_t ld_out) {
+  using A = typename Acc<T>::type;
+  const int64_t b = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+  if (b >= nb) return;
+  const int64_t s = start[b], e = start[b + 1];
+  const A inv = static_cast<A>(1.0 / static_cast<double>(e - s));
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * kFineRows;
+  const int64_t k1 = (k0 + kFineRows < K) ? k0 + kFineRows : K;
+  for (int64_t k = k0; k < k1; ++k) {
+    const T* row = v + k * ld;
+    A acc = A(0);
+    int64_t c = s;
+    for (; c + 4 <= e; c += 4) {
+      const A x0 = static_cast<A>(row[c]), x1 = static_cast<A>(row[c + 1]);
+      const A x2 = static_cast<A>(row[c + 2]), x3 = static_cast<A>(row[c + 3]);
+      acc += x0;
+      acc += x1;
+      acc += x2;
+      acc += x3;
+    }
+    for (; c < e; ++c) acc += static_cast<A>(row[c]);
+    out[k * ld_out + b] = static_cast<T>(acc * inv);
   }
 }
 
@@ -891,11 +948,33 @@ mbar_status bin_means_multi(const void* v, int dtype_bytes, int64_t K, int64_t N
     return MBAR_EINVAL;
   }
   const int64_t ntiles = ceil_div(N, kBmTile);
-  MultiLevel ml{};
-  ml.L = L;
-  unsigned char* q = static_cast<unsigned char*>(tmp);
+  // levels with small bins go to bin_means_fine (its own read of v); the
+  // others share one bin_sums_multi pass
+  std::vector<int> coarse;
   for (int l = 0; l < L; ++l) {
-    LevelOut& o = ml.l[l];
+    if (static_cast<double>(N) / static_cast<double>(std::max<int64_t>(nb[l], 1)) <= kFineMaxMean) {
+      const dim3 gf(static_cast<unsigned>(ceil_div(nb[l], kThreads)), static_cast<unsigned>(ceil_div(K, kFineRows)));
+      if (dtype_bytes == 4)
+        bin_means_fine<float><<<gf, kThreads, 0, st>>>(static_cast<const float*>(v), K, ld, start[l], nb[l],
+                                                       static_cast<float*>(out[l]), ld_out[l]);
+      else
+        bin_means_fine<double><<<gf, kThreads, 0, st>>>(static_cast<const double*>(v), K, ld, start[l], nb[l],
+                                                        static_cast<double*>(out[l]), ld_out[l]);
+      count_launches(1);
+    } else {
+      coarse.push_back(l);
+    }
+  }
+  if (coarse.empty()) {
+    BUMBAR_CUDA(cudaGetLastError());
+    return MBAR_OK;
+  }
+  MultiLevel ml{};
+  ml.L = static_cast<int>(coarse.size());
+  unsigned char* q = static_cast<unsigned char*>(tmp);
+  for (int i = 0; i < ml.L; ++i) {
+    const int l = coarse[i];
+    LevelOut& o = ml.l[i];
     o.seg = seg[l];
     o.start = start[l];
     o.out = out[l];
@@ -917,7 +996,7 @@ mbar_status bin_means_multi(const void* v, int dtype_bytes, int64_t K, int64_t N
   auto launch = [&](auto tag) {
     using T = decltype(tag);
     const T* vv = static_cast<const T*>(v);
-    switch (L) {
+    switch (ml.L) {
       case 1: bin_sums_multi<T, 1><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
       case 2: bin_sums_multi<T, 2><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
       case 3: bin_sums_multi<T, 3><<<g1, kThreads, 0, st>>>(vv, K, N, ld, ml, ntiles); break;
@@ -933,7 +1012,7 @@ mbar_status bin_means_multi(const void* v, int dtype_bytes, int64_t K, int64_t N
   else
     launch(double{});
   count_launches(1);
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < ml.L; ++l) {
     const LevelOut& o = ml.l[l];
     if (dtype_bytes == 4)
       bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, o.seg, o.start, o.inv, static_cast<float*>(o.out), o.ld_out,

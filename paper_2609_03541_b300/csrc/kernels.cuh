@@ -146,7 +146,11 @@ size_t overlap_tc_tmp_bytes(int64_t K, int64_t n);
 // 1 = CUDA cores, 2 = tensor cores.
 void set_hessian_path(int path);
 int hessian_path_for(int64_t K);
-bool tc_cluster_enabled();  // false: tensor-core path without the cluster variant
+bool tc_cluster_enabled();
+// Direct launches instead of captured CUDA graphs for a context's binned
+// loops (server workers: a stream capture in one thread would make another
+// thread's device-wide synchronisation fail).
+void ctx_set_graphs(mbar_ctx* c, bool on);  // false: tensor-core path without the cluster variant
 
 // ---- dense FP64 (cholesky.cu) ----
 // Solves A x = b for the (m x m) symmetric positive definite block

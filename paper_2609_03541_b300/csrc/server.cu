@@ -112,6 +112,9 @@ struct mbar_server {
   void run_one(Request& r, cudaStream_t st) {
     mbar_ctx* ctx = nullptr;
     mbar_status s = mbar_create(&ctx, r.K, r.N, r.Nk.data(), r.u, r.u_on_device, &cfg.opts, st);
+    // no stream capture on worker threads: the caller's other threads may
+    // synchronise the whole device at any time
+    if (s == MBAR_OK) ctx_set_graphs(ctx, false);
     if (s == MBAR_OK && r.phi) s = mbar_set_coordinate(ctx, r.phi, r.phi_on_device);
     if (s == MBAR_OK || s == MBAR_ENOTCONV) {
       if (s == MBAR_OK) s = mbar_solve(ctx, nullptr, &r.report);

@@ -330,7 +330,7 @@ def test_lse_pass_stateless(dtype):
     assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - O.log_denominator(u, f, Nk))) < tol * 100
 
 
-@pytest.mark.parametrize("case", ["gaussian", "umbrella_h0"])
+@pytest.mark.parametrize("case", ["gaussian", "umbrella_h0", "harmonic_wide"])
 def test_algorithm1_trajectory_matches_oracle_fp64(case):
     """Every Eq. 3 check of the second loop (level size, s_n, s_next) and the
     end of the first loop agree with the oracle's run: the binned levels,
@@ -340,10 +340,15 @@ def test_algorithm1_trajectory_matches_oracle_fp64(case):
         p = W.gaussian_overlap(M=12, N_0=2000, seed=4)
         opts = O.BUOptions()
         o = M.default_opts(M.MBAR_FP64)
-    else:
+    elif case == "umbrella_h0":
         p = W.umbrella(K=16, N_k=1000, seed=1, grid_points=1 << 13)
         opts = O.BUOptions(h0=0.1)
         o = M.default_opts(M.MBAR_FP64, h0=0.1)
+    else:   # 80 000 samples: single-bin tiles at 100 bins, boundaries at 1000, small bins at 10 000
+        p = W.harmonic(K=4, d=1, N_k=20000, seed=9)
+        p.phi = p.u_kn[0].copy()
+        opts = O.BUOptions()
+        o = M.default_opts(M.MBAR_FP64)
     tr = []
     O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, opts=opts, trace=tr)
     ctx = M.Context(p.u_kn, p.N_k, M.MBAR_FP64, opts=o)
@@ -357,8 +362,11 @@ def test_algorithm1_trajectory_matches_oracle_fp64(case):
     g2 = [r for r in gt if r[0] == 2]
     assert len(g1) == 1 and int(g1[0][3]) == len(ph1)
     assert g1[0][2] == pytest.approx(ph1[-1][2], rel=1e-6)
-    assert len(g2) == len(ph2) and len(g2) >= 2
+    assert len(g2) == len(ph2) and len(g2) >= 1
     for r, t in zip(g2, ph2):
         assert int(r[1]) == t[1]
-        assert r[2] == pytest.approx(t[2], rel=1e-6, abs=1e-15)
-        assert r[3] == pytest.approx(t[3], rel=1e-6, abs=1e-15)
+        for a, b in ((r[2], t[2]), (r[3], t[3])):
+            if b > 1e-9:
+                assert a == pytest.approx(b, rel=1e-6)
+            else:   # a converged level: both at the FP64 rounding floor
+                assert a < 1e-9

@@ -104,3 +104,21 @@ def test_batch_solve_matches_the_oracle_and_the_single_solves(prec):
     for f, (u, nk, phi, f_ref) in zip(fs, mix):
         assert np.max(np.abs(f - f_ref)) < TOL[prec]
         assert np.array_equal(f, _alone(u, nk, phi, prec))
+
+
+def test_server_tolerates_device_synchronisation_by_other_threads():
+    """Workers never capture streams, so the caller's device-wide syncs
+    (e.g. torch.cuda.synchronize while drawing the next inputs) do not fail
+    and do not disturb the solves."""
+    import torch
+    mix = _mix()
+    with M.Server(M.server_config(workers=4, hbm_budget_bytes=8 << 30)) as srv:
+        ids = [srv.submit(u, nk, phi) for u, nk, phi, _ in mix]
+        for _ in range(200):
+            torch.cuda.synchronize()
+            x = torch.ones(1 << 16, device="cuda")
+            torch.cuda.synchronize()
+            del x
+        out = [srv.wait(i) for i in ids]
+    for (f, _, _, _), (_, _, _, f_ref) in zip(out, mix):
+        assert np.max(np.abs(f - f_ref)) < TOL[M.MBAR_MIXED]
