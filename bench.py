@@ -634,6 +634,27 @@ def main():
                     "fp64_gpu_solve_s": t_fp64,
                     "mixed_speedup_vs_fp64_gpu": t_fp64 / (ms_per_step / 1e3)}
 
+    # ---- reweighting to a target state (Eqs. 5-6), outside the timed region ----
+    rew = None
+    if rank == 0 and not args.no_accuracy:
+        ctx = M.Context(u_dev, Nk, prec, opts=opts, stream=stream.cuda_stream)
+        if phi_dev is not None:
+            ctx.set_coordinate(phi_dev)
+        ctx.solve()
+        u0 = u_dev[prob["K"] // 2].contiguous()
+        ctx.reweight(u0)                                  # warm-up
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        reps = 5
+        for _ in range(reps):
+            pw, logc = ctx.reweight(u0)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t1) / reps
+        ctx.close()
+        rew = {"target": "state K/2", "ms_per_call": dt * 1e3, "samples_per_s": prob["N"] / dt,
+               "sum_p": float(pw.sum()),
+               "note": "one unbinned LSE pass + weights, N doubles copied to the host per call"}
+
     # ---- roofline of the dominant kernel (unbinned fused LSE pass) ----
     peaks, peaks_src = load_peaks()
     n_l, ms_l, by_l = acc.get(0, [0, 0.0, 0.0])
@@ -659,6 +680,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32" if prec == M.MBAR_MIXED else "f64", "data": "synthetic",
                 "config": config, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                 "latency": latency, "hessian": hess, "cpu_baseline": cpu, "clocks": clocks, "accuracy": accuracy,
+                "reweight": rew,
                 "report": rep.as_dict()}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -189,6 +189,29 @@ BUMBAR_API mbar_status mbar_newton_step(mbar_ctx* ctx, const double* f_in, doubl
  * report (host, nullable). ENOTCONV: limit reached, f still readable. */
 BUMBAR_API mbar_status mbar_solve(mbar_ctx* ctx, const double* f_init, mbar_report* report);
 
+/* Eqs. 5-6: statistical weight of every sample at a target state whose
+ * reduced potential is u0_n (beta_0 E_n in the paper), at the context's
+ * current free energies, over the unbinned samples:
+ *   p_n = (1/C) exp(-u0_n) / sum_m N_m exp(f_m - u_mn),
+ *   C   = sum_n exp(-u0_n) / sum_m N_m exp(f_m - u_mn).
+ * u0 (N finite FP64, host or device per u0_on_device) and p_out (host
+ * FP64[N], nullable) are in the caller's original sample order; log_C
+ * (nullable) receives log C. The weights stay on the device for
+ * mbar_weighted_histogram2d. EINVAL for non-finite u0. */
+BUMBAR_API mbar_status mbar_reweight(mbar_ctx* ctx, const double* u0, int32_t u0_on_device, double* p_out,
+                                     double* log_C);
+
+/* Histogram of the last mbar_reweight weights over per-sample coordinates
+ * (x_n, y_n) (original order, host or device per on_device): bin
+ * (floor((x - x0)/dx), floor((y - y0)/dy)), each subtraction and division
+ * rounded to nearest in binary64, kept when inside nx x ny; out (host FP64
+ * nx*ny, row-major by x bin) receives the summed weights (the paper's Fig. 1
+ * plots -log of this over two dihedral angles). ESTATE before any
+ * mbar_reweight; EINVAL for dx, dy <= 0 or nx, ny < 1. */
+BUMBAR_API mbar_status mbar_weighted_histogram2d(mbar_ctx* ctx, const double* x, const double* y, int32_t on_device,
+                                                 double x0, double dx, int64_t nx, double y0, double dy, int64_t ny,
+                                                 double* out);
+
 /* Copies the current free energies (gauge f_0 = 0) to f_out (host[K]). */
 BUMBAR_API mbar_status mbar_free_energies(mbar_ctx* ctx, double* f_out);
 

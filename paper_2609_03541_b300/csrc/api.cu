@@ -110,6 +110,7 @@ struct mbar_ctx {
   double t_width = 0.0, t_levels = 0.0;  // host seconds, accumulated during a solve
   cudaStream_t ust = nullptr;            // the caller's stream
   bool graphs = true;                    // capture the binned loops into CUDA graphs
+  double* weights = nullptr;             // last mbar_reweight weights (original sample order)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
@@ -1489,6 +1490,96 @@ mbar_status mbar_solve(mbar_ctx* c, const double* f_init, mbar_report* report) {
   return s2;
 }
 
+// Eqs. 5-6 at the context's current f on the unbinned data.
+mbar_status mbar_reweight(mbar_ctx* c, const double* u0, int32_t u0_on_device, double* p_out, double* log_C) {
+  CHECK_CTX(c);
+  if (!u0) {
+    set_error("mbar_reweight: u0 is NULL");
+    return MBAR_EINVAL;
+  }
+  cudaGetLastError();
+  StreamFence fence(c);
+  const int64_t N = c->N;
+  double* u0_dev = nullptr;
+  void* tmp = nullptr;
+  double* logc_dev = nullptr;
+  mbar_status s = MBAR_OK;
+  if (!c->weights) s = dalloc_t(c, &c->weights, N);
+  if (s == MBAR_OK) s = dalloc(c, &tmp, reweight_tmp_bytes(N));
+  if (s == MBAR_OK) s = dalloc_t(c, &logc_dev, 1);
+  const double* u0d = u0;
+  if (s == MBAR_OK && !u0_on_device) {
+    s = dalloc_t(c, &u0_dev, N);
+    if (s == MBAR_OK && cudaMemcpyAsync(u0_dev, u0, N * sizeof(double), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      s = cuda_status(cudaGetLastError(), "mbar_reweight: copy of u0");
+    u0d = u0_dev;
+  }
+  int bad = 0;
+  if (s == MBAR_OK) s = cudaMemsetAsync(c->bad, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
+  if (s == MBAR_OK) s = check_finite(u0d, N, c->bad, c->st);
+  if (s == MBAR_OK && (cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+                       cudaStreamSynchronize(c->st) != cudaSuccess))
+    s = MBAR_ECUDA;
+  if (s == MBAR_OK && bad) {
+    set_error("mbar_reweight: u0 has non-finite entries");
+    s = MBAR_EINVAL;
+  }
+  if (s == MBAR_OK) s = run_lse(c, c->full, c->f, kLseModePass, nullptr, nullptr, nullptr, 0.0, 0, c->logden);
+  if (s == MBAR_OK)
+    s = reweight_weights(u0d, c->perm, c->logden, c->dtype, c->cshift, N, c->weights, logc_dev, tmp,
+                         reweight_tmp_bytes(N), c->st);
+  double logc = 0.0;
+  if (s == MBAR_OK && p_out &&
+      cudaMemcpyAsync(p_out, c->weights, N * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "mbar_reweight: copy of p");
+  if (s == MBAR_OK && cudaMemcpyAsync(&logc, logc_dev, sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "mbar_reweight: copy of log C");
+  if (s == MBAR_OK) s = read_status(c);  // syncs
+  if (s == MBAR_OK && log_C) *log_C = logc;
+  dfree(c, u0_dev);
+  dfree(c, tmp);
+  dfree(c, logc_dev);
+  return s;
+}
+
+mbar_status mbar_weighted_histogram2d(mbar_ctx* c, const double* x, const double* y, int32_t on_device, double x0,
+                                      double dx, int64_t nx, double y0, double dy, int64_t ny, double* out) {
+  CHECK_CTX(c);
+  if (!x || !y || !out || !(dx > 0.0) || !(dy > 0.0) || nx < 1 || ny < 1 || nx * ny > (int64_t(1) << 31)) {
+    set_error("mbar_weighted_histogram2d: bad arguments");
+    return MBAR_EINVAL;
+  }
+  if (!c->weights) {
+    set_error("mbar_weighted_histogram2d: call mbar_reweight first");
+    return MBAR_ESTATE;
+  }
+  cudaGetLastError();
+  StreamFence fence(c);
+  const int64_t N = c->N;
+  double *xd = nullptr, *yd = nullptr, *hd = nullptr;
+  mbar_status s = dalloc_t(c, &hd, nx * ny);
+  const double* xs = x;
+  const double* ys = y;
+  if (s == MBAR_OK && !on_device) {
+    s = dalloc_t(c, &xd, N);
+    if (s == MBAR_OK) s = dalloc_t(c, &yd, N);
+    if (s == MBAR_OK && (cudaMemcpyAsync(xd, x, N * 8, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+                         cudaMemcpyAsync(yd, y, N * 8, cudaMemcpyHostToDevice, c->st) != cudaSuccess))
+      s = cuda_status(cudaGetLastError(), "mbar_weighted_histogram2d: copy of x, y");
+    xs = xd;
+    ys = yd;
+  }
+  if (s == MBAR_OK) s = weighted_hist2d(xs, ys, c->weights, N, x0, dx, nx, y0, dy, ny, hd, c->st);
+  if (s == MBAR_OK &&
+      cudaMemcpyAsync(out, hd, static_cast<size_t>(nx) * ny * 8, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    s = cuda_status(cudaGetLastError(), "mbar_weighted_histogram2d: copy of the histogram");
+  if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "sync");
+  dfree(c, xd);
+  dfree(c, yd);
+  dfree(c, hd);
+  return s;
+}
+
 mbar_status mbar_free_energies(mbar_ctx* c, double* f_out) {
   CHECK_CTX(c);
   if (!f_out) {
@@ -1570,7 +1661,7 @@ mbar_status mbar_destroy(mbar_ctx* c) {
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   level_free(c, &c->cur);
-  void* ptrs[] = {c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->d_pairs, c->f,
+  void* ptrs[] = {c->weights, c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->d_pairs, c->f,
                   c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->stat,
                   c->hess, c->delta,  c->info,  c->bad,    c->logden,  c->scratch,    c->seg,
                   c->start, c->count, c->nb_dev};

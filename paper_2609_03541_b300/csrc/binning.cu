@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
 // bin and chunk of rows, summing the bin's columns in order; the bins of a
 // warp are consecutive, so its loads of one row cover consecutive columns.
 constexpr int kFineRows = 64;
-constexpr double kFineMaxMean = 32.0;  // levels with at most this many samples per bin on average
+constexpr double kFineMaxMean = 4.0;  // levels with at most this many samples per bin on average
 template <typename T>
 __global__ void __launch_bounds__(kThreads) bin_means_fine(const T* __restrict__ v, int64_t K, int64_t ld,
                                                            const int32_t* __restrict__ start, int64_t nb,
@@ -737,19 +737,27 @@ __global__ void __launch_bounds__(kThreads) bin_means_fine(const T* __restrict__
   const A inv = static_cast<A>(1.0 / static_cast<double>(e - s));
   const int64_t k0 = static_cast<int64_t>(blockIdx.y) * kFineRows;
   const int64_t k1 = (k0 + kFineRows < K) ? k0 + kFineRows : K;
-  for (int64_t k = k0; k < k1; ++k) {
+  int64_t k = k0;
+  for (; k + 4 <= k1; k += 4) {  // four rows at a time: their loads are in flight together
+    const T* r0 = v + k * ld;
+    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0);
+    for (int64_t c = s; c < e; ++c) {
+      const A x0 = static_cast<A>(r0[c]), x1 = static_cast<A>(r0[ld + c]);
+      const A x2 = static_cast<A>(r0[2 * ld + c]), x3 = static_cast<A>(r0[3 * ld + c]);
+      a0 += x0;
+      a1 += x1;
+      a2 += x2;
+      a3 += x3;
+    }
+    out[k * ld_out + b] = static_cast<T>(a0 * inv);
+    out[(k + 1) * ld_out + b] = static_cast<T>(a1 * inv);
+    out[(k + 2) * ld_out + b] = static_cast<T>(a2 * inv);
+    out[(k + 3) * ld_out + b] = static_cast<T>(a3 * inv);
+  }
+  for (; k < k1; ++k) {
     const T* row = v + k * ld;
     A acc = A(0);
-    int64_t c = s;
-    for (; c + 4 <= e; c += 4) {
-      const A x0 = static_cast<A>(row[c]), x1 = static_cast<A>(row[c + 1]);
-      const A x2 = static_cast<A>(row[c + 2]), x3 = static_cast<A>(row[c + 3]);
-      acc += x0;
-      acc += x1;
-      acc += x2;
-      acc += x3;
-    }
-    for (; c < e; ++c) acc += static_cast<A>(row[c]);
+    for (int64_t c = s; c < e; ++c) acc += static_cast<A>(row[c]);
     out[k * ld_out + b] = static_cast<T>(acc * inv);
   }
 }
@@ -793,9 +801,9 @@ __global__ void bin_sums_fixup(int64_t K, const int32_t* __restrict__ seg, const
 }
 
 // out[k][i] = in[k][perm[i]]: each thread loads perm[i] once and moves it
-// for 8 rows; blocks run row-group major so the 8 input rows being gathered
-// stay in L2.
-constexpr int kGatherRows = 8;
+// for kGatherRows rows; blocks run row-group major so the input rows being
+// gathered (and the output rows being written) stay in L2 together.
+constexpr int kGatherRows = 4;
 template <typename T>
 __global__ void gather_cols_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t K, int64_t N, int64_t ld,
                                    const int32_t* __restrict__ perm) {

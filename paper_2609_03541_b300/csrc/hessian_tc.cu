@@ -372,13 +372,16 @@ __global__ void reduce_tc(const float* __restrict__ part, const TcCta* __restric
 // release at cluster scope), waits for its own pfull (all writers done) and
 // issues the MMAs. Every wait is bounded; a CTA that gives up records an
 // error and still reaches the final cluster barrier.
-constexpr int kClThreads = 512;
-constexpr int kClVStages = 3;
+constexpr int kClThreads = 512;                // threads that build P~ (16 warps)
+constexpr int kClThreadsAll = kClThreads + 32;  // + one warp that issues the MMAs
+constexpr int kClVStages = 2;
+constexpr int kClPStages = 3;                 // P~ stages (chunks in flight between producers and MMAs)
 constexpr int kClVStageBytes = 128 * 64 * 4;  // two 32-column 128B-swizzled boxes
 constexpr int kClPSlots = 3;
 constexpr int kClPSlotBytes = 128 * 128;      // one FP16 128 x 64 tile
 constexpr int kClPStageBytes = kClPSlots * kClPSlotBytes;
 constexpr int kClMaxTiles = 4;                // MT <= 4, i.e. K <= 512
+constexpr int kClColRing = 4;                 // chunks of per-sample columns staged ahead (3 ahead)
 
 __host__ __device__ inline int cl_dmax(int q, int MT) {
   return (MT - 1) / 2 + ((MT % 2 == 0 && q < MT / 2) ? 1 : 0);
@@ -467,19 +470,40 @@ __device__ __forceinline__ void umma_commit_multicast(uint64_t* bar, uint16_t ma
       : "memory");
 }
 
-__global__ void __launch_bounds__(kClThreads, 1)
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kClThreads) : "memory"); }
+// Barrier of the producer warps that also ORs a flag over them: every
+// producer gets the same answer (they all leave the loop together).
+__device__ __forceinline__ bool producers_sync_or(bool v) {
+  uint32_t res;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(res)
+      : "r"(static_cast<uint32_t>(v)), "n"(kClThreads)
+      : "memory");
+  return res != 0;
+}
+
+__global__ void __launch_bounds__(kClThreadsAll, 1)
     overlap_tc_cluster_kernel(const __grid_constant__ CUtensorMap tmap, ClParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   unsigned char* vbuf = smem;
   unsigned char* pbuf = smem + kClVStages * kClVStageBytes;
-  uint64_t* vfull = reinterpret_cast<uint64_t*>(pbuf + 2 * kClPStageBytes);  // [3]
-  uint64_t* pfull = vfull + kClVStages;                                        // [2]
-  uint64_t* pempty = pfull + 2;                                                // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pempty + 2);
+  uint64_t* vfull = reinterpret_cast<uint64_t*>(pbuf + kClPStages * kClPStageBytes);  // [kClVStages]
+  uint64_t* pfull = vfull + kClVStages;                                                 // [kClPStages]
+  uint64_t* pempty = pfull + kClPStages;                                                // [kClPStages]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pempty + kClPStages);
+  volatile int* fail_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // per-sample log2(logden) and sqrt(H) of the chunks ahead: [kClColRing][64] each
+  float* l2_ring = reinterpret_cast<float*>(pbuf + kClPStages * kClPStageBytes + 128);
+  float* sh_ring = l2_ring + kClColRing * 64;
 
   const int tid = threadIdx.x;
+  const bool producer = tid < kClThreads;
   const int warp = tid >> 5, lane = tid & 31;
   const int MT = p.MT;
   const int r = static_cast<int>(cluster_ctarank());
@@ -501,10 +525,11 @@ __global__ void __launch_bounds__(kClThreads, 1)
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   if (tid == 0) {
     for (int s = 0; s < kClVStages; ++s) mbar_init(&vfull[s], 1);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kClPStages; ++b) {
       mbar_init(&pfull[b], static_cast<uint32_t>(dm + 1));
       mbar_init(&pempty[b], static_cast<uint32_t>(nreaders));
     }
+    *fail_s = 0;
     fence_barrier_init();
     prefetch_tmap(&tmap);
   }
@@ -515,7 +540,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int row = r * 128 + lr0 + 64 * u;
-    a2r[u] = row < p.K ? static_cast<float>(p.a[row] * 1.4426950408889634) : -INFINITY;
+    a2r[u] = (producer && row < p.K) ? static_cast<float>(p.a[row] * 1.4426950408889634) : -INFINITY;
   }
   tc_fence_before();
   cluster_sync_all();  // barrier initialisation visible to the peers
@@ -536,102 +561,126 @@ __global__ void __launch_bounds__(kClThreads, 1)
   }
   issued = nchunks < kClVStages ? nchunks : kClVStages;
 
-  auto load_cols = [&](int64_t c, float* l2, float* sh) {
-    const int64_t col0 = c_begin + c * 64 + g * 8;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int64_t col = col0 + j;
+  // threads 0..63 stage chunk c's per-sample columns into ring slot c % kClColRing
+  auto stage_cols = [&](int64_t c) {
+    if (tid < 64) {
+      const int64_t col = c_begin + c * 64 + tid;
+      float l2 = INFINITY, sh = 0.f;  // padding samples contribute nothing
       if (col < c_end) {
-        l2[j] = p.logden[col] * kLog2e;
-        sh[j] = p.H ? sqrtf(static_cast<float>(p.H[col])) : 1.f;
-      } else {
-        l2[j] = INFINITY;  // padding samples contribute nothing
-        sh[j] = 0.f;
+        l2 = p.logden[col] * kLog2e;
+        sh = p.H ? sqrtf(static_cast<float>(p.H[col])) : 1.f;
       }
+      const int slot = static_cast<int>(c % kClColRing);
+      l2_ring[slot * 64 + tid] = l2;
+      sh_ring[slot * 64 + tid] = sh;
     }
   };
-  float l2n[8], shn[8];
-  if (nchunks > 0) load_cols(0, l2n, shn);
   constexpr uint32_t idesc = idesc_f16(128, 128);
-  bool failed = false;
-  bool t0_failed = false;  // thread 0 gave up on a pfull wait
   int64_t c = 0;
-  for (; c < nchunks; ++c) {
-    const int s = static_cast<int>(c % kClVStages);
-    const int b = static_cast<int>(c & 1);
-    bool ok = mbar_wait_timed(&vfull[s], static_cast<uint32_t>((c / kClVStages) & 1), kMaxSpins);
-    if (ok && c >= 2) ok = mbar_wait_cluster_bounded(&pempty[b], static_cast<uint32_t>(((c - 2) >> 1) & 1), kMaxSpins);
-    if (__syncthreads_or(!ok || t0_failed)) {
-      failed = true;
-      break;
-    }
-    float l2[8], sh[8];
+  if (producer) {
+    // producers: v tile in, P~ out to this CTA and its readers, then the
+    // readers' pfull barriers; they never wait for the MMA warp directly
+    for (int64_t cc = 0; cc < nchunks && cc < kClColRing - 1; ++cc) stage_cols(cc);
+    for (; c < nchunks; ++c) {
+      const int s = static_cast<int>(c % kClVStages);
+      const int b = static_cast<int>(c % kClPStages);
+      bool ok = mbar_wait_timed(&vfull[s], static_cast<uint32_t>((c / kClVStages) & 1), kMaxSpins);
+      if (ok && c >= kClPStages)
+        ok = mbar_wait_cluster_bounded(&pempty[b], static_cast<uint32_t>(((c - kClPStages) / kClPStages) & 1),
+                                       kMaxSpins);
+      if (producers_sync_or(!ok || *fail_s != 0)) {
+        *fail_s = 1;
+        break;
+      }
+      // chunk c's columns were staged three chunks ago (ordered by the
+      // producer barriers since); stage chunk c + 3 into the slot chunk c - 1 used
+      float l2[8], sh[8];
+      {
+        const int slot = static_cast<int>(c % kClColRing);
+        const float4 a0 = *reinterpret_cast<const float4*>(l2_ring + slot * 64 + g * 8);
+        const float4 a1 = *reinterpret_cast<const float4*>(l2_ring + slot * 64 + g * 8 + 4);
+        const float4 b0 = *reinterpret_cast<const float4*>(sh_ring + slot * 64 + g * 8);
+        const float4 b1 = *reinterpret_cast<const float4*>(sh_ring + slot * 64 + g * 8 + 4);
+        l2[0] = a0.x; l2[1] = a0.y; l2[2] = a0.z; l2[3] = a0.w;
+        l2[4] = a1.x; l2[5] = a1.y; l2[6] = a1.z; l2[7] = a1.w;
+        sh[0] = b0.x; sh[1] = b0.y; sh[2] = b0.z; sh[3] = b0.w;
+        sh[4] = b1.x; sh[5] = b1.y; sh[6] = b1.z; sh[7] = b1.w;
+      }
+      if (c + kClColRing - 1 < nchunks) stage_cols(c + kClColRing - 1);
+      const unsigned char* vb = vbuf + s * kClVStageBytes + (g >> 2) * (kClVStageBytes / 2);
+      unsigned char* pst = pbuf + b * kClPStageBytes;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      l2[j] = l2n[j];
-      sh[j] = shn[j];
-    }
-    if (c + 1 < nchunks) load_cols(c + 1, l2n, shn);
-    const unsigned char* vb = vbuf + s * kClVStageBytes + (g >> 2) * (kClVStageBytes / 2);
-    unsigned char* pst = pbuf + b * kClPStageBytes;
+      for (int u = 0; u < 2; ++u) {
+        const int lr = lr0 + 64 * u;
+        const float4 x0 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2));
+        const float4 x1 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2 + 1));
+        const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        float pv[8];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int lr = lr0 + 64 * u;
-      const float4 x0 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2));
-      const float4 x1 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2 + 1));
-      const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-      float pv[8];
+        for (int j = 0; j < 8; ++j) pv[j] = ex2_approx(fmaf(-x[j], kLog2e, a2r[u]) - l2[j]) * sh[j];
+        uint4 packed;
+        packed.x = pack_half2(pv[0], pv[1]);
+        packed.y = pack_half2(pv[2], pv[3]);
+        packed.z = pack_half2(pv[4], pv[5]);
+        packed.w = pack_half2(pv[6], pv[7]);
+        const uint32_t off = static_cast<uint32_t>(lr * 128 + ((g ^ (lr & 7)) << 4));
 #pragma unroll
-      for (int j = 0; j < 8; ++j) pv[j] = ex2_approx(fmaf(-x[j], kLog2e, a2r[u]) - l2[j]) * sh[j];
-      uint4 packed;
-      packed.x = pack_half2(pv[0], pv[1]);
-      packed.y = pack_half2(pv[2], pv[3]);
-      packed.z = pack_half2(pv[4], pv[5]);
-      packed.w = pack_half2(pv[6], pv[7]);
-      const uint32_t off = static_cast<uint32_t>(lr * 128 + ((g ^ (lr & 7)) << 4));
-#pragma unroll
-      for (int q = 0; q < kClMaxTiles; ++q) {
-        if (reader_mask & (1u << q)) {
-          const int slot = (r - q + MT) % MT;
-          if (q == r)
-            *reinterpret_cast<uint4*>(pst + off) = packed;  // own tile: slot 0
-          else
-            st_cluster_v4(mapa_shared(smem_u32(pst + slot * kClPSlotBytes) + off, static_cast<uint32_t>(q)),
-                          packed);
+        for (int q = 0; q < kClMaxTiles; ++q) {
+          if (reader_mask & (1u << q)) {
+            const int slot = (r - q + MT) % MT;
+            if (q == r)
+              *reinterpret_cast<uint4*>(pst + off) = packed;  // own tile: slot 0
+            else
+              st_cluster_v4(mapa_shared(smem_u32(pst + slot * kClPSlotBytes) + off, static_cast<uint32_t>(q)),
+                            packed);
+          }
         }
       }
-    }
-    fence_proxy_async_all();
-    __syncthreads();
-    if (tid == 0) {
-      if (c + kClVStages < nchunks) {
-        issue_v(c + kClVStages);  // every thread is past its reads of this stage
+      fence_proxy_async_all();
+      producers_sync();
+      if (tid == 0) {
+        if (c + kClVStages < nchunks) issue_v(c + kClVStages);  // every producer is past this stage
+        for (int q = 0; q < MT; ++q)
+          if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
       }
-      for (int q = 0; q < MT; ++q)
-        if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
-      if (mbar_wait_cluster_bounded(&pfull[b], static_cast<uint32_t>((c >> 1) & 1), kMaxSpins)) {
+      if (c + kClVStages < nchunks) ++issued;
+    }
+  } else {
+    // MMA warp: waits until every writer has delivered chunk c, issues the
+    // UMMAs and commits them to the writers' pempty barriers
+    for (int64_t cm = 0; cm < nchunks; ++cm) {
+      const int b = static_cast<int>(cm % kClPStages);
+      bool ok = true;
+      if (lane == 0)
+        ok = mbar_wait_cluster_bounded(&pfull[b], static_cast<uint32_t>((cm / kClPStages) & 1), kMaxSpins);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || *fail_s) {
+        if (lane == 0) *fail_s = 1;
+        break;
+      }
+      if (lane == 0) {
         tc_fence_after();
-        const uint32_t base = smem_u32(pst);
+        const uint32_t base = smem_u32(pbuf + b * kClPStageBytes);
         for (int t = 0; t < ntl; ++t) {
 #pragma unroll
           for (int k4 = 0; k4 < 4; ++k4)
             umma_f16(tmem + static_cast<uint32_t>(t * 128), sdesc_sw128(base + k4 * 32),
                      sdesc_sw128(base + static_cast<uint32_t>(t * kClPSlotBytes) + k4 * 32), idesc,
-                     (c > 0 || k4 > 0) ? 1u : 0u);
+                     (cm > 0 || k4 > 0) ? 1u : 0u);
         }
         umma_commit_multicast(&pempty[b], writer_mask);
-      } else {
-        t0_failed = true;
       }
+      __syncwarp();
     }
-    if (c + kClVStages < nchunks) ++issued;
   }
-  if (__syncthreads_or(t0_failed)) failed = true;
+  __syncthreads();
+  bool failed = *fail_s != 0;
   if (!failed && nchunks > 0) {
     // the last commits of every reader of this tile (they include this CTA's)
     bool ok = true;
-    for (int64_t last = nchunks - 1; last >= 0 && last >= nchunks - 2; --last)
-      ok = ok && mbar_wait_cluster_bounded(&pempty[last & 1], static_cast<uint32_t>((last >> 1) & 1), kMaxSpins);
+    for (int64_t last = nchunks - 1; last >= 0 && last >= nchunks - kClPStages; --last)
+      ok = ok && mbar_wait_cluster_bounded(&pempty[last % kClPStages], static_cast<uint32_t>((last / kClPStages) & 1),
+                                           kMaxSpins);
     if (__syncthreads_or(!ok)) failed = true;
   }
   if (failed) {
@@ -650,7 +699,7 @@ __global__ void __launch_bounds__(kClThreads, 1)
   const int sub = warp & 3;
   const int quarter = warp >> 2;
   const int row_local = sub * 32 + lane;
-  for (int c0 = quarter * 32; c0 < ntl * 128; c0 += 128) {
+  for (int c0 = quarter * 32; producer && c0 < ntl * 128; c0 += 128) {
     float rr[32];
     if (nchunks > 0 && !failed) {
       tmem_ld32(tmem + (static_cast<uint32_t>(sub * 32) << 16) + static_cast<uint32_t>(c0), rr);
@@ -695,7 +744,8 @@ __global__ void reduce_tc_cluster(const float* __restrict__ part, int S, int T, 
 }
 
 size_t tc_cluster_smem() {
-  return static_cast<size_t>(kClVStages) * kClVStageBytes + 2 * static_cast<size_t>(kClPStageBytes) + 64 + 1024;
+  return static_cast<size_t>(kClVStages) * kClVStageBytes + static_cast<size_t>(kClPStages) * kClPStageBytes + 128 +
+         2 * kClColRing * 64 * sizeof(float) + 1024;
 }
 
 struct ClPlan {
@@ -764,7 +814,7 @@ int max_active_clusters(int MT) {
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(MT * num_sms()));
-    cfg.blockDim = dim3(kClThreads);
+    cfg.blockDim = dim3(kClThreadsAll);
     cfg.dynamicSmemBytes = tc_cluster_smem();
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -843,7 +893,7 @@ static mbar_status overlap_tc_cluster(const void* v, int64_t K, int64_t n, int64
   const size_t smem = tc_cluster_smem();
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(pl.S * pl.MT));
-  cfg.blockDim = dim3(kClThreads);
+  cfg.blockDim = dim3(kClThreadsAll);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

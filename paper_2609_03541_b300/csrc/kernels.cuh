@@ -150,7 +150,17 @@ bool tc_cluster_enabled();
 // Direct launches instead of captured CUDA graphs for a context's binned
 // loops (server workers: a stream capture in one thread would make another
 // thread's device-wide synchronisation fail).
-void ctx_set_graphs(mbar_ctx* c, bool on);  // false: tensor-core path without the cluster variant
+void ctx_set_graphs(mbar_ctx* c, bool on);
+
+// Eqs. 5-6 (reweight.cu): p (original sample order) and log C from the
+// target potential u0 (original order), the LSE pass's logden (stored order,
+// dtype of the data) and the per-sample shift (nullable).
+size_t reweight_tmp_bytes(int64_t N);
+mbar_status reweight_weights(const double* u0, const int32_t* perm, const void* logden, int dtype_bytes,
+                             const double* shift, int64_t N, double* p, double* log_c, void* tmp, size_t tmp_bytes,
+                             cudaStream_t st);
+mbar_status weighted_hist2d(const double* x, const double* y, const double* p, int64_t N, double x0, double dx,
+                            int64_t nx, double y0, double dy, int64_t ny, double* out, cudaStream_t st);  // false: tensor-core path without the cluster variant
 
 // ---- dense FP64 (cholesky.cu) ----
 // Solves A x = b for the (m x m) symmetric positive definite block

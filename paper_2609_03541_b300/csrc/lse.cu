@@ -533,6 +533,18 @@ size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes) {
 }
 
 mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream) {
+  // same shared-memory carveout as the pass kernels it alternates with, so the
+  // SMs need not repartition L1 / shared memory between the two launches
+  static bool carveout = false;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (!carveout) {
+      cudaFuncSetAttribute(lse_epilogue_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           static_cast<int>(cudaSharedmemCarveoutMaxShared));
+      cudaGetLastError();
+      carveout = true;
+    }
+  }
   lse_epilogue_kernel<<<static_cast<unsigned>(ceil_div(prm.K, kEpiWarps)), 32 * kEpiWarps, 0, stream>>>(prm);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());

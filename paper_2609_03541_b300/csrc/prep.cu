@@ -28,6 +28,50 @@ __device__ __forceinline__ double from_ordered(unsigned long long k) {
   return __longlong_as_double(static_cast<long long>(b));
 }
 
+// Binary64 -> binary32 with round-to-nearest-even using integer operations
+// only (the FP64 pipe is the bottleneck of this kernel): keep the top 23 of
+// the 52 fraction bits and round on the 29 dropped ones; a carry out of the
+// fraction moves into the exponent (up to infinity), as IEEE rounding does.
+// Results that would be subnormal or zero in binary32 take the hardware
+// conversion (rare for shifted energies).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long d = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned int hi = static_cast<unsigned int>(d >> 32), lo = static_cast<unsigned int>(d);
+  const int e = static_cast<int>((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (e <= 0 || e >= 255) return __double2float_rn(x);  // zero, subnormal, overflow, inf/nan
+  const unsigned int sign = hi & 0x80000000u;
+  const unsigned int mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 fraction bits
+  const unsigned int rest = lo & 0x1FFFFFFFu;                     // the 29 dropped bits
+  const unsigned int half = 0x10000000u;
+  const unsigned int up = (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
+  const unsigned int bits = ((static_cast<unsigned int>(e) << 23) | mant) + up;
+  return __uint_as_float(sign | bits);
+}
+
+// Splits a binary64 x into hi = RN32(x) and lo ~ x - hi with integer
+// operations only: the residual is (dropped 29 fraction bits - the rounding
+// increment) x 2^(E - 1075), formed as an int -> float conversion and a
+// power-of-two scale. False when hi or the scale would leave the normal
+// binary32 range (the caller then uses FP64 arithmetic).
+__device__ __forceinline__ bool split_f64(double x, float& hi, float& lo) {
+  const unsigned long long d = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned int dh = static_cast<unsigned int>(d >> 32), dl = static_cast<unsigned int>(d);
+  const int E = static_cast<int>((dh >> 20) & 0x7FFu);
+  const int e = E - 1023 + 127;
+  const int s = E - 1075;  // weight of the last binary64 fraction bit
+  if (e <= 0 || e >= 254 || s < -126) return false;
+  const unsigned int sign = dh & 0x80000000u;
+  const unsigned int mant = ((dh & 0xFFFFFu) << 3) | (dl >> 29);
+  const unsigned int rest = dl & 0x1FFFFFFFu;
+  const unsigned int half = 0x10000000u;
+  const unsigned int up = (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
+  hi = __uint_as_float(sign | (((static_cast<unsigned int>(e) << 23) | mant) + up));
+  const int r = static_cast<int>(rest) - (up ? (1 << 29) : 0);
+  const float scale = __uint_as_float(static_cast<unsigned int>(s + 127) << 23);
+  lo = __uint_as_float(sign ^ __float_as_uint(__int2float_rn(r) * scale));
+  return true;
+}
+
 __global__ void __launch_bounds__(256) shift_fp32_kernel(const double* __restrict__ u, int64_t K, int64_t N,
                                                          int64_t ldu, double* __restrict__ c, float* __restrict__ v,
                                                          int64_t ldv, int* bad) {
@@ -80,15 +124,25 @@ __global__ void __launch_bounds__(256) shift_fp32_kernel(const double* __restric
         cm = 0.0;
       }
       if (rg == 0) c[n] = cm;
+      // v = (uh - mh) + (ul - ml) in FP32 from the hi/lo splits of u and of
+      // the column minimum (no FP64 arithmetic in the common case); FP64
+      // subtraction for values outside the split's range
+      float mh = 0.f, ml = 0.f;
+      const bool msplit = split_f64(cm, mh, ml) || cm == 0.0;
+      auto shifted = [&](double x) -> float {
+        float xh, xl;
+        if (msplit && split_f64(x, xh, xl)) return __fadd_rn(__fsub_rn(xh, mh), __fsub_rn(xl, ml));
+        return f64_to_f32_rn(x - cm);
+      };
       int64_t k = rg;
       for (; k + 56 < K; k += 64) {
         double x[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) x[j] = u[(k + 8 * j) * ldu + n];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[(k + 8 * j) * ldv + n] = static_cast<float>(x[j] - cm);
+        for (int j = 0; j < 8; ++j) v[(k + 8 * j) * ldv + n] = shifted(x[j]);
       }
-      for (; k < K; k += 8) v[k * ldv + n] = static_cast<float>(u[k * ldu + n] - cm);
+      for (; k < K; k += 8) v[k * ldv + n] = shifted(u[k * ldu + n]);
     }
   }
 }

@@ -113,6 +113,9 @@ _SIGNATURES = {
     "mbar_kernel_launches": ([_i64p], ctypes.c_int),
     "mbar_get_trace": ([_vp, _i64p, _dp, ctypes.c_int64], ctypes.c_int),
     "mbar_set_hessian_path": ([ctypes.c_int32], ctypes.c_int),
+    "mbar_reweight": ([_vp, _vp, ctypes.c_int32, _dp, _dp], ctypes.c_int),
+    "mbar_weighted_histogram2d": ([_vp, _vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int64, _dp], ctypes.c_int),
     "mbar_footprint_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32], ctypes.c_uint64),
     "mbar_server_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ServerConfig)], ctypes.c_int),
     "mbar_server_submit": ([_vp, ctypes.c_int64, ctypes.c_int64, _i64p, _vp, ctypes.c_int32, _vp, ctypes.c_int32,
@@ -293,6 +296,29 @@ class Context:
         _check(lib().mbar_get_trace(self._h, ctypes.byref(n), None, 0))
         out = np.empty((n.value, 4))
         _check(lib().mbar_get_trace(self._h, ctypes.byref(n), _ptr(out), n.value))
+        return out
+
+    # -- reweighting (Eqs. 5-6) and the weighted 2-D histogram -----------------
+    def reweight(self, u0):
+        """(p, log C): weights of every sample (original order) at the target
+        state with reduced potential u0 (``mbar_reweight``)."""
+        p = np.empty(self.N)
+        logc = ctypes.c_double()
+        dptr, on_dev = _device_ptr(u0)
+        if on_dev:
+            _check(lib().mbar_reweight(self._h, dptr, 1, _ptr(p), ctypes.byref(logc)))
+        else:
+            a = _f64(u0)
+            _check(lib().mbar_reweight(self._h, ctypes.c_void_p(a.ctypes.data), 0, _ptr(p), ctypes.byref(logc)))
+        return p, logc.value
+
+    def weighted_histogram2d(self, x, y, x0: float, dx: float, nx: int, y0: float, dy: float, ny: int):
+        """``mbar_weighted_histogram2d`` of the last reweight weights."""
+        out = np.empty((int(nx), int(ny)))
+        xa, ya = _f64(x), _f64(y)
+        _check(lib().mbar_weighted_histogram2d(self._h, ctypes.c_void_p(xa.ctypes.data), ctypes.c_void_p(ya.ctypes.data),
+                                               0, float(x0), float(dx), int(nx), float(y0), float(dy), int(ny),
+                                               _ptr(out)))
         return out
 
     def close(self):

@@ -1,0 +1,72 @@
+"""The FP32 per-sample shift of the mixed-precision store (prep.cu):
+v = (uh - mh) + (ul - ml) from integer hi/lo splits of u and of the column
+minimum m, restated in Python integers and numpy float32 arithmetic. Pinned
+against the exact u - m: within 1.5 units in the last place of fl32(u - m)
+plus 2^-46 max(|u|, |m|) (the binary32 rounding of the residuals), exact
+when the difference is exactly representable in FP32, never negative."""
+import struct
+
+import numpy as np
+
+
+def split(x: float):
+    d = struct.unpack("<Q", struct.pack("<d", x))[0]
+    dh, dl = d >> 32, d & 0xFFFFFFFF
+    E = (dh >> 20) & 0x7FF
+    e, s = E - 1023 + 127, E - 1075
+    if e <= 0 or e >= 254 or s < -126:
+        return None
+    sign = dh & 0x80000000
+    mant = ((dh & 0xFFFFF) << 3) | (dl >> 29)
+    rest = dl & 0x1FFFFFFF
+    up = 1 if (rest > 0x10000000 or (rest == 0x10000000 and (mant & 1))) else 0
+    hi = struct.unpack("<f", struct.pack("<I", sign | (((e << 23) | mant) + up)))[0]
+    r = rest - (up << 29)
+    scale = struct.unpack("<f", struct.pack("<I", (s + 127) << 23))[0]
+    lo = np.float32(np.float32(r) * np.float32(scale))
+    if sign:
+        lo = -lo
+    return np.float32(hi), np.float32(lo)
+
+
+def shifted(u: float, m: float) -> np.float32:
+    mu = split(m) if m != 0.0 else (np.float32(0), np.float32(0))
+    su = split(u)
+    if mu is None or su is None:
+        return np.float32(u - m)
+    return np.float32(np.float32(su[0] - mu[0]) + np.float32(su[1] - mu[1]))
+
+
+def within_bound(v: np.float32, u: float, m: float) -> bool:
+    exact = u - m
+    ref = np.float32(exact)
+    bound = 1.5 * float(np.spacing(np.float32(max(abs(float(ref)), 1e-38)))) + 2.0 ** -46 * max(abs(u), abs(m))
+    return abs(float(v) - exact) <= bound
+
+
+def test_alchemical_like_columns():
+    g = np.random.default_rng(0)
+    for _ in range(300):
+        m = -1e4 + 100 * g.standard_normal()
+        for du in np.abs(20 * g.standard_t(4, size=30)) * g.uniform(0, 1, size=30):
+            u = m + du
+            v = shifted(u, m)
+            assert v >= 0.0
+            assert within_bound(v, u, m), (u, m, v)
+
+
+def test_wide_magnitudes_and_the_minimum_itself():
+    g = np.random.default_rng(1)
+    for _ in range(3000):
+        m = g.standard_normal() * 10.0 ** g.integers(-6, 8)
+        u = m + abs(g.standard_normal()) * 10.0 ** g.integers(-8, 8)
+        v = shifted(u, m)
+        assert v >= 0.0
+        assert within_bound(v, u, m), (u, m, v)
+        assert shifted(m, m) == 0.0
+
+
+def test_exact_when_the_difference_is_a_float():
+    for m in [-1e4, -12345.678, 3.25, 1e-3]:
+        for du in [0.0, 0.5, 1.25, 7.0, 1024.0]:
+            assert shifted(m + du, m) == np.float32((m + du) - m)
