@@ -38,6 +38,9 @@ WORKLOADS = {
                           "N_k=5000 (N=320k), FP64, bin schedule h=0.1->0"),
     "harmonic": dict(K=8, N_k=1000, precision="fp64", h0=0.0,
                      desc="K=8 harmonic states in d=3, N_k=1000 (N=8000), FP64"),
+    "pt": dict(K=50, N_k=200_000, precision="mixed", h0=0.0,
+               desc="parallel-tempering stand-in (Sec. III shape): K=50 temperatures 298-600 K exponentially "
+                    "spaced, N_k=2e5 (N=1e7), Gaussian density of states, u_kn=b_k E_n, binned on E"),
 }
 
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
@@ -64,6 +67,8 @@ def make_problem(name: str, seed: int = 0):
                     rows=lambda k0, k1: W.alchemical_rows(lam, u0, du, k0, k1))
     if name == "umbrella":
         p = W.umbrella(K=cfg["K"], N_k=cfg["N_k"], seed=seed)
+    elif name == "pt":
+        p = W.parallel_tempering(K=cfg["K"], N_k=cfg["N_k"], seed=seed)
     else:
         p = W.harmonic(K=cfg["K"], N_k=cfg["N_k"], seed=seed)
     u = p.u_kn

@@ -561,18 +561,26 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
   }
   issued = nchunks < kClVStages ? nchunks : kClVStages;
 
-  // threads 0..63 stage chunk c's per-sample columns into ring slot c % kClColRing
-  auto stage_cols = [&](int64_t c) {
+  // threads 0..63 fetch chunk c's per-sample columns into registers (load_cols)
+  // and write them to ring slot c % kClColRing one chunk later (put_cols), so
+  // no producer waits on the global loads
+  float col_l2 = INFINITY, col_sh = 0.f;  // padding samples contribute nothing
+  auto load_cols = [&](int64_t c) {
     if (tid < 64) {
       const int64_t col = c_begin + c * 64 + tid;
-      float l2 = INFINITY, sh = 0.f;  // padding samples contribute nothing
+      col_l2 = INFINITY;
+      col_sh = 0.f;
       if (col < c_end) {
-        l2 = p.logden[col] * kLog2e;
-        sh = p.H ? sqrtf(static_cast<float>(p.H[col])) : 1.f;
+        col_l2 = p.logden[col];
+        col_sh = p.H ? static_cast<float>(p.H[col]) : 1.f;
       }
+    }
+  };
+  auto put_cols = [&](int64_t c) {
+    if (tid < 64) {
       const int slot = static_cast<int>(c % kClColRing);
-      l2_ring[slot * 64 + tid] = l2;
-      sh_ring[slot * 64 + tid] = sh;
+      l2_ring[slot * 64 + tid] = col_l2 * kLog2e;
+      sh_ring[slot * 64 + tid] = p.H ? sqrtf(col_sh) : col_sh;
     }
   };
   constexpr uint32_t idesc = idesc_f16(128, 128);
@@ -580,7 +588,11 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
   if (producer) {
     // producers: v tile in, P~ out to this CTA and its readers, then the
     // readers' pfull barriers; they never wait for the MMA warp directly
-    for (int64_t cc = 0; cc < nchunks && cc < kClColRing - 1; ++cc) stage_cols(cc);
+    for (int64_t cc = 0; cc < nchunks && cc < kClColRing - 1; ++cc) {
+      load_cols(cc);
+      put_cols(cc);
+    }
+    if (kClColRing - 1 < nchunks) load_cols(kClColRing - 1);
     for (; c < nchunks; ++c) {
       const int s = static_cast<int>(c % kClVStages);
       const int b = static_cast<int>(c % kClPStages);
@@ -606,7 +618,10 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
         sh[0] = b0.x; sh[1] = b0.y; sh[2] = b0.z; sh[3] = b0.w;
         sh[4] = b1.x; sh[5] = b1.y; sh[6] = b1.z; sh[7] = b1.w;
       }
-      if (c + kClColRing - 1 < nchunks) stage_cols(c + kClColRing - 1);
+      if (c + kClColRing - 1 < nchunks) {
+        put_cols(c + kClColRing - 1);  // loaded during the previous chunk
+        if (c + kClColRing < nchunks) load_cols(c + kClColRing);
+      }
       const unsigned char* vb = vbuf + s * kClVStageBytes + (g >> 2) * (kClVStageBytes / 2);
       unsigned char* pst = pbuf + b * kClPStageBytes;
 #pragma unroll
