@@ -41,39 +41,12 @@ __host__ __device__ inline size_t rupr(size_t x, size_t m) { return (x + m - 1) 
 
 }  // namespace
 
-// Packed FP32 pairs (f32x2 arithmetic of sm_100+): two rows per instruction.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-
-// shared memory: stages | a pairs [max(Kpad, 8 H J)] f32 | slots [16][Kpad] f64 |
-//                colm[2][32] | cols[2][32] | mbarriers[8]
-// The a table holds, for row group r and pair jj, (a_k, a_k') with k = r + RG (2 jj),
-// k' = k + RG, so a thread reads its two rows' a with one 8-byte load; rows >= K
-// hold -inf (their entries vanish without a bounds test).
+// shared memory: stages | a [Kpad] f32 | slots [16][Kpad] f64 | colm[2][32] |
+//                cols[2][32] | mbarriers[8]
 struct RegsSmem {
   static __host__ __device__ size_t kpad(int K) { return rupr(static_cast<size_t>(K), 16); }
-  static __host__ __device__ size_t apad(int K, int J, int H) {
-    const size_t t = static_cast<size_t>(8 * H * J);
-    return rupr(kpad(K) > t ? kpad(K) : t, 16);
-  }
-  static __host__ __device__ size_t extra(int K, int nslots, int J, int H) {
-    return apad(K, J, H) * 4 + nslots * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64;
+  static __host__ __device__ size_t extra(int K, int nslots) {
+    return kpad(K) * 4 + nslots * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64;
   }
 };
 
@@ -95,8 +68,8 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   const size_t sbytes = SUB * subbytes;
   const size_t kp = RegsSmem::kpad(K);
   unsigned char* cur = smem + p.stages * sbytes;
-  float* a2s = reinterpret_cast<float*>(cur);  // [RG * J / 2] pairs
-  cur += RegsSmem::apad(K, J, H) * 4;
+  float* a_s = reinterpret_cast<float*>(cur);
+  cur += kp * 4;
   double* slots = reinterpret_cast<double*>(cur);  // [NSLOT][kp]
   cur += NSLOT * kp * 8;
   float* colm = reinterpret_cast<float*>(cur);     // [2][32]
@@ -113,14 +86,8 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     for (int s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
   }
-  for (int idx = tid; idx < RG * (J / 2); idx += kRThreads) {
-    const int r = idx % RG, jj = idx / RG;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int k = r + RG * (2 * jj + t);
-      a2s[2 * idx + t] = k < K ? static_cast<float>((p.f[k] + p.logN[k]) * 1.4426950408889634) : -INFINITY;
-    }
-  }
+  for (int k = tid; k < static_cast<int>(kp); k += kRThreads)
+    a_s[k] = k < K ? static_cast<float>((p.f[k] + p.logN[k]) * 1.4426950408889634) : 0.f;
   for (int i = tid; i < static_cast<int>(NSLOT * kp); i += kRThreads) slots[i] = 0.0;
   __syncthreads();
 
@@ -146,24 +113,21 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   const uint32_t off0 = static_cast<uint32_t>(sub * subbytes) + static_cast<uint32_t>(r0) * 128u +
                         ((static_cast<uint32_t>(q) ^ (lane & 7u)) << 4) + static_cast<uint32_t>((lane >> 3) * 4);
   constexpr uint32_t kStep = RG * 128u;
-  constexpr int JP = J / 2;  // row pairs per thread
-  float2 acc[JP];
+  float acc[J];
 #pragma unroll
-  for (int jj = 0; jj < JP; ++jj) acc[jj] = make_float2(0.f, 0.f);
+  for (int j = 0; j < J; ++j) acc[j] = 0.f;
   int it_fail = -1;
-  const float2* a_pair = reinterpret_cast<const float2*>(a2s) + r0;  // pair jj at a_pair[jj * RG]
 
   auto flush = [&]() {
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      float v = (j & 1) ? acc[j / 2].y : acc[j / 2].x;
+      float v = acc[j];
       v += __shfl_xor_sync(0xffffffffu, v, 8);
       v += __shfl_xor_sync(0xffffffffu, v, 16);
       const int k = r0 + RG * j;
       if (lane < 8 && k < K) slots[warp * kp + k] += static_cast<double>(v);
+      acc[j] = 0.f;
     }
-#pragma unroll
-    for (int jj = 0; jj < JP; ++jj) acc[jj] = make_float2(0.f, 0.f);
   };
 
   for (int it = 0; it < my_count; ++it) {
@@ -178,21 +142,22 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     }
     const int gcol = strip * CS + sub * 32 + col;
 
-    // A1: x_j = a_j - v_j log2(e) for two rows per f32x2 instruction, column
-    // max. Rows >= K read row r0 of the tile (finite data) against a = -inf.
-    float2 x[JP];
+    // A1: x_j in registers, column max
+    float x[J];
     float m0 = -INFINITY, m1 = -INFINITY;
-    const float2 nl2e = make_float2(-kLog2e, -kLog2e);
 #pragma unroll
-    for (int jj = 0; jj < JP; ++jj) {
-      const int k0 = r0 + RG * (2 * jj);
-      const uint32_t o0 = (k0 < K) ? off0 + (2 * jj) * kStep : off0;
-      const uint32_t o1 = (k0 + RG < K) ? off0 + (2 * jj + 1) * kStep : off0;
-      const float2 v = make_float2(*reinterpret_cast<const float*>(tile + o0),
-                                   *reinterpret_cast<const float*>(tile + o1));
-      x[jj] = ffma2(v, nl2e, a_pair[jj * RG]);
-      m0 = fmaxf(m0, x[jj].x);
-      m1 = fmaxf(m1, x[jj].y);
+    for (int j = 0; j < J; ++j) {
+      const int k = r0 + RG * j;
+      if (k < K) {
+        const float v = *reinterpret_cast<const float*>(tile + off0 + j * kStep);
+        x[j] = fmaf(-v, kLog2e, a_s[k]);
+        if (j & 1)
+          m1 = fmaxf(m1, x[j]);
+        else
+          m0 = fmaxf(m0, x[j]);
+      } else {
+        x[j] = -INFINITY;
+      }
     }
     float m = fmaxf(m0, m1);
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
@@ -207,17 +172,16 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     if constexpr (H == 2) m = fmaxf(colm[col], colm[32 + col]);
 
     // A2: e_j = 2^(x_j - m), column sum
-    float2 s2 = make_float2(0.f, 0.f);
-    const float2 nm = make_float2(-m, -m);
+    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int jj = 0; jj < JP; ++jj) {
-      float2 t = fadd2(x[jj], nm);
-      t.x = ex2_approx(t.x);
-      t.y = ex2_approx(t.y);
-      x[jj] = t;
-      s2 = fadd2(s2, t);
+    for (int j = 0; j < J; ++j) {
+      x[j] = ex2_approx(x[j] - m);
+      if (j & 1)
+        s1 += x[j];
+      else
+        s0 += x[j];
     }
-    float ssum = s2.x + s2.y;
+    float ssum = s0 + s1;
     ssum += __shfl_xor_sync(0xffffffffu, ssum, 1);
     ssum += __shfl_xor_sync(0xffffffffu, ssum, 2);
     ssum += __shfl_xor_sync(0xffffffffu, ssum, 4);
@@ -235,9 +199,8 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     }
 
     // B: row partials
-    const float2 w2 = make_float2(w, w);
 #pragma unroll
-    for (int jj = 0; jj < JP; ++jj) acc[jj] = ffma2(x[jj], w2, acc[jj]);
+    for (int j = 0; j < J; ++j) acc[j] = fmaf(x[j], w, acc[j]);
     if ((it + 1) % kFlush == 0) flush();
   }
 
@@ -339,7 +302,7 @@ LsePlan lse_regs_plan(int64_t K, int64_t n) {
   pl.box_rows = static_cast<int>(std::min<int64_t>(256, round_up(K, 8)));
   pl.nbox = static_cast<int>(ceil_div(K, pl.box_rows));
   const size_t sb = static_cast<size_t>(SUB) * pl.nbox * pl.box_rows * 128;
-  const size_t extra = RegsSmem::extra(static_cast<int>(K), 16, J, H) + 1024;
+  const size_t extra = RegsSmem::extra(static_cast<int>(K), 16) + 1024;
   pl.stages = 4;
   while (pl.stages > 2 && pl.stages * sb + extra > 220 * 1024) --pl.stages;
   pl.smem = pl.stages * sb + extra;
