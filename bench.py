@@ -58,9 +58,11 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
-def make_problem(name: str, seed: int = 0):
+def make_problem(name: str, seed: int = 0, nk: int | None = None):
     from paper_2609_03541_b300 import workloads as W
-    cfg = WORKLOADS[name]
+    cfg = dict(WORKLOADS[name])
+    if nk:
+        cfg["N_k"] = nk
     if name == "alchemical":
         lam, u0, du, Nk = W.alchemical_factors(K=cfg["K"], N_k=cfg["N_k"], seed=seed)
         return dict(kind=name, K=cfg["K"], N=int(Nk.sum()), N_k=Nk, phi=du,
@@ -482,6 +484,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=140.0, help="batch/serve: device memory budget of the server")
     ap.add_argument("--wave-gb", type=float, default=80.0, help="batch/serve: FP64 input memory held at once")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--nk", type=int, default=None,
+                    help="samples per state override (smaller instances for profiling captures)")
     args = ap.parse_args()
     if args.workload == "batch":
         return batch_bench(args)
@@ -498,6 +502,9 @@ def main():
     cfg = dict(WORKLOADS[args.workload])
     if args.precision:
         cfg["precision"] = args.precision
+    if args.nk:   # a smaller instance of the workload (profiling captures); not the headline configuration
+        cfg["N_k"] = args.nk
+        cfg["desc"] += f" [N_k overridden to {args.nk}]"
     metric = "MBAR solves/sec"
     config = {"workload": cfg["desc"], "K": cfg["K"], "N": cfg["K"] * cfg["N_k"], "precision": cfg["precision"],
               "tolerance_kT": 1e-4 if cfg["precision"] == "mixed" else 1e-8,
@@ -537,7 +544,7 @@ def main():
     dev = torch.device("cuda", local_rank)
     prec = M.MBAR_MIXED if cfg["precision"] == "mixed" else M.MBAR_FP64
 
-    prob = make_problem(args.workload, seed=rank)
+    prob = make_problem(args.workload, seed=rank, nk=args.nk)
     t0 = time.time()
     host = fill_pinned(prob, torch)
     phi_host = torch.from_numpy(np.ascontiguousarray(prob["phi"])).pin_memory() if prob["phi"] is not None else None

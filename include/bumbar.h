@@ -386,6 +386,14 @@ BUMBAR_API mbar_status mbar_batch_solve(int32_t P, const int64_t* K, const int64
                                         int32_t phi_on_device, const mbar_server_config* cfg, double* const* f_out,
                                         mbar_report* reports, mbar_status* statuses);
 
+/* Self-test of the device-side failure path (diagnostics; no counterpart
+ * in the paper): one kernel waits on an mbarrier that nothing completes,
+ * gives up after limit_us (1 us .. 2 s), records the timeout and returns.
+ * Returns MBAR_ETIMEOUT (the expected outcome) with *waited_s (nullable)
+ * the time the wait ran; the device stays usable. Every wait in this
+ * library's kernels is bounded the same way and reports MBAR_ETIMEOUT. */
+BUMBAR_API mbar_status mbar_selftest_wait_timeout(int64_t limit_us, double* waited_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -216,6 +216,7 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   p.noise = noise;
   p.d_out = d_out;
   p.skip_if_done = skip_if_done;
+  p.skip_if_underflow = mode == kLseModeSci ? 1 : 0;
   const bool timed = !L.binned;
   if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
   mbar_status s = lse_launch(L.tmap, pl, p, c->dtype, c->st);
@@ -243,6 +244,58 @@ mbar_status read_status(mbar_ctx* c) {
 }
 
 mbar_status check_device_errors(mbar_ctx* c) { return read_status(c); }
+
+// True (and the device flag cleared) when the last SCI step(s) read by
+// read_status stopped on an underflowed state.
+bool take_underflow(mbar_ctx* c) {
+  if (!c->hstat->ctrl.underflow) return false;
+  c->hstat->ctrl.underflow = 0;
+  cudaMemsetAsync(&c->ctrl->underflow, 0, sizeof(int), c->st);
+  return true;
+}
+
+// The SCI step of run_lse redone exactly in the log domain: logden by a
+// pass over the level, then log Q_k = LSE_p(log H_p + a_k - v_kp - logden_p).
+mbar_status log_sci_step(mbar_ctx* c, const Level& L, const double* f_in, double* f_out, double* g_out,
+                         double* s_out, double eps, double* d_out, double noise) {
+  BUMBAR_TRY(run_lse(c, L, f_in, kLseModePass, nullptr, nullptr, nullptr, 0.0, 0, c->logden));
+  LseParams p{};
+  p.K = static_cast<int>(c->K);
+  p.n = static_cast<int>(L.n);
+  p.f = f_in;
+  p.logN = c->logN_d;
+  p.H = L.H;
+  p.logden = c->logden;
+  p.Q = c->Q;
+  p.mode = kLseModeSci;
+  p.Nk = c->Nk_d;
+  p.f_out = f_out;
+  p.g_out = g_out;
+  p.s_out = s_out;
+  p.d_out = d_out;
+  p.ctrl = c->ctrl;
+  p.eps = eps;
+  p.noise = noise;
+  void* tmp = nullptr;
+  const size_t bytes = log_sci_tmp_bytes(c->K, L.n);
+  BUMBAR_TRY(dalloc(c, &tmp, bytes));
+  const mbar_status s = log_sci_finish(L.v, c->dtype, c->K, L.n, L.ld, p, tmp, bytes, c->st);
+  dfree(c, tmp);
+  return s;
+}
+
+// One SCI step with its status read back; a step that underflowed is redone
+// in the log domain.
+mbar_status sci_step_exact(mbar_ctx* c, const Level& L, const double* f_in, double* f_out, double* g_out,
+                           double* s_out, void* logden_out, double* d_out = nullptr) {
+  BUMBAR_TRY(run_lse(c, L, f_in, kLseModeSci, f_out, g_out, s_out, 0.0, 0, logden_out, d_out));
+  BUMBAR_TRY(read_status(c));
+  if (take_underflow(c)) {
+    BUMBAR_TRY(log_sci_step(c, L, f_in, f_out, g_out, s_out, 0.0, d_out, 0.0));
+    BUMBAR_TRY(read_status(c));
+  }
+  return MBAR_OK;
+}
 
 mbar_status ensure_sorted(mbar_ctx* c);
 
@@ -400,8 +453,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
   const Level& L = c->full;
   std::vector<double> gh(K), dh(K);
   // evaluate at f: SCI step (fs), gradient (g), logden
-  BUMBAR_TRY(run_lse(c, L, c->f, kLseModeSci, c->fs, c->g, c->s, 0.0, 0, c->logden));
-  BUMBAR_TRY(check_device_errors(c));
+  BUMBAR_TRY(sci_step_exact(c, L, c->f, c->fs, c->g, c->s, c->logden));
   BUMBAR_TRY(d2h(c, gh.data(), c->g, K));
   BUMBAR_CUDA(cudaStreamSynchronize(c->st));
   double gmax = max_abs(gh);
@@ -411,6 +463,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
   BUMBAR_TRY(dalloc(c, &tmp, std::max(htmp, ntmp)));
   mbar_status st = MBAR_ENOTCONV;
   int rejects = 0;
+  double prev_step = INFINITY;
   for (int it = 0; it < c->opts.max_newton; ++it) {
     if (gmax == 0.0 || K == 1) {
       st = MBAR_OK;
@@ -440,8 +493,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
     bool accepted = false;
     if (info == 0 && std::isfinite(step)) {
       s = vec_add_gauge(c->f, c->delta, c->ft, K, c->st);
-      if (s == MBAR_OK) s = run_lse(c, L, c->ft, kLseModeSci, c->fts, c->gt, c->s2, 0.0, 0, c->logden);
-      if (s == MBAR_OK) s = check_device_errors(c);
+      if (s == MBAR_OK) s = sci_step_exact(c, L, c->ft, c->fts, c->gt, c->s2, c->logden);
       if (s == MBAR_OK) s = d2h(c, gh.data(), c->gt, K);
       if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
       if (s != MBAR_OK && s != MBAR_ENOTCONV) {
@@ -462,6 +514,13 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
           st = MBAR_OK;
           break;
         }
+        // Newton contracts quadratically; accepted steps that stop shrinking
+        // while already small are moving on the rounding noise of the gradient
+        if (step > 0.5 * prev_step && step < 1e3 * c->opts.f_tol) {
+          st = MBAR_OK;
+          break;
+        }
+        prev_step = step;
       }
     }
     if (!accepted) {
@@ -474,8 +533,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
         break;
       }
       std::swap(c->f, c->fs);
-      s = run_lse(c, L, c->f, kLseModeSci, c->fs, c->g, c->s, 0.0, 0, c->logden);
-      if (s == MBAR_OK) s = check_device_errors(c);
+      s = sci_step_exact(c, L, c->f, c->fs, c->g, c->s, c->logden);
       if (s == MBAR_OK) s = d2h(c, gh.data(), c->g, K);
       if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
       if (s != MBAR_OK) {
@@ -487,6 +545,9 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
   }
   dfree(c, tmp);
   rep->max_abs_grad = gmax;
+  if (st == MBAR_ENOTCONV)
+    set_error("Newton phase: no convergence in %d iterations (last step %.3g, max|g| %.3g)", c->opts.max_newton,
+              rep->last_step, gmax);
   return st;
 }
 
@@ -545,6 +606,10 @@ mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
       BUMBAR_TRY(batch());
     }
     BUMBAR_TRY(read_status(c));
+    if (take_underflow(c)) {  // the batch stopped at that step: redo it exactly
+      BUMBAR_TRY(log_sci_step(c, L, c->f, c->f, nullptr, c->s, c->opts.eps, nullptr, c->opts.noise_floor));
+      BUMBAR_TRY(read_status(c));
+    }
     const Ctrl h = c->hstat->ctrl;
     done_iters = h.iters;
     if (h.done || done_iters >= c->opts.max_sci) {
@@ -891,10 +956,24 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
     BUMBAR_TRY(run_lse(c, nxt, c->f, kLseModeSci, c->fts, nullptr, c->s2, 0.0, 0, nullptr));
     return MBAR_OK;
   };
+  // the steps of one round in order: n_intermediate in-place steps on cur,
+  // then the probes at n (-> ft, s, d) and at n * inc (-> fts, s2)
+  auto round_step = [&](int idx, bool exact_log) -> mbar_status {
+    const Level& L = idx <= o.n_intermediate ? cur : nxt;
+    double* out = idx < o.n_intermediate ? c->f : (idx == o.n_intermediate ? c->ft : c->fts);
+    double* so = idx < o.n_intermediate ? nullptr : (idx == o.n_intermediate ? c->s : c->s2);
+    double* dd = idx == o.n_intermediate ? c->d : nullptr;
+    if (exact_log) {
+      BUMBAR_TRY(log_sci_step(c, L, c->f, out, nullptr, so, 0.0, dd, 0.0));
+      return read_status(c);
+    }
+    return sci_step_exact(c, L, c->f, out, nullptr, so, nullptr, dd);
+  };
   Graph g;
   bool captured = false;
   for (int64_t round = 0; s == MBAR_OK; ++round) {
     if (rep->iters_second_loop >= o.max_sci) break;
+    const int64_t iters_before = c->hstat->ctrl.iters;
     const bool use_graph = cur.binned && nxt.binned && c->graphs;
     if (use_graph && !captured) {
       s = capture(c, &g, round_body);
@@ -912,6 +991,11 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
       s = round_body();
     }
     if (s == MBAR_OK) s = read_status(c);
+    if (s == MBAR_OK && take_underflow(c)) {
+      // the round stopped at step `first`: that step exactly, then the rest
+      const int first = static_cast<int>(c->hstat->ctrl.iters - iters_before);
+      for (int idx = first; idx < o.n_intermediate + 2 && s == MBAR_OK; ++idx) s = round_step(idx, idx == first);
+    }
     if (s != MBAR_OK) break;
     const double s_n = c->hstat->s, s_next = c->hstat->s2, d_n = c->hstat->d;
     rep->iters_second_loop += o.n_intermediate + 2;
@@ -951,8 +1035,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
 mbar_status plain_warmup(mbar_ctx* c, mbar_report* rep) {
   std::vector<double> gh(c->K);
   for (int64_t it = 0; it < c->opts.max_sci; ++it) {
-    BUMBAR_TRY(run_lse(c, c->full, c->f, kLseModeSci, c->fs, c->g, c->s, 0.0, 0, nullptr));
-    BUMBAR_TRY(check_device_errors(c));
+    BUMBAR_TRY(sci_step_exact(c, c->full, c->f, c->fs, c->g, c->s, nullptr));
     BUMBAR_TRY(d2h(c, gh.data(), c->g, c->K));
     BUMBAR_CUDA(cudaStreamSynchronize(c->st));
     double r = 0.0;
@@ -1355,8 +1438,7 @@ mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double
   }
   const int64_t K = c->K;
   BUMBAR_TRY(upload_f(c, f_in, c->ft));
-  BUMBAR_TRY(run_lse(c, c->cur, c->ft, kLseModeSci, c->fts, c->gt, c->s2, 0.0, 0, logden ? c->logden : nullptr));
-  BUMBAR_TRY(check_device_errors(c));
+  BUMBAR_TRY(sci_step_exact(c, c->cur, c->ft, c->fts, c->gt, c->s2, logden ? c->logden : nullptr));
   if (f_out) BUMBAR_TRY(d2h(c, f_out, c->fts, K));
   if (grad) BUMBAR_TRY(d2h(c, grad, c->gt, K));
   if (s_out) BUMBAR_TRY(d2h(c, s_out, c->s2, 1));
@@ -1427,7 +1509,7 @@ mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, dou
   const int64_t K = c->K;
   const Level& L = c->cur;
   BUMBAR_TRY(upload_f(c, f_in, c->ft));
-  BUMBAR_TRY(run_lse(c, L, c->ft, kLseModeSci, c->fts, c->gt, c->s2, 0.0, 0, c->logden));
+  BUMBAR_TRY(sci_step_exact(c, L, c->ft, c->fts, c->gt, c->s2, c->logden));
   const size_t htmp = hessian_tmp_bytes(K, L.n), ntmp = newton_tmp_bytes(K);
   void* tmp = nullptr;
   BUMBAR_TRY(dalloc(c, &tmp, std::max(htmp, ntmp)));

@@ -14,7 +14,7 @@ struct Ctrl {
   int done;       // first loop of Algorithm 1: set when s < eps
   int nonfinite;  // an update produced a non-finite f
   int iters;      // SCI steps executed by the guarded kernels
-  int pad;
+  int underflow;  // an SCI step found Q_k below 1e-20 N_k (its linear-domain sum lost the state): f kept
   double last_s;  // relative step (Eq. 2) of the last SCI step
 };
 
@@ -45,7 +45,13 @@ struct LseParams {
   double eps;        // > 0: set ctrl->done when s < eps
   double noise;      // > 0: set ctrl->done when max|f_out - f| < noise
   int skip_if_done;  // return at once if ctrl->done
+  int skip_if_underflow;  // return at once if ctrl->underflow (SCI steps after an underflowed one)
 };
+
+// The guard every LSE pass kernel and its epilogue apply first.
+__device__ __forceinline__ bool lse_skip(const LseParams& p) {
+  return p.ctrl != nullptr && ((p.skip_if_done && p.ctrl->done) || (p.skip_if_underflow && p.ctrl->underflow));
+}
 
 struct LsePlan {
   int C, num_strips, box_rows, nbox, stages, grid, threads;
@@ -61,6 +67,13 @@ bool lse_regs_supported(int64_t K, int dtype_bytes);
 LsePlan lse_regs_plan(int64_t K, int64_t n);
 mbar_status lse_regs_launch(const CUtensorMap& tmap, const LsePlan& pl, const LseParams& prm, cudaStream_t st);
 size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes);
+// Exact log-domain SCI step (lse.cu) for steps whose linear-domain row sums
+// underflowed: logQ_k = log sum_p H_p exp(a_k - v_kp - logden_p) from the
+// pass's logden, then the Eq. 1 update, gauge, Eq. 2 and loop control like
+// the epilogue. K x n work in FP32 with running maxima, FP64 combination.
+size_t log_sci_tmp_bytes(int64_t K, int64_t n);
+mbar_status log_sci_finish(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const LseParams& p,
+                           void* tmp, size_t tmp_bytes, cudaStream_t st);
 // Scratch of a pass whose plan has `grid` CTAs: 256 bytes (counter, error
 // word), grid x K FP64 partials, then the epilogue's new f and per-CTA slots.
 size_t lse_scratch_for_grid(int64_t K, int grid);

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
 
-  if (p.ctrl != nullptr && p.skip_if_done && p.ctrl->done) return;
+  if (lse_skip(p)) return;
 
   const size_t sbytes = LseSmem<T, G>::stage_bytes(p.nbox, p.box_rows);
   unsigned char* stage_base = smem;
@@ -409,7 +409,7 @@ constexpr int kEpiWarps = 4;  // states per epilogue CTA (one warp each)
 // long dependent FP64 chains), updates the loop control and copies the new
 // f out.
 __global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams p) {
-  if (p.ctrl != nullptr && p.skip_if_done && p.ctrl->done) return;  // same guard as the pass
+  if (lse_skip(p)) return;  // same guard as the pass
   const int K = p.K;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = blockIdx.x * kEpiWarps + warp;
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams 
   };
   __shared__ double f0new_s;
   __shared__ double smax_s[kEpiWarps], dmax_s[kEpiWarps];
-  __shared__ int fin_s[kEpiWarps];
+  __shared__ int fin_s[kEpiWarps], unf_s[kEpiWarps];
   if (sci && warp == 0) {
     const double q0 = rowsum(0);
     if (lane == 0) f0new_s = p.f[0] + p.logN[0] - log(q0);
@@ -439,8 +439,11 @@ __global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams 
   if (!sci) return;
   __syncthreads();
   double smax = -1.0, dmax = 0.0;  // smax -1: no f_k != 0 seen
-  int finite = 1;
+  int finite = 1, under = 0;
   if (k < K && lane == 0) {
+    // a state whose expected count fell below 1e-20 N_k lost (part of) its
+    // sum to the linear-domain exponentials: the step is redone exactly
+    under = (qk >= 1e-20 * p.Nk[k]) ? 0 : 1;
     const double fo = fnew - f0new_s;
     const double fi = p.f[k];
     p.epi[k] = fo;
@@ -453,22 +456,24 @@ __global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams 
     smax_s[warp] = smax;
     dmax_s[warp] = dmax;
     fin_s[warp] = finite;
+    unf_s[warp] = under;
   }
   __syncthreads();
   __shared__ unsigned int is_last;
   if (threadIdx.x == 0) {
     double sm = -1.0, dm = 0.0;
-    int ok = 1;
+    int ok = 1, un = 0;
 #pragma unroll
     for (int w = 0; w < kEpiWarps; ++w) {
       sm = fmax(sm, smax_s[w]);
       dm = fmax(dm, dmax_s[w]);
       ok &= fin_s[w];
+      un |= unf_s[w];
     }
     double* slot = p.epi + K + 3 * static_cast<size_t>(blockIdx.x);
     slot[0] = sm;
     slot[1] = dm;
-    slot[2] = ok ? 1.0 : 0.0;
+    slot[2] = (ok ? 1.0 : 0.0) + (un ? 2.0 : 0.0);
     __threadfence();
     const unsigned int ticket = atomicAdd(p.counter, 1u);
     is_last = (ticket == gridDim.x - 1) ? 1u : 0u;
@@ -476,28 +481,42 @@ __global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams 
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  if (p.f_out)
-    for (int j = threadIdx.x; j < K; j += blockDim.x) p.f_out[j] = p.epi[j];
   double sm = -1.0, dm = 0.0;
-  int okm = 1;
+  int okm = 1, unm = 0;
   for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     const double* slot = p.epi + K + 3 * static_cast<size_t>(b);
     sm = fmax(sm, slot[0]);
     dm = fmax(dm, slot[1]);
-    okm &= slot[2] != 0.0 ? 1 : 0;
+    okm &= (static_cast<int>(slot[2]) & 1);
+    unm |= (static_cast<int>(slot[2]) >> 1) & 1;
   }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     sm = fmax(sm, __shfl_xor_sync(0xffffffffu, sm, o));
     dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
     okm &= __shfl_xor_sync(0xffffffffu, okm, o);
+    unm |= __shfl_xor_sync(0xffffffffu, unm, o);
   }
   if (lane == 0) {
     smax_s[warp] = sm;
     dmax_s[warp] = dm;
     fin_s[warp] = okm;
+    unf_s[warp] = unm;
   }
   __syncthreads();
+  int unf = 0;
+#pragma unroll
+  for (int w = 0; w < kEpiWarps; ++w) unf |= unf_s[w];
+  if (unf && p.ctrl) {  // keep f; the host redoes this step in the log domain
+    if (threadIdx.x == 0) {
+      p.ctrl->underflow = 1;
+      if (p.s_out) *p.s_out = INFINITY;
+      *p.counter = 0u;
+    }
+    return;
+  }
+  if (p.f_out)
+    for (int j = threadIdx.x; j < K; j += blockDim.x) p.f_out[j] = p.epi[j];
   if (threadIdx.x != 0) return;
   double smf = -1.0, dmf = 0.0;
   int okf = 1;
@@ -521,6 +540,155 @@ __global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams 
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// exact log-domain SCI step (steps whose linear-domain row sums underflowed)
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kLogThreads = 256;
+constexpr int64_t kLogCols = 8192;  // columns per block
+
+template <typename A>
+__device__ __forceinline__ void lse_acc(A& m, A& s, A m2, A s2) {
+  if (m2 == -INFINITY) return;
+  if (m == -INFINITY) {
+    m = m2;
+    s = s2;
+  } else if (m2 > m) {
+    s = s * exp(m - m2) + s2;
+    m = m2;
+  } else {
+    s += s2 * exp(m2 - m);
+  }
+}
+
+// (max, sum) of t_kp = a_k - v_kp - logden_p + log H_p over one chunk of
+// columns of row k = blockIdx.y, in the data's precision.
+template <typename T>
+__global__ void __launch_bounds__(kLogThreads) row_logsum_partial(const T* __restrict__ v, int64_t ld, int64_t n,
+                                                                  const double* __restrict__ f,
+                                                                  const double* __restrict__ logN,
+                                                                  const T* __restrict__ logden,
+                                                                  const int32_t* __restrict__ H,
+                                                                  double* __restrict__ part, int64_t nchunks) {
+  const int64_t k = blockIdx.y;
+  const T a = static_cast<T>(f[k] + logN[k]);
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kLogCols;
+  const int64_t c1 = (c0 + kLogCols < n) ? c0 + kLogCols : n;
+  T m = -INFINITY, s = T(0);
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += kLogThreads) {
+    T t = a - v[k * ld + c] - logden[c];
+    if (H) t += log(static_cast<T>(H[c]));
+    lse_acc(m, s, t, T(1));
+  }
+  __shared__ double sm[kLogThreads], ss[kLogThreads];
+  sm[threadIdx.x] = static_cast<double>(m);
+  ss[threadIdx.x] = static_cast<double>(s);
+  __syncthreads();
+  for (int o = kLogThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      double x = sm[threadIdx.x], y = ss[threadIdx.x];
+      lse_acc(x, y, sm[threadIdx.x + o], ss[threadIdx.x + o]);
+      sm[threadIdx.x] = x;
+      ss[threadIdx.x] = y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * (k * nchunks + blockIdx.x)] = sm[0];
+    part[2 * (k * nchunks + blockIdx.x) + 1] = ss[0];
+  }
+}
+
+// logQ_k from the chunk partials (in chunk order), then Eq. 1, gauge, the
+// gradient, Eq. 2 and the loop control, as lse_epilogue_kernel does. One
+// block, K <= 1024 threads.
+__global__ void __launch_bounds__(1024) log_sci_finish_kernel(LseParams p, const double* __restrict__ part,
+                                                              int64_t nchunks) {
+  const int K = p.K, k = threadIdx.x;
+  __shared__ double fnew_s[1024];
+  __shared__ double red_s[32], red_d[32];
+  __shared__ int red_f[32];
+  __shared__ double f00;
+  double fi = 0.0, fn = 0.0;
+  if (k < K) {
+    double m = -INFINITY, s = 0.0;
+    for (int64_t b = 0; b < nchunks; ++b) lse_acc(m, s, part[2 * (k * nchunks + b)], part[2 * (k * nchunks + b) + 1]);
+    const double logq = m + log(s);
+    fi = p.f[k];
+    fn = fi + p.logN[k] - logq;
+    fnew_s[k] = fn;
+    p.Q[k] = exp(logq);
+    if (p.g_out) p.g_out[k] = exp(logq) - p.Nk[k];
+  }
+  if (k == 0) f00 = p.f[0];
+  __syncthreads();
+  double smax = -1.0, dmax = 0.0;
+  int finite = 1;
+  if (k < K) {
+    const double fo = fn - fnew_s[0];
+    if (!isfinite(fo)) finite = 0;
+    if (fi != 0.0) smax = fabs(fo / fi - 1.0);
+    dmax = fabs(fo - (fi - f00));
+    fnew_s[k] = fo;
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    finite &= __shfl_xor_sync(0xffffffffu, finite, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_s[threadIdx.x >> 5] = smax;
+    red_d[threadIdx.x >> 5] = dmax;
+    red_f[threadIdx.x >> 5] = finite;
+  }
+  __syncthreads();  // every read of f is done: f_out may be f
+  if (k < K && p.f_out) p.f_out[k] = fnew_s[k];
+  if (threadIdx.x == 0) {
+    double sm = -1.0, dm = 0.0;
+    int ok = 1;
+    for (int w = 0; w < static_cast<int>((blockDim.x + 31) / 32); ++w) {
+      sm = fmax(sm, red_s[w]);
+      dm = fmax(dm, red_d[w]);
+      ok &= red_f[w];
+    }
+    const double sv = (sm < 0.0) ? INFINITY : sm;
+    if (p.s_out) *p.s_out = sv;
+    if (p.d_out) *p.d_out = dm;
+    if (p.ctrl) {
+      p.ctrl->iters += 1;
+      p.ctrl->last_s = sv;
+      if (!ok) p.ctrl->nonfinite = 1;
+      if ((p.eps > 0.0 && sv < p.eps) || (p.noise > 0.0 && dm < p.noise)) p.ctrl->done = 1;
+    }
+  }
+}
+
+}  // namespace
+
+size_t log_sci_tmp_bytes(int64_t K, int64_t n) { return round_up(K * ceil_div(n, kLogCols) * 16, 256) + 256; }
+
+mbar_status log_sci_finish(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const LseParams& p,
+                           void* tmp, size_t tmp_bytes, cudaStream_t st) {
+  if (K > 1024 || tmp_bytes < log_sci_tmp_bytes(K, n)) {
+    set_error("log_sci_finish: bad sizes");
+    return MBAR_EINVAL;
+  }
+  const int64_t nchunks = ceil_div(n, kLogCols);
+  double* part = static_cast<double*>(tmp);
+  const dim3 g(static_cast<unsigned>(nchunks), static_cast<unsigned>(K));
+  if (dtype_bytes == 4)
+    row_logsum_partial<float><<<g, kLogThreads, 0, st>>>(static_cast<const float*>(v), ld, n, p.f, p.logN,
+                                                         static_cast<const float*>(p.logden), p.H, part, nchunks);
+  else
+    row_logsum_partial<double><<<g, kLogThreads, 0, st>>>(static_cast<const double*>(v), ld, n, p.f, p.logN,
+                                                          static_cast<const double*>(p.logden), p.H, part, nchunks);
+  log_sci_finish_kernel<<<1, static_cast<unsigned>(round_up(K, 32)), 0, st>>>(p, part, nchunks);
+  count_launches(2);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
 
 size_t lse_scratch_for_grid(int64_t K, int grid) {
   return 256 + static_cast<size_t>(grid) * K * sizeof(double) + sizeof(double) * K +

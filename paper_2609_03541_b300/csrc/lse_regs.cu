@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int K = p.K;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (p.ctrl != nullptr && p.skip_if_done && p.ctrl->done) return;
+  if (lse_skip(p)) return;
 
   const size_t subbytes = static_cast<size_t>(p.nbox) * p.box_rows * 128;
   const size_t sbytes = SUB * subbytes;

@@ -116,6 +116,7 @@ _SIGNATURES = {
     "mbar_reweight": ([_vp, _vp, ctypes.c_int32, _dp, _dp], ctypes.c_int),
     "mbar_weighted_histogram2d": ([_vp, _vp, _vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int64, _dp], ctypes.c_int),
+    "mbar_selftest_wait_timeout": ([ctypes.c_int64, _dp], ctypes.c_int),
     "mbar_footprint_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32], ctypes.c_uint64),
     "mbar_server_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ServerConfig)], ctypes.c_int),
     "mbar_server_submit": ([_vp, ctypes.c_int64, ctypes.c_int64, _i64p, _vp, ctypes.c_int32, _vp, ctypes.c_int32,
@@ -521,3 +522,10 @@ def batch_solve(problems, cfg: ServerConfig):
     lib().mbar_batch_solve(P, K_a.ctypes.data_as(_i64p), N_a.ctypes.data_as(_i64p), nk_ptrs, u_ptrs, int(on_dev or 0),
                            phi_ptrs, int(p_dev), ctypes.byref(cfg), f_ptrs, reps, sts)
     return fs, [reps[i] for i in range(P)], [int(sts[i]) for i in range(P)]
+
+
+def selftest_wait_timeout(limit_us: int = 50_000):
+    """``mbar_selftest_wait_timeout``: (status name, seconds waited)."""
+    w = ctypes.c_double()
+    st = lib().mbar_selftest_wait_timeout(int(limit_us), ctypes.byref(w))
+    return STATUS.get(st, str(st)), w.value

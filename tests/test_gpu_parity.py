@@ -370,3 +370,43 @@ def test_algorithm1_trajectory_matches_oracle_fp64(case):
                 assert a == pytest.approx(b, rel=1e-6)
             else:   # a converged level: both at the FP64 rounding floor
                 assert a < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_parallel_tempering_spread_needs_log_domain_steps(prec):
+    """Sec. III-shaped energies spread over ~1000 kT between the coldest and
+    hottest state: from f = 0 some states' linear-domain row sums underflow
+    (even in FP64); those steps are redone exactly in the log domain."""
+    p = W.parallel_tempering(K=16, N_k=800, seed=2)
+    f_ref = O.solve_mbar(p.u_kn, p.N_k)
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    ctx.set_coordinate(p.phi)
+    rep = ctx.solve()
+    f = ctx.free_energies()
+    ctx.close()
+    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL[prec], rep.as_dict()
+
+
+def test_parallel_tempering_trajectory_matches_oracle_fp64():
+    """The log-domain redo of an underflowed step is the oracle's step: the
+    first loop's length and every Eq. 3 check agree."""
+    p = W.parallel_tempering(K=12, N_k=1000, seed=4)
+    tr = []
+    O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, trace=tr)
+    ctx = M.Context(p.u_kn, p.N_k, M.MBAR_FP64)
+    ctx.set_coordinate(p.phi)
+    ctx.solve()
+    gt = ctx.trace()
+    ctx.close()
+    ph1 = [t for t in tr if t[0] == "phase1"]
+    g1 = [r for r in gt if r[0] == 1]
+    assert int(g1[0][3]) == len(ph1)
+    ph2 = [t for t in tr if t[0] == "phase2"]
+    g2 = [r for r in gt if r[0] == 2]
+    assert len(g2) == len(ph2)
+    for r, t in zip(g2, ph2):
+        for a, b in ((r[2], t[2]), (r[3], t[3])):
+            if b > 1e-9:
+                assert a == pytest.approx(b, rel=1e-6)
+            else:
+                assert a < 1e-9
