@@ -161,11 +161,13 @@ def oracle_sample(name: str, target_seconds: float = 20.0):
     cfg = WORKLOADS[name]
     K = cfg["K"]
     nk_full = cfg["N_k"]
-    nk = {"alchemical": 8, "umbrella": 200, "harmonic": nk_full}[name]
+    nk = {"alchemical": 8, "umbrella": 200, "harmonic": nk_full, "pt": 100}[name]
     if name == "alchemical":
         p = W.alchemical(K=K, N_k=nk, seed=1)
     elif name == "umbrella":
         p = W.umbrella(K=K, N_k=nk, seed=1, grid_points=1 << 14)
+    elif name == "pt":
+        p = W.parallel_tempering(K=K, N_k=nk, seed=1)
     else:
         p = W.harmonic(K=K, N_k=nk, seed=1)
     opts = O.BUOptions(h0=cfg["h0"])
@@ -201,31 +203,45 @@ def lse_only(args):
     dt = torch.float32 if args.lse_dtype == "float32" else torch.float64
     g = torch.Generator(device=dev)
     g.manual_seed(0)
-    ld = (n + 31) // 32 * 32
-    v = torch.empty((K, ld), dtype=dt, device=dev)
-    v[:, :n] = (3.0 * torch.randn((K, n), generator=g, device=dev, dtype=torch.float32)).abs().to(dt)
-    vv = v[:, :n]
+    samples = args.lse_layout == "samples" and dt == torch.float32
     f = torch.linspace(-1, 1, K, device=dev, dtype=torch.float64)
     logN = torch.full((K,), float(np.log(n / K)), device=dev, dtype=torch.float64)
     Q = torch.empty(K, device=dev, dtype=torch.float64)
     logden = torch.empty(n, device=dev, dtype=dt)
-    scratch = torch.zeros(M.lse_scratch_bytes(K, n, v.element_size()), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if samples:
+        Kp = (K + 3) // 4 * 4
+        v = torch.zeros((n, Kp), dtype=dt, device=dev)
+        v[:, :K] = (3.0 * torch.randn((n, K), generator=g, device=dev, dtype=torch.float32)).abs()
+        scratch = torch.zeros(M.lse_samples_scratch_bytes(K, n), dtype=torch.uint8, device=dev)
+
+        def one():
+            M.lse_pass_samples(v, K, f, logN, Q, logden=logden, scratch=scratch, stream=stream)
+    else:
+        ld = (n + 31) // 32 * 32
+        v = torch.empty((K, ld), dtype=dt, device=dev)
+        v[:, :n] = (3.0 * torch.randn((K, n), generator=g, device=dev, dtype=torch.float32)).abs().to(dt)
+        vv = v[:, :n]
+        scratch = torch.zeros(M.lse_scratch_bytes(K, n, v.element_size()), dtype=torch.uint8, device=dev)
+
+        def one():
+            M.lse_pass(vv, f, logN, Q, logden=logden, scratch=scratch, stream=stream)
     for _ in range(max(args.warmup, 1)):
-        M.lse_pass(vv, f, logN, Q, logden=logden, scratch=scratch, stream=stream)
+        one()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        M.lse_pass(vv, f, logN, Q, logden=logden, scratch=scratch, stream=stream)
+        one()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     peaks, src = load_peaks()
     algo = K * n * v.element_size()
     gbs = algo / (ms / 1e3) / 1e9
-    print(json.dumps({"kernel": f"lse_pass_kernel<{args.lse_dtype}>", "K": K, "n": n, "ms_per_launch": ms,
+    kname = "lse_smaj_kernel (sample-major FP32)" if samples else f"lse_pass (row-major {args.lse_dtype})"
+    print(json.dumps({"kernel": kname, "K": K, "n": n, "ms_per_launch": ms,
                       "algorithmic_bytes": algo, "achieved_GBps": gbs, "peak_GBps": peaks["hbm_gbs"],
                       "frac": gbs / peaks["hbm_gbs"], "peak_source": src,
                       "entries_per_s": K * n / (ms / 1e3)}), flush=True)
@@ -474,6 +490,8 @@ def main():
     ap.add_argument("--lse-K", type=int, default=500)
     ap.add_argument("--lse-n", type=int, default=2_000_000)
     ap.add_argument("--lse-dtype", default="float32", choices=["float32", "float64"])
+    ap.add_argument("--lse-layout", default="samples", choices=["samples", "rows"],
+                    help="--lse-only: sample-major FP32 store (MIXED's unbinned passes) or row-major")
     ap.add_argument("--hess-only", action="store_true",
                     help="time mbar_hessian (one fused LSE pass + the tensor-core Hessian) on a random K x n problem")
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
@@ -675,7 +693,8 @@ def main():
         achieved = by_l / (ms_l / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "kernel": "lse_pass_kernel<float> (unbinned passes)", "launches": n_l,
+                    "kernel": ("lse_smaj_kernel (unbinned passes, sample-major FP32)" if prec == M.MBAR_MIXED
+                               else "lse_pass_kernel<double> (unbinned passes)"), "launches": n_l,
                     "avg_launch_ms": ms_l / n_l, "bytes_per_launch": by_l / n_l,
                     "peak_source": f"{peaks_src} hbm_gbs"}
     n_h, ms_h, by_h = acc.get(1, [0, 0.0, 0.0])

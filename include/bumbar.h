@@ -282,6 +282,20 @@ BUMBAR_API mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t
                           const double* f, const double* log_N, const int32_t* H, double* Q, void* logden,
                           void* scratch, size_t scratch_bytes, void* stream);
 
+/* The same pass over FP32 data stored sample-major, the layout of MIXED's
+ * unbinned passes: v_nk (device FP32, 16-byte aligned) holds sample p's
+ * K values contiguously at v_nk[p * Kp + k], Kp = K rounded up to a
+ * multiple of 4; the Kp - K padding entries of each sample must be finite
+ * (they get weight 0). Each stage of the pass is then one contiguous run
+ * of samples, fetched by a single bulk copy. f, log_N, H, Q as above;
+ * logden (device FP32[n], nullable) per sample. scratch of at least
+ * mbar_lse_samples_scratch_bytes(K, n) bytes, same rules as above.
+ * EINVAL on bad sizes or alignment, EUNSUPPORTED for K > 1024. */
+BUMBAR_API size_t mbar_lse_samples_scratch_bytes(int64_t K, int64_t n);
+BUMBAR_API mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const double* f,
+                                             const double* log_N, const int32_t* H, double* Q, float* logden,
+                                             void* scratch, size_t scratch_bytes, void* stream);
+
 /* ---------------------------------------------------------------------
  * Allocation-free variant of mbar_lse_pass (no counterpart in the paper;
  * an interface for callers that cannot allocate device memory: for example

@@ -64,8 +64,13 @@ struct mbar_ctx {
   std::vector<double> Nk_h;
   double* Nk_d = nullptr;
   double* logN_d = nullptr;
-  // unbinned data in the current column order
+  // unbinned data in the current column order (allocated when first needed)
   void* v = nullptr;
+  // sample-major copy of the data (vst[n * stage_pitch(K) + k], original
+  // sample order): from creation until v is formed, and for MIXED for good
+  // (the unbinned LSE passes stream it)
+  void* vst = nullptr;
+  float* logden_orig = nullptr;  // MIXED: logden of those passes, original order
   int64_t ld = 0;
   double* cshift = nullptr;  // mixed: per-column shift (current order)
   int32_t* perm = nullptr;   // current column -> original sample
@@ -219,7 +224,16 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   p.skip_if_underflow = mode == kLseModeSci ? 1 : 0;
   const bool timed = !L.binned;
   if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
-  mbar_status s = lse_launch(L.tmap, pl, p, c->dtype, c->st);
+  mbar_status s = MBAR_OK;
+  if (!L.binned && c->dtype == 4 && c->vst) {
+    // unbinned MIXED pass over the sample-major copy (original sample order);
+    // logden comes back to the store's column order through perm
+    p.logden = logden_out ? c->logden_orig : nullptr;
+    s = lse_smaj_launch(static_cast<const float*>(c->vst), lse_smaj_plan(c->K, L.n), p, c->st);
+    if (s == MBAR_OK && logden_out) s = gather_columns(c->logden_orig, logden_out, 4, 1, L.n, L.n, c->perm, c->st);
+  } else {
+    s = lse_launch(L.tmap, pl, p, c->dtype, c->st);
+  }
   if (timed) time_mark(c, false, 0, 0);
   return s;
 }
@@ -372,6 +386,35 @@ mbar_status width_search(mbar_ctx* c, int64_t n, double* w_out, bool* found) {
   return width_search_multi(c, &n, 1, w_out, found);
 }
 
+// Forms the row-major store v from the sample-major staging, columns in the
+// order perm (absolute: column i holds original sample perm[i]); FP64
+// releases the staging.
+mbar_status form_store(mbar_ctx* c, const int32_t* perm) {
+  void* v = nullptr;
+  BUMBAR_TRY(dalloc(c, &v, static_cast<size_t>(c->K) * c->ld * c->dtype));
+  mbar_status s = gather_transpose(c->vst, c->dtype, c->K, c->N, perm, v, c->ld, c->st);
+  if (s != MBAR_OK) {
+    dfree(c, v);
+    return s;
+  }
+  if (c->dtype != 4) {  // MIXED keeps the sample-major copy for its LSE passes
+    dfree(c, c->vst);
+    c->vst = nullptr;
+  }
+  c->v = v;
+  c->full.v = v;
+  BUMBAR_TRY(level_tmap(c, &c->full));
+  if (!c->cur.binned) c->cur = c->full;
+  return MBAR_OK;
+}
+
+// The unbinned store in the current column order (the identity until a
+// coordinate is set).
+mbar_status ensure_store(mbar_ctx* c) {
+  if (c->v) return MBAR_OK;
+  return form_store(c, c->perm);
+}
+
 mbar_status set_coordinate_dev(mbar_ctx* c, const double* phi_orig) {
   // phi in the caller's original order -> current column order
   const int64_t N = c->N;
@@ -379,20 +422,28 @@ mbar_status set_coordinate_dev(mbar_ctx* c, const double* phi_orig) {
   int32_t* perm_rel = nullptr;
   void* tmp = nullptr;
   const size_t stmp = sort_tmp_bytes(N);
+  // while the data is still staged the current order is the original one
+  // (perm = identity) and the store is formed directly in the sorted order
+  const bool staged = c->v == nullptr;
+  const size_t vbytes = staged ? 0 : static_cast<size_t>(c->K) * c->ld * c->dtype;
   BUMBAR_TRY(dalloc_t(c, &phi_cur, N));
   mbar_status s = dalloc_t(c, &perm_rel, N);
-  if (s == MBAR_OK) s = dalloc(c, &tmp, std::max<size_t>(stmp, static_cast<size_t>(c->K) * c->ld * c->dtype));
+  if (s == MBAR_OK) s = dalloc(c, &tmp, std::max<size_t>(stmp, vbytes));
   // phi_cur[i] = phi[perm[i]]
   if (s == MBAR_OK) s = gather_columns(phi_orig, phi_cur, 8, 1, N, N, c->perm, c->st);
   if (s == MBAR_OK) s = sort_coordinate(phi_cur, N, c->phi_sorted, perm_rel, tmp, stmp, c->st);
   if (s == MBAR_OK) s = offsets_from_min(c->phi_sorted, N, c->d_sorted, c->d_pairs, c->st);
   // reorder the data columns and the bookkeeping by perm_rel
-  if (s == MBAR_OK) s = gather_columns(c->v, tmp, c->dtype, c->K, N, c->ld, perm_rel, c->st);
-  if (s == MBAR_OK) {
-    std::swap(c->v, tmp);
-    c->full.v = c->v;
+  if (staged) {
+    if (s == MBAR_OK) s = form_store(c, perm_rel);
+  } else {
+    if (s == MBAR_OK) s = gather_columns(c->v, tmp, c->dtype, c->K, N, c->ld, perm_rel, c->st);
+    if (s == MBAR_OK) {
+      std::swap(c->v, tmp);
+      c->full.v = c->v;
+    }
+    if (s == MBAR_OK) s = level_tmap(c, &c->full);
   }
-  if (s == MBAR_OK) s = level_tmap(c, &c->full);
   if (s == MBAR_OK && c->cshift) {
     s = gather_columns(c->cshift, phi_cur, 8, 1, N, N, perm_rel, c->st);  // phi_cur reused as scratch
     if (s == MBAR_OK) {
@@ -946,6 +997,22 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   rep->n_rebins += nxt.binned ? 1 : 0;
   const int64_t N = c->N;
   const int64_t K = c->K;
+  // MIXED: the pair's FP32 data re-centred per column at the current f, so
+  // the step-to-step rounding of the exponents is that of numbers near 0
+  // (Eq. 3 and the noise floor compare steps at that rounding level)
+  auto recenter_pair = [&]() -> mbar_status {
+    if (c->dtype != 4) return MBAR_OK;
+    for (Level* L : {&cur, &nxt})
+      if (L->binned) BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
+    return MBAR_OK;
+  };
+  s = recenter_pair();
+  if (s != MBAR_OK) {
+    level_free(c, &cur);
+    level_free(c, &nxt);
+    free_rest();
+    return s;
+  }
   // one round: N_intermediate in-place steps on cur, the probe at n (-> ft)
   // and the probe at n * inc (-> fts); the f buffers keep their addresses so
   // the captured round stays valid until the level pair changes
@@ -1016,6 +1083,8 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
       if (!cur.binned || 2.0 * o.inc * static_cast<double>(cur.n_sched) > static_cast<double>(N)) break;
       nxt = take(idx + 1);
       rep->n_rebins += nxt.binned ? 1 : 0;
+      s = recenter_pair();
+      if (s != MBAR_OK) break;
     } else {
       if (cudaMemcpyAsync(c->f, c->ft, K * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess) {
         s = MBAR_ECUDA;
@@ -1248,7 +1317,8 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
 
   if (cudaMemsetAsync(c->bad, 0, sizeof(int), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   if (cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
-  TRYC(dalloc(c, &c->v, static_cast<size_t>(K) * c->ld * c->dtype));
+  TRYC(dalloc(c, &c->vst, static_cast<size_t>(stage_pitch(K)) * N * c->dtype + 16));
+  if (c->dtype == 4) TRYC(dalloc_t(c, &c->logden_orig, N));
   TRYC(dalloc(c, &c->logden, static_cast<size_t>(N) * c->dtype));
   TRYC(dalloc_t(c, &c->perm, N));
   TRYC(dalloc_t(c, &c->seg, N));
@@ -1268,12 +1338,8 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
     }
     u_dev = u_tmp;
   }
-  if (c->dtype == 4) {
-    s = dalloc_t(c, &c->cshift, N);
-    if (s == MBAR_OK) s = shift_to_fp32(u_dev, K, N, N, c->cshift, static_cast<float*>(c->v), c->ld, c->bad, c->st);
-  } else {
-    s = copy_fp64_checked(u_dev, K, N, N, static_cast<double*>(c->v), c->ld, c->bad, c->st);
-  }
+  if (c->dtype == 4) s = dalloc_t(c, &c->cshift, N);
+  if (s == MBAR_OK) s = stage_samples(u_dev, K, N, N, c->cshift, c->vst, c->dtype, c->bad, c->st);
   if (s == MBAR_OK && cudaMemcpyAsync(c->phi0, u_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
     s = MBAR_ECUDA;
   {
@@ -1297,16 +1363,17 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   // LSE scratch sized for the widest grid of this K
   {
     const LsePlan pl = lse_plan(K, N, c->dtype);
-    c->scratch_bytes = lse_scratch_for_grid(K, pl.grid);
+    int grid = pl.grid;
+    if (c->dtype == 4) grid = std::max(grid, lse_smaj_plan(K, N).grid);
+    c->scratch_bytes = lse_scratch_for_grid(K, grid);
     TRYC(dalloc(c, &c->scratch, c->scratch_bytes));
     if (cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   }
   c->full.binned = false;
   c->full.n = N;
   c->full.ld = c->ld;
-  c->full.v = c->v;
+  c->full.v = nullptr;  // formed from the staging by the first call that needs it
   c->full.n_sched = N;
-  TRYC(level_tmap(c, &c->full));
   c->cur = c->full;
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "mbar_create"));
 #undef TRYC
@@ -1432,6 +1499,7 @@ mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   StreamFence fence(c);
+  BUMBAR_TRY(ensure_store(c));
   if (!f_in) {
     set_error("mbar_sci_step: f_in is NULL");
     return MBAR_EINVAL;
@@ -1478,6 +1546,7 @@ mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   StreamFence fence(c);
+  BUMBAR_TRY(ensure_store(c));
   if (!f_in || !hess_out) {
     set_error("mbar_hessian: null pointer argument");
     return MBAR_EINVAL;
@@ -1502,6 +1571,7 @@ mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, dou
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   StreamFence fence(c);
+  BUMBAR_TRY(ensure_store(c));
   if (!f_in) {
     set_error("mbar_newton_step: f_in is NULL");
     return MBAR_EINVAL;
@@ -1540,6 +1610,9 @@ mbar_status mbar_solve(mbar_ctx* c, const double* f_init, mbar_report* report) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
   StreamFence fence(c);
+  // Algorithm 1 bins: store the data directly in the coordinate's order
+  if (c->opts.use_binning && c->K > 1) BUMBAR_TRY(ensure_sorted(c));
+  BUMBAR_TRY(ensure_store(c));
   mbar_report rep{};
   const int64_t K = c->K;
   if (f_init) {
@@ -1581,6 +1654,7 @@ mbar_status mbar_reweight(mbar_ctx* c, const double* u0, int32_t u0_on_device, d
   }
   cudaGetLastError();
   StreamFence fence(c);
+  BUMBAR_TRY(ensure_store(c));
   const int64_t N = c->N;
   double* u0_dev = nullptr;
   void* tmp = nullptr;
@@ -1743,7 +1817,7 @@ mbar_status mbar_destroy(mbar_ctx* c) {
   }
   for (auto e : c->pool) cudaEventDestroy(e);
   level_free(c, &c->cur);
-  void* ptrs[] = {c->weights, c->Nk_d, c->logN_d, c->v,     c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->d_pairs, c->f,
+  void* ptrs[] = {c->weights, c->Nk_d, c->logN_d, c->v, c->vst, c->logden_orig, c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->d_pairs, c->f,
                   c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->stat,
                   c->hess, c->delta,  c->info,  c->bad,    c->logden,  c->scratch,    c->seg,
                   c->start, c->count, c->nb_dev};
@@ -1808,6 +1882,51 @@ mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t K, int64_t
   p.logden = logden;
   p.mode = kLseModePass;
   return lse_launch(map, pl, p, dtype_bytes, static_cast<cudaStream_t>(stream));
+}
+
+size_t mbar_lse_samples_scratch_bytes(int64_t K, int64_t n) {
+  if (K < 1 || K > 1024 || n < 1) return 0;
+  return lse_scratch_for_grid(K, lse_smaj_plan(K, n).grid) + 256;
+}
+
+mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const double* f, const double* log_N,
+                                  const int32_t* H, double* Q, float* logden, void* scratch, size_t scratch_bytes,
+                                  void* stream) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
+  if (!v_nk || !f || !log_N || !Q || !scratch) {
+    set_error("mbar_lse_pass_samples: null pointer argument");
+    return MBAR_EINVAL;
+  }
+  if (K < 1 || n < 1 || n > 2000000000LL) {
+    set_error("mbar_lse_pass_samples: bad sizes K=%lld n=%lld", (long long)K, (long long)n);
+    return MBAR_EINVAL;
+  }
+  if (K > 1024) {
+    set_error("mbar_lse_pass_samples: K=%lld exceeds 1024", (long long)K);
+    return MBAR_EUNSUPPORTED;
+  }
+  if ((reinterpret_cast<uintptr_t>(v_nk) & 15) != 0) {
+    set_error("mbar_lse_pass_samples: v_nk must be 16-byte aligned");
+    return MBAR_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(scratch) & 15) != 0 || scratch_bytes < mbar_lse_samples_scratch_bytes(K, n)) {
+    set_error("mbar_lse_pass_samples: scratch must be 16-byte aligned and at least mbar_lse_samples_scratch_bytes()");
+    return MBAR_EINVAL;
+  }
+  LseParams p{};
+  p.K = static_cast<int>(K);
+  p.n = static_cast<int>(n);
+  p.f = f;
+  p.logN = log_N;
+  p.H = H;
+  unsigned char* sc = static_cast<unsigned char*>(scratch);
+  p.counter = reinterpret_cast<unsigned*>(sc);
+  p.err = reinterpret_cast<unsigned*>(sc + 4);
+  p.partials = reinterpret_cast<double*>(sc + 256);
+  p.Q = Q;
+  p.logden = logden;
+  p.mode = kLseModePass;
+  return lse_smaj_launch(v_nk, lse_smaj_plan(K, n), p, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -12,6 +12,7 @@
 // (__dsub_rn/__ddiv_rn; no contraction into FMA).
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -820,6 +821,61 @@ __global__ void gather_cols_kernel(const T* __restrict__ in, T* __restrict__ out
     if (k0 + r < K) out[(k0 + r) * ld + i] = vals[r];
 }
 
+// v[k][i] = vst[perm[i]][k] (sample pitch stage_pitch(K)): sample-major
+// staging -> row-major store in the new column order. A block takes one 128-byte line of output columns
+// (CS = 32 FP32 / 16 FP64): it reads its CS source samples as contiguous
+// K-vectors into shared memory (pitch P with P words = 1 mod 32, so both
+// the row-wise fill and the column-wise read are conflict-free) and writes
+// every row's CS columns as one full line.
+constexpr int kGtThreads = 256;
+template <typename T>
+__host__ __device__ constexpr int gt_cols() {
+  return 128 / static_cast<int>(sizeof(T));
+}
+template <typename T>
+__host__ __device__ inline int64_t gt_pitch(int64_t K) {
+  // in elements; P * sizeof(T) / 4 = 1 (FP32) or 2 (FP64) mod 32
+  return sizeof(T) == 4 ? (K + 31) / 32 * 32 + 1 : (K + 15) / 16 * 16 + 1;
+}
+template <typename T>
+__global__ void __launch_bounds__(kGtThreads) gather_transpose_kernel(const T* __restrict__ vst, int64_t K, int64_t N,
+                                                                      const int32_t* __restrict__ perm,
+                                                                      T* __restrict__ v, int64_t ld) {
+  constexpr int CS = gt_cols<T>();
+  extern __shared__ __align__(16) unsigned char gt_raw[];
+  T* xs = reinterpret_cast<T*>(gt_raw);  // [CS][P]
+  const int64_t P = gt_pitch<T>(K);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * CS;
+  for (int c = warp; c < CS; c += kGtThreads / 32) {
+    const int64_t i = i0 + c;
+    if (i >= N) break;
+    const T* src = vst + static_cast<int64_t>(perm[i]) * stage_pitch(K);
+    T* dst = xs + c * P;
+    // up to 16 loads in flight per lane (a whole column for K <= 512)
+    for (int64_t k0 = 0; k0 < K; k0 += 16 * 32) {
+      T x[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int64_t k = k0 + lane + 32 * r;
+        if (k < K) x[r] = src[k];
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int64_t k = k0 + lane + 32 * r;
+        if (k < K) dst[k] = x[r];
+      }
+    }
+  }
+  __syncthreads();
+  constexpr int RPW = 32 / CS;  // rows per warp instruction
+  const int c = lane % CS, rs = lane / CS;
+  if (i0 + c >= N) return;
+  const T* col = xs + c * P;
+  T* out = v + i0 + c;
+  for (int64_t k = warp * RPW + rs; k < K; k += (kGtThreads / 32) * RPW) out[k * ld] = col[k];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1070,6 +1126,34 @@ mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int6
                                                     carry1, ntiles);
     count_launches(1);
   }
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+mbar_status gather_transpose(const void* vst, int dtype_bytes, int64_t K, int64_t N, const int32_t* perm, void* v,
+                             int64_t ld, cudaStream_t st) {
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    static bool init = false;
+    if (!init) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      cudaFuncSetAttribute(gather_transpose_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      cudaFuncSetAttribute(gather_transpose_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      init = true;
+    }
+  }
+  if (dtype_bytes == 4) {
+    const size_t smem = static_cast<size_t>(gt_cols<float>()) * gt_pitch<float>(K) * 4;
+    gather_transpose_kernel<float><<<static_cast<unsigned>(ceil_div(N, gt_cols<float>())), kGtThreads, smem, st>>>(
+        static_cast<const float*>(vst), K, N, perm, static_cast<float*>(v), ld);
+  } else {
+    const size_t smem = static_cast<size_t>(gt_cols<double>()) * gt_pitch<double>(K) * 8;
+    gather_transpose_kernel<double><<<static_cast<unsigned>(ceil_div(N, gt_cols<double>())), kGtThreads, smem, st>>>(
+        static_cast<const double*>(vst), K, N, perm, static_cast<double*>(v), ld);
+  }
+  count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
 }

@@ -64,6 +64,14 @@ struct LsePlan {
 
 LsePlan lse_plan(int64_t K, int64_t n, int dtype_bytes);
 bool lse_regs_supported(int64_t K, int dtype_bytes);
+// Sample-major FP32 variant (lse_smaj.cu): v given as vst[n * Kp + k],
+// Kp = K rounded up to 4 (entries k >= K zero), n = prm.n samples; logden
+// (if requested) in the same sample order. Launches the pass and the
+// epilogue.
+LsePlan lse_smaj_plan(int64_t K, int64_t n);
+mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st);
+// The SCI epilogue over the partials of a pass (lse.cu).
+mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream);
 LsePlan lse_regs_plan(int64_t K, int64_t n);
 mbar_status lse_regs_launch(const CUtensorMap& tmap, const LsePlan& pl, const LseParams& prm, cudaStream_t st);
 size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes);
@@ -129,13 +137,22 @@ mbar_status gather_columns(const void* in, void* out, int dtype_bytes, int64_t K
                            const int32_t* perm, cudaStream_t stream);
 
 // ---- data preparation (prep.cu) ----
-// Per-column minimum c[n] over the K rows of FP64 u (row pitch ldu), then
-// v[k][n] = float(u[k][n] - c[n]) with row pitch ldv. Also flags non-finite
-// entries in *bad.
-mbar_status shift_to_fp32(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, float* v, int64_t ldv,
-                          int* bad, cudaStream_t stream);
-mbar_status copy_fp64_checked(const double* u, int64_t K, int64_t N, int64_t ldu, double* v, int64_t ldv, int* bad,
-                              cudaStream_t stream);
+// Sample pitch of the staging: K rounded up to 4 (16-byte aligned samples).
+__host__ __device__ inline int64_t stage_pitch(int64_t K) { return (K + 3) / 4 * 4; }
+// u_kn (K x N FP64, row pitch ldu) -> sample-major staging
+// vst[n * stage_pitch(K) + k] (entries k >= K set to 0): fl32(u - c_n) with
+// c_n = min_k u_kn written to c (dtype_bytes 4), or the FP64 values
+// (dtype_bytes 8; c unused); *bad |= 1 if any entry is not finite.
+mbar_status stage_samples(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, void* vst, int dtype_bytes,
+                          int* bad, cudaStream_t st);
+// v[k * ld + i] = vst[perm[i] * stage_pitch(K) + k] for i < N (the row-major
+// store in the column order perm).
+mbar_status gather_transpose(const void* vst, int dtype_bytes, int64_t K, int64_t N, const int32_t* perm, void* v,
+                             int64_t ld, cudaStream_t st);
+// Adds o_p = max_k (f_k + log N_k - v_kp) to column p of an FP32 K x n
+// matrix (row pitch ld), p < n; K <= 1024.
+mbar_status recenter_columns(float* v, int64_t K, int64_t n, int64_t ld, const double* f, const double* logN,
+                             cudaStream_t st);
 mbar_status check_finite(const double* x, int64_t n, int* bad, cudaStream_t stream);
 
 // ---- Hessian (hessian.cu) ----

@@ -66,14 +66,17 @@ __host__ __device__ inline size_t rup(size_t x, size_t m) { return (x + m - 1) /
 }  // namespace
 
 // Shared-memory carve-up (dynamic, base aligned up to 1024 in the kernel):
-//   stages x stage bytes | a_k [K] | w_c [32] | column partials [2][G][32] |
+//   stages x stage bytes | a_k [K] (FP32: hi [K], lo [K]) | w_c [32] | column partials [2][G][32] |
 //   mbarriers [8]
 template <typename T, int G>
 struct LseSmem {
   static __host__ __device__ size_t stage_bytes(int nbox, int box_rows) {
     return static_cast<size_t>(nbox) * box_rows * 128;
   }
-  static __host__ __device__ size_t a_bytes(int K) { return rup(static_cast<size_t>(K) * sizeof(T), 16); }
+  // FP32: a_k log2(e) as an unevaluated pair, hi [K] then lo [K]
+  static __host__ __device__ size_t a_bytes(int K) {
+    return rup(static_cast<size_t>(K) * sizeof(T) * (sizeof(T) == 4 ? 2 : 1), 16);
+  }
   static constexpr size_t kW = 32 * sizeof(T);
   static constexpr size_t kParts = 2 * G * 32 * sizeof(T);
   static constexpr size_t kBars = 64;
@@ -119,14 +122,28 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
     for (int s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
   }
+  // FP32 keeps the rounding of a_k log2(e) beside it (lo), and of log2(e)
+  // in kLog2eLo, so the state offsets are not quantised to the FP32 spacing
+  // at |a_k| and v carries no systematic scale error: x_kp is rounded once
+  // per entry, not once per row for every column alike
+  T* a_lo = a_s + K;
   for (int k = tid; k < K; k += THREADS) {
     const double a = p.f[k] + p.logN[k];
     if constexpr (sizeof(T) == 4) {
-      a_s[k] = static_cast<T>(a * 1.4426950408889634);
+      const double al = a * 1.4426950408889634;
+      a_s[k] = static_cast<T>(al);
+      a_lo[k] = isfinite(a_s[k]) ? static_cast<T>(al - static_cast<double>(a_s[k])) : T(0);
     } else {
       a_s[k] = static_cast<T>(a);
     }
   }
+  auto xk = [&](int k, T v) -> T {
+    if constexpr (sizeof(T) == 4) {
+      return expo(a_s[k], v) + fmaf(-v, kLog2eLo, a_lo[k]);
+    } else {
+      return expo(a_s[k], v);
+    }
+  };
   __syncthreads();
 
   const uint32_t tx_bytes = static_cast<uint32_t>(sbytes);
@@ -181,10 +198,10 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
       for (; k + R < K; k += 2 * R, off += 2 * kRowStep) {
         const T v0 = *reinterpret_cast<const T*>(tile + off);
         const T v1 = *reinterpret_cast<const T*>(tile + off + kRowStep);
-        m0 = tmax(m0, expo(a_s[k], v0));
-        m1 = tmax(m1, expo(a_s[k + R], v1));
+        m0 = tmax(m0, xk(k, v0));
+        m1 = tmax(m1, xk(k + R, v1));
       }
-      if (k < K) m0 = tmax(m0, expo(a_s[k], *reinterpret_cast<const T*>(tile + off)));
+      if (k < K) m0 = tmax(m0, xk(k, *reinterpret_cast<const T*>(tile + off)));
     }
     T m = tmax(m0, m1);
 #pragma unroll
@@ -204,8 +221,8 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
       for (; k + R < K; k += 2 * R, off += 2 * kRowStep) {
         T* p0 = reinterpret_cast<T*>(tile + off);
         T* p1 = reinterpret_cast<T*>(tile + off + kRowStep);
-        const T e0 = lse_exp(expo(a_s[k], *p0) - m);
-        const T e1 = lse_exp(expo(a_s[k + R], *p1) - m);
+        const T e0 = lse_exp(xk(k, *p0) - m);
+        const T e1 = lse_exp(xk(k + R, *p1) - m);
         *p0 = e0;
         *p1 = e1;
         s0 += e0;
@@ -213,7 +230,7 @@ __global__ void __launch_bounds__(Cfg<T, G>::THREADS, 1) lse_pass_kernel(const _
       }
       if (k < K) {
         T* p0 = reinterpret_cast<T*>(tile + off);
-        const T e0 = lse_exp(expo(a_s[k], *p0) - m);
+        const T e0 = lse_exp(xk(k, *p0) - m);
         *p0 = e0;
         s0 += e0;
       }
@@ -573,12 +590,14 @@ __global__ void __launch_bounds__(kLogThreads) row_logsum_partial(const T* __res
                                                                   const int32_t* __restrict__ H,
                                                                   double* __restrict__ part, int64_t nchunks) {
   const int64_t k = blockIdx.y;
-  const T a = static_cast<T>(f[k] + logN[k]);
+  const double ad = f[k] + logN[k];
+  const T a = static_cast<T>(ad);
+  const T a_lo = isfinite(a) ? static_cast<T>(ad - static_cast<double>(a)) : T(0);  // 0 for FP64
   const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kLogCols;
   const int64_t c1 = (c0 + kLogCols < n) ? c0 + kLogCols : n;
   T m = -INFINITY, s = T(0);
   for (int64_t c = c0 + threadIdx.x; c < c1; c += kLogThreads) {
-    T t = a - v[k * ld + c] - logden[c];
+    T t = (a - v[k * ld + c] - logden[c]) + a_lo;
     if (H) t += log(static_cast<T>(H[c]));
     lse_acc(m, s, t, T(1));
   }

@@ -21,8 +21,18 @@
 // (fixed order, deterministic); at the end a row's slots are summed in order
 // and the common epilogue (lse_common.cuh) runs. H = 1 (two 32-column
 // sub-tiles per stage, no cross-warp exchange) serves K <= 256; H = 2 serves
-// K <= 512. Per entry: one shared-memory read of v and one of a, one FFMA,
-// one max, one SFU ex2, two adds and one FFMA.
+// K <= 512. Per entry: one shared-memory read of v and one of a, two FFMA
+// and an add for x, one max, one SFU ex2, two adds and one FFMA.
+//
+// x_kp = a_k log2(e) - v_kp log2(e) is formed from unevaluated FP32 pairs,
+// (a_hi, a_lo) for the state offset and (kLog2e, kLog2eLo) for the scale.
+// A single FP32 offset would be quantised to the FP32 spacing at |a_k|
+// (about 1e-4 kT at |a_k| ~ 700, as on tempering data spread over hundreds
+// of kT), the same rounding for every column, which turns the SCI map into
+// a step function of f; a single FP32 scale multiplies every v by the same
+// relative error (1.3e-8), which moves the fixed point by 1.3e-8 times the
+// energy differences. With the pairs x_kp is rounded once per entry, at
+// positions that differ from column to column.
 #include <cmath>
 
 #include "common.cuh"
@@ -41,12 +51,12 @@ __host__ __device__ inline size_t rupr(size_t x, size_t m) { return (x + m - 1) 
 
 }  // namespace
 
-// shared memory: stages | a [Kpad] f32 | slots [16][Kpad] f64 | colm[2][32] |
+// shared memory: stages | a [Kpad] (hi, lo) f32 pairs | slots [16][Kpad] f64 | colm[2][32] |
 //                cols[2][32] | mbarriers[8]
 struct RegsSmem {
   static __host__ __device__ size_t kpad(int K) { return rupr(static_cast<size_t>(K), 16); }
   static __host__ __device__ size_t extra(int K, int nslots) {
-    return kpad(K) * 4 + nslots * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64;
+    return kpad(K) * 8 + nslots * kpad(K) * 8 + 2 * 32 * 4 * 2 + 64;
   }
 };
 
@@ -68,8 +78,8 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   const size_t sbytes = SUB * subbytes;
   const size_t kp = RegsSmem::kpad(K);
   unsigned char* cur = smem + p.stages * sbytes;
-  float* a_s = reinterpret_cast<float*>(cur);
-  cur += kp * 4;
+  float2* a_s = reinterpret_cast<float2*>(cur);
+  cur += kp * 8;
   double* slots = reinterpret_cast<double*>(cur);  // [NSLOT][kp]
   cur += NSLOT * kp * 8;
   float* colm = reinterpret_cast<float*>(cur);     // [2][32]
@@ -86,8 +96,11 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     for (int s = 0; s < p.stages; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
   }
-  for (int k = tid; k < static_cast<int>(kp); k += kRThreads)
-    a_s[k] = k < K ? static_cast<float>((p.f[k] + p.logN[k]) * 1.4426950408889634) : 0.f;
+  for (int k = tid; k < static_cast<int>(kp); k += kRThreads) {
+    const double a = k < K ? (p.f[k] + p.logN[k]) * 1.4426950408889634 : 0.0;
+    const float hi = static_cast<float>(a);
+    a_s[k] = make_float2(hi, isfinite(hi) ? static_cast<float>(a - static_cast<double>(hi)) : 0.f);
+  }
   for (int i = tid; i < static_cast<int>(NSLOT * kp); i += kRThreads) slots[i] = 0.0;
   __syncthreads();
 
@@ -150,7 +163,8 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
       const int k = r0 + RG * j;
       if (k < K) {
         const float v = *reinterpret_cast<const float*>(tile + off0 + j * kStep);
-        x[j] = fmaf(-v, kLog2e, a_s[k]);
+        const float2 a = a_s[k];
+        x[j] = fmaf(-v, kLog2e, a.x) + fmaf(-v, kLog2eLo, a.y);
         if (j & 1)
           m1 = fmaxf(m1, x[j]);
         else

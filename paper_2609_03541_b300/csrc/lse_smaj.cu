@@ -1,0 +1,376 @@
+// Sample-major variant of the fused paired-LSE pass (Eq. 1) for FP32 data:
+// the unbinned passes of MIXED read the staging copy of the data, where
+// every sample is one contiguous K-vector (vst[n * Kp + k], Kp = K rounded
+// up to 4, zero padded). For every sample n
+//     logden_n = log sum_j exp(a_j - v_jn),          a_j = f_j + log N_j,
+//     Q_i     += exp(a_i - v_in - logden_n),
+// in one read of v.
+//
+// Layout and schedule (one persistent CTA per SM):
+//   * a stage is S consecutive samples, i.e. ONE contiguous run of S*Kp*4
+//     bytes, fetched by a single 1-D bulk copy (cp.async.bulk) into a ring
+//     of stages; a producer warp issues the copies, the other warps compute.
+//     Long contiguous runs keep the DRAM pages open: the 2-D strip pattern
+//     of the row-major store (128 bytes from each of K rows) measured
+//     4.5 TB/s for the copies alone on B300, contiguous runs 7.1 TB/s;
+//   * LPS lanes own one sample (LPS = 32 for Kp > 64, fewer for small K, so
+//     a warp then takes several samples at once); a lane holds 4*NK entries
+//     of the sample in registers (float4 reads from shared memory), with the
+//     state offsets a_k log2(e) as FP32 (hi, lo) pairs in registers;
+//   * per sample: x = a - v log2(e) (pairs: a_hi, a_lo and kLog2e,
+//     kLog2eLo), max and sum by shuffles within the lane group, e = 2^(x -
+//     max), and the lanes' row partials acc_k += e / sum; a lane group takes
+//     two consecutive samples at once, so each lane runs two independent
+//     dependency chains through the shuffle reductions;
+//   * every 32 samples a warp folds its FP32 partials (and those of its lane
+//     groups) into its FP64 row of shared memory; at the end the warps' rows
+//     are added in warp order (deterministic) and written as the CTA's row
+//     of the partial sums, which lse_epilogue_kernel reduces.
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bumbar {
+
+namespace {
+
+constexpr uint32_t kSmSpin = 1u << 28;  // bounded mbarrier polls
+constexpr int kSmFlush = 32;            // sample slots between FP32 -> FP64 folds
+constexpr int kSmStageBytes = 32 * 1024;
+
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+}  // namespace
+
+// LPS lanes per sample, NK float4 chunks per lane, NT threads (warp 0 is
+// the producer, the other NT / 32 - 1 warps compute).
+template <int LPS, int NK, int NT>
+__global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict__ vst, int Kp, int S, int stages,
+                                                         LseParams p) {
+  constexpr int SPW = 32 / LPS;  // samples per warp at once
+  constexpr int NWC = NT / 32 - 1;  // compute warps
+  constexpr int E = 4 * NK;      // entries per lane
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int K = p.K;
+  const int64_t n = p.n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (lse_skip(p)) return;
+
+  const size_t sbytes = static_cast<size_t>(S) * Kp * 4;
+  double* slots64 = reinterpret_cast<double*>(smem + stages * sbytes);  // [NWC][Kp] FP64 row partials
+  uint64_t* full = reinterpret_cast<uint64_t*>(slots64 + static_cast<size_t>(NWC) * Kp);
+  uint64_t* empty = full + stages;
+  int* abort_flag = reinterpret_cast<int*>(empty + stages);
+
+  const int64_t nchunks = (n + S - 1) / S;
+  const int64_t first = blockIdx.x, stride = gridDim.x;
+  const int count = first < nchunks ? static_cast<int>((nchunks - 1 - first) / stride + 1) : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NWC);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  for (int i = tid; i < NWC * Kp; i += NT) slots64[i] = 0.0;
+  __syncthreads();
+
+  const int lig = lane % LPS;  // lane in group
+  const int grp = lane / LPS;  // sample group within the warp
+
+  if (warp == 0) {
+    // ---- producer: one elected lane issues the ring of bulk copies ----
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < count; ++it) {
+        const int s = it % stages;
+        if (it >= stages) {
+          if (!mbar_wait_bounded(&empty[s], static_cast<uint32_t>((it / stages - 1) & 1), kSmSpin)) {
+            atomicAdd(p.err, 1u);
+            *reinterpret_cast<volatile int*>(abort_flag) = 1;
+            break;
+          }
+        }
+        if (*reinterpret_cast<volatile int*>(abort_flag)) break;
+        const int64_t chunk = first + static_cast<int64_t>(it) * stride;
+        const int64_t n0 = chunk * S;
+        const int64_t ns = (n - n0 < S) ? n - n0 : S;
+        // the bytes of ns samples, rounded up to 16 (the staging buffer has
+        // 16 bytes of slack after its last sample)
+        const uint32_t bytes = static_cast<uint32_t>((ns * Kp * 4 + 15) / 16 * 16);
+        mbar_expect_tx(&full[s], bytes);
+        bulk_load_1d(smem + s * sbytes, vst + n0 * Kp, bytes, &full[s]);
+        ++issued;
+      }
+      // copies still in flight when leaving early: wait for them (bounded)
+      for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
+        (void)mbar_wait_bounded(&full[it % stages], static_cast<uint32_t>((it / stages) & 1), kSmSpin);
+    }
+  } else {
+    // ---- compute warps ----
+    const int cw = warp - 1;
+    // this lane's entries: k = 4 * (lig + LPS * i) + t
+    float ahi[E], alo[E];
+#pragma unroll
+    for (int i = 0; i < NK; ++i)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = 4 * (lig + LPS * i) + t;
+        if (k < K) {
+          const double a = (p.f[k] + p.logN[k]) * 1.4426950408889634;
+          const float hi = static_cast<float>(a);
+          ahi[4 * i + t] = hi;
+          alo[4 * i + t] = isfinite(hi) ? static_cast<float>(a - static_cast<double>(hi)) : 0.f;  // N_k = 0: -inf
+        } else {
+          ahi[4 * i + t] = -INFINITY;  // padding rows: weight 0
+          alo[4 * i + t] = 0.f;
+        }
+      }
+    float acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = 0.f;
+    int slots = 0;
+    double* myslots = slots64 + static_cast<size_t>(cw) * Kp;
+    auto fold = [&]() {
+#pragma unroll
+      for (int i = 0; i < NK; ++i)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int e = 4 * i + t;
+          float v = acc[e];
+#pragma unroll
+          for (int o = LPS; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          const int k = 4 * (lig + LPS * i) + t;
+          if (grp == 0 && k < Kp) myslots[k] += static_cast<double>(v);
+          acc[e] = 0.f;
+        }
+    };
+    for (int it = 0; it < count; ++it) {
+      const int s = it % stages;
+      const bool ok = mbar_wait_bounded(&full[s], static_cast<uint32_t>((it / stages) & 1), kSmSpin);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) {
+          atomicAdd(p.err, 1u);
+          *reinterpret_cast<volatile int*>(abort_flag) = 1;
+        }
+        break;
+      }
+      const int64_t n0 = (first + static_cast<int64_t>(it) * stride) * S;
+      const int ns = static_cast<int>((n - n0 < S) ? n - n0 : S);
+      const unsigned char* stage = smem + s * sbytes;
+      // sample slots in pairs (two consecutive samples per lane group, two
+      // independent dependency chains per lane); the pairs go round-robin
+      // over the compute warps across stages, so no warp takes the extra
+      // pair of every stage
+      const int npairs = (ns + 2 * SPW - 1) / (2 * SPW);
+      const int npairs_full = (S + 2 * SPW - 1) / (2 * SPW);
+      int ps = cw - static_cast<int>((static_cast<int64_t>(it) * npairs_full) % NWC);
+      if (ps < 0) ps += NWC;
+      for (; ps < npairs; ps += NWC) {
+        const int j0 = (2 * ps) * SPW + grp, j1 = (2 * ps + 1) * SPW + grp;
+        const bool v0 = j0 < ns, v1 = j1 < ns;
+        const float* c0 = reinterpret_cast<const float*>(stage + static_cast<size_t>(v0 ? j0 : 0) * Kp * 4);
+        const float* c1 = reinterpret_cast<const float*>(stage + static_cast<size_t>(v1 ? j1 : 0) * Kp * 4);
+        float x0[E], x1[E];
+        float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+        for (int i = 0; i < NK; ++i) {
+          const int k4 = 4 * (lig + LPS * i);
+          float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+          if (k4 < Kp) {
+            a = *reinterpret_cast<const float4*>(c0 + k4);
+            b = *reinterpret_cast<const float4*>(c1 + k4);
+          }
+          const float va[4] = {a.x, a.y, a.z, a.w}, vb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int e = 4 * i + t;
+            x0[e] = fmaf(-va[t], kLog2e, ahi[e]) + fmaf(-va[t], kLog2eLo, alo[e]);
+            x1[e] = fmaf(-vb[t], kLog2e, ahi[e]) + fmaf(-vb[t], kLog2eLo, alo[e]);
+            m0 = fmaxf(m0, x0[e]);
+            m1 = fmaxf(m1, x1[e]);
+          }
+        }
+#pragma unroll
+        for (int o = LPS / 2; o >= 1; o >>= 1) {
+          m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+          m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        }
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          x0[e] = ex2_approx(x0[e] - m0);
+          x1[e] = ex2_approx(x1[e] - m1);
+          s0 += x0[e];
+          s1 += x1[e];
+        }
+#pragma unroll
+        for (int o = LPS / 2; o >= 1; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        float w0 = 0.f, w1 = 0.f;
+        if (v0) {
+          const int64_t gn = n0 + j0;
+          w0 = (p.H ? static_cast<float>(p.H[gn]) : 1.f) / s0;
+          if (p.logden != nullptr && lig == 0) static_cast<float*>(p.logden)[gn] = (m0 + __log2f(s0)) * kLn2;
+        }
+        if (v1) {
+          const int64_t gn = n0 + j1;
+          w1 = (p.H ? static_cast<float>(p.H[gn]) : 1.f) / s1;
+          if (p.logden != nullptr && lig == 0) static_cast<float*>(p.logden)[gn] = (m1 + __log2f(s1)) * kLn2;
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = fmaf(x1[e], w1, fmaf(x0[e], w0, acc[e]));
+        slots += 2;
+        if (slots >= kSmFlush) {
+          fold();
+          slots = 0;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    fold();
+  }
+
+  // ---- per-CTA row sums: the compute warps' FP64 partials in warp order ----
+  __syncthreads();
+  double* out = p.partials + static_cast<size_t>(blockIdx.x) * K;
+  for (int k = tid; k < K; k += NT) {
+    double t = 0.0;
+    for (int w = 0; w < NWC; ++w) t += slots64[static_cast<size_t>(w) * Kp + k];
+    out[k] = t;
+  }
+}
+
+namespace {
+
+// lanes per sample: the smallest power of two whose lanes cover Kp / 4
+// float4 chunks, at most 32; float4 chunks per lane beyond that
+void smaj_shape(int64_t K, int* lps, int* nk, int* nt) {
+  const int64_t q = round_up(K, 4) / 4;
+  int l = 1;
+  while (l < 32 && l < q) l <<= 1;
+  *lps = l;
+  *nk = static_cast<int>(ceil_div(q, l));
+  *nt = *nk <= 4 ? 512 : 256;  // 15 or 7 compute warps + the producer warp
+}
+
+template <int LPS, int NK, int NT>
+void smaj_attr(size_t smem) {
+  cudaFuncSetAttribute(lse_smaj_kernel<LPS, NK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(smem));
+}
+
+template <int LPS, int NK, int NT>
+void smaj_run(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm, cudaStream_t st) {
+  static bool init = false;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (!init) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      smaj_attr<LPS, NK, NT>(static_cast<size_t>(optin));
+      init = true;
+    }
+  }
+  lse_smaj_kernel<LPS, NK, NT><<<pl.grid, NT, pl.smem, st>>>(vst, Kp, pl.C, pl.stages, prm);
+}
+
+}  // namespace
+
+LsePlan lse_smaj_plan(int64_t K, int64_t n) {
+  LsePlan pl{};
+  int lps = 0, nk = 0, nt = 0;
+  smaj_shape(K, &lps, &nk, &nt);
+  const int64_t Kp = round_up(K, 4);
+  const int spw = 32 / lps;
+  // samples per stage: about 32 KB, a multiple of 4 (16-byte aligned runs)
+  // and at least one sample slot per compute warp
+  int64_t S = std::max<int64_t>(kSmStageBytes / (Kp * 4), 1);
+  S = std::max<int64_t>(S, static_cast<int64_t>(spw) * (nt / 32 - 1));
+  S = round_up(S, 4);
+  const size_t sb = static_cast<size_t>(S) * Kp * 4;
+  const size_t part = static_cast<size_t>(nt / 32 - 1) * Kp * 8;
+  int stages = 6;
+  while (stages > 2 && stages * sb + part > 200 * 1024) --stages;
+  pl.variant = 2;
+  pl.C = static_cast<int>(S);
+  pl.stages = stages;
+  pl.threads = nt;
+  pl.J = nk;
+  pl.H = lps;
+  pl.num_strips = static_cast<int>(ceil_div(n, S));
+  pl.smem = stages * sb + part + 2 * stages * 8 + 16 + 1024;
+  static int optin = -1;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (optin < 0) {
+      int dev = 0, v = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      cudaGetLastError();
+      optin = v;
+    }
+  }
+  pl.ok = optin > 0 && pl.smem <= static_cast<size_t>(optin);
+  pl.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(pl.num_strips, num_sms())));
+  return pl;
+}
+
+bool lse_smaj_supported(int64_t K) { return K >= 1 && K <= 1024; }
+
+mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st) {
+  if (!pl.ok) {
+    set_error("lse pass: %zu bytes of shared memory per CTA exceed the device limit", pl.smem);
+    return MBAR_EUNSUPPORTED;
+  }
+  prm.nparts = pl.grid;
+  prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
+  const int Kp = static_cast<int>(round_up(prm.K, 4));
+  const int lps = pl.H, nk = pl.J;
+  if (lps < 32) {
+    switch (lps) {
+      case 1: smaj_run<1, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 2: smaj_run<2, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 4: smaj_run<4, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 8: smaj_run<8, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 16: smaj_run<16, 1, 512>(pl, vst, Kp, prm, st); break;
+      default: set_error("lse_smaj_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+    }
+  } else {
+    switch (nk) {
+      case 1: smaj_run<32, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 2: smaj_run<32, 2, 512>(pl, vst, Kp, prm, st); break;
+      case 3: smaj_run<32, 3, 512>(pl, vst, Kp, prm, st); break;
+      case 4: smaj_run<32, 4, 512>(pl, vst, Kp, prm, st); break;
+      case 5: smaj_run<32, 5, 256>(pl, vst, Kp, prm, st); break;
+      case 6: smaj_run<32, 6, 256>(pl, vst, Kp, prm, st); break;
+      case 7: smaj_run<32, 7, 256>(pl, vst, Kp, prm, st); break;
+      case 8: smaj_run<32, 8, 256>(pl, vst, Kp, prm, st); break;
+      default: set_error("lse_smaj_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+    }
+  }
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return lse_epilogue_launch(prm, st);
+}
+
+}  // namespace bumbar

@@ -6,6 +6,7 @@
 // between numerator and denominator of Eq. 1), the stored magnitudes stay
 // small for the entries that carry weight, and every v_kn >= 0.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -14,11 +15,8 @@ namespace bumbar {
 
 namespace {
 
-// Persistent blocks, each handling strips of 32 columns: 8 row groups x 32
-// columns, eight rows in flight per thread. Pass 1 takes the column minimum with integer comparisons on an
-// order-preserving image of the binary64 bits (FP64 arithmetic is slow on
-// this part); pass 2 re-reads the same 32 x K block -- few enough blocks are
-// resident that it is still in L2 -- and writes fl32(u - min).
+// Column minima are taken with integer comparisons on an order-preserving
+// image of the binary64 bits (FP64 arithmetic is slow on this part).
 __device__ __forceinline__ unsigned long long ordered_bits(double x) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
@@ -72,89 +70,157 @@ __device__ __forceinline__ bool split_f64(double x, float& hi, float& lo) {
   return true;
 }
 
-__global__ void __launch_bounds__(256) shift_fp32_kernel(const double* __restrict__ u, int64_t K, int64_t N,
-                                                         int64_t ldu, double* __restrict__ c, float* __restrict__ v,
-                                                         int64_t ldv, int* bad) {
-  __shared__ unsigned long long part[8][32];
-  __shared__ int okp[8][32];
-  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
-  const int64_t nstrips = (N + 31) / 32;
-  for (int64_t strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
-    const int64_t n = strip * 32 + lane;
-    unsigned long long m = ~0ull;
-    bool ok = true;
-    if (n < N) {
-      // eight independent loads in flight per thread
-      int64_t k = rg;
-      for (; k + 56 < K; k += 64) {
-        double x[8];
+// Staging at creation, sample-major: block b takes the kStageCols samples
+// n0 = b * kStageCols .. n0 + kStageCols - 1 with all K rows into shared
+// memory (one read of u, 128-byte row pieces), takes each column's minimum
+// there (MIXED) and writes the samples out as contiguous K-vectors,
+// vst[n * stage_pitch(K) + k], padded with zeros to a multiple of 4 entries
+// so every sample starts 16-byte aligned. The later reordering by the bin
+// coordinate then moves whole contiguous samples (gather_transpose in
+// binning.cu) instead of single elements of K separate rows, and the
+// unbinned LSE passes of MIXED stream it as contiguous runs (lse_smaj.cu).
+constexpr int kStageCols = 16;
+constexpr int kStageThreads = 256;
+constexpr int kStageRows = kStageThreads / kStageCols;  // row residues covered at once
+constexpr int kStagePitch = kStageCols + 1;             // shared-memory row pitch (doubles)
+
+size_t stage_smem_bytes(int64_t K) { return static_cast<size_t>(K) * kStagePitch * sizeof(double); }
+
+template <bool kShift>
+__global__ void __launch_bounds__(kStageThreads) stage_kernel(const double* __restrict__ u, int64_t K, int64_t N,
+                                                              int64_t ldu, double* __restrict__ c,
+                                                              void* __restrict__ vst, int* bad) {
+  extern __shared__ double xs[];  // [K][kStagePitch]
+  __shared__ unsigned long long part[kStageRows][kStageCols];
+  __shared__ int okp[kStageRows][kStageCols];
+  __shared__ double cmin[kStageCols];
+  __shared__ float mhs[kStageCols], mls[kStageCols];
+  __shared__ int msp[kStageCols];
+  const int t = threadIdx.x;
+  const int j = t % kStageCols, g = t / kStageCols;
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * kStageCols;
+  const int64_t n = n0 + j;
+  const bool inb = n < N;
+  unsigned long long m = ~0ull;
+  bool ok = true;
+  auto take = [&](int64_t k, double x) {
+    xs[k * kStagePitch + j] = x;
+    const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+    ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
+    if constexpr (kShift) {
+      const unsigned long long kx = ordered_bits(x);
+      m = kx < m ? kx : m;
+    }
+  };
+  if (inb) {
+    // sixteen independent loads in flight per thread (K <= 256 in one batch)
+    for (int64_t k0 = g; k0 < K; k0 += 16 * kStageRows) {
+      double x[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = u[(k + 8 * j) * ldu + n];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x[j]));
-          ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
-          const unsigned long long kx = ordered_bits(x[j]);
-          m = kx < m ? kx : m;
-        }
+      for (int r = 0; r < 16; ++r) {
+        const int64_t k = k0 + r * kStageRows;
+        if (k < K) x[r] = __ldg(u + k * ldu + n);
       }
-      for (; k < K; k += 8) {
-        const double x = u[k * ldu + n];
-        const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
-        ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
-        const unsigned long long kx = ordered_bits(x);
-        m = kx < m ? kx : m;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int64_t k = k0 + r * kStageRows;
+        if (k < K) take(k, x[r]);
       }
     }
-    part[rg][lane] = m;
-    okp[rg][lane] = ok ? 1 : 0;
-    __syncthreads();
-    unsigned long long mm = part[0][lane];
-    int allok = okp[0][lane];
+  }
+  part[g][j] = m;
+  okp[g][j] = ok ? 1 : 0;
+  __syncthreads();
+  if (t < kStageCols && n0 + t < N) {
+    unsigned long long mm = part[0][t];
+    int allok = okp[0][t];
 #pragma unroll
-    for (int g = 1; g < 8; ++g) {
-      mm = part[g][lane] < mm ? part[g][lane] : mm;
-      allok &= okp[g][lane];
+    for (int r = 1; r < kStageRows; ++r) {
+      mm = part[r][t] < mm ? part[r][t] : mm;
+      allok &= okp[r][t];
     }
-    __syncthreads();
-    if (n < N) {
-      double cm = from_ordered(mm);
-      if (!allok) {
-        if (rg == 0) atomicOr(bad, 1);
-        cm = 0.0;
-      }
-      if (rg == 0) c[n] = cm;
+    if (!allok) atomicOr(bad, 1);
+    if constexpr (kShift) {
+      const double cm = allok ? from_ordered(mm) : 0.0;
+      c[n0 + t] = cm;
+      cmin[t] = cm;
+      float mh = 0.f, ml = 0.f;
+      msp[t] = (split_f64(cm, mh, ml) || cm == 0.0) ? 1 : 0;
+      mhs[t] = mh;
+      mls[t] = ml;
+    }
+  }
+  __syncthreads();
+  // sample-major write-out: the block's samples form one contiguous run
+  const int64_t Kp = stage_pitch(K);
+  const int ncols = static_cast<int>(N - n0 < kStageCols ? N - n0 : kStageCols);
+  for (int jj = 0; jj < ncols; ++jj) {
+    if constexpr (kShift) {
       // v = (uh - mh) + (ul - ml) in FP32 from the hi/lo splits of u and of
       // the column minimum (no FP64 arithmetic in the common case); FP64
       // subtraction for values outside the split's range
-      float mh = 0.f, ml = 0.f;
-      const bool msplit = split_f64(cm, mh, ml) || cm == 0.0;
-      auto shifted = [&](double x) -> float {
-        float xh, xl;
-        if (msplit && split_f64(x, xh, xl)) return __fadd_rn(__fsub_rn(xh, mh), __fsub_rn(xl, ml));
-        return f64_to_f32_rn(x - cm);
-      };
-      int64_t k = rg;
-      for (; k + 56 < K; k += 64) {
-        double x[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = u[(k + 8 * j) * ldu + n];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[(k + 8 * j) * ldv + n] = shifted(x[j]);
+      const double cm = cmin[jj];
+      const float mh = mhs[jj], ml = mls[jj];
+      const bool msplit = msp[jj] != 0;
+      float* out = static_cast<float*>(vst) + (n0 + jj) * Kp;
+      for (int64_t k = t; k < Kp; k += kStageThreads) {
+        float r = 0.f;
+        if (k < K) {
+          const double x = xs[k * kStagePitch + jj];
+          float xh, xl;
+          if (msplit && split_f64(x, xh, xl))
+            r = __fadd_rn(__fsub_rn(xh, mh), __fsub_rn(xl, ml));
+          else
+            r = f64_to_f32_rn(x - cm);
+        }
+        out[k] = r;
       }
-      for (; k < K; k += 8) v[k * ldv + n] = shifted(u[k * ldu + n]);
+    } else {
+      double* out = static_cast<double*>(vst) + (n0 + jj) * Kp;
+      for (int64_t k = t; k < Kp; k += kStageThreads) out[k] = k < K ? xs[k * kStagePitch + jj] : 0.0;
     }
   }
 }
 
-__global__ void copy_checked_kernel(const double* __restrict__ u, int64_t K, int64_t N, int64_t ldu,
-                                    double* __restrict__ v, int64_t ldv, int* bad) {
-  const int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t k = blockIdx.y;
-  if (n >= N) return;
-  const double x = u[k * ldu + n];
-  if (!isfinite(x)) atomicOr(bad, 1);
-  v[k * ldv + n] = x;
+// Per-column re-centring of a binned FP32 level at the current f: column p
+// gets o_p = max_k (a_k - v_kp), a_k = f_k + ln N_k, added to every entry,
+// so the exponents a_k - v_kp of its dominant states are near 0 instead of
+// near the size of a_k. A per-column shift leaves Eq. 1 unchanged (it
+// cancels between numerator and denominator); the FP32 rounding of the
+// shifted values is a fixed perturbation of the level's data, while the
+// rounding of the exponents, which moves with f from step to step, is then
+// that of numbers near 0.
+constexpr int kRecCols = 32;
+constexpr int kRecGroups = 8;  // row groups (warps) per block
+__global__ void __launch_bounds__(kRecCols * kRecGroups) recenter_kernel(float* __restrict__ v, int64_t K, int64_t n,
+                                                                         int64_t ld, const double* __restrict__ f,
+                                                                         const double* __restrict__ logN) {
+  __shared__ float a_s[1024];
+  __shared__ float part[kRecGroups][kRecCols];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  for (int64_t k = threadIdx.x; k < K; k += kRecCols * kRecGroups) a_s[k] = static_cast<float>(f[k] + logN[k]);
+  __syncthreads();
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * kRecCols + lane;
+  float m = -INFINITY;
+  if (p < n) {
+    // rows grp, grp + 8, ...; eight loads in flight
+    for (int64_t k0 = grp; k0 < K; k0 += 8 * kRecGroups) {
+      float x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t k = k0 + r * kRecGroups;
+        x[r] = k < K ? a_s[k] - v[k * ld + p] : -INFINITY;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) m = fmaxf(m, x[r]);
+    }
+  }
+  part[grp][lane] = m;
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < kRecGroups; ++g) m = fmaxf(m, part[g][lane]);
+  if (p >= n) return;
+  for (int64_t k = grp; k < K; k += kRecGroups) v[k * ld + p] += m;
 }
 
 __global__ void finite_kernel(const double* __restrict__ x, int64_t n, int* bad) {
@@ -172,20 +238,37 @@ __global__ void add_gauge_kernel(const double* __restrict__ f, const double* __r
 
 }  // namespace
 
-mbar_status shift_to_fp32(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, float* v, int64_t ldv,
+mbar_status stage_samples(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, void* vst, int dtype_bytes,
                           int* bad, cudaStream_t st) {
-  const int64_t strips = ceil_div(N, 32);
-  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(strips, 4 * static_cast<int64_t>(num_sms())));
-  shift_fp32_kernel<<<grid, 256, 0, st>>>(u, K, N, ldu, c, v, ldv, bad);
+  const size_t smem = stage_smem_bytes(K);
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    static bool init = false;
+    if (!init) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      const int lim = optin - 8 * 1024;  // room for the static arrays
+      cudaFuncSetAttribute(stage_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(stage_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      init = true;
+    }
+  }
+  const unsigned grid = static_cast<unsigned>(ceil_div(N, kStageCols));
+  if (dtype_bytes == 4)
+    stage_kernel<true><<<grid, kStageThreads, smem, st>>>(u, K, N, ldu, c, vst, bad);
+  else
+    stage_kernel<false><<<grid, kStageThreads, smem, st>>>(u, K, N, ldu, c, vst, bad);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;
 }
 
-mbar_status copy_fp64_checked(const double* u, int64_t K, int64_t N, int64_t ldu, double* v, int64_t ldv, int* bad,
-                              cudaStream_t st) {
-  const dim3 g(static_cast<unsigned>(ceil_div(N, kThreads)), static_cast<unsigned>(K));
-  copy_checked_kernel<<<g, kThreads, 0, st>>>(u, K, N, ldu, v, ldv, bad);
+mbar_status recenter_columns(float* v, int64_t K, int64_t n, int64_t ld, const double* f, const double* logN,
+                             cudaStream_t st) {
+  if (n < 1) return MBAR_OK;
+  recenter_kernel<<<static_cast<unsigned>(ceil_div(n, kRecCols)), kRecCols * kRecGroups, 0, st>>>(v, K, n, ld, f,
+                                                                                                 logN);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;

@@ -135,6 +135,9 @@ _SIGNATURES = {
     "mbar_lse_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32], ctypes.c_size_t),
     "mbar_lse_pass": ([_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
                        _vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
+    "mbar_lse_samples_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_size_t),
+    "mbar_lse_pass_samples": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                               _vp], ctypes.c_int),
 }
 
 
@@ -366,6 +369,26 @@ def lse_pass(v, f, log_N, Q, H=None, logden=None, scratch=None, stream=None):
     st = stream.cuda_stream if stream is not None else 0
     _check(lib().mbar_lse_pass(
         ctypes.c_void_p(v.data_ptr()), eb, K, n, int(v.stride(0)),
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(log_N.data_ptr()),
+        ctypes.c_void_p(H.data_ptr()) if H is not None else None,
+        ctypes.c_void_p(Q.data_ptr()),
+        ctypes.c_void_p(logden.data_ptr()) if logden is not None else None,
+        ctypes.c_void_p(scratch.data_ptr()), int(scratch.numel()), ctypes.c_void_p(st)))
+
+
+def lse_samples_scratch_bytes(K: int, n: int) -> int:
+    return int(lib().mbar_lse_samples_scratch_bytes(int(K), int(n)))
+
+
+def lse_pass_samples(v_nk, K, f, log_N, Q, H=None, logden=None, scratch=None, stream=None):
+    """``mbar_lse_pass_samples``: the fused LSE pass over a sample-major
+    float32 CUDA tensor ``v_nk`` of shape (n, Kp), Kp = K rounded up to 4
+    (padding entries finite). ``scratch``: uint8 tensor of
+    ``lse_samples_scratch_bytes`` bytes, zero before its first use."""
+    n = int(v_nk.shape[0])
+    st = stream.cuda_stream if stream is not None else 0
+    _check(lib().mbar_lse_pass_samples(
+        ctypes.c_void_p(v_nk.data_ptr()), int(K), n,
         ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(log_N.data_ptr()),
         ctypes.c_void_p(H.data_ptr()) if H is not None else None,
         ctypes.c_void_p(Q.data_ptr()),

@@ -330,6 +330,43 @@ def test_lse_pass_stateless(dtype):
     assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - O.log_denominator(u, f, Nk))) < tol * 100
 
 
+@pytest.mark.parametrize("K,N", [(1, 7), (3, 4099), (8, 3), (37, 5001), (64, 1000), (130, 2049), (500, 1333),
+                                 (1000, 777)])
+@pytest.mark.parametrize("counts", [False, True])
+def test_lse_pass_sample_major(K, N, counts):
+    """The sample-major FP32 pass (the layout of MIXED's unbinned passes):
+    every lane-group shape, ragged last stages, per-sample counts H, and
+    padding entries that must get weight 0."""
+    import torch
+    u, Nk = rand_problem(K, N, seed=K + 7 * N)
+    f = rand_f(K, seed=5)
+    dev = torch.device("cuda")
+    Kp = (K + 3) // 4 * 4
+    v = torch.full((N, Kp), 7.0, dtype=torch.float32, device=dev)   # padding: finite, weight 0
+    v[:, :K] = torch.from_numpy(np.ascontiguousarray(u.T)).to(dev, torch.float32)
+    H = None
+    Hn = np.ones(N)
+    if counts:
+        Hn = 1.0 + (np.arange(N) % 5)
+        H = torch.from_numpy(Hn.astype(np.int32)).to(dev)
+    ft = torch.from_numpy(f).to(dev)
+    lN = torch.from_numpy(np.log(Nk.astype(np.float64))).to(dev)
+    Q = torch.empty(K, dtype=torch.float64, device=dev)
+    logden = torch.empty(N, dtype=torch.float32, device=dev)
+    scratch = torch.zeros(M.lse_samples_scratch_bytes(K, N), dtype=torch.uint8, device=dev)
+    for _ in range(2):
+        M.lse_pass_samples(v, K, ft, lN, Q, H=H, logden=logden, scratch=scratch)
+    torch.cuda.synchronize()
+    u32 = u.astype(np.float32).astype(np.float64)        # the data as stored
+    ld_ref = O.log_denominator(u32, f, Nk)
+    Q_ref = Nk * (O.mbar_weights(u32, f, Nk) * Hn[None, :]).sum(axis=1)
+    Qg = Q.cpu().numpy()
+    occupied = Nk > 0                                  # N // K < 1 leaves states without samples
+    assert np.max(np.abs(Qg[occupied] - Q_ref[occupied]) / Q_ref[occupied]) < 1e-5
+    assert np.all(Qg[~occupied] == 0.0)
+    assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - ld_ref)) < 1e-4
+
+
 @pytest.mark.parametrize("case", ["gaussian", "umbrella_h0", "harmonic_wide"])
 def test_algorithm1_trajectory_matches_oracle_fp64(case):
     """Every Eq. 3 check of the second loop (level size, s_n, s_next) and the
@@ -410,3 +447,57 @@ def test_parallel_tempering_trajectory_matches_oracle_fp64():
                 assert a == pytest.approx(b, rel=1e-6)
             else:
                 assert a < 1e-9
+
+
+def test_mixed_tempering_offsets_are_not_quantised():
+    """States whose offsets a_k = f_k + ln N_k reach hundreds of kT (the
+    tempering spread) keep their full precision in the FP32 passes: MIXED's
+    loops stop about where FP64's do, instead of cycling at the FP32 spacing
+    of a_k (4e-5 kT at |a_k| ~ 760) until max_sci, and it ends within
+    3 f_tol of the oracle (the FP32 log2(e) alone biased it by 1e-5 kT)."""
+    p = W.parallel_tempering(K=16, N_k=1500, seed=6)
+    f_ref = O.solve_mbar(p.u_kn, p.N_k)
+    out = {}
+    for prec in (M.MBAR_FP64, M.MBAR_MIXED):
+        ctx = M.Context(p.u_kn, p.N_k, prec)
+        ctx.set_coordinate(p.phi)
+        rep = ctx.solve().as_dict()
+        out[prec] = (ctx.free_energies(), rep)
+        ctx.close()
+    assert np.max(np.abs(f_ref[1:] - f_ref[:-1])) > 10.0     # the spread is really there
+    f, rep = out[M.MBAR_MIXED]
+    _, rep64 = out[M.MBAR_FP64]
+    assert np.max(np.abs(f - f_ref)) < 3e-5, rep
+    sci = rep["iters_first_loop"] + rep["iters_second_loop"]
+    sci64 = rep64["iters_first_loop"] + rep64["iters_second_loop"]
+    assert sci <= 2 * sci64 + 500, (rep, rep64)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,N", [(3, 37), (500, 4133), (1000, 1031)])
+def test_store_formed_late_or_early_is_the_same(prec, K, N):
+    """The data is staged sample-major at creation and stored row-major by
+    the first call that needs it: in the coordinate's order when that call is
+    the coordinate (one gather of whole samples), in the original order
+    otherwise (a later coordinate then reorders the stored columns). Both
+    routes end in the same store: identical SCI steps and solves."""
+    u, Nk = rand_problem(K, N, seed=K, offset=50.0)
+    phi = u[0] + 0.01 * np.arange(N) % 7
+    f = rand_f(K)
+    a = M.Context(u, Nk, PREC[prec])            # coordinate first
+    a.set_coordinate(phi)
+    b = M.Context(u, Nk, PREC[prec])            # unbinned step first, coordinate later
+    fb0, _, _, ldb0 = b.sci_step(f, want_logden=True)
+    b.set_coordinate(phi)
+    fa, ga, sa, lda = a.sci_step(f, want_logden=True)
+    fb, gb, sb, ldb = b.sci_step(f, want_logden=True)
+    tol = F_TOL[prec]
+    assert np.max(np.abs(fb0 - O.gauge(O.sci_step(u, f, Nk)))) < tol
+    assert np.array_equal(fa, fb) and np.array_equal(lda, ldb) and sa == sb and np.array_equal(ga, gb)
+    assert np.max(np.abs(ldb0 - ldb)) < tol
+    if K <= 500:
+        a.solve()
+        b.solve()
+        assert np.array_equal(a.free_energies(), b.free_energies())
+    a.close()
+    b.close()
