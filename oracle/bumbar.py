@@ -25,6 +25,9 @@ Section map (BU-MBAR: Mueller, Alesiani, Christiansen):
                                    ones of the convex MBAR objective)
   Eqs. 5-6     reweight            per-sample weights at a target state
   Eq. 7        mae
+  (none)       mbar_covariance     asymptotic covariance of f (standard MBAR
+                                   large-sample theory; the paper reports
+                                   no error bars)
 
 Pins (tests/test_oracle_pins.py) tie each function to something other than
 itself: closed forms, Bennett's acceptance ratio for K = 2, a 40-digit
@@ -44,7 +47,7 @@ __all__ = [
     "mbar_weights", "mbar_objective", "mbar_gradient", "mbar_hessian",
     "newton_direction", "newton_finish", "solve_mbar",
     "bin_keys", "nonempty_bins", "histogram", "binned_u", "width_for_bins",
-    "BUOptions", "bu_mbar", "reweight", "mae",
+    "BUOptions", "bu_mbar", "reweight", "mbar_covariance", "mae",
 ]
 
 
@@ -436,6 +439,35 @@ def reweight(u0_n: np.ndarray, u_kn: np.ndarray, f_k: np.ndarray, N_k: np.ndarra
     logden = log_denominator(u_kn, f_k, N_k)
     logp = -np.asarray(u0_n, dtype=np.float64) - logden
     return np.exp(logp - logsumexp(logp, axis=0))
+
+
+# ---------------------------------------------------------------------------
+# Uncertainty: asymptotic covariance of the free energies (not in the paper;
+# the standard output of an MBAR solve)
+# ---------------------------------------------------------------------------
+
+def mbar_covariance(u_kn: np.ndarray, f_k: np.ndarray, N_k: np.ndarray) -> np.ndarray:
+    """Asymptotic covariance of the estimated free energies at the solution
+    f_k, in the gauge f_0 = 0: entry (i, j) is cov(f_i - f_0, f_j - f_0).
+
+    Written as the weight-matrix form of the MBAR large-sample theory: with
+    the N x K matrix W (W_nk = exp(f_k - u_kn) / sum_j N_j exp(f_j - u_jn))
+    and N = diag(N_k),
+
+        Theta = W^T (I_N - W N W^T)^+ W,
+
+    and cov(f_i - f_0, f_j - f_0) = Theta_ij - Theta_i0 - Theta_0j + Theta_00.
+    The N x N pseudo-inverse is formed explicitly (numpy.linalg.pinv), so this
+    is for small N only.
+    """
+    Wt = mbar_weights(u_kn, f_k, N_k).T                     # N x K
+    Nd = np.diag(np.asarray(N_k, dtype=np.float64))
+    A = np.eye(Wt.shape[0]) - Wt @ Nd @ Wt.T
+    theta = Wt.T @ np.linalg.pinv(A, rcond=1e-10, hermitian=True) @ Wt
+    d = theta - theta[:, :1] - theta[:1, :] + theta[0, 0]
+    d[0, :] = 0.0
+    d[:, 0] = 0.0
+    return d
 
 
 def mae(f_ref: np.ndarray, f: np.ndarray) -> float:
