@@ -254,6 +254,19 @@ BUMBAR_API mbar_status mbar_set_hessian_path(int32_t path);
 /* Number of CUDA kernels this library has launched in this process. */
 BUMBAR_API mbar_status mbar_kernel_launches(int64_t* count);
 
+/* Asymptotic covariance of the free energies at the context's current f
+ * (call after mbar_solve). Not in the paper; the standard large-sample
+ * result for the MBAR estimator: with H the Hessian of the MBAR objective at
+ * the solution (the Laplacian of the overlap matrix, as used by the Newton
+ * phase) and H_red its block without state 0,
+ *   cov_out[i*K + j] = cov(f_i - f_0, f_j - f_0)
+ *                    = [H_red^-1]_(i-1)(j-1) - delta_ij / N_i - 1 / N_0,
+ * i, j >= 1; row and column 0 are zero (the gauge f_0 = 0).
+ * cov_out: host FP64[K*K]. H comes from the same kernels as mbar_hessian
+ * (FP16 tensor-core products for K >= 64: relative error ~1e-3).
+ * ENOTCONV if H_red is not positive definite (states without overlap). */
+BUMBAR_API mbar_status mbar_covariance(mbar_ctx* ctx, double* cov_out);
+
 /* Bytes of device memory the context currently holds. */
 BUMBAR_API mbar_status mbar_device_bytes(mbar_ctx* ctx, int64_t* bytes);
 

@@ -71,6 +71,7 @@ struct mbar_ctx {
   // (the unbinned LSE passes stream it)
   void* vst = nullptr;
   float* logden_orig = nullptr;  // MIXED: logden of those passes, original order
+  bool smaj = false;             // unbinned passes on the sample-major copy
   int64_t ld = 0;
   double* cshift = nullptr;  // mixed: per-column shift (current order)
   int32_t* perm = nullptr;   // current column -> original sample
@@ -225,7 +226,7 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   const bool timed = !L.binned;
   if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
   mbar_status s = MBAR_OK;
-  if (!L.binned && c->dtype == 4 && c->vst) {
+  if (!L.binned && c->smaj && c->vst) {
     // unbinned MIXED pass over the sample-major copy (original sample order);
     // logden comes back to the store's column order through perm
     p.logden = logden_out ? c->logden_orig : nullptr;
@@ -397,7 +398,7 @@ mbar_status form_store(mbar_ctx* c, const int32_t* perm) {
     dfree(c, v);
     return s;
   }
-  if (c->dtype != 4) {  // MIXED keeps the sample-major copy for its LSE passes
+  if (!c->smaj) {  // the sample-major copy stays only where the LSE passes stream it
     dfree(c, c->vst);
     c->vst = nullptr;
   }
@@ -999,9 +1000,17 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   const int64_t K = c->K;
   // MIXED: the pair's FP32 data re-centred per column at the current f, so
   // the step-to-step rounding of the exponents is that of numbers near 0
-  // (Eq. 3 and the noise floor compare steps at that rounding level)
+  // (Eq. 3 and the noise floor compare steps at that rounding level). A
+  // column's largest exponent lies between min_k a_k and max_k a_k (v >= 0),
+  // so this only matters when some |a_k| is large: below 64 kT the FP32
+  // spacing there is under 1e-5 kT per entry and the data stay as they are.
   auto recenter_pair = [&]() -> mbar_status {
     if (c->dtype != 4) return MBAR_OK;
+    BUMBAR_TRY(d2h(c, c->f_h.data(), c->f, K));
+    BUMBAR_CUDA(cudaStreamSynchronize(c->st));
+    double amax = 0.0;
+    for (int64_t k = 0; k < K; ++k) amax = std::max(amax, std::fabs(c->f_h[k] + std::log(c->Nk_h[k])));
+    if (!(amax > 64.0)) return MBAR_OK;
     for (Level* L : {&cur, &nxt})
       if (L->binned) BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
     return MBAR_OK;
@@ -1318,7 +1327,8 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   if (cudaMemsetAsync(c->bad, 0, sizeof(int), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   if (cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   TRYC(dalloc(c, &c->vst, static_cast<size_t>(stage_pitch(K)) * N * c->dtype + 16));
-  if (c->dtype == 4) TRYC(dalloc_t(c, &c->logden_orig, N));
+  c->smaj = c->dtype == 4 && lse_smaj_preferred(K);
+  if (c->smaj) TRYC(dalloc_t(c, &c->logden_orig, N));
   TRYC(dalloc(c, &c->logden, static_cast<size_t>(N) * c->dtype));
   TRYC(dalloc_t(c, &c->perm, N));
   TRYC(dalloc_t(c, &c->seg, N));
@@ -1339,7 +1349,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
     u_dev = u_tmp;
   }
   if (c->dtype == 4) s = dalloc_t(c, &c->cshift, N);
-  if (s == MBAR_OK) s = stage_samples(u_dev, K, N, N, c->cshift, c->vst, c->dtype, c->bad, c->st);
+  if (s == MBAR_OK) s = stage_samples(u_dev, K, N, N, c->cshift, c->vst, c->dtype, c->bad, &c->stat->err, c->st);
   if (s == MBAR_OK && cudaMemcpyAsync(c->phi0, u_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
     s = MBAR_ECUDA;
   {
@@ -1356,6 +1366,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
       set_error("mbar_create: u_kn has non-finite entries");
       s = MBAR_EINVAL;
     }
+    if (s == MBAR_OK) s = read_status(c);  // a bounded wait of the staging that gave up
   }
   dfree(c, u_tmp);
   if (s == MBAR_ECUDA) set_error("mbar_create: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1364,7 +1375,7 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   {
     const LsePlan pl = lse_plan(K, N, c->dtype);
     int grid = pl.grid;
-    if (c->dtype == 4) grid = std::max(grid, lse_smaj_plan(K, N).grid);
+    if (c->smaj) grid = std::max(grid, lse_smaj_plan(K, N).grid);
     c->scratch_bytes = lse_scratch_for_grid(K, grid);
     TRYC(dalloc(c, &c->scratch, c->scratch_bytes));
     if (cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->st) != cudaSuccess) return fail(MBAR_ECUDA);
@@ -1563,6 +1574,45 @@ mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
   if (s == MBAR_OK) s = check_device_errors(c);
   if (s == MBAR_OK) s = d2h(c, hess_out, c->hess, K * K);
   if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+  dfree(c, tmp);
+  return s;
+}
+
+// Asymptotic covariance of f at the context's current f (after mbar_solve),
+// from the Hessian of the MBAR objective on the unbinned data.
+mbar_status mbar_covariance(mbar_ctx* c, double* cov_out) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
+  CHECK_CTX(c);
+  StreamFence fence(c);
+  if (!cov_out) {
+    set_error("mbar_covariance: cov_out is NULL");
+    return MBAR_EINVAL;
+  }
+  BUMBAR_TRY(ensure_store(c));
+  const int64_t K = c->K;
+  const Level& L = c->full;
+  BUMBAR_TRY(run_lse(c, L, c->f, kLseModePass, nullptr, nullptr, nullptr, 0.0, 0, c->logden));
+  const size_t htmp = std::max(hessian_tmp_bytes(K, L.n), covariance_tmp_bytes(K));
+  void* tmp = nullptr;
+  double* cov = nullptr;
+  BUMBAR_TRY(dalloc(c, &tmp, htmp));
+  mbar_status s = dalloc_t(c, &cov, K * K);
+  if (s == MBAR_OK)
+    s = hessian(L.v, c->dtype, K, L.n, L.ld, c->f, c->logN_d, c->logden, nullptr, c->hess, err_word(c), tmp, htmp,
+                c->st);
+  if (s == MBAR_OK) s = check_device_errors(c);
+  int info = 0;
+  if (s == MBAR_OK && cudaMemsetAsync(c->info, 0, sizeof(int), c->st) != cudaSuccess) s = MBAR_ECUDA;
+  if (s == MBAR_OK) s = covariance(c->hess, K, c->Nk_d, cov, c->info, tmp, htmp, c->st);
+  if (s == MBAR_OK) s = d2h(c, cov_out, cov, K * K);
+  if (s == MBAR_OK && cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    s = MBAR_ECUDA;
+  if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+  if (s == MBAR_OK && info) {
+    set_error("mbar_covariance: the reduced Hessian is not positive definite (states without overlap)");
+    s = MBAR_ENOTCONV;
+  }
+  dfree(c, cov);
   dfree(c, tmp);
   return s;
 }

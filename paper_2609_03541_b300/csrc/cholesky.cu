@@ -4,7 +4,9 @@
 // positive definite for connected data, is factored by a blocked
 // right-looking Cholesky (32-wide panels: diagonal block in shared memory,
 // panel triangular solve, trailing symmetric update) followed by forward
-// and backward substitution.
+// and backward substitution. The same factor gives the asymptotic
+// covariance of f (its inverse, column by column, minus the sample terms).
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -173,7 +175,100 @@ __global__ void __launch_bounds__(1024) chol_solve(const double* __restrict__ A,
   if (tid == 0) delta[0] = 0.0;
 }
 
+// Columns of the inverse of A = L L^T (L: lower factor in the lower triangle
+// of the m x m row-major `A`), one CTA per column j: forward substitution of
+// e_j (column-oriented: each step scales y_i and updates the rows below it),
+// then backward substitution with L^T (row-oriented: row i of L is column i
+// of L^T). X[:, j] = A^{-1} e_j.
+constexpr int kInvThreads = 256;
+__global__ void __launch_bounds__(kInvThreads) chol_inverse_cols(const double* __restrict__ A, int64_t m,
+                                                                 double* __restrict__ X) {
+  __shared__ double y[1024];
+  const int64_t j = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int64_t i = tid; i < m; i += kInvThreads) y[i] = (i == j) ? 1.0 : 0.0;
+  __syncthreads();
+  // L y = e_j (y_i = 0 for i < j)
+  for (int64_t i = j; i < m; ++i) {
+    const double yi = y[i] / A[i * m + i];
+    __syncthreads();  // every thread has read y[i]
+    if (tid == 0) y[i] = yi;
+    for (int64_t r = i + 1 + tid; r < m; r += kInvThreads) y[r] -= A[r * m + i] * yi;
+    __syncthreads();
+  }
+  // L^T x = y
+  for (int64_t i = m - 1; i >= 0; --i) {
+    const double xi = y[i] / A[i * m + i];
+    __syncthreads();
+    if (tid == 0) y[i] = xi;
+    for (int64_t r = tid; r < i; r += kInvThreads) y[r] -= A[i * m + r] * xi;
+    __syncthreads();
+  }
+  for (int64_t i = tid; i < m; i += kInvThreads) X[i * m + j] = y[i];
+}
+
+// cov(f_i - f_0, f_j - f_0) = [H_red^-1]_(i-1)(j-1) - delta_ij / N_i - 1 / N_0
+// for i, j >= 1; row and column 0 are 0 (the gauge).
+__global__ void covariance_from_inverse(const double* __restrict__ X, int64_t K, const double* __restrict__ Nk,
+                                        double* __restrict__ cov) {
+  const int64_t i = blockIdx.x;
+  const int64_t m = K - 1;
+  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) {
+    double v = 0.0;
+    if (i > 0 && j > 0) v = X[(i - 1) * m + (j - 1)] - (i == j ? 1.0 / Nk[i] : 0.0) - 1.0 / Nk[0];
+    cov[i * K + j] = v;
+  }
+}
+
+// Blocked right-looking Cholesky of the m x m row-major A in place.
+void factor_blocked(double* A, int64_t m, int* info, cudaStream_t st) {
+  for (int64_t kb = 0; kb < m; kb += NB) {
+    const int nb = static_cast<int>(std::min<int64_t>(NB, m - kb));
+    potrf_block<<<1, NB * NB, 0, st>>>(A, m, kb, nb, info);
+    count_launches(1);
+    const int64_t rest = m - kb - nb;
+    if (rest > 0) {
+      trsm_panel<<<static_cast<unsigned>(ceil_div(rest, 128)), 128, 0, st>>>(A, m, kb, nb);
+      count_launches(1);
+      const unsigned nt = static_cast<unsigned>(ceil_div(rest, NB));
+      syrk_update<<<dim3(nt, nt), NB * NB, 0, st>>>(A, m, kb, nb);
+      count_launches(1);
+    }
+  }
+}
+
 }  // namespace
+
+size_t covariance_tmp_bytes(int64_t K) {
+  const int64_t m = std::max<int64_t>(K - 1, 1);
+  return 2 * round_up(m * m * 8, 256) + round_up(K * 8, 256) + 256;
+}
+
+mbar_status covariance(const double* hess, int64_t K, const double* Nk, double* cov, int* info, void* tmp,
+                       size_t tmp_bytes, cudaStream_t st) {
+  if (K == 1) {
+    BUMBAR_CUDA(cudaMemsetAsync(cov, 0, sizeof(double), st));
+    return MBAR_OK;
+  }
+  if (K > 1024 || tmp_bytes < covariance_tmp_bytes(K)) {
+    set_error("covariance: K > 1024 or scratch too small");
+    return MBAR_EINVAL;
+  }
+  const int64_t m = K - 1;
+  double* A = static_cast<double*>(tmp);
+  double* X = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + round_up(m * m * 8, 256));
+  double* b = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + 2 * round_up(m * m * 8, 256));
+  // copy_reduced's right-hand side is not needed here (b gets -hess[1..K-1]
+  // and is ignored)
+  copy_reduced<<<static_cast<unsigned>(m), kThreads, 0, st>>>(hess, K, hess, A, b);
+  count_launches(1);
+  factor_blocked(A, m, info, st);
+  chol_inverse_cols<<<static_cast<unsigned>(m), kInvThreads, 0, st>>>(A, m, X);
+  covariance_from_inverse<<<static_cast<unsigned>(K), kThreads, 0, st>>>(X, K, Nk, cov);
+  count_launches(2);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
 
 size_t newton_tmp_bytes(int64_t K) { return round_up((K - 1) * (K - 1) * 8, 256) + round_up(K * 8, 256) + 256; }
 
@@ -192,19 +287,7 @@ mbar_status newton_solve(double* hess, int64_t K, const double* g, double* delta
   double* b = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + round_up(m * m * 8, 256));
   copy_reduced<<<static_cast<unsigned>(m), kThreads, 0, st>>>(hess, K, g, A, b);
   count_launches(1);
-  for (int64_t kb = 0; kb < m; kb += NB) {
-    const int nb = static_cast<int>(std::min<int64_t>(NB, m - kb));
-    potrf_block<<<1, NB * NB, 0, st>>>(A, m, kb, nb, info);
-    count_launches(1);
-    const int64_t rest = m - kb - nb;
-    if (rest > 0) {
-      trsm_panel<<<static_cast<unsigned>(ceil_div(rest, 128)), 128, 0, st>>>(A, m, kb, nb);
-      count_launches(1);
-      const unsigned nt = static_cast<unsigned>(ceil_div(rest, NB));
-      syrk_update<<<dim3(nt, nt), NB * NB, 0, st>>>(A, m, kb, nb);
-      count_launches(1);
-    }
-  }
+  factor_blocked(A, m, info, st);
   chol_solve<<<1, 1024, 0, st>>>(A, m, b, delta);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());

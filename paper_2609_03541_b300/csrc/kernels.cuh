@@ -69,6 +69,7 @@ bool lse_regs_supported(int64_t K, int dtype_bytes);
 // (if requested) in the same sample order. Launches the pass and the
 // epilogue.
 LsePlan lse_smaj_plan(int64_t K, int64_t n);
+bool lse_smaj_preferred(int64_t K);
 mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st);
 // The SCI epilogue over the partials of a pass (lse.cu).
 mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream);
@@ -142,9 +143,10 @@ __host__ __device__ inline int64_t stage_pitch(int64_t K) { return (K + 3) / 4 *
 // u_kn (K x N FP64, row pitch ldu) -> sample-major staging
 // vst[n * stage_pitch(K) + k] (entries k >= K set to 0): fl32(u - c_n) with
 // c_n = min_k u_kn written to c (dtype_bytes 4), or the FP64 values
-// (dtype_bytes 8; c unused); *bad |= 1 if any entry is not finite.
+// (dtype_bytes 8; c unused); *bad |= 1 if any entry is not finite; *err
+// counts bounded waits that gave up.
 mbar_status stage_samples(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, void* vst, int dtype_bytes,
-                          int* bad, cudaStream_t st);
+                          int* bad, unsigned* err, cudaStream_t st);
 // v[k * ld + i] = vst[perm[i] * stage_pitch(K) + k] for i < N (the row-major
 // store in the column order perm).
 mbar_status gather_transpose(const void* vst, int dtype_bytes, int64_t K, int64_t N, const int32_t* perm, void* v,
@@ -193,6 +195,13 @@ mbar_status weighted_hist2d(const double* x, const double* y, const double* p, i
                             int64_t nx, double y0, double dy, int64_t ny, double* out, cudaStream_t st);  // false: tensor-core path without the cluster variant
 
 // ---- dense FP64 (cholesky.cu) ----
+// Asymptotic covariance of f in the gauge f_0 = 0 from the MBAR Hessian
+// (K x K, the Laplacian of the overlap matrix at the solution): cov[i][j] =
+// [H_red^-1]_(i-1)(j-1) - delta_ij / N_i - 1 / N_0 for i, j >= 1, row and
+// column 0 zero; *info |= 1 if H_red is not positive definite.
+size_t covariance_tmp_bytes(int64_t K);
+mbar_status covariance(const double* hess, int64_t K, const double* Nk, double* cov, int* info, void* tmp,
+                       size_t tmp_bytes, cudaStream_t st);
 // Solves A x = b for the (m x m) symmetric positive definite block
 // A = hess[1:,1:] (row pitch K) and b = -g[1:]; x written to delta[1:],
 // delta[0] = 0. Sets *info != 0 if a pivot is not positive.

@@ -182,6 +182,168 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const double* __re
   }
 }
 
+// TMA-fed variant of the MIXED staging for K <= 512 (u 16-byte aligned, row
+// pitch a multiple of 16 bytes): persistent CTAs take strips of 16 samples
+// (one 128-byte line of each of the K rows) through a two-stage ring of 2-D
+// TMA loads; the column minima are taken over the swizzled tile, the
+// converted samples are written to a padded shared-memory tile and leave by
+// 1-D bulk stores (one contiguous K-vector per sample), so the threads only
+// do the arithmetic. Same results as stage_kernel<true>.
+constexpr int kStThreads = 512;
+constexpr int kStCols = 16;                    // FP64 samples per strip
+constexpr int kStRows = kStThreads / kStCols;  // row residues covered at once
+constexpr uint32_t kStSpin = 1u << 28;
+
+__device__ __forceinline__ void bulk_store_1d(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// shared-memory pitch (floats) of one converted sample: Kp, or Kp + 4 when
+// Kp / 4 is even, so the 16 samples written by one warp spread over the banks
+__host__ __device__ inline int64_t stage_tma_ypitch(int64_t Kp) { return ((Kp / 4) & 1) ? Kp : Kp + 4; }
+
+struct StageTmaSmem {
+  static __host__ __device__ size_t xbytes(int nbox, int box_rows) {
+    return static_cast<size_t>(nbox) * box_rows * 128;
+  }
+  static __host__ __device__ size_t ybytes(int64_t K) {
+    return static_cast<size_t>(kStCols) * stage_tma_ypitch(stage_pitch(K)) * 4;
+  }
+  static __host__ __device__ size_t total(int64_t K, int nbox, int box_rows) {
+    return 2 * xbytes(nbox, box_rows) + 2 * ybytes(K) + 1024 /* alignment */ + 64 /* barriers */;
+  }
+};
+
+__global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t K,
+                                                                  int64_t N, int nbox, int box_rows,
+                                                                  double* __restrict__ c, float* __restrict__ vst,
+                                                                  int* bad, unsigned* err) {
+  extern __shared__ __align__(1024) unsigned char st_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(st_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ unsigned long long part[kStRows][kStCols];
+  __shared__ int okp[kStRows][kStCols];
+  __shared__ double cmin[kStCols];
+  __shared__ float mhs[kStCols], mls[kStCols];
+  __shared__ int msp[kStCols];
+  const size_t xb = StageTmaSmem::xbytes(nbox, box_rows);
+  const size_t yb = StageTmaSmem::ybytes(K);
+  unsigned char* xs = smem;
+  float* ys = reinterpret_cast<float*>(smem + 2 * xb);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * xb + 2 * yb);
+  const int64_t Kp = stage_pitch(K), Yp = stage_tma_ypitch(Kp);
+  const int tid = threadIdx.x, jj = tid % kStCols, r0 = tid / kStCols;
+  const int64_t nstrips = (N + kStCols - 1) / kStCols;
+  const int64_t first = blockIdx.x, stride = gridDim.x;
+  const int count = first < nstrips ? static_cast<int>((nstrips - 1 - first) / stride + 1) : 0;
+  const uint32_t tx = static_cast<uint32_t>(xb);
+  auto issue = [&](int s, int it) {
+    const int64_t strip = first + static_cast<int64_t>(it) * stride;
+    mbar_expect_tx(&bars[s], tx);
+    for (int b = 0; b < nbox; ++b)
+      tma_load_2d(xs + s * xb + static_cast<size_t>(b) * box_rows * 128, &tmap, &bars[s],
+                  static_cast<int>(strip * kStCols), b * box_rows);
+  };
+  if (tid == 0) {
+    prefetch_tmap(&tmap);
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_barrier_init();
+    for (int s = 0; s < 2 && s < count; ++s) issue(s, s);
+  }
+  __syncthreads();
+  int it_fail = -1;
+  for (int it = 0; it < count; ++it) {
+    const int s = it & 1;
+    const bool ok_wait = mbar_wait_bounded(&bars[s], static_cast<uint32_t>((it >> 1) & 1), kStSpin);
+    if (__syncthreads_or(!ok_wait)) {
+      it_fail = it;
+      break;
+    }
+    const int64_t n0 = (first + static_cast<int64_t>(it) * stride) * kStCols;
+    const int ns = static_cast<int>(N - n0 < kStCols ? N - n0 : kStCols);
+    const unsigned char* X = xs + s * xb;
+    auto xat = [&](int64_t k) -> double {
+      return *reinterpret_cast<const double*>(X + k * 128 + (((jj >> 1) ^ static_cast<int>(k & 7)) << 4) +
+                                              (jj & 1) * 8);
+    };
+    // pass 1: column minimum (order-preserving integer image) and finiteness
+    unsigned long long m = ~0ull;
+    bool ok = true;
+    for (int64_t k = r0; k < K; k += kStRows) {
+      const double x = xat(k);
+      const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+      ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
+      const unsigned long long kx = ordered_bits(x);
+      m = kx < m ? kx : m;
+    }
+    part[r0][jj] = m;
+    okp[r0][jj] = ok ? 1 : 0;
+    // the bulk stores of two strips ago must have read their tile
+    if (tid == 0) bulk_wait_read1();
+    __syncthreads();
+    if (tid < ns) {
+      unsigned long long mm = part[0][tid];
+      int allok = okp[0][tid];
+#pragma unroll 8
+      for (int r = 1; r < kStRows; ++r) {
+        mm = part[r][tid] < mm ? part[r][tid] : mm;
+        allok &= okp[r][tid];
+      }
+      if (!allok) atomicOr(bad, 1);
+      const double cm = allok ? from_ordered(mm) : 0.0;
+      c[n0 + tid] = cm;
+      cmin[tid] = cm;
+      float mh = 0.f, ml = 0.f;
+      msp[tid] = (split_f64(cm, mh, ml) || cm == 0.0) ? 1 : 0;
+      mhs[tid] = mh;
+      mls[tid] = ml;
+    }
+    __syncthreads();
+    // pass 2: fl32(u - c) as (uh - ch) + (ul - cl), into the sample-major tile
+    float* Y = ys + static_cast<size_t>(it & 1) * (yb / 4);
+    if (jj < ns) {
+      const double cm = cmin[jj];
+      const float mh = mhs[jj], ml = mls[jj];
+      const bool msplit = msp[jj] != 0;
+      for (int64_t k = r0; k < Kp; k += kStRows) {
+        float r = 0.f;
+        if (k < K) {
+          const double x = xat(k);
+          float xh, xl;
+          if (msplit && split_f64(x, xh, xl))
+            r = __fadd_rn(__fsub_rn(xh, mh), __fsub_rn(xl, ml));
+          else
+            r = f64_to_f32_rn(x - cm);
+        }
+        Y[jj * Yp + k] = r;
+      }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 0; q < ns; ++q)
+        bulk_store_1d(vst + (n0 + q) * Kp, Y + q * Yp, static_cast<uint32_t>(Kp * 4));
+      bulk_commit();
+      if (it + 2 < count) issue(s, it + 2);  // the tile of stage s is no longer read
+    }
+  }
+  if (tid == 0) {
+    if (it_fail >= 0) {
+      atomicAdd(err, 1u);
+      for (int j = it_fail; j < count && j < it_fail + 2; ++j)
+        (void)mbar_wait_bounded(&bars[j & 1], static_cast<uint32_t>((j >> 1) & 1), kStSpin);
+    }
+    bulk_wait_all();
+  }
+  __syncthreads();
+}
+
 // Per-column re-centring of a binned FP32 level at the current f: column p
 // gets o_p = max_k (a_k - v_kp), a_k = f_k + ln N_k, added to every entry,
 // so the exponents a_k - v_kp of its dominant states are near 0 instead of
@@ -239,7 +401,34 @@ __global__ void add_gauge_kernel(const double* __restrict__ f, const double* __r
 }  // namespace
 
 mbar_status stage_samples(const double* u, int64_t K, int64_t N, int64_t ldu, double* c, void* vst, int dtype_bytes,
-                          int* bad, cudaStream_t st) {
+                          int* bad, unsigned* err, cudaStream_t st) {
+  if (dtype_bytes == 4 && K <= 512 && (reinterpret_cast<uintptr_t>(u) & 15) == 0 && (ldu * 8) % 16 == 0) {
+    const int box_rows = static_cast<int>(std::min<int64_t>(256, round_up(K, 8)));
+    const int nbox = static_cast<int>(ceil_div(K, box_rows));
+    CUtensorMap map;
+    if (make_tmap_2d(&map, u, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, K, N, ldu, kStCols, box_rows) == MBAR_OK) {
+      const size_t smem = StageTmaSmem::total(K, nbox, box_rows);
+      static bool init = false;
+      {
+        std::lock_guard<std::recursive_mutex> lock(init_mutex());
+        if (!init) {
+          int dev = 0, optin = 0;
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+          cudaFuncSetAttribute(stage_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 8 * 1024);
+          init = true;
+        }
+      }
+      const int64_t strips = ceil_div(N, kStCols);
+      const unsigned grid = static_cast<unsigned>(std::min<int64_t>(strips, num_sms()));
+      stage_tma_kernel<<<grid, kStThreads, smem, st>>>(map, K, N, nbox, box_rows, c, static_cast<float*>(vst), bad,
+                                                       err);
+      count_launches(1);
+      BUMBAR_CUDA(cudaGetLastError());
+      return MBAR_OK;
+    }
+    cudaGetLastError();
+  }
   const size_t smem = stage_smem_bytes(K);
   {
     std::lock_guard<std::recursive_mutex> lock(init_mutex());

@@ -57,11 +57,12 @@ uint64_t footprint(int64_t K, int64_t N, int32_t precision, int32_t use_binning,
   const uint64_t el = precision == MBAR_FP64 ? 8 : 4;
   // creation: the FP64 upload (host input) and the sample-major copy; the
   // coordinate: that copy and the row-major store; the solve: the store,
-  // MIXED's sample-major copy (kept for its LSE passes) and the levels
+  // the sample-major copy where MIXED's LSE passes stream it, and the levels
   const uint64_t es = static_cast<uint64_t>(stage_pitch(K)) * static_cast<uint64_t>(N) + 4;
   const uint64_t create = (u_on_device ? 0 : e * 8) + es * el;
   const uint64_t coord = es * el + e * el;
-  const uint64_t solve = e * el + (precision == MBAR_FP64 ? 0 : es * 4) + (use_binning ? e * el * 6 / 10 : 0);
+  const bool keeps_copy = precision != MBAR_FP64 && lse_smaj_preferred(K);
+  const uint64_t solve = e * el + (keeps_copy ? es * 4 : 0) + (use_binning ? e * el * 6 / 10 : 0);
   const uint64_t fixed = static_cast<uint64_t>(N) * 96 + static_cast<uint64_t>(K) * K * 8 * 4 + (64ull << 20);
   return std::max(std::max(create, coord), solve) + fixed;
 }

@@ -101,6 +101,7 @@ _SIGNATURES = {
     "mbar_get_bins": ([_vp, _i64p, _i64p, _dp], ctypes.c_int),
     "mbar_sci_step": ([_vp, _dp, _dp, _dp, _dp, _dp], ctypes.c_int),
     "mbar_hessian": ([_vp, _dp, _dp], ctypes.c_int),
+    "mbar_covariance": ([_vp, _dp], ctypes.c_int),
     "mbar_newton_step": ([_vp, _dp, _dp, _dp], ctypes.c_int),
     "mbar_solve": ([_vp, _dp, ctypes.POINTER(Report)], ctypes.c_int),
     "mbar_free_energies": ([_vp, _dp], ctypes.c_int),
@@ -258,6 +259,13 @@ class Context:
         H = np.empty((self.K, self.K))
         _check(lib().mbar_hessian(self._h, _ptr(f), _ptr(H)))
         return H
+
+    def covariance(self):
+        """``mbar_covariance``: K x K asymptotic covariance of f at the current
+        solution, gauge f_0 = 0 (row and column 0 zero)."""
+        C = np.empty((self.K, self.K))
+        _check(lib().mbar_covariance(self._h, _ptr(C)))
+        return C
 
     def newton_step(self, f):
         f = _f64(f)

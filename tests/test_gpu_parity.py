@@ -474,7 +474,7 @@ def test_mixed_tempering_offsets_are_not_quantised():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("K,N", [(3, 37), (500, 4133), (1000, 1031)])
+@pytest.mark.parametrize("K,N", [(3, 37), (100, 2001), (500, 4133), (1000, 1031)])
 def test_store_formed_late_or_early_is_the_same(prec, K, N):
     """The data is staged sample-major at creation and stored row-major by
     the first call that needs it: in the coordinate's order when that call is
@@ -501,3 +501,22 @@ def test_store_formed_late_or_early_is_the_same(prec, K, N):
         assert np.array_equal(a.free_energies(), b.free_energies())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,N_k", [(3, 400), (12, 150), (80, 30)])
+def test_covariance_matches_oracle(prec, K, N_k):
+    """mbar_covariance (Cholesky of the reduced Hessian, column-by-column
+    inverse, sample terms) against the oracle's weight-matrix formula at the
+    same f; the tensor-core Hessian (K >= 64) carries FP16 products."""
+    p = W.harmonic(K=K, d=2, N_k=N_k, seed=K)
+    ctx = M.Context(p.u_kn, p.N_k, PREC[prec])
+    ctx.solve()
+    f = ctx.free_energies()
+    C = ctx.covariance()
+    ctx.close()
+    C_ref = O.mbar_covariance(p.u_kn, f, p.N_k)
+    scale = np.sqrt(np.outer(np.diag(C_ref), np.diag(C_ref)))[1:, 1:]
+    tol = 3e-2 if K >= 64 else 1e-3       # the Hessian kernels' FP16 / FP32 products
+    assert np.all(C[0] == 0.0) and np.all(C[:, 0] == 0.0)
+    assert np.max(np.abs(C[1:, 1:] - C_ref[1:, 1:]) / scale) < tol
