@@ -638,7 +638,57 @@ mbar_status capture(mbar_ctx* c, Graph* g, F&& body) {
 // Phase-1 loop of Algorithm 1 on level L: guarded in-place SCI steps until
 // s < eps (the guard turns later launches of a batch into no-ops). A binned
 // level replays a captured batch of kPhase1Batch launches.
+// The first loop on a small FP32 level in single launches (sci_loop.cu): the
+// level is transposed to sample-major once; an underflowed step stops the
+// kernel and is redone exactly here, then the loop resumes.
+mbar_status first_loop_fused(mbar_ctx* c, const Level& L, mbar_report* rep) {
+  BUMBAR_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st));
+  float* vT = nullptr;
+  BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&vT), sci_loop_level_bytes(c->K, L.n)));
+  mbar_status s = level_to_samples(static_cast<const float*>(L.v), c->K, L.n, L.ld, vT, c->st);
+  SciLoopParams q{};
+  q.K = static_cast<int>(c->K);
+  q.n = static_cast<int>(L.n);
+  q.H = L.H;
+  q.f = c->f;
+  q.logN = c->logN_d;
+  q.Nk = c->Nk_d;
+  q.ctrl = c->ctrl;
+  q.s_out = c->s;
+  q.d_out = nullptr;
+  q.err = err_word(c);
+  q.eps = c->opts.eps;
+  q.noise = c->opts.noise_floor;
+  int64_t done_iters = 0;
+  while (s == MBAR_OK) {
+    q.max_steps = c->opts.max_sci - done_iters;
+    s = sci_loop_launch(vT, q, c->st);
+    if (s == MBAR_OK) s = read_status(c);
+    if (s != MBAR_OK) break;
+    const bool redo = take_underflow(c);
+    if (redo) {
+      s = log_sci_step(c, L, c->f, c->f, nullptr, c->s, c->opts.eps, nullptr, c->opts.noise_floor);
+      if (s == MBAR_OK) s = read_status(c);
+      if (s != MBAR_OK) break;
+    }
+    const Ctrl h = c->hstat->ctrl;
+    done_iters = h.iters;
+    if (h.done || done_iters >= c->opts.max_sci) {
+      trace_row(c, 1, static_cast<double>(L.n_sched), h.last_s, static_cast<double>(done_iters));
+      break;
+    }
+    if (!redo) {
+      set_error("first loop: the fused SCI kernel stopped without converging");
+      s = MBAR_ENOTCONV;
+    }
+  }
+  dfree(c, vT);
+  if (s == MBAR_OK) rep->iters_first_loop += done_iters;
+  return s;
+}
+
 mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
+  if (c->dtype == 4 && L.binned && sci_loop_supported(c->K, L.n)) return first_loop_fused(c, L, rep);
   BUMBAR_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st));
   auto batch = [&]() -> mbar_status {
     for (int b = 0; b < kPhase1Batch; ++b)

@@ -68,6 +68,32 @@ bool lse_regs_supported(int64_t K, int dtype_bytes);
 // Kp = K rounded up to 4 (entries k >= K zero), n = prm.n samples; logden
 // (if requested) in the same sample order. Launches the pass and the
 // epilogue.
+// Repeated SCI steps on one small binned FP32 level in a single launch
+// (sci_loop.cu); vT is the level sample-major (n x stage_pitch(K), zero
+// padded). f is read at the start and written back at the end (gauge
+// f_0 = 0); ctrl->iters counts the applied steps, ctrl->done is set when the
+// last one met s < eps or max|df| < noise, ctrl->underflow when a step was
+// not applied (some Q_k < 1e-20 N_k; redo it exactly), ctrl->nonfinite as in
+// the LSE epilogue. s_out / d_out (nullable) get the last step's s and
+// max|df|.
+struct SciLoopParams {
+  int K, n;
+  const int32_t* H;    // [n] counts
+  double* f;           // [K] in/out
+  const double* logN;  // [K]
+  const double* Nk;    // [K]
+  Ctrl* ctrl;
+  double* s_out;
+  double* d_out;
+  unsigned* err;  // timeouts of bounded waits
+  double eps, noise;
+  int64_t max_steps;
+};
+bool sci_loop_supported(int64_t K, int64_t n);
+size_t sci_loop_level_bytes(int64_t K, int64_t n);
+mbar_status sci_loop_launch(const float* vT, const SciLoopParams& prm, cudaStream_t st);
+// out[p * stage_pitch(K) + k] = v[k * ld + p] for p < n (entries k >= K zero).
+mbar_status level_to_samples(const float* v, int64_t K, int64_t n, int64_t ld, float* out, cudaStream_t st);
 LsePlan lse_smaj_plan(int64_t K, int64_t n);
 bool lse_smaj_preferred(int64_t K);
 mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st);

@@ -344,6 +344,24 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
   __syncthreads();
 }
 
+// Row-major K x n (pitch ld) -> sample-major n x Kp through 32 x 32 tiles.
+__global__ void level_to_samples_kernel(const float* __restrict__ v, int64_t K, int64_t n, int64_t ld,
+                                        float* __restrict__ out) {
+  __shared__ float tile[32][33];
+  const int64_t Kp = stage_pitch(K);
+  const int64_t p0 = static_cast<int64_t>(blockIdx.x) * 32, k0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t k = k0 + r, p = p0 + tx;
+    tile[r][tx] = (k < K && p < n) ? v[k * ld + p] : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t p = p0 + r, k = k0 + tx;
+    if (p < n && k < Kp) out[p * Kp + k] = tile[tx][r];
+  }
+}
+
 // Per-column re-centring of a binned FP32 level at the current f: column p
 // gets o_p = max_k (a_k - v_kp), a_k = f_k + ln N_k, added to every entry,
 // so the exponents a_k - v_kp of its dominant states are near 0 instead of
@@ -448,6 +466,15 @@ mbar_status stage_samples(const double* u, int64_t K, int64_t N, int64_t ldu, do
     stage_kernel<true><<<grid, kStageThreads, smem, st>>>(u, K, N, ldu, c, vst, bad);
   else
     stage_kernel<false><<<grid, kStageThreads, smem, st>>>(u, K, N, ldu, c, vst, bad);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+mbar_status level_to_samples(const float* v, int64_t K, int64_t n, int64_t ld, float* out, cudaStream_t st) {
+  if (n < 1) return MBAR_OK;
+  const dim3 g(static_cast<unsigned>(ceil_div(n, 32)), static_cast<unsigned>(ceil_div(stage_pitch(K), 32)));
+  level_to_samples_kernel<<<g, dim3(32, 8), 0, st>>>(v, K, n, ld, out);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;

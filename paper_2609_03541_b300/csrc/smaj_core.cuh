@@ -1,0 +1,82 @@
+// The arithmetic of one lane group on two samples of a sample-major FP32
+// tile (the per-sample work of Eq. 1): for sample columns c0, c1 (Kp
+// consecutive floats each) the lane's entries k = 4 (lig + LPS i) + t give
+//     x_k = a_k log2(e) - v_k log2(e)     (FP32 pairs (ahi, alo), (kLog2e, kLog2eLo)),
+// the group's maxima m0, m1 and sums s0, s1 of 2^(x - m) by shuffles within
+// the group of LPS lanes, and x0, x1 overwritten with 2^(x - m).
+#pragma once
+
+#include "common.cuh"
+
+namespace bumbar {
+
+template <int LPS, int NK>
+__device__ __forceinline__ void smaj_pair(const float* c0, const float* c1, int lig, int Kp, const float (&ahi)[4 * NK],
+                                          const float (&alo)[4 * NK], float (&x0)[4 * NK], float (&x1)[4 * NK],
+                                          float& m0, float& m1, float& s0, float& s1) {
+  constexpr int E = 4 * NK;
+  m0 = -INFINITY;
+  m1 = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k4 = 4 * (lig + LPS * i);
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (k4 < Kp) {
+      a = *reinterpret_cast<const float4*>(c0 + k4);
+      b = *reinterpret_cast<const float4*>(c1 + k4);
+    }
+    const float va[4] = {a.x, a.y, a.z, a.w}, vb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = 4 * i + t;
+      x0[e] = fmaf(-va[t], kLog2e, ahi[e]) + fmaf(-va[t], kLog2eLo, alo[e]);
+      x1[e] = fmaf(-vb[t], kLog2e, ahi[e]) + fmaf(-vb[t], kLog2eLo, alo[e]);
+      m0 = fmaxf(m0, x0[e]);
+      m1 = fmaxf(m1, x1[e]);
+    }
+  }
+#pragma unroll
+  for (int o = LPS / 2; o >= 1; o >>= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  s0 = 0.f;
+  s1 = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    x0[e] = ex2_approx(x0[e] - m0);
+    x1[e] = ex2_approx(x1[e] - m1);
+    s0 += x0[e];
+    s1 += x1[e];
+  }
+#pragma unroll
+  for (int o = LPS / 2; o >= 1; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+}
+
+// lanes per sample: the smallest power of two whose lanes cover Kp / 4
+// float4 chunks, at most 32; float4 chunks per lane beyond that; threads
+// (15 or 7 compute warps + one producer warp)
+inline void smaj_shape_of(int64_t K, int* lps, int* nk, int* nt) {
+  const int64_t q = (K + 3) / 4;
+  int l = 1;
+  while (l < 32 && l < q) l <<= 1;
+  *lps = l;
+  *nk = static_cast<int>((q + l - 1) / l);
+  *nt = *nk <= 4 ? 512 : 256;
+}
+
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+}  // namespace bumbar

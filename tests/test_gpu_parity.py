@@ -520,3 +520,35 @@ def test_covariance_matches_oracle(prec, K, N_k):
     tol = 3e-2 if K >= 64 else 1e-3       # the Hessian kernels' FP16 / FP32 products
     assert np.all(C[0] == 0.0) and np.all(C[:, 0] == 0.0)
     assert np.max(np.abs(C[1:, 1:] - C_ref[1:, 1:]) / scale) < tol
+
+
+@pytest.mark.parametrize("case", ["gaussian", "umbrella_h0", "alchemical"])
+def test_mixed_first_loop_follows_the_oracle(case):
+    """MIXED runs the first loop on its small FP32 level in single launches
+    (the whole loop on chip): it stops within one step of where the oracle's
+    FP64 first loop stops, with the same last relative step to 2 % (Eq. 2
+    divides FP32 rounding by the small f_k next to the gauge state), and the
+    solve still ends at the oracle's free energies."""
+    if case == "gaussian":
+        p = W.gaussian_overlap(M=12, N_0=2000, seed=4)
+        opts, o = O.BUOptions(), M.default_opts(M.MBAR_MIXED)
+    elif case == "umbrella_h0":
+        p = W.umbrella(K=16, N_k=1000, seed=1, grid_points=1 << 13)
+        opts, o = O.BUOptions(h0=0.1), M.default_opts(M.MBAR_MIXED, h0=0.1)
+    else:
+        p = W.alchemical(K=40, N_k=300, seed=3)
+        opts, o = O.BUOptions(), M.default_opts(M.MBAR_MIXED)
+    tr = []
+    f_ref = O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, opts=opts, trace=tr)
+    ctx = M.Context(p.u_kn, p.N_k, M.MBAR_MIXED, opts=o)
+    ctx.set_coordinate(p.phi)
+    ctx.solve()
+    gt = ctx.trace()
+    f = ctx.free_energies()
+    ctx.close()
+    ph1 = [t for t in tr if t[0] == "phase1"]
+    g1 = [r for r in gt if r[0] == 1]
+    assert len(g1) == 1 and abs(int(g1[0][3]) - len(ph1)) <= 1
+    if int(g1[0][3]) == len(ph1):
+        assert g1[0][2] == pytest.approx(ph1[-1][2], rel=2e-2)
+    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL["mixed"]
