@@ -52,6 +52,7 @@ struct Level {
   double w = 0.0;
   int64_t n_sched = 0;  // n used by Algorithm 1's break rule
   CUtensorMap tmap;
+  float* vT = nullptr;  // owned: the level sample-major (MIXED passes of the second loop)
 };
 
 }  // namespace
@@ -157,8 +158,20 @@ void level_free(mbar_ctx* c, Level* L) {
     dfree(c, L->v);
     dfree(c, L->H);
     dfree(c, L->keys);
+    dfree(c, L->vT);
   }
   *L = Level{};
+}
+
+// The binned level also sample-major, for the sample-major pass (MIXED, the
+// K where that pass is the faster one); rebuilt after the row-major data
+// change.
+mbar_status level_samples(mbar_ctx* c, Level* L, bool rebuild) {
+  if (!L->binned || !c->smaj) return MBAR_OK;
+  if (L->vT && !rebuild) return MBAR_OK;
+  lse_smaj_prepare(c->K);  // its passes may be captured in a graph
+  if (!L->vT) BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&L->vT), sci_loop_level_bytes(c->K, L->n)));
+  return level_to_samples(static_cast<const float*>(L->v), c->K, L->n, L->ld, L->vT, c->st);
 }
 
 mbar_status level_tmap(mbar_ctx* c, Level* L) {
@@ -226,7 +239,10 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   const bool timed = !L.binned;
   if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
   mbar_status s = MBAR_OK;
-  if (!L.binned && c->smaj && c->vst) {
+  if (L.binned && L.vT) {
+    // binned level, sample-major copy (columns in the level's own order)
+    s = lse_smaj_launch(L.vT, lse_smaj_plan(c->K, L.n), p, c->st);
+  } else if (!L.binned && c->smaj && c->vst) {
     // unbinned MIXED pass over the sample-major copy (original sample order);
     // logden comes back to the store's column order through perm
     p.logden = logden_out ? c->logden_orig : nullptr;
@@ -516,6 +532,12 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
   mbar_status st = MBAR_ENOTCONV;
   int rejects = 0;
   double prev_step = INFINITY;
+  // the rounding floor of a gradient evaluation: below it max|g| says
+  // nothing about whether a step helped (FP32 data and exponentials give
+  // ~1e-6..1e-5 of N_k; FP64 ~1e-13)
+  double nk_max = 0.0;
+  for (int64_t k = 0; k < K; ++k) nk_max = std::max(nk_max, c->Nk_h[k]);
+  const double g_floor = (c->dtype == 4 ? 1e-5 : 1e-13) * nk_max;
   for (int it = 0; it < c->opts.max_newton; ++it) {
     if (gmax == 0.0 || K == 1) {
       st = MBAR_OK;
@@ -553,7 +575,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
         return s;
       }
       const double gmax_t = (s == MBAR_OK) ? max_abs(gh) : INFINITY;
-      if (std::isfinite(gmax_t) && (gmax_t <= gmax || step <= 10.0 * c->opts.f_tol)) {
+      if (std::isfinite(gmax_t) && (gmax_t <= gmax || step <= 10.0 * c->opts.f_tol || gmax_t <= g_floor)) {
         std::swap(c->f, c->ft);
         std::swap(c->fs, c->fts);
         std::swap(c->g, c->gt);
@@ -1060,9 +1082,13 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
     BUMBAR_CUDA(cudaStreamSynchronize(c->st));
     double amax = 0.0;
     for (int64_t k = 0; k < K; ++k) amax = std::max(amax, std::fabs(c->f_h[k] + std::log(c->Nk_h[k])));
-    if (!(amax > 64.0)) return MBAR_OK;
-    for (Level* L : {&cur, &nxt})
-      if (L->binned) BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
+    const bool recenter = amax > 64.0;
+    for (Level* L : {&cur, &nxt}) {
+      if (!L->binned) continue;
+      if (recenter)
+        BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
+      BUMBAR_TRY(level_samples(c, L, recenter));
+    }
     return MBAR_OK;
   };
   s = recenter_pair();
