@@ -52,7 +52,6 @@ struct Level {
   double w = 0.0;
   int64_t n_sched = 0;  // n used by Algorithm 1's break rule
   CUtensorMap tmap;
-  float* vT = nullptr;  // owned: the level sample-major (MIXED passes of the second loop)
 };
 
 }  // namespace
@@ -158,20 +157,8 @@ void level_free(mbar_ctx* c, Level* L) {
     dfree(c, L->v);
     dfree(c, L->H);
     dfree(c, L->keys);
-    dfree(c, L->vT);
   }
   *L = Level{};
-}
-
-// The binned level also sample-major, for the sample-major pass (MIXED, the
-// K where that pass is the faster one); rebuilt after the row-major data
-// change.
-mbar_status level_samples(mbar_ctx* c, Level* L, bool rebuild) {
-  if (!L->binned || !c->smaj) return MBAR_OK;
-  if (L->vT && !rebuild) return MBAR_OK;
-  lse_smaj_prepare(c->K);  // its passes may be captured in a graph
-  if (!L->vT) BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&L->vT), sci_loop_level_bytes(c->K, L->n)));
-  return level_to_samples(static_cast<const float*>(L->v), c->K, L->n, L->ld, L->vT, c->st);
 }
 
 mbar_status level_tmap(mbar_ctx* c, Level* L) {
@@ -239,10 +226,7 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   const bool timed = !L.binned;
   if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
   mbar_status s = MBAR_OK;
-  if (L.binned && L.vT) {
-    // binned level, sample-major copy (columns in the level's own order)
-    s = lse_smaj_launch(L.vT, lse_smaj_plan(c->K, L.n), p, c->st);
-  } else if (!L.binned && c->smaj && c->vst) {
+  if (!L.binned && c->smaj && c->vst) {
     // unbinned MIXED pass over the sample-major copy (original sample order);
     // logden comes back to the store's column order through perm
     p.logden = logden_out ? c->logden_orig : nullptr;
@@ -1082,13 +1066,9 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
     BUMBAR_CUDA(cudaStreamSynchronize(c->st));
     double amax = 0.0;
     for (int64_t k = 0; k < K; ++k) amax = std::max(amax, std::fabs(c->f_h[k] + std::log(c->Nk_h[k])));
-    const bool recenter = amax > 64.0;
-    for (Level* L : {&cur, &nxt}) {
-      if (!L->binned) continue;
-      if (recenter)
-        BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
-      BUMBAR_TRY(level_samples(c, L, recenter));
-    }
+    if (!(amax > 64.0)) return MBAR_OK;
+    for (Level* L : {&cur, &nxt})
+      if (L->binned) BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
     return MBAR_OK;
   };
   s = recenter_pair();

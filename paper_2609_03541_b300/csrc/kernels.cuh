@@ -96,8 +96,6 @@ mbar_status sci_loop_launch(const float* vT, const SciLoopParams& prm, cudaStrea
 mbar_status level_to_samples(const float* v, int64_t K, int64_t n, int64_t ld, float* out, cudaStream_t st);
 LsePlan lse_smaj_plan(int64_t K, int64_t n);
 bool lse_smaj_preferred(int64_t K);
-// The sample-major pass's one-time kernel set-up for K (before a capture).
-void lse_smaj_prepare(int64_t K);
 mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st);
 // The SCI epilogue over the partials of a pass (lse.cu).
 mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream);

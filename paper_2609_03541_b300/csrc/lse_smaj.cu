@@ -279,25 +279,18 @@ void smaj_attr(size_t smem) {
 }
 
 template <int LPS, int NK, int NT>
-void smaj_init() {
+void smaj_run(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm, cudaStream_t st) {
   static bool init = false;
-  std::lock_guard<std::recursive_mutex> lock(init_mutex());
-  if (!init) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    smaj_attr<LPS, NK, NT>(static_cast<size_t>(optin));
-    init = true;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (!init) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      smaj_attr<LPS, NK, NT>(static_cast<size_t>(optin));
+      init = true;
+    }
   }
-}
-
-// prepare = true: only the one-time kernel attribute (callers do this before
-// a stream capture)
-template <int LPS, int NK, int NT>
-void smaj_run(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm, cudaStream_t st,
-              bool prepare = false) {
-  smaj_init<LPS, NK, NT>();
-  if (prepare) return;
   lse_smaj_kernel<LPS, NK, NT><<<pl.grid, NT, pl.smem, st>>>(vst, Kp, pl.C, pl.stages, prm);
 }
 
@@ -350,42 +343,6 @@ bool lse_smaj_supported(int64_t K) { return K >= 1 && K <= 1024; }
 // 1.8 ms).
 bool lse_smaj_preferred(int64_t K) { return K <= 48 || K >= 256; }
 
-namespace {
-
-bool smaj_dispatch(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm, cudaStream_t st, bool prepare) {
-  const int lps = pl.H, nk = pl.J;
-  if (lps < 32) {
-    switch (lps) {
-      case 1: smaj_run<1, 1, 512>(pl, vst, Kp, prm, st, prepare); return true;
-      case 2: smaj_run<2, 1, 512>(pl, vst, Kp, prm, st, prepare); return true;
-      case 4: smaj_run<4, 1, 512>(pl, vst, Kp, prm, st, prepare); return true;
-      case 8: smaj_run<8, 1, 512>(pl, vst, Kp, prm, st, prepare); return true;
-      case 16: smaj_run<16, 1, 512>(pl, vst, Kp, prm, st, prepare); return true;
-      default: return false;
-    }
-  }
-  switch (nk) {
-    case 1: smaj_run<32, 1, 512>(pl, vst, Kp, prm, st, prepare); return true;
-    case 2: smaj_run<32, 2, 512>(pl, vst, Kp, prm, st, prepare); return true;
-    case 3: smaj_run<32, 3, 512>(pl, vst, Kp, prm, st, prepare); return true;
-    case 4: smaj_run<32, 4, 512>(pl, vst, Kp, prm, st, prepare); return true;
-    case 5: smaj_run<32, 5, 256>(pl, vst, Kp, prm, st, prepare); return true;
-    case 6: smaj_run<32, 6, 256>(pl, vst, Kp, prm, st, prepare); return true;
-    case 7: smaj_run<32, 7, 256>(pl, vst, Kp, prm, st, prepare); return true;
-    case 8: smaj_run<32, 8, 256>(pl, vst, Kp, prm, st, prepare); return true;
-    default: return false;
-  }
-}
-
-}  // namespace
-
-void lse_smaj_prepare(int64_t K) {
-  const LsePlan pl = lse_smaj_plan(K, 1);
-  LseParams p{};
-  (void)smaj_dispatch(pl, nullptr, 0, p, nullptr, true);
-  cudaGetLastError();
-}
-
 mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st) {
   if (!pl.ok) {
     set_error("lse pass: %zu bytes of shared memory per CTA exceed the device limit", pl.smem);
@@ -394,9 +351,28 @@ mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, 
   prm.nparts = pl.grid;
   prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
   const int Kp = static_cast<int>(round_up(prm.K, 4));
-  if (!smaj_dispatch(pl, vst, Kp, prm, st, false)) {
-    set_error("lse_smaj_launch: unsupported shape");
-    return MBAR_EUNSUPPORTED;
+  const int lps = pl.H, nk = pl.J;
+  if (lps < 32) {
+    switch (lps) {
+      case 1: smaj_run<1, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 2: smaj_run<2, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 4: smaj_run<4, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 8: smaj_run<8, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 16: smaj_run<16, 1, 512>(pl, vst, Kp, prm, st); break;
+      default: set_error("lse_smaj_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+    }
+  } else {
+    switch (nk) {
+      case 1: smaj_run<32, 1, 512>(pl, vst, Kp, prm, st); break;
+      case 2: smaj_run<32, 2, 512>(pl, vst, Kp, prm, st); break;
+      case 3: smaj_run<32, 3, 512>(pl, vst, Kp, prm, st); break;
+      case 4: smaj_run<32, 4, 512>(pl, vst, Kp, prm, st); break;
+      case 5: smaj_run<32, 5, 256>(pl, vst, Kp, prm, st); break;
+      case 6: smaj_run<32, 6, 256>(pl, vst, Kp, prm, st); break;
+      case 7: smaj_run<32, 7, 256>(pl, vst, Kp, prm, st); break;
+      case 8: smaj_run<32, 8, 256>(pl, vst, Kp, prm, st); break;
+      default: set_error("lse_smaj_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+    }
   }
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
