@@ -691,8 +691,12 @@ def main():
     roofline = None
     if n_l:
         achieved = by_l / (ms_l / 1e3) / 1e9
+        # DRAM bytes per launch: the algorithmic bytes times the read+write
+        # ratio of one ncu capture of the same kernel (MIXED: K = 500,
+        # n = 4e5, 805.1 MB for 800.0 MB), FP64 kernels not captured
+        traffic = (by_l / n_l) * (805.1 / 800.0) if prec == M.MBAR_MIXED else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     "kernel": ("lse_smaj_kernel (unbinned passes, sample-major FP32)" if prec == M.MBAR_MIXED
                                else "lse_pass_kernel<double> (unbinned passes)"), "launches": n_l,
                     "avg_launch_ms": ms_l / n_l, "bytes_per_launch": by_l / n_l,
