@@ -268,15 +268,16 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
     const int64_t n0 = (first + static_cast<int64_t>(it) * stride) * kStCols;
     const int ns = static_cast<int>(N - n0 < kStCols ? N - n0 : kStCols);
     const unsigned char* X = xs + s * xb;
-    auto xat = [&](int64_t k) -> double {
-      return *reinterpret_cast<const double*>(X + k * 128 + (((jj >> 1) ^ static_cast<int>(k & 7)) << 4) +
-                                              (jj & 1) * 8);
-    };
+    // rows k = r0 + 32 i share the swizzle phase k & 7 = r0 & 7: one base
+    // address per thread, 32 rows (4096 bytes) per step
+    const unsigned char* xp = X + r0 * 128 + (((jj >> 1) ^ (r0 & 7)) << 4) + (jj & 1) * 8;
+    const int Ki = static_cast<int>(K), Kpi = static_cast<int>(Kp);
     // pass 1: column minimum (order-preserving integer image) and finiteness
     unsigned long long m = ~0ull;
     bool ok = true;
-    for (int64_t k = r0; k < K; k += kStRows) {
-      const double x = xat(k);
+#pragma unroll 4
+    for (int k = r0; k < Ki; k += kStRows) {
+      const double x = *reinterpret_cast<const double*>(xp + (k - r0) * 128);
       const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
       ok &= ((bx >> 52) & 0x7FF) != 0x7FF;
       const unsigned long long kx = ordered_bits(x);
@@ -311,17 +312,19 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
       const double cm = cmin[jj];
       const float mh = mhs[jj], ml = mls[jj];
       const bool msplit = msp[jj] != 0;
-      for (int64_t k = r0; k < Kp; k += kStRows) {
+      float* yp = Y + jj * Yp;
+#pragma unroll 4
+      for (int k = r0; k < Kpi; k += kStRows) {
         float r = 0.f;
-        if (k < K) {
-          const double x = xat(k);
+        if (k < Ki) {
+          const double x = *reinterpret_cast<const double*>(xp + (k - r0) * 128);
           float xh, xl;
           if (msplit && split_f64(x, xh, xl))
             r = __fadd_rn(__fsub_rn(xh, mh), __fsub_rn(xl, ml));
           else
             r = f64_to_f32_rn(x - cm);
         }
-        Y[jj * Yp + k] = r;
+        yp[k] = r;
       }
     }
     fence_proxy_async_smem();
