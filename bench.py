@@ -333,6 +333,10 @@ def batch_bench(args):
         bad = [i for i, st in enumerate(sts) if st != 0]
         wave_info.append({"problems": len(wave), "seconds": dt, "failed": len(bad)})
         log(f"[bench] batch wave {wi}: {len(wave)} problems in {dt:.3f} s, failed {len(bad)}")
+        slow = sorted(range(len(wave)), key=lambda i: -(reps[i].seconds_sci + reps[i].seconds_newton))[:3]
+        for i in slow:
+            kind, K, Nk, _ = wave[i]
+            log(f"[bench]   slowest: {kind} K={K} N_k={Nk} " + json.dumps(reps[i].as_dict()))
         if wi == 0 and not args.no_accuracy:
             cfg64 = M.server_config(workers=args.workers, hbm_budget_bytes=int(args.budget_gb * (1 << 30)),
                                     precision=M.MBAR_FP64)

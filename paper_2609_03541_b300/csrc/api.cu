@@ -1103,6 +1103,9 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   };
   Graph g;
   bool captured = false;
+  constexpr int kStallRounds = 40;
+  double d_mark = INFINITY;
+  int stall = 0;
   for (int64_t round = 0; s == MBAR_OK; ++round) {
     if (rep->iters_second_loop >= o.max_sci) break;
     const int64_t iters_before = c->hstat->ctrl.iters;
@@ -1132,9 +1135,21 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
     const double s_n = c->hstat->s, s_next = c->hstat->s2, d_n = c->hstat->d;
     rep->iters_second_loop += o.n_intermediate + 2;
     trace_row(c, 2, static_cast<double>(cur.n_sched), s_n, s_next);
+    // MIXED: SCI contracts geometrically, so a level whose step max|df|
+    // has not halved in kStallRounds rounds is moving on the FP32 rounding of
+    // its own evaluation (which can sit above the fixed noise floor)
+    if (d_n <= 0.5 * d_mark) {
+      d_mark = d_n;
+      stall = 0;
+    } else {
+      ++stall;
+    }
+    const bool stalled = c->dtype == 4 && stall >= kStallRounds;
     // Eq. 3, plus: a step under the evaluation's rounding floor means the
     // level has converged as far as this arithmetic can tell
-    if (2.0 * s_next > static_cast<double>(o.inc) * s_n || (o.noise_floor > 0.0 && d_n < o.noise_floor)) {
+    if (2.0 * s_next > static_cast<double>(o.inc) * s_n || (o.noise_floor > 0.0 && d_n < o.noise_floor) || stalled) {
+      d_mark = INFINITY;
+      stall = 0;
       if (cudaMemcpyAsync(c->f, c->fts, K * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess) {
         s = MBAR_ECUDA;
         break;

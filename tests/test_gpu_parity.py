@@ -552,3 +552,23 @@ def test_mixed_first_loop_follows_the_oracle(case):
     if int(g1[0][3]) == len(ph1):
         assert g1[0][2] == pytest.approx(ph1[-1][2], rel=2e-2)
     assert np.max(np.abs(f - f_ref)) < SOLVE_TOL["mixed"]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mixed_second_loop_ends_at_its_rounding_floor(seed):
+    """Four umbrella windows 1.0 apart barely overlap (the reduced Hessian's
+    smallest eigenvalue is 0.02-0.2): SCI contracts so slowly that the FP64
+    second loop runs 1e5-2e5 steps. MIXED raises n once its steps stop
+    shrinking (they sit on the FP32 rounding of the evaluation) instead of
+    running to max_sci, and ends within its rounding over that eigenvalue of
+    the oracle: error ~ (FP32 rounding of Q ~ 6e-8 N) / lambda_min."""
+    p = W.umbrella(K=4, N_k=4299, seed=seed, grid_points=1 << 13)
+    f_ref = O.solve_mbar(p.u_kn, p.N_k)
+    lam = np.linalg.eigvalsh(O.mbar_hessian(p.u_kn, f_ref, p.N_k)[1:, 1:]).min()
+    ctx = M.Context(p.u_kn, p.N_k, M.MBAR_MIXED)
+    ctx.set_coordinate(p.phi)
+    rep = ctx.solve().as_dict()
+    f = ctx.free_energies()
+    ctx.close()
+    assert rep["iters_second_loop"] < 20000, rep
+    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL["mixed"] + 6e-8 * p.N / lam, (rep, lam)
