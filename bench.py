@@ -698,10 +698,13 @@ def main():
         # DRAM bytes per launch: the algorithmic bytes times the read+write
         # ratio of one ncu capture of the same kernel (MIXED: K = 500,
         # n = 4e5, 805.1 MB for 800.0 MB), FP64 kernels not captured
-        traffic = (by_l / n_l) * (805.1 / 800.0) if prec == M.MBAR_MIXED else None
+        smaj = prec == M.MBAR_MIXED and (prob["K"] <= 48 or prob["K"] >= 256)
+        traffic = (by_l / n_l) * (805.1 / 800.0) if smaj else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                    "kernel": ("lse_smaj_kernel (unbinned passes, sample-major FP32)" if prec == M.MBAR_MIXED
+                    # the library's layout rule: sample-major for MIXED at K <= 48 or K >= 256
+                    "kernel": ("lse_smaj_kernel (unbinned passes, sample-major FP32)" if smaj
+                               else "lse_regs_kernel (unbinned passes, row-major FP32)" if prec == M.MBAR_MIXED
                                else "lse_pass_kernel<double> (unbinned passes)"), "launches": n_l,
                     "avg_launch_ms": ms_l / n_l, "bytes_per_launch": by_l / n_l,
                     "peak_source": f"{peaks_src} hbm_gbs"}

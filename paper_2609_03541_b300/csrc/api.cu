@@ -693,8 +693,10 @@ mbar_status first_loop_fused(mbar_ctx* c, const Level& L, mbar_report* rep) {
   return s;
 }
 
+constexpr double kFusedFirstBytes = 4.0 * (1 << 20);
+
 mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
-  if (c->dtype == 4 && L.binned && sci_loop_supported(c->K, L.n)) return first_loop_fused(c, L, rep);
+  if (c->dtype == 4 && L.binned && sci_loop_supported(c->K, L.n, kFusedFirstBytes)) return first_loop_fused(c, L, rep);
   BUMBAR_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st));
   auto batch = [&]() -> mbar_status {
     for (int b = 0; b < kPhase1Batch; ++b)
@@ -1060,19 +1062,31 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   // column's largest exponent lies between min_k a_k and max_k a_k (v >= 0),
   // so this only matters when some |a_k| is large: below 64 kT the FP32
   // spacing there is under 1e-5 kT per entry and the data stay as they are.
+  float* cur_vT = nullptr;  // owned: the current level sample-major, when small
+  constexpr double kFusedRoundBytes = 4.0 * (1 << 20);
   auto recenter_pair = [&]() -> mbar_status {
     if (c->dtype != 4) return MBAR_OK;
     BUMBAR_TRY(d2h(c, c->f_h.data(), c->f, K));
     BUMBAR_CUDA(cudaStreamSynchronize(c->st));
     double amax = 0.0;
     for (int64_t k = 0; k < K; ++k) amax = std::max(amax, std::fabs(c->f_h[k] + std::log(c->Nk_h[k])));
-    if (!(amax > 64.0)) return MBAR_OK;
-    for (Level* L : {&cur, &nxt})
-      if (L->binned) BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
+    if (amax > 64.0)
+      for (Level* L : {&cur, &nxt})
+        if (L->binned)
+          BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
+    // a small current level: its in-place steps run in one launch on its
+    // sample-major copy (sci_loop.cu)
+    dfree(c, cur_vT);
+    cur_vT = nullptr;
+    if (cur.binned && sci_loop_supported(K, cur.n, kFusedRoundBytes)) {
+      BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&cur_vT), sci_loop_level_bytes(K, cur.n)));
+      BUMBAR_TRY(level_to_samples(static_cast<const float*>(cur.v), K, cur.n, cur.ld, cur_vT, c->st));
+    }
     return MBAR_OK;
   };
   s = recenter_pair();
   if (s != MBAR_OK) {
+    dfree(c, cur_vT);
     level_free(c, &cur);
     level_free(c, &nxt);
     free_rest();
@@ -1082,8 +1096,22 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   // and the probe at n * inc (-> fts); the f buffers keep their addresses so
   // the captured round stays valid until the level pair changes
   auto round_body = [&]() -> mbar_status {
-    for (int i = 0; i < o.n_intermediate; ++i)
-      BUMBAR_TRY(run_lse(c, cur, c->f, kLseModeSci, c->f, nullptr, nullptr, 0.0, 0, nullptr));
+    if (cur_vT) {
+      SciLoopParams q{};
+      q.K = static_cast<int>(K);
+      q.n = static_cast<int>(cur.n);
+      q.H = cur.H;
+      q.f = c->f;
+      q.logN = c->logN_d;
+      q.Nk = c->Nk_d;
+      q.ctrl = c->ctrl;
+      q.err = err_word(c);
+      q.max_steps = o.n_intermediate;  // eps = noise = 0: exactly these steps
+      BUMBAR_TRY(sci_loop_launch(cur_vT, q, c->st));
+    } else {
+      for (int i = 0; i < o.n_intermediate; ++i)
+        BUMBAR_TRY(run_lse(c, cur, c->f, kLseModeSci, c->f, nullptr, nullptr, 0.0, 0, nullptr));
+    }
     BUMBAR_TRY(run_lse(c, cur, c->f, kLseModeSci, c->ft, nullptr, c->s, 0.0, 0, nullptr, c->d));
     BUMBAR_TRY(run_lse(c, nxt, c->f, kLseModeSci, c->fts, nullptr, c->s2, 0.0, 0, nullptr));
     return MBAR_OK;
@@ -1174,6 +1202,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   }
   g.reset();
   rep->final_bins = cur.binned ? cur.n : 0;
+  dfree(c, cur_vT);
   level_free(c, &cur);
   level_free(c, &nxt);
   free_rest();

@@ -147,10 +147,14 @@ __global__ void add_vectors(const double* __restrict__ x, const double* __restri
 
 static int g_hessian_path = 0;
 void set_hessian_path(int path) { g_hessian_path = path; }
-int hessian_path_for(int64_t K) {
+// Automatic choice: tensor cores from K = 64 for FP64 data (below that the
+// CUDA-core kernel's FP32 products keep Newton quadratic to f_tol = 1e-10),
+// from K = 16 for FP32 data (MIXED, f_tol 1e-5; on the parallel-tempering
+// shape, K = 50 and N = 1e7, the CUDA-core overlap took 8.8 ms per Hessian)
+int hessian_path_for(int64_t K, int dtype_bytes) {
   if (g_hessian_path == 1 || g_hessian_path == 2) return g_hessian_path;
   if (g_hessian_path == 3) return 2;
-  return K >= 64 ? 2 : 1;
+  return K >= (dtype_bytes == 4 ? 16 : 64) ? 2 : 1;
 }
 bool tc_cluster_enabled() { return g_hessian_path != 3; }
 
@@ -189,7 +193,7 @@ mbar_status hessian(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_
   const size_t simt = round_up(static_cast<int64_t>(p.nslices) * p.npairs * kTile * kTile * 4, 256);
   const size_t tc = overlap_tc_tmp_bytes(K, n) + round_up(K * 8, 256);
   double* G = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + std::max(simt, tc));
-  if (hessian_path_for(K) == 2) {
+  if (hessian_path_for(K, dtype_bytes) == 2) {
     double* a = static_cast<double*>(tmp);
     unsigned char* rest = static_cast<unsigned char*>(tmp) + round_up(K * 8, 256);
     add_vectors<<<static_cast<unsigned>(ceil_div(K, 256)), 256, 0, st>>>(f, logN, a, K);

@@ -89,7 +89,9 @@ struct SciLoopParams {
   double eps, noise;
   int64_t max_steps;
 };
-bool sci_loop_supported(int64_t K, int64_t n);
+// K within the kernel's shapes and the level (n x stage_pitch(K) floats) at
+// most max_bytes.
+bool sci_loop_supported(int64_t K, int64_t n, double max_bytes);
 size_t sci_loop_level_bytes(int64_t K, int64_t n);
 mbar_status sci_loop_launch(const float* vT, const SciLoopParams& prm, cudaStream_t st);
 // out[p * stage_pitch(K) + k] = v[k * ld + p] for p < n (entries k >= K zero).
@@ -203,7 +205,7 @@ size_t overlap_tc_tmp_bytes(int64_t K, int64_t n);
 // Which contraction hessian() uses: 0 = by size (tensor cores for K >= 64),
 // 1 = CUDA cores, 2 = tensor cores.
 void set_hessian_path(int path);
-int hessian_path_for(int64_t K);
+int hessian_path_for(int64_t K, int dtype_bytes);
 bool tc_cluster_enabled();
 // Direct launches instead of captured CUDA graphs for a context's binned
 // loops (server workers: a stream capture in one thread would make another

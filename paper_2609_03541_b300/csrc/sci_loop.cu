@@ -449,12 +449,12 @@ LoopPlan loop_plan(int64_t K) {
 
 }  // namespace
 
-bool sci_loop_supported(int64_t K, int64_t n) {
+bool sci_loop_supported(int64_t K, int64_t n, double max_bytes) {
   if (K < 1 || K > 1024 || n < 1) return false;
   // one cluster of 8 CTAs sweeps the whole level each step: worth it while
-  // the level is small (a separate pass + epilogue costs ~30 us of latency
-  // per step)
-  return static_cast<double>(n) * stage_pitch(K) * 4 <= 1.0 * (1 << 20) && loop_plan(K).smem <= 220 * 1024;
+  // the level is small (a separate pass + epilogue costs ~30-40 us of
+  // latency per step)
+  return static_cast<double>(n) * stage_pitch(K) * 4 <= max_bytes && loop_plan(K).smem <= 220 * 1024;
 }
 
 size_t sci_loop_level_bytes(int64_t K, int64_t n) { return static_cast<size_t>(n) * stage_pitch(K) * 4; }
