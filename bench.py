@@ -697,9 +697,9 @@ def main():
         achieved = by_l / (ms_l / 1e3) / 1e9
         # DRAM bytes per launch: the algorithmic bytes times the read+write
         # ratio of one ncu capture of the same kernel (MIXED: K = 500,
-        # n = 4e5, 805.1 MB for 800.0 MB), FP64 kernels not captured
+        # n = 4e5, 804.7 MB for 800.0 MB), FP64 kernels not captured
         smaj = prec == M.MBAR_MIXED and (prob["K"] <= 48 or prob["K"] >= 256)
-        traffic = (by_l / n_l) * (805.1 / 800.0) if smaj else None
+        traffic = (by_l / n_l) * (804.7 / 800.0) if smaj else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     # the library's layout rule: sample-major for MIXED at K <= 48 or K >= 256

