@@ -109,6 +109,14 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
 }
 
 // 2^x on the SFU (MUFU.EX2), flushing denormal results to zero.
+// 1/x to within 1 ulp, denormals flushed (callers pass sums whose largest
+// term is 1); the IEEE division takes about ten instructions
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -16,10 +16,13 @@
 //     stage is then released and its next TMA load issued at once;
 //   * A2 turns x_j into e_j = 2^(x_j - max) in place; column sum likewise;
 //   * B accumulates e_j * H_c / s_c into per-thread row partials acc_j.
-// Every 32 stages the four column lanes that share rows are combined by
-// shuffles and added into one FP64 slot per warp and row in shared memory
-// (fixed order, deterministic); at the end a row's slots are summed in order
-// and the common epilogue (lse_common.cuh) runs. H = 1 (two 32-column
+// Every 64 stages the four column lanes that share rows are combined by
+// shuffles and added by TwoSum into one slot per warp and row in shared
+// memory, an unevaluated FP32 sum hi + lo (fixed order, deterministic; FP64
+// adds there stall every warp on B300's slow FP64 pipe, as all warps fold
+// in the same stage); at the end a row's slots are summed in order in FP64
+// and the common epilogue (lse_common.cuh) runs. 1 / column sum by
+// rcp.approx (1 ulp). H = 1 (two 32-column
 // sub-tiles per stage, no cross-warp exchange) serves K <= 256; H = 2 serves
 // K <= 512. Per entry: one shared-memory read of v and one of a, two FFMA
 // and an add for x, one max, one SFU ex2, two adds and one FFMA.
@@ -44,14 +47,14 @@ namespace bumbar {
 namespace {
 
 constexpr int kRThreads = 512;
-constexpr int kFlush = 32;  // stages between FP32 -> FP64 flushes
+constexpr int kFlush = 64;  // stages between folds of the FP32 row partials
 constexpr uint32_t kSpin = 1u << 28;
 
 __host__ __device__ inline size_t rupr(size_t x, size_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-// shared memory: stages | a [Kpad] (hi, lo) f32 pairs | slots [16][Kpad] f64 | colm[2][32] |
+// shared memory: stages | a [Kpad] (hi, lo) f32 pairs | slots [16][Kpad] (hi, lo) f32 | colm[2][32] |
 //                cols[2][32] | mbarriers[8]
 struct RegsSmem {
   static __host__ __device__ size_t kpad(int K) { return rupr(static_cast<size_t>(K), 16); }
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
   unsigned char* cur = smem + p.stages * sbytes;
   float2* a_s = reinterpret_cast<float2*>(cur);
   cur += kp * 8;
-  double* slots = reinterpret_cast<double*>(cur);  // [NSLOT][kp]
+  float2* slots = reinterpret_cast<float2*>(cur);  // [NSLOT][kp] unevaluated sums hi + lo
   cur += NSLOT * kp * 8;
   float* colm = reinterpret_cast<float*>(cur);     // [2][32]
   float* cols = colm + 64;                         // [2][32]
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     const float hi = static_cast<float>(a);
     a_s[k] = make_float2(hi, isfinite(hi) ? static_cast<float>(a - static_cast<double>(hi)) : 0.f);
   }
-  for (int i = tid; i < static_cast<int>(NSLOT * kp); i += kRThreads) slots[i] = 0.0;
+  for (int i = tid; i < static_cast<int>(NSLOT * kp); i += kRThreads) slots[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
   const uint32_t tx = static_cast<uint32_t>(sbytes);
@@ -138,7 +141,13 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
       v += __shfl_xor_sync(0xffffffffu, v, 8);
       v += __shfl_xor_sync(0xffffffffu, v, 16);
       const int k = r0 + RG * j;
-      if (lane < 8 && k < K) slots[warp * kp + k] += static_cast<double>(v);
+      if (lane < 8 && k < K) {
+        // TwoSum (Knuth): hi + v = sum + err exactly
+        const float2 c = slots[warp * kp + k];
+        const float sum = c.x + v, bv = sum - c.x;
+        const float err = (c.x - (sum - bv)) + (v - bv);
+        slots[warp * kp + k] = make_float2(sum, c.y + err);
+      }
       acc[j] = 0.f;
     }
   };
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     const bool valid = gcol < p.n;
     float w = 0.f;
     if (valid) {
-      w = (p.H ? static_cast<float>(p.H[gcol]) : 1.f) / ssum;
+      w = (p.H ? static_cast<float>(p.H[gcol]) : 1.f) * rcp_approx(ssum);
       if (p.logden != nullptr && h == 0 && (lane & 7) == 0)
         static_cast<float*>(p.logden)[gcol] = (m + __log2f(ssum)) * kLn2;
     }
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(kRThreads, 1) lse_regs_kernel(const __grid_con
     double t = 0.0;
     if (k < K) {
 #pragma unroll
-      for (int g = 0; g < NSLOT; ++g) t += slots[g * kp + k];
+      for (int g = 0; g < NSLOT; ++g) t += static_cast<double>(slots[g * kp + k].x) + static_cast<double>(slots[g * kp + k].y);
     }
     rowsum[j] = t;
   }

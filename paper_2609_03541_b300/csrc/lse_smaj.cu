@@ -24,10 +24,17 @@
 //     max), and the lanes' row partials acc_k += e / sum (one sample per
 //     lane group at a time: two samples at once measured slower with the
 //     large stages, 0.92 vs 0.81 ms);
-//   * every 32 samples a warp folds its FP32 partials (and those of its lane
-//     groups) into its FP64 row of shared memory; at the end the warps' rows
-//     are added in warp order (deterministic) and written as the CTA's row
-//     of the partial sums, which lse_epilogue_kernel reduces.
+//   * every 64 sample slots a warp folds its FP32 partials (and those of its
+//     lane groups) into its row of shared memory, kept as unevaluated FP32
+//     sums hi + lo updated by TwoSum (64 FP32 terms <= 1 each: relative
+//     error <= 3.8e-6, ~2e-7 typical, before the fold). FP64 adds there (the
+//     FP64 pipe of B300 is slow, and the warps fold at about the same time)
+//     cost 6.5 % of the pass at K = 500 with folds every 32 slots; TwoSum
+//     every 32 slots 2.7 %, every 64 slots 1.4 %. At the end the warps' rows are added in warp order
+//     (deterministic, FP64) and written as the CTA's row of the partial
+//     sums, which lse_epilogue_kernel reduces;
+//   * 1 / sum by rcp.approx (1 ulp; the IEEE division measured 2.3 % of the
+//     pass at K = 500, 10 % at K = 16).
 #include <cmath>
 #include <mutex>
 
@@ -39,7 +46,7 @@ namespace bumbar {
 namespace {
 
 constexpr uint32_t kSmSpin = 1u << 28;  // bounded mbarrier polls
-constexpr int kSmFlush = 32;            // sample slots between FP32 -> FP64 folds
+constexpr int kSmFlush = 64;            // sample slots between folds of the FP32 partials
 constexpr int kSmStageBytes = 48 * 1024;
 
 __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -72,8 +79,9 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
   if (lse_skip(p)) return;
 
   const size_t sbytes = static_cast<size_t>(S) * Kp * 4;
-  double* slots64 = reinterpret_cast<double*>(smem + stages * sbytes);  // [NWC][Kp] FP64 row partials
-  uint64_t* full = reinterpret_cast<uint64_t*>(slots64 + static_cast<size_t>(NWC) * Kp);
+  // [NWC][Kp] row partials as unevaluated FP32 sums hi + lo
+  float2* rows = reinterpret_cast<float2*>(smem + stages * sbytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(rows + static_cast<size_t>(NWC) * Kp);
   uint64_t* empty = full + stages;
   int* abort_flag = reinterpret_cast<int*>(empty + stages);
 
@@ -89,7 +97,22 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
     *abort_flag = 0;
     fence_barrier_init();
   }
-  for (int i = tid; i < NWC * Kp; i += NT) slots64[i] = 0.0;
+  // the state offsets a_k log2(e) as FP32 (hi, lo) pairs, computed once per
+  // CTA (the FP64 pipe is slow) into the first compute warp's partial row
+  // (2 Kp floats); that row is zeroed once every compute warp
+  // has copied its entries to registers
+  float* a2 = reinterpret_cast<float*>(rows);
+  for (int k = tid; k < Kp; k += NT) {
+    float hi = -INFINITY, lo = 0.f;  // padding rows: weight 0
+    if (k < K) {
+      const double a = (p.f[k] + p.logN[k]) * 1.4426950408889634;
+      hi = static_cast<float>(a);
+      lo = isfinite(hi) ? static_cast<float>(a - static_cast<double>(hi)) : 0.f;  // N_k = 0: -inf
+    }
+    a2[k] = hi;
+    a2[Kp + k] = lo;
+  }
+  for (int i = Kp + tid; i < NWC * Kp; i += NT) rows[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
   const int lig = lane % LPS;  // lane in group
@@ -133,21 +156,19 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int k = 4 * (lig + LPS * i) + t;
-        if (k < K) {
-          const double a = (p.f[k] + p.logN[k]) * 1.4426950408889634;
-          const float hi = static_cast<float>(a);
-          ahi[4 * i + t] = hi;
-          alo[4 * i + t] = isfinite(hi) ? static_cast<float>(a - static_cast<double>(hi)) : 0.f;  // N_k = 0: -inf
-        } else {
-          ahi[4 * i + t] = -INFINITY;  // padding rows: weight 0
-          alo[4 * i + t] = 0.f;
-        }
+        ahi[4 * i + t] = k < Kp ? a2[k] : -INFINITY;
+        alo[4 * i + t] = k < Kp ? a2[Kp + k] : 0.f;
       }
+    asm volatile("bar.sync 1, %0;" ::"n"(NWC * 32) : "memory");
+    if (cw == 0) {
+      for (int k = lane; k < Kp; k += 32) rows[k] = make_float2(0.f, 0.f);
+      __syncwarp();
+    }
     float acc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[e] = 0.f;
     int slots = 0;
-    double* myslots = slots64 + static_cast<size_t>(cw) * Kp;
+    float2* myrow = rows + static_cast<size_t>(cw) * Kp;
     auto fold = [&]() {
 #pragma unroll
       for (int i = 0; i < NK; ++i)
@@ -158,7 +179,14 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
 #pragma unroll
           for (int o = LPS; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
           const int k = 4 * (lig + LPS * i) + t;
-          if (grp == 0 && k < Kp) myslots[k] += static_cast<double>(v);
+          if (grp == 0 && k < Kp) {
+            // TwoSum (Knuth): hi + v = s + err exactly; the FP32 pair
+            // carries ~48 bits, without the slow FP64 pipe
+            const float2 c = myrow[k];
+            const float sum = c.x + v, bv = sum - c.x;
+            const float err = (c.x - (sum - bv)) + (v - bv);
+            myrow[k] = make_float2(sum, c.y + err);
+          }
           acc[e] = 0.f;
         }
     };
@@ -216,7 +244,7 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
         float w0 = 0.f;
         if (v0) {
           const int64_t gn = n0 + j0;
-          w0 = (p.H ? static_cast<float>(p.H[gn]) : 1.f) / s0;
+          w0 = (p.H ? static_cast<float>(p.H[gn]) : 1.f) * rcp_approx(s0);
           if (p.logden != nullptr && lig == 0) static_cast<float*>(p.logden)[gn] = (m0 + __log2f(s0)) * kLn2;
         }
 #pragma unroll
@@ -232,12 +260,15 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
     fold();
   }
 
-  // ---- per-CTA row sums: the compute warps' FP64 partials in warp order ----
+  // ---- per-CTA row sums: the compute warps' partials in warp order ----
   __syncthreads();
   double* out = p.partials + static_cast<size_t>(blockIdx.x) * K;
   for (int k = tid; k < K; k += NT) {
     double t = 0.0;
-    for (int w = 0; w < NWC; ++w) t += slots64[static_cast<size_t>(w) * Kp + k];
+    for (int w = 0; w < NWC; ++w) {
+      const float2 c = rows[static_cast<size_t>(w) * Kp + k];
+      t += static_cast<double>(c.x) + static_cast<double>(c.y);
+    }
     out[k] = t;
   }
 }
