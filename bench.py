@@ -203,6 +203,8 @@ def lse_only(args):
     dt = torch.float32 if args.lse_dtype == "float32" else torch.float64
     g = torch.Generator(device=dev)
     g.manual_seed(0)
+    if args.lse_layout == "factorised":
+        return lse_factorised_only(args)
     samples = args.lse_layout == "samples" and dt == torch.float32
     f = torch.linspace(-1, 1, K, device=dev, dtype=torch.float64)
     logN = torch.full((K,), float(np.log(n / K)), device=dev, dtype=torch.float64)
@@ -245,6 +247,58 @@ def lse_only(args):
                       "algorithmic_bytes": algo, "achieved_GBps": gbs, "peak_GBps": peaks["hbm_gbs"],
                       "frac": gbs / peaks["hbm_gbs"], "peak_source": src,
                       "entries_per_s": K * n / (ms / 1e3)}), flush=True)
+    return 0
+
+
+def lse_factorised_only(args):
+    """Times mbar_lse_pass_factorised on tempering-shaped factorised
+    potentials u_kp = b_k E_p (b_k = T_min / T_k over 298..600 K, E from a
+    Gaussian density of states of variance 2000 kT^2, f at its analytic
+    value) with CUDA events on the launching stream. The pass reads n * 8
+    bytes and evaluates K * n exponentials: its roofline is the SFU rate,
+    148 SMs x 16 ex2 per clock x the maximum SM clock."""
+    import torch
+    from paper_2609_03541_b300 import mbar as M
+    dev = torch.device("cuda", 0)
+    K, n = args.lse_K, args.lse_n
+    s2 = 2000.0
+    t = np.linspace(0.0, np.log(600.0 / 298.0), K)
+    b = 1.0 / np.exp(t)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    bt = torch.from_numpy(b).to(dev)
+    state = torch.arange(n, device=dev) % K
+    phi = -bt[state] * s2 + np.sqrt(s2) * torch.randn(n, generator=g, device=dev, dtype=torch.float64)
+    a = torch.zeros(K, device=dev, dtype=torch.float64)
+    f = torch.from_numpy(-(b ** 2) * s2 / 2).to(dev)
+    logN = torch.full((K,), float(np.log(n / K)), device=dev, dtype=torch.float64)
+    Q = torch.empty(K, device=dev, dtype=torch.float64)
+    logden = torch.empty(n, device=dev, dtype=torch.float64)
+    scratch = torch.zeros(M.lse_factorised_scratch_bytes(K, n), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def one():
+        M.lse_pass_factorised(a, bt, phi, f, logN, Q, logden=logden, scratch=scratch, stream=stream)
+    for _ in range(max(args.warmup, 1)):
+        one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    peaks, src = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 16 * peaks.get("sm_max_mhz", 2032.0) * 1e6     # ex2 per second
+    eps = K * n / (ms / 1e3)
+    print(json.dumps({"kernel": "lse_fact_kernel (u_kp = a_k + b_k phi_p, generated)", "K": K, "n": n,
+                      "ms_per_launch": ms, "bound": "alu (SFU ex2)", "entries_per_s": eps,
+                      "peak_entries_per_s": peak, "frac": eps / peak,
+                      "peak_source": f"{sms} SMs x 16 ex2/clk x {src} sm_max_mhz",
+                      "bytes_read": n * 8, "Q_rel_spread": float((Q / Q.mean()).std())}), flush=True)
     return 0
 
 
@@ -494,8 +548,9 @@ def main():
     ap.add_argument("--lse-K", type=int, default=500)
     ap.add_argument("--lse-n", type=int, default=2_000_000)
     ap.add_argument("--lse-dtype", default="float32", choices=["float32", "float64"])
-    ap.add_argument("--lse-layout", default="samples", choices=["samples", "rows"],
-                    help="--lse-only: sample-major FP32 store (MIXED's unbinned passes) or row-major")
+    ap.add_argument("--lse-layout", default="samples", choices=["samples", "rows", "factorised"],
+                    help="--lse-only: sample-major FP32 store (MIXED's unbinned passes), row-major, or "
+                         "factorised u_kp = a_k + b_k phi_p generated from phi")
     ap.add_argument("--hess-only", action="store_true",
                     help="time mbar_hessian (one fused LSE pass + the tensor-core Hessian) on a random K x n problem")
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")

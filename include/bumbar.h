@@ -309,6 +309,27 @@ BUMBAR_API mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64
                                              const double* log_N, const int32_t* H, double* Q, float* logden,
                                              void* scratch, size_t scratch_bytes, void* stream);
 
+/* The same pass over factorised reduced potentials u_kp = a_k + b_k phi_p
+ * (Sec. II: the paper's energies u_kp = beta_k E_p are the case a = 0,
+ * b = beta, phi = E), generated on the device from the 2 K + n inputs
+ * instead of read from a K x n store. The exponents are formed from
+ * unevaluated FP32 pairs of the FP64 inputs and rounded once where
+ * f_k + log N_k - a_k and b_k phi_p cancel, so potentials of thousands of
+ * kT keep about FP32 resolution of the exponent itself; the sums are FP32
+ * per sample and FP64 across samples.
+ *   a, b (device FP64[K]); phi (device FP64[n], finite);
+ *   f, log_N, H, Q as for mbar_lse_pass;
+ *   logden (device FP64[n], nullable, out): logden_p as above;
+ *   scratch of at least mbar_lse_factorised_scratch_bytes(K, n) bytes,
+ *   16-byte aligned, zero before the first call (left zero again).
+ * Runs asynchronously on `stream`. EINVAL on null pointers, bad sizes or
+ * a short or misaligned scratch; EUNSUPPORTED for K > 1024. */
+BUMBAR_API size_t mbar_lse_factorised_scratch_bytes(int64_t K, int64_t n);
+BUMBAR_API mbar_status mbar_lse_pass_factorised(const double* a, const double* b, const double* phi, int64_t K,
+                                                int64_t n, const double* f, const double* log_N, const int32_t* H,
+                                                double* Q, double* logden, void* scratch, size_t scratch_bytes,
+                                                void* stream);
+
 /* ---------------------------------------------------------------------
  * Allocation-free variant of mbar_lse_pass (no counterpart in the paper;
  * an interface for callers that cannot allocate device memory: for example

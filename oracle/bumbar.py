@@ -15,6 +15,7 @@ float64 numpy, in the paper's order and (generalised) notation:
 
 Section map (BU-MBAR: Mueller, Alesiani, Christiansen):
   Eq. 1        sci_step            self-consistent (WHAM) update over n bins
+  Sec. II      factorised_u        u_kp = a_k + b_k phi_p (the paper's beta_i E_p)
   Sec. II      bin_keys, histogram, nonempty_bins, width_for_bins, binned_u
   Eq. 2        relative_step
   Eq. 3 / Alg. 1  bu_mbar          binned-to-unbinned driver
@@ -43,7 +44,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "logsumexp", "log_denominator", "sci_step", "gauge", "relative_step",
+    "logsumexp", "log_denominator", "factorised_u", "sci_step", "gauge", "relative_step",
     "mbar_weights", "mbar_objective", "mbar_gradient", "mbar_hessian",
     "newton_direction", "newton_finish", "solve_mbar",
     "bin_keys", "nonempty_bins", "histogram", "binned_u", "width_for_bins",
@@ -71,6 +72,21 @@ def log_denominator(u_kp: np.ndarray, f_k: np.ndarray, N_k: np.ndarray) -> np.nd
     u_kp = np.asarray(u_kp, dtype=np.float64)
     a = np.asarray(f_k, dtype=np.float64)[:, None] + np.log(np.asarray(N_k, dtype=np.float64))[:, None]
     return logsumexp(a - u_kp, axis=0)
+
+
+def factorised_u(a_k: np.ndarray, b_k: np.ndarray, phi_p: np.ndarray) -> np.ndarray:
+    """Reduced potentials of the factorised form the paper starts from
+    (Sec. II: u_ip = beta_i E_p for samples with energy E_p at inverse
+    temperatures beta_i), generalised by a per-state offset:
+
+        u_kp = a_k + b_k phi_p.
+
+    Every other function here takes the K x n matrix this returns.
+    """
+    a = np.asarray(a_k, dtype=np.float64)
+    b = np.asarray(b_k, dtype=np.float64)
+    phi = np.asarray(phi_p, dtype=np.float64)
+    return a[:, None] + b[:, None] * phi[None, :]
 
 
 def sci_step(u_kp: np.ndarray, f_k: np.ndarray, N_k: np.ndarray,

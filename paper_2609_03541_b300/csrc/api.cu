@@ -2079,4 +2079,46 @@ mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const
   return lse_smaj_launch(v_nk, lse_smaj_plan(K, n), p, static_cast<cudaStream_t>(stream));
 }
 
+size_t mbar_lse_factorised_scratch_bytes(int64_t K, int64_t n) {
+  if (K < 1 || K > 1024 || n < 1) return 0;
+  return lse_scratch_for_grid(K, lse_fact_plan(K, n).grid) + 256;
+}
+
+mbar_status mbar_lse_pass_factorised(const double* a, const double* b, const double* phi, int64_t K, int64_t n,
+                                     const double* f, const double* log_N, const int32_t* H, double* Q,
+                                     double* logden, void* scratch, size_t scratch_bytes, void* stream) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
+  if (!a || !b || !phi || !f || !log_N || !Q || !scratch) {
+    set_error("mbar_lse_pass_factorised: null pointer argument");
+    return MBAR_EINVAL;
+  }
+  if (K < 1 || n < 1 || n > 2000000000LL) {
+    set_error("mbar_lse_pass_factorised: bad sizes K=%lld n=%lld", (long long)K, (long long)n);
+    return MBAR_EINVAL;
+  }
+  if (K > 1024) {
+    set_error("mbar_lse_pass_factorised: K=%lld exceeds 1024", (long long)K);
+    return MBAR_EUNSUPPORTED;
+  }
+  if ((reinterpret_cast<uintptr_t>(scratch) & 15) != 0 || scratch_bytes < mbar_lse_factorised_scratch_bytes(K, n)) {
+    set_error("mbar_lse_pass_factorised: scratch must be 16-byte aligned and at least "
+              "mbar_lse_factorised_scratch_bytes()");
+    return MBAR_EINVAL;
+  }
+  LseParams p{};
+  p.K = static_cast<int>(K);
+  p.n = static_cast<int>(n);
+  p.f = f;
+  p.logN = log_N;
+  p.H = H;
+  unsigned char* sc = static_cast<unsigned char*>(scratch);
+  p.counter = reinterpret_cast<unsigned*>(sc);
+  p.err = reinterpret_cast<unsigned*>(sc + 4);
+  p.partials = reinterpret_cast<double*>(sc + 256);
+  p.Q = Q;
+  p.logden = logden;
+  p.mode = kLseModePass;
+  return lse_fact_launch(a, b, phi, lse_fact_plan(K, n), p, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

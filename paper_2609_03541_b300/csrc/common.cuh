@@ -138,4 +138,47 @@ __device__ __forceinline__ uint32_t swz128(uint32_t row, uint32_t chunk) {
 mbar_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
                          int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows);
 
+// Splits a binary64 x into hi = RN32(x) and lo = RN32(x - hi) with integer
+// operations only: the residual is (dropped 29 fraction bits - the rounding
+// increment) x 2^(E - 1075), formed as an int -> float conversion and a
+// power-of-two scale. False when hi or the scale would leave the normal
+// binary32 range (the caller then uses FP64 arithmetic).
+__device__ __forceinline__ bool split_f64(double x, float& hi, float& lo) {
+  const unsigned long long d = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned int dh = static_cast<unsigned int>(d >> 32), dl = static_cast<unsigned int>(d);
+  const int E = static_cast<int>((dh >> 20) & 0x7FFu);
+  const int e = E - 1023 + 127;
+  const int s = E - 1075;  // weight of the last binary64 fraction bit
+  if (e <= 0 || e >= 254 || s < -126) return false;
+  const unsigned int sign = dh & 0x80000000u;
+  const unsigned int mant = ((dh & 0xFFFFFu) << 3) | (dl >> 29);
+  const unsigned int rest = dl & 0x1FFFFFFFu;
+  const unsigned int half = 0x10000000u;
+  const unsigned int up = (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
+  hi = __uint_as_float(sign | (((static_cast<unsigned int>(e) << 23) | mant) + up));
+  const int r = static_cast<int>(rest) - (up ? (1 << 29) : 0);
+  const float scale = __uint_as_float(static_cast<unsigned int>(s + 127) << 23);
+  lo = __uint_as_float(sign ^ __float_as_uint(__int2float_rn(r) * scale));
+  return true;
+}
+
+// binary32 -> binary64 with integer operations only (exact: widen the
+// exponent, shift the fraction); subnormal inputs take the hardware
+// conversion, which runs on the FP64 pipe.
+__device__ __forceinline__ double f32_to_f64_bits(float x) {
+  const unsigned int u = __float_as_uint(x);
+  const unsigned int sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  unsigned int hi;
+  if (e == 0u) {
+    if (m != 0u) return static_cast<double>(x);
+    hi = sign;  // +-0
+  } else if (e == 0xFFu) {
+    hi = sign | 0x7FF00000u | (m >> 3);  // inf / nan
+  } else {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+  }
+  const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | (static_cast<unsigned long long>(m) << 29);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 }  // namespace bumbar

@@ -101,6 +101,11 @@ bool lse_smaj_preferred(int64_t K);
 mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st);
 // The SCI epilogue over the partials of a pass (lse.cu).
 mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream);
+// Factorised u_kp = a_k + b_k phi_p (lse_fact.cu): a, b device FP64[K],
+// phi device FP64[n]; logden (if set) device FP64[n].
+LsePlan lse_fact_plan(int64_t K, int64_t n);
+mbar_status lse_fact_launch(const double* a, const double* b, const double* phi, const LsePlan& pl, LseParams prm,
+                            cudaStream_t st);
 LsePlan lse_regs_plan(int64_t K, int64_t n);
 mbar_status lse_regs_launch(const CUtensorMap& tmap, const LsePlan& pl, const LseParams& prm, cudaStream_t st);
 size_t lse_scratch_bytes(int64_t K, int64_t n, int dtype_bytes);

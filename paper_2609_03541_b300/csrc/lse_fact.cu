@@ -1,0 +1,283 @@
+// Fused paired-LSE pass (Eq. 1) over factorised reduced potentials
+//     u_kp = a_k + b_k phi_p,
+// the setting the paper starts from (u_kp = beta_k E_p: a = 0, b = beta,
+// phi = the sample's energy). u is generated in registers from phi, so the
+// pass reads 8 bytes per sample (12 with counts) instead of K * 4: it is
+// bound by the SFU (one ex2 per entry) and the FP32 pipe, not by HBM.
+// For every sample p
+//     logden_p = log sum_j exp(f_j + log N_j - a_j - b_j phi_p),
+//     Q_i     += H_p exp(f_i + log N_i - a_i - b_i phi_p - logden_p).
+//
+// Arithmetic: per state the FP64 constants c_k = (f_k + log N_k - a_k)
+// log2(e) and b'_k = b_k log2(e) become unevaluated FP32 pairs (hi, lo), as
+// does each phi_p. The exponent in log2 units,
+//     x_kp = c_k - b'_k phi_p
+//          = fma(-b_hi, p_hi, c_hi) + fma(-b_lo, p_hi, fma(-b_hi, p_lo, c_lo)),
+// rounds once where c_k and b'_k phi_p cancel (the first fma is exact before
+// its rounding), so x carries an absolute error of about one FP32 ulp of x
+// itself even when a_k + b_k phi_p is thousands of kT (tempering energies);
+// the dropped b_lo p_lo term is 2^-48 of the product. Four FP32 operations
+// per entry, then max, ex2, sum and one FMA into the row partial.
+//
+// Schedule: one CTA per SM, every warp computes. Warps take 32-sample chunks
+// round robin over the grid; lane l loads phi (and H) of sample l of the
+// chunk, and LPS-lane groups take the samples one after another (shuffles).
+// A lane holds 4 NK states (LPS lanes cover Kp = K rounded up to 4; up to 16
+// states per lane below K = 256, so at K <= 16 a lane owns whole samples),
+// with the four constants of each in registers. Row partials as in the
+// sample-major pass: FP32 per lane, folded every 64 samples into the warp's
+// row of shared memory as an unevaluated FP32 sum (TwoSum), the rows added
+// in warp order in FP64 at the end; lse_epilogue_kernel reduces the CTAs'
+// rows.
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace bumbar {
+
+namespace {
+
+constexpr int kFactFlush = 64;  // sample slots between folds of the FP32 partials
+
+// FP64 -> FP32 pair (hi, lo), hi = RN32(x); lo = 0 when hi is not finite
+__device__ __forceinline__ void split_pair(double x, float& hi, float& lo) {
+  hi = static_cast<float>(x);
+  lo = isfinite(hi) ? static_cast<float>(x - static_cast<double>(hi)) : 0.f;
+}
+
+// The same per sample with integer operations (the FP64 pipe of B300 is
+// narrow, and this conversion sits on every sample's path); zero, tiny and
+// huge values take the FP64 route.
+__device__ __forceinline__ void split_pair_fast(double x, float& hi, float& lo) {
+  if (!split_f64(x, hi, lo)) split_pair(x, hi, lo);
+}
+
+}  // namespace
+
+template <int LPS, int NK, int NT>
+__global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                         const double* __restrict__ phi, int Kp, LseParams p) {
+  constexpr int SPW = 32 / LPS;  // samples per warp at once
+  constexpr int NW = NT / 32;
+  constexpr int E = 4 * NK;      // states per lane
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* cst = reinterpret_cast<float4*>(smem_raw);   // [Kp] (c_hi, c_lo, b_hi, b_lo)
+  float2* rows = reinterpret_cast<float2*>(cst + Kp);  // [NW][Kp] unevaluated sums hi + lo
+  const int K = p.K;
+  const int64_t n = p.n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (lse_skip(p)) return;
+
+  for (int k = tid; k < Kp; k += NT) {
+    float4 c = make_float4(-INFINITY, 0.f, 0.f, 0.f);  // padding states: weight 0
+    if (k < K) {
+      split_pair((p.f[k] + p.logN[k] - a[k]) * 1.4426950408889634, c.x, c.y);  // N_k = 0: -inf
+      split_pair(b[k] * 1.4426950408889634, c.z, c.w);
+    }
+    cst[k] = c;
+  }
+  for (int i = tid; i < NW * Kp; i += NT) rows[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  const int lig = lane % LPS;  // lane in group
+  const int grp = lane / LPS;  // sample group within the warp
+  float ch[E], cl[E], bh[E], bl[E];
+#pragma unroll
+  for (int i = 0; i < NK; ++i)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = 4 * (lig + LPS * i) + t;
+      const float4 c = k < Kp ? cst[k] : make_float4(-INFINITY, 0.f, 0.f, 0.f);
+      ch[4 * i + t] = c.x;
+      cl[4 * i + t] = c.y;
+      bh[4 * i + t] = c.z;
+      bl[4 * i + t] = c.w;
+    }
+  float acc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) acc[e] = 0.f;
+  float2* myrow = rows + static_cast<size_t>(warp) * Kp;
+  auto fold = [&]() {
+#pragma unroll
+    for (int i = 0; i < NK; ++i)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = 4 * i + t;
+        float v = acc[e];
+#pragma unroll
+        for (int o = LPS; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int k = 4 * (lig + LPS * i) + t;
+        if (grp == 0 && k < Kp) {
+          // TwoSum (Knuth): hi + v = sum + err exactly
+          const float2 c = myrow[k];
+          const float sum = c.x + v, bv = sum - c.x;
+          const float err = (c.x - (sum - bv)) + (v - bv);
+          myrow[k] = make_float2(sum, c.y + err);
+        }
+        acc[e] = 0.f;
+      }
+  };
+
+  int since = 0;
+  const int64_t nchunks = (n + 31) / 32;
+  for (int64_t chunk = static_cast<int64_t>(blockIdx.x) * NW + warp; chunk < nchunks;
+       chunk += static_cast<int64_t>(gridDim.x) * NW) {
+    const int64_t base = chunk * 32;
+    const int nloc = static_cast<int>(n - base < 32 ? n - base : 32);
+    float ph_l = 0.f, pl_l = 0.f, h_l = 0.f;
+    if (lane < nloc) {
+      split_pair_fast(phi[base + lane], ph_l, pl_l);
+      h_l = p.H ? static_cast<float>(p.H[base + lane]) : 1.f;
+    }
+    for (int j0 = 0; j0 < nloc; j0 += SPW) {
+      const int j = j0 + grp;  // < 32: j0 is a multiple of SPW, grp < SPW
+      const float ph = __shfl_sync(0xffffffffu, ph_l, j);
+      const float pl = __shfl_sync(0xffffffffu, pl_l, j);
+      const float hw = __shfl_sync(0xffffffffu, h_l, j);
+      float x[E];
+      float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        x[e] = fmaf(-bh[e], ph, ch[e]) + fmaf(-bl[e], ph, fmaf(-bh[e], pl, cl[e]));
+        if (e & 1) m1 = fmaxf(m1, x[e]); else m0 = fmaxf(m0, x[e]);
+      }
+      float m = fmaxf(m0, m1);
+#pragma unroll
+      for (int o = LPS / 2; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int e = 0; e < E; e += 2) {
+        x[e] = ex2_approx(x[e] - m);
+        x[e + 1] = ex2_approx(x[e + 1] - m);
+        s0 += x[e];
+        s1 += x[e + 1];
+      }
+      float s = s0 + s1;
+#pragma unroll
+      for (int o = LPS / 2; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      float w = 0.f;
+      if (j < nloc) {
+        w = hw * rcp_approx(s);
+        if (p.logden != nullptr && lig == 0)
+          static_cast<double*>(p.logden)[base + j] = f32_to_f64_bits((m + __log2f(s)) * kLn2);
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[e] = fmaf(x[e], w, acc[e]);
+      if (++since >= kFactFlush) {
+        fold();
+        since = 0;
+      }
+    }
+  }
+  fold();
+
+  // ---- per-CTA row sums: the warps' partials in warp order ----
+  __syncthreads();
+  double* out = p.partials + static_cast<size_t>(blockIdx.x) * K;
+  for (int k = tid; k < K; k += NT) {
+    double t = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      const float2 c = rows[static_cast<size_t>(w) * Kp + k];
+      t += static_cast<double>(c.x) + static_cast<double>(c.y);
+    }
+    out[k] = t;
+  }
+}
+
+namespace {
+
+template <int LPS, int NK, int NT>
+void fact_run(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp, const LseParams& prm,
+              cudaStream_t st) {
+  static bool init = false;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (!init) {
+      // the device maximum once, so every K of this instantiation fits
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      cudaFuncSetAttribute(lse_fact_kernel<LPS, NK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      init = true;
+    }
+  }
+  lse_fact_kernel<LPS, NK, NT><<<pl.grid, NT, pl.smem, st>>>(a, b, phi, Kp, prm);
+}
+
+}  // namespace
+
+LsePlan lse_fact_plan(int64_t K, int64_t n) {
+  LsePlan pl{};
+  // lanes per sample: as few as give every lane at most 16 states (four
+  // float4 groups), so the per-sample shuffles, reciprocal and logden write
+  // are spread over as many entries as the registers allow; 32 lanes (and up
+  // to 32 states each) from K = 256
+  const int64_t q = round_up(K, 4) / 4;
+  int lps = 1;
+  while (lps < 32 && lps * 4 < q) lps <<= 1;
+  int nk = static_cast<int>(ceil_div(q, static_cast<int64_t>(lps)));
+  if (lps < 32 && nk == 3) nk = 4;
+  // four FP32 constants per state in registers: 512 threads (128 registers)
+  // up to 12 states per lane, 384 at 16 (512 spilled), 256 beyond
+  const int nt = nk <= 3 ? 512 : (nk == 4 ? 384 : 256);
+  const int64_t Kp = round_up(K, 4);
+  pl.variant = 3;
+  pl.threads = nt;
+  pl.J = nk;
+  pl.H = lps;
+  pl.C = 32;
+  pl.num_strips = static_cast<int>(ceil_div(n, 32));
+  pl.smem = static_cast<size_t>(Kp) * 16 + static_cast<size_t>(nt / 32) * Kp * 8;
+  pl.ok = K >= 1 && K <= 1024;
+  // every warp of every CTA gets at least one chunk where n allows
+  pl.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(pl.num_strips, nt / 32), num_sms())));
+  return pl;
+}
+
+mbar_status lse_fact_launch(const double* a, const double* b, const double* phi, const LsePlan& pl, LseParams prm,
+                            cudaStream_t st) {
+  if (!pl.ok) {
+    set_error("factorised lse pass: unsupported K=%d", prm.K);
+    return MBAR_EUNSUPPORTED;
+  }
+  prm.nparts = pl.grid;
+  prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
+  const int Kp = static_cast<int>(round_up(prm.K, 4));
+  const int lps = pl.H, nk = pl.J;
+#define BUMBAR_FACT_SMALL(L)                                          \
+  case L:                                                             \
+    if (nk == 1) fact_run<L, 1, 512>(pl, a, b, phi, Kp, prm, st);     \
+    else if (nk == 2) fact_run<L, 2, 512>(pl, a, b, phi, Kp, prm, st); \
+    else fact_run<L, 4, 384>(pl, a, b, phi, Kp, prm, st);             \
+    break;
+  if (lps < 32) {
+    switch (lps) {
+      BUMBAR_FACT_SMALL(1)
+      BUMBAR_FACT_SMALL(2)
+      BUMBAR_FACT_SMALL(4)
+      BUMBAR_FACT_SMALL(8)
+      BUMBAR_FACT_SMALL(16)
+      default: set_error("lse_fact_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+    }
+  } else {
+    switch (nk) {
+      case 1: fact_run<32, 1, 512>(pl, a, b, phi, Kp, prm, st); break;
+      case 2: fact_run<32, 2, 512>(pl, a, b, phi, Kp, prm, st); break;
+      case 3: fact_run<32, 3, 512>(pl, a, b, phi, Kp, prm, st); break;
+      case 4: fact_run<32, 4, 384>(pl, a, b, phi, Kp, prm, st); break;
+      case 5: fact_run<32, 5, 256>(pl, a, b, phi, Kp, prm, st); break;
+      case 6: fact_run<32, 6, 256>(pl, a, b, phi, Kp, prm, st); break;
+      case 7: fact_run<32, 7, 256>(pl, a, b, phi, Kp, prm, st); break;
+      case 8: fact_run<32, 8, 256>(pl, a, b, phi, Kp, prm, st); break;
+      default: set_error("lse_fact_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+    }
+  }
+#undef BUMBAR_FACT_SMALL
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return lse_epilogue_launch(prm, st);
+}
+
+}  // namespace bumbar

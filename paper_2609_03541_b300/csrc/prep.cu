@@ -46,30 +46,6 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   return __uint_as_float(sign | bits);
 }
 
-// Splits a binary64 x into hi = RN32(x) and lo ~ x - hi with integer
-// operations only: the residual is (dropped 29 fraction bits - the rounding
-// increment) x 2^(E - 1075), formed as an int -> float conversion and a
-// power-of-two scale. False when hi or the scale would leave the normal
-// binary32 range (the caller then uses FP64 arithmetic).
-__device__ __forceinline__ bool split_f64(double x, float& hi, float& lo) {
-  const unsigned long long d = static_cast<unsigned long long>(__double_as_longlong(x));
-  const unsigned int dh = static_cast<unsigned int>(d >> 32), dl = static_cast<unsigned int>(d);
-  const int E = static_cast<int>((dh >> 20) & 0x7FFu);
-  const int e = E - 1023 + 127;
-  const int s = E - 1075;  // weight of the last binary64 fraction bit
-  if (e <= 0 || e >= 254 || s < -126) return false;
-  const unsigned int sign = dh & 0x80000000u;
-  const unsigned int mant = ((dh & 0xFFFFFu) << 3) | (dl >> 29);
-  const unsigned int rest = dl & 0x1FFFFFFFu;
-  const unsigned int half = 0x10000000u;
-  const unsigned int up = (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
-  hi = __uint_as_float(sign | (((static_cast<unsigned int>(e) << 23) | mant) + up));
-  const int r = static_cast<int>(rest) - (up ? (1 << 29) : 0);
-  const float scale = __uint_as_float(static_cast<unsigned int>(s + 127) << 23);
-  lo = __uint_as_float(sign ^ __float_as_uint(__int2float_rn(r) * scale));
-  return true;
-}
-
 // Staging at creation, sample-major: block b takes the kStageCols samples
 // n0 = b * kStageCols .. n0 + kStageCols - 1 with all K rows into shared
 // memory (one read of u, 128-byte row pieces), takes each column's minimum

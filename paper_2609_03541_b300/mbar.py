@@ -137,6 +137,9 @@ _SIGNATURES = {
     "mbar_lse_pass": ([_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
                        _vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
     "mbar_lse_samples_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_size_t),
+    "mbar_lse_factorised_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_size_t),
+    "mbar_lse_pass_factorised": ([_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  ctypes.c_size_t, _vp], ctypes.c_int),
     "mbar_lse_pass_samples": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                _vp], ctypes.c_int),
 }
@@ -397,6 +400,26 @@ def lse_pass_samples(v_nk, K, f, log_N, Q, H=None, logden=None, scratch=None, st
     st = stream.cuda_stream if stream is not None else 0
     _check(lib().mbar_lse_pass_samples(
         ctypes.c_void_p(v_nk.data_ptr()), int(K), n,
+        ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(log_N.data_ptr()),
+        ctypes.c_void_p(H.data_ptr()) if H is not None else None,
+        ctypes.c_void_p(Q.data_ptr()),
+        ctypes.c_void_p(logden.data_ptr()) if logden is not None else None,
+        ctypes.c_void_p(scratch.data_ptr()), int(scratch.numel()), ctypes.c_void_p(st)))
+
+
+def lse_factorised_scratch_bytes(K: int, n: int) -> int:
+    return int(lib().mbar_lse_factorised_scratch_bytes(int(K), int(n)))
+
+
+def lse_pass_factorised(a, b, phi, f, log_N, Q, H=None, logden=None, scratch=None, stream=None):
+    """``mbar_lse_pass_factorised``: the fused LSE pass over u_kp = a_k + b_k
+    phi_p from float64 CUDA tensors ``a``, ``b`` (K) and ``phi`` (n);
+    ``logden`` float64 (n) or None. ``scratch``: uint8 tensor of
+    ``lse_factorised_scratch_bytes`` bytes, zero before its first use."""
+    K, n = int(a.numel()), int(phi.numel())
+    st = stream.cuda_stream if stream is not None else 0
+    _check(lib().mbar_lse_pass_factorised(
+        ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(phi.data_ptr()), K, n,
         ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(log_N.data_ptr()),
         ctypes.c_void_p(H.data_ptr()) if H is not None else None,
         ctypes.c_void_p(Q.data_ptr()),

@@ -367,6 +367,72 @@ def test_lse_pass_sample_major(K, N, counts):
     assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - ld_ref)) < 1e-4
 
 
+@pytest.mark.parametrize("K,N", [(1, 7), (3, 4099), (8, 3), (37, 5001), (64, 1000), (130, 2049), (500, 1333),
+                                 (1000, 777)])
+@pytest.mark.parametrize("regime", ["tempering", "small"])
+@pytest.mark.parametrize("counts", [False, True])
+def test_lse_pass_factorised(K, N, regime, counts):
+    """u_kp = a_k + b_k phi_p generated on the device (mbar_lse_pass_factorised)
+    against the oracle on the materialised u: every lane-group shape, ragged
+    chunks and counts. "tempering": b over 298..600 K, energies of a Gaussian
+    density of states (variance 2000 kT^2), so u and logden are ~1e3 kT;
+    "small": O(1) potentials. The exponent is FP32 at its own magnitude
+    X = max |logden|: the bound is a few FP32 ulps of X."""
+    import torch
+    g = np.random.default_rng(K * 31 + N)
+    state = np.arange(N) % K
+    Nk = np.bincount(state, minlength=K).astype(np.int64)
+    if regime == "tempering":
+        s2 = 2000.0
+        b = 1.0 / np.exp(np.linspace(0.0, np.log(600.0 / 298.0), K))
+        phi = -b[state] * s2 + np.sqrt(s2) * g.standard_normal(N)
+        a = 5.0 * g.standard_normal(K)
+        f = -(b**2) * s2 / 2 + a
+    else:
+        b = g.uniform(0.5, 1.5, size=K)
+        phi = 3.0 * g.standard_normal(N)
+        a = g.standard_normal(K)
+        f = 0.3 * g.standard_normal(K)
+    Hn = np.ones(N)
+    dev = torch.device("cuda")
+    H = None
+    if counts:
+        Hn = 1.0 + (np.arange(N) % 5)
+        H = torch.from_numpy(Hn.astype(np.int32)).to(dev)
+    u = O.factorised_u(a, b, phi)
+    ld_ref = O.log_denominator(u, f, Nk)
+    Q_ref = Nk * (O.mbar_weights(u, f, Nk) * Hn[None, :]).sum(axis=1)
+    td = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(dev)
+    lN = np.log(np.maximum(Nk, 0).astype(np.float64))
+    Q = torch.empty(K, dtype=torch.float64, device=dev)
+    logden = torch.empty(N, dtype=torch.float64, device=dev)
+    scratch = torch.zeros(M.lse_factorised_scratch_bytes(K, N), dtype=torch.uint8, device=dev)
+    for _ in range(2):   # the scratch is left zero for the next call
+        M.lse_pass_factorised(td(a), td(b), td(phi), td(f), td(lN), Q, H=H, logden=logden, scratch=scratch)
+    torch.cuda.synchronize()
+    X = float(np.max(np.abs(ld_ref)))
+    tol = 1e-6 + 8.0 * X * 2.0**-24
+    Qg = Q.cpu().numpy()
+    occupied = Nk > 0
+    assert np.max(np.abs(Qg[occupied] - Q_ref[occupied]) / Q_ref[occupied]) < tol
+    assert np.all(Qg[~occupied] == 0.0)
+    assert np.max(np.abs(logden.cpu().numpy() - ld_ref)) < tol
+
+
+def test_lse_pass_factorised_rejects_bad_arguments():
+    import torch
+    dev = torch.device("cuda")
+    K, N = 4, 10
+    z = lambda n: torch.zeros(n, dtype=torch.float64, device=dev)
+    Q = z(K)
+    small = torch.zeros(16, dtype=torch.uint8, device=dev)
+    with pytest.raises(M.MbarError):
+        M.lse_pass_factorised(z(K), z(K), z(N), z(K), z(K), Q, scratch=small)
+    big = torch.zeros(M.lse_factorised_scratch_bytes(K, N), dtype=torch.uint8, device=dev)
+    with pytest.raises(M.MbarError):
+        M.lse_pass_factorised(z(1025), z(1025), z(N), z(1025), z(1025), z(1025), scratch=big)
+
+
 @pytest.mark.parametrize("case", ["gaussian", "umbrella_h0", "harmonic_wide"])
 def test_algorithm1_trajectory_matches_oracle_fp64(case):
     """Every Eq. 3 check of the second loop (level size, s_n, s_next) and the

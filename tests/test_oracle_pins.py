@@ -326,6 +326,45 @@ def test_gaussian_overlap_analytic():
     assert np.all(np.abs(f - exact)[1:] < 5 * sig[1:] + 1e-3)
 
 
+def test_factorised_u_without_phi_dependence_is_closed_form():
+    """b = 0: every sample sees the same potentials a_k, so logden_p =
+    log sum_j N_j exp(f_j - a_j) for every p, and Q_i = N_i sum_p W_ip =
+    n N_i exp(f_i - a_i) / sum_j N_j exp(f_j - a_j)."""
+    g = np.random.default_rng(3)
+    K, n = 5, 11
+    a = 3.0 * g.normal(size=K)
+    f = g.normal(size=K)
+    Nk = g.integers(1, 9, size=K)
+    phi = 100.0 * g.normal(size=n)
+    u = O.factorised_u(a, np.zeros(K), phi)
+    ld = O.log_denominator(u, f, Nk)
+    exact = math.log(sum(int(Nk[j]) * math.exp(f[j] - a[j]) for j in range(K)))
+    assert np.max(np.abs(ld - exact)) < 1e-13
+    Q = Nk * O.mbar_weights(u, f, Nk).sum(axis=1)
+    Q_exact = n * Nk * np.exp(f - a) / math.exp(exact)
+    assert np.max(np.abs(Q / Q_exact - 1.0)) < 1e-13
+
+
+def test_factorised_u_gaussian_density_of_states():
+    """u_kp = b_k E_p with E from a Gaussian density of states of variance s2
+    (state b draws N(-b s2, s2)): f(b) = -b^2 s2 / 2 + const, the paper's
+    tempering setting. The MBAR solution on factorised_u(0, b, E) lies
+    within statistical error of it, and a per-state offset a_k moves f_k by
+    a_k exactly (u_kp + a_k has Boltzmann factor e^{-a_k} times the old)."""
+    s2 = 40.0
+    p = W.parallel_tempering(K=6, N_k=3000, sigma2=s2, seed=2, materialize=False)
+    b = p.meta["b"]
+    u = O.factorised_u(np.zeros_like(b), b, p.phi)
+    f = O.solve_mbar(u, p.N_k)
+    exact = -(b**2 - b[0] ** 2) * s2 / 2
+    sig = _sigma(u, f, p.N_k)
+    assert np.all(np.abs(f - exact)[1:] < 5 * sig[1:] + 1e-3)
+    assert np.max(sig) < 0.2
+    a = np.linspace(-3.0, 5.0, len(b))
+    f2 = O.solve_mbar(O.factorised_u(a, b, p.phi), p.N_k)
+    assert np.max(np.abs((f2 - f) - (a - a[0]))) < 1e-8
+
+
 def test_umbrella_quadrature():
     from scipy.integrate import quad
     p = W.umbrella(K=12, N_k=800, seed=2, grid_points=1 << 14)

@@ -70,3 +70,46 @@ def test_exact_when_the_difference_is_a_float():
     for m in [-1e4, -12345.678, 3.25, 1e-3]:
         for du in [0.0, 0.5, 1.25, 7.0, 1024.0]:
             assert shifted(m + du, m) == np.float32((m + du) - m)
+
+
+def test_split_is_round_to_nearest_pair():
+    """The same split on the per-sample coordinate of the factorised pass
+    (lse_fact.cu): hi = RN32(x) and lo = RN32(x - hi), checked against
+    numpy's conversions on energies of the tempering workload's range."""
+    g = np.random.default_rng(11)
+    xs = np.concatenate([-2000.0 + 45.0 * g.standard_normal(2000), g.uniform(-1e6, 1e6, 2000),
+                         g.uniform(-1e-3, 1e-3, 200), [1.0, -1.5, 3.0e5, 2.0**-100]])
+    for x in xs:
+        r = split(float(x))
+        if r is None:           # the kernel takes its FP64 route there
+            assert abs(x) < 2.0**-60
+            continue
+        hi, lo = r
+        assert hi == np.float32(x)
+        assert lo == np.float32(float(x) - float(hi))
+
+
+def widen(x: np.float32) -> float:
+    """binary32 -> binary64 by integer fields (f32_to_f64_bits in common.cuh)."""
+    u = struct.unpack("<I", struct.pack("<f", x))[0]
+    sign, e, m = u & 0x80000000, (u >> 23) & 0xFF, u & 0x7FFFFF
+    if e == 0:
+        if m:
+            return float(x)
+        hi = sign
+    elif e == 0xFF:
+        hi = sign | 0x7FF00000 | (m >> 3)
+    else:
+        hi = sign | ((e + 896) << 20) | (m >> 3)
+    bits = (hi << 32) | (m << 29)
+    return struct.unpack("<d", struct.pack("<Q", bits))[0]
+
+
+def test_widen_matches_the_conversion():
+    g = np.random.default_rng(12)
+    xs = np.concatenate([g.standard_normal(3000) * 10.0 ** g.integers(-30, 30, 3000),
+                         [0.0, -0.0, 1.0, -2.5, 3.4028235e38, -1.1754944e-38, np.inf, -np.inf]]).astype(np.float32)
+    for x in xs:
+        w = widen(x)
+        assert w == float(x) and np.signbit(w) == np.signbit(x)
+    assert np.isnan(widen(np.float32(np.nan)))
