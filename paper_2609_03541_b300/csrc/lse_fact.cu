@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       split_pair_fast(phi[base + lane], ph_l, pl_l);
       h_l = p.H ? static_cast<float>(p.H[base + lane]) : 1.f;
     }
+    float ld_mine = 0.f;  // logden of sample `lane` of the chunk, written once per chunk
     for (int j0 = 0; j0 < nloc; j0 += SPW) {
       const int j = j0 + grp;  // < 32: j0 is a multiple of SPW, grp < SPW
       const float ph = __shfl_sync(0xffffffffu, ph_l, j);
@@ -157,12 +158,12 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       float s = s0 + s1;
 #pragma unroll
       for (int o = LPS / 2; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      float w = 0.f;
-      if (j < nloc) {
-        w = hw * rcp_approx(s);
-        if (p.logden != nullptr && lig == 0)
-          static_cast<double*>(p.logden)[base + j] = f32_to_f64_bits((m + __log2f(s)) * kLn2);
-      }
+      const float w = j < nloc ? hw * rcp_approx(s) : 0.f;
+      // every lane of a group holds its sample's m and s: lane l takes the
+      // logden of sample l from the group that has it in this round
+      const float lv = (m + __log2f(s)) * kLn2;
+      const float lv_l = __shfl_sync(0xffffffffu, lv, ((lane - j0) & (SPW - 1)) * LPS);
+      if (lane >= j0 && lane < j0 + SPW) ld_mine = lv_l;
 #pragma unroll
       for (int e = 0; e < E; ++e) acc[e] = fmaf(x[e], w, acc[e]);
       if (++since >= kFactFlush) {
@@ -170,6 +171,9 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
         since = 0;
       }
     }
+    // one coalesced store of the chunk's logden (FP64 built with integer
+    // operations: a conversion per sample on the FP64 pipe stalled the warp)
+    if (p.logden != nullptr && lane < nloc) static_cast<double*>(p.logden)[base + lane] = f32_to_f64_bits(ld_mine);
   }
   fold();
 
