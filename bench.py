@@ -65,8 +65,11 @@ def make_problem(name: str, seed: int = 0, nk: int | None = None):
         cfg["N_k"] = nk
     if name == "alchemical":
         lam, u0, du, Nk = W.alchemical_factors(K=cfg["K"], N_k=cfg["N_k"], seed=seed)
+        # factorised form (mbar_create_factorised): a = 0, b = lambda, phi = du;
+        # the per-sample u0_n is dropped (a per-sample shift leaves f unchanged)
         return dict(kind=name, K=cfg["K"], N=int(Nk.sum()), N_k=Nk, phi=du,
-                    rows=lambda k0, k1: W.alchemical_rows(lam, u0, du, k0, k1))
+                    rows=lambda k0, k1: W.alchemical_rows(lam, u0, du, k0, k1),
+                    fact=(np.zeros(cfg["K"]), np.asarray(lam, dtype=np.float64), du))
     if name == "umbrella":
         p = W.umbrella(K=cfg["K"], N_k=cfg["N_k"], seed=seed)
     elif name == "pt":
@@ -74,7 +77,8 @@ def make_problem(name: str, seed: int = 0, nk: int | None = None):
     else:
         p = W.harmonic(K=cfg["K"], N_k=cfg["N_k"], seed=seed)
     u = p.u_kn
-    return dict(kind=name, K=p.K, N=p.N, N_k=p.N_k, phi=p.phi, rows=lambda k0, k1: u[k0:k1])
+    fact = (np.zeros(p.K), p.meta["b"], p.phi) if name == "pt" else None   # u_kn = b_k E_n
+    return dict(kind=name, K=p.K, N=p.N, N_k=p.N_k, phi=p.phi, rows=lambda k0, k1: u[k0:k1], fact=fact)
 
 
 def fill_pinned(prob, torch):
@@ -707,6 +711,33 @@ def main():
         e2e = {"value": whole_job_rate(world, args.steps, ms_e2e), "unit": "solves/s",
                "h2d_bytes_per_step": hbytes, "d2h_bytes_per_step": prob["K"] * 8}
 
+    # ---- end to end from the factorised form: 2K + N numbers cross the link ----
+    e2e_fact = None
+    if not args.no_e2e and prob.get("fact") is not None:
+        fa, fb, fp = (torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).pin_memory().numpy()
+                      for x in prob["fact"])
+
+        def fstep():
+            ctx = M.Context.factorised(fa, fb, fp, Nk, prec, opts=opts, stream=stream.cuda_stream)
+            ctx.solve()
+            f = ctx.free_energies()
+            ctx.close()
+            return f
+        f_fact = fstep()   # warm-up
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fstep()
+        e1.record(stream)
+        barrier()
+        ms_f = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+        e2e_fact = {"value": whole_job_rate(world, args.steps, ms_f), "unit": "solves/s",
+                    "h2d_bytes_per_step": (2 * prob["K"] + prob["N"]) * 8, "d2h_bytes_per_step": prob["K"] * 8,
+                    "api": "mbar_create_factorised (u_kn = a_k + b_k phi_n generated on the device)",
+                    "max_abs_df_vs_timed_solve_kT": float(np.max(np.abs(f_fact - f_last)))}
+
     # ---- accuracy of the timed solve against the FP64 GPU path (outside timing) ----
     accuracy = None
     if prec == M.MBAR_MIXED and rank == 0 and not args.no_accuracy:
@@ -775,7 +806,8 @@ def main():
         line = {"metric": metric, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == M.MBAR_MIXED else "f64", "data": "synthetic",
-                "config": config, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "config": config, "e2e": e2e, "e2e_factorised": e2e_fact, "gpu_launches": launches,
+                "roofline": roofline,
                 "latency": latency, "hessian": hess, "cpu_baseline": cpu, "clocks": clocks, "accuracy": accuracy,
                 "reweight": rew,
                 "report": rep.as_dict()}

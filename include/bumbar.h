@@ -121,6 +121,22 @@ BUMBAR_API mbar_status mbar_opts_default(mbar_opts* opts, int32_t precision);
 BUMBAR_API mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
                         int32_t u_on_device, const mbar_opts* opts, void* cuda_stream);
 
+/* Creates a context from factorised reduced potentials
+ *     u_kn = a_k + b_k phi_n
+ * (Sec. II: the paper's u = beta_k E_n is a = 0, b = beta, phi = E): only
+ * the 2 K + N numbers cross the host link; u is generated on the device,
+ * with the product and the sum each rounded to nearest in binary64, exactly
+ * as a host evaluating a + b * phi gets it, and then stored like mbar_create
+ * stores a given u. phi also becomes the bin coordinate (as by
+ * mbar_set_coordinate). a, b: FP64[K]; phi: FP64[N]; all three on the host
+ * (on_device = 0) or all in device memory (on_device = 1). N_k, opts,
+ * cuda_stream and the errors as for mbar_create; the call holds a
+ * temporary K x N FP64 buffer (ENOMEM if it cannot be allocated) and
+ * returns after the context's copy is complete. */
+BUMBAR_API mbar_status mbar_create_factorised(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k,
+                                              const double* a, const double* b, const double* phi,
+                                              int32_t on_device, const mbar_opts* opts, void* cuda_stream);
+
 /* Sets the 1-D bin coordinate phi_n (Sec. II bins the energies E_p; here any
  * per-sample coordinate). phi: N finite FP64 values, host or device.
  * Sorts the samples by phi once (stable LSD radix sort) and reorders the

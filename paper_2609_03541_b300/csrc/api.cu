@@ -1492,6 +1492,72 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   return MBAR_OK;
 }
 
+mbar_status mbar_create_factorised(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* a,
+                                   const double* b, const double* phi, int32_t on_device, const mbar_opts* opts,
+                                   void* cuda_stream) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
+  if (!out || !N_k || !a || !b || !phi) {
+    set_error("mbar_create_factorised: null pointer argument");
+    return MBAR_EINVAL;
+  }
+  *out = nullptr;
+  if (K < 1 || N < 1 || K > 1024 || N > 2000000000LL) {
+    set_error("mbar_create_factorised: bad sizes K=%lld N=%lld", (long long)K, (long long)N);
+    return K > 1024 || N > 2000000000LL ? MBAR_EUNSUPPORTED : MBAR_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  double* buf = nullptr;  // [a | b | phi] when given on the host, then u
+  double* u = nullptr;
+  const size_t in_bytes = static_cast<size_t>(2 * K + N) * sizeof(double);
+  const size_t u_bytes = static_cast<size_t>(K) * static_cast<size_t>(N) * sizeof(double);
+  auto release = [&]() {
+    if (u) cudaFreeAsync(u, st);
+    if (buf) cudaFreeAsync(buf, st);
+    cudaStreamSynchronize(st);
+  };
+  const double *ad = a, *bd = b, *pd = phi;
+  if (!on_device) {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&buf), in_bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("mbar_create_factorised: cannot allocate %zu bytes", in_bytes);
+      return MBAR_ENOMEM;
+    }
+    if (cudaMemcpyAsync(buf, a, K * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(buf + K, b, K * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(buf + 2 * K, phi, N * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      mbar_status e = cuda_status(cudaGetLastError(), "mbar_create_factorised: upload");
+      release();
+      return e;
+    }
+    ad = buf;
+    bd = buf + K;
+    pd = buf + 2 * K;
+  }
+  if (cudaMallocAsync(reinterpret_cast<void**>(&u), u_bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    set_error("mbar_create_factorised: cannot allocate %zu bytes for u", u_bytes);
+    return MBAR_ENOMEM;
+  }
+  mbar_status s = factorised_u(ad, bd, pd, K, N, u, st);
+  // mbar_create validates u (non-finite a, b or phi give EINVAL there),
+  // stages it on the context's stream after the work queued on `st`
+  if (s == MBAR_OK) s = mbar_create(out, K, N, N_k, u, 1, opts, cuda_stream);
+  if (s == MBAR_OK) {
+    // the context's copy is complete before u is released
+    if (cudaStreamSynchronize((*out)->st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "create");
+  }
+  if (s == MBAR_OK) s = mbar_set_coordinate(*out, pd, 1);
+  // the context's reads of phi are complete before the buffers are released
+  if (s == MBAR_OK && cudaStreamSynchronize((*out)->st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "create");
+  release();
+  if (s != MBAR_OK && *out) {
+    mbar_destroy(*out);
+    *out = nullptr;
+  }
+  return s;
+}
+
 mbar_status mbar_set_coordinate(mbar_ctx* c, const double* phi, int32_t phi_on_device) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);

@@ -103,6 +103,9 @@ mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, 
 mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream);
 // Factorised u_kp = a_k + b_k phi_p (lse_fact.cu): a, b device FP64[K],
 // phi device FP64[n]; logden (if set) device FP64[n].
+// u_kn = a_k + b_k phi_n into a K x N FP64 buffer (prep.cu)
+mbar_status factorised_u(const double* a, const double* b, const double* phi, int64_t K, int64_t N, double* u,
+                         cudaStream_t st);
 LsePlan lse_fact_plan(int64_t K, int64_t n);
 mbar_status lse_fact_launch(const double* a, const double* b, const double* phi, const LsePlan& pl, LseParams prm,
                             cudaStream_t st);

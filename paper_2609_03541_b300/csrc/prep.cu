@@ -483,4 +483,26 @@ mbar_status vec_add_gauge(const double* f, const double* d, double* out, int64_t
   return MBAR_OK;
 }
 
+// u_kn = a_k + b_k phi_n (factorised potentials, K x N row-major, pitch N),
+// the product and the sum each rounded to nearest in binary64 (no FMA), as
+// a host evaluating a + b * phi gets them.
+__global__ void factorised_u_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                    const double* __restrict__ phi, int64_t K, int64_t N, double* __restrict__ u) {
+  const int64_t k = blockIdx.y;
+  const double ak = a[k], bk = b[k];
+  double* row = u + k * N;
+  for (int64_t n = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; n < N;
+       n += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    row[n] = __dadd_rn(ak, __dmul_rn(bk, phi[n]));
+}
+
+mbar_status factorised_u(const double* a, const double* b, const double* phi, int64_t K, int64_t N, double* u,
+                         cudaStream_t st) {
+  const unsigned gx = static_cast<unsigned>(std::min<int64_t>(ceil_div(N, 256), 1024));
+  factorised_u_kernel<<<dim3(gx, static_cast<unsigned>(K)), 256, 0, st>>>(a, b, phi, K, N, u);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
 }  // namespace bumbar

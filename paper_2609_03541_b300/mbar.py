@@ -138,6 +138,8 @@ _SIGNATURES = {
                        _vp, _vp, ctypes.c_size_t, _vp], ctypes.c_int),
     "mbar_lse_samples_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_size_t),
     "mbar_lse_factorised_scratch_bytes": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_size_t),
+    "mbar_create_factorised": ([ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int64, _i64p, _vp, _vp, _vp,
+                                ctypes.c_int32, ctypes.POINTER(Opts), _vp], ctypes.c_int),
     "mbar_lse_pass_factorised": ([_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
                                   ctypes.c_size_t, _vp], ctypes.c_int),
     "mbar_lse_pass_samples": ([_vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
@@ -218,6 +220,43 @@ class Context:
                                  ctypes.byref(opts), st))
         self._keep = None
         self.K, self.N, self.precision = K, N, precision
+
+    @classmethod
+    def factorised(cls, a, b, phi, N_k, precision: int = MBAR_MIXED, opts: Opts | None = None, stream=None):
+        """``mbar_create_factorised``: u_kn = a_k + b_k phi_n generated on the
+        device from float64 ``a``, ``b`` (K) and ``phi`` (N), all numpy
+        arrays or all CUDA tensors; ``phi`` also becomes the bin coordinate."""
+        self = cls.__new__(cls)
+        self._h = ctypes.c_void_p()
+        Nk = np.ascontiguousarray(np.asarray(N_k, dtype=np.int64))
+        K = int(Nk.shape[0])
+        ptrs = [_device_ptr(x) for x in (a, b, phi)]
+        on_dev = ptrs[0][1]
+        if any(p[1] != on_dev for p in ptrs):
+            raise ValueError("a, b and phi must all be host arrays or all CUDA tensors")
+        if on_dev:
+            for x in (a, b, phi):
+                if x.dtype.__repr__() != "torch.float64" or not x.is_contiguous():
+                    raise ValueError("device a, b, phi must be contiguous float64 CUDA tensors")
+            keep = (a, b, phi)
+            vp = [p[0] for p in ptrs]
+            N = int(phi.numel())
+        else:
+            keep = tuple(_f64(x) for x in (a, b, phi))
+            vp = [ctypes.c_void_p(x.ctypes.data) for x in keep]
+            N = int(keep[2].shape[0])
+        if len(keep[0]) != K or len(keep[1]) != K:
+            raise ValueError("a and b need one entry per state")
+        if opts is None:
+            opts = default_opts(precision)
+        else:
+            opts.precision = precision
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else 0))
+        _check(lib().mbar_create_factorised(ctypes.byref(self._h), K, N, Nk.ctypes.data_as(_i64p), vp[0], vp[1],
+                                            vp[2], on_dev, ctypes.byref(opts), st))
+        self._keep = None
+        self.K, self.N, self.precision = K, N, precision
+        return self
 
     # -- binning ---------------------------------------------------------
     def set_coordinate(self, phi):

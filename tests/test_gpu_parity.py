@@ -433,6 +433,51 @@ def test_lse_pass_factorised_rejects_bad_arguments():
         M.lse_pass_factorised(z(1025), z(1025), z(N), z(1025), z(1025), z(1025), scratch=big)
 
 
+def _pt_factorised(K=6, N_k=3000, s2=40.0, seed=2):
+    p = W.parallel_tempering(K=K, N_k=N_k, sigma2=s2, seed=seed, materialize=False)
+    b = p.meta["b"]
+    a = np.linspace(-2.0, 3.0, K)
+    return a, b, p.phi, p.N_k
+
+
+@pytest.mark.parametrize("prec", [M.MBAR_FP64, M.MBAR_MIXED])
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_create_factorised_is_create_on_the_generated_u(prec, where):
+    """mbar_create_factorised generates u_kn = a_k + b_k phi_n with the
+    host's binary64 rounding and bins by phi: the solve is bit for bit the
+    one of mbar_create on the oracle's materialised u with phi set as the
+    coordinate, and both match the oracle's MBAR solution."""
+    import torch
+    a, b, phi, Nk = _pt_factorised()
+    if where == "device":
+        td = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+        c1 = M.Context.factorised(td(a), td(b), td(phi), Nk, prec)
+    else:
+        c1 = M.Context.factorised(a, b, phi, Nk, prec)
+    c1.solve()
+    f1 = c1.free_energies()
+    c1.close()
+    u = O.factorised_u(a, b, phi)
+    c2 = M.Context(u, Nk, prec)
+    c2.set_coordinate(phi)
+    c2.solve()
+    f2 = c2.free_energies()
+    c2.close()
+    assert np.array_equal(f1, f2)
+    f_ref = O.solve_mbar(u, Nk)
+    assert np.max(np.abs(f1 - f_ref)) < (1e-8 if prec == M.MBAR_FP64 else 1e-4)
+
+
+def test_create_factorised_rejects_bad_input():
+    a, b, phi, Nk = _pt_factorised(K=3, N_k=50)
+    with pytest.raises(M.MbarError):
+        M.Context.factorised(a, b, np.where(np.arange(len(phi)) == 7, np.nan, phi), Nk, M.MBAR_MIXED)
+    with pytest.raises(M.MbarError):
+        M.Context.factorised(a, b, phi, Nk + 1, M.MBAR_MIXED)
+    with pytest.raises(ValueError):
+        M.Context.factorised(a[:2], b, phi, Nk, M.MBAR_MIXED)
+
+
 @pytest.mark.parametrize("case", ["gaussian", "umbrella_h0", "harmonic_wide"])
 def test_algorithm1_trajectory_matches_oracle_fp64(case):
     """Every Eq. 3 check of the second loop (level size, s_n, s_next) and the
