@@ -782,13 +782,15 @@ def main():
     if n_l:
         achieved = by_l / (ms_l / 1e3) / 1e9
         # DRAM bytes per launch: the algorithmic bytes times the read+write
-        # ratio of one ncu capture of the same kernel (MIXED: K = 500,
-        # n = 4e5, 804.7 MB for 800.0 MB), FP64 kernels not captured
-        smaj = prec == M.MBAR_MIXED and (prob["K"] <= 48 or prob["K"] >= 256)
-        traffic = (by_l / n_l) * (804.7 / 800.0) if smaj else None
+        # ratio of one ncu capture of the same kernel instance (MIXED, 32
+        # lanes x 16 states per sample, 385 <= K <= 512: K = 500, n = 4e5,
+        # 804.7 MB for 800.0 MB); other instances and FP64 not captured
+        smaj = prec == M.MBAR_MIXED and prob["K"] <= 1024
+        same_instance = smaj and 385 <= prob["K"] <= 512
+        traffic = (by_l / n_l) * (804.7 / 800.0) if same_instance else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                    # the library's layout rule: sample-major for MIXED at K <= 48 or K >= 256
+                    # the library's layout rule: sample-major for every MIXED unbinned pass
                     "kernel": ("lse_smaj_kernel (unbinned passes, sample-major FP32)" if smaj
                                else "lse_regs_kernel (unbinned passes, row-major FP32)" if prec == M.MBAR_MIXED
                                else "lse_pass_kernel<double> (unbinned passes)"), "launches": n_l,

@@ -275,15 +275,19 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
 
 namespace {
 
-// lanes per sample: the smallest power of two whose lanes cover Kp / 4
-// float4 chunks, at most 32; float4 chunks per lane beyond that
+// lanes per sample: as few as give every lane at most four float4 chunks
+// (16 states), so the per-sample shuffles, reciprocal and logden write are
+// spread over as many entries as the registers allow; 32 lanes (and more
+// chunks per lane) from K = 256
 void smaj_shape(int64_t K, int* lps, int* nk, int* nt) {
   const int64_t q = round_up(K, 4) / 4;
   int l = 1;
-  while (l < 32 && l < q) l <<= 1;
+  while (l < 32 && l * 4 < q) l <<= 1;
+  int c = static_cast<int>(ceil_div(q, static_cast<int64_t>(l)));
+  if (l < 32 && c == 3) c = 4;
   *lps = l;
-  *nk = static_cast<int>(ceil_div(q, l));
-  *nt = *nk <= 4 ? 512 : 256;  // 15 or 7 compute warps + the producer warp
+  *nk = c;
+  *nt = c <= 4 ? 512 : 256;  // 15 or 7 compute warps + the producer warp
 }
 
 template <int LPS, int NK, int NT>
@@ -352,11 +356,13 @@ LsePlan lse_smaj_plan(int64_t K, int64_t n) {
 
 bool lse_smaj_supported(int64_t K) { return K >= 1 && K <= 1024; }
 
-// Where the sample-major pass beats the row-major FP32 kernels (measured on
-// B300 at 1e9 entries: K = 16, 32: 1.2 vs 3.4 / 1.7 ms; K = 64, 128: 1.3 vs
-// 1.1 ms; K = 256: equal; K = 500: 0.90 vs 0.98 ms; K = 1000: 0.92 vs
-// 1.8 ms).
-bool lse_smaj_preferred(int64_t K) { return K <= 48 || K >= 256; }
+// Where the sample-major pass beats the row-major FP32 kernels: everywhere
+// it runs (measured on B300 at 1e9 entries, sample-major vs row-major: K =
+// 16: 0.64 vs 3.03 ms; K = 50: 0.84 vs 1.29; K = 64: 0.69 vs 1.02; K = 128:
+// 0.71 vs 1.06; K = 200: 0.86 vs 0.95; K = 500: 0.73 vs 0.87; K = 1000:
+// 0.79 vs 1.82). Before lanes per sample were cut to give each lane up to
+// 16 states, K = 64..128 measured 1.3-1.5 ms and the row-major kernel won.
+bool lse_smaj_preferred(int64_t K) { return lse_smaj_supported(K); }
 
 mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st) {
   if (!pl.ok) {
@@ -367,15 +373,22 @@ mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, 
   prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
   const int Kp = static_cast<int>(round_up(prm.K, 4));
   const int lps = pl.H, nk = pl.J;
+#define BUMBAR_SMAJ_SMALL(L)                                 \
+  case L:                                                    \
+    if (nk == 1) smaj_run<L, 1, 512>(pl, vst, Kp, prm, st);    \
+    else if (nk == 2) smaj_run<L, 2, 512>(pl, vst, Kp, prm, st); \
+    else smaj_run<L, 4, 512>(pl, vst, Kp, prm, st);            \
+    break;
   if (lps < 32) {
     switch (lps) {
-      case 1: smaj_run<1, 1, 512>(pl, vst, Kp, prm, st); break;
-      case 2: smaj_run<2, 1, 512>(pl, vst, Kp, prm, st); break;
-      case 4: smaj_run<4, 1, 512>(pl, vst, Kp, prm, st); break;
-      case 8: smaj_run<8, 1, 512>(pl, vst, Kp, prm, st); break;
-      case 16: smaj_run<16, 1, 512>(pl, vst, Kp, prm, st); break;
+      BUMBAR_SMAJ_SMALL(1)
+      BUMBAR_SMAJ_SMALL(2)
+      BUMBAR_SMAJ_SMALL(4)
+      BUMBAR_SMAJ_SMALL(8)
+      BUMBAR_SMAJ_SMALL(16)
       default: set_error("lse_smaj_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
     }
+#undef BUMBAR_SMAJ_SMALL
   } else {
     switch (nk) {
       case 1: smaj_run<32, 1, 512>(pl, vst, Kp, prm, st); break;
