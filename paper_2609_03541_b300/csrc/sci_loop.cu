@@ -432,8 +432,15 @@ struct LoopPlan {
 
 LoopPlan loop_plan(int64_t K) {
   LoopPlan pl{};
-  smaj_shape_of(K, &pl.lps, &pl.nk, &pl.nt);
-  if (pl.nk >= 4) pl.nt = 256;  // the register budget of 512 threads is too small for 16 entries here
+  // lanes per sample: as few as give every lane at most 16 states (the
+  // per-sample shuffles and reciprocals spread over more entries; the rule
+  // of the sample-major pass, which it made 2x faster at K = 16..128)
+  const int64_t q = stage_pitch(K) / 4;
+  pl.lps = 1;
+  while (pl.lps < 32 && pl.lps * 4 < q) pl.lps <<= 1;
+  pl.nk = static_cast<int>(ceil_div(q, static_cast<int64_t>(pl.lps)));
+  if (pl.lps < 32 && pl.nk == 3) pl.nk = 4;
+  pl.nt = pl.nk >= 4 ? 256 : 512;  // the register budget of 512 threads is too small for 16 entries here
   const int64_t Kp = stage_pitch(K);
   const int nwc = pl.nt / 32 - 1;
   int64_t S = std::max<int64_t>(16 * 1024 / (Kp * 4), 1);
@@ -464,11 +471,17 @@ mbar_status sci_loop_launch(const float* vT, const SciLoopParams& prm, cudaStrea
   const int Kp = static_cast<int>(stage_pitch(prm.K));
   if (pl.lps < 32) {
     switch (pl.lps) {
-      case 1: return loop_run<1, 1, 512>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);
-      case 2: return loop_run<2, 1, 512>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);
-      case 4: return loop_run<4, 1, 512>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);
-      case 8: return loop_run<8, 1, 512>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);
-      case 16: return loop_run<16, 1, 512>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);
+#define BUMBAR_LOOP_SMALL(L)                                                                   \
+  case L:                                                                                      \
+    if (pl.nk == 1) return loop_run<L, 1, 512>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);     \
+    if (pl.nk == 2) return loop_run<L, 2, 512>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);     \
+    return loop_run<L, 4, 256>(vT, Kp, pl.S, pl.stages, pl.smem, prm, st);
+      BUMBAR_LOOP_SMALL(1)
+      BUMBAR_LOOP_SMALL(2)
+      BUMBAR_LOOP_SMALL(4)
+      BUMBAR_LOOP_SMALL(8)
+      BUMBAR_LOOP_SMALL(16)
+#undef BUMBAR_LOOP_SMALL
       default: break;
     }
   } else {
