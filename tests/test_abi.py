@@ -118,3 +118,32 @@ def test_server_rejects_bad_configuration_without_a_gpu(L):
     cfg = M.server_config(workers=2, hbm_budget_bytes=0)
     with pytest.raises(M.MbarError):
         M.Server(cfg)
+
+
+@pytest.mark.parametrize("K,N,code", [(0, 4, "MBAR_EINVAL"), (2, 0, "MBAR_EINVAL"), (2000, 4, "MBAR_EUNSUPPORTED")])
+def test_create_factorised_rejects_bad_sizes_before_any_device_work(L, K, N, code):
+    a = np.zeros(max(K, 1))
+    phi = np.zeros(max(N, 1))
+    Nk = np.ones(max(K, 1), dtype=np.int64)
+    h = ctypes.c_void_p()
+    p = lambda x: ctypes.c_void_p(x.ctypes.data)
+    st = L.mbar_create_factorised(ctypes.byref(h), K, N, Nk.ctypes.data_as(M._i64p), p(a), p(a), p(phi), 0, None,
+                                  None)
+    assert M.STATUS[st] == code
+    assert not h.value
+    st = L.mbar_create_factorised(ctypes.byref(h), 2, 4, Nk.ctypes.data_as(M._i64p), None, p(a), p(phi), 0, None,
+                                  None)
+    assert M.STATUS[st] == "MBAR_EINVAL"
+
+
+def test_factorised_pass_rejects_bad_arguments_before_any_device_work(L):
+    assert L.mbar_lse_factorised_scratch_bytes(0, 10) == 0
+    assert L.mbar_lse_factorised_scratch_bytes(2000, 10) == 0
+    x = np.zeros(16)
+    p = ctypes.c_void_p(x.ctypes.data)
+    st = L.mbar_lse_pass_factorised(None, p, p, 2, 4, p, p, None, p, None, p, 4096, None)
+    assert M.STATUS[st] == "MBAR_EINVAL"
+    st = L.mbar_lse_pass_factorised(p, p, p, 2000, 4, p, p, None, p, None, p, 4096, None)
+    assert M.STATUS[st] == "MBAR_EUNSUPPORTED"
+    st = L.mbar_lse_pass_factorised(p, p, p, 0, 4, p, p, None, p, None, p, 4096, None)
+    assert M.STATUS[st] == "MBAR_EINVAL"
