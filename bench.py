@@ -782,12 +782,13 @@ def main():
     if n_l:
         achieved = by_l / (ms_l / 1e3) / 1e9
         # DRAM bytes per launch: the algorithmic bytes times the read+write
-        # ratio of one ncu capture of the same kernel instance (MIXED, 32
-        # lanes x 16 states per sample, 385 <= K <= 512: K = 500, n = 4e5,
-        # 804.7 MB for 800.0 MB); other instances and FP64 not captured
+        # ratio of one ncu capture of the same kernel instance and padding
+        # (MIXED, K = 500: 32 lanes x 16 states, n = 4e5, 804.7 MB for 800.0 MB;
+        # K = 50: 4 lanes x 16 states, Kp = 52, n = 4e6, 849.0 MB for 800.0 MB);
+        # other K and FP64 not captured
         smaj = prec == M.MBAR_MIXED and prob["K"] <= 1024
-        same_instance = smaj and 385 <= prob["K"] <= 512
-        traffic = (by_l / n_l) * (804.7 / 800.0) if same_instance else None
+        ratio = {500: 804.7 / 800.0, 50: 849.0 / 800.0}.get(prob["K"]) if smaj else None
+        traffic = (by_l / n_l) * ratio if ratio else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                     # the library's layout rule: sample-major for every MIXED unbinned pass
