@@ -365,6 +365,24 @@ def test_factorised_u_gaussian_density_of_states():
     assert np.max(np.abs((f2 - f) - (a - a[0]))) < 1e-8
 
 
+def test_binned_factorised_u_is_factorised_u_at_the_bin_means():
+    """Reading c4 (bin representative = mean of the members) on factorised
+    potentials: the mean of a_k + b_k phi_n over a bin is a_k + b_k times the
+    mean phi of the bin, so a binned level of factorised u is itself
+    factorised, (mean phi_b, H_b), up to FP64 rounding."""
+    p = W.parallel_tempering(K=5, N_k=400, sigma2=40.0, seed=4, materialize=False)
+    b = p.meta["b"]
+    a = np.linspace(-1.0, 2.0, len(b))
+    u = O.factorised_u(a, b, p.phi)
+    for n_bins in (7, 60, 500):
+        w = O.width_for_bins(p.phi, n_bins)
+        hist = O.histogram(p.phi, w)
+        ub = O.binned_u(u, hist)
+        phib = np.array([p.phi[m].mean() for m in hist.members])
+        assert np.max(np.abs(ub - O.factorised_u(a, b, phib))) < 1e-12 * np.max(np.abs(u))
+        assert int(hist.H.sum()) == len(p.phi)
+
+
 def test_umbrella_quadrature():
     from scipy.integrate import quad
     p = W.umbrella(K=12, N_k=800, seed=2, grid_points=1 << 14)
