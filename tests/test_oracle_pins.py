@@ -282,6 +282,60 @@ def test_algorithm1_reaches_the_mbar_solution():
     assert set(ns) <= {100, 1000, 10000}
 
 
+def _trace_fixture(golden_dir):
+    with open(os.path.join(golden_dir, "algorithm1_trace.json")) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("which", ["trace", "trace_noise_floor"])
+def test_algorithm1_trace_matches_the_derivation(golden_dir, which):
+    """The oracle's Algorithm 1 takes every decision of the 50-digit
+    derivation (tests/golden/derive_algorithm1_trace.py: Eqs. 1-3 in their
+    printed form): the same first-loop length under s < eps, the same Eq. 3
+    outcome in every round (the next round's n), the same end by the break
+    rule 2 inc n > sum N_i, and the same step widths s, s_n, s_next. The
+    second case adds the noise-floor rule of the finite-precision reading."""
+    spec = _trace_fixture(golden_dir)
+    P = spec["params"]
+    floor = spec["noise_floor"] if which == "trace_noise_floor" else 0.0
+    opts = O.BUOptions(n0=P["n0"], eps=P["eps"], inc=P["inc"], n_intermediate=P["n_intermediate"],
+                       noise_floor=floor)
+    tr = []
+    O.bu_mbar(np.asarray(spec["u"]), np.asarray(spec["N_k"]), phi=np.asarray(spec["phi"]), opts=opts, trace=tr)
+    rows = [t for t in tr if t[0] in ("phase1", "phase2")]
+    exp = spec[which]
+    assert [(r[0], r[1]) for r in rows] == [(f"phase{e['phase']}", e["n"]) for e in exp]
+    for r, e in zip(rows, exp):
+        if e["phase"] == 1:
+            assert (r[2] == math.inf) if e["s"] == "inf" else r[2] == pytest.approx(e["s"], rel=1e-7)
+        else:
+            assert r[2] == pytest.approx(e["s_n"], rel=1e-7)
+            assert r[3] == pytest.approx(e["s_next"], rel=1e-7)
+
+
+def test_algorithm1_trace_fixture_tells_the_rules_apart(golden_dir):
+    """The derived trace would change under the plausible slips in Eq. 3 and
+    the break rule: it has rounds that raise n and rounds that do not (a
+    flipped inequality), a round that raises n only with the factor 2
+    (inc s_n < 2 s_next but not inc s_n < s_next), a last raise where
+    2 inc n exceeds sum N_i but inc n does not, a first loop that stops on
+    s < eps, and, with the noise floor, a first-loop stop and a raise that
+    come from the floor alone."""
+    spec = _trace_fixture(golden_dir)
+    inc, N = spec["params"]["inc"], sum(spec["N_k"])
+    p2 = [e for e in spec["trace"] if e["phase"] == 2]
+    assert any(e["raise_n"] for e in p2) and any(not e["raise_n"] for e in p2)
+    assert all(e["raise_n"] == (inc * e["s_n"] < 2 * e["s_next"]) for e in p2)
+    assert any(inc * e["s_n"] < 2 * e["s_next"] and not inc * e["s_n"] < e["s_next"] for e in p2)
+    n_last = p2[-1]["n"] * inc
+    assert p2[-1]["raise_n"] and 2 * inc * n_last > N and not inc * n_last > N
+    assert spec["trace"][[e["phase"] for e in spec["trace"]].index(2) - 1]["stop"]
+    nf = spec["trace_noise_floor"]
+    assert any(e["phase"] == 1 and e["by_noise_floor"] for e in nf)
+    assert any(e["phase"] == 2 and e["by_noise_floor"] for e in nf)
+    assert min(e["eq3_margin"] for e in p2) > 1e-3      # no decision within rounding of its threshold
+
+
 def test_algorithm1_width_schedule():
     p = W.umbrella(K=8, N_k=400, seed=4, grid_points=1 << 12)
     o = O.BUOptions(h0=0.1)
