@@ -359,9 +359,10 @@ BUMBAR_API mbar_status mbar_lse_pass_factorised(const double* a, const double* b
  * which every GPU that loads the library holds until the process exits.
  * The call allocates nothing (no cudaMalloc/cudaFree, no allocating library
  * routine); it zeroes the array's counter on `stream` before launching.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make this first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress; it allocates nothing); the first call on a
+ *     device also loads the library's module there, so make it before any
+ *     stream capture.
  *   - All calls share the one array, which keeps the last call's contents:
  *     calls that overlap on the GPU (concurrent streams, several host
  *     threads) race and give wrong results; order them.

@@ -5,6 +5,7 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -24,7 +25,7 @@ def nvcc() -> str:
 def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    objs = []
+    objs, cmds = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
         if not os.path.exists(path):
@@ -33,11 +34,20 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
         deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
         deps.append(os.path.join(ROOT, "include", "bumbar.h"))
         if not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps):
-            cmd = [nvcc(), *ARCH, *FLAGS, *(extra or []), "-c", path, "-o", obj]
+            cmds.append([nvcc(), *ARCH, *FLAGS, *(extra or []), "-c", path, "-o", obj])
+        objs.append(obj)
+    # translation units compile independently: one nvcc per core
+    workers = max(1, min(len(cmds), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as pool:
+        for cmd in cmds:
             if verbose:
                 print(" ".join(cmd), flush=True)
-            subprocess.run(cmd, check=True)
-        objs.append(obj)
+        for r in pool.map(lambda c: subprocess.run(c, capture_output=True, text=True), cmds):
+            if verbose or r.returncode != 0:
+                sys.stdout.write(r.stdout)
+                sys.stderr.write(r.stderr)
+            if r.returncode != 0:
+                raise subprocess.CalledProcessError(r.returncode, r.args)
     cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
     if verbose:
         print(" ".join(cmd), flush=True)

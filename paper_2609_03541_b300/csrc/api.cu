@@ -517,11 +517,12 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
   int rejects = 0;
   double prev_step = INFINITY;
   // the rounding floor of a gradient evaluation: below it max|g| says
-  // nothing about whether a step helped (FP32 data and exponentials give
-  // ~1e-6..1e-5 of N_k; FP64 ~1e-13)
+  // nothing about whether a step helped (FP32 data and exponentials, with
+  // each sample's largest weight split into an exact count and its small
+  // remainder, give ~1e-9 of N_k; FP64 ~1e-13)
   double nk_max = 0.0;
   for (int64_t k = 0; k < K; ++k) nk_max = std::max(nk_max, c->Nk_h[k]);
-  const double g_floor = (c->dtype == 4 ? 1e-5 : 1e-13) * nk_max;
+  const double g_floor = (c->dtype == 4 ? 1e-8 : 1e-13) * nk_max;
   for (int it = 0; it < c->opts.max_newton; ++it) {
     if (gmax == 0.0 || K == 1) {
       st = MBAR_OK;
@@ -574,7 +575,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
         }
         // Newton contracts quadratically; accepted steps that stop shrinking
         // while already small are moving on the rounding noise of the gradient
-        if (step > 0.5 * prev_step && step < 1e3 * c->opts.f_tol) {
+        if (step > 0.5 * prev_step && step < 1e2 * c->opts.f_tol) {
           st = MBAR_OK;
           break;
         }
@@ -586,7 +587,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
       rep->newton_fallbacks++;
       trace_row(c, 4, it, step, gmax);
       rejects++;
-      if (rejects >= 3 && step < 1e3 * c->opts.f_tol) {  // at the noise floor of the gradient
+      if (rejects >= 3 && step < 1e2 * c->opts.f_tol) {  // at the noise floor of the gradient
         st = MBAR_OK;
         break;
       }
@@ -2051,7 +2052,7 @@ mbar_status mbar_destroy(mbar_ctx* c) {
 
 size_t mbar_lse_scratch_bytes(int64_t K, int64_t n, int32_t dtype_bytes) {
   if (K < 1 || K > 1024 || n < 1 || (dtype_bytes != 4 && dtype_bytes != 8)) return 0;
-  return lse_scratch_bytes(K, n, dtype_bytes) + 256;
+  return lse_scratch_bytes(K, n, dtype_bytes);
 }
 
 mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
@@ -2102,7 +2103,7 @@ mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t K, int64_t
 
 size_t mbar_lse_samples_scratch_bytes(int64_t K, int64_t n) {
   if (K < 1 || K > 1024 || n < 1) return 0;
-  return lse_scratch_for_grid(K, lse_smaj_plan(K, n).grid) + 256;
+  return lse_scratch_for_grid(K, lse_smaj_plan(K, n).grid);
 }
 
 mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const double* f, const double* log_N,
@@ -2147,7 +2148,7 @@ mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const
 
 size_t mbar_lse_factorised_scratch_bytes(int64_t K, int64_t n) {
   if (K < 1 || K > 1024 || n < 1) return 0;
-  return lse_scratch_for_grid(K, lse_fact_plan(K, n).grid) + 256;
+  return lse_scratch_for_grid(K, lse_fact_plan(K, n).grid);
 }
 
 mbar_status mbar_lse_pass_factorised(const double* a, const double* b, const double* phi, int64_t K, int64_t n,

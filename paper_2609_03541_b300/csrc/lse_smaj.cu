@@ -34,7 +34,18 @@
 //     (deterministic, FP64) and written as the CTA's row of the partial
 //     sums, which lse_epilogue_kernel reduces;
 //   * 1 / sum by rcp.approx (1 ulp; the IEEE division measured 2.3 % of the
-//     pass at K = 500, 10 % at K = 16).
+//     pass at K = 500, 10 % at K = 16);
+//   * the state(s) attaining a sample's maximum exponent contribute exactly 1
+//     to its sum, the others r = sum_{k != k*} 2^(x_k - m). With a single
+//     maximum its weight 1 / (1 + r) is accumulated as the exact count 1
+//     (an integer counter per state in shared memory) plus the small
+//     remainder -r / (1 + r): as a plain FP32 term close to 1 its deficit r
+//     is rounded away, by the FP32 sum 1 + r itself and by partial sums of
+//     ~64 terms close to 1, which biases Q_k (and the gradient Q_k - N_k) by
+//     up to ~N_k 6e-8. On poorly overlapping states the Newton solution
+//     then moves by that bias over the smallest eigenvalue of the Hessian
+//     (1e-3..1e-2 kT for four umbrella windows 1.0 apart in an FP32 emulation
+//     of the pass; 3.5e-6 kT with the split). Tied maxima get 1 / sum each.
 #include <cmath>
 #include <mutex>
 
@@ -84,6 +95,8 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
   uint64_t* full = reinterpret_cast<uint64_t*>(rows + static_cast<size_t>(NWC) * Kp);
   uint64_t* empty = full + stages;
   int* abort_flag = reinterpret_cast<int*>(empty + stages);
+  // [Kp] per-state counts of samples whose single maximum is that state
+  unsigned* cnt = reinterpret_cast<unsigned*>(abort_flag + 4);
 
   const int64_t nchunks = (n + S - 1) / S;
   const int64_t first = blockIdx.x, stride = gridDim.x;
@@ -113,6 +126,7 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
     a2[Kp + k] = lo;
   }
   for (int i = Kp + tid; i < NWC * Kp; i += NT) rows[i] = make_float2(0.f, 0.f);
+  for (int k = tid; k < Kp; k += NT) cnt[k] = 0u;
   __syncthreads();
 
   const int lig = lane % LPS;  // lane in group
@@ -230,25 +244,65 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
         m0 = fmaxf(m0, m1);
 #pragma unroll
         for (int o = LPS / 2; o >= 1; o >>= 1) m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        // r = the sum of 2^(x - m) over the entries below the maximum; the
+        // maximal entries (each exactly 1) are zeroed and marked in `top`
         float s0 = 0.f, s1 = 0.f;
+        unsigned top = 0u;
 #pragma unroll
         for (int e = 0; e < E; e += 2) {
-          x0[e] = ex2_approx(x0[e] - m0);
-          x0[e + 1] = ex2_approx(x0[e + 1] - m0);
+          const float d0 = x0[e] - m0, d1 = x0[e + 1] - m0;
+          const bool z0 = d0 == 0.f, z1 = d1 == 0.f;
+          x0[e] = z0 ? 0.f : ex2_approx(d0);
+          x0[e + 1] = z1 ? 0.f : ex2_approx(d1);
+          if (z0) top |= 1u << e;
+          if (z1) top |= 2u << e;
           s0 += x0[e];
           s1 += x0[e + 1];
         }
         s0 += s1;
+        int nt = __popc(top);
 #pragma unroll
-        for (int o = LPS / 2; o >= 1; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        float w0 = 0.f;
+        for (int o = LPS / 2; o >= 1; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          nt += __shfl_xor_sync(0xffffffffu, nt, o);
+        }
+        const float sum = static_cast<float>(nt) + s0;
+        float w0 = 0.f, h0 = 0.f;
         if (v0) {
           const int64_t gn = n0 + j0;
-          w0 = (p.H ? static_cast<float>(p.H[gn]) : 1.f) * rcp_approx(s0);
-          if (p.logden != nullptr && lig == 0) static_cast<float*>(p.logden)[gn] = (m0 + __log2f(s0)) * kLn2;
+          h0 = p.H ? static_cast<float>(p.H[gn]) : 1.f;
+          w0 = h0 * rcp_approx(sum);
+          if (p.logden != nullptr && lig == 0) static_cast<float*>(p.logden)[gn] = (m0 + __log2f(sum)) * kLn2;
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) acc[e] = fmaf(x0[e], w0, acc[e]);
+        if (top != 0u && w0 != 0.f) {
+          // the maximal entries of this lane: a single maximum adds
+          // -r / sum to its row and H to its count, tied maxima 1 / sum each
+          const float add = nt == 1 ? -s0 * w0 : w0;
+          if (nt == 1) {
+            const int e = __ffs(top) - 1;
+            atomicAdd(&cnt[4 * (lig + LPS * (e >> 2)) + (e & 3)], static_cast<unsigned>(h0));
+          }
+          do {
+            const int e = __ffs(top) - 1;
+            top &= top - 1u;
+            if constexpr (LPS == 32) {
+              // one sample per warp: the row entry of state k is only ever
+              // updated by this lane (here and in fold), so it takes the term
+              // directly (TwoSum into the unevaluated pair)
+              const int k = 4 * (lig + 32 * (e >> 2)) + (e & 3);
+              const float2 c = myrow[k];
+              const float sum2 = c.x + add, bv = sum2 - c.x;
+              const float err = (c.x - (sum2 - bv)) + (add - bv);
+              myrow[k] = make_float2(sum2, c.y + err);
+            } else {
+#pragma unroll
+              for (int q = 0; q < E; ++q)
+                if (q == e) acc[q] += add;
+            }
+          } while (top != 0u);
+        }
         if (++slots >= kSmFlush) {
           fold();
           slots = 0;
@@ -269,7 +323,7 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
       const float2 c = rows[static_cast<size_t>(w) * Kp + k];
       t += static_cast<double>(c.x) + static_cast<double>(c.y);
     }
-    out[k] = t;
+    out[k] = t + static_cast<double>(cnt[k]);
   }
 }
 
@@ -337,7 +391,7 @@ LsePlan lse_smaj_plan(int64_t K, int64_t n) {
   pl.J = nk;
   pl.H = lps;
   pl.num_strips = static_cast<int>(ceil_div(n, S));
-  pl.smem = stages * sb + part + 2 * stages * 8 + 16 + 1024;
+  pl.smem = stages * sb + part + 2 * stages * 8 + 16 + Kp * 4 + 1024;
   static int optin = -1;
   {
     std::lock_guard<std::recursive_mutex> lock(init_mutex());

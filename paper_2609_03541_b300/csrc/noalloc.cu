@@ -1,8 +1,6 @@
 // A variant of mbar_lse_pass for callers that must not allocate device
 // memory: its per-CTA partial sums and completion counter live in a fixed
 // array compiled into this library instead of a caller-provided buffer.
-#include <mutex>
-
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -15,28 +13,15 @@ namespace {
 constexpr size_t kStaticScratchBytes = size_t(1) << 20;
 static __device__ __align__(256) unsigned char g_lse_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_lse_scratch on the current device, looked up once per
-// device (the host-side name g_lse_scratch is only a stand-in, not a device
-// address).
+// Device address of g_lse_scratch on the current device (the host-side name
+// g_lse_scratch is only a stand-in, not a device address). Looked up on
+// every call: the lookup allocates nothing, and a cached address would go
+// stale if the device's primary context were reset and the module reloaded.
 mbar_status static_scratch(void** out) {
-  int dev = 0;
-  BUMBAR_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("mbar_lse_pass_static: device ordinal %d out of range", dev);
-    return MBAR_EUNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_lse_scratch);
-    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_lse_scratch)");
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_lse_scratch);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_lse_scratch)");
+  *out = p;
   return MBAR_OK;
 }
 

@@ -56,18 +56,6 @@ __device__ __forceinline__ void smaj_pair(const float* c0, const float* c1, int 
   }
 }
 
-// lanes per sample: the smallest power of two whose lanes cover Kp / 4
-// float4 chunks, at most 32; float4 chunks per lane beyond that; threads
-// (15 or 7 compute warps + one producer warp)
-inline void smaj_shape_of(int64_t K, int* lps, int* nk, int* nt) {
-  const int64_t q = (K + 3) / 4;
-  int l = 1;
-  while (l < 32 && l < q) l <<= 1;
-  *lps = l;
-  *nk = static_cast<int>((q + l - 1) / l);
-  *nt = *nk <= 4 ? 512 : 256;
-}
-
 __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),

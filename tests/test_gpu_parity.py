@@ -15,6 +15,7 @@ import pytest
 import oracle as O
 from paper_2609_03541_b300 import mbar as M
 from paper_2609_03541_b300 import workloads as W
+from shapes import LANE_SHAPE_CASES
 
 pytestmark = pytest.mark.gpu
 
@@ -330,8 +331,7 @@ def test_lse_pass_stateless(dtype):
     assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - O.log_denominator(u, f, Nk))) < tol * 100
 
 
-@pytest.mark.parametrize("K,N", [(1, 7), (3, 4099), (8, 3), (20, 3001), (37, 5001), (64, 1000), (100, 1999),
-                                 (130, 2049), (500, 1333), (1000, 777)])
+@pytest.mark.parametrize("K,N", LANE_SHAPE_CASES)
 @pytest.mark.parametrize("counts", [False, True])
 def test_lse_pass_sample_major(K, N, counts):
     """The sample-major FP32 pass (the layout of MIXED's unbinned passes):
@@ -367,8 +367,7 @@ def test_lse_pass_sample_major(K, N, counts):
     assert np.max(np.abs(logden.cpu().numpy().astype(np.float64) - ld_ref)) < 1e-4
 
 
-@pytest.mark.parametrize("K,N", [(1, 7), (3, 4099), (8, 3), (20, 3001), (37, 5001), (64, 1000), (100, 1999),
-                                 (130, 2049), (500, 1333), (1000, 777)])
+@pytest.mark.parametrize("K,N", LANE_SHAPE_CASES)
 @pytest.mark.parametrize("regime", ["tempering", "small"])
 @pytest.mark.parametrize("counts", [False, True])
 def test_lse_pass_factorised(K, N, regime, counts):
@@ -666,20 +665,20 @@ def test_mixed_first_loop_follows_the_oracle(case):
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_mixed_second_loop_ends_at_its_rounding_floor(seed):
+def test_mixed_second_loop_stall_then_newton_reaches_the_oracle(seed):
     """Four umbrella windows 1.0 apart barely overlap (the reduced Hessian's
     smallest eigenvalue is 0.02-0.2): SCI contracts so slowly that the FP64
     second loop runs 1e5-2e5 steps. MIXED raises n once its steps stop
     shrinking (they sit on the FP32 rounding of the evaluation) instead of
-    running to max_sci, and ends within its rounding over that eigenvalue of
-    the oracle: error ~ (FP32 rounding of Q ~ 6e-8 N) / lambda_min."""
+    running to max_sci; the unbinned Newton phase, whose gradient keeps each
+    sample's largest weight as an exact count plus its small remainder, then
+    ends within the mixed tolerance of the oracle."""
     p = W.umbrella(K=4, N_k=4299, seed=seed, grid_points=1 << 13)
     f_ref = O.solve_mbar(p.u_kn, p.N_k)
-    lam = np.linalg.eigvalsh(O.mbar_hessian(p.u_kn, f_ref, p.N_k)[1:, 1:]).min()
     ctx = M.Context(p.u_kn, p.N_k, M.MBAR_MIXED)
     ctx.set_coordinate(p.phi)
     rep = ctx.solve().as_dict()
     f = ctx.free_energies()
     ctx.close()
     assert rep["iters_second_loop"] < 20000, rep
-    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL["mixed"] + 6e-8 * p.N / lam, (rep, lam)
+    assert np.max(np.abs(f - f_ref)) < SOLVE_TOL["mixed"], rep
