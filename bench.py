@@ -648,7 +648,7 @@ def main():
         f = ctx.free_energies()
         traces.append(ctx.trace())
         if timing and acc is not None:
-            for kind in (0, 1, 2):
+            for kind in (0, 1, 2, 3):
                 n, ms, by = ctx.timing(kind)
                 a = acc.setdefault(kind, [0, 0.0, 0.0])
                 a[0] += n
@@ -777,7 +777,11 @@ def main():
 
     # ---- roofline of the dominant kernel (unbinned fused LSE pass) ----
     peaks, peaks_src = load_peaks()
-    n_l, ms_l, by_l = acc.get(0, [0, 0.0, 0.0])
+    # every unbinned pass: the exact-split passes that drive Newton steps
+    # (kind 0) and the plain ones that only confirm a step below f_tol (3)
+    n_x, ms_x, by_x = acc.get(0, [0, 0.0, 0.0])
+    n_c, ms_c, by_c = acc.get(3, [0, 0.0, 0.0])
+    n_l, ms_l, by_l = n_x + n_c, ms_x + ms_c, by_x + by_c
     roofline = None
     if n_l:
         achieved = by_l / (ms_l / 1e3) / 1e9
@@ -796,7 +800,12 @@ def main():
                                else "lse_regs_kernel (unbinned passes, row-major FP32)" if prec == M.MBAR_MIXED
                                else "lse_pass_kernel<double> (unbinned passes)"), "launches": n_l,
                     "avg_launch_ms": ms_l / n_l, "bytes_per_launch": by_l / n_l,
-                    "peak_source": f"{peaks_src} hbm_gbs"}
+                    "peak_source": f"{peaks_src} hbm_gbs",
+                    "variants": {
+                        "exact_split": {"launches": n_x, "avg_launch_ms": (ms_x / n_x) if n_x else None,
+                                        "frac": (by_x / (ms_x / 1e3) / 1e9 / peaks["hbm_gbs"]) if n_x else None},
+                        "confirm_plain": {"launches": n_c, "avg_launch_ms": (ms_c / n_c) if n_c else None,
+                                          "frac": (by_c / (ms_c / 1e3) / 1e9 / peaks["hbm_gbs"]) if n_c else None}}}
     n_h, ms_h, by_h = acc.get(1, [0, 0.0, 0.0])
     hess = {"launches": n_h, "avg_ms": (ms_h / n_h) if n_h else None}
 

@@ -244,7 +244,10 @@ BUMBAR_API const char* mbar_last_error(void);
  * stream (for profiling; adds two event records per timed launch).
  * mbar_set_timing(ctx, 1) clears earlier records and starts recording,
  * 0 stops. mbar_get_timing sums the records of one kind:
- *   0 = unbinned fused LSE passes, 1 = Hessian, 2 = FP64 Newton solve;
+ *   0 = unbinned fused LSE passes, 1 = Hessian, 2 = FP64 Newton solve,
+ *   3 = unbinned passes that only confirm a Newton step below f_tol (FP32
+ *       data: plain FP32 sums instead of the exact split of each sample's
+ *       largest weight that kind 0 uses);
  * launches, total_ms (device time) and bytes (K x n x element size of the
  * data each launch streams; K x K x 8 for the solve) are all nullable. */
 BUMBAR_API mbar_status mbar_set_timing(mbar_ctx* ctx, int32_t enable);

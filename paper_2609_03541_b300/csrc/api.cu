@@ -72,6 +72,10 @@ struct mbar_ctx {
   void* vst = nullptr;
   float* logden_orig = nullptr;  // MIXED: logden of those passes, original order
   bool smaj = false;             // unbinned passes on the sample-major copy
+  // the next unbinned pass only confirms a Newton step already below f_tol:
+  // the plain FP32 sums suffice (every other unbinned pass splits each
+  // sample's largest weight into an exact count and its remainder)
+  bool confirm_only = false;
   int64_t ld = 0;
   double* cshift = nullptr;  // mixed: per-column shift (current order)
   int32_t* perm = nullptr;   // current column -> original sample
@@ -224,18 +228,20 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   p.skip_if_done = skip_if_done;
   p.skip_if_underflow = mode == kLseModeSci ? 1 : 0;
   const bool timed = !L.binned;
-  if (timed) time_mark(c, true, 0, static_cast<double>(c->K) * L.n * c->dtype);
+  const int tkind = (c->confirm_only && c->smaj && c->vst) ? 3 : 0;
+  if (timed) time_mark(c, true, tkind, static_cast<double>(c->K) * L.n * c->dtype);
   mbar_status s = MBAR_OK;
   if (!L.binned && c->smaj && c->vst) {
     // unbinned MIXED pass over the sample-major copy (original sample order);
     // logden comes back to the store's column order through perm
     p.logden = logden_out ? c->logden_orig : nullptr;
+    p.exact_max = c->confirm_only ? 0 : 1;
     s = lse_smaj_launch(static_cast<const float*>(c->vst), lse_smaj_plan(c->K, L.n), p, c->st);
     if (s == MBAR_OK && logden_out) s = gather_columns(c->logden_orig, logden_out, 4, 1, L.n, L.n, c->perm, c->st);
   } else {
     s = lse_launch(L.tmap, pl, p, c->dtype, c->st);
   }
-  if (timed) time_mark(c, false, 0, 0);
+  if (timed) time_mark(c, false, tkind, 0);
   return s;
 }
 
@@ -552,7 +558,11 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
     bool accepted = false;
     if (info == 0 && std::isfinite(step)) {
       s = vec_add_gauge(c->f, c->delta, c->ft, K, c->st);
+      // a step below f_tol is accepted and ends the phase whatever the
+      // gradient at its end: that evaluation only confirms it
+      c->confirm_only = step < c->opts.f_tol;
       if (s == MBAR_OK) s = sci_step_exact(c, L, c->ft, c->fts, c->gt, c->s2, c->logden);
+      c->confirm_only = false;
       if (s == MBAR_OK) s = d2h(c, gh.data(), c->gt, K);
       if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
       if (s != MBAR_OK && s != MBAR_ENOTCONV) {
@@ -2143,6 +2153,7 @@ mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const
   p.Q = Q;
   p.logden = logden;
   p.mode = kLseModePass;
+  p.exact_max = 1;
   return lse_smaj_launch(v_nk, lse_smaj_plan(K, n), p, static_cast<cudaStream_t>(stream));
 }
 

@@ -123,6 +123,28 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Two FP32 values in one 64-bit register for the f32x2 instructions of
+// sm_100-family GPUs: one issue slot does the add or FMA of both halves,
+// each rounded exactly as the scalar instruction would round it.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // Byte offset of 16-byte chunk `chunk` of 128-byte row `row` inside a tile
 // written by TMA with CU_TENSOR_MAP_SWIZZLE_128B (tile base 1024-aligned):
 // chunk index is XORed with row % 8.

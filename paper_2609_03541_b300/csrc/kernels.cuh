@@ -46,6 +46,8 @@ struct LseParams {
   double noise;      // > 0: set ctrl->done when max|f_out - f| < noise
   int skip_if_done;  // return at once if ctrl->done
   int skip_if_underflow;  // return at once if ctrl->underflow (SCI steps after an underflowed one)
+  int exact_max;          // sample-major FP32 pass: split each sample's largest weight into an exact
+                          // count and its remainder (the gradient's bias on poorly overlapping states)
 };
 
 // The guard every LSE pass kernel and its epilogue apply first.

@@ -38,7 +38,8 @@
 //   * the state(s) attaining a sample's maximum exponent contribute exactly 1
 //     to its sum, the others r = sum_{k != k*} 2^(x_k - m). With a single
 //     maximum its weight 1 / (1 + r) is accumulated as the exact count 1
-//     (an integer counter per state in shared memory) plus the small
+//     (into the warp's unevaluated row pair with 32 lanes per sample, else
+//     into a per-warp integer row in shared memory) plus the small
 //     remainder -r / (1 + r): as a plain FP32 term close to 1 its deficit r
 //     is rounded away, by the FP32 sum 1 + r itself and by partial sums of
 //     ~64 terms close to 1, which biases Q_k (and the gradient Q_k - N_k) by
@@ -74,8 +75,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }  // namespace
 
 // LPS lanes per sample, NK float4 chunks per lane, NT threads (warp 0 is
-// the producer, the other NT / 32 - 1 warps compute).
-template <int LPS, int NK, int NT>
+// the producer, the other NT / 32 - 1 warps compute). EXACT: each sample's
+// largest weight is split into its exact count and remainder (below); the
+// plain variant adds every weight as an FP32 term (~30 % fewer instructions).
+template <int LPS, int NK, int NT, bool EXACT>
 __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict__ vst, int Kp, int S, int stages,
                                                          LseParams p) {
   constexpr int SPW = 32 / LPS;  // samples per warp at once
@@ -95,7 +98,10 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
   uint64_t* full = reinterpret_cast<uint64_t*>(rows + static_cast<size_t>(NWC) * Kp);
   uint64_t* empty = full + stages;
   int* abort_flag = reinterpret_cast<int*>(empty + stages);
-  // [Kp] per-state counts of samples whose single maximum is that state
+  // below 32 lanes per sample: [NWC][Kp] per-warp counts of the samples
+  // whose single maximum is state k (a warp's lane groups may share k, so
+  // these take shared-memory atomics, private to the warp); with 32 lanes
+  // the counts go into the warps' rows directly
   unsigned* cnt = reinterpret_cast<unsigned*>(abort_flag + 4);
 
   const int64_t nchunks = (n + S - 1) / S;
@@ -126,7 +132,8 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
     a2[Kp + k] = lo;
   }
   for (int i = Kp + tid; i < NWC * Kp; i += NT) rows[i] = make_float2(0.f, 0.f);
-  for (int k = tid; k < Kp; k += NT) cnt[k] = 0u;
+  if constexpr (LPS < 32)
+    for (int i = tid; i < NWC * Kp; i += NT) cnt[i] = 0u;
   __syncthreads();
 
   const int lig = lane % LPS;  // lane in group
@@ -163,24 +170,27 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
   } else {
     // ---- compute warps ----
     const int cw = warp - 1;
-    // this lane's entries: k = 4 * (lig + LPS * i) + t
-    float ahi[E], alo[E];
+    constexpr int E2 = E / 2;
+    // this lane's entries: k = 4 * (lig + LPS * i) + t, held as packed pairs
+    // (entries 2j, 2j + 1) for the f32x2 instructions
+    unsigned long long ahp[E2], alp[E2];
 #pragma unroll
     for (int i = 0; i < NK; ++i)
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < 4; t += 2) {
         const int k = 4 * (lig + LPS * i) + t;
-        ahi[4 * i + t] = k < Kp ? a2[k] : -INFINITY;
-        alo[4 * i + t] = k < Kp ? a2[Kp + k] : 0.f;
+        ahp[(4 * i + t) / 2] = pk2(k < Kp ? a2[k] : -INFINITY, k + 1 < Kp ? a2[k + 1] : -INFINITY);
+        alp[(4 * i + t) / 2] = pk2(k < Kp ? a2[Kp + k] : 0.f, k + 1 < Kp ? a2[Kp + k + 1] : 0.f);
       }
     asm volatile("bar.sync 1, %0;" ::"n"(NWC * 32) : "memory");
     if (cw == 0) {
       for (int k = lane; k < Kp; k += 32) rows[k] = make_float2(0.f, 0.f);
       __syncwarp();
     }
-    float acc[E];
+    const unsigned long long nl2e = pk2(-kLog2e, -kLog2e), nl2elo = pk2(-kLog2eLo, -kLog2eLo);
+    unsigned long long accp[E2];
 #pragma unroll
-    for (int e = 0; e < E; ++e) acc[e] = 0.f;
+    for (int j = 0; j < E2; ++j) accp[j] = 0ull;
     int slots = 0;
     float2* myrow = rows + static_cast<size_t>(cw) * Kp;
     auto fold = [&]() {
@@ -189,7 +199,9 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const int e = 4 * i + t;
-          float v = acc[e];
+          float lo, hi;
+          upk2(accp[e / 2], lo, hi);
+          float v = (e & 1) ? hi : lo;
 #pragma unroll
           for (int o = LPS; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
           const int k = 4 * (lig + LPS * i) + t;
@@ -201,8 +213,9 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
             const float err = (c.x - (sum - bv)) + (v - bv);
             myrow[k] = make_float2(sum, c.y + err);
           }
-          acc[e] = 0.f;
         }
+#pragma unroll
+      for (int j = 0; j < E2; ++j) accp[j] = 0ull;
     };
     for (int it = 0; it < count; ++it) {
       const int s = it % stages;
@@ -226,47 +239,68 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
         const int j0 = sl * SPW + grp;
         const bool v0 = j0 < ns;
         const float* c0 = reinterpret_cast<const float*>(stage + static_cast<size_t>(v0 ? j0 : 0) * Kp * 4);
-        float x0[E];
+        // x = a log2(e) - v log2(e) from the FP32 pairs (a_hi, a_lo) and
+        // (kLog2e, kLog2eLo), two entries per f32x2 instruction
+        unsigned long long xp[E2];
         float m0 = -INFINITY, m1 = -INFINITY;
 #pragma unroll
         for (int i = 0; i < NK; ++i) {
           const int k4 = 4 * (lig + LPS * i);
           float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
           if (k4 < Kp) a = *reinterpret_cast<const float4*>(c0 + k4);
-          const float va[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const int e = 4 * i + t;
-            x0[e] = fmaf(-va[t], kLog2e, ahi[e]) + fmaf(-va[t], kLog2eLo, alo[e]);
-            if (t & 1) m1 = fmaxf(m1, x0[e]); else m0 = fmaxf(m0, x0[e]);
-          }
+          const unsigned long long v01 = pk2(a.x, a.y), v23 = pk2(a.z, a.w);
+          xp[2 * i] = add2(fma2(v01, nl2e, ahp[2 * i]), fma2(v01, nl2elo, alp[2 * i]));
+          xp[2 * i + 1] = add2(fma2(v23, nl2e, ahp[2 * i + 1]), fma2(v23, nl2elo, alp[2 * i + 1]));
+          float p0, p1, q0, q1;
+          upk2(xp[2 * i], p0, p1);
+          upk2(xp[2 * i + 1], q0, q1);
+          m0 = fmaxf(m0, fmaxf(p0, q0));
+          m1 = fmaxf(m1, fmaxf(p1, q1));
         }
         m0 = fmaxf(m0, m1);
 #pragma unroll
         for (int o = LPS / 2; o >= 1; o >>= 1) m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        // r = the sum of 2^(x - m) over the entries below the maximum; the
-        // maximal entries (each exactly 1) are zeroed and marked in `top`
-        float s0 = 0.f, s1 = 0.f;
+        const unsigned long long nm = pk2(-m0, -m0);
+        unsigned long long sp = 0ull;   // (sum over even entries, sum over odd entries)
         unsigned top = 0u;
+        int nt = 0;
+        if constexpr (EXACT) {
+          // r = the sum of 2^(x - m) over the entries below the maximum; the
+          // maximal entries (each exactly 1) are zeroed and marked in `top`
 #pragma unroll
-        for (int e = 0; e < E; e += 2) {
-          const float d0 = x0[e] - m0, d1 = x0[e + 1] - m0;
-          const bool z0 = d0 == 0.f, z1 = d1 == 0.f;
-          x0[e] = z0 ? 0.f : ex2_approx(d0);
-          x0[e + 1] = z1 ? 0.f : ex2_approx(d1);
-          if (z0) top |= 1u << e;
-          if (z1) top |= 2u << e;
-          s0 += x0[e];
-          s1 += x0[e + 1];
+          for (int j = 0; j < E2; ++j) {
+            float d0, d1;
+            upk2(add2(xp[j], nm), d0, d1);
+            const bool z0 = d0 == 0.f, z1 = d1 == 0.f;
+            xp[j] = pk2(z0 ? 0.f : ex2_approx(d0), z1 ? 0.f : ex2_approx(d1));
+            if (z0) top |= 1u << (2 * j);
+            if (z1) top |= 2u << (2 * j);
+            sp = add2(sp, xp[j]);
+          }
+          // the group's number of maximal entries: its lanes holding one,
+          // counted exactly when some lane holds two or lanes tie
+          const unsigned gm = LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u) << (grp * LPS);
+          nt = __popc(__ballot_sync(0xffffffffu, top != 0u) & gm);
+          if (__any_sync(0xffffffffu, (top & (top - 1u)) != 0u || nt > 1)) {
+            nt = __popc(top);
+#pragma unroll
+            for (int o = LPS / 2; o >= 1; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < E2; ++j) {
+            float d0, d1;
+            upk2(add2(xp[j], nm), d0, d1);
+            xp[j] = pk2(ex2_approx(d0), ex2_approx(d1));
+            sp = add2(sp, xp[j]);
+          }
         }
+        float s0, s1;
+        upk2(sp, s0, s1);
         s0 += s1;
-        int nt = __popc(top);
 #pragma unroll
-        for (int o = LPS / 2; o >= 1; o >>= 1) {
-          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-          nt += __shfl_xor_sync(0xffffffffu, nt, o);
-        }
-        const float sum = static_cast<float>(nt) + s0;
+        for (int o = LPS / 2; o >= 1; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        const float sum = EXACT ? static_cast<float>(nt) + s0 : s0;
         float w0 = 0.f, h0 = 0.f;
         if (v0) {
           const int64_t gn = n0 + j0;
@@ -274,32 +308,41 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
           w0 = h0 * rcp_approx(sum);
           if (p.logden != nullptr && lig == 0) static_cast<float*>(p.logden)[gn] = (m0 + __log2f(sum)) * kLn2;
         }
+        const unsigned long long wp = pk2(w0, w0);
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc[e] = fmaf(x0[e], w0, acc[e]);
-        if (top != 0u && w0 != 0.f) {
+        for (int j = 0; j < E2; ++j) accp[j] = fma2(xp[j], wp, accp[j]);
+        if (EXACT && top != 0u && w0 != 0.f) {
           // the maximal entries of this lane: a single maximum adds
           // -r / sum to its row and H to its count, tied maxima 1 / sum each
           const float add = nt == 1 ? -s0 * w0 : w0;
-          if (nt == 1) {
-            const int e = __ffs(top) - 1;
-            atomicAdd(&cnt[4 * (lig + LPS * (e >> 2)) + (e & 3)], static_cast<unsigned>(h0));
-          }
           do {
             const int e = __ffs(top) - 1;
             top &= top - 1u;
+            const int k = 4 * (lig + LPS * (e >> 2)) + (e & 3);
             if constexpr (LPS == 32) {
               // one sample per warp: the row entry of state k is only ever
-              // updated by this lane (here and in fold), so it takes the term
-              // directly (TwoSum into the unevaluated pair)
-              const int k = 4 * (lig + 32 * (e >> 2)) + (e & 3);
-              const float2 c = myrow[k];
+              // updated by this lane (here and in fold), so the count and
+              // the remainder go into the unevaluated pair directly (TwoSum)
+              float2 c = myrow[k];
+              if (nt == 1) {
+                const float sum1 = c.x + h0, b1 = sum1 - c.x;
+                c.y += (c.x - (sum1 - b1)) + (h0 - b1);
+                c.x = sum1;
+              }
               const float sum2 = c.x + add, bv = sum2 - c.x;
-              const float err = (c.x - (sum2 - bv)) + (add - bv);
-              myrow[k] = make_float2(sum2, c.y + err);
+              c.y += (c.x - (sum2 - bv)) + (add - bv);
+              c.x = sum2;
+              myrow[k] = c;
             } else {
+              if (nt == 1) atomicAdd(&cnt[cw * Kp + k], static_cast<unsigned>(h0));
 #pragma unroll
-              for (int q = 0; q < E; ++q)
-                if (q == e) acc[q] += add;
+              for (int q = 0; q < E2; ++q)
+                if (q == (e >> 1)) {
+                  float lo, hi;
+                  upk2(accp[q], lo, hi);
+                  if (e & 1) hi += add; else lo += add;
+                  accp[q] = pk2(lo, hi);
+                }
             }
           } while (top != 0u);
         }
@@ -322,8 +365,9 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
     for (int w = 0; w < NWC; ++w) {
       const float2 c = rows[static_cast<size_t>(w) * Kp + k];
       t += static_cast<double>(c.x) + static_cast<double>(c.y);
+      if constexpr (LPS < 32) t += static_cast<double>(cnt[static_cast<size_t>(w) * Kp + k]);
     }
-    out[k] = t + static_cast<double>(cnt[k]);
+    out[k] = t;
   }
 }
 
@@ -344,14 +388,8 @@ void smaj_shape(int64_t K, int* lps, int* nk, int* nt) {
   *nt = c <= 4 ? 512 : 256;  // 15 or 7 compute warps + the producer warp
 }
 
-template <int LPS, int NK, int NT>
-void smaj_attr(size_t smem) {
-  cudaFuncSetAttribute(lse_smaj_kernel<LPS, NK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(smem));
-}
-
-template <int LPS, int NK, int NT>
-void smaj_run(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm, cudaStream_t st) {
+template <int LPS, int NK, int NT, bool EXACT>
+void smaj_run_one(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm, cudaStream_t st) {
   static bool init = false;
   {
     std::lock_guard<std::recursive_mutex> lock(init_mutex());
@@ -359,11 +397,17 @@ void smaj_run(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm,
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      smaj_attr<LPS, NK, NT>(static_cast<size_t>(optin));
+      cudaFuncSetAttribute(lse_smaj_kernel<LPS, NK, NT, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       init = true;
     }
   }
-  lse_smaj_kernel<LPS, NK, NT><<<pl.grid, NT, pl.smem, st>>>(vst, Kp, pl.C, pl.stages, prm);
+  lse_smaj_kernel<LPS, NK, NT, EXACT><<<pl.grid, NT, pl.smem, st>>>(vst, Kp, pl.C, pl.stages, prm);
+}
+
+template <int LPS, int NK, int NT>
+void smaj_run(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm, cudaStream_t st) {
+  if (prm.exact_max) smaj_run_one<LPS, NK, NT, true>(pl, vst, Kp, prm, st);
+  else smaj_run_one<LPS, NK, NT, false>(pl, vst, Kp, prm, st);
 }
 
 }  // namespace
@@ -391,7 +435,8 @@ LsePlan lse_smaj_plan(int64_t K, int64_t n) {
   pl.J = nk;
   pl.H = lps;
   pl.num_strips = static_cast<int>(ceil_div(n, S));
-  pl.smem = stages * sb + part + 2 * stages * 8 + 16 + Kp * 4 + 1024;
+  const size_t counts = lps < 32 ? static_cast<size_t>(nt / 32 - 1) * Kp * 4 : 0;
+  pl.smem = stages * sb + part + 2 * stages * 8 + 16 + counts + 1024;
   static int optin = -1;
   {
     std::lock_guard<std::recursive_mutex> lock(init_mutex());
@@ -427,34 +472,32 @@ mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, 
   prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
   const int Kp = static_cast<int>(round_up(prm.K, 4));
   const int lps = pl.H, nk = pl.J;
-#define BUMBAR_SMAJ_SMALL(L)                                 \
-  case L:                                                    \
-    if (nk == 1) smaj_run<L, 1, 512>(pl, vst, Kp, prm, st);    \
-    else if (nk == 2) smaj_run<L, 2, 512>(pl, vst, Kp, prm, st); \
-    else smaj_run<L, 4, 512>(pl, vst, Kp, prm, st);            \
-    break;
-  if (lps < 32) {
-    switch (lps) {
-      BUMBAR_SMAJ_SMALL(1)
-      BUMBAR_SMAJ_SMALL(2)
-      BUMBAR_SMAJ_SMALL(4)
-      BUMBAR_SMAJ_SMALL(8)
-      BUMBAR_SMAJ_SMALL(16)
-      default: set_error("lse_smaj_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
-    }
-#undef BUMBAR_SMAJ_SMALL
-  } else {
+  // the instances the shape rule reaches: one lane per sample with 1, 2 or
+  // 4 chunks; 2..16 lanes with 4 chunks; 32 lanes with 3..8 chunks
+  bool ok = true;
+  if (lps == 1 && nk == 1) smaj_run<1, 1, 512>(pl, vst, Kp, prm, st);
+  else if (lps == 1 && nk == 2) smaj_run<1, 2, 512>(pl, vst, Kp, prm, st);
+  else if (lps == 1 && nk == 4) smaj_run<1, 4, 512>(pl, vst, Kp, prm, st);
+  else if (lps == 2 && nk == 4) smaj_run<2, 4, 512>(pl, vst, Kp, prm, st);
+  else if (lps == 4 && nk == 4) smaj_run<4, 4, 512>(pl, vst, Kp, prm, st);
+  else if (lps == 8 && nk == 4) smaj_run<8, 4, 512>(pl, vst, Kp, prm, st);
+  else if (lps == 16 && nk == 4) smaj_run<16, 4, 512>(pl, vst, Kp, prm, st);
+  else if (lps == 32) {
     switch (nk) {
-      case 1: smaj_run<32, 1, 512>(pl, vst, Kp, prm, st); break;
-      case 2: smaj_run<32, 2, 512>(pl, vst, Kp, prm, st); break;
       case 3: smaj_run<32, 3, 512>(pl, vst, Kp, prm, st); break;
       case 4: smaj_run<32, 4, 512>(pl, vst, Kp, prm, st); break;
       case 5: smaj_run<32, 5, 256>(pl, vst, Kp, prm, st); break;
       case 6: smaj_run<32, 6, 256>(pl, vst, Kp, prm, st); break;
       case 7: smaj_run<32, 7, 256>(pl, vst, Kp, prm, st); break;
       case 8: smaj_run<32, 8, 256>(pl, vst, Kp, prm, st); break;
-      default: set_error("lse_smaj_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+      default: ok = false;
     }
+  } else {
+    ok = false;
+  }
+  if (!ok) {
+    set_error("lse_smaj_launch: unsupported shape (%d lanes, %d chunks)", lps, nk);
+    return MBAR_EUNSUPPORTED;
   }
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());

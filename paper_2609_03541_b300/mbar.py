@@ -337,7 +337,8 @@ class Context:
 
     def timing(self, kind: int):
         """(launches, total device ms, streamed bytes) of one launch kind:
-        0 unbinned LSE pass, 1 Hessian, 2 Newton solve."""
+        0 unbinned LSE pass, 1 Hessian, 2 Newton solve, 3 unbinned pass that
+        only confirms a Newton step below f_tol."""
         n = ctypes.c_int64()
         ms = ctypes.c_double()
         by = ctypes.c_double()
