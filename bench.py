@@ -156,40 +156,108 @@ class ClockSampler:
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(name: str, target_seconds: float = 20.0):
-    """Time the CPU oracle's Algorithm 1 + Newton solve on a bounded sample
-    of the workload (all K states, a reduced number of samples per state)
-    and scale to full-size solves/s by the entry count."""
-    import oracle as O
-    from paper_2609_03541_b300 import workloads as W
-    cfg = WORKLOADS[name]
-    K = cfg["K"]
-    nk_full = cfg["N_k"]
-    nk = {"alchemical": 8, "umbrella": 200, "harmonic": nk_full, "pt": 100}[name]
-    if name == "alchemical":
-        p = W.alchemical(K=K, N_k=nk, seed=1)
-    elif name == "umbrella":
-        p = W.umbrella(K=K, N_k=nk, seed=1, grid_points=1 << 14)
-    elif name == "pt":
-        p = W.parallel_tempering(K=K, N_k=nk, seed=1)
-    else:
-        p = W.harmonic(K=K, N_k=nk, seed=1)
-    opts = O.BUOptions(h0=cfg["h0"])
-    t0 = time.perf_counter()
-    O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, opts=opts)
-    dt = time.perf_counter() - t0
-    scale = (K * nk) / (K * nk_full)
-    value = (1.0 / dt) * scale
+# samples per state of the bounded sample the oracle solves end to end
+REDUCED_NK = {"alchemical": 8, "umbrella": 200, "harmonic": 1000, "pt": 100}
+
+
+def cpu_info():
+    """CPU model, cores the process may use, and the thread count of the
+    BLAS numpy calls (numpy's elementwise exp/log run on one thread)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    blas = None
     try:
         import threadpoolctl
-        threads = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) if threadpoolctl.threadpool_info() else 1
+        info = threadpoolctl.threadpool_info()
+        blas = max((i.get("num_threads", 1) for i in info), default=None)
     except Exception:
-        threads = os.cpu_count() or 1
-    sample = (f"oracle Algorithm 1 + Newton on {name} with all K={K} states and N_k={nk} "
-              f"({K * nk} of {K * nk_full} samples); {dt:.2f} s per sample solve, scaled to the full "
-              f"size by the entry ratio {scale:.2e} (assumes cost linear in K*N)")
-    return dict(value=value, unit="solves/s", cores=int(threads), kind="oracle", sample=sample,
-                seconds=dt)
+        pass
+    return {"cpu_model": model, "cores_available": cores, "blas_threads": blas}
+
+
+def reduced_problem(name: str):
+    """The bounded sample of a workload: all K states, REDUCED_NK samples each."""
+    from paper_2609_03541_b300 import workloads as W
+    cfg = WORKLOADS[name]
+    K, nk = cfg["K"], REDUCED_NK[name]
+    if name == "alchemical":
+        return W.alchemical(K=K, N_k=nk, seed=1)
+    if name == "umbrella":
+        return W.umbrella(K=K, N_k=nk, seed=1, grid_points=1 << 14)
+    if name == "pt":
+        return W.parallel_tempering(K=K, N_k=nk, seed=1)
+    return W.harmonic(K=K, N_k=nk, seed=1)
+
+
+def oracle_solve_seconds(name: str, p, want_f: bool = False):
+    """Time-to-solution of the oracle's Algorithm 1 + Newton finish on p
+    (and its free energies if asked)."""
+    import oracle as O
+    opts = O.BUOptions(h0=WORKLOADS[name]["h0"])
+    t0 = time.perf_counter()
+    f = O.bu_mbar(p.u_kn, p.N_k, phi=p.phi, opts=opts)
+    dt = time.perf_counter() - t0
+    return (dt, f) if want_f else dt
+
+
+def oracle_iteration_seconds(u_full: np.ndarray, N_k, chunk: int = 100_000):
+    """One unbinned Eq. 1 iteration of the oracle over the full K x N matrix,
+    chunked over samples: per chunk the oracle's log_denominator and its
+    per-state log-sum-exp of -u - logden (the two sums of sci_step), then
+    the chunks' per-state sums combined by the oracle's logsumexp and the
+    gauge. Only the oracle calls are timed."""
+    import oracle as O
+    K, N = u_full.shape
+    f = np.zeros(K)
+    parts = []
+    t = 0.0
+    for c0 in range(0, N, chunk):
+        u = np.ascontiguousarray(u_full[:, c0:c0 + chunk])
+        t0 = time.perf_counter()
+        ld = O.log_denominator(u, f, N_k)
+        parts.append(O.logsumexp(-u - ld[None, :], axis=1))
+        t += time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.gauge(-O.logsumexp(np.stack(parts, axis=0), axis=0))
+    t += time.perf_counter() - t0
+    return t
+
+
+def cpu_baseline_block(name: str, p, u_full: np.ndarray | None, N_k, gpu_solve_s=None, gpu_iter_s=None):
+    """The oracle, as it stands, on the host cores: its time-to-solution on
+    the bounded sample p (the `value`, in solves/s of that sample, no
+    scaling) and one unbinned Eq. 1 iteration over the full matrix. Returns
+    (block, the oracle's free energies of p)."""
+    solve_s, f_ref = oracle_solve_seconds(name, p, want_f=True)
+    iter_s = oracle_iteration_seconds(u_full, N_k) if u_full is not None else None
+    info = cpu_info()
+    out = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": info["cores_available"], "kind": "oracle",
+           "sample": (f"time-to-solution of the oracle's Algorithm 1 + Newton finish on the bounded sample "
+                      f"{name} K={p.K}, N_k={REDUCED_NK[name]} (N={p.N}, seed 1): value = solves/s of that sample; "
+                      f"per_iteration_s = one unbinned Eq. 1 iteration over the full K x N matrix "
+                      f"({u_full.shape[0]} x {u_full.shape[1]}, chunked over samples)" if u_full is not None else
+                      f"time-to-solution of the oracle's Algorithm 1 + Newton finish on the bounded sample "
+                      f"{name} K={p.K}, N_k={REDUCED_NK[name]} (N={p.N}, seed 1)"),
+           "solve_s": solve_s, "solve_config": f"{name} K={p.K} N_k={REDUCED_NK[name]} N={p.N}",
+           "per_iteration_s": iter_s, **info}
+    if gpu_solve_s is not None:
+        out["gpu_solve_s_same_config"] = gpu_solve_s
+        out["solve_speedup_same_config"] = solve_s / gpu_solve_s
+    if gpu_iter_s is not None and iter_s is not None:
+        out["gpu_per_iteration_s"] = gpu_iter_s
+        out["iteration_speedup_full_config"] = iter_s / gpu_iter_s
+    return out, f_ref
 
 
 # ---------------------------------------------------------------------------
@@ -346,6 +414,79 @@ def _gen_device(kind: str, K: int, Nk: int, seed: int):
     if kind == "harmonic":
         return W.harmonic_device(K, Nk, seed)
     return W.umbrella_device(K, Nk, seed)
+
+
+# Sec. IV: N_i = N_0, N_0 / M or N_0 / M^2 samples per replica, with N_0
+# chosen so that every scenario has 1e4 samples per replica at M = 300
+GAUSS_SCENARIOS = (("i", 1e4, 0), ("ii", 3e6, 1), ("iii", 9e8, 2))
+
+
+def gaussian_bench(args):
+    """The synthetic overlap study of Sec. IV: unit-variance normal energy
+    histograms with 80 % overlap between neighbouring replicas, u_kn =
+    beta_k E_n, in the paper's three scenarios for the samples per replica
+    (N_0; N_0 / M; N_0 / M^2 with N_0 = 1e4, 3e6, 9e8). For each scenario and
+    replica count M, `--seeds` seeded problems are drawn on the device, sent
+    to mbar_create_factorised (E and beta only), solved (MIXED unless
+    --precision fp64) and timed end to end on the device (create + solve +
+    free energies + destroy, events on the stream, inputs resident); every
+    solve is checked against the analytic f_k = -beta_k^2 / 2 + c within 5
+    of its asymptotic standard deviations (mbar_covariance)."""
+    import torch
+    from paper_2609_03541_b300 import mbar as M
+    from paper_2609_03541_b300 import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    prec = M.MBAR_FP64 if args.precision == "fp64" else M.MBAR_MIXED
+    stream = torch.cuda.current_stream(dev)
+    Ms = [int(x) for x in args.gauss_M.split(",")]
+    rows, worst_z, total_s, solves = [], 0.0, 0.0, 0
+    for name, N0, power in GAUSS_SCENARIOS:
+        for Mrep in Ms:
+            N_i = int(round(N0 / Mrep ** power))
+            times, zs, entries = [], [], Mrep * Mrep * N_i
+            for seed in range(args.seeds):
+                beta, E, Nk = W.gaussian_overlap_device(Mrep, N_i, seed=1000 * Mrep + seed, device=dev)
+                a = torch.zeros_like(beta)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx = M.Context.factorised(a, beta, E, Nk, prec, stream=stream.cuda_stream)
+                ctx.solve()
+                f = ctx.free_energies()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                C = ctx.covariance()
+                ctx.close()
+                times.append(e0.elapsed_time(e1) / 1e3)
+                b = beta.cpu().numpy()
+                exact = -(b * b - b[0] * b[0]) / 2.0
+                sd = np.sqrt(np.maximum(np.diag(C), 0.0))
+                z = float(np.max(np.abs(f - exact)[1:] / sd[1:])) if Mrep > 1 else 0.0
+                zs.append(z)
+                del beta, E, a
+            t_med = statistics.median(times)
+            total_s += sum(times)
+            solves += len(times)
+            worst_z = max(worst_z, max(zs))
+            rows.append({"scenario": name, "M": Mrep, "N_i": N_i, "N": Mrep * N_i, "entries": entries,
+                         "seeds": args.seeds, "median_s": t_med, "solves_per_s": 1.0 / t_med,
+                         "max_z": max(zs), "all_within_5_sigma": max(zs) < 5.0})
+            log(f"[bench] gaussian {name} M={Mrep} N_i={N_i}: {t_med * 1e3:.2f} ms median, max z {max(zs):.2f}")
+            torch.cuda.empty_cache()
+    line = {"metric": "MBAR solves/sec (Sec. IV synthetic overlap scenarios)", "value": solves / total_s,
+            "unit": "solves/s", "n_gpus": 1, "steps": solves, "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == M.MBAR_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": "gaussian overlap (Sec. IV): unit-variance normal energies, 80 % neighbour "
+                                   "overlap, u_kn = beta_k E_n; N_i = N_0 (1e4), N_0/M (3e6), N_0/M^2 (9e8)",
+                       "M": Ms, "seeds": args.seeds,
+                       "step": "mbar_create_factorised + mbar_solve + mbar_free_energies + mbar_destroy",
+                       "check": "|f_k - f_0 + (beta_k^2 - beta_0^2)/2| < 5 sd (asymptotic covariance)"},
+            "scenarios": rows, "max_z": worst_z, "all_within_5_sigma": worst_z < 5.0}
+    print(json.dumps(line), flush=True)
+    return 0 if worst_z < 5.0 else 1
 
 
 def batch_bench(args):
@@ -541,7 +682,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="alchemical", choices=list(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="alchemical", choices=list(WORKLOADS) + ["batch", "serve", "gaussian"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -565,6 +706,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=140.0, help="batch/serve: device memory budget of the server")
     ap.add_argument("--wave-gb", type=float, default=80.0, help="batch/serve: FP64 input memory held at once")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--gauss-M", default="10,30,100,300", help="gaussian: replica counts M")
+    ap.add_argument("--seeds", type=int, default=12, help="gaussian: seeds per (scenario, M) (the paper uses 12)")
     ap.add_argument("--nk", type=int, default=None,
                     help="samples per state override (smaller instances for profiling captures)")
     args = ap.parse_args()
@@ -572,6 +715,8 @@ def main():
         return batch_bench(args)
     if args.workload == "serve":
         return serve_bench(args)
+    if args.workload == "gaussian":
+        return gaussian_bench(args)
     if args.lse_only:
         return lse_only(args)
     if args.hess_only:
@@ -593,22 +738,27 @@ def main():
               "step": "mbar_create + mbar_set_coordinate + mbar_solve + mbar_free_energies + mbar_destroy"}
 
     if args.impl == "reference":
+        # the oracle (numpy, as it stands) on the host cores; rank 0 only
         if rank != 0:
             return 0
-        steps = []
+        p = reduced_problem(args.workload)
+        secs = []
         for i in range(args.warmup + args.steps):
-            r = oracle_sample(args.workload)
+            t = oracle_solve_seconds(args.workload, p)
             if i >= args.warmup:
-                steps.append(r)
-        val = statistics.median(s["value"] for s in steps)
-        base = steps[0]
+                secs.append(t)
+        med = statistics.median(secs)
+        val = 1.0 / med
+        info = cpu_info()
+        sample = (f"each step: the oracle's Algorithm 1 + Newton finish on the bounded sample {args.workload} "
+                  f"K={p.K}, N_k={REDUCED_NK[args.workload]} (N={p.N} of {config['N']} samples, seed 1); "
+                  f"value = solves/s of that sample, not scaled to the full size")
         line = {"impl": "reference", "metric": metric, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": statistics.median(s["seconds"] for s in steps) * 1e3,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": med * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
-                "cpu_baseline": {"value": val, "unit": "solves/s", "cores": base["cores"], "kind": "oracle",
-                                 "sample": base["sample"]},
+                "cpu_baseline": {"value": val, "unit": "solves/s", "cores": info["cores_available"],
+                                 "kind": "oracle", "sample": sample, **info},
                 "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -811,8 +961,33 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(args.workload)
-        cpu.pop("seconds", None)
+        # the GPU on the oracle's bounded sample (same precision and options;
+        # resident input, median of 5 event-timed solves), then the oracle
+        pr = reduced_problem(args.workload)
+        u_red = torch.from_numpy(np.ascontiguousarray(pr.u_kn)).to(dev)
+        phi_red = torch.from_numpy(np.ascontiguousarray(pr.phi)).to(dev) if pr.phi is not None else None
+        t_red = []
+        for i in range(6):
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            ctx = M.Context(u_red, pr.N_k, prec, opts=opts, stream=stream.cuda_stream)
+            if phi_red is not None:
+                ctx.set_coordinate(phi_red)
+            ctx.solve()
+            f_red = ctx.free_energies()
+            ctx.close()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                t_red.append(a0.elapsed_time(a1) / 1e3)
+        gpu_iter = (ms_x / n_x / 1e3) if n_x else ((ms_l / n_l / 1e3) if n_l else None)
+        cpu, f_red_ref = cpu_baseline_block(args.workload, pr, host.numpy(), Nk,
+                                            gpu_solve_s=statistics.median(t_red), gpu_iter_s=gpu_iter)
+        if accuracy is None:
+            accuracy = {}
+        accuracy["max_abs_df_vs_oracle_kT"] = float(np.max(np.abs(f_red - f_red_ref)))
+        accuracy["oracle_config"] = cpu["solve_config"]
 
     if rank == 0:
         line = {"metric": metric, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

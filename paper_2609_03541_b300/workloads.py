@@ -162,6 +162,27 @@ def gaussian_overlap(M: int = 20, N_0: int = 1000, overlap: float = 0.8, seed: i
                    meta=dict(beta=beta, spacing=D))
 
 
+def overlap_spacing(overlap: float = 0.8) -> float:
+    """Distance D between the means of two unit normals whose overlapping
+    coefficient 2 Phi(-D/2) is ``overlap`` (the Sec. IV construction)."""
+    from statistics import NormalDist
+    return -2.0 * NormalDist().inv_cdf(overlap / 2.0)
+
+
+def gaussian_overlap_device(M: int, N_i: int, seed: int, overlap: float = 0.8, device="cuda"):
+    """(beta float64 [M] on `device`, E float64 [M N_i] on `device`, N_k):
+    the Sec. IV energies of `gaussian_overlap` drawn with torch's Philox
+    generator on the device (state k: E ~ N(-beta_k, 1), beta_k = 1 + D k);
+    the reduced potentials are u_kn = beta_k E_n (the factorised form)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    beta = 1.0 + overlap_spacing(overlap) * torch.arange(M, device=device, dtype=torch.float64)
+    E = torch.randn(M, N_i, generator=g, device=device, dtype=torch.float64)
+    E.sub_(beta[:, None])
+    return beta, E.reshape(-1).contiguous(), np.full(M, N_i, dtype=np.int64)
+
+
 def parallel_tempering(K: int = 50, N_k: int = 200_000, T_min: float = 298.0, T_max: float = 600.0,
                        sigma2: float = 2000.0, seed: int = 0, materialize: bool = True) -> Problem:
     """PT-shaped stand-in for the Sec. III workload (no MD data available).
