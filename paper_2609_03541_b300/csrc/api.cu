@@ -318,6 +318,18 @@ mbar_status sci_step_exact(mbar_ctx* c, const Level& L, const double* f_in, doub
   return MBAR_OK;
 }
 
+// The Hessian at f on level L, with logden at f from the last pass over L.
+// Unbinned MIXED data with a tensor-core K read the sample-major copy
+// (contiguous 64-sample runs for the kernel's TMA boxes; logden in that
+// order); everything else the level's row-major store.
+mbar_status level_hessian(mbar_ctx* c, const Level& L, const double* f, void* tmp, size_t htmp) {
+  if (!L.binned && c->smaj && c->vst && c->dtype == 4 && hessian_smaj_eligible(c->K))
+    return hessian_smaj(static_cast<const float*>(c->vst), c->K, L.n, f, c->logN_d,
+                        static_cast<const float*>(c->logden_orig), c->hess, err_word(c), tmp, htmp, c->st);
+  return hessian(L.v, c->dtype, c->K, L.n, L.ld, f, c->logN_d, c->logden, L.binned ? L.H : nullptr, c->hess,
+                 err_word(c), tmp, htmp, c->st);
+}
+
 mbar_status ensure_sorted(mbar_ctx* c);
 
 // Histogram at width w over the sorted coordinate -> a binned level.
@@ -536,8 +548,7 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
     }
     rep->iters_newton++;
     time_mark(c, true, 1, static_cast<double>(K) * L.n * c->dtype);
-    mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->f, c->logN_d, c->logden, nullptr, c->hess, err_word(c),
-                            tmp, htmp, c->st);
+    mbar_status s = level_hessian(c, L, c->f, tmp, htmp);
     time_mark(c, false, 1, 0);
     if (s == MBAR_OK) s = cudaMemsetAsync(c->info, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
     time_mark(c, true, 2, static_cast<double>(K) * K * 8);
@@ -1746,8 +1757,7 @@ mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
   const size_t htmp = hessian_tmp_bytes(K, L.n);
   void* tmp = nullptr;
   BUMBAR_TRY(dalloc(c, &tmp, htmp));
-  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, err_word(c), tmp,
-                          htmp, c->st);
+  mbar_status s = level_hessian(c, L, c->ft, tmp, htmp);
   if (s == MBAR_OK) s = check_device_errors(c);
   if (s == MBAR_OK) s = d2h(c, hess_out, c->hess, K * K);
   if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
@@ -1775,8 +1785,7 @@ mbar_status mbar_covariance(mbar_ctx* c, double* cov_out) {
   BUMBAR_TRY(dalloc(c, &tmp, htmp));
   mbar_status s = dalloc_t(c, &cov, K * K);
   if (s == MBAR_OK)
-    s = hessian(L.v, c->dtype, K, L.n, L.ld, c->f, c->logN_d, c->logden, nullptr, c->hess, err_word(c), tmp, htmp,
-                c->st);
+    s = level_hessian(c, L, c->f, tmp, htmp);
   if (s == MBAR_OK) s = check_device_errors(c);
   int info = 0;
   if (s == MBAR_OK && cudaMemsetAsync(c->info, 0, sizeof(int), c->st) != cudaSuccess) s = MBAR_ECUDA;
@@ -1810,8 +1819,7 @@ mbar_status mbar_newton_step(mbar_ctx* c, const double* f_in, double* f_out, dou
   const size_t htmp = hessian_tmp_bytes(K, L.n), ntmp = newton_tmp_bytes(K);
   void* tmp = nullptr;
   BUMBAR_TRY(dalloc(c, &tmp, std::max(htmp, ntmp)));
-  mbar_status s = hessian(L.v, c->dtype, K, L.n, L.ld, c->ft, c->logN_d, c->logden, L.H, c->hess, err_word(c), tmp,
-                          htmp, c->st);
+  mbar_status s = level_hessian(c, L, c->ft, tmp, htmp);
   if (s == MBAR_OK) s = cudaMemsetAsync(c->info, 0, sizeof(int), c->st) == cudaSuccess ? MBAR_OK : MBAR_ECUDA;
   if (s == MBAR_OK) s = newton_solve(c->hess, K, c->gt, c->delta, c->info, tmp, ntmp, c->st);
   if (s == MBAR_OK) s = vec_add_gauge(c->ft, c->delta, c->fts, K, c->st);

@@ -62,6 +62,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 mbar_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
                          int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows) {
+  return make_tmap_2d_swz(map, base, dtype, elem_bytes, rows, cols, ld, box_cols, box_rows, true);
+}
+
+mbar_status make_tmap_2d_swz(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
+                             int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows, bool swizzle128) {
   auto encode = get_encode();
   if (!encode) {
     set_error("cuTensorMapEncodeTiled unavailable from the driver");
@@ -76,7 +81,8 @@ mbar_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType
   cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d): rows=%lld cols=%lld ld=%lld box=%dx%d", static_cast<int>(r),

@@ -86,6 +86,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 1-D bulk copy global -> shared memory (both 16-byte aligned, bytes a
+// multiple of 16), completion on `bar` (complete_tx).
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -159,6 +172,10 @@ __device__ __forceinline__ uint32_t swz128(uint32_t row, uint32_t chunk) {
 // a box of (box_cols x box_rows) elements and 128-byte swizzle.
 mbar_status make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
                          int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows);
+// The same with the 128-byte swizzle optional (false: boxes land in shared
+// memory as plain row-major tiles; inner extent up to 256 elements).
+mbar_status make_tmap_2d_swz(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
+                             int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows, bool swizzle128);
 
 // Splits a binary64 x into hi = RN32(x) and lo = RN32(x - hi) with integer
 // operations only: the residual is (dropped 29 fraction bits - the rounding

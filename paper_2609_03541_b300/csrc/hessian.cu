@@ -182,6 +182,30 @@ size_t hessian_tmp_bytes(int64_t K, int64_t n) {
   return std::max(simt, tc) + round_up(K * K * 8, 256);
 }
 
+bool hessian_smaj_eligible(int64_t K) { return hessian_path_for(K, 4) == 2 && overlap_tc_smaj_eligible(K); }
+
+mbar_status hessian_smaj(const float* vst, int64_t K, int64_t n, const double* f, const double* logN,
+                         const float* logden, double* hess, unsigned* err, void* tmp, size_t tmp_bytes,
+                         cudaStream_t st) {
+  if (tmp_bytes < hessian_tmp_bytes(K, n)) {
+    set_error("hessian: scratch too small");
+    return MBAR_EINVAL;
+  }
+  const SimtPlan p = simt_plan(K, n);
+  const size_t simt = round_up(static_cast<int64_t>(p.nslices) * p.npairs * kTile * kTile * 4, 256);
+  const size_t tc = overlap_tc_tmp_bytes(K, n) + round_up(K * 8, 256);
+  double* G = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + std::max(simt, tc));
+  double* a = static_cast<double*>(tmp);
+  unsigned char* rest = static_cast<unsigned char*>(tmp) + round_up(K * 8, 256);
+  add_vectors<<<static_cast<unsigned>(ceil_div(K, 256)), 256, 0, st>>>(f, logN, a, K);
+  count_launches(1);
+  BUMBAR_TRY(overlap_tc_smaj(vst, K, n, a, logden, G, err, rest, overlap_tc_tmp_bytes(K, n), st));
+  laplacian_from_overlap<<<static_cast<unsigned>(K), kThreads, 0, st>>>(G, K, hess);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
 mbar_status hessian(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
                     const double* logN, const void* logden, const int32_t* H, double* hess, unsigned* err,
                     void* tmp, size_t tmp_bytes, cudaStream_t st) {

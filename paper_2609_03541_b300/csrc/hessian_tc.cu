@@ -364,16 +364,27 @@ __global__ void reduce_tc(const float* __restrict__ part, const TcCta* __restric
 // the upper triangle of G exactly once (a circulant assignment: at most
 // three 128 x 128 FP32 accumulators per CTA, within the 512 TMEM columns).
 //
-// Per 64-sample chunk: TMA brings the CTA's 128 x 64 FP32 block of v into a
-// three-stage ring (vfull barriers); all threads wait until every reader of
-// the previous use of the P~ stage has finished its MMAs (pempty, arrived
-// by tcgen05.commit multicast to the writers), build and distribute P~, and
-// thread 0 then signals the readers' pfull barriers (remote arrive,
-// release at cluster scope), waits for its own pfull (all writers done) and
-// issues the MMAs. Every wait is bounded; a CTA that gives up records an
-// error and still reaches the final cluster barrier.
+// Three roles per CTA, coupled only by mbarriers (no CTA-wide barrier in
+// the chunk loop):
+//   * a loader warp streams the CTA's 128 x 64 FP32 blocks of v into a
+//     two-stage ring by TMA (vfull), refilling a stage once every producer
+//     warp has read it (vempty);
+//   * 16 producer warps: per 64-sample chunk each thread waits for its v
+//     block and for the P~ stage to be free (pempty: every reader of the
+//     tile finished its MMAs on the stage's previous chunk), forms P~ for
+//     two rows and eight samples and stores the FP16 pieces to this CTA and
+//     its readers. The proxy fence that makes those stores visible to the
+//     tensor cores, and the per-warp arrivals on the readers' pfull
+//     barriers, are issued one chunk later, after the next chunk's
+//     exponentials: by then the remote stores have drained and the fence
+//     does not stall;
+//   * an MMA warp waits until every writer's warps have delivered a chunk
+//     (pfull), issues the UMMAs and commits them to the writers' pempty.
+// Every wait is bounded; a CTA that gives up records an error and still
+// reaches the final cluster barrier.
 constexpr int kClThreads = 512;                // threads that build P~ (16 warps)
-constexpr int kClThreadsAll = kClThreads + 32;  // + one warp that issues the MMAs
+constexpr int kClWarps = kClThreads / 32;
+constexpr int kClThreadsAll = kClThreads + 64;  // + the MMA warp + the loader warp
 constexpr int kClVStages = 2;
 constexpr int kClPStages = 3;                 // P~ stages (chunks in flight between producers and MMAs)
 constexpr int kClVStageBytes = 128 * 64 * 4;  // two 32-column 128B-swizzled boxes
@@ -381,7 +392,6 @@ constexpr int kClPSlots = 3;
 constexpr int kClPSlotBytes = 128 * 128;      // one FP16 128 x 64 tile
 constexpr int kClPStageBytes = kClPSlots * kClPSlotBytes;
 constexpr int kClMaxTiles = 4;                // MT <= 4, i.e. K <= 512
-constexpr int kClColRing = 4;                 // chunks of per-sample columns staged ahead (3 ahead)
 
 __host__ __device__ inline int cl_dmax(int q, int MT) {
   return (MT - 1) / 2 + ((MT % 2 == 0 && q < MT / 2) ? 1 : 0);
@@ -461,29 +471,17 @@ __device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, uint32_t parity, 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// generic-proxy writes to shared memory (this CTA's and the cluster peers')
+// made visible to the async proxy (the tensor cores' operand reads)
+__device__ __forceinline__ void fence_proxy_async_smem_cluster() {
+  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
 __device__ __forceinline__ void umma_commit_multicast(uint64_t* bar, uint16_t mask) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
           smem_u32(bar)),
       "h"(mask)
       : "memory");
-}
-
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kClThreads) : "memory"); }
-// Barrier of the producer warps that also ORs a flag over them: every
-// producer gets the same answer (they all leave the loop together).
-__device__ __forceinline__ bool producers_sync_or(bool v) {
-  uint32_t res;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.or.pred p, 1, %2, q;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(res)
-      : "r"(static_cast<uint32_t>(v)), "n"(kClThreads)
-      : "memory");
-  return res != 0;
 }
 
 __global__ void __launch_bounds__(kClThreadsAll, 1)
@@ -494,17 +492,18 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
   unsigned char* vbuf = smem;
   unsigned char* pbuf = smem + kClVStages * kClVStageBytes;
   uint64_t* vfull = reinterpret_cast<uint64_t*>(pbuf + kClPStages * kClPStageBytes);  // [kClVStages]
-  uint64_t* pfull = vfull + kClVStages;                                                 // [kClPStages]
+  uint64_t* vempty = vfull + kClVStages;                                                // [kClVStages]
+  uint64_t* pfull = vempty + kClVStages;                                                // [kClPStages]
   uint64_t* pempty = pfull + kClPStages;                                                // [kClPStages]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pempty + kClPStages);
   volatile int* fail_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  // per-sample log2(logden) and sqrt(H) of the chunks ahead: [kClColRing][64] each
-  float* l2_ring = reinterpret_cast<float*>(pbuf + kClPStages * kClPStageBytes + 128);
-  float* sh_ring = l2_ring + kClColRing * 64;
+  int* issued_s = reinterpret_cast<int*>(tmem_slot + 2);  // v chunks the loader sent
 
   const int tid = threadIdx.x;
-  const bool producer = tid < kClThreads;
   const int warp = tid >> 5, lane = tid & 31;
+  const bool producer = tid < kClThreads;
+  const bool mma_warp = warp == kClWarps;
+  const bool loader_warp = warp == kClWarps + 1;
   const int MT = p.MT;
   const int r = static_cast<int>(cluster_ctarank());
   const int64_t slice = blockIdx.x / MT;
@@ -524,18 +523,22 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
 
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   if (tid == 0) {
-    for (int s = 0; s < kClVStages; ++s) mbar_init(&vfull[s], 1);
+    for (int s = 0; s < kClVStages; ++s) {
+      mbar_init(&vfull[s], 1);
+      mbar_init(&vempty[s], kClWarps);
+    }
     for (int b = 0; b < kClPStages; ++b) {
-      mbar_init(&pfull[b], static_cast<uint32_t>(dm + 1));
+      mbar_init(&pfull[b], static_cast<uint32_t>((dm + 1) * kClWarps));
       mbar_init(&pempty[b], static_cast<uint32_t>(nreaders));
     }
     *fail_s = 0;
+    *issued_s = 0;
     fence_barrier_init();
     prefetch_tmap(&tmap);
   }
   // this thread's rows (lr0, lr0 + 64) of tile r and 8-sample group g
   const int g = tid & 7;
-  const int lr0 = tid >> 3;
+  const int lr0 = (tid >> 3) & 63;
   float a2r[2];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
@@ -546,123 +549,125 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
   cluster_sync_all();  // barrier initialisation visible to the peers
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  auto issue_v = [&](int64_t c) {
-    const int s = static_cast<int>(c % kClVStages);
-    unsigned char* dst = vbuf + s * kClVStageBytes;
-    const int col = static_cast<int>(c_begin + c * 64);
-    mbar_expect_tx(&vfull[s], kClVStageBytes);
-    tma_load_2d(dst, &tmap, &vfull[s], col, r * 128);
-    tma_load_2d(dst + kClVStageBytes / 2, &tmap, &vfull[s], col + 32, r * 128);
-  };
-  int64_t issued = 0;
-  if (tid == 0) {
-    for (int64_t c = 0; c < nchunks && c < kClVStages; ++c) issue_v(c);
-  }
-  issued = nchunks < kClVStages ? nchunks : kClVStages;
-
-  // threads 0..63 fetch chunk c's per-sample columns into registers (load_cols)
-  // and write them to ring slot c % kClColRing one chunk later (put_cols), so
-  // no producer waits on the global loads
-  float col_l2 = INFINITY, col_sh = 0.f;  // padding samples contribute nothing
-  auto load_cols = [&](int64_t c) {
-    if (tid < 64) {
-      const int64_t col = c_begin + c * 64 + tid;
-      col_l2 = INFINITY;
-      col_sh = 0.f;
-      if (col < c_end) {
-        col_l2 = p.logden[col];
-        col_sh = p.H ? static_cast<float>(p.H[col]) : 1.f;
-      }
-    }
-  };
-  auto put_cols = [&](int64_t c) {
-    if (tid < 64) {
-      const int slot = static_cast<int>(c % kClColRing);
-      l2_ring[slot * 64 + tid] = col_l2 * kLog2e;
-      sh_ring[slot * 64 + tid] = p.H ? sqrtf(col_sh) : col_sh;
-    }
-  };
   constexpr uint32_t idesc = idesc_f16(128, 128);
-  int64_t c = 0;
+
   if (producer) {
-    // producers: v tile in, P~ out to this CTA and its readers, then the
-    // readers' pfull barriers; they never wait for the MMA warp directly
-    for (int64_t cc = 0; cc < nchunks && cc < kClColRing - 1; ++cc) {
-      load_cols(cc);
-      put_cols(cc);
-    }
-    if (kClColRing - 1 < nchunks) load_cols(kClColRing - 1);
+    // per-sample log2(e) logden and sqrt(H) of this thread's 8 samples,
+    // loaded one chunk ahead (padding samples: 2^-inf = 0)
+    float l2n[8], shn[8];
+    auto load_cols = [&](int64_t cc) {
+      const int64_t col0 = c_begin + cc * 64 + g * 8;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        l2n[j] = INFINITY;
+        shn[j] = 0.f;
+      }
+      if (col0 + 8 <= c_end) {
+        const float4 d0 = *reinterpret_cast<const float4*>(p.logden + col0);
+        const float4 d1 = *reinterpret_cast<const float4*>(p.logden + col0 + 4);
+        const float dd[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          l2n[j] = dd[j] * kLog2e;
+          shn[j] = p.H ? sqrtf(static_cast<float>(p.H[col0 + j])) : 1.f;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (col0 + j < c_end) {
+            l2n[j] = p.logden[col0 + j] * kLog2e;
+            shn[j] = p.H ? sqrtf(static_cast<float>(p.H[col0 + j])) : 1.f;
+          }
+      }
+    };
+    // readers' pfull barriers of stage b: arrive once per warp, after the
+    // proxy fence that covers this thread's earlier P~ stores
+    auto deliver = [&](int b) {
+      fence_proxy_async_smem_cluster();
+      __syncwarp();
+      if (lane == 0)
+        for (int q = 0; q < MT; ++q)
+          if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
+    };
+    if (nchunks > 0) load_cols(0);
+    bool failed = false;
+    int64_t c = 0;
     for (; c < nchunks; ++c) {
       const int s = static_cast<int>(c % kClVStages);
       const int b = static_cast<int>(c % kClPStages);
       bool ok = mbar_wait_timed(&vfull[s], static_cast<uint32_t>((c / kClVStages) & 1), kMaxSpins);
-      if (ok && c >= kClPStages)
-        ok = mbar_wait_cluster_bounded(&pempty[b], static_cast<uint32_t>(((c - kClPStages) / kClPStages) & 1),
-                                       kMaxSpins);
-      if (producers_sync_or(!ok || *fail_s != 0)) {
-        *fail_s = 1;
+      float x[2][8];
+      if (ok) {
+        const unsigned char* vb = vbuf + s * kClVStageBytes + (g >> 2) * (kClVStageBytes / 2);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int lr = lr0 + 64 * u;
+          const float4 x0 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2));
+          const float4 x1 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2 + 1));
+          x[u][0] = x0.x; x[u][1] = x0.y; x[u][2] = x0.z; x[u][3] = x0.w;
+          x[u][4] = x1.x; x[u][5] = x1.y; x[u][6] = x1.z; x[u][7] = x1.w;
+        }
+      }
+      if (__all_sync(0xffffffffu, ok)) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&vempty[s]);  // this warp is done with the v stage
+      }
+      if (ok && c >= kClPStages) {
+        // the stage's previous chunk is consumed by every reader: one lane
+        // polls, the warp follows
+        if (lane == 0)
+          ok = mbar_wait_cluster_bounded(&pempty[b], static_cast<uint32_t>(((c - kClPStages) / kClPStages) & 1),
+                                         kMaxSpins);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+      if (!__all_sync(0xffffffffu, ok && *fail_s == 0)) {
+        if (lane == 0) *fail_s = 1;
+        failed = true;
         break;
       }
-      // chunk c's columns were staged three chunks ago (ordered by the
-      // producer barriers since); stage chunk c + 3 into the slot chunk c - 1 used
       float l2[8], sh[8];
-      {
-        const int slot = static_cast<int>(c % kClColRing);
-        const float4 a0 = *reinterpret_cast<const float4*>(l2_ring + slot * 64 + g * 8);
-        const float4 a1 = *reinterpret_cast<const float4*>(l2_ring + slot * 64 + g * 8 + 4);
-        const float4 b0 = *reinterpret_cast<const float4*>(sh_ring + slot * 64 + g * 8);
-        const float4 b1 = *reinterpret_cast<const float4*>(sh_ring + slot * 64 + g * 8 + 4);
-        l2[0] = a0.x; l2[1] = a0.y; l2[2] = a0.z; l2[3] = a0.w;
-        l2[4] = a1.x; l2[5] = a1.y; l2[6] = a1.z; l2[7] = a1.w;
-        sh[0] = b0.x; sh[1] = b0.y; sh[2] = b0.z; sh[3] = b0.w;
-        sh[4] = b1.x; sh[5] = b1.y; sh[6] = b1.z; sh[7] = b1.w;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        l2[j] = l2n[j];
+        sh[j] = shn[j];
       }
-      if (c + kClColRing - 1 < nchunks) {
-        put_cols(c + kClColRing - 1);  // loaded during the previous chunk
-        if (c + kClColRing < nchunks) load_cols(c + kClColRing);
+      uint4 packed[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        float pv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pv[j] = ex2_approx(fmaf(-x[u][j], kLog2e, a2r[u]) - l2[j]) * sh[j];
+        packed[u].x = pack_half2(pv[0], pv[1]);
+        packed[u].y = pack_half2(pv[2], pv[3]);
+        packed[u].z = pack_half2(pv[4], pv[5]);
+        packed[u].w = pack_half2(pv[6], pv[7]);
       }
-      const unsigned char* vb = vbuf + s * kClVStageBytes + (g >> 2) * (kClVStageBytes / 2);
+      if (c > 0) deliver(static_cast<int>((c - 1) % kClPStages));  // the previous chunk's stores
       unsigned char* pst = pbuf + b * kClPStageBytes;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int lr = lr0 + 64 * u;
-        const float4 x0 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2));
-        const float4 x1 = *reinterpret_cast<const float4*>(vb + swz128(lr, (g & 3) * 2 + 1));
-        const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        float pv[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) pv[j] = ex2_approx(fmaf(-x[j], kLog2e, a2r[u]) - l2[j]) * sh[j];
-        uint4 packed;
-        packed.x = pack_half2(pv[0], pv[1]);
-        packed.y = pack_half2(pv[2], pv[3]);
-        packed.z = pack_half2(pv[4], pv[5]);
-        packed.w = pack_half2(pv[6], pv[7]);
         const uint32_t off = static_cast<uint32_t>(lr * 128 + ((g ^ (lr & 7)) << 4));
 #pragma unroll
         for (int q = 0; q < kClMaxTiles; ++q) {
           if (reader_mask & (1u << q)) {
             const int slot = (r - q + MT) % MT;
             if (q == r)
-              *reinterpret_cast<uint4*>(pst + off) = packed;  // own tile: slot 0
+              *reinterpret_cast<uint4*>(pst + off) = packed[u];  // own tile: slot 0
             else
               st_cluster_v4(mapa_shared(smem_u32(pst + slot * kClPSlotBytes) + off, static_cast<uint32_t>(q)),
-                            packed);
+                            packed[u]);
           }
         }
       }
-      fence_proxy_async_all();
-      producers_sync();
-      if (tid == 0) {
-        if (c + kClVStages < nchunks) issue_v(c + kClVStages);  // every producer is past this stage
-        for (int q = 0; q < MT; ++q)
-          if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
-      }
-      if (c + kClVStages < nchunks) ++issued;
+      // the next chunk's per-sample columns, issued after the fence above
+      // (a proxy fence also waits for this thread's loads in flight)
+      if (c + 1 < nchunks) load_cols(c + 1);
     }
-  } else {
-    // MMA warp: waits until every writer has delivered chunk c, issues the
-    // UMMAs and commits them to the writers' pempty barriers
+    if (!failed && nchunks > 0) deliver(static_cast<int>((nchunks - 1) % kClPStages));
+  } else if (mma_warp) {
+    // waits until every writer has delivered chunk c, issues the UMMAs and
+    // commits them to the writers' pempty barriers
     for (int64_t cm = 0; cm < nchunks; ++cm) {
       const int b = static_cast<int>(cm % kClPStages);
       bool ok = true;
@@ -687,6 +692,25 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
       }
       __syncwarp();
     }
+  } else if (loader_warp && lane == 0) {
+    // the CTA's v blocks, each stage refilled once every producer warp read it
+    int64_t issued = 0;
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int s = static_cast<int>(c % kClVStages);
+      if (c >= kClVStages &&
+          !mbar_wait_timed(&vempty[s], static_cast<uint32_t>(((c - kClVStages) / kClVStages) & 1), kMaxSpins)) {
+        *fail_s = 1;
+        break;
+      }
+      if (*fail_s) break;
+      unsigned char* dst = vbuf + s * kClVStageBytes;
+      const int col = static_cast<int>(c_begin + c * 64);
+      mbar_expect_tx(&vfull[s], kClVStageBytes);
+      tma_load_2d(dst, &tmap, &vfull[s], col, r * 128);
+      tma_load_2d(dst + kClVStageBytes / 2, &tmap, &vfull[s], col + 32, r * 128);
+      ++issued;
+    }
+    *issued_s = static_cast<int>(issued);
   }
   __syncthreads();
   bool failed = *fail_s != 0;
@@ -699,9 +723,11 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
     if (__syncthreads_or(!ok)) failed = true;
   }
   if (failed) {
-    // let this CTA's own tensor copies in flight land before leaving
+    // let this CTA's own tensor copies in flight land before leaving (at
+    // most one outstanding per v stage: the last kClVStages issued)
     if (tid == 0) {
-      for (int64_t cc = c; cc < issued; ++cc)
+      const int64_t iss = *issued_s;
+      for (int64_t cc = (iss > kClVStages ? iss - kClVStages : 0); cc < iss; ++cc)
         mbar_wait_timed(&vfull[cc % kClVStages], static_cast<uint32_t>((cc / kClVStages) & 1), kMaxSpins);
       atomicAdd(p.err, 1u);
     }
@@ -735,6 +761,217 @@ __global__ void __launch_bounds__(kClThreadsAll, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same cluster contraction for unbinned FP32 data read from the
+// sample-major copy vst[n][Kp] (MIXED contexts keep it for their LSE
+// passes), logden in that sample order, no counts.
+//
+// A generic-proxy write of UMMA operands must be followed by a proxy fence
+// before the tensor cores read it, and that fence is expensive (about 1,700
+// cycles per warp measured on B300, whatever is outstanding), so each fence
+// here covers a whole 32-state x 64-sample block per warp. The 16 producer
+// warps form four groups; group q builds the chunks c = q (mod 4) into P~
+// stage c mod 4 (four stages), warp w of a group the 32 states 32 w + lane of
+// the CTA's tile for all 64 samples: it loads their v straight from the
+// sample-major copy (a warp load is 128 contiguous bytes of one sample; the
+// first 32 samples of a chunk are loaded during the group's previous chunk),
+// forms P~, stores the eight 16-byte pieces of its row to this CTA and the
+// tile's readers, fences once and arrives on the readers' pfull barriers.
+// While one group loads or fences, the other three compute. The MMA warp
+// consumes the chunks in order.
+constexpr int kSmjGroups = 4;
+constexpr int kSmjPStages = kSmjGroups;
+constexpr int kSmjThreadsAll = kClThreads + 32;  // 16 producer warps + the MMA warp
+
+__global__ void __launch_bounds__(kSmjThreadsAll, 1)
+    overlap_tc_smaj_kernel(const float* __restrict__ vst, int Kp, ClParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* pbuf = smem;
+  uint64_t* pfull = reinterpret_cast<uint64_t*>(pbuf + kSmjPStages * kClPStageBytes);  // [kSmjPStages]
+  uint64_t* pempty = pfull + kSmjPStages;                                              // [kSmjPStages]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pempty + kSmjPStages);
+  volatile int* fail_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const bool producer = tid < kClThreads;
+  const int MT = p.MT;
+  const int r = static_cast<int>(cluster_ctarank());
+  const int64_t slice = blockIdx.x / MT;
+  const int dm = cl_dmax(r, MT);
+  const int ntl = dm + 1;
+  const uint32_t ncols = ntl == 1 ? 128u : (ntl == 2 ? 256u : 512u);
+  uint32_t reader_mask = 0;
+  for (int q = 0; q < MT; ++q)
+    if ((r - q + MT) % MT <= cl_dmax(q, MT)) reader_mask |= 1u << q;
+  const int nreaders = __popc(reader_mask);
+  uint16_t writer_mask = 0;
+  for (int d = 0; d <= dm; ++d) writer_mask |= static_cast<uint16_t>(1u << ((r + d) % MT));
+  const int64_t c_begin = slice * p.per;
+  const int64_t c_end = (c_begin + p.per < p.n) ? c_begin + p.per : p.n;
+  const int64_t nchunks = c_end > c_begin ? (c_end - c_begin + 63) / 64 : 0;
+
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  if (tid == 0) {
+    for (int b = 0; b < kSmjPStages; ++b) {
+      // one chunk is delivered by the four warps of one group of each writer
+      mbar_init(&pfull[b], static_cast<uint32_t>((dm + 1) * (kClWarps / kSmjGroups)));
+      mbar_init(&pempty[b], static_cast<uint32_t>(nreaders));
+    }
+    *fail_s = 0;
+    fence_barrier_init();
+  }
+  const int grp = warp / (kClWarps / kSmjGroups);   // chunk group
+  const int lr = 32 * (warp % (kClWarps / kSmjGroups)) + lane;   // row (state) of tile r
+  const int row = r * 128 + lr;
+  const float a2 = (producer && row < p.K) ? static_cast<float>(p.a[row] * 1.4426950408889634) : -INFINITY;
+  const bool row_stored = row < Kp;   // states K..Kp-1 are zero padding of the copy; beyond Kp nothing is read
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = idesc_f16(128, 128);
+
+  if (producer) {
+    // v of samples [32 h, 32 h + 32) of chunk cc at this thread's state, and
+    // log2(e) logden of samples lane and lane + 32 (padding: x = 0, +inf)
+    auto load_half = [&](int64_t cc, int h, float* dst) {
+      const int64_t s0 = c_begin + cc * 64;
+      const int ns = static_cast<int>(c_end - s0 < 64 ? c_end - s0 : 64);
+      const float* src = vst + (s0 + 32 * h) * Kp + row;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        dst[j] = (row_stored && 32 * h + j < ns) ? src[static_cast<int64_t>(j) * Kp] : 0.f;
+    };
+    auto load_l2 = [&](int64_t cc, float& la, float& lb) {
+      const int64_t s0 = c_begin + cc * 64;
+      const int ns = static_cast<int>(c_end - s0 < 64 ? c_end - s0 : 64);
+      la = lane < ns ? p.logden[s0 + lane] * kLog2e : INFINITY;
+      lb = lane + 32 < ns ? p.logden[s0 + lane + 32] * kLog2e : INFINITY;
+    };
+    // the first half of each chunk is loaded during the previous chunk of
+    // the group (after its fence: a proxy fence also waits for this
+    // thread's loads in flight), the second half at the chunk's start
+    float xa[32], xb[32], l2a = INFINITY, l2b = INFINITY;
+    if (grp < nchunks) {
+      load_half(grp, 0, xa);
+      load_l2(grp, l2a, l2b);
+    }
+    for (int64_t c = grp; c < nchunks; c += kSmjGroups) {
+      const int b = static_cast<int>(c % kSmjPStages);
+      bool ok = true;
+      if (c >= kSmjPStages) {
+        if (lane == 0)
+          ok = mbar_wait_cluster_bounded(&pempty[b], static_cast<uint32_t>(((c - kSmjPStages) / kSmjPStages) & 1),
+                                         kMaxSpins);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+      if (!__all_sync(0xffffffffu, ok && *fail_s == 0)) {
+        if (lane == 0) *fail_s = 1;
+        break;
+      }
+      load_half(c, 1, xb);
+      unsigned char* pst = pbuf + b * kClPStageBytes;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        float pv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int sj = 8 * k + j;
+          const float l2 = __shfl_sync(0xffffffffu, sj < 32 ? l2a : l2b, sj & 31);
+          pv[j] = ex2_approx(fmaf(-(sj < 32 ? xa[sj] : xb[sj - 32]), kLog2e, a2) - l2);
+        }
+        uint4 packed;
+        packed.x = pack_half2(pv[0], pv[1]);
+        packed.y = pack_half2(pv[2], pv[3]);
+        packed.z = pack_half2(pv[4], pv[5]);
+        packed.w = pack_half2(pv[6], pv[7]);
+        const uint32_t off = static_cast<uint32_t>(lr * 128 + ((k ^ (lr & 7)) << 4));
+#pragma unroll
+        for (int q = 0; q < kClMaxTiles; ++q) {
+          if (reader_mask & (1u << q)) {
+            const int slot = (r - q + MT) % MT;
+            if (q == r)
+              *reinterpret_cast<uint4*>(pst + off) = packed;
+            else
+              st_cluster_v4(mapa_shared(smem_u32(pst + slot * kClPSlotBytes) + off, static_cast<uint32_t>(q)), packed);
+          }
+        }
+      }
+      fence_proxy_async_smem_cluster();
+      __syncwarp();
+      if (lane == 0)
+        for (int q = 0; q < MT; ++q)
+          if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
+      if (c + kSmjGroups < nchunks) {
+        load_half(c + kSmjGroups, 0, xa);
+        load_l2(c + kSmjGroups, l2a, l2b);
+      }
+    }
+  } else {
+    for (int64_t cm = 0; cm < nchunks; ++cm) {
+      const int b = static_cast<int>(cm % kSmjPStages);
+      bool ok = true;
+      if (lane == 0)
+        ok = mbar_wait_cluster_bounded(&pfull[b], static_cast<uint32_t>((cm / kSmjPStages) & 1), kMaxSpins);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || *fail_s) {
+        if (lane == 0) *fail_s = 1;
+        break;
+      }
+      if (lane == 0) {
+        tc_fence_after();
+        const uint32_t base = smem_u32(pbuf + b * kClPStageBytes);
+        for (int t = 0; t < ntl; ++t) {
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)
+            umma_f16(tmem + static_cast<uint32_t>(t * 128), sdesc_sw128(base + k4 * 32),
+                     sdesc_sw128(base + static_cast<uint32_t>(t * kClPSlotBytes) + k4 * 32), idesc,
+                     (cm > 0 || k4 > 0) ? 1u : 0u);
+        }
+        umma_commit_multicast(&pempty[b], writer_mask);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  bool failed = *fail_s != 0;
+  if (!failed && nchunks > 0) {
+    bool ok = true;
+    for (int64_t last = nchunks - 1; last >= 0 && last >= nchunks - kSmjPStages; --last)
+      ok = ok && mbar_wait_cluster_bounded(&pempty[last % kSmjPStages],
+                                           static_cast<uint32_t>((last / kSmjPStages) & 1), kMaxSpins);
+    if (__syncthreads_or(!ok)) failed = true;
+  }
+  if (failed && tid == 0) atomicAdd(p.err, 1u);
+  tc_fence_after();
+  float* out = p.out + (slice * p.T + cl_tile_base(r, MT)) * 128 * 128;
+  const int sub = warp & 3;
+  const int quarter = warp >> 2;
+  const int row_local = sub * 32 + lane;
+  for (int c0 = quarter * 32; producer && c0 < ntl * 128; c0 += 128) {
+    float rr[32];
+    if (nchunks > 0 && !failed) {
+      tmem_ld32(tmem + (static_cast<uint32_t>(sub * 32) << 16) + static_cast<uint32_t>(c0), rr);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) rr[i] = 0.f;
+    }
+    float4* dst = reinterpret_cast<float4*>(out + (c0 >> 7) * 128 * 128 + row_local * 128 + (c0 & 127));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[i] = make_float4(rr[4 * i], rr[4 * i + 1], rr[4 * i + 2], rr[4 * i + 3]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
 // Fixed-order FP64 sum of the slices of each accumulator tile; tile
 // (q, d) is G's block (q, (q + d) mod MT), mirrored into its transpose.
 __global__ void reduce_tc_cluster(const float* __restrict__ part, int S, int T, int MT, int K,
@@ -760,7 +997,7 @@ __global__ void reduce_tc_cluster(const float* __restrict__ part, int S, int T, 
 
 size_t tc_cluster_smem() {
   return static_cast<size_t>(kClVStages) * kClVStageBytes + static_cast<size_t>(kClPStages) * kClPStageBytes + 128 +
-         2 * kClColRing * 64 * sizeof(float) + 1024;
+         1024;
 }
 
 struct ClPlan {
@@ -988,6 +1225,84 @@ mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int
   BUMBAR_CUDA(cudaGetLastError());
   const unsigned gx = static_cast<unsigned>(ceil_div(128 * 512, 256));
   reduce_tc<<<dim3(gx, ni), 256, 0, st>>>(part, ctas_d, pl.stride, first_d, count_d, static_cast<int>(K), G);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+bool overlap_tc_smaj_eligible(int64_t K) { return K >= 128 && K <= 128 * kClMaxTiles && tc_cluster_enabled(); }
+
+mbar_status overlap_tc_smaj(const float* vst, int64_t K, int64_t n, const double* a, const float* logden, double* G,
+                            unsigned* err, void* tmp, size_t tmp_bytes, cudaStream_t st) {
+  if (!overlap_tc_smaj_eligible(K)) {
+    set_error("overlap_tc_smaj: unsupported K=%lld", static_cast<long long>(K));
+    return MBAR_EUNSUPPORTED;
+  }
+  if (tmp_bytes < overlap_tc_tmp_bytes(K, n)) {
+    set_error("overlap_tc_smaj: scratch too small");
+    return MBAR_EINVAL;
+  }
+  const int MT = static_cast<int>(ceil_div(K, 128));
+  const size_t smem = static_cast<size_t>(kSmjPStages) * kClPStageBytes + 128 + 1024;  // + barriers, TMEM slot, flag
+  static int resident[kClMaxTiles + 1] = {0, 0, 0, 0, 0};
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (resident[MT] == 0) {
+      if (cudaFuncSetAttribute(overlap_tc_smaj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("overlap_tc_smaj: cannot raise the shared-memory limit");
+        return MBAR_ECUDA;
+      }
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(static_cast<unsigned>(MT * num_sms()));
+      q.blockDim = dim3(kSmjThreadsAll);
+      q.dynamicSmemBytes = smem;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = static_cast<unsigned>(MT);
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int nres = 0;
+      if (cudaOccupancyMaxActiveClusters(&nres, overlap_tc_smaj_kernel, &q) != cudaSuccess || nres <= 0) {
+        cudaGetLastError();
+        nres = std::max(1, num_sms() / MT / 2);
+      }
+      resident[MT] = nres;
+    }
+  }
+  const int clusters = std::min(resident[MT], std::max(1, num_sms() / MT));
+  const ClPlan pl = cl_plan(K, n, clusters);
+  BUMBAR_CUDA(cudaMemsetAsync(G, 0, static_cast<size_t>(K) * K * sizeof(double), st));
+  ClParams prm{};
+  prm.K = static_cast<int>(K);
+  prm.MT = pl.MT;
+  prm.T = pl.T;
+  prm.n = n;
+  prm.per = pl.per;
+  prm.a = a;
+  prm.logden = logden;
+  prm.H = nullptr;
+  prm.out = static_cast<float*>(tmp);
+  prm.err = err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(pl.S * pl.MT));
+  cfg.blockDim = dim3(kSmjThreadsAll);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(pl.MT);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BUMBAR_CUDA(cudaLaunchKernelEx(&cfg, overlap_tc_smaj_kernel, vst, static_cast<int>(round_up(K, 4)), prm));
+  count_launches(1);
+  reduce_tc_cluster<<<dim3(128 * 128 / 256, static_cast<unsigned>(pl.T)), 256, 0, st>>>(prm.out, pl.S, pl.T, pl.MT,
+                                                                                       static_cast<int>(K), G);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;

@@ -203,6 +203,14 @@ mbar_status hessian(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_
                     const double* logN, const void* logden, const int32_t* H, double* hess, unsigned* err,
                     void* tmp, size_t tmp_bytes, cudaStream_t stream);
 size_t hessian_tmp_bytes(int64_t K, int64_t n);
+// The same Hessian of unbinned FP32 data read from the sample-major copy
+// vst[n][round_up(K, 4)] (logden in that sample order); false from
+// hessian_smaj_eligible when the tensor-core cluster kernel does not take
+// this K (the caller then uses hessian on the row-major store).
+bool hessian_smaj_eligible(int64_t K);
+mbar_status hessian_smaj(const float* vst, int64_t K, int64_t n, const double* f, const double* logN,
+                         const float* logden, double* hess, unsigned* err, void* tmp, size_t tmp_bytes,
+                         cudaStream_t stream);
 
 // Tensor-core overlap matrix (hessian_tc.cu): G[K x K] (FP64, symmetric) =
 // sum_p H_p P_ip P_jp with FP16 operands and FP32 accumulation in TMEM.
@@ -211,6 +219,9 @@ mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int
                        const void* logden, const int32_t* H, double* G, unsigned* err, void* tmp, size_t tmp_bytes,
                        cudaStream_t st);
 size_t overlap_tc_tmp_bytes(int64_t K, int64_t n);
+bool overlap_tc_smaj_eligible(int64_t K);
+mbar_status overlap_tc_smaj(const float* vst, int64_t K, int64_t n, const double* a, const float* logden, double* G,
+                            unsigned* err, void* tmp, size_t tmp_bytes, cudaStream_t st);
 
 // Which contraction hessian() uses: 0 = by size (tensor cores for K >= 64),
 // 1 = CUDA cores, 2 = tensor cores.

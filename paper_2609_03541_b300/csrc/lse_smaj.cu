@@ -61,17 +61,6 @@ constexpr uint32_t kSmSpin = 1u << 28;  // bounded mbarrier polls
 constexpr int kSmFlush = 64;            // sample slots between folds of the FP32 partials
 constexpr int kSmStageBytes = 48 * 1024;
 
-__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 }  // namespace
 
 // LPS lanes per sample, NK float4 chunks per lane, NT threads (warp 0 is
