@@ -46,6 +46,26 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   return __uint_as_float(sign | bits);
 }
 
+// x = hi + lo for the per-sample shift: hi = x truncated toward zero to 24
+// significant bits (the sign, the exponent and the top 23 fraction bits of
+// x, moved by integer operations) and lo = the 29 dropped fraction bits as
+// an FP32 value (one integer-to-float rounding: |lo - exact| <= 2^-48 |x|).
+// About half the integer work of the round-to-nearest split_f64 (no
+// rounding increment, no carry into the exponent). False when hi or the
+// scale of lo would leave the normal binary32 range (|x| outside
+// [2^-74, 2^128)); the caller then uses FP64 arithmetic.
+__device__ __forceinline__ bool split_f64_trunc(double x, float& hi, float& lo) {
+  const unsigned long long d = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned int dh = static_cast<unsigned int>(d >> 32), dl = static_cast<unsigned int>(d);
+  const unsigned int E = (dh >> 20) & 0x7FFu;
+  if (E - 949u > 1150u - 949u) return false;
+  const unsigned int sign = dh & 0x80000000u;
+  hi = __uint_as_float(sign | (((dh & 0x7FFFFFFFu) - 0x38000000u) << 3) | (dl >> 29));
+  const float scale = __uint_as_float((E - 948u) << 23);  // 2^(E - 1075)
+  lo = __uint_as_float(sign ^ __float_as_uint(__uint2float_rn(dl & 0x1FFFFFFFu) * scale));
+  return true;
+}
+
 // Staging at creation, sample-major: block b takes the kStageCols samples
 // n0 = b * kStageCols .. n0 + kStageCols - 1 with all K rows into shared
 // memory (one read of u, 128-byte row pieces), takes each column's minimum
@@ -121,7 +141,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const double* __re
       c[n0 + t] = cm;
       cmin[t] = cm;
       float mh = 0.f, ml = 0.f;
-      msp[t] = (split_f64(cm, mh, ml) || cm == 0.0) ? 1 : 0;
+      msp[t] = (split_f64_trunc(cm, mh, ml) || cm == 0.0) ? 1 : 0;
       mhs[t] = mh;
       mls[t] = ml;
     }
@@ -144,7 +164,7 @@ __global__ void __launch_bounds__(kStageThreads) stage_kernel(const double* __re
         if (k < K) {
           const double x = xs[k * kStagePitch + jj];
           float xh, xl;
-          if (msplit && split_f64(x, xh, xl))
+          if (msplit && split_f64_trunc(x, xh, xl))
             r = __fadd_rn(__fsub_rn(xh, mh), __fsub_rn(xl, ml));
           else
             r = f64_to_f32_rn(x - cm);
@@ -277,7 +297,7 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
       c[n0 + tid] = cm;
       cmin[tid] = cm;
       float mh = 0.f, ml = 0.f;
-      msp[tid] = (split_f64(cm, mh, ml) || cm == 0.0) ? 1 : 0;
+      msp[tid] = (split_f64_trunc(cm, mh, ml) || cm == 0.0) ? 1 : 0;
       mhs[tid] = mh;
       mls[tid] = ml;
     }
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
         if (k < Ki) {
           const double x = *reinterpret_cast<const double*>(xp + (k - r0) * 128);
           float xh, xl;
-          if (msplit && split_f64(x, xh, xl))
+          if (msplit && split_f64_trunc(x, xh, xl))
             r = __fadd_rn(__fsub_rn(xh, mh), __fsub_rn(xl, ml));
           else
             r = f64_to_f32_rn(x - cm);

@@ -1,9 +1,12 @@
 """The FP32 per-sample shift of the mixed-precision store (prep.cu):
 v = (uh - mh) + (ul - ml) from integer hi/lo splits of u and of the column
-minimum m, restated in Python integers and numpy float32 arithmetic. Pinned
-against the exact u - m: within 1.5 units in the last place of fl32(u - m)
-plus 2^-46 max(|u|, |m|) (the binary32 rounding of the residuals), exact
-when the difference is exactly representable in FP32, never negative."""
+minimum m (hi = the value truncated toward zero to 24 significant bits, lo =
+the dropped 29 fraction bits rounded once to FP32), restated in Python
+integers and numpy float32 arithmetic. Pinned against the exact u - m:
+within 1.5 units in the last place of fl32(u - m) plus 2^-46 max(|u|, |m|)
+(the binary32 rounding of the residuals), exact when the difference is
+exactly representable in FP32, never negative. The round-to-nearest split
+of the factorised pass (common.cuh split_f64) is pinned separately."""
 import struct
 
 import numpy as np
@@ -29,9 +32,28 @@ def split(x: float):
     return np.float32(hi), np.float32(lo)
 
 
+def split_trunc(x: float):
+    """prep.cu split_f64_trunc: hi = x truncated to 24 significant bits,
+    lo = RN32 of the 29 dropped fraction bits; None outside the normal range
+    of hi and of lo's scale (|x| outside [2^-74, 2^128))."""
+    d = struct.unpack("<Q", struct.pack("<d", x))[0]
+    dh, dl = d >> 32, d & 0xFFFFFFFF
+    E = (dh >> 20) & 0x7FF
+    if not (949 <= E <= 1150):
+        return None
+    sign = dh & 0x80000000
+    hi_bits = sign | ((((dh & 0x7FFFFFFF) - 0x38000000) << 3) & 0xFFFFFFFF) | (dl >> 29)
+    hi = struct.unpack("<f", struct.pack("<I", hi_bits))[0]
+    scale = struct.unpack("<f", struct.pack("<I", (E - 948) << 23))[0]
+    lo = np.float32(np.float32(dl & 0x1FFFFFFF) * np.float32(scale))
+    if sign:
+        lo = -lo
+    return np.float32(hi), np.float32(lo)
+
+
 def shifted(u: float, m: float) -> np.float32:
-    mu = split(m) if m != 0.0 else (np.float32(0), np.float32(0))
-    su = split(u)
+    mu = split_trunc(m) if m != 0.0 else (np.float32(0), np.float32(0))
+    su = split_trunc(u)
     if mu is None or su is None:
         return np.float32(u - m)
     return np.float32(np.float32(su[0] - mu[0]) + np.float32(su[1] - mu[1]))
@@ -64,6 +86,36 @@ def test_wide_magnitudes_and_the_minimum_itself():
         assert v >= 0.0
         assert within_bound(v, u, m), (u, m, v)
         assert shifted(m, m) == 0.0
+
+
+def test_truncating_split_is_exact_in_its_pair():
+    """hi + lo reproduces x to within the one rounding of lo: hi is x with
+    its low 29 fraction bits cleared (so |hi| <= |x|, same sign) and
+    |hi + lo - x| <= 2^-48 |x|."""
+    g = np.random.default_rng(5)
+    xs = np.concatenate([g.standard_normal(3000) * 10.0 ** g.integers(-20, 30, 3000), [1.0, -1.0, 3.0e5]])
+    for x in xs:
+        r = split_trunc(float(x))
+        if r is None:
+            continue
+        hi, lo = r
+        assert abs(float(hi)) <= abs(float(x)) and np.signbit(hi) == np.signbit(x)
+        assert abs(float(hi) + float(lo) - float(x)) <= 2.0 ** -48 * abs(float(x))
+
+
+def test_binade_boundaries_stay_non_negative():
+    """u just above m across powers of two (where truncated hi parts step to
+    the next exponent) never gives a negative shifted value."""
+    for e in range(-30, 40):
+        for m0 in (2.0 ** e, -(2.0 ** e)):
+            for k in range(1, 40):
+                m = np.nextafter(m0, -np.inf) if k % 2 else m0
+                u = float(m)
+                for _ in range(k):
+                    u = float(np.nextafter(u, np.inf))
+                v = shifted(u, float(m))
+                assert v >= 0.0
+                assert within_bound(v, u, float(m)), (u, m, v)
 
 
 def test_exact_when_the_difference_is_a_float():
