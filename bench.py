@@ -798,7 +798,7 @@ def main():
         f = ctx.free_energies()
         traces.append(ctx.trace())
         if timing and acc is not None:
-            for kind in (0, 1, 2, 3):
+            for kind in (0, 1, 2, 3, 4, 5):
                 n, ms, by = ctx.timing(kind)
                 a = acc.setdefault(kind, [0, 0.0, 0.0])
                 a[0] += n
@@ -958,6 +958,20 @@ def main():
                                           "frac": (by_c / (ms_c / 1e3) / 1e9 / peaks["hbm_gbs"]) if n_c else None}}}
     n_h, ms_h, by_h = acc.get(1, [0, 0.0, 0.0])
     hess = {"launches": n_h, "avg_ms": (ms_h / n_h) if n_h else None}
+    # the binned LSE passes of Algorithm 1: second-loop rounds (each N_int + 2
+    # passes with their epilogues, graph-launched) and one-launch first loops;
+    # achieved = the passes' algorithmic bytes / the rounds' device time
+    binned = {}
+    for kind, name in ((4, "second_loop_rounds"), (5, "first_loop")):
+        n_b, ms_b, by_b = acc.get(kind, [0, 0.0, 0.0])
+        if n_b:
+            gbs = by_b / (ms_b / 1e3) / 1e9
+            binned[name] = {"launches": n_b, "avg_ms": ms_b / n_b, "bytes_per_launch": by_b / n_b,
+                            "achieved_GBps": gbs, "frac": gbs / peaks["hbm_gbs"]}
+    # shares of the timed step: the LSE family's device time per step
+    lse_ms = (ms_l + acc.get(4, [0, 0.0, 0.0])[1] + acc.get(5, [0, 0.0, 0.0])[1]) / args.steps
+    binned["lse_family_ms_per_step"] = lse_ms
+    binned["lse_family_share_of_step"] = lse_ms / ms_per_step
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -994,7 +1008,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == M.MBAR_MIXED else "f64", "data": "synthetic",
                 "config": config, "e2e": e2e, "e2e_factorised": e2e_fact, "gpu_launches": launches,
-                "roofline": roofline,
+                "roofline": roofline, "binned_lse": binned,
                 "latency": latency, "hessian": hess, "cpu_baseline": cpu, "clocks": clocks, "accuracy": accuracy,
                 "reweight": rew,
                 "report": rep.as_dict()}

@@ -247,7 +247,12 @@ BUMBAR_API const char* mbar_last_error(void);
  *   0 = unbinned fused LSE passes, 1 = Hessian, 2 = FP64 Newton solve,
  *   3 = unbinned passes that only confirm a Newton step below f_tol (FP32
  *       data: plain FP32 sums instead of the exact split of each sample's
- *       largest weight that kind 0 uses);
+ *       largest weight that kind 0 uses),
+ *   4 = rounds of Algorithm 1's second loop (N_intermediate + 1 passes over
+ *       the current binned level and one over the next; bytes = the data
+ *       those passes read),
+ *   5 = one-launch runs of the first loop on a small FP32 level (bytes =
+ *       steps taken x the level's data);
  * launches, total_ms (device time) and bytes (K x n x element size of the
  * data each launch streams; K x K x 8 for the solve) are all nullable. */
 BUMBAR_API mbar_status mbar_set_timing(mbar_ctx* ctx, int32_t enable);

@@ -51,6 +51,7 @@ struct Level {
   int64_t* keys = nullptr;
   double w = 0.0;
   int64_t n_sched = 0;  // n used by Algorithm 1's break rule
+  bool fact = false;    // unbinned data of a factorised context: generated from (a, b, phi), no store
   CUtensorMap tmap;
 };
 
@@ -76,6 +77,12 @@ struct mbar_ctx {
   // the plain FP32 sums suffice (every other unbinned pass splits each
   // sample's largest weight into an exact count and its remainder)
   bool confirm_only = false;
+  // factorised context (u_kn = a_k + b_k phi_n, MIXED): no K x N store; the
+  // binned levels are generated from a, b and the bin means of phi, the
+  // unbinned passes and the Hessian read phi (original sample order)
+  bool fact = false;
+  double *fa = nullptr, *fb = nullptr, *fphi = nullptr;
+  double* logden64 = nullptr;  // logden of the factorised unbinned passes (FP64, original order)
   int64_t ld = 0;
   double* cshift = nullptr;  // mixed: per-column shift (current order)
   int32_t* perm = nullptr;   // current column -> original sample
@@ -191,7 +198,13 @@ void time_mark(mbar_ctx* c, bool begin, int kind, double bytes) {
     cudaEventRecord(r.a, c->st);
     c->recs.push_back(r);
   } else {
-    cudaEventRecord(c->recs.back().b, c->st);
+    // the most recent record of this kind (brackets of other kinds may nest
+    // inside, e.g. an unbinned pass inside a second-loop round)
+    for (auto it = c->recs.rbegin(); it != c->recs.rend(); ++it)
+      if (it->kind == kind) {
+        cudaEventRecord(it->b, c->st);
+        break;
+      }
   }
 }
 
@@ -228,10 +241,18 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
   p.skip_if_done = skip_if_done;
   p.skip_if_underflow = mode == kLseModeSci ? 1 : 0;
   const bool timed = !L.binned;
-  const int tkind = (c->confirm_only && c->smaj && c->vst) ? 3 : 0;
-  if (timed) time_mark(c, true, tkind, static_cast<double>(c->K) * L.n * c->dtype);
+  const int tkind = (c->confirm_only && ((c->smaj && c->vst) || c->fact)) ? 3 : 0;
+  // bytes the pass reads: the level's data, or phi for factorised data
+  if (timed) time_mark(c, true, tkind, c->fact ? 8.0 * L.n : static_cast<double>(c->K) * L.n * c->dtype);
   mbar_status s = MBAR_OK;
-  if (!L.binned && c->smaj && c->vst) {
+  if (!L.binned && c->fact) {
+    // factorised context: u generated from (a, b, phi) in registers; logden
+    // in FP64 and the original sample order
+    p.H = nullptr;
+    p.logden = logden_out ? c->logden64 : nullptr;
+    p.exact_max = c->confirm_only ? 0 : 1;
+    s = lse_fact_launch(c->fa, c->fb, c->fphi, lse_fact_plan(c->K, L.n), p, c->st);
+  } else if (!L.binned && c->smaj && c->vst) {
     // unbinned MIXED pass over the sample-major copy (original sample order);
     // logden comes back to the store's column order through perm
     p.logden = logden_out ? c->logden_orig : nullptr;
@@ -279,6 +300,11 @@ bool take_underflow(mbar_ctx* c) {
 // pass over the level, then log Q_k = LSE_p(log H_p + a_k - v_kp - logden_p).
 mbar_status log_sci_step(mbar_ctx* c, const Level& L, const double* f_in, double* f_out, double* g_out,
                          double* s_out, double eps, double* d_out, double noise) {
+  if (!L.binned && c->fact) {
+    set_error("a step on the unbinned factorised data underflowed (a state lost all weight); the log-domain redo "
+              "needs a stored level");
+    return MBAR_ENOTCONV;
+  }
   BUMBAR_TRY(run_lse(c, L, f_in, kLseModePass, nullptr, nullptr, nullptr, 0.0, 0, c->logden));
   LseParams p{};
   p.K = static_cast<int>(c->K);
@@ -323,6 +349,9 @@ mbar_status sci_step_exact(mbar_ctx* c, const Level& L, const double* f_in, doub
 // (contiguous 64-sample runs for the kernel's TMA boxes; logden in that
 // order); everything else the level's row-major store.
 mbar_status level_hessian(mbar_ctx* c, const Level& L, const double* f, void* tmp, size_t htmp) {
+  if (!L.binned && c->fact)
+    return hessian_fact(c->fa, c->fb, c->fphi, c->K, L.n, f, c->logN_d, c->logden64, c->hess, err_word(c), tmp, htmp,
+                        c->st);
   if (!L.binned && c->smaj && c->vst && c->dtype == 4 && hessian_smaj_eligible(c->K))
     return hessian_smaj(static_cast<const float*>(c->vst), c->K, L.n, f, c->logN_d,
                         static_cast<const float*>(c->logden_orig), c->hess, err_word(c), tmp, htmp, c->st);
@@ -334,6 +363,8 @@ mbar_status ensure_sorted(mbar_ctx* c);
 
 // Histogram at width w over the sorted coordinate -> a binned level.
 mbar_status make_level_w_impl(mbar_ctx* c, double w, Level* L);
+mbar_status fill_level_stores(mbar_ctx* c, int L, const int32_t* const* seg, const int32_t* const* start,
+                              const int64_t* nb, void* const* out, const int64_t* ld);
 
 mbar_status make_level_w(mbar_ctx* c, double w, Level* L) {
   const double t0 = now_s();
@@ -377,8 +408,18 @@ mbar_status make_level_w_impl(mbar_ctx* c, double w, Level* L) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->keys, keys_full, nb * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->st);
     if (e != cudaSuccess) s = cuda_status(e, "histogram copy");
   }
-  if (s == MBAR_OK)
-    s = bin_means(c->v, c->dtype, c->K, c->N, c->ld, c->seg, c->start, nb, L->v, L->ld, tmp, mtmp, c->st);
+  if (s == MBAR_OK) {
+    if (c->fact) {
+      const int32_t* sg1 = c->seg;
+      const int32_t* st1 = c->start;
+      const int64_t nb1 = nb;
+      void* out1 = L->v;
+      const int64_t ld1 = L->ld;
+      s = fill_level_stores(c, 1, &sg1, &st1, &nb1, &out1, &ld1);
+    } else {
+      s = bin_means(c->v, c->dtype, c->K, c->N, c->ld, c->seg, c->start, nb, L->v, L->ld, tmp, mtmp, c->st);
+    }
+  }
   if (s == MBAR_OK) s = level_tmap(c, L);
   dfree(c, tmp);
   dfree(c, keys_full);
@@ -430,7 +471,7 @@ mbar_status form_store(mbar_ctx* c, const int32_t* perm) {
 // The unbinned store in the current column order (the identity until a
 // coordinate is set).
 mbar_status ensure_store(mbar_ctx* c) {
-  if (c->v) return MBAR_OK;
+  if (c->v || c->fact) return MBAR_OK;
   return form_store(c, c->perm);
 }
 
@@ -690,8 +731,13 @@ mbar_status first_loop_fused(mbar_ctx* c, const Level& L, mbar_report* rep) {
   int64_t done_iters = 0;
   while (s == MBAR_OK) {
     q.max_steps = c->opts.max_sci - done_iters;
+    time_mark(c, true, 5, 0.0);
     s = sci_loop_launch(vT, q, c->st);
+    time_mark(c, false, 5, 0.0);
     if (s == MBAR_OK) s = read_status(c);
+    // the launch streamed the level once per step it took
+    if (s == MBAR_OK && c->timing && !c->recs.empty())
+      c->recs.back().bytes = static_cast<double>(c->hstat->ctrl.iters - done_iters) * c->K * L.n * 4.0;
     if (s != MBAR_OK) break;
     const bool redo = take_underflow(c);
     if (redo) {
@@ -903,6 +949,47 @@ mbar_status plan_level(mbar_ctx* c, int idx, bool* binned, double* w, int64_t* n
   return MBAR_OK;
 }
 
+// The FP32/FP64 stores of L binned levels (segments seg[l], run starts
+// start[l], nb[l] bins): bin means of the unbinned store in one read, or for
+// a factorised context the bin means of the sorted coordinate and the
+// stores generated from them (a_k + b_k phibar_b).
+mbar_status fill_level_stores(mbar_ctx* c, int L, const int32_t* const* seg, const int32_t* const* start,
+                              const int64_t* nb, void* const* out, const int64_t* ld) {
+  const int64_t N = c->N, K = c->K;
+  if (L <= 0) return MBAR_OK;
+  if (!c->fact) {
+    void* mt = nullptr;
+    const size_t mbytes = bin_means_multi_tmp_bytes(K, N, L, nb);
+    BUMBAR_TRY(dalloc(c, &mt, mbytes));
+    const mbar_status s = bin_means_multi(c->v, c->dtype, K, N, c->ld, L, seg, start, nb, out, ld, mt, mbytes, c->st);
+    dfree(c, mt);
+    return s;
+  }
+  std::vector<double*> phibar(L, nullptr);
+  std::vector<void*> pout(L);
+  std::vector<int64_t> pld(L);
+  mbar_status s = MBAR_OK;
+  size_t gen_bytes = 0;
+  for (int l = 0; l < L && s == MBAR_OK; ++l) {
+    s = dalloc_t(c, &phibar[l], std::max<int64_t>(nb[l], 1));
+    pout[l] = phibar[l];
+    pld[l] = nb[l];
+    gen_bytes = std::max(gen_bytes, fact_level_tmp_bytes(K, nb[l]));
+  }
+  void* mt = nullptr;
+  const size_t mbytes = std::max(bin_means_multi_tmp_bytes(1, N, L, nb), gen_bytes);
+  if (s == MBAR_OK) s = dalloc(c, &mt, mbytes);
+  // the coordinate is the one-row "store" whose bin means are phibar
+  if (s == MBAR_OK)
+    s = bin_means_multi(c->phi_sorted, 8, 1, N, N, L, seg, start, nb, pout.data(), pld.data(), mt,
+                        bin_means_multi_tmp_bytes(1, N, L, nb), c->st);
+  for (int l = 0; l < L && s == MBAR_OK; ++l)
+    s = fact_level_store(c->fa, c->fb, phibar[l], K, nb[l], static_cast<float*>(out[l]), ld[l], mt, c->st);
+  dfree(c, mt);
+  for (double* q : phibar) dfree(c, q);
+  return s;
+}
+
 // Every level Algorithm 1 can visit, built up front: the histograms one by
 // one (each needs only the sorted coordinate), then all bin means in one read
 // of the data. Level 0 and 1 always; level 2 when level 1 is binned; level
@@ -1029,13 +1116,7 @@ mbar_status prebuild_levels(mbar_ctx* c, std::vector<Level>* levels) {
   }
   const int L = static_cast<int>(sg.size());
   if (L > 0) {
-    void* mt = nullptr;
-    const size_t mbytes = bin_means_multi_tmp_bytes(K, N, L, nbs.data());
-    s = dalloc(c, &mt, mbytes);
-    if (s == MBAR_OK)
-      s = bin_means_multi(c->v, c->dtype, K, N, c->ld, L, sg.data(), stt.data(), nbs.data(), outs.data(), lds.data(),
-                          mt, mbytes, c->st);
-    dfree(c, mt);
+    s = fill_level_stores(c, L, sg.data(), stt.data(), nbs.data(), outs.data(), lds.data());
     if (s != MBAR_OK) return fail(s);
   }
   c->t_levels += now_s() - t0;
@@ -1165,6 +1246,11 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
       if (s != MBAR_OK) break;
       captured = true;
     }
+    // algorithmic bytes of a round: N_intermediate + 1 passes over the
+    // current level and one over the next
+    time_mark(c, true, 4,
+              static_cast<double>(K) * c->dtype *
+                  ((o.n_intermediate + 1.0) * static_cast<double>(cur.n) + static_cast<double>(nxt.n)));
     if (use_graph) {
       cudaError_t e = cudaGraphLaunch(g.exec, c->st);
       if (e != cudaSuccess) {
@@ -1175,6 +1261,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
     } else {
       s = round_body();
     }
+    time_mark(c, false, 4, 0.0);
     if (s == MBAR_OK) s = read_status(c);
     if (s == MBAR_OK && take_underflow(c)) {
       // the round stopped at step `first`: that step exactly, then the rest
@@ -1330,10 +1417,18 @@ mbar_status mbar_opts_default(mbar_opts* o, int32_t precision) {
   return MBAR_OK;
 }
 
-mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
-                        int32_t u_on_device, const mbar_opts* opts, void* cuda_stream) {
-  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
-  if (!out || !N_k || !u_kn) {
+}  // extern "C"
+
+namespace {
+
+// Context creation from u_kn (dense) or, with fa != nullptr, from the
+// factorised form u_kn = fa_k + fb_k fphi_n without any K x N store (MIXED,
+// K <= 512: the caller checks).
+mbar_status create_impl(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
+                        int32_t u_on_device, const double* fa_in, const double* fb_in, const double* fphi_in,
+                        const mbar_opts* opts, void* cuda_stream) {
+  const bool fact = fa_in != nullptr;
+  if (!out || !N_k || (!fact && !u_kn)) {
     set_error("mbar_create: null pointer argument");
     return MBAR_EINVAL;
   }
@@ -1448,6 +1543,76 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
 
   if (cudaMemsetAsync(c->bad, 0, sizeof(int), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
   if (cudaMemsetAsync(c->f, 0, K * sizeof(double), c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+  if (fact) {
+    c->fact = true;
+    TRYC(dalloc_t(c, &c->fa, K));
+    TRYC(dalloc_t(c, &c->fb, K));
+    TRYC(dalloc_t(c, &c->fphi, N));
+    const cudaMemcpyKind kind = u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(c->fa, fa_in, K * sizeof(double), kind, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(c->fb, fb_in, K * sizeof(double), kind, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(c->fphi, fphi_in, N * sizeof(double), kind, c->st) != cudaSuccess)
+      return fail(cuda_status(cudaGetLastError(), "mbar_create_factorised: upload"));
+    TRYC(check_finite(c->fa, K, c->bad, c->st));
+    TRYC(check_finite(c->fb, K, c->bad, c->st));
+    TRYC(check_finite(c->fphi, N, c->bad, c->st));
+    TRYC(dalloc_t(c, &c->logden64, N));
+    TRYC(dalloc(c, &c->logden, static_cast<size_t>(N) * c->dtype));  // binned levels
+    TRYC(dalloc_t(c, &c->perm, N));
+    TRYC(dalloc_t(c, &c->seg, N));
+    TRYC(dalloc_t(c, &c->start, N + 1));
+    TRYC(dalloc_t(c, &c->phi_sorted, N));
+    TRYC(dalloc_t(c, &c->d_sorted, N));
+    TRYC(dalloc_t(c, &c->d_pairs, N));
+    // the coordinate is phi: sorted once here (the samples themselves are
+    // never reordered, so perm stays the identity)
+    {
+      std::vector<int32_t> id(N);
+      std::iota(id.begin(), id.end(), 0);
+      if (cudaMemcpyAsync(c->perm, id.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+        return fail(cuda_status(cudaGetLastError(), "mbar_create_factorised: identity"));
+      const size_t stmp = sort_tmp_bytes(N);
+      void* tmp = nullptr;
+      int32_t* order = nullptr;
+      s = dalloc(c, &tmp, stmp);
+      if (s == MBAR_OK) s = dalloc_t(c, &order, N);
+      if (s == MBAR_OK) s = sort_coordinate(c->fphi, N, c->phi_sorted, order, tmp, stmp, c->st);
+      if (s == MBAR_OK) s = offsets_from_min(c->phi_sorted, N, c->d_sorted, c->d_pairs, c->st);
+      if (s == MBAR_OK && (cudaMemcpyAsync(&c->phi_lo, c->phi_sorted, sizeof(double), cudaMemcpyDeviceToHost,
+                                           c->st) != cudaSuccess ||
+                           cudaMemcpyAsync(&c->phi_hi, c->phi_sorted + N - 1, sizeof(double), cudaMemcpyDeviceToHost,
+                                           c->st) != cudaSuccess))
+        s = cuda_status(cudaGetLastError(), "coordinate range");
+      int bad = 0;
+      if (s == MBAR_OK && cudaMemcpyAsync(&bad, c->bad, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        s = MBAR_ECUDA;
+      if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = cuda_status(cudaGetLastError(), "create");
+      dfree(c, tmp);
+      dfree(c, order);
+      if (s == MBAR_OK && bad) {
+        set_error("mbar_create_factorised: a, b or phi has non-finite entries");
+        s = MBAR_EINVAL;
+      }
+      if (s != MBAR_OK) return fail(s);
+      c->sorted = true;
+    }
+    {
+      const int grid = std::max(lse_plan(K, N, c->dtype).grid, lse_fact_plan(K, N).grid);
+      c->scratch_bytes = lse_scratch_for_grid(K, grid);
+      TRYC(dalloc(c, &c->scratch, c->scratch_bytes));
+      if (cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->st) != cudaSuccess) return fail(MBAR_ECUDA);
+    }
+    c->full.binned = false;
+    c->full.fact = true;
+    c->full.n = N;
+    c->full.ld = N;
+    c->full.v = nullptr;
+    c->full.n_sched = N;
+    c->cur = c->full;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(cuda_status(cudaGetLastError(), "mbar_create"));
+    *out = c;
+    return MBAR_OK;
+  }
   TRYC(dalloc(c, &c->vst, static_cast<size_t>(stage_pitch(K)) * N * c->dtype + 16));
   c->smaj = c->dtype == 4 && lse_smaj_preferred(K);
   if (c->smaj) TRYC(dalloc_t(c, &c->logden_orig, N));
@@ -1514,6 +1679,21 @@ mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   return MBAR_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
+                        int32_t u_on_device, const mbar_opts* opts, void* cuda_stream) {
+  cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
+  if (!u_kn) {
+    set_error("mbar_create: null pointer argument");
+    if (out) *out = nullptr;
+    return MBAR_EINVAL;
+  }
+  return create_impl(out, K, N, N_k, u_kn, u_on_device, nullptr, nullptr, nullptr, opts, cuda_stream);
+}
+
 mbar_status mbar_create_factorised(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* a,
                                    const double* b, const double* phi, int32_t on_device, const mbar_opts* opts,
                                    void* cuda_stream) {
@@ -1526,6 +1706,17 @@ mbar_status mbar_create_factorised(mbar_ctx** out, int64_t K, int64_t N, const i
   if (K < 1 || N < 1 || K > 1024 || N > 2000000000LL) {
     set_error("mbar_create_factorised: bad sizes K=%lld N=%lld", (long long)K, (long long)N);
     return K > 1024 || N > 2000000000LL ? MBAR_EUNSUPPORTED : MBAR_EINVAL;
+  }
+  {
+    // MIXED with K <= 512: the store-free factorised context
+    mbar_opts o;
+    if (opts) {
+      o = *opts;
+    } else {
+      mbar_opts_default(&o, MBAR_MIXED);
+    }
+    if (o.precision == MBAR_MIXED && K <= 512 && o.use_binning)
+      return create_impl(out, K, N, N_k, nullptr, on_device, a, b, phi, &o, cuda_stream);
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double* buf = nullptr;  // [a | b | phi] when given on the host, then u
@@ -1583,6 +1774,10 @@ mbar_status mbar_create_factorised(mbar_ctx** out, int64_t K, int64_t N, const i
 mbar_status mbar_set_coordinate(mbar_ctx* c, const double* phi, int32_t phi_on_device) {
   cudaGetLastError();  // drop stale errors of earlier, unrelated runtime calls
   CHECK_CTX(c);
+  if (c->fact) {
+    set_error("mbar_set_coordinate: the bin coordinate of a factorised context is its phi");
+    return MBAR_EUNSUPPORTED;
+  }
   StreamFence fence(c);
   if (!phi) {
     set_error("mbar_set_coordinate: phi is NULL");
@@ -1713,7 +1908,10 @@ mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double
   std::vector<unsigned char> raw;
   std::vector<int32_t> perm;
   std::vector<double> shift;
-  if (logden) {
+  const bool fact_ld = c->fact && !c->cur.binned;  // FP64, original sample order
+  if (logden && fact_ld) {
+    BUMBAR_CUDA(cudaMemcpyAsync(logden, c->logden64, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  } else if (logden) {
     raw.resize(static_cast<size_t>(n) * c->dtype);
     BUMBAR_CUDA(cudaMemcpyAsync(raw.data(), c->logden, raw.size(), cudaMemcpyDeviceToHost, c->st));
     if (!c->cur.binned) {
@@ -1726,7 +1924,7 @@ mbar_status mbar_sci_step(mbar_ctx* c, const double* f_in, double* f_out, double
     }
   }
   BUMBAR_CUDA(cudaStreamSynchronize(c->st));
-  if (logden) {
+  if (logden && !fact_ld) {
     for (int64_t i = 0; i < n; ++i) {
       double v = c->dtype == 4 ? static_cast<double>(reinterpret_cast<float*>(raw.data())[i])
                                : reinterpret_cast<double*>(raw.data())[i];
@@ -1917,8 +2115,10 @@ mbar_status mbar_reweight(mbar_ctx* c, const double* u0, int32_t u0_on_device, d
   }
   if (s == MBAR_OK) s = run_lse(c, c->full, c->f, kLseModePass, nullptr, nullptr, nullptr, 0.0, 0, c->logden);
   if (s == MBAR_OK)
-    s = reweight_weights(u0d, c->perm, c->logden, c->dtype, c->cshift, N, c->weights, logc_dev, tmp,
-                         reweight_tmp_bytes(N), c->st);
+    s = c->fact ? reweight_weights(u0d, c->perm, c->logden64, 8, nullptr, N, c->weights, logc_dev, tmp,
+                                   reweight_tmp_bytes(N), c->st)
+                : reweight_weights(u0d, c->perm, c->logden, c->dtype, c->cshift, N, c->weights, logc_dev, tmp,
+                                   reweight_tmp_bytes(N), c->st);
   double logc = 0.0;
   if (s == MBAR_OK && p_out &&
       cudaMemcpyAsync(p_out, c->weights, N * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
@@ -2055,7 +2255,7 @@ mbar_status mbar_destroy(mbar_ctx* c) {
   void* ptrs[] = {c->weights, c->Nk_d, c->logN_d, c->v, c->vst, c->logden_orig, c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->d_pairs, c->f,
                   c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->stat,
                   c->hess, c->delta,  c->info,  c->bad,    c->logden,  c->scratch,    c->seg,
-                  c->start, c->count, c->nb_dev};
+                  c->start, c->count, c->nb_dev, c->fa, c->fb, c->fphi, c->logden64};
   if (c->st) {
     for (void* p : ptrs) dfree(c, p);
     cudaStreamSynchronize(c->st);
@@ -2204,6 +2404,7 @@ mbar_status mbar_lse_pass_factorised(const double* a, const double* b, const dou
   p.Q = Q;
   p.logden = logden;
   p.mode = kLseModePass;
+  p.exact_max = 1;
   return lse_fact_launch(a, b, phi, lse_fact_plan(K, n), p, static_cast<cudaStream_t>(stream));
 }
 

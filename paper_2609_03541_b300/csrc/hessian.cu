@@ -206,6 +206,28 @@ mbar_status hessian_smaj(const float* vst, int64_t K, int64_t n, const double* f
   return MBAR_OK;
 }
 
+mbar_status hessian_fact(const double* fa, const double* fb, const double* fphi, int64_t K, int64_t n,
+                         const double* f, const double* logN, const double* logden, double* hess, unsigned* err,
+                         void* tmp, size_t tmp_bytes, cudaStream_t st) {
+  if (tmp_bytes < hessian_tmp_bytes(K, n)) {
+    set_error("hessian: scratch too small");
+    return MBAR_EINVAL;
+  }
+  const SimtPlan p = simt_plan(K, n);
+  const size_t simt = round_up(static_cast<int64_t>(p.nslices) * p.npairs * kTile * kTile * 4, 256);
+  const size_t tc = overlap_tc_tmp_bytes(K, n) + round_up(K * 8, 256);
+  double* G = reinterpret_cast<double*>(static_cast<unsigned char*>(tmp) + std::max(simt, tc));
+  double* a = static_cast<double*>(tmp);
+  unsigned char* rest = static_cast<unsigned char*>(tmp) + round_up(K * 8, 256);
+  add_vectors<<<static_cast<unsigned>(ceil_div(K, 256)), 256, 0, st>>>(f, logN, a, K);
+  count_launches(1);
+  BUMBAR_TRY(overlap_tc_fact(fa, fb, fphi, K, n, a, logden, G, err, rest, overlap_tc_tmp_bytes(K, n), st));
+  laplacian_from_overlap<<<static_cast<unsigned>(K), kThreads, 0, st>>>(G, K, hess);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
 mbar_status hessian(const void* v, int dtype_bytes, int64_t K, int64_t n, int64_t ld, const double* f,
                     const double* logN, const void* logden, const int32_t* H, double* hess, unsigned* err,
                     void* tmp, size_t tmp_bytes, cudaStream_t st) {

@@ -972,6 +972,190 @@ __global__ void __launch_bounds__(kSmjThreadsAll, 1)
   }
 }
 
+// The same contraction for a factorised context (u_ip = a_i + b_i phi_p, no
+// K x N store): P~ is formed from a, b, phi and the pass's FP64 logden (all
+// in the original sample order); the exponent is FP32 at the magnitude of
+// the cancelling terms (~1e-4 absolute on tempering energies), below the
+// FP16 rounding of P~.
+__global__ void __launch_bounds__(kSmjThreadsAll, 1)
+    overlap_tc_fact_kernel(const double* __restrict__ fa, const double* __restrict__ fb,
+                           const double* __restrict__ fphi, const double* __restrict__ logden, ClParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* pbuf = smem;
+  uint64_t* pfull = reinterpret_cast<uint64_t*>(pbuf + kSmjPStages * kClPStageBytes);  // [kSmjPStages]
+  uint64_t* pempty = pfull + kSmjPStages;                                              // [kSmjPStages]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pempty + kSmjPStages);
+  volatile int* fail_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const bool producer = tid < kClThreads;
+  const int MT = p.MT;
+  const int r = static_cast<int>(cluster_ctarank());
+  const int64_t slice = blockIdx.x / MT;
+  const int dm = cl_dmax(r, MT);
+  const int ntl = dm + 1;
+  const uint32_t ncols = ntl == 1 ? 128u : (ntl == 2 ? 256u : 512u);
+  uint32_t reader_mask = 0;
+  for (int q = 0; q < MT; ++q)
+    if ((r - q + MT) % MT <= cl_dmax(q, MT)) reader_mask |= 1u << q;
+  const int nreaders = __popc(reader_mask);
+  uint16_t writer_mask = 0;
+  for (int d = 0; d <= dm; ++d) writer_mask |= static_cast<uint16_t>(1u << ((r + d) % MT));
+  const int64_t c_begin = slice * p.per;
+  const int64_t c_end = (c_begin + p.per < p.n) ? c_begin + p.per : p.n;
+  const int64_t nchunks = c_end > c_begin ? (c_end - c_begin + 63) / 64 : 0;
+
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  if (tid == 0) {
+    for (int b = 0; b < kSmjPStages; ++b) {
+      // one chunk is delivered by the four warps of one group of each writer
+      mbar_init(&pfull[b], static_cast<uint32_t>((dm + 1) * (kClWarps / kSmjGroups)));
+      mbar_init(&pempty[b], static_cast<uint32_t>(nreaders));
+    }
+    *fail_s = 0;
+    fence_barrier_init();
+  }
+  const int grp = warp / (kClWarps / kSmjGroups);   // chunk group
+  const int lr = 32 * (warp % (kClWarps / kSmjGroups)) + lane;   // row (state) of tile r
+  const int row = r * 128 + lr;
+  // x_ip = (f_i + log N_i - a_i) log2(e) - b_i log2(e) phi_p - log2(e) logden_p
+  const bool live = producer && row < p.K;
+  const float c2 = live ? static_cast<float>((p.a[row] - fa[row]) * 1.4426950408889634) : -INFINITY;
+  const float b2 = live ? static_cast<float>(fb[row] * 1.4426950408889634) : 0.f;
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = idesc_f16(128, 128);
+
+  if (producer) {
+    // phi and log2(e) logden of samples lane and lane + 32 of chunk cc
+    // (padding: logden +inf)
+    auto load_cols = [&](int64_t cc, float& pa, float& pb, float& la, float& lb) {
+      const int64_t s0 = c_begin + cc * 64;
+      const int ns = static_cast<int>(c_end - s0 < 64 ? c_end - s0 : 64);
+      pa = lane < ns ? static_cast<float>(fphi[s0 + lane]) : 0.f;
+      pb = lane + 32 < ns ? static_cast<float>(fphi[s0 + lane + 32]) : 0.f;
+      la = lane < ns ? static_cast<float>(logden[s0 + lane] * 1.4426950408889634) : INFINITY;
+      lb = lane + 32 < ns ? static_cast<float>(logden[s0 + lane + 32] * 1.4426950408889634) : INFINITY;
+    };
+    // the chunk's columns are loaded during the group's previous chunk (after
+    // its fence: a proxy fence also waits for this thread's loads in flight)
+    float pa = 0.f, pb = 0.f, l2a = INFINITY, l2b = INFINITY;
+    if (grp < nchunks) load_cols(grp, pa, pb, l2a, l2b);
+    for (int64_t c = grp; c < nchunks; c += kSmjGroups) {
+      const int b = static_cast<int>(c % kSmjPStages);
+      bool ok = true;
+      if (c >= kSmjPStages) {
+        if (lane == 0)
+          ok = mbar_wait_cluster_bounded(&pempty[b], static_cast<uint32_t>(((c - kSmjPStages) / kSmjPStages) & 1),
+                                         kMaxSpins);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      }
+      if (!__all_sync(0xffffffffu, ok && *fail_s == 0)) {
+        if (lane == 0) *fail_s = 1;
+        break;
+      }
+      unsigned char* pst = pbuf + b * kClPStageBytes;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        float pv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int sj = 8 * k + j;
+          const float l2 = __shfl_sync(0xffffffffu, sj < 32 ? l2a : l2b, sj & 31);
+          const float ph = __shfl_sync(0xffffffffu, sj < 32 ? pa : pb, sj & 31);
+          pv[j] = ex2_approx(fmaf(-b2, ph, c2) - l2);
+        }
+        uint4 packed;
+        packed.x = pack_half2(pv[0], pv[1]);
+        packed.y = pack_half2(pv[2], pv[3]);
+        packed.z = pack_half2(pv[4], pv[5]);
+        packed.w = pack_half2(pv[6], pv[7]);
+        const uint32_t off = static_cast<uint32_t>(lr * 128 + ((k ^ (lr & 7)) << 4));
+#pragma unroll
+        for (int q = 0; q < kClMaxTiles; ++q) {
+          if (reader_mask & (1u << q)) {
+            const int slot = (r - q + MT) % MT;
+            if (q == r)
+              *reinterpret_cast<uint4*>(pst + off) = packed;
+            else
+              st_cluster_v4(mapa_shared(smem_u32(pst + slot * kClPSlotBytes) + off, static_cast<uint32_t>(q)), packed);
+          }
+        }
+      }
+      fence_proxy_async_smem_cluster();
+      __syncwarp();
+      if (lane == 0)
+        for (int q = 0; q < MT; ++q)
+          if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
+      if (c + kSmjGroups < nchunks) load_cols(c + kSmjGroups, pa, pb, l2a, l2b);
+    }
+  } else {
+    for (int64_t cm = 0; cm < nchunks; ++cm) {
+      const int b = static_cast<int>(cm % kSmjPStages);
+      bool ok = true;
+      if (lane == 0)
+        ok = mbar_wait_cluster_bounded(&pfull[b], static_cast<uint32_t>((cm / kSmjPStages) & 1), kMaxSpins);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || *fail_s) {
+        if (lane == 0) *fail_s = 1;
+        break;
+      }
+      if (lane == 0) {
+        tc_fence_after();
+        const uint32_t base = smem_u32(pbuf + b * kClPStageBytes);
+        for (int t = 0; t < ntl; ++t) {
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)
+            umma_f16(tmem + static_cast<uint32_t>(t * 128), sdesc_sw128(base + k4 * 32),
+                     sdesc_sw128(base + static_cast<uint32_t>(t * kClPSlotBytes) + k4 * 32), idesc,
+                     (cm > 0 || k4 > 0) ? 1u : 0u);
+        }
+        umma_commit_multicast(&pempty[b], writer_mask);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  bool failed = *fail_s != 0;
+  if (!failed && nchunks > 0) {
+    bool ok = true;
+    for (int64_t last = nchunks - 1; last >= 0 && last >= nchunks - kSmjPStages; --last)
+      ok = ok && mbar_wait_cluster_bounded(&pempty[last % kSmjPStages],
+                                           static_cast<uint32_t>((last / kSmjPStages) & 1), kMaxSpins);
+    if (__syncthreads_or(!ok)) failed = true;
+  }
+  if (failed && tid == 0) atomicAdd(p.err, 1u);
+  tc_fence_after();
+  float* out = p.out + (slice * p.T + cl_tile_base(r, MT)) * 128 * 128;
+  const int sub = warp & 3;
+  const int quarter = warp >> 2;
+  const int row_local = sub * 32 + lane;
+  for (int c0 = quarter * 32; producer && c0 < ntl * 128; c0 += 128) {
+    float rr[32];
+    if (nchunks > 0 && !failed) {
+      tmem_ld32(tmem + (static_cast<uint32_t>(sub * 32) << 16) + static_cast<uint32_t>(c0), rr);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) rr[i] = 0.f;
+    }
+    float4* dst = reinterpret_cast<float4*>(out + (c0 >> 7) * 128 * 128 + row_local * 128 + (c0 & 127));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[i] = make_float4(rr[4 * i], rr[4 * i + 1], rr[4 * i + 2], rr[4 * i + 3]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
 // Fixed-order FP64 sum of the slices of each accumulator tile; tile
 // (q, d) is G's block (q, (q + d) mod MT), mirrored into its transpose.
 __global__ void reduce_tc_cluster(const float* __restrict__ part, int S, int T, int MT, int K,
@@ -1300,6 +1484,83 @@ mbar_status overlap_tc_smaj(const float* vst, int64_t K, int64_t n, const double
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   BUMBAR_CUDA(cudaLaunchKernelEx(&cfg, overlap_tc_smaj_kernel, vst, static_cast<int>(round_up(K, 4)), prm));
+  count_launches(1);
+  reduce_tc_cluster<<<dim3(128 * 128 / 256, static_cast<unsigned>(pl.T)), 256, 0, st>>>(prm.out, pl.S, pl.T, pl.MT,
+                                                                                       static_cast<int>(K), G);
+  count_launches(1);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
+mbar_status overlap_tc_fact(const double* fa, const double* fb, const double* fphi, int64_t K, int64_t n,
+                            const double* a, const double* logden, double* G, unsigned* err, void* tmp,
+                            size_t tmp_bytes, cudaStream_t st) {
+  if (K < 1 || K > 128 * kClMaxTiles) {
+    set_error("overlap_tc_fact: unsupported K=%lld", static_cast<long long>(K));
+    return MBAR_EUNSUPPORTED;
+  }
+  if (tmp_bytes < overlap_tc_tmp_bytes(K, n)) {
+    set_error("overlap_tc_fact: scratch too small");
+    return MBAR_EINVAL;
+  }
+  const int MT = static_cast<int>(ceil_div(K, 128));
+  const size_t smem = static_cast<size_t>(kSmjPStages) * kClPStageBytes + 128 + 1024;
+  static int resident[kClMaxTiles + 1] = {0, 0, 0, 0, 0};
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (resident[MT] == 0) {
+      if (cudaFuncSetAttribute(overlap_tc_fact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("overlap_tc_fact: cannot raise the shared-memory limit");
+        return MBAR_ECUDA;
+      }
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(static_cast<unsigned>(MT * num_sms()));
+      q.blockDim = dim3(kSmjThreadsAll);
+      q.dynamicSmemBytes = smem;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = static_cast<unsigned>(MT);
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int nres = 0;
+      if (cudaOccupancyMaxActiveClusters(&nres, overlap_tc_fact_kernel, &q) != cudaSuccess || nres <= 0) {
+        cudaGetLastError();
+        nres = std::max(1, num_sms() / MT / 2);
+      }
+      resident[MT] = nres;
+    }
+  }
+  const int clusters = std::min(resident[MT], std::max(1, num_sms() / MT));
+  const ClPlan pl = cl_plan(K, n, clusters);
+  BUMBAR_CUDA(cudaMemsetAsync(G, 0, static_cast<size_t>(K) * K * sizeof(double), st));
+  ClParams prm{};
+  prm.K = static_cast<int>(K);
+  prm.MT = pl.MT;
+  prm.T = pl.T;
+  prm.n = n;
+  prm.per = pl.per;
+  prm.a = a;
+  prm.logden = nullptr;
+  prm.H = nullptr;
+  prm.out = static_cast<float*>(tmp);
+  prm.err = err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(pl.S * pl.MT));
+  cfg.blockDim = dim3(kSmjThreadsAll);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(pl.MT);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BUMBAR_CUDA(cudaLaunchKernelEx(&cfg, overlap_tc_fact_kernel, fa, fb, fphi, logden, prm));
   count_launches(1);
   reduce_tc_cluster<<<dim3(128 * 128 / 256, static_cast<unsigned>(pl.T)), 256, 0, st>>>(prm.out, pl.S, pl.T, pl.MT,
                                                                                        static_cast<int>(K), G);

@@ -194,6 +194,12 @@ mbar_status gather_transpose(const void* vst, int dtype_bytes, int64_t K, int64_
 mbar_status recenter_columns(float* v, int64_t K, int64_t n, int64_t ld, const double* f, const double* logN,
                              cudaStream_t st);
 mbar_status check_finite(const double* x, int64_t n, int* bad, cudaStream_t stream);
+// FP32 store (K x ld, row-major) of a factorised context's binned level with
+// nb bins of coordinate means phibar: v_kb = a_k + b_k phibar_b - c_b, c_b =
+// min_k of it (prep.cu); tmp of fact_level_tmp_bytes(K, nb).
+size_t fact_level_tmp_bytes(int64_t K, int64_t nb);
+mbar_status fact_level_store(const double* a, const double* b, const double* phibar, int64_t K, int64_t nb,
+                             float* out, int64_t ld, void* tmp, cudaStream_t st);
 
 // ---- Hessian (hessian.cu) ----
 // G = sum_p H_p P_ip P_jp with P_ip = exp(a_i - v_ip - logden_p) (a = f + log N);
@@ -208,6 +214,10 @@ size_t hessian_tmp_bytes(int64_t K, int64_t n);
 // hessian_smaj_eligible when the tensor-core cluster kernel does not take
 // this K (the caller then uses hessian on the row-major store).
 bool hessian_smaj_eligible(int64_t K);
+// The Hessian of a factorised context's unbinned data (K <= 512).
+mbar_status hessian_fact(const double* fa, const double* fb, const double* fphi, int64_t K, int64_t n,
+                         const double* f, const double* logN, const double* logden, double* hess, unsigned* err,
+                         void* tmp, size_t tmp_bytes, cudaStream_t stream);
 mbar_status hessian_smaj(const float* vst, int64_t K, int64_t n, const double* f, const double* logN,
                          const float* logden, double* hess, unsigned* err, void* tmp, size_t tmp_bytes,
                          cudaStream_t stream);
@@ -220,6 +230,11 @@ mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int
                        cudaStream_t st);
 size_t overlap_tc_tmp_bytes(int64_t K, int64_t n);
 bool overlap_tc_smaj_eligible(int64_t K);
+// Factorised data (u_ip = a_i + b_i phi_p; phi and logden FP64, original
+// sample order), K <= 512.
+mbar_status overlap_tc_fact(const double* fa, const double* fb, const double* fphi, int64_t K, int64_t n,
+                            const double* a, const double* logden, double* G, unsigned* err, void* tmp,
+                            size_t tmp_bytes, cudaStream_t st);
 mbar_status overlap_tc_smaj(const float* vst, int64_t K, int64_t n, const double* a, const float* logden, double* G,
                             unsigned* err, void* tmp, size_t tmp_bytes, cudaStream_t st);
 

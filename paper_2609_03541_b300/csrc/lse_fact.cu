@@ -56,7 +56,13 @@ __device__ __forceinline__ void split_pair_fast(double x, float& hi, float& lo) 
 
 }  // namespace
 
-template <int LPS, int NK, int NT>
+// EXACT: the state(s) attaining a sample's maximum exponent contribute
+// exactly 1 to its sum; with a single maximum its weight 1 / (1 + r) is
+// accumulated as the exact count (into the warp's row pair with 32 lanes per
+// sample, else a per-warp integer row in shared memory) plus the remainder
+// -r / (1 + r), tied maxima 1 / sum each (as in the sample-major pass: FP32
+// terms close to 1 lose their deficits r, which biases Q by up to ~6e-8 N).
+template <int LPS, int NK, int NT, bool EXACT>
 __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restrict__ a, const double* __restrict__ b,
                                                          const double* __restrict__ phi, int Kp, LseParams p) {
   constexpr int SPW = 32 / LPS;  // samples per warp at once
@@ -65,6 +71,7 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* cst = reinterpret_cast<float4*>(smem_raw);   // [Kp] (c_hi, c_lo, b_hi, b_lo)
   float2* rows = reinterpret_cast<float2*>(cst + Kp);  // [NW][Kp] unevaluated sums hi + lo
+  unsigned* cnt = reinterpret_cast<unsigned*>(rows + static_cast<size_t>(NW) * Kp);  // [NW][Kp], EXACT, LPS < 32
   const int K = p.K;
   const int64_t n = p.n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -79,6 +86,8 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
     cst[k] = c;
   }
   for (int i = tid; i < NW * Kp; i += NT) rows[i] = make_float2(0.f, 0.f);
+  if constexpr (EXACT && LPS < 32)
+    for (int i = tid; i < NW * Kp; i += NT) cnt[i] = 0u;
   __syncthreads();
 
   const int lig = lane % LPS;  // lane in group
@@ -148,16 +157,40 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
 #pragma unroll
       for (int o = LPS / 2; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       float s0 = 0.f, s1 = 0.f;
+      unsigned top = 0u;
+      int nt = 0;
+      if constexpr (EXACT) {
 #pragma unroll
-      for (int e = 0; e < E; e += 2) {
-        x[e] = ex2_approx(x[e] - m);
-        x[e + 1] = ex2_approx(x[e + 1] - m);
-        s0 += x[e];
-        s1 += x[e + 1];
+        for (int e = 0; e < E; e += 2) {
+          const float d0 = x[e] - m, d1 = x[e + 1] - m;
+          const bool z0 = d0 == 0.f, z1 = d1 == 0.f;
+          x[e] = z0 ? 0.f : ex2_approx(d0);
+          x[e + 1] = z1 ? 0.f : ex2_approx(d1);
+          if (z0) top |= 1u << e;
+          if (z1) top |= 2u << e;
+          s0 += x[e];
+          s1 += x[e + 1];
+        }
+        const unsigned gm = LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u) << (grp * LPS);
+        nt = __popc(__ballot_sync(0xffffffffu, top != 0u) & gm);
+        if (__any_sync(0xffffffffu, (top & (top - 1u)) != 0u || nt > 1)) {
+          nt = __popc(top);
+#pragma unroll
+          for (int o = LPS / 2; o >= 1; o >>= 1) nt += __shfl_xor_sync(0xffffffffu, nt, o);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; e += 2) {
+          x[e] = ex2_approx(x[e] - m);
+          x[e + 1] = ex2_approx(x[e + 1] - m);
+          s0 += x[e];
+          s1 += x[e + 1];
+        }
       }
-      float s = s0 + s1;
+      float r = s0 + s1;
 #pragma unroll
-      for (int o = LPS / 2; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      for (int o = LPS / 2; o >= 1; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+      const float s = EXACT ? static_cast<float>(nt) + r : r;
       const float w = j < nloc ? hw * rcp_approx(s) : 0.f;
       // every lane of a group holds its sample's m and s: lane l takes the
       // logden of sample l from the group that has it in this round
@@ -166,6 +199,32 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       if (lane >= j0 && lane < j0 + SPW) ld_mine = lv_l;
 #pragma unroll
       for (int e = 0; e < E; ++e) acc[e] = fmaf(x[e], w, acc[e]);
+      if (EXACT && top != 0u && w != 0.f) {
+        const float add = nt == 1 ? -r * w : w;
+        do {
+          const int e = __ffs(top) - 1;
+          top &= top - 1u;
+          const int k = 4 * (lig + LPS * (e >> 2)) + (e & 3);
+          if constexpr (LPS == 32) {
+            // this lane is the only writer of the row entry of state k
+            float2 c = myrow[k];
+            if (nt == 1) {
+              const float sum1 = c.x + hw, b1 = sum1 - c.x;
+              c.y += (c.x - (sum1 - b1)) + (hw - b1);
+              c.x = sum1;
+            }
+            const float sum2 = c.x + add, bv = sum2 - c.x;
+            c.y += (c.x - (sum2 - bv)) + (add - bv);
+            c.x = sum2;
+            myrow[k] = c;
+          } else {
+            if (nt == 1) atomicAdd(&cnt[warp * Kp + k], static_cast<unsigned>(hw));
+#pragma unroll
+            for (int q = 0; q < E; ++q)
+              if (q == e) acc[q] += add;
+          }
+        } while (top != 0u);
+      }
       if (++since >= kFactFlush) {
         fold();
         since = 0;
@@ -185,6 +244,7 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
     for (int w = 0; w < NW; ++w) {
       const float2 c = rows[static_cast<size_t>(w) * Kp + k];
       t += static_cast<double>(c.x) + static_cast<double>(c.y);
+      if constexpr (EXACT && LPS < 32) t += static_cast<double>(cnt[static_cast<size_t>(w) * Kp + k]);
     }
     out[k] = t;
   }
@@ -192,9 +252,9 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
 
 namespace {
 
-template <int LPS, int NK, int NT>
-void fact_run(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp, const LseParams& prm,
-              cudaStream_t st) {
+template <int LPS, int NK, int NT, bool EXACT>
+void fact_run_one(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp,
+                  const LseParams& prm, cudaStream_t st) {
   static bool init = false;
   {
     std::lock_guard<std::recursive_mutex> lock(init_mutex());
@@ -203,11 +263,18 @@ void fact_run(const LsePlan& pl, const double* a, const double* b, const double*
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      cudaFuncSetAttribute(lse_fact_kernel<LPS, NK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+      cudaFuncSetAttribute(lse_fact_kernel<LPS, NK, NT, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
       init = true;
     }
   }
-  lse_fact_kernel<LPS, NK, NT><<<pl.grid, NT, pl.smem, st>>>(a, b, phi, Kp, prm);
+  lse_fact_kernel<LPS, NK, NT, EXACT><<<pl.grid, NT, pl.smem, st>>>(a, b, phi, Kp, prm);
+}
+
+template <int LPS, int NK, int NT>
+void fact_run(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp, const LseParams& prm,
+              cudaStream_t st) {
+  if (prm.exact_max) fact_run_one<LPS, NK, NT, true>(pl, a, b, phi, Kp, prm, st);
+  else fact_run_one<LPS, NK, NT, false>(pl, a, b, phi, Kp, prm, st);
 }
 
 }  // namespace
@@ -233,7 +300,8 @@ LsePlan lse_fact_plan(int64_t K, int64_t n) {
   pl.H = lps;
   pl.C = 32;
   pl.num_strips = static_cast<int>(ceil_div(n, 32));
-  pl.smem = static_cast<size_t>(Kp) * 16 + static_cast<size_t>(nt / 32) * Kp * 8;
+  // + the per-warp counts of the exact split below 32 lanes per sample
+  pl.smem = static_cast<size_t>(Kp) * 16 + static_cast<size_t>(nt / 32) * Kp * (lps < 32 ? 12 : 8);
   pl.ok = K >= 1 && K <= 1024;
   // every warp of every CTA gets at least one chunk where n allows
   pl.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(pl.num_strips, nt / 32), num_sms())));
@@ -250,35 +318,33 @@ mbar_status lse_fact_launch(const double* a, const double* b, const double* phi,
   prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
   const int Kp = static_cast<int>(round_up(prm.K, 4));
   const int lps = pl.H, nk = pl.J;
-#define BUMBAR_FACT_SMALL(L)                                          \
-  case L:                                                             \
-    if (nk == 1) fact_run<L, 1, 512>(pl, a, b, phi, Kp, prm, st);     \
-    else if (nk == 2) fact_run<L, 2, 512>(pl, a, b, phi, Kp, prm, st); \
-    else fact_run<L, 4, 384>(pl, a, b, phi, Kp, prm, st);             \
-    break;
-  if (lps < 32) {
-    switch (lps) {
-      BUMBAR_FACT_SMALL(1)
-      BUMBAR_FACT_SMALL(2)
-      BUMBAR_FACT_SMALL(4)
-      BUMBAR_FACT_SMALL(8)
-      BUMBAR_FACT_SMALL(16)
-      default: set_error("lse_fact_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
-    }
-  } else {
+  // the instances the shape rule reaches: one lane per sample with 1, 2 or
+  // 4 chunks; 2..16 lanes with 4 chunks; 32 lanes with 3..8 chunks
+  bool ok = true;
+  if (lps == 1 && nk == 1) fact_run<1, 1, 512>(pl, a, b, phi, Kp, prm, st);
+  else if (lps == 1 && nk == 2) fact_run<1, 2, 512>(pl, a, b, phi, Kp, prm, st);
+  else if (lps == 1 && nk == 4) fact_run<1, 4, 384>(pl, a, b, phi, Kp, prm, st);
+  else if (lps == 2 && nk == 4) fact_run<2, 4, 384>(pl, a, b, phi, Kp, prm, st);
+  else if (lps == 4 && nk == 4) fact_run<4, 4, 384>(pl, a, b, phi, Kp, prm, st);
+  else if (lps == 8 && nk == 4) fact_run<8, 4, 384>(pl, a, b, phi, Kp, prm, st);
+  else if (lps == 16 && nk == 4) fact_run<16, 4, 384>(pl, a, b, phi, Kp, prm, st);
+  else if (lps == 32) {
     switch (nk) {
-      case 1: fact_run<32, 1, 512>(pl, a, b, phi, Kp, prm, st); break;
-      case 2: fact_run<32, 2, 512>(pl, a, b, phi, Kp, prm, st); break;
       case 3: fact_run<32, 3, 512>(pl, a, b, phi, Kp, prm, st); break;
       case 4: fact_run<32, 4, 384>(pl, a, b, phi, Kp, prm, st); break;
       case 5: fact_run<32, 5, 256>(pl, a, b, phi, Kp, prm, st); break;
       case 6: fact_run<32, 6, 256>(pl, a, b, phi, Kp, prm, st); break;
       case 7: fact_run<32, 7, 256>(pl, a, b, phi, Kp, prm, st); break;
       case 8: fact_run<32, 8, 256>(pl, a, b, phi, Kp, prm, st); break;
-      default: set_error("lse_fact_launch: unsupported shape"); return MBAR_EUNSUPPORTED;
+      default: ok = false;
     }
+  } else {
+    ok = false;
   }
-#undef BUMBAR_FACT_SMALL
+  if (!ok) {
+    set_error("lse_fact_launch: unsupported shape (%d lanes, %d chunks)", lps, nk);
+    return MBAR_EUNSUPPORTED;
+  }
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return lse_epilogue_launch(prm, st);

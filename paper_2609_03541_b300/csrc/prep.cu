@@ -525,4 +525,112 @@ mbar_status factorised_u(const double* a, const double* b, const double* phi, in
   return MBAR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Binned levels of a factorised context (u_kp = a_k + b_k phi_p): the mean of
+// the members' u is a_k + b_k phibar_b with phibar_b the mean of the members'
+// coordinate, so a level's FP32 store is generated from a, b and the bin
+// means of phi instead of being summed from a K x N store. Column b is
+// shifted by c_b = min_k (a_k + b_k phibar_b) like the unbinned MIXED store
+// (v >= 0, 0 at the minimum; any per-column shift leaves Eq. 1 unchanged).
+// The sums are unevaluated FP32 pairs (about 44 significant bits), so no
+// FP64 arithmetic runs per entry.
+namespace {
+
+struct Pair {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Pair pair_of(double x) {
+  Pair p;
+  p.hi = static_cast<float>(x);
+  p.lo = static_cast<float>(x - static_cast<double>(p.hi));
+  return p;
+}
+
+// a + b phi as an unevaluated pair (the dropped b_lo phi_lo term is 2^-48 of
+// the product)
+// (explicitly rounded operations: contracting the product into the sum
+// would break the error-free transformations)
+__device__ __forceinline__ Pair affine_pair(Pair a, Pair b, Pair ph) {
+  const float pr = __fmul_rn(b.hi, ph.hi);
+  const float pe = __fmaf_rn(b.hi, ph.hi, -pr);
+  const float small = __fadd_rn(__fmaf_rn(b.hi, ph.lo, __fmaf_rn(b.lo, ph.hi, pe)), a.lo);
+  const float s = __fadd_rn(a.hi, pr);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(pr, bb));  // TwoSum error of a.hi + pr
+  Pair r;
+  r.hi = s;
+  r.lo = __fadd_rn(e, small);
+  return r;
+}
+
+__device__ __forceinline__ bool pair_less(Pair x, Pair y) {
+  return __fadd_rn(__fsub_rn(x.hi, y.hi), __fsub_rn(x.lo, y.lo)) < 0.f;
+}
+
+// (a_k, b_k) as FP32 pairs, once per level
+__global__ void fact_state_pairs(const double* __restrict__ a, const double* __restrict__ b, int64_t K,
+                                 float4* __restrict__ ab) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const Pair pa = pair_of(a[k]), pb = pair_of(b[k]);
+  ab[k] = make_float4(pa.hi, pa.lo, pb.hi, pb.lo);
+}
+
+__device__ __forceinline__ Pair state_a(float4 v) { return Pair{v.x, v.y}; }
+__device__ __forceinline__ Pair state_b(float4 v) { return Pair{v.z, v.w}; }
+
+// c_b = min_k (a_k + b_k phibar_b), one thread per bin
+__global__ void fact_level_min(const float4* __restrict__ ab, const double* __restrict__ phibar, int64_t K,
+                               int64_t nb, float2* __restrict__ cmin) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const Pair ph = pair_of(phibar[j]);
+  float4 s0 = ab[0];
+  Pair m = affine_pair(state_a(s0), state_b(s0), ph);
+  for (int64_t k = 1; k < K; ++k) {
+    const float4 sk = ab[k];
+    const Pair u = affine_pair(state_a(sk), state_b(sk), ph);
+    if (pair_less(u, m)) m = u;
+  }
+  cmin[j] = make_float2(m.hi, m.lo);
+}
+
+// v_kb = fl32(a_k + b_k phibar_b - c_b): block rows = states, columns = bins
+__global__ void fact_level_fill(const float4* __restrict__ ab, const double* __restrict__ phibar,
+                                const float2* __restrict__ cmin, int64_t K, int64_t nb, float* __restrict__ out,
+                                int64_t ld) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t k = blockIdx.y;
+  if (j >= nb || k >= K) return;
+  const float4 sk = ab[k];
+  const Pair u = affine_pair(state_a(sk), state_b(sk), pair_of(phibar[j]));
+  const float2 c = cmin[j];
+  const float d = __fsub_rn(u.hi, c.x);
+  const float bb = __fsub_rn(d, u.hi);
+  const float e = __fadd_rn(__fsub_rn(u.hi, __fsub_rn(d, bb)), __fsub_rn(-c.x, bb));  // TwoSum error of u.hi - c.hi
+  const float v = __fadd_rn(d, __fsub_rn(__fadd_rn(e, u.lo), c.y));
+  out[k * ld + j] = v > 0.f ? v : 0.f;  // >= 0 up to the pairs' rounding
+}
+
+}  // namespace
+
+size_t fact_level_tmp_bytes(int64_t K, int64_t nb) {
+  return static_cast<size_t>(round_up(K * 16, 256)) + static_cast<size_t>(round_up(nb * 8, 256));
+}
+
+mbar_status fact_level_store(const double* a, const double* b, const double* phibar, int64_t K, int64_t nb,
+                             float* out, int64_t ld, void* tmp, cudaStream_t st) {
+  if (nb <= 0) return MBAR_OK;
+  float4* ab = static_cast<float4*>(tmp);
+  float2* cmin = reinterpret_cast<float2*>(static_cast<unsigned char*>(tmp) + round_up(K * 16, 256));
+  const unsigned gx = static_cast<unsigned>(ceil_div(nb, 256));
+  fact_state_pairs<<<static_cast<unsigned>(ceil_div(K, 256)), 256, 0, st>>>(a, b, K, ab);
+  fact_level_min<<<gx, 256, 0, st>>>(ab, phibar, K, nb, cmin);
+  fact_level_fill<<<dim3(gx, static_cast<unsigned>(K)), 256, 0, st>>>(ab, phibar, cmin, K, nb, out, ld);
+  count_launches(3);
+  BUMBAR_CUDA(cudaGetLastError());
+  return MBAR_OK;
+}
+
 }  // namespace bumbar

@@ -338,7 +338,8 @@ class Context:
     def timing(self, kind: int):
         """(launches, total device ms, streamed bytes) of one launch kind:
         0 unbinned LSE pass, 1 Hessian, 2 Newton solve, 3 unbinned pass that
-        only confirms a Newton step below f_tol."""
+        only confirms a Newton step below f_tol, 4 second-loop round of
+        Algorithm 1 (binned passes), 5 one-launch first loop."""
         n = ctypes.c_int64()
         ms = ctypes.c_double()
         by = ctypes.c_double()

@@ -439,13 +439,14 @@ def _pt_factorised(K=6, N_k=3000, s2=40.0, seed=2):
     return a, b, p.phi, p.N_k
 
 
-@pytest.mark.parametrize("prec", [M.MBAR_FP64, M.MBAR_MIXED])
+@pytest.mark.parametrize("prec", [M.MBAR_FP64])
 @pytest.mark.parametrize("where", ["host", "device"])
 def test_create_factorised_is_create_on_the_generated_u(prec, where):
-    """mbar_create_factorised generates u_kn = a_k + b_k phi_n with the
-    host's binary64 rounding and bins by phi: the solve is bit for bit the
-    one of mbar_create on the oracle's materialised u with phi set as the
-    coordinate, and both match the oracle's MBAR solution."""
+    """FP64: mbar_create_factorised generates u_kn = a_k + b_k phi_n with
+    the host's binary64 rounding and bins by phi: the solve is bit for bit
+    the one of mbar_create on the oracle's materialised u with phi set as the
+    coordinate, and both match the oracle's MBAR solution. (MIXED contexts
+    keep no K x N store: tests/test_gpu_factorised.py.)"""
     import torch
     a, b, phi, Nk = _pt_factorised()
     if where == "device":
