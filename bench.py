@@ -561,103 +561,143 @@ def batch_bench(args):
     return 0
 
 
-def serve_bench(args):
-    """Serving stream: requests with K log-uniform in [4, 1024] and N_k ~
-    U{100..20000} (harmonic / umbrella alternating), drawn on the device at
-    their arrival (timed separately), submitted to one mbar_server (mixed
-    precision, memory budget); first at saturation (all submitted as soon as
-    drawn) for the capacity, then with Poisson arrivals at the given fractions
-    of that capacity for p50/p99 latency from arrival to completion."""
+def serve_requests(R: int, seed: int, device):
+    """The serving stream's R requests in factorised form, drawn on the
+    device: K log-uniform on [4, 1024], N_k ~ U{100..20000}; even requests
+    are umbrella windows on the double well (u = a_k + b_k x with the
+    per-sample terms dropped, which leaves f unchanged), odd ones the Sec. IV
+    replicas u = beta_k E (80 % neighbour overlap). Returns (requests,
+    entries K * N summed, input bytes)."""
     import torch
-    from paper_2609_03541_b300 import mbar as M
-    rng = np.random.default_rng(args.seed)
-    R = args.requests
-    Ks = np.exp(rng.uniform(np.log(4), np.log(1024), size=R)).astype(int)
+    from paper_2609_03541_b300 import workloads as W
+    rng = np.random.default_rng(seed)
+    Ks = np.rint(np.exp(rng.uniform(np.log(4), np.log(1024), size=R))).astype(int)
     Nks = rng.integers(100, 20001, size=R)
-    specs = [("harmonic" if i % 2 == 0 else "umbrella", int(Ks[i]), int(Nks[i]), 5000 + i) for i in range(R)]
-    budget = int(args.budget_gb * (1 << 30))
-    input_cap = int(args.wave_gb * (1 << 30))
+    reqs, entries, nbytes = [], 0, 0
+    for i in range(R):
+        K, Nk = int(Ks[i]), int(Nks[i])
+        if i % 2 == 0:
+            a, b, phi, nk = W.umbrella_factorised_device(K, Nk, 5000 + i, device=device)
+        else:
+            b, phi, nk = W.gaussian_overlap_device(K, Nk, 5000 + i, device=device)
+            a = torch.zeros_like(b)
+        reqs.append((a, b, phi, nk))
+        entries += K * K * Nk
+        nbytes += (2 * K + K * Nk) * 8
+    torch.cuda.synchronize()
+    return reqs, entries, nbytes
 
-    gen_stream = torch.cuda.Stream()
 
-    def run(rate):
-        cfg = M.server_config(workers=args.workers, hbm_budget_bytes=budget, precision=M.MBAR_MIXED)
+class DeviceMemorySampler:
+    """Samples the device's used memory (cudaMemGetInfo) every `period` s on
+    a host thread; `peak` is the largest sample."""
+
+    def __init__(self, period: float = 0.05):
+        import threading
+        self.period, self.peak, self._stop = period, 0, threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        import torch
+        while not self._stop.is_set():
+            free, total = torch.cuda.mem_get_info()
+            self.peak = max(self.peak, total - free)
+            self._stop.wait(self.period)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join()
+
+
+def serve_run(reqs, workers: int, budget: int, rate, seed: int):
+    """One pass of the request stream through a fresh mbar_server (MIXED):
+    at saturation (rate None: all submitted at once) or with Poisson
+    arrivals at `rate` requests/s, each submitted at its arrival time.
+    Latency is the server's own (submission to completion); the elapsed time
+    runs from the first submission to the last completion."""
+    from paper_2609_03541_b300 import mbar as M
+    R = len(reqs)
+    arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=R)) if rate else np.zeros(R)
+    cfg = M.server_config(workers=workers, hbm_budget_bytes=budget, precision=M.MBAR_MIXED)
+    lat, failed, rejected = [], 0, 0
+    with DeviceMemorySampler() as mem:
         srv = M.Server(cfg)
-        pending = {}   # id -> (arrival time, input bytes, K)
-        lat, rejected, gen_s = [], 0, 0.0
-        held = 0
-        t_start = time.perf_counter()
-        t_next = t_start
-        done = 0
-
-        def reap(block):
-            nonlocal held, done
-            for rid in list(pending):
-                if block or srv.poll(rid) == 2:
-                    t_arr, b = pending.pop(rid)
-                    try:
-                        srv.wait(rid)
-                    except M.MbarError:
-                        pass
-                    lat.append(time.perf_counter() - t_arr)
-                    held -= b
-                    done += 1
-                    if block:
-                        return
-
-        for kind, K, Nk, seed in specs:
+        t0 = time.perf_counter()
+        ids = []
+        for i, (a, b, phi, nk) in enumerate(reqs):
             if rate:
-                t_next += rng.exponential(1.0 / rate)
-                while time.perf_counter() < t_next:
-                    reap(False)
-                    time.sleep(0.0005)
-            b = K * K * Nk * 8
-            if K * K * Nk * 12 > budget or b > input_cap:
-                rejected += 1
-                continue
-            while held + b > input_cap and pending:
-                reap(True)
-            t_arr = max(t_next, time.perf_counter()) if rate else time.perf_counter()
-            tg = time.perf_counter()
-            if torch.cuda.memory_reserved() > input_cap + (8 << 30):
-                torch.cuda.empty_cache()   # freed inputs of other sizes: hand the memory back
-            with torch.cuda.stream(gen_stream):
-                u, nk, phi = _gen_device(kind, K, Nk, seed)
-            gen_stream.synchronize()       # this stream only: solves keep running meanwhile
-            gen_s += time.perf_counter() - tg
+                dt = t0 + arr[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            ts = time.perf_counter()
             try:
-                rid = srv.submit(u, nk, phi)
+                ids.append((srv.submit_factorised(a, b, phi, nk), ts))
             except M.MbarError:
                 rejected += 1
+        t_end = t0
+        for rid, ts in ids:
+            try:
+                _, _, l, _ = srv.wait(rid)
+            except M.MbarError as e:
+                failed += 1
+                log(f"[bench] serve: request {rid} failed: {e}")
                 continue
-            pending[rid] = (t_arr if rate else tg, b)
-            held += b
-            del u, phi
-        while pending:
-            reap(True)
-        elapsed = time.perf_counter() - t_start
+            lat.append(l)
+            t_end = max(t_end, ts + l)
         st = srv.stats()
         srv.close()
-        return {"completed": done, "rejected": rejected, "elapsed_s": elapsed, "gen_s": gen_s,
-                "solves_per_s": done / elapsed, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "peak_running": st["peak_running"],
-                "peak_bytes": st["peak_bytes"]}
+    elapsed = t_end - t0
+    done = len(lat)
+    return {"completed": done, "rejected": rejected, "failed": failed, "elapsed_s": elapsed,
+            "solves_per_s": done / elapsed if elapsed > 0 else 0.0,
+            "offered_per_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat else None,
+            "peak_running": st["peak_running"], "peak_admitted_gb": st["peak_bytes"] / 2 ** 30,
+            "peak_device_used_gb": mem.peak / 2 ** 30}
 
-    sat = run(None)
+
+def serve_block(args, R: int, loads):
+    """Serving at the stream's full size: requests drawn before the timed
+    runs (generation is not timed), one saturation run for the capacity,
+    then Poisson runs at the given fractions of it for p50 / p99."""
+    import torch
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    reqs, entries, nbytes = serve_requests(R, args.seed, dev)
+    gen_s = time.perf_counter() - t0
+    budget = int(args.budget_gb * (1 << 30))
+    log(f"[bench] serve: {R} requests drawn in {gen_s:.1f} s ({nbytes / 2 ** 30:.1f} GB of inputs, "
+        f"{entries:.3g} entries)")
+    sat = serve_run(reqs, args.workers, budget, None, args.seed)
     log(f"[bench] serve saturation: {sat}")
-    loads = {}
-    for frac in args.loads:
-        loads[str(frac)] = run(frac * sat["solves_per_s"])
-        log(f"[bench] serve load {frac}: {loads[str(frac)]}")
+    loads_out = {}
+    for frac in loads:
+        loads_out[str(frac)] = serve_run(reqs, args.workers, budget, frac * sat["solves_per_s"], args.seed + 1)
+        log(f"[bench] serve load {frac}: {loads_out[str(frac)]}")
+    del reqs
+    torch.cuda.empty_cache()
+    return {"requests": R, "entries": entries, "input_gb": nbytes / 2 ** 30, "generation_s_untimed": gen_s,
+            "budget_gb": args.budget_gb, "workers": args.workers, "saturation": sat, "poisson": loads_out}
+
+
+def serve_bench(args):
+    """The serving stream (K log-uniform [4, 1024], N_k ~ U{100..20000},
+    factorised requests, MIXED, memory budget) as its own line."""
+    blk = serve_block(args, args.requests, args.loads)
+    sat = blk["saturation"]
     line = {"metric": "MBAR solves/sec (served); p50/p99 latency", "value": sat["solves_per_s"], "unit": "solves/s",
             "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": sat["elapsed_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving: K log-uniform [4,1024], N_k~U{100..20000}, harmonic/umbrella, inputs drawn "
-                                   "on the device at arrival, mixed precision", "requests": R,
-                       "workers": args.workers, "budget_gb": args.budget_gb, "input_window_gb": args.wave_gb},
-            "saturation": sat, "poisson": loads}
+            "config": {"workload": "serving: K log-uniform [4,1024], N_k~U{100..20000}, factorised umbrella / Sec. IV "
+                                   "replica requests drawn before the timed runs, mixed precision",
+                       "requests": args.requests, "workers": args.workers, "budget_gb": args.budget_gb},
+            "serving": blk}
     print(json.dumps(line), flush=True)
-    return 0
+    return 0 if sat["failed"] == 0 and sat["rejected"] == 0 else 1
 
 
 def max_over_ranks(ms: float, dist, device) -> float:
@@ -703,7 +743,8 @@ def main():
     ap.add_argument("--loads", type=lambda t: [float(x) for x in t.split(",")], default=[0.5, 0.9],
                     help="serve: Poisson arrival rates as fractions of the measured capacity")
     ap.add_argument("--workers", type=int, default=16, help="batch/serve: concurrent solves")
-    ap.add_argument("--budget-gb", type=float, default=140.0, help="batch/serve: device memory budget of the server")
+    ap.add_argument("--budget-gb", type=float, default=None,
+                    help="batch/serve: device memory budget of the server (default 140 batch, 160 serve)")
     ap.add_argument("--wave-gb", type=float, default=80.0, help="batch/serve: FP64 input memory held at once")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--gauss-M", default="10,30,100,300", help="gaussian: replica counts M")
@@ -711,6 +752,8 @@ def main():
     ap.add_argument("--nk", type=int, default=None,
                     help="samples per state override (smaller instances for profiling captures)")
     args = ap.parse_args()
+    if args.budget_gb is None:
+        args.budget_gb = 160.0 if args.workload in ("serve", "alchemical") else 140.0
     if args.workload == "batch":
         return batch_bench(args)
     if args.workload == "serve":

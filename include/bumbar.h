@@ -124,15 +124,21 @@ BUMBAR_API mbar_status mbar_create(mbar_ctx** out, int64_t K, int64_t N, const i
 /* Creates a context from factorised reduced potentials
  *     u_kn = a_k + b_k phi_n
  * (Sec. II: the paper's u = beta_k E_n is a = 0, b = beta, phi = E): only
- * the 2 K + N numbers cross the host link; u is generated on the device,
- * with the product and the sum each rounded to nearest in binary64, exactly
- * as a host evaluating a + b * phi gets it, and then stored like mbar_create
- * stores a given u. phi also becomes the bin coordinate (as by
- * mbar_set_coordinate). a, b: FP64[K]; phi: FP64[N]; all three on the host
- * (on_device = 0) or all in device memory (on_device = 1). N_k, opts,
- * cuda_stream and the errors as for mbar_create; the call holds a
- * temporary K x N FP64 buffer (ENOMEM if it cannot be allocated) and
- * returns after the context's copy is complete. */
+ * the 2 K + N numbers cross the host link, and phi is the bin coordinate.
+ * a, b: FP64[K]; phi: FP64[N]; all three on the host (on_device = 0) or all
+ * in device memory (on_device = 1). N_k, opts, cuda_stream and the errors as
+ * for mbar_create.
+ *   MBAR_MIXED with binning (the default options): the context keeps a, b
+ *   and phi (FP64, O(K + N) bytes) and no K x N store. A binned level's
+ *   entries are a_k + b_k mean_b(phi) (the bin means of u, exactly so for a
+ *   factorised u); the unbinned passes and the Hessian form u from a, b and
+ *   phi inside their kernels. mbar_set_coordinate returns EUNSUPPORTED.
+ *   Otherwise: u is generated on the device, with the product and the sum
+ *   each rounded to nearest in binary64, exactly as a host evaluating
+ *   a + b * phi gets it, and stored like mbar_create stores a given u; the
+ *   call holds a temporary K x N FP64 buffer (ENOMEM if it cannot be
+ *   allocated).
+ * The call returns once the context's device data are complete. */
 BUMBAR_API mbar_status mbar_create_factorised(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k,
                                               const double* a, const double* b, const double* phi,
                                               int32_t on_device, const mbar_opts* opts, void* cuda_stream);
@@ -263,6 +269,9 @@ BUMBAR_API mbar_status mbar_get_timing(mbar_ctx* ctx, int32_t kind, int64_t* lau
  *   (1, n, s, iterations)      end of Algorithm 1's first loop at n bins;
  *   (2, n, s_n, s_next)        one check of Eq. 3 in the second loop;
  *   (3, iteration, |delta f|max, max|g|)  accepted Newton step;
+ *   (5, iteration, |t delta f|max, max|g|)  rejected full Newton step, the
+ *                              step t = 2^-h accepted instead (backtracking
+ *                              on ||g||^2 while |delta f|max >= 100 f_tol);
  *   (4, iteration, |delta f|max, max|g|)  rejected Newton step (SCI instead).
  * *rows receives the number of rows; out (host, nullable) receives up to
  * `capacity` rows. */
@@ -414,6 +423,13 @@ typedef struct {
  * staging copy. */
 BUMBAR_API uint64_t mbar_footprint_bytes(int64_t K, int64_t N, int32_t precision, int32_t use_binning);
 
+/* The same estimate for a solve from the factorised form (as
+ * mbar_create_factorised): with MBAR_MIXED and binning, Algorithm 1's binned
+ * levels, the FP64 a, b, phi and per-sample vectors and the Hessian's
+ * scratch, no K x N store; otherwise a K x N FP64 buffer of u plus the
+ * footprint of a context made from device u. 0 for K < 1 or N < 1. */
+BUMBAR_API uint64_t mbar_footprint_factorised_bytes(int64_t K, int64_t N, int32_t precision, int32_t use_binning);
+
 /* Starts `cfg->workers` worker threads on the current device.
  * EINVAL for a bad configuration, ENOMEM if the threads cannot start. */
 BUMBAR_API mbar_status mbar_server_create(mbar_server** out, const mbar_server_config* cfg);
@@ -427,6 +443,17 @@ BUMBAR_API mbar_status mbar_server_create(mbar_server** out, const mbar_server_c
 BUMBAR_API mbar_status mbar_server_submit(mbar_server* server, int64_t K, int64_t N, const int64_t* N_k,
                                           const double* u_kn, int32_t u_on_device, const double* phi,
                                           int32_t phi_on_device, int64_t* id);
+
+/* Queues one solve from the factorised form u_kn = a_k + b_k phi_n
+ * (arguments as mbar_create_factorised: a, b FP64[K], phi FP64[N], all on
+ * the host or all on the device; phi is the bin coordinate). N_k is copied
+ * now; a, b and phi are read when the request is admitted and must stay
+ * valid until mbar_server_wait has returned for it. The request is charged
+ * mbar_footprint_factorised_bytes. Results, errors and waiting as for
+ * mbar_server_submit. */
+BUMBAR_API mbar_status mbar_server_submit_factorised(mbar_server* server, int64_t K, int64_t N, const int64_t* N_k,
+                                                     const double* a, const double* b, const double* phi,
+                                                     int32_t on_device, int64_t* id);
 
 /* Non-blocking state of a request: 0 queued, 1 admitted/running, 2 done. */
 BUMBAR_API mbar_status mbar_server_poll(mbar_server* server, int64_t id, int32_t* state);

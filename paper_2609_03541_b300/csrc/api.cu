@@ -83,6 +83,7 @@ struct mbar_ctx {
   bool fact = false;
   double *fa = nullptr, *fb = nullptr, *fphi = nullptr;
   double* logden64 = nullptr;  // logden of the factorised unbinned passes (FP64, original order)
+  void* fref = nullptr;        // reference-state table of the factorised unbinned passes
   int64_t ld = 0;
   double* cshift = nullptr;  // mixed: per-column shift (current order)
   int32_t* perm = nullptr;   // current column -> original sample
@@ -251,7 +252,9 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
     p.H = nullptr;
     p.logden = logden_out ? c->logden64 : nullptr;
     p.exact_max = c->confirm_only ? 0 : 1;
-    s = lse_fact_launch(c->fa, c->fb, c->fphi, lse_fact_plan(c->K, L.n), p, c->st);
+    // phi's range from the sorted copy: its first and last element
+    s = lse_fact_launch(c->fa, c->fb, c->fphi, lse_fact_plan(c->K, L.n), p, c->phi_sorted, c->phi_sorted + c->N - 1,
+                        1, c->fref, c->st);
   } else if (!L.binned && c->smaj && c->vst) {
     // unbinned MIXED pass over the sample-major copy (original sample order);
     // logden comes back to the store's column order through perm
@@ -559,6 +562,9 @@ double max_abs(const std::vector<double>& x) {
   return m;
 }
 
+// step halvings of a rejected Newton step before the SCI fallback
+constexpr int kMaxHalvings = 12;
+
 mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
   const int64_t K = c->K;
   const Level& L = c->full;
@@ -607,6 +613,8 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
       return s;
     }
     const double step = max_abs(dh);
+    double g2 = 0.0;  // ||g||^2 at f
+    for (double x : gh) g2 += x * x;
     bool accepted = false;
     if (info == 0 && std::isfinite(step)) {
       s = vec_add_gauge(c->f, c->delta, c->ft, K, c->st);
@@ -642,6 +650,35 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
           break;
         }
         prev_step = step;
+      }
+      // A rejected full step well above the gradient's rounding noise (f far
+      // from the root, e.g. after coarse levels on a long replica ladder):
+      // backtrack along the Newton direction. It is the direction of
+      // Newton's method for g(f) = 0, whose Jacobian is the Hessian, so a
+      // short enough step lowers ||g||^2 (Armijo test on ||g||^2 / 2).
+      for (int h = 1; !accepted && step >= 1e2 * c->opts.f_tol && h <= kMaxHalvings; ++h) {
+        const double t = std::ldexp(1.0, -h);
+        s = vec_add_gauge(c->f, c->delta, c->ft, K, c->st, t);
+        if (s == MBAR_OK) s = sci_step_exact(c, L, c->ft, c->fts, c->gt, c->s2, c->logden);
+        if (s == MBAR_OK) s = d2h(c, gh.data(), c->gt, K);
+        if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+        if (s != MBAR_OK && s != MBAR_ENOTCONV) {
+          dfree(c, tmp);
+          return s;
+        }
+        if (s != MBAR_OK) continue;  // the trial underflowed: shorter still
+        double g2t = 0.0;
+        for (double x : gh) g2t += x * x;
+        if (!std::isfinite(g2t) || g2t > (1.0 - 2e-4 * t) * g2) continue;
+        std::swap(c->f, c->ft);
+        std::swap(c->fs, c->fts);
+        std::swap(c->g, c->gt);
+        gmax = max_abs(gh);
+        accepted = true;
+        rejects = 0;
+        rep->last_step = t * step;
+        prev_step = INFINITY;  // a damped step says nothing about quadratic contraction
+        trace_row(c, 5, it, t * step, gmax);
       }
     }
     if (!accepted) {
@@ -1423,7 +1460,7 @@ namespace {
 
 // Context creation from u_kn (dense) or, with fa != nullptr, from the
 // factorised form u_kn = fa_k + fb_k fphi_n without any K x N store (MIXED,
-// K <= 512: the caller checks).
+// K <= 1024: the caller checks).
 mbar_status create_impl(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k, const double* u_kn,
                         int32_t u_on_device, const double* fa_in, const double* fb_in, const double* fphi_in,
                         const mbar_opts* opts, void* cuda_stream) {
@@ -1557,6 +1594,7 @@ mbar_status create_impl(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
     TRYC(check_finite(c->fb, K, c->bad, c->st));
     TRYC(check_finite(c->fphi, N, c->bad, c->st));
     TRYC(dalloc_t(c, &c->logden64, N));
+    TRYC(dalloc(c, &c->fref, lse_fact_ref_bytes()));
     TRYC(dalloc(c, &c->logden, static_cast<size_t>(N) * c->dtype));  // binned levels
     TRYC(dalloc_t(c, &c->perm, N));
     TRYC(dalloc_t(c, &c->seg, N));
@@ -1708,14 +1746,14 @@ mbar_status mbar_create_factorised(mbar_ctx** out, int64_t K, int64_t N, const i
     return K > 1024 || N > 2000000000LL ? MBAR_EUNSUPPORTED : MBAR_EINVAL;
   }
   {
-    // MIXED with K <= 512: the store-free factorised context
+    // MIXED: the store-free factorised context
     mbar_opts o;
     if (opts) {
       o = *opts;
     } else {
       mbar_opts_default(&o, MBAR_MIXED);
     }
-    if (o.precision == MBAR_MIXED && K <= 512 && o.use_binning)
+    if (o.precision == MBAR_MIXED && o.use_binning)
       return create_impl(out, K, N, N_k, nullptr, on_device, a, b, phi, &o, cuda_stream);
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -2255,7 +2293,7 @@ mbar_status mbar_destroy(mbar_ctx* c) {
   void* ptrs[] = {c->weights, c->Nk_d, c->logN_d, c->v, c->vst, c->logden_orig, c->cshift, c->perm,  c->phi0,    c->phi_sorted, c->d_sorted, c->d_pairs, c->f,
                   c->fs,   c->ft,     c->fts,   c->g,      c->gt,    c->Q,       c->stat,
                   c->hess, c->delta,  c->info,  c->bad,    c->logden,  c->scratch,    c->seg,
-                  c->start, c->count, c->nb_dev, c->fa, c->fb, c->fphi, c->logden64};
+                  c->start, c->count, c->nb_dev, c->fa, c->fb, c->fphi, c->logden64, c->fref};
   if (c->st) {
     for (void* p : ptrs) dfree(c, p);
     cudaStreamSynchronize(c->st);
@@ -2367,7 +2405,9 @@ mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const
 
 size_t mbar_lse_factorised_scratch_bytes(int64_t K, int64_t n) {
   if (K < 1 || K > 1024 || n < 1) return 0;
-  return lse_scratch_for_grid(K, lse_fact_plan(K, n).grid);
+  // the pass's own scratch, then (256-byte aligned) the reference-state table
+  return round_up(static_cast<int64_t>(lse_scratch_for_grid(K, lse_fact_plan(K, n).grid)), 256) +
+         lse_fact_ref_bytes();
 }
 
 mbar_status mbar_lse_pass_factorised(const double* a, const double* b, const double* phi, int64_t K, int64_t n,
@@ -2405,7 +2445,9 @@ mbar_status mbar_lse_pass_factorised(const double* a, const double* b, const dou
   p.logden = logden;
   p.mode = kLseModePass;
   p.exact_max = 1;
-  return lse_fact_launch(a, b, phi, lse_fact_plan(K, n), p, static_cast<cudaStream_t>(stream));
+  const LsePlan pl = lse_fact_plan(K, n);
+  void* ref = sc + round_up(static_cast<int64_t>(lse_scratch_for_grid(K, pl.grid)), 256);
+  return lse_fact_launch(a, b, phi, pl, p, nullptr, nullptr, 0, ref, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

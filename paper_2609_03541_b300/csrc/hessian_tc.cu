@@ -392,6 +392,8 @@ constexpr int kClPSlots = 3;
 constexpr int kClPSlotBytes = 128 * 128;      // one FP16 128 x 64 tile
 constexpr int kClPStageBytes = kClPSlots * kClPSlotBytes;
 constexpr int kClMaxTiles = 4;                // MT <= 4, i.e. K <= 512
+constexpr int kClMaxFactTiles = 8;            // factorised form: MT <= 8 (K <= 1024) in distance windows
+constexpr int kClWindow = 3;                  // tile distances per launch of the factorised kernel
 
 __host__ __device__ inline int cl_dmax(int q, int MT) {
   return (MT - 1) / 2 + ((MT % 2 == 0 && q < MT / 2) ? 1 : 0);
@@ -413,6 +415,7 @@ struct ClParams {
   const int32_t* H;
   float* out;     // [slices][T][128][128]
   unsigned* err;
+  int dlo;        // factorised kernel: this launch forms the tiles at distances dlo .. dlo + kClWindow - 1
 };
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -995,25 +998,46 @@ __global__ void __launch_bounds__(kSmjThreadsAll, 1)
   const int MT = p.MT;
   const int r = static_cast<int>(cluster_ctarank());
   const int64_t slice = blockIdx.x / MT;
-  const int dm = cl_dmax(r, MT);
-  const int ntl = dm + 1;
-  const uint32_t ncols = ntl == 1 ? 128u : (ntl == 2 ? 256u : 512u);
+  // This launch forms the tiles (q, q + d) with dlo <= d < dlo + kClWindow
+  // and d <= cl_dmax(q): at most three per CTA, so the accumulators fit one
+  // 512-column TMEM allocation at any MT <= 8. Slot 0 of a P~ stage holds the
+  // CTA's own tile (the A operand); with dlo > 0 the window's B tiles follow
+  // in slots 1 .. 2, with dlo = 0 tile d sits in slot d.
+  const int dlo = p.dlo;
+  const int own = dlo > 0 ? 1 : 0;
+  auto ntiles = [&](int q) {
+    const int hi = min(cl_dmax(q, MT), dlo + kClWindow - 1);
+    return hi >= dlo ? hi - dlo + 1 : 0;
+  };
+  const int ntl = ntiles(r);
+  const uint32_t ncols = ntl <= 1 ? 128u : (ntl == 2 ? 256u : 512u);
   uint32_t reader_mask = 0;
-  for (int q = 0; q < MT; ++q)
-    if ((r - q + MT) % MT <= cl_dmax(q, MT)) reader_mask |= 1u << q;
+  for (int q = 0; q < MT; ++q) {
+    const int d = (r - q + MT) % MT;
+    const int nq = ntiles(q);
+    if (nq > 0 && (d == 0 || (d >= dlo && d < dlo + nq))) reader_mask |= 1u << q;
+  }
   const int nreaders = __popc(reader_mask);
   uint16_t writer_mask = 0;
-  for (int d = 0; d <= dm; ++d) writer_mask |= static_cast<uint16_t>(1u << ((r + d) % MT));
+  if (ntl > 0) {
+    writer_mask = static_cast<uint16_t>(1u << r);
+    for (int d = dlo; d < dlo + ntl; ++d) writer_mask |= static_cast<uint16_t>(1u << ((r + d) % MT));
+  }
+  const int nwriters = __popc(static_cast<uint32_t>(writer_mask));
   const int64_t c_begin = slice * p.per;
   const int64_t c_end = (c_begin + p.per < p.n) ? c_begin + p.per : p.n;
   const int64_t nchunks = c_end > c_begin ? (c_end - c_begin + 63) / 64 : 0;
+  // chunks this CTA produces (none when no CTA reads its tile in this
+  // window) and consumes (none when it forms no tile)
+  const int64_t nprod = nreaders > 0 ? nchunks : 0;
+  const int64_t ncons = ntl > 0 ? nchunks : 0;
 
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   if (tid == 0) {
     for (int b = 0; b < kSmjPStages; ++b) {
       // one chunk is delivered by the four warps of one group of each writer
-      mbar_init(&pfull[b], static_cast<uint32_t>((dm + 1) * (kClWarps / kSmjGroups)));
-      mbar_init(&pempty[b], static_cast<uint32_t>(nreaders));
+      mbar_init(&pfull[b], static_cast<uint32_t>(max(nwriters, 1) * (kClWarps / kSmjGroups)));
+      mbar_init(&pempty[b], static_cast<uint32_t>(max(nreaders, 1)));
     }
     *fail_s = 0;
     fence_barrier_init();
@@ -1045,8 +1069,8 @@ __global__ void __launch_bounds__(kSmjThreadsAll, 1)
     // the chunk's columns are loaded during the group's previous chunk (after
     // its fence: a proxy fence also waits for this thread's loads in flight)
     float pa = 0.f, pb = 0.f, l2a = INFINITY, l2b = INFINITY;
-    if (grp < nchunks) load_cols(grp, pa, pb, l2a, l2b);
-    for (int64_t c = grp; c < nchunks; c += kSmjGroups) {
+    if (grp < nprod) load_cols(grp, pa, pb, l2a, l2b);
+    for (int64_t c = grp; c < nprod; c += kSmjGroups) {
       const int b = static_cast<int>(c % kSmjPStages);
       bool ok = true;
       if (c >= kSmjPStages) {
@@ -1077,9 +1101,9 @@ __global__ void __launch_bounds__(kSmjThreadsAll, 1)
         packed.w = pack_half2(pv[6], pv[7]);
         const uint32_t off = static_cast<uint32_t>(lr * 128 + ((k ^ (lr & 7)) << 4));
 #pragma unroll
-        for (int q = 0; q < kClMaxTiles; ++q) {
+        for (int q = 0; q < kClMaxFactTiles; ++q) {
           if (reader_mask & (1u << q)) {
-            const int slot = (r - q + MT) % MT;
+            const int slot = q == r ? 0 : (r - q + MT) % MT - dlo + own;
             if (q == r)
               *reinterpret_cast<uint4*>(pst + off) = packed;
             else
@@ -1092,10 +1116,10 @@ __global__ void __launch_bounds__(kSmjThreadsAll, 1)
       if (lane == 0)
         for (int q = 0; q < MT; ++q)
           if (reader_mask & (1u << q)) mbar_arrive_cluster(mapa_shared(smem_u32(&pfull[b]), static_cast<uint32_t>(q)));
-      if (c + kSmjGroups < nchunks) load_cols(c + kSmjGroups, pa, pb, l2a, l2b);
+      if (c + kSmjGroups < nprod) load_cols(c + kSmjGroups, pa, pb, l2a, l2b);
     }
   } else {
-    for (int64_t cm = 0; cm < nchunks; ++cm) {
+    for (int64_t cm = 0; cm < ncons; ++cm) {
       const int b = static_cast<int>(cm % kSmjPStages);
       bool ok = true;
       if (lane == 0)
@@ -1112,7 +1136,7 @@ __global__ void __launch_bounds__(kSmjThreadsAll, 1)
 #pragma unroll
           for (int k4 = 0; k4 < 4; ++k4)
             umma_f16(tmem + static_cast<uint32_t>(t * 128), sdesc_sw128(base + k4 * 32),
-                     sdesc_sw128(base + static_cast<uint32_t>(t * kClPSlotBytes) + k4 * 32), idesc,
+                     sdesc_sw128(base + static_cast<uint32_t>((t + own) * kClPSlotBytes) + k4 * 32), idesc,
                      (cm > 0 || k4 > 0) ? 1u : 0u);
         }
         umma_commit_multicast(&pempty[b], writer_mask);
@@ -1122,16 +1146,16 @@ __global__ void __launch_bounds__(kSmjThreadsAll, 1)
   }
   __syncthreads();
   bool failed = *fail_s != 0;
-  if (!failed && nchunks > 0) {
+  if (!failed && nprod > 0) {
     bool ok = true;
-    for (int64_t last = nchunks - 1; last >= 0 && last >= nchunks - kSmjPStages; --last)
+    for (int64_t last = nprod - 1; last >= 0 && last >= nprod - kSmjPStages; --last)
       ok = ok && mbar_wait_cluster_bounded(&pempty[last % kSmjPStages],
                                            static_cast<uint32_t>((last / kSmjPStages) & 1), kMaxSpins);
     if (__syncthreads_or(!ok)) failed = true;
   }
   if (failed && tid == 0) atomicAdd(p.err, 1u);
   tc_fence_after();
-  float* out = p.out + (slice * p.T + cl_tile_base(r, MT)) * 128 * 128;
+  float* out = p.out + (slice * p.T + cl_tile_base(r, MT) + dlo) * 128 * 128;
   const int sub = warp & 3;
   const int quarter = warp >> 2;
   const int row_local = sub * 32 + lane;
@@ -1298,7 +1322,7 @@ size_t overlap_tc_tmp_bytes(int64_t K, int64_t n) {
   const size_t nc = pl.ctas.size(), ni = pl.first.size();
   const size_t items = round_up(static_cast<int64_t>(nc) * 128 * 512 * 4, 256) + round_up(nc * sizeof(TcCta), 256) +
                        round_up(2 * ni * sizeof(int), 256) + 256;
-  return K <= 128 * kClMaxTiles ? std::max(items, cl_tmp_bytes(K)) : items;
+  return K <= 128 * kClMaxFactTiles ? std::max(items, cl_tmp_bytes(K)) : items;
 }
 
 static mbar_status overlap_tc_cluster(const void* v, int64_t K, int64_t n, int64_t ld, const double* a,
@@ -1495,7 +1519,7 @@ mbar_status overlap_tc_smaj(const float* vst, int64_t K, int64_t n, const double
 mbar_status overlap_tc_fact(const double* fa, const double* fb, const double* fphi, int64_t K, int64_t n,
                             const double* a, const double* logden, double* G, unsigned* err, void* tmp,
                             size_t tmp_bytes, cudaStream_t st) {
-  if (K < 1 || K > 128 * kClMaxTiles) {
+  if (K < 1 || K > 128 * kClMaxFactTiles) {
     set_error("overlap_tc_fact: unsupported K=%lld", static_cast<long long>(K));
     return MBAR_EUNSUPPORTED;
   }
@@ -1505,7 +1529,7 @@ mbar_status overlap_tc_fact(const double* fa, const double* fb, const double* fp
   }
   const int MT = static_cast<int>(ceil_div(K, 128));
   const size_t smem = static_cast<size_t>(kSmjPStages) * kClPStageBytes + 128 + 1024;
-  static int resident[kClMaxTiles + 1] = {0, 0, 0, 0, 0};
+  static int resident[kClMaxFactTiles + 1] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   {
     std::lock_guard<std::recursive_mutex> lock(init_mutex());
     if (resident[MT] == 0) {
@@ -1560,8 +1584,13 @@ mbar_status overlap_tc_fact(const double* fa, const double* fb, const double* fp
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BUMBAR_CUDA(cudaLaunchKernelEx(&cfg, overlap_tc_fact_kernel, fa, fb, fphi, logden, prm));
-  count_launches(1);
+  // one launch per window of kClWindow tile distances (two at MT = 6..8);
+  // every launch forms all of P~ and writes its own tiles of the partials
+  for (int dlo = 0; dlo <= cl_dmax(0, MT); dlo += kClWindow) {
+    prm.dlo = dlo;
+    BUMBAR_CUDA(cudaLaunchKernelEx(&cfg, overlap_tc_fact_kernel, fa, fb, fphi, logden, prm));
+    count_launches(1);
+  }
   reduce_tc_cluster<<<dim3(128 * 128 / 256, static_cast<unsigned>(pl.T)), 256, 0, st>>>(prm.out, pl.S, pl.T, pl.MT,
                                                                                        static_cast<int>(K), G);
   count_launches(1);

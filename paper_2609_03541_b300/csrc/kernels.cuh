@@ -108,8 +108,25 @@ mbar_status lse_epilogue_launch(const LseParams& prm, cudaStream_t stream);
 // u_kn = a_k + b_k phi_n into a K x N FP64 buffer (prep.cu)
 mbar_status factorised_u(const double* a, const double* b, const double* phi, int64_t K, int64_t N, double* u,
                          cudaStream_t st);
+// Reference-state table of a factorised pass: the state of the largest
+// exponent at kRefGrid points spread evenly over [min phi, max phi]; a
+// sample's state is state[rint((phi - lo) * inv_step)] (clamped).
+constexpr int kRefGrid = 4096;
+struct FactRef {
+  float lo, inv_step;
+  int pad[2];
+  int16_t state[kRefGrid];
+};
+// Device bytes of a pass's table plus the partial (min, max) of phi that a
+// pass without a known range computes first.
+size_t lse_fact_ref_bytes();
 LsePlan lse_fact_plan(int64_t K, int64_t n);
+// phi_min / phi_max: device pointers to `nparts` partial minima / maxima of
+// phi (a sorted copy's first and last element, nparts = 1), or nullptr: the
+// range is then reduced from phi into `ref_buf` first. ref_buf: device,
+// lse_fact_ref_bytes(), 16-byte aligned.
 mbar_status lse_fact_launch(const double* a, const double* b, const double* phi, const LsePlan& pl, LseParams prm,
+                            const double* phi_min, const double* phi_max, int nparts, void* ref_buf,
                             cudaStream_t st);
 LsePlan lse_regs_plan(int64_t K, int64_t n);
 mbar_status lse_regs_launch(const CUtensorMap& tmap, const LsePlan& pl, const LseParams& prm, cudaStream_t st);
@@ -214,7 +231,7 @@ size_t hessian_tmp_bytes(int64_t K, int64_t n);
 // hessian_smaj_eligible when the tensor-core cluster kernel does not take
 // this K (the caller then uses hessian on the row-major store).
 bool hessian_smaj_eligible(int64_t K);
-// The Hessian of a factorised context's unbinned data (K <= 512).
+// The Hessian of a factorised context's unbinned data (K <= 1024).
 mbar_status hessian_fact(const double* fa, const double* fb, const double* fphi, int64_t K, int64_t n,
                          const double* f, const double* logN, const double* logden, double* hess, unsigned* err,
                          void* tmp, size_t tmp_bytes, cudaStream_t stream);
@@ -231,7 +248,8 @@ mbar_status overlap_tc(const void* v, int dtype_bytes, int64_t K, int64_t n, int
 size_t overlap_tc_tmp_bytes(int64_t K, int64_t n);
 bool overlap_tc_smaj_eligible(int64_t K);
 // Factorised data (u_ip = a_i + b_i phi_p; phi and logden FP64, original
-// sample order), K <= 512.
+// sample order), K <= 1024: clusters of ceil(K / 128) CTAs, one launch per
+// window of three tile distances (two launches above K = 640).
 mbar_status overlap_tc_fact(const double* fa, const double* fb, const double* fphi, int64_t K, int64_t n,
                             const double* a, const double* logden, double* G, unsigned* err, void* tmp,
                             size_t tmp_bytes, cudaStream_t st);
@@ -274,6 +292,8 @@ mbar_status newton_solve(double* hess, int64_t K, const double* g, double* delta
 size_t newton_tmp_bytes(int64_t K);
 
 // small helpers (prep.cu)
-mbar_status vec_add_gauge(const double* f, const double* d, double* out, int64_t K, cudaStream_t stream);
+// out = f + t d in the gauge out_0 = 0
+mbar_status vec_add_gauge(const double* f, const double* d, double* out, int64_t K, cudaStream_t stream,
+                          double t = 1.0);
 
 }  // namespace bumbar

@@ -10,15 +10,19 @@
 //
 // Arithmetic: per state the FP64 constants c_k = (f_k + log N_k - a_k)
 // log2(e) and b'_k = b_k log2(e) become unevaluated FP32 pairs (hi, lo), as
-// does each phi_p. The exponent in log2 units,
-//     x_kp = c_k - b'_k phi_p
-//          = fma(-b_hi, p_hi, c_hi) + fma(-b_lo, p_hi, fma(-b_hi, p_lo, c_lo)),
-// rounds once where c_k and b'_k phi_p cancel (the first fma is exact before
-// its rounding), so x carries an absolute error of about one FP32 ulp of x
-// itself even when a_k + b_k phi_p is thousands of kT (tempering energies);
-// the dropped b_lo p_lo term is 2^-48 of the product. Four FP32 operations
-// per entry, then max, ex2, sum and one FMA into the row partial.
-//
+// does each phi_p. Each sample is taken relative to a reference state r(p)
+// close to its largest exponent (a table of the maximising state at 4096
+// points spread over the range of phi, built per pass by fact_ref_kernel):
+//     x_kp - x_rp = [(c_hi,k - c_hi,r) - (b_hi,k - b_hi,r) p_hi]
+//                 + [lo_k - lo_r],   lo_k = c_lo,k - b_lo,k p_hi - b_hi,k p_lo.
+// Where c_k and c_r (b'_k and b'_r) lie within a factor of two of each other
+// -- the states that carry weight, on large magnitudes -- both differences
+// are exact (Sterbenz); elsewhere they round at their own magnitude. The
+// bracket then rounds once, at the magnitude of x_kp - x_rp rather than of
+// x_kp: u in the thousands or hundreds of thousands of kT (replica ladders
+// u = beta_k E) keeps the accuracy of u near 0. The dropped b_lo p_lo term is
+// 2^-48 of the product. The pairs of entries go through f32x2 instructions:
+// seven per two entries, then max, ex2, sum and one FMA into the row partial.
 // Schedule: one CTA per SM, every warp computes. Warps take 32-sample chunks
 // round robin over the grid; lane l loads phi (and H) of sample l of the
 // chunk, and LPS-lane groups take the samples one after another (shuffles).
@@ -54,6 +58,91 @@ __device__ __forceinline__ void split_pair_fast(double x, float& hi, float& lo) 
   if (!split_f64(x, hi, lo)) split_pair(x, hi, lo);
 }
 
+constexpr int kRangeParts = 256;  // partial (min, max) of phi for a pass without a known range
+constexpr int kRefThreads = 256;
+
+// Per-CTA min and max of phi (grid-stride), for passes given no range.
+__global__ void __launch_bounds__(kRefThreads) fact_range_kernel(const double* __restrict__ phi, int64_t n,
+                                                                 double* __restrict__ mins,
+                                                                 double* __restrict__ maxs) {
+  __shared__ double smin[kRefThreads], smax[kRefThreads];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * kRefThreads + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kRefThreads) {
+    const double v = phi[i];
+    lo = fmin(lo, v);
+    hi = fmax(hi, v);
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int o = kRefThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    mins[blockIdx.x] = smin[0];
+    maxs[blockIdx.x] = smax[0];
+  }
+}
+
+// The reference-state table of one pass: the range [lo, hi] of phi from
+// `nparts` partial minima and maxima, then for grid point g (one thread) the
+// state maximising c_k - b'_k phi_g, phi_g = lo + g (hi - lo) / (G - 1), in
+// FP32 (a state within rounding of the maximum serves as well). States of
+// weight zero (c_k = -inf) are never chosen while another state exists.
+__global__ void __launch_bounds__(kRefThreads) fact_ref_kernel(const double* __restrict__ a,
+                                                               const double* __restrict__ b, const double* f,
+                                                               const double* logN, int K, const double* mins,
+                                                               const double* maxs, int nparts, FactRef* out) {
+  __shared__ float2 cb[1024];
+  __shared__ double slo[kRefThreads], shi[kRefThreads];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = threadIdx.x; i < nparts; i += kRefThreads) {
+    lo = fmin(lo, mins[i]);
+    hi = fmax(hi, maxs[i]);
+  }
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  for (int k = threadIdx.x; k < K; k += kRefThreads)
+    cb[k] = make_float2(static_cast<float>((f[k] + logN[k] - a[k]) * 1.4426950408889634),
+                        static_cast<float>(b[k] * 1.4426950408889634));
+  __syncthreads();
+  for (int o = kRefThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + o]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  lo = slo[0];
+  hi = shi[0];
+  const bool spread = hi > lo;
+  const double step = spread ? (hi - lo) / (kRefGrid - 1) : 0.0;
+  const int g = blockIdx.x * kRefThreads + threadIdx.x;
+  if (g < kRefGrid) {
+    const float x = static_cast<float>(lo + step * g);
+    int best = 0;
+    float bv = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+      const float2 c = cb[k];
+      const float v = fmaf(-c.y, x, c.x);
+      if (v > bv) {
+        bv = v;
+        best = k;
+      }
+    }
+    out->state[g] = static_cast<int16_t>(best);
+  }
+  if (g == 0) {
+    out->lo = static_cast<float>(lo);
+    out->inv_step = spread ? static_cast<float>(1.0 / step) : 0.f;
+  }
+}
+
 }  // namespace
 
 // EXACT: the state(s) attaining a sample's maximum exponent contribute
@@ -64,14 +153,16 @@ __device__ __forceinline__ void split_pair_fast(double x, float& hi, float& lo) 
 // terms close to 1 lose their deficits r, which biases Q by up to ~6e-8 N).
 template <int LPS, int NK, int NT, bool EXACT>
 __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                                         const double* __restrict__ phi, int Kp, LseParams p) {
+                                                         const double* __restrict__ phi, int Kp,
+                                                         const FactRef* __restrict__ ref, LseParams p) {
   constexpr int SPW = 32 / LPS;  // samples per warp at once
   constexpr int NW = NT / 32;
   constexpr int E = 4 * NK;      // states per lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* cst = reinterpret_cast<float4*>(smem_raw);   // [Kp] (c_hi, c_lo, b_hi, b_lo)
   float2* rows = reinterpret_cast<float2*>(cst + Kp);  // [NW][Kp] unevaluated sums hi + lo
-  unsigned* cnt = reinterpret_cast<unsigned*>(rows + static_cast<size_t>(NW) * Kp);  // [NW][Kp], EXACT, LPS < 32
+  int16_t* tbl = reinterpret_cast<int16_t*>(rows + static_cast<size_t>(NW) * Kp);  // [kRefGrid] reference states
+  unsigned* cnt = reinterpret_cast<unsigned*>(tbl + kRefGrid);  // [NW][Kp], EXACT, LPS < 32
   const int K = p.K;
   const int64_t n = p.n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -86,23 +177,29 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
     cst[k] = c;
   }
   for (int i = tid; i < NW * Kp; i += NT) rows[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < kRefGrid / 8; i += NT)
+    reinterpret_cast<int4*>(tbl)[i] = reinterpret_cast<const int4*>(ref->state)[i];
   if constexpr (EXACT && LPS < 32)
     for (int i = tid; i < NW * Kp; i += NT) cnt[i] = 0u;
+  const float ref_lo = ref->lo, ref_inv = ref->inv_step;
   __syncthreads();
 
   const int lig = lane % LPS;  // lane in group
   const int grp = lane / LPS;  // sample group within the warp
-  float ch[E], cl[E], bh[E], bl[E];
+  // entries e and e + 1 of the lane side by side (f32x2): c_hi, c_lo, -b_hi, -b_lo
+  unsigned long long ch2[E / 2], cl2[E / 2], nbh2[E / 2], nbl2[E / 2];
 #pragma unroll
   for (int i = 0; i < NK; ++i)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < 4; t += 2) {
       const int k = 4 * (lig + LPS * i) + t;
-      const float4 c = k < Kp ? cst[k] : make_float4(-INFINITY, 0.f, 0.f, 0.f);
-      ch[4 * i + t] = c.x;
-      cl[4 * i + t] = c.y;
-      bh[4 * i + t] = c.z;
-      bl[4 * i + t] = c.w;
+      const float4 c0 = k < Kp ? cst[k] : make_float4(-INFINITY, 0.f, 0.f, 0.f);
+      const float4 c1 = k + 1 < Kp ? cst[k + 1] : make_float4(-INFINITY, 0.f, 0.f, 0.f);
+      const int q = (4 * i + t) / 2;
+      ch2[q] = pk2(c0.x, c1.x);
+      cl2[q] = pk2(c0.y, c1.y);
+      nbh2[q] = pk2(-c0.z, -c1.z);
+      nbl2[q] = pk2(-c0.w, -c1.w);
     }
   float acc[E];
 #pragma unroll
@@ -140,18 +237,38 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       split_pair_fast(phi[base + lane], ph_l, pl_l);
       h_l = p.H ? static_cast<float>(p.H[base + lane]) : 1.f;
     }
+    // the lane's sample: reference state r from the table, its c_hi and b_hi,
+    // and lo_r = c_lo,r - b_lo,r p_hi - b_hi,r p_lo
+    float chr_l, bhr_l, lor_l;
+    {
+      const int g = min(max(__float2int_rn((ph_l - ref_lo) * ref_inv), 0), kRefGrid - 1);
+      const float4 cr = cst[tbl[g]];
+      chr_l = cr.x;
+      bhr_l = cr.z;
+      lor_l = fmaf(-cr.w, ph_l, fmaf(-cr.z, pl_l, cr.y));
+    }
     float ld_mine = 0.f;  // logden of sample `lane` of the chunk, written once per chunk
     for (int j0 = 0; j0 < nloc; j0 += SPW) {
       const int j = j0 + grp;  // < 32: j0 is a multiple of SPW, grp < SPW
       const float ph = __shfl_sync(0xffffffffu, ph_l, j);
       const float pl = __shfl_sync(0xffffffffu, pl_l, j);
       const float hw = __shfl_sync(0xffffffffu, h_l, j);
-      float x[E];
+      const float chr = __shfl_sync(0xffffffffu, chr_l, j);
+      const float bhr = __shfl_sync(0xffffffffu, bhr_l, j);
+      const float lor = __shfl_sync(0xffffffffu, lor_l, j);
+      const unsigned long long ph2 = pk2(ph, ph), pl2 = pk2(pl, pl);
+      const unsigned long long nchr2 = pk2(-chr, -chr), bhr2 = pk2(bhr, bhr), nlor2 = pk2(-lor, -lor);
+      float x[E];  // x_kp - x_rp (log2 units)
       float m0 = -INFINITY, m1 = -INFINITY;
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        x[e] = fmaf(-bh[e], ph, ch[e]) + fmaf(-bl[e], ph, fmaf(-bh[e], pl, cl[e]));
-        if (e & 1) m1 = fmaxf(m1, x[e]); else m0 = fmaxf(m0, x[e]);
+      for (int q = 0; q < E / 2; ++q) {
+        const unsigned long long dch = add2(ch2[q], nchr2);     // c_hi,k - c_hi,r (exact)
+        const unsigned long long ndb = add2(nbh2[q], bhr2);     // -(b_hi,k - b_hi,r) (exact)
+        const unsigned long long xh = fma2(ndb, ph2, dch);      // one rounding
+        const unsigned long long lo = fma2(nbl2[q], ph2, fma2(nbh2[q], pl2, cl2[q]));
+        upk2(add2(xh, add2(lo, nlor2)), x[2 * q], x[2 * q + 1]);
+        m0 = fmaxf(m0, x[2 * q]);
+        m1 = fmaxf(m1, x[2 * q + 1]);
       }
       float m = fmaxf(m0, m1);
 #pragma unroll
@@ -194,7 +311,8 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       const float w = j < nloc ? hw * rcp_approx(s) : 0.f;
       // every lane of a group holds its sample's m and s: lane l takes the
       // logden of sample l from the group that has it in this round
-      const float lv = (m + __log2f(s)) * kLn2;
+      // logden_p = (x_rp + m + log2 s) ln 2, x_rp = c_r - b'_r phi_p
+      const float lv = ((fmaf(-bhr, ph, chr) + lor) + (m + __log2f(s))) * kLn2;
       const float lv_l = __shfl_sync(0xffffffffu, lv, ((lane - j0) & (SPW - 1)) * LPS);
       if (lane >= j0 && lane < j0 + SPW) ld_mine = lv_l;
 #pragma unroll
@@ -253,7 +371,7 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
 namespace {
 
 template <int LPS, int NK, int NT, bool EXACT>
-void fact_run_one(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp,
+void fact_run_one(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp, const FactRef* ref,
                   const LseParams& prm, cudaStream_t st) {
   static bool init = false;
   {
@@ -267,14 +385,14 @@ void fact_run_one(const LsePlan& pl, const double* a, const double* b, const dou
       init = true;
     }
   }
-  lse_fact_kernel<LPS, NK, NT, EXACT><<<pl.grid, NT, pl.smem, st>>>(a, b, phi, Kp, prm);
+  lse_fact_kernel<LPS, NK, NT, EXACT><<<pl.grid, NT, pl.smem, st>>>(a, b, phi, Kp, ref, prm);
 }
 
 template <int LPS, int NK, int NT>
-void fact_run(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp, const LseParams& prm,
-              cudaStream_t st) {
-  if (prm.exact_max) fact_run_one<LPS, NK, NT, true>(pl, a, b, phi, Kp, prm, st);
-  else fact_run_one<LPS, NK, NT, false>(pl, a, b, phi, Kp, prm, st);
+void fact_run(const LsePlan& pl, const double* a, const double* b, const double* phi, int Kp, const FactRef* ref,
+              const LseParams& prm, cudaStream_t st) {
+  if (prm.exact_max) fact_run_one<LPS, NK, NT, true>(pl, a, b, phi, Kp, ref, prm, st);
+  else fact_run_one<LPS, NK, NT, false>(pl, a, b, phi, Kp, ref, prm, st);
 }
 
 }  // namespace
@@ -301,18 +419,46 @@ LsePlan lse_fact_plan(int64_t K, int64_t n) {
   pl.C = 32;
   pl.num_strips = static_cast<int>(ceil_div(n, 32));
   // + the per-warp counts of the exact split below 32 lanes per sample
-  pl.smem = static_cast<size_t>(Kp) * 16 + static_cast<size_t>(nt / 32) * Kp * (lps < 32 ? 12 : 8);
+  pl.smem = static_cast<size_t>(Kp) * 16 + static_cast<size_t>(nt / 32) * Kp * (lps < 32 ? 12 : 8) +
+            static_cast<size_t>(kRefGrid) * sizeof(int16_t);
   pl.ok = K >= 1 && K <= 1024;
   // every warp of every CTA gets at least one chunk where n allows
   pl.grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(pl.num_strips, nt / 32), num_sms())));
   return pl;
 }
 
+size_t lse_fact_ref_bytes() {
+  return round_up(static_cast<int64_t>(sizeof(FactRef)), 256) + 2 * kRangeParts * sizeof(double);
+}
+
 mbar_status lse_fact_launch(const double* a, const double* b, const double* phi, const LsePlan& pl, LseParams prm,
+                            const double* phi_min, const double* phi_max, int nparts, void* ref_buf,
                             cudaStream_t st) {
   if (!pl.ok) {
     set_error("factorised lse pass: unsupported K=%d", prm.K);
     return MBAR_EUNSUPPORTED;
+  }
+  if (!ref_buf || (reinterpret_cast<uintptr_t>(ref_buf) & 15) != 0) {
+    set_error("factorised lse pass: the reference-table buffer must be 16-byte aligned");
+    return MBAR_EINVAL;
+  }
+  FactRef* ref = static_cast<FactRef*>(ref_buf);
+  {
+    // a pass its guard skips still builds the table (it only reads f)
+    if (!phi_min) {
+      double* mins = reinterpret_cast<double*>(static_cast<unsigned char*>(ref_buf) +
+                                               round_up(static_cast<int64_t>(sizeof(FactRef)), 256));
+      double* maxs = mins + kRangeParts;
+      const int g = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kRangeParts, ceil_div(prm.n, 4096))));
+      fact_range_kernel<<<g, kRefThreads, 0, st>>>(phi, prm.n, mins, maxs);
+      phi_min = mins;
+      phi_max = maxs;
+      nparts = g;
+      count_launches(1);
+    }
+    fact_ref_kernel<<<kRefGrid / kRefThreads, kRefThreads, 0, st>>>(a, b, prm.f, prm.logN, prm.K, phi_min, phi_max,
+                                                                     nparts, ref);
+    count_launches(1);
   }
   prm.nparts = pl.grid;
   prm.epi = prm.partials + static_cast<size_t>(pl.grid) * prm.K;
@@ -321,21 +467,21 @@ mbar_status lse_fact_launch(const double* a, const double* b, const double* phi,
   // the instances the shape rule reaches: one lane per sample with 1, 2 or
   // 4 chunks; 2..16 lanes with 4 chunks; 32 lanes with 3..8 chunks
   bool ok = true;
-  if (lps == 1 && nk == 1) fact_run<1, 1, 512>(pl, a, b, phi, Kp, prm, st);
-  else if (lps == 1 && nk == 2) fact_run<1, 2, 512>(pl, a, b, phi, Kp, prm, st);
-  else if (lps == 1 && nk == 4) fact_run<1, 4, 384>(pl, a, b, phi, Kp, prm, st);
-  else if (lps == 2 && nk == 4) fact_run<2, 4, 384>(pl, a, b, phi, Kp, prm, st);
-  else if (lps == 4 && nk == 4) fact_run<4, 4, 384>(pl, a, b, phi, Kp, prm, st);
-  else if (lps == 8 && nk == 4) fact_run<8, 4, 384>(pl, a, b, phi, Kp, prm, st);
-  else if (lps == 16 && nk == 4) fact_run<16, 4, 384>(pl, a, b, phi, Kp, prm, st);
+  if (lps == 1 && nk == 1) fact_run<1, 1, 512>(pl, a, b, phi, Kp, ref, prm, st);
+  else if (lps == 1 && nk == 2) fact_run<1, 2, 512>(pl, a, b, phi, Kp, ref, prm, st);
+  else if (lps == 1 && nk == 4) fact_run<1, 4, 384>(pl, a, b, phi, Kp, ref, prm, st);
+  else if (lps == 2 && nk == 4) fact_run<2, 4, 384>(pl, a, b, phi, Kp, ref, prm, st);
+  else if (lps == 4 && nk == 4) fact_run<4, 4, 384>(pl, a, b, phi, Kp, ref, prm, st);
+  else if (lps == 8 && nk == 4) fact_run<8, 4, 384>(pl, a, b, phi, Kp, ref, prm, st);
+  else if (lps == 16 && nk == 4) fact_run<16, 4, 384>(pl, a, b, phi, Kp, ref, prm, st);
   else if (lps == 32) {
     switch (nk) {
-      case 3: fact_run<32, 3, 512>(pl, a, b, phi, Kp, prm, st); break;
-      case 4: fact_run<32, 4, 384>(pl, a, b, phi, Kp, prm, st); break;
-      case 5: fact_run<32, 5, 256>(pl, a, b, phi, Kp, prm, st); break;
-      case 6: fact_run<32, 6, 256>(pl, a, b, phi, Kp, prm, st); break;
-      case 7: fact_run<32, 7, 256>(pl, a, b, phi, Kp, prm, st); break;
-      case 8: fact_run<32, 8, 256>(pl, a, b, phi, Kp, prm, st); break;
+      case 3: fact_run<32, 3, 512>(pl, a, b, phi, Kp, ref, prm, st); break;
+      case 4: fact_run<32, 4, 384>(pl, a, b, phi, Kp, ref, prm, st); break;
+      case 5: fact_run<32, 5, 256>(pl, a, b, phi, Kp, ref, prm, st); break;
+      case 6: fact_run<32, 6, 256>(pl, a, b, phi, Kp, ref, prm, st); break;
+      case 7: fact_run<32, 7, 256>(pl, a, b, phi, Kp, ref, prm, st); break;
+      case 8: fact_run<32, 8, 256>(pl, a, b, phi, Kp, ref, prm, st); break;
       default: ok = false;
     }
   } else {

@@ -407,12 +407,13 @@ __global__ void finite_kernel(const double* __restrict__ x, int64_t n, int* bad)
   if (i < n && !isfinite(x[i])) atomicOr(bad, 1);
 }
 
+// out = (f + t d) - (f_0 + t d_0); t = 1 gives f + d exactly
 __global__ void add_gauge_kernel(const double* __restrict__ f, const double* __restrict__ d, double* __restrict__ out,
-                                 int64_t K) {
+                                 int64_t K, double t) {
   __shared__ double base;
-  if (threadIdx.x == 0) base = f[0] + d[0];
+  if (threadIdx.x == 0) base = fma(t, d[0], f[0]);
   __syncthreads();
-  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) out[k] = (f[k] + d[k]) - base;
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) out[k] = fma(t, d[k], f[k]) - base;
 }
 
 }  // namespace
@@ -496,8 +497,8 @@ mbar_status check_finite(const double* x, int64_t n, int* bad, cudaStream_t st) 
   return MBAR_OK;
 }
 
-mbar_status vec_add_gauge(const double* f, const double* d, double* out, int64_t K, cudaStream_t st) {
-  add_gauge_kernel<<<1, kThreads, 0, st>>>(f, d, out, K);
+mbar_status vec_add_gauge(const double* f, const double* d, double* out, int64_t K, cudaStream_t st, double t) {
+  add_gauge_kernel<<<1, kThreads, 0, st>>>(f, d, out, K, t);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;

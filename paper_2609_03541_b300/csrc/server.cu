@@ -37,6 +37,10 @@ struct Request {
   int32_t u_on_device = 0;
   const double* phi = nullptr;
   int32_t phi_on_device = 0;
+  // factorised form u_kn = fa_k + fb_k phi_n (phi above; same residence)
+  bool factorised = false;
+  const double* fa = nullptr;
+  const double* fb = nullptr;
   uint64_t bytes = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
   int passed_over = 0;
@@ -65,6 +69,22 @@ uint64_t footprint(int64_t K, int64_t N, int32_t precision, int32_t use_binning,
   const uint64_t solve = e * el + (keeps_copy ? es * 4 : 0) + (use_binning ? e * el * 6 / 10 : 0);
   const uint64_t fixed = static_cast<uint64_t>(N) * 96 + static_cast<uint64_t>(K) * K * 8 * 4 + (64ull << 20);
   return std::max(std::max(create, coord), solve) + fixed;
+}
+
+// Peak device memory of a solve from the factorised form. MIXED with
+// binning keeps no K x N store: Algorithm 1's binned levels (as above), the
+// FP64 a, b, phi and per-sample vectors (sort keys, permutations, bin
+// segments, FP64 and FP32 logden), and the Hessian's scratch. Other options
+// materialise u as a K x N FP64 buffer on the device first.
+uint64_t footprint_factorised(int64_t K, int64_t N, int32_t precision, int32_t use_binning) {
+  if (K < 1 || N < 1) return 0;
+  if (precision == MBAR_MIXED && use_binning) {
+    const uint64_t e = static_cast<uint64_t>(K) * static_cast<uint64_t>(round_up(N, 32));
+    const uint64_t fixed = static_cast<uint64_t>(N) * 192 + static_cast<uint64_t>(K) * K * 8 * 4 +
+                           hessian_tmp_bytes(K, N) + (64ull << 20);
+    return e * 4 * 6 / 10 + fixed;
+  }
+  return static_cast<uint64_t>(K) * static_cast<uint64_t>(N) * 8 + footprint(K, N, precision, use_binning, 1);
 }
 
 }  // namespace
@@ -117,11 +137,13 @@ struct mbar_server {
 
   void run_one(Request& r, cudaStream_t st) {
     mbar_ctx* ctx = nullptr;
-    mbar_status s = mbar_create(&ctx, r.K, r.N, r.Nk.data(), r.u, r.u_on_device, &cfg.opts, st);
+    mbar_status s = r.factorised ? mbar_create_factorised(&ctx, r.K, r.N, r.Nk.data(), r.fa, r.fb, r.phi,
+                                                          r.phi_on_device, &cfg.opts, st)
+                                 : mbar_create(&ctx, r.K, r.N, r.Nk.data(), r.u, r.u_on_device, &cfg.opts, st);
     // no stream capture on worker threads: the caller's other threads may
     // synchronise the whole device at any time
     if (s == MBAR_OK) ctx_set_graphs(ctx, false);
-    if (s == MBAR_OK && r.phi) s = mbar_set_coordinate(ctx, r.phi, r.phi_on_device);
+    if (s == MBAR_OK && r.phi && !r.factorised) s = mbar_set_coordinate(ctx, r.phi, r.phi_on_device);
     if (s == MBAR_OK || s == MBAR_ENOTCONV) {
       if (s == MBAR_OK) s = mbar_solve(ctx, nullptr, &r.report);
       r.f.assign(static_cast<size_t>(r.K), 0.0);
@@ -163,7 +185,39 @@ struct mbar_server {
   }
 };
 
+namespace {
+
+// Charges, records and queues a prepared request (its footprint in
+// r->bytes); `who` names the entry point in error messages.
+mbar_status enqueue(mbar_server* s, const std::shared_ptr<Request>& r, int64_t* id, const char* who) {
+  if (r->bytes > s->cfg.hbm_budget_bytes) {
+    set_error("%s: the request needs about %llu bytes of device memory, more than the server's budget of %llu", who,
+              static_cast<unsigned long long>(r->bytes), static_cast<unsigned long long>(s->cfg.hbm_budget_bytes));
+    return MBAR_EUNSUPPORTED;
+  }
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      set_error("%s: the server is shutting down", who);
+      return MBAR_ESTATE;
+    }
+    r->id = s->next_id++;
+    s->all[r->id] = r;
+    s->queue.push_back(r);
+    s->admit_locked();
+  }
+  *id = r->id;
+  return MBAR_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+uint64_t mbar_footprint_factorised_bytes(int64_t K, int64_t N, int32_t precision, int32_t use_binning) {
+  return footprint_factorised(K, N, precision, use_binning);
+}
 
 uint64_t mbar_footprint_bytes(int64_t K, int64_t N, int32_t precision, int32_t use_binning) {
   return footprint(K, N, precision, use_binning, 0);
@@ -222,26 +276,31 @@ mbar_status mbar_server_submit(mbar_server* s, int64_t K, int64_t N, const int64
   r->phi = phi;
   r->phi_on_device = phi_on_device;
   r->bytes = footprint(K, N, s->cfg.opts.precision, s->cfg.opts.use_binning, u_on_device);
-  if (r->bytes > s->cfg.hbm_budget_bytes) {
-    set_error("mbar_server_submit: the request needs about %llu bytes of device memory, more than the server's "
-              "budget of %llu",
-              static_cast<unsigned long long>(r->bytes), static_cast<unsigned long long>(s->cfg.hbm_budget_bytes));
-    return MBAR_EUNSUPPORTED;
+  return enqueue(s, r, id, "mbar_server_submit");
+}
+
+mbar_status mbar_server_submit_factorised(mbar_server* s, int64_t K, int64_t N, const int64_t* N_k,
+                                          const double* a, const double* b, const double* phi, int32_t on_device,
+                                          int64_t* id) {
+  if (!s || !N_k || !a || !b || !phi || !id) {
+    set_error("mbar_server_submit_factorised: null pointer argument");
+    return MBAR_EINVAL;
   }
-  r->t_submit = Clock::now();
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stop) {
-      set_error("mbar_server_submit: the server is shutting down");
-      return MBAR_ESTATE;
-    }
-    r->id = s->next_id++;
-    s->all[r->id] = r;
-    s->queue.push_back(r);
-    s->admit_locked();
+  if (K < 1 || N < 1 || K > 1024) {
+    set_error("mbar_server_submit_factorised: need 1 <= K <= 1024 and N >= 1");
+    return K > 1024 ? MBAR_EUNSUPPORTED : MBAR_EINVAL;
   }
-  *id = r->id;
-  return MBAR_OK;
+  auto r = std::make_shared<Request>();
+  r->K = K;
+  r->N = N;
+  r->Nk.assign(N_k, N_k + K);
+  r->factorised = true;
+  r->fa = a;
+  r->fb = b;
+  r->phi = phi;
+  r->phi_on_device = on_device;
+  r->bytes = footprint_factorised(K, N, s->cfg.opts.precision, s->cfg.opts.use_binning);
+  return enqueue(s, r, id, "mbar_server_submit_factorised");
 }
 
 mbar_status mbar_server_poll(mbar_server* s, int64_t id, int32_t* state) {

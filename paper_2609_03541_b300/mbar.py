@@ -119,6 +119,10 @@ _SIGNATURES = {
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int64, _dp], ctypes.c_int),
     "mbar_selftest_wait_timeout": ([ctypes.c_int64, _dp], ctypes.c_int),
     "mbar_footprint_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32], ctypes.c_uint64),
+    "mbar_footprint_factorised_bytes": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32],
+                                        ctypes.c_uint64),
+    "mbar_server_submit_factorised": ([_vp, ctypes.c_int64, ctypes.c_int64, _i64p, _vp, _vp, _vp, ctypes.c_int32,
+                                       _i64p], ctypes.c_int),
     "mbar_server_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ServerConfig)], ctypes.c_int),
     "mbar_server_submit": ([_vp, ctypes.c_int64, ctypes.c_int64, _i64p, _vp, ctypes.c_int32, _vp, ctypes.c_int32,
                             _i64p], ctypes.c_int),
@@ -192,6 +196,30 @@ def _device_ptr(x):
     return None, 0
 
 
+def _factorised_args(a, b, phi, K: int):
+    """(arrays kept alive, [a, b, phi] pointers, N, on_device) of a
+    factorised input: float64 ``a``, ``b`` (K) and ``phi`` (N), all numpy
+    arrays or all contiguous float64 CUDA tensors."""
+    ptrs = [_device_ptr(x) for x in (a, b, phi)]
+    on_dev = ptrs[0][1]
+    if any(p[1] != on_dev for p in ptrs):
+        raise ValueError("a, b and phi must all be host arrays or all CUDA tensors")
+    if on_dev:
+        for x in (a, b, phi):
+            if x.dtype.__repr__() != "torch.float64" or not x.is_contiguous():
+                raise ValueError("device a, b, phi must be contiguous float64 CUDA tensors")
+        keep = (a, b, phi)
+        vp = [p[0] for p in ptrs]
+        N = int(phi.numel())
+    else:
+        keep = tuple(_f64(x) for x in (a, b, phi))
+        vp = [ctypes.c_void_p(x.ctypes.data) for x in keep]
+        N = int(keep[2].shape[0])
+    if len(keep[0]) != K or len(keep[1]) != K:
+        raise ValueError("a and b need one entry per state")
+    return keep, vp, N, on_dev
+
+
 class Context:
     """One MBAR problem resident on the device (``mbar_ctx``)."""
 
@@ -230,23 +258,7 @@ class Context:
         self._h = ctypes.c_void_p()
         Nk = np.ascontiguousarray(np.asarray(N_k, dtype=np.int64))
         K = int(Nk.shape[0])
-        ptrs = [_device_ptr(x) for x in (a, b, phi)]
-        on_dev = ptrs[0][1]
-        if any(p[1] != on_dev for p in ptrs):
-            raise ValueError("a, b and phi must all be host arrays or all CUDA tensors")
-        if on_dev:
-            for x in (a, b, phi):
-                if x.dtype.__repr__() != "torch.float64" or not x.is_contiguous():
-                    raise ValueError("device a, b, phi must be contiguous float64 CUDA tensors")
-            keep = (a, b, phi)
-            vp = [p[0] for p in ptrs]
-            N = int(phi.numel())
-        else:
-            keep = tuple(_f64(x) for x in (a, b, phi))
-            vp = [ctypes.c_void_p(x.ctypes.data) for x in keep]
-            N = int(keep[2].shape[0])
-        if len(keep[0]) != K or len(keep[1]) != K:
-            raise ValueError("a and b need one entry per state")
+        keep, vp, N, on_dev = _factorised_args(a, b, phi, K)
         if opts is None:
             opts = default_opts(precision)
         else:
@@ -492,6 +504,11 @@ def footprint_bytes(K: int, N: int, precision: int = MBAR_MIXED, use_binning: in
     return int(lib().mbar_footprint_bytes(int(K), int(N), int(precision), int(use_binning)))
 
 
+def footprint_factorised_bytes(K: int, N: int, precision: int = MBAR_MIXED, use_binning: int = 1) -> int:
+    """``mbar_footprint_factorised_bytes``: the same for a factorised solve."""
+    return int(lib().mbar_footprint_factorised_bytes(int(K), int(N), int(precision), int(use_binning)))
+
+
 def server_config(workers: int = 8, hbm_budget_bytes: int = 160 << 30, precision: int = MBAR_MIXED,
                   opts: Opts | None = None) -> ServerConfig:
     cfg = ServerConfig()
@@ -543,6 +560,19 @@ class Server:
                                         p_dev, ctypes.byref(rid)))
         self._keep[rid.value] = (ukeep, pkeep)   # read at admission: alive until wait
         self._K[rid.value] = int(Nk.shape[0])
+        return rid.value
+
+    def submit_factorised(self, a, b, phi, N_k) -> int:
+        """``mbar_server_submit_factorised``: one solve of u_kn = a_k +
+        b_k phi_n (arguments as ``Context.factorised``)."""
+        Nk = np.ascontiguousarray(np.asarray(N_k, dtype=np.int64))
+        K = int(Nk.shape[0])
+        keep, vp, N, on_dev = _factorised_args(a, b, phi, K)
+        rid = ctypes.c_int64()
+        _check(lib().mbar_server_submit_factorised(self._h, K, N, Nk.ctypes.data_as(_i64p), vp[0], vp[1], vp[2],
+                                                   on_dev, ctypes.byref(rid)))
+        self._keep[rid.value] = keep   # read at admission: alive until wait
+        self._K[rid.value] = K
         return rid.value
 
     def poll(self, rid: int) -> int:

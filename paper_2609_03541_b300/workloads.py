@@ -251,11 +251,8 @@ def harmonic_device(K: int, N_k: int, seed: int, d: int = 3, device="cuda"):
     return u.contiguous(), np.full(K, N_k, dtype=np.int64), None
 
 
-def umbrella_device(K: int, N_k: int, seed: int, kappa: float = 50.0, grid_points: int = 4096, device="cuda"):
-    """(u_kn float64 K x N, N_k array, phi = x): the umbrella windows of
-    `umbrella`, sampled by inverse CDF of each window's density tabulated on
-    `grid_points` points over [x_k - 1.5, x_k + 1.5] (trapezoid CDF, linear
-    interpolation)."""
+def _umbrella_samples_device(K: int, N_k: int, seed: int, kappa: float, grid_points: int, device):
+    """(window centres x_k, samples x in state-major order) of `umbrella_device`."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
@@ -274,9 +271,30 @@ def umbrella_device(K: int, N_k: int, seed: int, kappa: float = 50.0, grid_point
     x0 = torch.gather(grid, 1, j - 1)
     x1 = torch.gather(grid, 1, j)
     w = torch.where(c1 > c0, (r - c0) / (c1 - c0), torch.zeros_like(r))
-    x = (x0 + w * (x1 - x0)).reshape(-1)                               # N, state-major
-    del r, j, c0, c1, x0, x1, w
+    return xc, (x0 + w * (x1 - x0)).reshape(-1)
+
+
+def umbrella_device(K: int, N_k: int, seed: int, kappa: float = 50.0, grid_points: int = 4096, device="cuda"):
+    """(u_kn float64 K x N, N_k array, phi = x): the umbrella windows of
+    `umbrella`, sampled by inverse CDF of each window's density tabulated on
+    `grid_points` points over [x_k - 1.5, x_k + 1.5] (trapezoid CDF, linear
+    interpolation)."""
+    xc, x = _umbrella_samples_device(K, N_k, seed, kappa, grid_points, device)
     well = 5.0 * (x * x - 1.0) ** 2
     u = x[None, :].repeat(K, 1)                          # K x N, formed in place from here on
     u.sub_(xc[:, None]).square_().mul_(0.5 * kappa).add_(well[None, :])
     return u.contiguous(), np.full(K, N_k, dtype=np.int64), x.contiguous()
+
+
+def umbrella_factorised_device(K: int, N_k: int, seed: int, kappa: float = 50.0, grid_points: int = 4096,
+                               device="cuda"):
+    """(a, b, phi, N_k): the samples of `umbrella_device` with u in the
+    factorised form u_kn = a_k + b_k phi_n, a_k = kappa x_k^2 / 2,
+    b_k = -kappa x_k, phi = x. This drops U(x_n) + kappa x_n^2 / 2 from every
+    u_kn; a term that depends on the sample alone cancels between the
+    numerator and the denominator of Eq. 1, so f is unchanged."""
+    xc, x = _umbrella_samples_device(K, N_k, seed, kappa, grid_points, device)
+    a = (0.5 * kappa) * xc * xc
+    b = -kappa * xc
+    return a.contiguous(), b.contiguous(), x.contiguous(), np.full(K, N_k, dtype=np.int64)
+

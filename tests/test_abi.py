@@ -110,6 +110,18 @@ def test_footprint_estimate_grows_with_the_problem(L):
     assert M.footprint_bytes(0, 10) == 0
 
 
+def test_factorised_footprint_holds_no_store(L):
+    """A store-free (MIXED, binned) factorised solve is charged less than
+    the FP32 K x N store at the largest served size; on the FP64 path the
+    charge carries the K x N FP64 buffer of u."""
+    K, N = 1024, 20_000 * 1024
+    mixed = M.footprint_factorised_bytes(K, N, M.MBAR_MIXED)
+    assert 0 < mixed < K * N * 4
+    assert M.footprint_factorised_bytes(K, N, M.MBAR_FP64) > K * N * 8
+    assert M.footprint_factorised_bytes(K, N, M.MBAR_MIXED, use_binning=0) > K * N * 8
+    assert M.footprint_factorised_bytes(0, 10) == 0
+
+
 def test_server_rejects_bad_configuration_without_a_gpu(L):
     cfg = M.server_config(workers=0, hbm_budget_bytes=1 << 30)
     with pytest.raises(M.MbarError) as e:

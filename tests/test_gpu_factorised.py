@@ -47,6 +47,8 @@ CASES = {
     "gaussian_M12": lambda: _gaussian(12, 2000, 4),
     "alchemical_K40": lambda: _alchemical(40, 300, 3),
     "alchemical_K130": lambda: _alchemical(130, 100, 8),
+    # K > 512: the tensor-core Hessian in clusters of 6 CTAs, two launches
+    "alchemical_K700": lambda: _alchemical(700, 12, 9),
 }
 
 
@@ -85,7 +87,11 @@ def test_factorised_bench_shapes_match_the_stored_roots(name):
     assert np.max(np.abs(f - np.asarray(case["f"]))) < 1e-4, rep
 
 
-@pytest.mark.parametrize("K,N_k", [(20, 300), (150, 40), (300, 30), (500, 16)])
+# K = 600..1024 take clusters of 5..8 CTAs; above K = 640 the tile distances
+# are split over two launches (at K = 700 half the CTAs form no tile in the
+# second one, at K = 800 every CTA forms one, at K = 1024 two or one)
+@pytest.mark.parametrize("K,N_k", [(20, 300), (150, 40), (300, 30), (500, 16), (600, 10), (700, 8), (800, 8),
+                                   (1024, 6)])
 def test_factorised_hessian_matches_the_oracle(K, N_k):
     a, b, phi, Nk = _alchemical(K, N_k, seed=K)
     u = O.factorised_u(a, b, phi)
@@ -121,3 +127,42 @@ def test_factorised_context_rejects_a_new_coordinate():
     with M.Context.factorised(a, b, phi, Nk, M.MBAR_MIXED) as ctx:
         with pytest.raises(M.MbarError):
             ctx.set_coordinate(phi)
+
+
+def _umbrella_factorised(K, N_k, seed):
+    """The umbrella windows of workloads.umbrella in factorised form: the
+    per-sample terms U(x) + kappa x^2 / 2 cancel in Eq. 1 and are dropped."""
+    p = W.umbrella(K=K, N_k=N_k, seed=seed, grid_points=1 << 13)
+    xc, kappa = p.meta["centres"], p.meta["kappa"]
+    return 0.5 * kappa * xc * xc, -kappa * xc, p.phi, p.N_k
+
+
+@pytest.mark.parametrize("N_k,seed", [(1546, 504), (10664, 850)])
+def test_factorised_poorly_overlapping_windows_reach_the_oracle(N_k, seed):
+    """Four windows 1.0 apart: the binned levels leave f several kT from
+    the root and full Newton steps overshoot; backtracking along the Newton
+    direction must still reach the MBAR root."""
+    a, b, phi, Nk = _umbrella_factorised(4, N_k, seed)
+    f_ref = O.solve_mbar(O.factorised_u(a, b, phi), Nk)
+    with M.Context.factorised(a, b, phi, Nk, M.MBAR_MIXED) as ctx:
+        rep = ctx.solve().as_dict()
+        f = ctx.free_energies()
+    assert np.max(np.abs(f - f_ref)) < 1e-4, rep
+
+
+@pytest.mark.parametrize("M_,N_0", [(309, 396), (552, 760)])
+def test_factorised_long_replica_ladder_matches_the_analytic_free_energies(M_, N_0):
+    """Sec. IV replicas (80 % neighbour overlap) up to beta ~ 280: u reaches
+    ~1e5 kT, the binned levels end thousands of kT from the root, and the
+    root is checked against f_k = -beta_k^2 / 2 + c within 5 asymptotic
+    standard deviations (the oracle's solve takes too long at these sizes)."""
+    a, b, phi, Nk = _gaussian(M_, N_0, seed=M_)
+    with M.Context.factorised(a, b, phi, Nk, M.MBAR_MIXED) as ctx:
+        rep = ctx.solve().as_dict()
+        f = ctx.free_energies()
+        C = ctx.covariance()
+    exact = -(b * b - b[0] * b[0]) / 2.0
+    sd = np.sqrt(np.maximum(np.diag(C), 0.0))
+    z = np.abs(f - exact)[1:] / sd[1:]
+    assert np.max(z) < 5.0, (float(np.max(z)), rep)
+

@@ -122,3 +122,45 @@ def test_server_tolerates_device_synchronisation_by_other_threads():
         out = [srv.wait(i) for i in ids]
     for (f, _, _, _), (_, _, _, f_ref) in zip(out, mix):
         assert np.max(np.abs(f - f_ref)) < TOL[M.MBAR_MIXED]
+
+
+def _factorised_mix():
+    """Factorised requests of the serving stream's two kinds (umbrella
+    windows with the per-sample terms dropped; the Sec. IV replicas,
+    u = beta_k E), K from 5 to 700, with host copies for the oracle."""
+    import torch
+    out = []
+    for kind, K, Nk, seed in [("umbrella", 5, 800, 11), ("gaussian", 9, 1000, 12), ("umbrella", 40, 300, 13),
+                              ("gaussian", 130, 60, 14), ("umbrella", 700, 12, 15)]:
+        if kind == "umbrella":
+            a, b, phi, nk = W.umbrella_factorised_device(K, Nk, seed)
+        else:
+            b, phi, nk = W.gaussian_overlap_device(K, Nk, seed)
+            a = torch.zeros_like(b)
+        out.append((a, b, phi, nk))
+    torch.cuda.synchronize()
+    return out
+
+
+def test_server_factorised_requests_equal_the_same_solves_alone():
+    """mbar_server_submit_factorised: the store-free MIXED solves, several on
+    the GPU together, give the bits of the same solves run alone, and the
+    oracle's MBAR root within the mixed tolerance."""
+    mix = _factorised_mix()
+    prec = M.MBAR_MIXED
+    alone = []
+    for a, b, phi, nk in mix:
+        with M.Context.factorised(a, b, phi, nk, prec) as ctx:
+            ctx.solve()
+            alone.append(ctx.free_energies())
+    with M.Server(M.server_config(workers=4, hbm_budget_bytes=8 << 30, precision=prec)) as srv:
+        ids = [srv.submit_factorised(a, b, phi, nk) for a, b, phi, nk in mix]
+        out = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == len(mix)
+    assert st["peak_running"] >= 2
+    for (f, rep, lat, run), f1, (a, b, phi, nk) in zip(out, alone, mix):
+        assert np.array_equal(f, f1)
+        u = O.factorised_u(a.cpu().numpy(), b.cpu().numpy(), phi.cpu().numpy())
+        f_ref = O.solve_mbar(u, nk)
+        assert np.max(np.abs(f - f_ref)) < TOL[prec], (len(nk), rep.as_dict())
