@@ -490,6 +490,19 @@ def gaussian_bench(args):
 
 
 def batch_bench(args):
+    """The batched workload as its own line (see batch_block)."""
+    blk = batch_block(args)
+    line = {"metric": "MBAR solves/sec (batched)", "value": blk["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": blk["seconds"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": blk["workload"], "problems": blk["problems"], "entries": blk["entries"],
+                       "workers": args.workers, "budget_gb": args.budget_gb, "wave_input_gb": args.wave_gb},
+            "waves": blk["waves"], "accuracy": blk["accuracy"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def batch_block(args):
     """512 uneven problems (K ~ U{4..256}, N_k ~ U{100..10000} per problem,
     alternating harmonic d=3 / umbrella), mixed precision, solved by
     mbar_batch_solve in footprint waves: each wave's FP64 inputs are drawn on
@@ -549,16 +562,11 @@ def batch_bench(args):
                    "mixed_wave0_s": dt, "mixed_speedup_vs_fp64_gpu": dt64 / dt}
         del probs, fs
         torch.cuda.empty_cache()
-    line = {"metric": "MBAR solves/sec (batched)", "value": P / total_s, "unit": "solves/s", "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": total_s * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched: 512 problems, K~U{4..256}, N_k~U{100..10000} per problem, harmonic d=3 / "
-                                   "umbrella alternating, mixed precision, mbar_batch_solve in footprint waves",
-                       "problems": P, "entries": entries, "workers": args.workers, "budget_gb": args.budget_gb,
-                       "wave_input_gb": args.wave_gb},
-            "waves": wave_info, "accuracy": acc}
-    print(json.dumps(line), flush=True)
-    return 0
+    return {"workload": "batched: 512 problems, K~U{4..256}, N_k~U{100..10000} per problem, harmonic d=3 / "
+                        "umbrella alternating, mixed precision, mbar_batch_solve in footprint waves (inputs drawn "
+                        "on the device before each wave's timing)",
+            "problems": P, "entries": entries, "seconds": total_s, "solves_per_s": P / total_s, "waves": wave_info,
+            "accuracy": acc}
 
 
 def serve_requests(R: int, seed: int, device):
@@ -624,6 +632,9 @@ def serve_run(reqs, workers: int, budget: int, rate, seed: int):
     arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=R)) if rate else np.zeros(R)
     cfg = M.server_config(workers=workers, hbm_budget_bytes=budget, precision=M.MBAR_MIXED)
     lat, failed, rejected = [], 0, 0
+    phases = dict(width_s=0.0, levels_s=0.0, sci_s=0.0, newton_s=0.0, run_s=0.0, first_loop_iters=0,
+                  second_loop_iters=0, newton_iters=0)
+    slowest = []
     with DeviceMemorySampler() as mem:
         srv = M.Server(cfg)
         t0 = time.perf_counter()
@@ -639,15 +650,25 @@ def serve_run(reqs, workers: int, budget: int, rate, seed: int):
             except M.MbarError:
                 rejected += 1
         t_end = t0
-        for rid, ts in ids:
+        for i, (rid, ts) in enumerate(ids):
             try:
-                _, _, l, _ = srv.wait(rid)
+                _, rep, l, run_s = srv.wait(rid)
             except M.MbarError as e:
                 failed += 1
                 log(f"[bench] serve: request {rid} failed: {e}")
                 continue
             lat.append(l)
             t_end = max(t_end, ts + l)
+            phases["width_s"] += rep.seconds_width
+            phases["levels_s"] += rep.seconds_levels
+            phases["sci_s"] += rep.seconds_sci
+            phases["newton_s"] += rep.seconds_newton
+            phases["run_s"] += run_s
+            phases["first_loop_iters"] += rep.iters_first_loop
+            phases["second_loop_iters"] += rep.iters_second_loop
+            phases["newton_iters"] += rep.iters_newton
+            slowest.append((run_s, i, len(reqs[i][3]), int(reqs[i][3][0]), rep.iters_first_loop,
+                            rep.iters_second_loop, rep.iters_newton))
         st = srv.stats()
         srv.close()
     elapsed = t_end - t0
@@ -657,13 +678,17 @@ def serve_run(reqs, workers: int, budget: int, rate, seed: int):
             "offered_per_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat else None,
             "peak_running": st["peak_running"], "peak_admitted_gb": st["peak_bytes"] / 2 ** 30,
-            "peak_device_used_gb": mem.peak / 2 ** 30}
+            "peak_device_used_gb": mem.peak / 2 ** 30,
+            "worker_seconds": phases,
+            "slowest": [dict(run_s=r, request=i, K=K, N_k=nk, first_loop=a, second_loop=b, newton=c)
+                        for r, i, K, nk, a, b, c in sorted(slowest, reverse=True)[:8]]}
 
 
-def serve_block(args, R: int, loads):
+def serve_block(args, R: int, loads, poisson_requests: int | None = None):
     """Serving at the stream's full size: requests drawn before the timed
     runs (generation is not timed), one saturation run for the capacity,
-    then Poisson runs at the given fractions of it for p50 / p99."""
+    then Poisson runs at the given fractions of it for p50 / p99 (over the
+    first `poisson_requests` of the stream, all by default)."""
     import torch
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
@@ -675,13 +700,17 @@ def serve_block(args, R: int, loads):
     sat = serve_run(reqs, args.workers, budget, None, args.seed)
     log(f"[bench] serve saturation: {sat}")
     loads_out = {}
+    sub = reqs[:poisson_requests] if poisson_requests else reqs
     for frac in loads:
-        loads_out[str(frac)] = serve_run(reqs, args.workers, budget, frac * sat["solves_per_s"], args.seed + 1)
+        loads_out[str(frac)] = serve_run(sub, args.workers, budget, frac * sat["solves_per_s"], args.seed + 1)
         log(f"[bench] serve load {frac}: {loads_out[str(frac)]}")
     del reqs
     torch.cuda.empty_cache()
-    return {"requests": R, "entries": entries, "input_gb": nbytes / 2 ** 30, "generation_s_untimed": gen_s,
-            "budget_gb": args.budget_gb, "workers": args.workers, "saturation": sat, "poisson": loads_out}
+    return {"workload": "serving: K log-uniform [4,1024], N_k~U{100..20000}, factorised umbrella / Sec. IV replica "
+                        "requests drawn before the timed runs, mixed precision, one mbar_server",
+            "requests": R, "entries": entries, "input_gb": nbytes / 2 ** 30, "generation_s_untimed": gen_s,
+            "budget_gb": args.budget_gb, "workers": args.workers, "saturation": sat,
+            "poisson_requests": len(sub), "poisson": loads_out}
 
 
 def serve_bench(args):
@@ -726,6 +755,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and served workloads that follow the headline line's timing")
     ap.add_argument("--precision", default=None, choices=["mixed", "fp64"],
                     help="override the workload's precision")
     ap.add_argument("--lse-only", action="store_true",
@@ -740,7 +771,7 @@ def main():
                     help="time mbar_hessian (one fused LSE pass + the tensor-core Hessian) on a random K x n problem")
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
     ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
-    ap.add_argument("--loads", type=lambda t: [float(x) for x in t.split(",")], default=[0.5, 0.9],
+    ap.add_argument("--loads", type=lambda t: [float(x) for x in t.split(",") if x], default=[0.5, 0.9],
                     help="serve: Poisson arrival rates as fractions of the measured capacity")
     ap.add_argument("--workers", type=int, default=16, help="batch/serve: concurrent solves")
     ap.add_argument("--budget-gb", type=float, default=None,
@@ -1046,6 +1077,18 @@ def main():
         accuracy["max_abs_df_vs_oracle_kT"] = float(np.max(np.abs(f_red - f_red_ref)))
         accuracy["oracle_config"] = cpu["solve_config"]
 
+    # ---- the batched and served workloads on this GPU (single-process runs only) ----
+    batch_blk, serve_blk = None, None
+    if world == 1 and not args.no_extra:
+        torch.cuda.empty_cache()
+        budget_gb = args.budget_gb
+        args.budget_gb = 140.0
+        batch_blk = batch_block(args)
+        log(f"[bench] batch: {batch_blk['solves_per_s']:.1f} solves/s")
+        args.budget_gb = 160.0
+        serve_blk = serve_block(args, args.requests, [0.5], poisson_requests=500)
+        args.budget_gb = budget_gb
+
     if rank == 0:
         line = {"metric": metric, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -1054,7 +1097,7 @@ def main():
                 "roofline": roofline, "binned_lse": binned,
                 "latency": latency, "hessian": hess, "cpu_baseline": cpu, "clocks": clocks, "accuracy": accuracy,
                 "reweight": rew,
-                "report": rep.as_dict()}
+                "report": rep.as_dict(), "batch": batch_blk, "serving": serve_blk}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
