@@ -497,6 +497,7 @@ def batch_bench(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": blk["workload"], "problems": blk["problems"], "entries": blk["entries"],
                        "workers": args.workers, "budget_gb": args.budget_gb, "wave_input_gb": args.wave_gb},
+            "solves_per_s_builtin_shapes": blk["solves_per_s_builtin_shapes"], "autotune": blk["autotune"],
             "waves": blk["waves"], "accuracy": blk["accuracy"]}
     print(json.dumps(line), flush=True)
     return 0
@@ -528,7 +529,21 @@ def batch_block(args):
         waves.append(cur)
     cfg = M.server_config(workers=args.workers, hbm_budget_bytes=int(args.budget_gb * (1 << 30)),
                           precision=M.MBAR_MIXED)
-    total_s, entries, wave_info = 0.0, 0, []
+    # autotuning (untimed): one search per key (K rounded up to a power of two,
+    # floor(log2 N)) of the sample-major pass that MIXED's unbinned passes use
+    tune_reps = {}
+    for kind, K, Nk, seed in specs:
+        kb = 4
+        while kb < K:
+            kb *= 2
+        tune_reps.setdefault((kb, (K * Nk).bit_length() - 1), (K, K * Nk))
+    t_tune = time.perf_counter()
+    tuned = [M.autotune_lse(M.TUNE_SAMPLES, K, N) for K, N in tune_reps.values()]
+    tune_info = {"keys": len(tuned), "search_s_untimed": time.perf_counter() - t_tune,
+                 "keys_changed": sum(1 for r in tuned if r["ms"] < 0.97 * r["heuristic_ms"]),
+                 "pass_time_ratio_tuned_over_rule": float(np.mean([r["ms"] / r["heuristic_ms"] for r in tuned]))}
+    log(f"[bench] batch autotune: {tune_info}")
+    total_s, total_rule_s, entries, wave_info = 0.0, 0.0, 0, []
     acc = None
     for wi, wave in enumerate(waves):
         probs = []
@@ -536,11 +551,20 @@ def batch_block(args):
             u, nk, phi = _gen_device(kind, K, Nk, seed)
             probs.append((u, nk, phi))
             entries += K * K * Nk
+        # the built-in shapes, then the tuned ones, on the same inputs
+        M.autotune_enable(False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.batch_solve(probs, cfg)
+        torch.cuda.synchronize()
+        total_rule_s += time.perf_counter() - t0
+        M.autotune_enable(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fs, reps, sts = M.batch_solve(probs, cfg)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        M.autotune_enable(False)
         total_s += dt
         bad = [i for i, st in enumerate(sts) if st != 0]
         wave_info.append({"problems": len(wave), "seconds": dt, "failed": len(bad)})
@@ -565,7 +589,8 @@ def batch_block(args):
     return {"workload": "batched: 512 problems, K~U{4..256}, N_k~U{100..10000} per problem, harmonic d=3 / "
                         "umbrella alternating, mixed precision, mbar_batch_solve in footprint waves (inputs drawn "
                         "on the device before each wave's timing)",
-            "problems": P, "entries": entries, "seconds": total_s, "solves_per_s": P / total_s, "waves": wave_info,
+            "problems": P, "entries": entries, "seconds": total_s, "solves_per_s": P / total_s,
+            "solves_per_s_builtin_shapes": P / total_rule_s, "autotune": tune_info, "waves": wave_info,
             "accuracy": acc}
 
 

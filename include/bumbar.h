@@ -284,6 +284,50 @@ BUMBAR_API mbar_status mbar_get_trace(mbar_ctx* ctx, int64_t* rows, double* out,
  * with K <= 512). For testing and tuning; EINVAL for other values. */
 BUMBAR_API mbar_status mbar_set_hessian_path(int32_t path);
 
+/* ---- Autotuning of the LSE passes' launch shapes ----------------------
+ * Not part of the method: a measurement-driven choice among the compiled
+ * launch shapes of the two streaming passes that have several, the
+ * sample-major FP32 pass (every MIXED unbinned pass; MBAR_TUNE_SAMPLES) and
+ * the factorised pass (MBAR_TUNE_FACTORISED). A key is (device name, family,
+ * K rounded up to a power of two >= 4, floor(log2 n)). The candidates are
+ * the compiled shapes (lanes per sample, chunks of 4 states per lane) that
+ * cover the key's K with the fewest chunks, and for the sample-major pass
+ * stage sizes of 24-96 KB; each is timed on synthetic device data of the
+ * given size (capped at 1 GB) with CUDA events: the median of three rounds
+ * of the exact-split pass plus the plain pass. While tuning is enabled,
+ * every plan of those passes whose key is in the table takes its shape (the
+ * FP32 partial sums then add in another order: results move at their
+ * rounding level); otherwise the built-in shape rules apply. */
+enum { MBAR_TUNE_SAMPLES = 0, MBAR_TUNE_FACTORISED = 1 };
+
+typedef struct {
+  int32_t family;            /* MBAR_TUNE_* */
+  int32_t lanes_per_sample;  /* the chosen shape */
+  int32_t chunks_per_lane;
+  int32_t threads;
+  int32_t stage_bytes;       /* sample-major pass only (0 otherwise) */
+  int32_t candidates;        /* shapes timed */
+  double ms;                 /* chosen shape: one exact-split + one plain pass */
+  double heuristic_ms;       /* the built-in rule's shape, the same way */
+  int32_t cached;            /* 1: taken from the table, nothing was timed */
+  int32_t pad;
+} mbar_tune_result;
+
+/* Searches the shape of (family, K, n)'s key, unless the table already has
+ * it, and records it (and appends it to the cache file, if one is set).
+ * Allocates and frees its own device buffers (up to ~1 GB) on the current
+ * device and synchronises its own stream. EINVAL for a bad family or sizes,
+ * EUNSUPPORTED for K > 1024, ENOMEM, ECUDA. */
+BUMBAR_API mbar_status mbar_autotune_lse(int32_t family, int64_t K, int64_t n, mbar_tune_result* out);
+/* Plans consult the tuned table (on != 0) or the built-in rules (0, the
+ * default). Process-wide. */
+BUMBAR_API mbar_status mbar_autotune_enable(int32_t on);
+/* Sets the text file the table is appended to, and loads its lines now
+ * (NULL or "": none). A missing file is not an error. */
+BUMBAR_API mbar_status mbar_autotune_cache(const char* path);
+/* Empties the in-memory table (the file is left as it is). */
+BUMBAR_API mbar_status mbar_autotune_clear(void);
+
 /* Number of CUDA kernels this library has launched in this process. */
 BUMBAR_API mbar_status mbar_kernel_launches(int64_t* count);
 

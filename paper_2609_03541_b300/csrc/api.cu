@@ -1635,7 +1635,8 @@ mbar_status create_impl(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
       c->sorted = true;
     }
     {
-      const int grid = std::max(lse_plan(K, N, c->dtype).grid, lse_fact_plan(K, N).grid);
+      // one CTA per SM bounds every plan's grid, tuned shapes included
+      const int grid = std::max({lse_plan(K, N, c->dtype).grid, lse_fact_plan(K, N).grid, num_sms()});
       c->scratch_bytes = lse_scratch_for_grid(K, grid);
       TRYC(dalloc(c, &c->scratch, c->scratch_bytes));
       if (cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->st) != cudaSuccess) return fail(MBAR_ECUDA);
@@ -1700,7 +1701,8 @@ mbar_status create_impl(mbar_ctx** out, int64_t K, int64_t N, const int64_t* N_k
   {
     const LsePlan pl = lse_plan(K, N, c->dtype);
     int grid = pl.grid;
-    if (c->smaj) grid = std::max(grid, lse_smaj_plan(K, N).grid);
+    // one CTA per SM bounds the sample-major plans' grids, tuned shapes included
+    if (c->smaj) grid = std::max({grid, lse_smaj_plan(K, N).grid, num_sms()});
     c->scratch_bytes = lse_scratch_for_grid(K, grid);
     TRYC(dalloc(c, &c->scratch, c->scratch_bytes));
     if (cudaMemsetAsync(c->scratch, 0, c->scratch_bytes, c->st) != cudaSuccess) return fail(MBAR_ECUDA);
@@ -2359,7 +2361,8 @@ mbar_status mbar_lse_pass(const void* v, int32_t dtype_bytes, int64_t K, int64_t
 
 size_t mbar_lse_samples_scratch_bytes(int64_t K, int64_t n) {
   if (K < 1 || K > 1024 || n < 1) return 0;
-  return lse_scratch_for_grid(K, lse_smaj_plan(K, n).grid);
+  // tuned shapes (mbar_autotune_enable) take at most one CTA per SM
+  return lse_scratch_for_grid(K, std::max(lse_smaj_plan(K, n).grid, num_sms()));
 }
 
 mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const double* f, const double* log_N,
@@ -2406,7 +2409,8 @@ mbar_status mbar_lse_pass_samples(const float* v_nk, int64_t K, int64_t n, const
 size_t mbar_lse_factorised_scratch_bytes(int64_t K, int64_t n) {
   if (K < 1 || K > 1024 || n < 1) return 0;
   // the pass's own scratch, then (256-byte aligned) the reference-state table
-  return round_up(static_cast<int64_t>(lse_scratch_for_grid(K, lse_fact_plan(K, n).grid)), 256) +
+  return round_up(static_cast<int64_t>(lse_scratch_for_grid(K, std::max(lse_fact_plan(K, n).grid, num_sms()))),
+                  256) +
          lse_fact_ref_bytes();
 }
 
@@ -2446,7 +2450,7 @@ mbar_status mbar_lse_pass_factorised(const double* a, const double* b, const dou
   p.mode = kLseModePass;
   p.exact_max = 1;
   const LsePlan pl = lse_fact_plan(K, n);
-  void* ref = sc + round_up(static_cast<int64_t>(lse_scratch_for_grid(K, pl.grid)), 256);
+  void* ref = sc + round_up(static_cast<int64_t>(lse_scratch_for_grid(K, std::max(pl.grid, num_sms()))), 256);
   return lse_fact_launch(a, b, phi, pl, p, nullptr, nullptr, 0, ref, static_cast<cudaStream_t>(stream));
 }
 

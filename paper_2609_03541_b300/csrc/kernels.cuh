@@ -99,6 +99,8 @@ mbar_status sci_loop_launch(const float* vT, const SciLoopParams& prm, cudaStrea
 // out[p * stage_pitch(K) + k] = v[k * ld + p] for p < n (entries k >= K zero).
 mbar_status level_to_samples(const float* v, int64_t K, int64_t n, int64_t ld, float* out, cudaStream_t st);
 LsePlan lse_smaj_plan(int64_t K, int64_t n);
+LsePlan lse_smaj_plan_rule(int64_t K, int64_t n);  // the built-in shape rule (no tuned table)
+LsePlan lse_smaj_plan_for(int64_t K, int64_t n, int lps, int nk, int nt, int stage_bytes);
 bool lse_smaj_preferred(int64_t K);
 mbar_status lse_smaj_launch(const float* vst, const LsePlan& pl, LseParams prm, cudaStream_t st);
 // The SCI epilogue over the partials of a pass (lse.cu).
@@ -121,6 +123,14 @@ struct FactRef {
 // pass without a known range computes first.
 size_t lse_fact_ref_bytes();
 LsePlan lse_fact_plan(int64_t K, int64_t n);
+LsePlan lse_fact_plan_rule(int64_t K, int64_t n);  // the built-in shape rule (no tuned table)
+LsePlan lse_fact_plan_for(int64_t K, int64_t n, int lps, int nk);
+int fact_threads(int nk);
+// LSE-pass autotuning (autotune.cu): the tuned shape of a (family, K, n), if
+// tuning is enabled and the table has the key.
+constexpr int kTuneSamples = MBAR_TUNE_SAMPLES;
+constexpr int kTuneFactorised = MBAR_TUNE_FACTORISED;
+bool tuned_shape(int family, int64_t K, int64_t n, int* lps, int* nk, int* nt, int* stage_bytes);
 // phi_min / phi_max: device pointers to `nparts` partial minima / maxima of
 // phi (a sorted copy's first and last element, nparts = 1), or nullptr: the
 // range is then reduced from phi into `ref_buf` first. ref_buf: device,

@@ -397,20 +397,34 @@ void fact_run(const LsePlan& pl, const double* a, const double* b, const double*
 
 }  // namespace
 
+// Threads of the compiled factorised instance with `nk` chunks per lane:
+// four FP32 constants per state in registers, 512 threads (128 registers)
+// up to 12 states per lane, 384 at 16 (512 spilled), 256 beyond.
+int fact_threads(int nk) { return nk <= 3 ? 512 : (nk == 4 ? 384 : 256); }
+
 LsePlan lse_fact_plan(int64_t K, int64_t n) {
-  LsePlan pl{};
+  int lps = 0, nk = 0, nt = 0, unused = 0;
+  if (tuned_shape(kTuneFactorised, K, n, &lps, &nk, &nt, &unused)) return lse_fact_plan_for(K, n, lps, nk);
+  return lse_fact_plan_rule(K, n);
+}
+
+LsePlan lse_fact_plan_rule(int64_t K, int64_t n) {
+  int lps = 0, nk = 0;
   // lanes per sample: as few as give every lane at most 16 states (four
   // float4 groups), so the per-sample shuffles, reciprocal and logden write
   // are spread over as many entries as the registers allow; 32 lanes (and up
   // to 32 states each) from K = 256
   const int64_t q = round_up(K, 4) / 4;
-  int lps = 1;
+  lps = 1;
   while (lps < 32 && lps * 4 < q) lps <<= 1;
-  int nk = static_cast<int>(ceil_div(q, static_cast<int64_t>(lps)));
+  nk = static_cast<int>(ceil_div(q, static_cast<int64_t>(lps)));
   if (lps < 32 && nk == 3) nk = 4;
-  // four FP32 constants per state in registers: 512 threads (128 registers)
-  // up to 12 states per lane, 384 at 16 (512 spilled), 256 beyond
-  const int nt = nk <= 3 ? 512 : (nk == 4 ? 384 : 256);
+  return lse_fact_plan_for(K, n, lps, nk);
+}
+
+LsePlan lse_fact_plan_for(int64_t K, int64_t n, int lps, int nk) {
+  LsePlan pl{};
+  const int nt = fact_threads(nk);
   const int64_t Kp = round_up(K, 4);
   pl.variant = 3;
   pl.threads = nt;

@@ -402,15 +402,26 @@ void smaj_run(const LsePlan& pl, const float* vst, int Kp, const LseParams& prm,
 }  // namespace
 
 LsePlan lse_smaj_plan(int64_t K, int64_t n) {
-  LsePlan pl{};
+  int lps = 0, nk = 0, nt = 0, stage_bytes = 0;
+  if (tuned_shape(kTuneSamples, K, n, &lps, &nk, &nt, &stage_bytes))
+    return lse_smaj_plan_for(K, n, lps, nk, nt, stage_bytes);
+  return lse_smaj_plan_rule(K, n);
+}
+
+LsePlan lse_smaj_plan_rule(int64_t K, int64_t n) {
   int lps = 0, nk = 0, nt = 0;
   smaj_shape(K, &lps, &nk, &nt);
+  return lse_smaj_plan_for(K, n, lps, nk, nt, kSmStageBytes);
+}
+
+LsePlan lse_smaj_plan_for(int64_t K, int64_t n, int lps, int nk, int nt, int stage_bytes) {
+  LsePlan pl{};
   const int64_t Kp = round_up(K, 4);
   const int spw = 32 / lps;
-  // samples per stage: about 48 KB (also at small K, where 32 KB stages
-  // measured 7 % slower), a multiple of 4 (16-byte aligned runs) and at
-  // least one sample slot per compute warp
-  int64_t S = std::max<int64_t>(kSmStageBytes / (Kp * 4), 1);
+  // samples per stage: about stage_bytes (48 KB by the shape rule, also at
+  // small K, where 32 KB stages measured 7 % slower), a multiple of 4
+  // (16-byte aligned runs) and at least one sample slot per compute warp
+  int64_t S = std::max<int64_t>(stage_bytes / (Kp * 4), 1);
   S = std::max<int64_t>(S, static_cast<int64_t>(spw) * (nt / 32 - 1));
   S = round_up(S, 4);
   const size_t sb = static_cast<size_t>(S) * Kp * 4;

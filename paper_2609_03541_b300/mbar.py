@@ -77,6 +77,27 @@ class Report(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [
+        ("family", ctypes.c_int32),
+        ("lanes_per_sample", ctypes.c_int32),
+        ("chunks_per_lane", ctypes.c_int32),
+        ("threads", ctypes.c_int32),
+        ("stage_bytes", ctypes.c_int32),
+        ("candidates", ctypes.c_int32),
+        ("ms", ctypes.c_double),
+        ("heuristic_ms", ctypes.c_double),
+        ("cached", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad"}
+
+
+TUNE_SAMPLES, TUNE_FACTORISED = 0, 1
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [
         ("workers", ctypes.c_int32),
@@ -123,6 +144,10 @@ _SIGNATURES = {
                                         ctypes.c_uint64),
     "mbar_server_submit_factorised": ([_vp, ctypes.c_int64, ctypes.c_int64, _i64p, _vp, _vp, _vp, ctypes.c_int32,
                                        _i64p], ctypes.c_int),
+    "mbar_autotune_lse": ([ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(TuneResult)], ctypes.c_int),
+    "mbar_autotune_enable": ([ctypes.c_int32], ctypes.c_int),
+    "mbar_autotune_cache": ([ctypes.c_char_p], ctypes.c_int),
+    "mbar_autotune_clear": ([], ctypes.c_int),
     "mbar_server_create": ([ctypes.POINTER(_vp), ctypes.POINTER(ServerConfig)], ctypes.c_int),
     "mbar_server_submit": ([_vp, ctypes.c_int64, ctypes.c_int64, _i64p, _vp, ctypes.c_int32, _vp, ctypes.c_int32,
                             _i64p], ctypes.c_int),
@@ -502,6 +527,29 @@ def lse_pass_static(v, f, log_N, Q, H=None, logden=None, stream=None):
 def footprint_bytes(K: int, N: int, precision: int = MBAR_MIXED, use_binning: int = 1) -> int:
     """``mbar_footprint_bytes``: estimated peak device memory of one solve."""
     return int(lib().mbar_footprint_bytes(int(K), int(N), int(precision), int(use_binning)))
+
+
+def autotune_lse(family: int, K: int, n: int) -> dict:
+    """``mbar_autotune_lse``: the tuned launch shape of one LSE pass family
+    (TUNE_SAMPLES or TUNE_FACTORISED) for (K, n); searched unless cached."""
+    r = TuneResult()
+    _check(lib().mbar_autotune_lse(int(family), int(K), int(n), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def autotune_enable(on: bool = True) -> None:
+    """``mbar_autotune_enable``: plans take the tuned shapes (process-wide)."""
+    _check(lib().mbar_autotune_enable(1 if on else 0))
+
+
+def autotune_cache(path) -> None:
+    """``mbar_autotune_cache``: append tuned shapes to, and load them from, ``path``."""
+    _check(lib().mbar_autotune_cache(None if path is None else str(path).encode()))
+
+
+def autotune_clear() -> None:
+    """``mbar_autotune_clear``: empty the in-memory table."""
+    _check(lib().mbar_autotune_clear())
 
 
 def footprint_factorised_bytes(K: int, N: int, precision: int = MBAR_MIXED, use_binning: int = 1) -> int:

@@ -122,6 +122,36 @@ def test_factorised_footprint_holds_no_store(L):
     assert M.footprint_factorised_bytes(0, 10) == 0
 
 
+def test_autotune_rejects_bad_arguments_without_a_gpu(L):
+    for fam, K, n, code in [(7, 50, 1000, "MBAR_EINVAL"), (M.TUNE_SAMPLES, 0, 1000, "MBAR_EINVAL"),
+                            (M.TUNE_SAMPLES, 2000, 1000, "MBAR_EUNSUPPORTED"),
+                            (M.TUNE_FACTORISED, 50, 0, "MBAR_EINVAL")]:
+        with pytest.raises(M.MbarError) as e:
+            M.autotune_lse(fam, K, n)
+        assert e.value.name == code
+
+
+def test_autotune_cache_file_is_read_back(L, tmp_path):
+    """A cache line is served without timing anything (cached = 1). Without
+    a GPU the device name is "unknown", so a line for that name is found;
+    the key is K rounded up to a power of two and floor(log2 n)."""
+    path = tmp_path / "tune.txt"
+    path.write_text("unknown 0 64 17 8 4 512 65536 20 0.5 0.6\n"
+                    "unknown 1 512 20 32 4 384 0 6 1.0 1.1\n")
+    M.autotune_clear()
+    M.autotune_cache(path)
+    try:
+        r = M.autotune_lse(M.TUNE_SAMPLES, 50, 200_000)      # 50 -> 64, log2(2e5) -> 17
+        assert r["cached"] == 1
+        assert (r["lanes_per_sample"], r["chunks_per_lane"], r["stage_bytes"]) == (8, 4, 65536)
+        r = M.autotune_lse(M.TUNE_FACTORISED, 500, 2_000_000)  # 500 -> 512, log2(2e6) -> 20
+        assert (r["lanes_per_sample"], r["chunks_per_lane"], r["threads"]) == (32, 4, 384)
+        assert r["ms"] == 1.0 and r["heuristic_ms"] == 1.1
+    finally:
+        M.autotune_cache(None)
+        M.autotune_clear()
+
+
 def test_server_rejects_bad_configuration_without_a_gpu(L):
     cfg = M.server_config(workers=0, hbm_budget_bytes=1 << 30)
     with pytest.raises(M.MbarError) as e:
