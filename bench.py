@@ -333,7 +333,10 @@ def lse_factorised_only(args):
     from paper_2609_03541_b300 import mbar as M
     dev = torch.device("cuda", 0)
     K, n = args.lse_K, args.lse_n
-    s2 = 2000.0
+    # tempering magnitudes (|x| up to ~4e3: the exponents relative to each
+    # sample's reference state) or, --lse-regime small, O(1) potentials (x
+    # formed directly)
+    s2 = 2000.0 if args.lse_regime == "tempering" else 2.0
     t = np.linspace(0.0, np.log(600.0 / 298.0), K)
     b = 1.0 / np.exp(t)
     g = torch.Generator(device=dev)
@@ -367,6 +370,7 @@ def lse_factorised_only(args):
     peak = sms * 16 * peaks.get("sm_max_mhz", 2032.0) * 1e6     # ex2 per second
     eps = K * n / (ms / 1e3)
     print(json.dumps({"kernel": "lse_fact_kernel (u_kp = a_k + b_k phi_p, generated)", "K": K, "n": n,
+                      "regime": args.lse_regime,
                       "ms_per_launch": ms, "bound": "alu (SFU ex2)", "entries_per_s": eps,
                       "peak_entries_per_s": peak, "frac": eps / peak,
                       "peak_source": f"{sms} SMs x 16 ex2/clk x {src} sm_max_mhz",
@@ -376,10 +380,37 @@ def lse_factorised_only(args):
 
 def hess_only(args):
     """Times mbar_hessian on a random mixed-precision K x n problem (host
-    f in, host K x K out); reports the library-timed Hessian launches."""
+    f in, host K x K out); reports the library-timed Hessian launches.
+    --hess-layout factorised: a store-free factorised context on a Sec. IV
+    replica ladder (M = K replicas, n / K energies each, u = beta_k E) at
+    the analytic f, whose Hessian forms P~ from E."""
     import torch
     from paper_2609_03541_b300 import mbar as M
+    from paper_2609_03541_b300 import workloads as W
     K, n = args.lse_K, args.lse_n
+    if args.hess_layout == "factorised":
+        beta, E, Nk = W.gaussian_overlap_device(K, max(1, n // K), seed=0)
+        ctx = M.Context.factorised(torch.zeros_like(beta), beta, E, Nk, M.MBAR_MIXED)
+        bb = beta.cpu().numpy()
+        f = -(bb * bb - bb[0] * bb[0]) / 2.0
+        ctx.set_timing(True)
+        for _ in range(max(args.warmup, 1)):
+            ctx.hessian(f)
+        torch.cuda.synchronize()
+        l0, ms0, _ = ctx.timing(1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.hessian(f)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3 / args.steps
+        l1, ms1, _ = ctx.timing(1)
+        n_all = int(Nk.sum())
+        dev_ms = (ms1 - ms0) / max(l1 - l0, 1)
+        print(json.dumps({"kernel": "mbar_hessian, factorised context (overlap_tc_fact_kernel, P~ from E)",
+                          "K": K, "n": n_all, "ms_per_call_wall": wall, "hessian_device_ms": dev_ms,
+                          "tflops_upper_triangle": 2.0 * K * K * n_all * 0.5 / (dev_ms / 1e3) / 1e12}), flush=True)
+        ctx.close()
+        return 0
     g = np.random.default_rng(0)
     x = g.uniform(0, 1, size=n)
     centres = np.linspace(0, 1, K)
@@ -792,6 +823,10 @@ def main():
     ap.add_argument("--lse-layout", default="samples", choices=["samples", "rows", "factorised"],
                     help="--lse-only: sample-major FP32 store (MIXED's unbinned passes), row-major, or "
                          "factorised u_kp = a_k + b_k phi_p generated from phi")
+    ap.add_argument("--lse-regime", default="tempering", choices=["tempering", "small"],
+                    help="--lse-layout factorised: tempering magnitudes (relative exponents) or O(1) potentials")
+    ap.add_argument("--hess-layout", default="dense", choices=["dense", "factorised"],
+                    help="--hess-only: a dense MIXED context, or a store-free factorised one")
     ap.add_argument("--hess-only", action="store_true",
                     help="time mbar_hessian (one fused LSE pass + the tensor-core Hessian) on a random K x n problem")
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")

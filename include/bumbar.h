@@ -250,7 +250,8 @@ BUMBAR_API const char* mbar_last_error(void);
  * stream (for profiling; adds two event records per timed launch).
  * mbar_set_timing(ctx, 1) clears earlier records and starts recording,
  * 0 stops. mbar_get_timing sums the records of one kind:
- *   0 = unbinned fused LSE passes, 1 = Hessian, 2 = FP64 Newton solve,
+ *   0 = unbinned fused LSE passes, 1 = Hessian (in the Newton phase and in
+ *       mbar_hessian), 2 = FP64 Newton solve,
  *   3 = unbinned passes that only confirm a Newton step below f_tol (FP32
  *       data: plain FP32 sums instead of the exact split of each sample's
  *       largest weight that kind 0 uses),

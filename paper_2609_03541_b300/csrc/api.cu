@@ -1995,7 +1995,9 @@ mbar_status mbar_hessian(mbar_ctx* c, const double* f_in, double* hess_out) {
   const size_t htmp = hessian_tmp_bytes(K, L.n);
   void* tmp = nullptr;
   BUMBAR_TRY(dalloc(c, &tmp, htmp));
+  time_mark(c, true, 1, static_cast<double>(K) * L.n * c->dtype);
   mbar_status s = level_hessian(c, L, c->ft, tmp, htmp);
+  time_mark(c, false, 1, 0);
   if (s == MBAR_OK) s = check_device_errors(c);
   if (s == MBAR_OK) s = d2h(c, hess_out, c->hess, K * K);
   if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;

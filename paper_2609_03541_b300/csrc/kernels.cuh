@@ -112,11 +112,14 @@ mbar_status factorised_u(const double* a, const double* b, const double* phi, in
                          cudaStream_t st);
 // Reference-state table of a factorised pass: the state of the largest
 // exponent at kRefGrid points spread evenly over [min phi, max phi]; a
-// sample's state is state[rint((phi - lo) * inv_step)] (clamped).
+// sample's state is state[rint((phi - lo) * inv_step)] (clamped). `relative`
+// is set where the exponents can exceed 2^12 in magnitude (one FP32 ulp
+// 2.4e-4 or more): only then does the pass form them relative to that state.
 constexpr int kRefGrid = 4096;
 struct FactRef {
   float lo, inv_step;
-  int pad[2];
+  int relative;  // exponents relative to the reference state (else absolute)
+  int pad;
   int16_t state[kRefGrid];
 };
 // Device bytes of a pass's table plus the partial (min, max) of phi that a

@@ -21,8 +21,14 @@
 // bracket then rounds once, at the magnitude of x_kp - x_rp rather than of
 // x_kp: u in the thousands or hundreds of thousands of kT (replica ladders
 // u = beta_k E) keeps the accuracy of u near 0. The dropped b_lo p_lo term is
-// 2^-48 of the product. The pairs of entries go through f32x2 instructions:
-// seven per two entries, then max, ex2, sum and one FMA into the row partial.
+// 2^-48 of the product. That form costs three more FP32 operations per entry
+// (measured 1.55x the pass time at K = 500), so it is taken only where it is
+// needed: the table kernel bounds |x| by max|c| + max|b'| max|phi| and sets
+// the table's `relative` flag above 2^12 (one FP32 ulp 2.4e-4); below it the
+// pass forms x_kp itself, fma(-b_hi, p_hi, c_hi) + lo_k, rounded once at
+// |x_kp|. The flag is the same for the whole grid (a uniform branch). The
+// pairs of entries go through f32x2 instructions, then max, ex2, sum and one
+// FMA into the row partial.
 // Schedule: one CTA per SM, every warp computes. Warps take 32-sample chunks
 // round robin over the grid; lane l loads phi (and H) of sample l of the
 // chunk, and LPS-lane groups take the samples one after another (shuffles).
@@ -100,6 +106,7 @@ __global__ void __launch_bounds__(kRefThreads) fact_ref_kernel(const double* __r
                                                                const double* maxs, int nparts, FactRef* out) {
   __shared__ float2 cb[1024];
   __shared__ double slo[kRefThreads], shi[kRefThreads];
+  __shared__ float smc[kRefThreads], smb[kRefThreads];
   double lo = INFINITY, hi = -INFINITY;
   for (int i = threadIdx.x; i < nparts; i += kRefThreads) {
     lo = fmin(lo, mins[i]);
@@ -107,14 +114,23 @@ __global__ void __launch_bounds__(kRefThreads) fact_ref_kernel(const double* __r
   }
   slo[threadIdx.x] = lo;
   shi[threadIdx.x] = hi;
-  for (int k = threadIdx.x; k < K; k += kRefThreads)
-    cb[k] = make_float2(static_cast<float>((f[k] + logN[k] - a[k]) * 1.4426950408889634),
-                        static_cast<float>(b[k] * 1.4426950408889634));
+  float mc = 0.f, mb = 0.f;  // largest finite |c_k| and |b'_k|
+  for (int k = threadIdx.x; k < K; k += kRefThreads) {
+    const float2 v = make_float2(static_cast<float>((f[k] + logN[k] - a[k]) * 1.4426950408889634),
+                                 static_cast<float>(b[k] * 1.4426950408889634));
+    cb[k] = v;
+    if (isfinite(v.x)) mc = fmaxf(mc, fabsf(v.x));
+    mb = fmaxf(mb, fabsf(v.y));
+  }
+  smc[threadIdx.x] = mc;
+  smb[threadIdx.x] = mb;
   __syncthreads();
   for (int o = kRefThreads / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
       slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + o]);
       shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + o]);
+      smc[threadIdx.x] = fmaxf(smc[threadIdx.x], smc[threadIdx.x + o]);
+      smb[threadIdx.x] = fmaxf(smb[threadIdx.x], smb[threadIdx.x + o]);
     }
     __syncthreads();
   }
@@ -140,6 +156,9 @@ __global__ void __launch_bounds__(kRefThreads) fact_ref_kernel(const double* __r
   if (g == 0) {
     out->lo = static_cast<float>(lo);
     out->inv_step = spread ? static_cast<float>(1.0 / step) : 0.f;
+    // a bound on |x_kp| = |c_k - b'_k phi_p|
+    const double X = static_cast<double>(smc[0]) + static_cast<double>(smb[0]) * fmax(fabs(lo), fabs(hi));
+    out->relative = X > 4096.0 ? 1 : 0;
   }
 }
 
@@ -182,6 +201,7 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
   if constexpr (EXACT && LPS < 32)
     for (int i = tid; i < NW * Kp; i += NT) cnt[i] = 0u;
   const float ref_lo = ref->lo, ref_inv = ref->inv_step;
+  const bool rel = ref->relative != 0;  // the same for the whole grid
   __syncthreads();
 
   const int lig = lane % LPS;  // lane in group
@@ -239,8 +259,8 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
     }
     // the lane's sample: reference state r from the table, its c_hi and b_hi,
     // and lo_r = c_lo,r - b_lo,r p_hi - b_hi,r p_lo
-    float chr_l, bhr_l, lor_l;
-    {
+    float chr_l = 0.f, bhr_l = 0.f, lor_l = 0.f;
+    if (rel) {
       const int g = min(max(__float2int_rn((ph_l - ref_lo) * ref_inv), 0), kRefGrid - 1);
       const float4 cr = cst[tbl[g]];
       chr_l = cr.x;
@@ -258,17 +278,29 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       const float lor = __shfl_sync(0xffffffffu, lor_l, j);
       const unsigned long long ph2 = pk2(ph, ph), pl2 = pk2(pl, pl);
       const unsigned long long nchr2 = pk2(-chr, -chr), bhr2 = pk2(bhr, bhr), nlor2 = pk2(-lor, -lor);
-      float x[E];  // x_kp - x_rp (log2 units)
+      float x[E];  // x_kp - x_rp, or x_kp (log2 units)
       float m0 = -INFINITY, m1 = -INFINITY;
+      if (rel) {
 #pragma unroll
-      for (int q = 0; q < E / 2; ++q) {
-        const unsigned long long dch = add2(ch2[q], nchr2);     // c_hi,k - c_hi,r (exact)
-        const unsigned long long ndb = add2(nbh2[q], bhr2);     // -(b_hi,k - b_hi,r) (exact)
-        const unsigned long long xh = fma2(ndb, ph2, dch);      // one rounding
-        const unsigned long long lo = fma2(nbl2[q], ph2, fma2(nbh2[q], pl2, cl2[q]));
-        upk2(add2(xh, add2(lo, nlor2)), x[2 * q], x[2 * q + 1]);
-        m0 = fmaxf(m0, x[2 * q]);
-        m1 = fmaxf(m1, x[2 * q + 1]);
+        for (int q = 0; q < E / 2; ++q) {
+          const unsigned long long dch = add2(ch2[q], nchr2);     // c_hi,k - c_hi,r (exact)
+          const unsigned long long ndb = add2(nbh2[q], bhr2);     // -(b_hi,k - b_hi,r) (exact)
+          const unsigned long long xh = fma2(ndb, ph2, dch);      // one rounding
+          const unsigned long long lo = fma2(nbl2[q], ph2, fma2(nbh2[q], pl2, cl2[q]));
+          upk2(add2(xh, add2(lo, nlor2)), x[2 * q], x[2 * q + 1]);
+          m0 = fmaxf(m0, x[2 * q]);
+          m1 = fmaxf(m1, x[2 * q + 1]);
+        }
+      } else {
+        // |x| <= 2^12: x_kp itself, rounded once where c_k and b'_k phi_p cancel
+#pragma unroll
+        for (int q = 0; q < E / 2; ++q) {
+          const unsigned long long xh = fma2(nbh2[q], ph2, ch2[q]);
+          const unsigned long long lo = fma2(nbl2[q], ph2, fma2(nbh2[q], pl2, cl2[q]));
+          upk2(add2(xh, lo), x[2 * q], x[2 * q + 1]);
+          m0 = fmaxf(m0, x[2 * q]);
+          m1 = fmaxf(m1, x[2 * q + 1]);
+        }
       }
       float m = fmaxf(m0, m1);
 #pragma unroll
@@ -311,8 +343,9 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       const float w = j < nloc ? hw * rcp_approx(s) : 0.f;
       // every lane of a group holds its sample's m and s: lane l takes the
       // logden of sample l from the group that has it in this round
-      // logden_p = (x_rp + m + log2 s) ln 2, x_rp = c_r - b'_r phi_p
-      const float lv = ((fmaf(-bhr, ph, chr) + lor) + (m + __log2f(s))) * kLn2;
+      // logden_p = (x_rp + m + log2 s) ln 2, x_rp = c_r - b'_r phi_p (0 in the absolute form)
+      const float xr = rel ? fmaf(-bhr, ph, chr) + lor : 0.f;
+      const float lv = (xr + (m + __log2f(s))) * kLn2;
       const float lv_l = __shfl_sync(0xffffffffu, lv, ((lane - j0) & (SPW - 1)) * LPS);
       if (lane >= j0 && lane < j0 + SPW) ld_mine = lv_l;
 #pragma unroll

@@ -1,6 +1,8 @@
 """The exponent of the factorised pass (lse_fact.cu), restated with exact
-rational arithmetic for each FP32 add and fused multiply-add. Every sample
-is taken relative to a reference state r near its largest exponent:
+rational arithmetic for each FP32 add and fused multiply-add. Where the
+exponents can exceed 2^12 in magnitude, every sample is taken relative to a
+reference state r near its largest exponent (below that the pass forms x_kp
+itself; the second test):
 
     x_k - x_r = fma(-(b_hi,k - b_hi,r), p_hi, c_hi,k - c_hi,r) + (lo_k - lo_r),
     lo_k      = fma(-b_lo,k, p_hi, fma(-b_hi,k, p_lo, c_lo,k)),
@@ -101,3 +103,31 @@ def test_relative_exponent_is_within_a_few_ulps_of_the_difference():
                 worst_abs = max(worst_abs, abs(absd - exact) / scale)
     assert worst <= 2.0
     assert worst_abs > 100.0 * worst
+
+
+def test_absolute_exponent_is_within_a_few_ulps_of_itself():
+    """Below the 2^12 switch the pass forms x_kp itself: fma(-b_hi, p_hi,
+    c_hi) + lo_k, rounded once where c and b' phi cancel. Pinned on
+    tempering magnitudes (|c|, |b' phi| ~ 1e3, |x| a few hundred): within
+    two FP32 ulps of x, while a plain FP32 product and difference lose the
+    operands' ulps (tens of ulps of x)."""
+    g = np.random.default_rng(5)
+    s2 = 2000.0
+    worst, worst_naive = 0.0, 0.0
+    for _ in range(3000):
+        bk = g.uniform(0.5, 1.0)
+        bp = g.uniform(0.5, 1.0)                      # the sample's own state
+        phi = -bp * s2 + np.sqrt(s2) * g.standard_normal()
+        f = -bk * bk * s2 / 2 + g.normal() * 3        # near the solution
+        c = (f + np.log(4000.0)) * LOG2E
+        b = bk * LOG2E
+        k = (*pair(c), *pair(b))
+        ph, pl = pair(phi)
+        x = absolute_exponent(k, ph, pl)
+        exact = Fraction(c) - Fraction(b) * Fraction(float(phi))
+        assert abs(float(exact)) < 4096.0               # the absolute form's range
+        worst = max(worst, abs(float(Fraction(float(x)) - exact)) / ulp32(float(exact)))
+        naive = f32(float(k[0]) - float(f32(float(k[2]) * float(ph))))
+        worst_naive = max(worst_naive, abs(float(Fraction(float(naive)) - exact)) / ulp32(float(exact)))
+    assert worst <= 2.0
+    assert worst_naive > 10.0 * worst
