@@ -130,6 +130,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// max over the 32 lanes of the warp in one instruction (NaN inputs ignored)
+__device__ __forceinline__ float warp_max_f32(float v) {
+  float r;
+  asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -273,9 +273,13 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       const float ph = __shfl_sync(0xffffffffu, ph_l, j);
       const float pl = __shfl_sync(0xffffffffu, pl_l, j);
       const float hw = __shfl_sync(0xffffffffu, h_l, j);
-      const float chr = __shfl_sync(0xffffffffu, chr_l, j);
-      const float bhr = __shfl_sync(0xffffffffu, bhr_l, j);
-      const float lor = __shfl_sync(0xffffffffu, lor_l, j);
+      // the reference state's values: only the relative form uses them
+      float chr = 0.f, bhr = 0.f, lor = 0.f;
+      if (rel) {
+        chr = __shfl_sync(0xffffffffu, chr_l, j);
+        bhr = __shfl_sync(0xffffffffu, bhr_l, j);
+        lor = __shfl_sync(0xffffffffu, lor_l, j);
+      }
       const unsigned long long ph2 = pk2(ph, ph), pl2 = pk2(pl, pl);
       const unsigned long long nchr2 = pk2(-chr, -chr), bhr2 = pk2(bhr, bhr), nlor2 = pk2(-lor, -lor);
       float x[E];  // x_kp - x_rp, or x_kp (log2 units)
@@ -303,8 +307,12 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
         }
       }
       float m = fmaxf(m0, m1);
+      if constexpr (LPS == 32) {
+        m = warp_max_f32(m);  // the whole warp holds one sample
+      } else {
 #pragma unroll
-      for (int o = LPS / 2; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int o = LPS / 2; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      }
       float s0 = 0.f, s1 = 0.f;
       unsigned top = 0u;
       int nt = 0;

@@ -247,8 +247,12 @@ __global__ void __launch_bounds__(NT, 1) lse_smaj_kernel(const float* __restrict
           m1 = fmaxf(m1, fmaxf(p1, q1));
         }
         m0 = fmaxf(m0, m1);
+        if constexpr (LPS == 32) {
+          m0 = warp_max_f32(m0);  // the whole warp holds the sample
+        } else {
 #pragma unroll
-        for (int o = LPS / 2; o >= 1; o >>= 1) m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+          for (int o = LPS / 2; o >= 1; o >>= 1) m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        }
         const unsigned long long nm = pk2(-m0, -m0);
         unsigned long long sp = 0ull;   // (sum over even entries, sum over odd entries)
         unsigned top = 0u;

@@ -35,10 +35,15 @@ __device__ __forceinline__ void smaj_pair(const float* c0, const float* c1, int 
       m1 = fmaxf(m1, x1[e]);
     }
   }
+  if constexpr (LPS == 32) {
+    m0 = warp_max_f32(m0);  // the whole warp holds each sample
+    m1 = warp_max_f32(m1);
+  } else {
 #pragma unroll
-  for (int o = LPS / 2; o >= 1; o >>= 1) {
-    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    for (int o = LPS / 2; o >= 1; o >>= 1) {
+      m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+      m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    }
   }
   s0 = 0.f;
   s1 = 0.f;
