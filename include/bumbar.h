@@ -454,9 +454,11 @@ BUMBAR_API mbar_status mbar_lse_pass_static(const void* v, int32_t dtype_bytes, 
  * ------------------------------------------------------------------- */
 typedef struct mbar_server mbar_server;
 
+enum { MBAR_BATCH_PERSISTENT = 1 };
+
 typedef struct {
   int32_t workers;           /* concurrent solves, 1..256 */
-  int32_t pad;
+  int32_t flags;             /* MBAR_BATCH_PERSISTENT: see mbar_batch_solve; servers ignore it */
   uint64_t hbm_budget_bytes; /* device memory the admitted requests may hold together */
   mbar_opts opts;            /* options of every solve */
 } mbar_server_config;
@@ -520,12 +522,21 @@ BUMBAR_API mbar_status mbar_server_stats(mbar_server* server, int64_t* completed
  * waiters get ESTATE). mbar_server_destroy(NULL) is MBAR_OK. */
 BUMBAR_API mbar_status mbar_server_destroy(mbar_server* server);
 
-/* P independent solves through a temporary server with configuration cfg:
- * problem p has K[p] states, N[p] samples, counts N_k[p], energies u_kn[p]
- * (all host, or all device with u_on_device) and coordinate phi[p] (phi
- * nullable, or entries nullable). f_out[p] (host[K[p]]) receives its free
- * energies, reports[p] / statuses[p] (nullable arrays) its report and
- * status. Returns the first failing status, MBAR_OK if all succeeded. */
+/* P independent solves with configuration cfg: problem p has K[p] states,
+ * N[p] samples, counts N_k[p], energies u_kn[p] (all host, or all device
+ * with u_on_device) and coordinate phi[p] (phi nullable, or entries
+ * nullable). f_out[p] (host[K[p]]) receives its free energies, reports[p] /
+ * statuses[p] (nullable arrays) its report and status. Returns the first
+ * failing status, MBAR_OK if all succeeded.
+ * The problems run through a temporary server (cfg->workers threads,
+ * admission within the budget). Without MBAR_BATCH_PERSISTENT in cfg->flags
+ * results are bit for bit those of each problem solved alone. With it
+ * (MBAR_MIXED and binning), every first loop of Algorithm 1 whose level fits
+ * a CTA's shared memory (K <= 256) is queued to a batcher thread, which runs
+ * all queued first loops in one persistent launch (a device queue of the
+ * problems, one CTA each; loops that arrive meanwhile go into the next
+ * launch); those loops sum in another order, so results agree with the
+ * solve alone to rounding, not bit for bit. */
 BUMBAR_API mbar_status mbar_batch_solve(int32_t P, const int64_t* K, const int64_t* N, const int64_t* const* N_k,
                                         const double* const* u_kn, int32_t u_on_device, const double* const* phi,
                                         int32_t phi_on_device, const mbar_server_config* cfg, double* const* f_out,

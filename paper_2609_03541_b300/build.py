@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbumbar.so")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["common.cu", "lse.cu", "lse_regs.cu", "lse_smaj.cu", "lse_fact.cu", "sci_loop.cu", "binning.cu", "prep.cu", "hessian.cu", "hessian_tc.cu", "cholesky.cu", "api.cu", "noalloc.cu", "server.cu", "reweight.cu", "selftest.cu", "autotune.cu"]
+SOURCES = ["common.cu", "lse.cu", "lse_regs.cu", "lse_smaj.cu", "lse_fact.cu", "sci_loop.cu", "binning.cu", "prep.cu", "hessian.cu", "hessian_tc.cu", "cholesky.cu", "api.cu", "noalloc.cu", "server.cu", "reweight.cu", "selftest.cu", "autotune.cu", "batch_loop.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -128,6 +128,7 @@ struct mbar_ctx {
   double t_width = 0.0, t_levels = 0.0;  // host seconds, accumulated during a solve
   cudaStream_t ust = nullptr;            // the caller's stream
   bool graphs = true;                    // capture the binned loops into CUDA graphs
+  FirstLoopBatcher* batcher = nullptr;   // first loops through a shared persistent launch
   double* weights = nullptr;             // last mbar_reweight weights (original sample order)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
@@ -800,7 +801,47 @@ mbar_status first_loop_fused(mbar_ctx* c, const Level& L, mbar_report* rep) {
 
 constexpr double kFusedFirstBytes = 4.0 * (1 << 20);
 
+// The first loop through the context's batcher: the level sample-major, one
+// item of a shared persistent launch (batch_loop.cu); a loop that stopped on
+// an underflowed step continues with the one-problem path, which redoes it.
+mbar_status first_loop_batched(mbar_ctx* c, const Level& L, mbar_report* rep) {
+  float* vT = nullptr;
+  BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&vT), sci_loop_level_bytes(c->K, L.n)));
+  mbar_status s = level_to_samples(static_cast<const float*>(L.v), c->K, L.n, L.ld, vT, c->st);
+  if (s == MBAR_OK && cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st) != cudaSuccess) s = MBAR_ECUDA;
+  if (s == MBAR_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = MBAR_ECUDA;
+  if (s == MBAR_OK) {
+    BatchLoopItem q{};
+    q.vT = vT;
+    q.K = static_cast<int>(c->K);
+    q.n = static_cast<int>(L.n);
+    q.Kp = static_cast<int>(stage_pitch(c->K));
+    q.H = L.H;
+    q.f = c->f;
+    q.logN = c->logN_d;
+    q.Nk = c->Nk_d;
+    q.ctrl = c->ctrl;
+    q.s_out = c->s;
+    q.eps = c->opts.eps;
+    q.noise = c->opts.noise_floor;
+    q.max_steps = c->opts.max_sci;
+    s = first_loop_batcher_run(c->batcher, q);
+  }
+  if (s == MBAR_OK) s = read_status(c);
+  dfree(c, vT);
+  if (s != MBAR_OK) return s;
+  const Ctrl h = c->hstat->ctrl;
+  rep->iters_first_loop += h.iters;
+  if (!h.underflow && (h.done || h.iters >= c->opts.max_sci)) {
+    trace_row(c, 1, static_cast<double>(L.n_sched), h.last_s, static_cast<double>(h.iters));
+    return MBAR_OK;
+  }
+  return first_loop_fused(c, L, rep);
+}
+
 mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
+  if (c->batcher && c->dtype == 4 && L.binned && first_loop_batch_supported(c->K, L.n))
+    return first_loop_batched(c, L, rep);
   if (c->dtype == 4 && L.binned && sci_loop_supported(c->K, L.n, kFusedFirstBytes)) return first_loop_fused(c, L, rep);
   BUMBAR_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st));
   auto batch = [&]() -> mbar_status {
@@ -1408,6 +1449,10 @@ struct StreamFence {
 namespace bumbar {
 void ctx_set_graphs(mbar_ctx* c, bool on) {
   if (c) c->graphs = on;
+}
+
+void ctx_set_batcher(mbar_ctx* c, FirstLoopBatcher* b) {
+  if (c) c->batcher = b;
 }
 }  // namespace bumbar
 

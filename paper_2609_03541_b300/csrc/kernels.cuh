@@ -96,6 +96,32 @@ struct SciLoopParams {
 bool sci_loop_supported(int64_t K, int64_t n, double max_bytes);
 size_t sci_loop_level_bytes(int64_t K, int64_t n);
 mbar_status sci_loop_launch(const float* vT, const SciLoopParams& prm, cudaStream_t st);
+// Algorithm 1's first loop for many problems in one persistent launch
+// (batch_loop.cu): a device queue of descriptors, one CTA per problem with its
+// level in shared memory; K <= 256.
+struct BatchLoopItem {
+  const float* vT;  // the level sample-major (n x Kp, zero padded)
+  int K, n, Kp, pad;
+  const int32_t* H;
+  double* f;  // [K] in/out
+  const double* logN;
+  const double* Nk;
+  Ctrl* ctrl;
+  double* s_out;
+  double eps, noise;
+  int64_t max_steps;
+};
+bool first_loop_batch_supported(int64_t K, int64_t n);
+// level_floats: the largest n x Kp of the items
+mbar_status first_loop_batch_launch(const BatchLoopItem* items_dev, int count, int* next_dev, size_t level_floats,
+                                    cudaStream_t st);
+// Continuous batching of the first loops of concurrent solves (batch_loop.cu):
+// run() queues one item and blocks until the launch that took it has ended.
+struct FirstLoopBatcher;
+FirstLoopBatcher* first_loop_batcher_create();
+void first_loop_batcher_destroy(FirstLoopBatcher* b);
+mbar_status first_loop_batcher_run(FirstLoopBatcher* b, const BatchLoopItem& item);
+void first_loop_batcher_stats(FirstLoopBatcher* b, int64_t* launches, int64_t* items);
 // out[p * stage_pitch(K) + k] = v[k * ld + p] for p < n (entries k >= K zero).
 mbar_status level_to_samples(const float* v, int64_t K, int64_t n, int64_t ld, float* out, cudaStream_t st);
 LsePlan lse_smaj_plan(int64_t K, int64_t n);
@@ -278,6 +304,9 @@ bool tc_cluster_enabled();
 // loops (server workers: a stream capture in one thread would make another
 // thread's device-wide synchronisation fail).
 void ctx_set_graphs(mbar_ctx* c, bool on);
+// A context whose first loop (MIXED, a level that fits the batched kernel)
+// goes through the batcher (nullptr: its own launches).
+void ctx_set_batcher(mbar_ctx* c, FirstLoopBatcher* b);
 
 // Eqs. 5-6 (reweight.cu): p (original sample order) and log C from the
 // target potential u0 (original order), the LSE pass's logden (stored order,

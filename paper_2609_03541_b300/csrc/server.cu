@@ -106,6 +106,7 @@ struct mbar_server {
   int running = 0;  // admitted and not finished
   bool stop = false;
   std::vector<std::thread> workers;
+  FirstLoopBatcher* batcher = nullptr;  // set by mbar_batch_solve with MBAR_BATCH_PERSISTENT
   // statistics
   uint64_t peak_bytes = 0;
   int peak_running = 0;
@@ -143,6 +144,7 @@ struct mbar_server {
     // no stream capture on worker threads: the caller's other threads may
     // synchronise the whole device at any time
     if (s == MBAR_OK) ctx_set_graphs(ctx, false);
+    if (s == MBAR_OK && batcher) ctx_set_batcher(ctx, batcher);
     if (s == MBAR_OK && r.phi && !r.factorised) s = mbar_set_coordinate(ctx, r.phi, r.phi_on_device);
     if (s == MBAR_OK || s == MBAR_ENOTCONV) {
       if (s == MBAR_OK) s = mbar_solve(ctx, nullptr, &r.report);
@@ -385,6 +387,18 @@ mbar_status mbar_batch_solve(int32_t P, const int64_t* K, const int64_t* N, cons
   }
   mbar_server* s = nullptr;
   BUMBAR_TRY(mbar_server_create(&s, cfg));
+  // MBAR_BATCH_PERSISTENT: the workers' first loops go through one batcher
+  // (continuous batching into persistent launches); set before any submit
+  FirstLoopBatcher* batcher = nullptr;
+  if ((cfg->flags & MBAR_BATCH_PERSISTENT) && cfg->opts.precision == MBAR_MIXED && cfg->opts.use_binning) {
+    batcher = first_loop_batcher_create();
+    if (!batcher) {
+      mbar_server_destroy(s);
+      set_error("mbar_batch_solve: cannot start the first-loop batcher");
+      return MBAR_ENOMEM;
+    }
+    s->batcher = batcher;
+  }
   std::vector<int64_t> ids(static_cast<size_t>(P), -1);
   mbar_status first_err = MBAR_OK;
   for (int32_t p = 0; p < P; ++p) {
@@ -402,6 +416,7 @@ mbar_status mbar_batch_solve(int32_t P, const int64_t* K, const int64_t* N, cons
     if (st != MBAR_OK && first_err == MBAR_OK) first_err = st;
   }
   mbar_server_destroy(s);
+  first_loop_batcher_destroy(batcher);
   return first_err;
 }
 

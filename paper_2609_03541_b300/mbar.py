@@ -98,10 +98,13 @@ class TuneResult(ctypes.Structure):
 TUNE_SAMPLES, TUNE_FACTORISED = 0, 1
 
 
+BATCH_PERSISTENT = 1
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [
         ("workers", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_uint64),
         ("opts", Opts),
     ]
@@ -558,9 +561,12 @@ def footprint_factorised_bytes(K: int, N: int, precision: int = MBAR_MIXED, use_
 
 
 def server_config(workers: int = 8, hbm_budget_bytes: int = 160 << 30, precision: int = MBAR_MIXED,
-                  opts: Opts | None = None) -> ServerConfig:
+                  opts: Opts | None = None, persistent: bool = False) -> ServerConfig:
+    """``mbar_server_config``; persistent: MBAR_BATCH_PERSISTENT for
+    ``batch_solve`` (the first loops of a group in one persistent launch)."""
     cfg = ServerConfig()
     cfg.workers = int(workers)
+    cfg.flags = BATCH_PERSISTENT if persistent else 0
     cfg.hbm_budget_bytes = int(hbm_budget_bytes)
     cfg.opts = opts if opts is not None else default_opts(precision)
     cfg.opts.precision = int(precision)

@@ -115,3 +115,36 @@ def test_mixed_gradient_keeps_small_weight_deficits(name):
     with M.Context(p.u_kn, p.N_k, M.MBAR_MIXED) as ctx:
         _, g, _ = ctx.sci_step(f_ref)
     assert np.max(np.abs(g)) < 5e-5, g
+
+
+def test_persistent_batched_solve_matches_the_oracle():
+    """mbar_batch_solve with MBAR_BATCH_PERSISTENT: the workers' first loops
+    are queued to a batcher that runs whatever is queued in one persistent
+    launch (one CTA per problem from a device queue); roots within the mixed
+    tolerance, and each first loop takes the steps of the solve alone, to
+    one step (its sums add in another order)."""
+    cases = [REFS[n] for n in BATCH_TYPES]
+    probs = [_problem(c) for c in cases]
+    cfg = M.server_config(workers=4, hbm_budget_bytes=8 << 30, precision=M.MBAR_MIXED, persistent=True)
+    fs, reps, sts = M.batch_solve([(p.u_kn, p.N_k, p.phi) for p in probs], cfg)
+    assert all(s == 0 for s in sts), sts
+    for c, p, f, r in zip(cases, probs, fs, reps):
+        assert np.max(np.abs(f - np.asarray(c["f"]))) < TOL[M.MBAR_MIXED], c["name"]
+        _, alone = _solve(p, M.MBAR_MIXED)
+        assert r.iters_first_loop > 0
+        assert abs(r.iters_first_loop - alone["iters_first_loop"]) <= 1, (c["name"], r.as_dict(), alone)
+
+
+def test_persistent_batched_solve_under_a_tight_budget():
+    """A budget of about two problems' footprints: admission keeps at most
+    two solves on the device, so the batcher's launches carry one or two
+    first loops each."""
+    names = ["umbrella_K9", "umbrella_K17", "harmonic_K33", "umbrella_K64", "harmonic_K4"]
+    cases = [REFS[n] for n in names]
+    probs = [_problem(c) for c in cases]
+    foot = max(M.footprint_bytes(len(p.N_k), int(p.N_k.sum())) for p in probs)
+    cfg = M.server_config(workers=3, hbm_budget_bytes=int(2.2 * foot), precision=M.MBAR_MIXED, persistent=True)
+    fs, reps, sts = M.batch_solve([(p.u_kn, p.N_k, p.phi) for p in probs], cfg)
+    assert all(s == 0 for s in sts), sts
+    for c, f in zip(cases, fs):
+        assert np.max(np.abs(f - np.asarray(c["f"]))) < TOL[M.MBAR_MIXED], c["name"]
