@@ -627,9 +627,23 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
     }
   }
 
+  // a tile one bin covers: where lane 0 puts its sum (the same on every row):
+  // 0 the continuation of a bin opened in an earlier tile (carry0), 1 the
+  // bin's mean (the bin lies inside the tile), 2 its opening part (carry1)
+  int one_mode[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    one_mode[l] = 0;
+    if (lane == 0 && nvalid > 0 && (bits[l] & (1u << 13))) {
+      const int64_t st = ml.l[l].start[b0[l]], en = ml.l[l].start[b0[l] + 1];
+      one_mode[l] = st < tile0 ? 0 : (en <= tile_end ? 1 : 2);
+    }
+  }
+
   const int64_t k_begin = static_cast<int64_t>(blockIdx.y) * kBmRowsPerBlock;
   const int64_t k_end = (k_begin + kBmRowsPerBlock < K) ? k_begin + kBmRowsPerBlock : K;
   A xn[kBmCols];
+  // row pointers advanced by their strides (no 64-bit products in the loop)
   if (k_begin < k_end) load8<T, A>(v + k_begin * ld + c0, nvalid, xn);
   for (int64_t k = k_begin; k < k_end; ++k) {
     A x[kBmCols];
@@ -650,12 +664,10 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) {
-          const int bin = b0[l];
-          const int64_t st = ml.l[l].start[bin], en = ml.l[l].start[bin + 1];
-          if (st < tile0)
+          if (one_mode[l] == 0)
             ml.l[l].carry0[tile * K + k] = static_cast<double>(t);
-          else if (en <= tile_end)
-            out[bin] = static_cast<T>(t * inv0[l]);
+          else if (one_mode[l] == 1)
+            out[b0[l]] = static_cast<T>(t * inv0[l]);
           else
             ml.l[l].carry1[tile * K + k] = static_cast<double>(t);
         }
@@ -739,21 +751,35 @@ __global__ void __launch_bounds__(kThreads) bin_means_fine(const T* __restrict__
   const int64_t k0 = static_cast<int64_t>(blockIdx.y) * kFineRows;
   const int64_t k1 = (k0 + kFineRows < K) ? k0 + kFineRows : K;
   int64_t k = k0;
-  for (; k + 4 <= k1; k += 4) {  // four rows at a time: their loads are in flight together
+  for (; k + 8 <= k1; k += 8) {  // eight rows at a time: their loads are in flight together
     const T* r0 = v + k * ld;
-    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0);
+    A a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = A(0);
     for (int64_t c = s; c < e; ++c) {
-      const A x0 = static_cast<A>(r0[c]), x1 = static_cast<A>(r0[ld + c]);
-      const A x2 = static_cast<A>(r0[2 * ld + c]), x3 = static_cast<A>(r0[3 * ld + c]);
-      a0 += x0;
-      a1 += x1;
-      a2 += x2;
-      a3 += x3;
+      A x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = static_cast<A>(r0[i * ld + c]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] += x[i];
     }
-    out[k * ld_out + b] = static_cast<T>(a0 * inv);
-    out[(k + 1) * ld_out + b] = static_cast<T>(a1 * inv);
-    out[(k + 2) * ld_out + b] = static_cast<T>(a2 * inv);
-    out[(k + 3) * ld_out + b] = static_cast<T>(a3 * inv);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[(k + i) * ld_out + b] = static_cast<T>(a[i] * inv);
+  }
+  for (; k + 4 <= k1; k += 4) {
+    const T* r0 = v + k * ld;
+    A a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = A(0);
+    for (int64_t c = s; c < e; ++c) {
+      A x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = static_cast<A>(r0[i * ld + c]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] += x[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[(k + i) * ld_out + b] = static_cast<T>(a[i] * inv);
   }
   for (; k < k1; ++k) {
     const T* row = v + k * ld;
