@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kSortTile = 1024;  // elements per warp tile
 constexpr int kScanBlock = 1024; // elements per block in the scan (256 threads x 4)
-constexpr int kMaxWidths = 15;   // candidate widths per counting pass
+constexpr int kMaxWidths = kWidthsPerPass;  // candidate widths per counting pass
 
 __device__ __forceinline__ unsigned long long order_key(double x) {
   unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
@@ -263,11 +263,15 @@ struct WidthSet {
 };
 constexpr int kCountChunk = 16;
 
+// Up to kWidthsPerRow widths per grid row (blockIdx.y): a full pass runs as
+// ceil(nw / kWidthsPerRow) times as many CTAs (several waves instead of one
+// and a small remainder), each row reading the chunks again from L2.
+constexpr int kWidthsPerRow = 4;
 __global__ void __launch_bounds__(kThreads) count_heads_multi(const float2* __restrict__ dhl,
                                                                const double* __restrict__ d, int64_t N, WidthSet ws,
                                                                unsigned long long* __restrict__ counts) {
-  __shared__ unsigned int cnt[kMaxWidths];
-  if (threadIdx.x < kMaxWidths) cnt[threadIdx.x] = 0u;
+  __shared__ unsigned int cnt[kWidthsPerRow];
+  if (threadIdx.x < kWidthsPerRow) cnt[threadIdx.x] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * kCountChunk;
@@ -306,7 +310,9 @@ __global__ void __launch_bounds__(kThreads) count_heads_multi(const float2* __re
     }
     return heads;
   };
-  for (int c = 0; c < ws.n; ++c) {
+  const int c0 = blockIdx.y * kWidthsPerRow;
+  const int c1 = (c0 + kWidthsPerRow < ws.n) ? c0 + kWidthsPerRow : ws.n;
+  for (int c = c0; c < c1; ++c) {
     unsigned int heads = 0;
     if (nv > 0) {
       const RecipW r = ws.r[c];
@@ -317,10 +323,11 @@ __global__ void __launch_bounds__(kThreads) count_heads_multi(const float2* __re
         heads = chunk_heads(r, [](float2 v, const RecipW& rw, const double* de) { return key_df(v.x, v.y, rw, de); });
     }
     for (int o = 16; o >= 1; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
-    if (lane == 0 && heads) atomicAdd(&cnt[c], heads);
+    if (lane == 0 && heads) atomicAdd(&cnt[c - c0], heads);
   }
   __syncthreads();
-  if (threadIdx.x < ws.n && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], static_cast<unsigned long long>(cnt[threadIdx.x]));
+  if (threadIdx.x < c1 - c0 && cnt[threadIdx.x])
+    atomicAdd(&counts[c0 + threadIdx.x], static_cast<unsigned long long>(cnt[threadIdx.x]));
 }
 
 __global__ void offsets_from_lo(const double* __restrict__ phi, int64_t N, double* __restrict__ d,
@@ -981,8 +988,9 @@ mbar_status count_bins(const float2* d_pairs, const double* d_sorted, int64_t N,
   ws.n = nw;
   for (int c = 0; c < nw; ++c) ws.r[c] = make_recip(widths[c]);
   BUMBAR_CUDA(cudaMemsetAsync(counts_dev, 0, kMaxWidths * sizeof(unsigned long long), st));
-  count_heads_multi<<<static_cast<unsigned>(ceil_div(N, static_cast<int64_t>(kThreads) * kCountChunk)), kThreads, 0,
-                      st>>>(d_pairs, d_sorted, N, ws, counts_dev);
+  const dim3 grid(static_cast<unsigned>(ceil_div(N, static_cast<int64_t>(kThreads) * kCountChunk)),
+                  static_cast<unsigned>(ceil_div(nw, kWidthsPerRow)));
+  count_heads_multi<<<grid, kThreads, 0, st>>>(d_pairs, d_sorted, N, ws, counts_dev);
   count_launches(1);
   BUMBAR_CUDA(cudaGetLastError());
   return MBAR_OK;

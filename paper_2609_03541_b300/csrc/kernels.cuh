@@ -198,7 +198,7 @@ mbar_status offsets_from_min(const double* phi_sorted, int64_t N, double* d_sort
 
 // Counts of nonempty bins g(w) over the sorted offsets for nw <= 15 widths
 // in one pass; counts_dev holds 15 entries.
-constexpr int kWidthsPerPass = 15;
+constexpr int kWidthsPerPass = 15;  // candidate widths per counting pass
 mbar_status count_bins(const float2* d_pairs, const double* d_sorted, int64_t N, const double* widths, int nw,
                        unsigned long long* counts_dev, cudaStream_t stream);
 
