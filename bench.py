@@ -388,6 +388,7 @@ def hess_only(args):
     from paper_2609_03541_b300 import mbar as M
     from paper_2609_03541_b300 import workloads as W
     K, n = args.lse_K, args.lse_n
+    M.set_hessian_path(args.hess_path)
     if args.hess_layout == "factorised":
         beta, E, Nk = W.gaussian_overlap_device(K, max(1, n // K), seed=0)
         ctx = M.Context.factorised(torch.zeros_like(beta), beta, E, Nk, M.MBAR_MIXED)
@@ -698,7 +699,7 @@ class DeviceMemorySampler:
         self._t.join()
 
 
-def serve_run(reqs, workers: int, budget: int, rate, seed: int):
+def serve_run(reqs, workers: int, budget: int, rate, seed: int, persistent: bool = False):
     """One pass of the request stream through a fresh mbar_server (MIXED):
     at saturation (rate None: all submitted at once) or with Poisson
     arrivals at `rate` requests/s, each submitted at its arrival time.
@@ -707,7 +708,7 @@ def serve_run(reqs, workers: int, budget: int, rate, seed: int):
     from paper_2609_03541_b300 import mbar as M
     R = len(reqs)
     arr = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=R)) if rate else np.zeros(R)
-    cfg = M.server_config(workers=workers, hbm_budget_bytes=budget, precision=M.MBAR_MIXED)
+    cfg = M.server_config(workers=workers, hbm_budget_bytes=budget, precision=M.MBAR_MIXED, persistent=persistent)
     lat, failed, rejected = [], 0, 0
     phases = dict(width_s=0.0, levels_s=0.0, sci_s=0.0, newton_s=0.0, run_s=0.0, first_loop_iters=0,
                   second_loop_iters=0, newton_iters=0)
@@ -774,12 +775,13 @@ def serve_block(args, R: int, loads, poisson_requests: int | None = None):
     budget = int(args.budget_gb * (1 << 30))
     log(f"[bench] serve: {R} requests drawn in {gen_s:.1f} s ({nbytes / 2 ** 30:.1f} GB of inputs, "
         f"{entries:.3g} entries)")
-    sat = serve_run(reqs, args.workers, budget, None, args.seed)
+    sat = serve_run(reqs, args.workers, budget, None, args.seed, args.serve_persistent)
     log(f"[bench] serve saturation: {sat}")
     loads_out = {}
     sub = reqs[:poisson_requests] if poisson_requests else reqs
     for frac in loads:
-        loads_out[str(frac)] = serve_run(sub, args.workers, budget, frac * sat["solves_per_s"], args.seed + 1)
+        loads_out[str(frac)] = serve_run(sub, args.workers, budget, frac * sat["solves_per_s"], args.seed + 1,
+                                         args.serve_persistent)
         log(f"[bench] serve load {frac}: {loads_out[str(frac)]}")
     del reqs
     torch.cuda.empty_cache()
@@ -848,6 +850,8 @@ def main():
                     help="--lse-layout factorised: tempering magnitudes (relative exponents) or O(1) potentials")
     ap.add_argument("--hess-layout", default="dense", choices=["dense", "factorised"],
                     help="--hess-only: a dense MIXED context, or a store-free factorised one")
+    ap.add_argument("--hess-path", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="--hess-only: mbar_set_hessian_path (0 by size, 3 tensor cores without clusters)")
     ap.add_argument("--hess-only", action="store_true",
                     help="time mbar_hessian (one fused LSE pass + the tensor-core Hessian) on a random K x n problem")
     ap.add_argument("--problems", type=int, default=512, help="batch: number of problems")
@@ -855,6 +859,8 @@ def main():
     ap.add_argument("--loads", type=lambda t: [float(x) for x in t.split(",") if x], default=[0.5, 0.9],
                     help="serve: Poisson arrival rates as fractions of the measured capacity")
     ap.add_argument("--workers", type=int, default=16, help="batch/serve: concurrent solves")
+    ap.add_argument("--serve-persistent", action="store_true",
+                    help="serve: the server batches its first loops into persistent launches")
     ap.add_argument("--budget-gb", type=float, default=None,
                     help="batch/serve: device memory budget of the server (default 140 batch, 160 serve)")
     ap.add_argument("--wave-gb", type=float, default=80.0, help="batch/serve: FP64 input memory held at once")

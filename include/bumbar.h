@@ -458,7 +458,7 @@ enum { MBAR_BATCH_PERSISTENT = 1 };
 
 typedef struct {
   int32_t workers;           /* concurrent solves, 1..256 */
-  int32_t flags;             /* MBAR_BATCH_PERSISTENT: see mbar_batch_solve; servers ignore it */
+  int32_t flags;             /* MBAR_BATCH_PERSISTENT: first loops batched (mbar_batch_solve) */
   uint64_t hbm_budget_bytes; /* device memory the admitted requests may hold together */
   mbar_opts opts;            /* options of every solve */
 } mbar_server_config;
@@ -477,7 +477,11 @@ BUMBAR_API uint64_t mbar_footprint_bytes(int64_t K, int64_t N, int32_t precision
  * footprint of a context made from device u. 0 for K < 1 or N < 1. */
 BUMBAR_API uint64_t mbar_footprint_factorised_bytes(int64_t K, int64_t N, int32_t precision, int32_t use_binning);
 
-/* Starts `cfg->workers` worker threads on the current device.
+/* Starts `cfg->workers` worker threads on the current device. With
+ * MBAR_BATCH_PERSISTENT in cfg->flags (MBAR_MIXED and binning) the server
+ * also runs a first-loop batcher: the first loops of the solves it runs go
+ * into shared persistent launches (see mbar_batch_solve), and results agree
+ * with the solves alone to rounding instead of bit for bit.
  * EINVAL for a bad configuration, ENOMEM if the threads cannot start. */
 BUMBAR_API mbar_status mbar_server_create(mbar_server** out, const mbar_server_config* cfg);
 

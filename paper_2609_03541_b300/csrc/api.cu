@@ -1244,7 +1244,13 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   // so this only matters when some |a_k| is large: below 64 kT the FP32
   // spacing there is under 1e-5 kT per entry and the data stay as they are.
   float* cur_vT = nullptr;  // owned: the current level sample-major, when small
-  constexpr double kFusedRoundBytes = 4.0 * (1 << 20);
+  // Levels up to 4 MB take the one-launch loop (a cluster of 8 SMs streaming
+  // the level from L2). Without CUDA graphs (server workers, with other
+  // solves on the GPU beside them) a round on a larger level is 2 x 21
+  // separate full-grid launches of a few microseconds each from a host
+  // thread; there the cluster loop runs up to 32 MB: 8 SMs per solve leave
+  // the rest of the GPU to the other solves.
+  const double kFusedRoundBytes = (c->graphs ? 4.0 : 32.0) * (1 << 20);
   auto recenter_pair = [&]() -> mbar_status {
     if (c->dtype != 4) return MBAR_OK;
     BUMBAR_TRY(d2h(c, c->f_h.data(), c->f, K));

@@ -106,7 +106,7 @@ struct mbar_server {
   int running = 0;  // admitted and not finished
   bool stop = false;
   std::vector<std::thread> workers;
-  FirstLoopBatcher* batcher = nullptr;  // set by mbar_batch_solve with MBAR_BATCH_PERSISTENT
+  FirstLoopBatcher* batcher = nullptr;  // MBAR_BATCH_PERSISTENT: the workers' first loops, batched
   // statistics
   uint64_t peak_bytes = 0;
   int peak_running = 0;
@@ -242,6 +242,14 @@ mbar_status mbar_server_create(mbar_server** out, const mbar_server_config* cfg)
   }
   s->cfg = *cfg;
   cudaGetDevice(&s->device);
+  if ((cfg->flags & MBAR_BATCH_PERSISTENT) && cfg->opts.precision == MBAR_MIXED && cfg->opts.use_binning) {
+    s->batcher = first_loop_batcher_create();
+    if (!s->batcher) {
+      delete s;
+      set_error("mbar_server_create: cannot start the first-loop batcher");
+      return MBAR_ENOMEM;
+    }
+  }
   try {
     for (int i = 0; i < cfg->workers; ++i) s->workers.emplace_back([s] { s->worker_main(); });
   } catch (...) {
@@ -251,6 +259,7 @@ mbar_status mbar_server_create(mbar_server** out, const mbar_server_config* cfg)
     }
     s->cv_work.notify_all();
     for (auto& t : s->workers) t.join();
+    first_loop_batcher_destroy(s->batcher);
     delete s;
     set_error("mbar_server_create: cannot start worker threads");
     return MBAR_ENOMEM;
@@ -373,6 +382,7 @@ mbar_status mbar_server_destroy(mbar_server* s) {
   s->cv_work.notify_all();
   s->cv_done.notify_all();
   for (auto& t : s->workers) t.join();
+  first_loop_batcher_destroy(s->batcher);  // after the workers: nothing is queued any more
   delete s;
   return MBAR_OK;
 }
@@ -387,18 +397,6 @@ mbar_status mbar_batch_solve(int32_t P, const int64_t* K, const int64_t* N, cons
   }
   mbar_server* s = nullptr;
   BUMBAR_TRY(mbar_server_create(&s, cfg));
-  // MBAR_BATCH_PERSISTENT: the workers' first loops go through one batcher
-  // (continuous batching into persistent launches); set before any submit
-  FirstLoopBatcher* batcher = nullptr;
-  if ((cfg->flags & MBAR_BATCH_PERSISTENT) && cfg->opts.precision == MBAR_MIXED && cfg->opts.use_binning) {
-    batcher = first_loop_batcher_create();
-    if (!batcher) {
-      mbar_server_destroy(s);
-      set_error("mbar_batch_solve: cannot start the first-loop batcher");
-      return MBAR_ENOMEM;
-    }
-    s->batcher = batcher;
-  }
   std::vector<int64_t> ids(static_cast<size_t>(P), -1);
   mbar_status first_err = MBAR_OK;
   for (int32_t p = 0; p < P; ++p) {
@@ -416,7 +414,6 @@ mbar_status mbar_batch_solve(int32_t P, const int64_t* K, const int64_t* N, cons
     if (st != MBAR_OK && first_err == MBAR_OK) first_err = st;
   }
   mbar_server_destroy(s);
-  first_loop_batcher_destroy(batcher);
   return first_err;
 }
 
