@@ -50,7 +50,7 @@ typedef enum {
   MBAR_ENOTCONV = 4,    /* iteration limit reached; the current f is readable */
   MBAR_ESTATE = 5,      /* call not valid in the context's current state */
   MBAR_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
-  MBAR_EUNSUPPORTED = 7 /* size outside what this build supports */
+  MBAR_EUNSUPPORTED = 7 /* size or option outside what the library supports */
 } mbar_status;
 
 typedef enum {

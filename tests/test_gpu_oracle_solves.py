@@ -5,7 +5,7 @@ tests/golden/make_solve_refs.py, which calls only the oracle (its solves
 take up to minutes on the host at these sizes). Each case is rebuilt here
 from the same seeded generator, solved on the device, and compared element
 by element: 1e-8 kT on the FP64 path, 1e-4 kT on the mixed path (the
-spec tolerances; Eq. 1 at its unbinned fixed point, Sec. II).
+mixed-precision and FP64 tolerances; Eq. 1 at its unbinned fixed point, Sec. II).
 
 Cases:
   * the batched workload's problem types: umbrella windows on the double
