@@ -453,8 +453,8 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
                                                            const int32_t* __restrict__ seg,
                                                            const int32_t* __restrict__ start,
                                                            const double* __restrict__ inv_count, T* __restrict__ out,
-                                                           int64_t ld_out, double* __restrict__ carry0,
-                                                           double* __restrict__ carry1, int64_t ntiles) {
+                                                           int64_t ld_out, typename Acc<T>::type* __restrict__ carry0,
+                                                           typename Acc<T>::type* __restrict__ carry1, int64_t ntiles) {
   using A = typename Acc<T>::type;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + warp;
@@ -535,18 +535,18 @@ __global__ void __launch_bounds__(kThreads) bin_sums_block(const T* __restrict__
         if (st_b0 >= tile0)
           out[k * ld_out + b0] = static_cast<T>(tot * inv_b0);
         else
-          carry0[tile * K + k] = static_cast<double>(tot);
+          carry0[tile * K + k] = tot;
       }
       if (last_ends_here) {
         if (st_bl >= tile0)
           out[k * ld_out + bl] = static_cast<T>(sv * inv_bl);
         else
-          carry0[tile * K + k] = static_cast<double>(sv);
+          carry0[tile * K + k] = sv;
       } else if (last_lane) {
         if (st_bl >= tile0)
-          carry1[tile * K + k] = static_cast<double>(sv);
+          carry1[tile * K + k] = sv;
         else
-          carry0[tile * K + k] = static_cast<double>(sv);
+          carry0[tile * K + k] = sv;
       }
     }
   }
@@ -565,8 +565,8 @@ struct LevelOut {
   const double* inv;
   void* out;
   int64_t ld_out;
-  double* carry0;
-  double* carry1;
+  void* carry0;  // partial sums at tile edges, in the kernel's accumulator type
+  void* carry1;
 };
 struct MultiLevel {
   LevelOut l[kMaxLevels];
@@ -672,11 +672,11 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
         for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) {
           if (one_mode[l] == 0)
-            ml.l[l].carry0[tile * K + k] = static_cast<double>(t);
+            static_cast<A*>(ml.l[l].carry0)[tile * K + k] = t;
           else if (one_mode[l] == 1)
             out[b0[l]] = static_cast<T>(t * inv0[l]);
           else
-            ml.l[l].carry1[tile * K + k] = static_cast<double>(t);
+            static_cast<A*>(ml.l[l].carry1)[tile * K + k] = t;
         }
         continue;
       }
@@ -716,25 +716,25 @@ __global__ void __launch_bounds__(kThreads) bin_sums_multi(const T* __restrict__
       if (lane == 0) prev = A(0);
       if (nvalid > 0) {
         const int nruns = static_cast<int>((b >> 16) & 15u);
-        double* carry0 = ml.l[l].carry0 + tile * K + k;
+        A* carry0 = static_cast<A*>(ml.l[l].carry0) + tile * K + k;
         if (nruns > 0) {  // the first run ends inside this lane
           const A tot = (((b >> 9) & 1) ? prev : A(0)) + head;
           if ((b >> 11) & 1)
             out[b0[l]] = static_cast<T>(tot * inv0[l]);
           else
-            *carry0 = static_cast<double>(tot);
+            *carry0 = tot;
         }
         const int bl = b0[l] + nruns;
         if ((b >> 10) & 1) {
           if ((b >> 12) & 1)
             out[bl] = static_cast<T>(sv * invl[l]);
           else
-            *carry0 = static_cast<double>(sv);
+            *carry0 = sv;
         } else if (last_lane) {
           if ((b >> 12) & 1)
-            ml.l[l].carry1[tile * K + k] = static_cast<double>(sv);
+            static_cast<A*>(ml.l[l].carry1)[tile * K + k] = sv;
           else
-            *carry0 = static_cast<double>(sv);
+            *carry0 = sv;
         }
       }
     }
@@ -810,7 +810,8 @@ constexpr int kFixWarps = kThreads / 32;
 template <typename T>
 __global__ void bin_sums_fixup(int64_t K, const int32_t* __restrict__ seg, const int32_t* __restrict__ start,
                                const double* __restrict__ inv_count, T* __restrict__ out, int64_t ld_out,
-                               const double* __restrict__ carry0, const double* __restrict__ carry1, int64_t ntiles) {
+                               const typename Acc<T>::type* __restrict__ carry0,
+                               const typename Acc<T>::type* __restrict__ carry1, int64_t ntiles) {
   const int lane = threadIdx.x & 31;
   const int64_t t = static_cast<int64_t>(blockIdx.x) * kFixWarps + (threadIdx.x >> 5) + 1;
   if (t >= ntiles) return;
@@ -821,16 +822,16 @@ __global__ void bin_sums_fixup(int64_t K, const int32_t* __restrict__ seg, const
   const int64_t k = static_cast<int64_t>(blockIdx.y) * 32 + lane;
   if (k >= K) return;
   const int64_t te = (static_cast<int64_t>(start[b + 1]) - 1) / kBmTile;
-  double sum = carry1[(t - 1) * K + k];
+  double sum = static_cast<double>(carry1[(t - 1) * K + k]);
   int64_t u = t;
   for (; u + 8 <= te + 1; u += 8) {  // eight loads in flight, added in order
     double x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = carry0[(u + j) * K + k];
+    for (int j = 0; j < 8; ++j) x[j] = static_cast<double>(carry0[(u + j) * K + k]);
 #pragma unroll
     for (int j = 0; j < 8; ++j) sum += x[j];
   }
-  for (; u <= te; ++u) sum += carry0[u * K + k];
+  for (; u <= te; ++u) sum += static_cast<double>(carry0[u * K + k]);
   out[k * ld_out + b] = static_cast<T>(sum * inv_count[b]);
 }
 
@@ -1077,9 +1078,9 @@ mbar_status bin_means_multi(const void* v, int dtype_bytes, int64_t K, int64_t N
     o.start = start[l];
     o.out = out[l];
     o.ld_out = ld_out[l];
-    o.carry0 = reinterpret_cast<double*>(q);
+    o.carry0 = q;  // sized for FP64 accumulators; FP32 data uses half
     q += round_up(K * ntiles * 8, 256);
-    o.carry1 = reinterpret_cast<double*>(q);
+    o.carry1 = q;
     q += round_up(K * ntiles * 8, 256);
     double* inv = reinterpret_cast<double*>(q);
     q += round_up(nb[l] * 8, 256);
@@ -1114,10 +1115,12 @@ mbar_status bin_means_multi(const void* v, int dtype_bytes, int64_t K, int64_t N
     const LevelOut& o = ml.l[l];
     if (dtype_bytes == 4)
       bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, o.seg, o.start, o.inv, static_cast<float*>(o.out), o.ld_out,
-                                                     o.carry0, o.carry1, ntiles);
+                                                     static_cast<const float*>(o.carry0),
+                                                     static_cast<const float*>(o.carry1), ntiles);
     else
       bin_sums_fixup<double><<<g2, kThreads, 0, st>>>(K, o.seg, o.start, o.inv, static_cast<double*>(o.out),
-                                                      o.ld_out, o.carry0, o.carry1, ntiles);
+                                                      o.ld_out, static_cast<const double*>(o.carry0),
+                                                      static_cast<const double*>(o.carry1), ntiles);
     count_launches(1);
   }
   BUMBAR_CUDA(cudaGetLastError());
@@ -1146,11 +1149,13 @@ mbar_status bin_means(const void* v, int dtype_bytes, int64_t K, int64_t N, int6
   const dim3 g2(static_cast<unsigned>(std::max<int64_t>(1, ceil_div(ntiles - 1, kFixWarps))),
                 static_cast<unsigned>(ceil_div(K, 32)));
   if (dtype_bytes == 4) {
+    float* c0f = reinterpret_cast<float*>(carry0);  // FP32 accumulators (the buffers fit FP64 ones)
+    float* c1f = reinterpret_cast<float*>(carry1);
     bin_sums_block<float><<<g1, kThreads, 0, st>>>(static_cast<const float*>(v), K, N, ld, seg, start, inv,
-                                                   static_cast<float*>(out), ld_out, carry0, carry1, ntiles);
+                                                   static_cast<float*>(out), ld_out, c0f, c1f, ntiles);
     count_launches(1);
-    bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, seg, start, inv, static_cast<float*>(out), ld_out, carry0,
-                                                   carry1, ntiles);
+    bin_sums_fixup<float><<<g2, kThreads, 0, st>>>(K, seg, start, inv, static_cast<float*>(out), ld_out, c0f, c1f,
+                                                   ntiles);
     count_launches(1);
   } else {
     bin_sums_block<double><<<g1, kThreads, 0, st>>>(static_cast<const double*>(v), K, N, ld, seg, start, inv,
