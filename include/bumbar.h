@@ -243,6 +243,18 @@ BUMBAR_API mbar_status mbar_destroy(mbar_ctx* ctx);
 /* Static description of a status code. */
 BUMBAR_API const char* mbar_status_string(mbar_status status);
 
+/* Whether the context may assume the GPU to itself (1, the default) or
+ * shares it with solves running concurrently on other streams (0). With 1
+ * the binned loops of Algorithm 1 are captured into CUDA graphs, and the
+ * SCI steps of binned FP32 levels that fit in the shared memory of all SMs
+ * (up to ~25 MB) run in one cooperative launch over every SM with the level
+ * resident in shared memory. With 0 no graphs are captured and such levels
+ * run on one cluster of 8 SMs (or as separate launches), leaving the other
+ * SMs to the concurrent solves; a cooperative launch of every SM would wait
+ * for them. Results agree within the tolerance of the mixed precision
+ * (the per-state sums are grouped differently). EINVAL for a null context. */
+BUMBAR_API mbar_status mbar_set_exclusive(mbar_ctx* ctx, int32_t exclusive);
+
 /* Message of the last failed call on this thread ("" if none). */
 BUMBAR_API const char* mbar_last_error(void);
 

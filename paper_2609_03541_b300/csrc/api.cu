@@ -710,8 +710,6 @@ mbar_status newton_phase(mbar_ctx* c, mbar_report* rep) {
   return st;
 }
 
-// Phase-1 loop of Algorithm 1 on level L: guarded in-place SCI steps until
-// s < eps (the guard turns later launches of a batch into no-ops).
 // A captured sequence of launches on the context's stream, replayed with
 // one cudaGraphLaunch (the binned loops of Algorithm 1 launch the same
 // kernels with the same arguments many times).
@@ -742,6 +740,14 @@ mbar_status capture(mbar_ctx* c, Graph* g, F&& body) {
   return MBAR_OK;
 }
 
+// The in-place SCI steps of a small FP32 level over the whole GPU
+// (sci_grid_launch): only where this solve has the device to itself -- a
+// context that captures graphs; server workers share the GPU with other
+// solves, which a cooperative launch of every SM would hold up.
+bool use_grid_loop(const mbar_ctx* c, int64_t n) {
+  return c->graphs && c->dtype == 4 && sci_grid_supported(c->K, n);
+}
+
 // Phase-1 loop of Algorithm 1 on level L: guarded in-place SCI steps until
 // s < eps (the guard turns later launches of a batch into no-ops). A binned
 // level replays a captured batch of kPhase1Batch launches.
@@ -753,6 +759,8 @@ mbar_status first_loop_fused(mbar_ctx* c, const Level& L, mbar_report* rep) {
   float* vT = nullptr;
   BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&vT), sci_loop_level_bytes(c->K, L.n)));
   mbar_status s = level_to_samples(static_cast<const float*>(L.v), c->K, L.n, L.ld, vT, c->st);
+  void* grid_scr = nullptr;
+  if (s == MBAR_OK && use_grid_loop(c, L.n)) s = dalloc(c, &grid_scr, sci_grid_scratch_bytes(c->K));
   SciLoopParams q{};
   q.K = static_cast<int>(c->K);
   q.n = static_cast<int>(L.n);
@@ -770,7 +778,7 @@ mbar_status first_loop_fused(mbar_ctx* c, const Level& L, mbar_report* rep) {
   while (s == MBAR_OK) {
     q.max_steps = c->opts.max_sci - done_iters;
     time_mark(c, true, 5, 0.0);
-    s = sci_loop_launch(vT, q, c->st);
+    s = grid_scr ? sci_grid_launch(vT, q, grid_scr, c->st) : sci_loop_launch(vT, q, c->st);
     time_mark(c, false, 5, 0.0);
     if (s == MBAR_OK) s = read_status(c);
     // the launch streamed the level once per step it took
@@ -795,6 +803,7 @@ mbar_status first_loop_fused(mbar_ctx* c, const Level& L, mbar_report* rep) {
     }
   }
   dfree(c, vT);
+  dfree(c, grid_scr);
   if (s == MBAR_OK) rep->iters_first_loop += done_iters;
   return s;
 }
@@ -842,7 +851,8 @@ mbar_status first_loop_batched(mbar_ctx* c, const Level& L, mbar_report* rep) {
 mbar_status first_loop(mbar_ctx* c, const Level& L, mbar_report* rep) {
   if (c->batcher && c->dtype == 4 && L.binned && first_loop_batch_supported(c->K, L.n))
     return first_loop_batched(c, L, rep);
-  if (c->dtype == 4 && L.binned && sci_loop_supported(c->K, L.n, kFusedFirstBytes)) return first_loop_fused(c, L, rep);
+  if (c->dtype == 4 && L.binned && (use_grid_loop(c, L.n) || sci_loop_supported(c->K, L.n, kFusedFirstBytes)))
+    return first_loop_fused(c, L, rep);
   BUMBAR_CUDA(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->st));
   auto batch = [&]() -> mbar_status {
     for (int b = 0; b < kPhase1Batch; ++b)
@@ -1244,6 +1254,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   // so this only matters when some |a_k| is large: below 64 kT the FP32
   // spacing there is under 1e-5 kT per entry and the data stay as they are.
   float* cur_vT = nullptr;  // owned: the current level sample-major, when small
+  void* grid_scr = nullptr;  // owned: scratch of the grid-wide loop, when it runs the level
   // Levels up to 4 MB take the one-launch loop (a cluster of 8 SMs streaming
   // the level from L2). Without CUDA graphs (server workers, with other
   // solves on the GPU beside them) a round on a larger level is 2 x 21
@@ -1262,18 +1273,25 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
         if (L->binned)
           BUMBAR_TRY(recenter_columns(static_cast<float*>(L->v), K, L->n, L->ld, c->f, c->logN_d, c->st));
     // a small current level: its in-place steps run in one launch on its
-    // sample-major copy (sci_loop.cu)
+    // sample-major copy (sci_loop.cu): over the whole GPU with the level in
+    // shared memory when this solve has the device to itself (graphs), else
+    // on one cluster
     dfree(c, cur_vT);
     cur_vT = nullptr;
-    if (cur.binned && sci_loop_supported(K, cur.n, kFusedRoundBytes)) {
+    dfree(c, grid_scr);
+    grid_scr = nullptr;
+    const bool grid = cur.binned && use_grid_loop(c, cur.n);
+    if (cur.binned && (grid || sci_loop_supported(K, cur.n, kFusedRoundBytes))) {
       BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&cur_vT), sci_loop_level_bytes(K, cur.n)));
       BUMBAR_TRY(level_to_samples(static_cast<const float*>(cur.v), K, cur.n, cur.ld, cur_vT, c->st));
+      if (grid) BUMBAR_TRY(dalloc(c, &grid_scr, sci_grid_scratch_bytes(K)));
     }
     return MBAR_OK;
   };
   s = recenter_pair();
   if (s != MBAR_OK) {
     dfree(c, cur_vT);
+    dfree(c, grid_scr);
     level_free(c, &cur);
     level_free(c, &nxt);
     free_rest();
@@ -1294,7 +1312,10 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
       q.ctrl = c->ctrl;
       q.err = err_word(c);
       q.max_steps = o.n_intermediate;  // eps = noise = 0: exactly these steps
-      BUMBAR_TRY(sci_loop_launch(cur_vT, q, c->st));
+      if (grid_scr)
+        BUMBAR_TRY(sci_grid_launch(cur_vT, q, grid_scr, c->st));
+      else
+        BUMBAR_TRY(sci_loop_launch(cur_vT, q, c->st));
     } else {
       for (int i = 0; i < o.n_intermediate; ++i)
         BUMBAR_TRY(run_lse(c, cur, c->f, kLseModeSci, c->f, nullptr, nullptr, 0.0, 0, nullptr));
@@ -1396,6 +1417,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   g.reset();
   rep->final_bins = cur.binned ? cur.n : 0;
   dfree(c, cur_vT);
+  dfree(c, grid_scr);
   level_free(c, &cur);
   level_free(c, &nxt);
   free_rest();
@@ -2277,6 +2299,12 @@ mbar_status mbar_free_energies(mbar_ctx* c, double* f_out) {
 mbar_status mbar_device_bytes(mbar_ctx* c, int64_t* bytes) {
   CHECK_CTX(c);
   if (bytes) *bytes = c->bytes;
+  return MBAR_OK;
+}
+
+mbar_status mbar_set_exclusive(mbar_ctx* c, int32_t exclusive) {
+  CHECK_CTX(c);
+  c->graphs = exclusive != 0;
   return MBAR_OK;
 }
 

@@ -881,23 +881,35 @@ __global__ void __launch_bounds__(kGtThreads) gather_transpose_kernel(const T* _
   const int64_t P = gt_pitch<T>(K);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * CS;
-  for (int c = warp; c < CS; c += kGtThreads / 32) {
-    const int64_t i = i0 + c;
-    if (i >= N) break;
-    const T* src = vst + static_cast<int64_t>(perm[i]) * stage_pitch(K);
-    T* dst = xs + c * P;
-    // up to 16 loads in flight per lane (a whole column for K <= 512)
+  // two source samples per warp at a time (columns c and c + NW): up to 32
+  // loads in flight per lane (two whole columns for K <= 512), which the
+  // latency of these scattered 2-4 KB reads needs at three CTAs per SM
+  constexpr int NW = kGtThreads / 32;
+  for (int c = warp; c < CS; c += 2 * NW) {
+    const int64_t ia = i0 + c, ib = i0 + c + NW;
+    if (ia >= N) break;
+    const bool hb = c + NW < CS && ib < N;
+    const T* sa = vst + static_cast<int64_t>(perm[ia]) * stage_pitch(K);
+    const T* sb = hb ? vst + static_cast<int64_t>(perm[ib]) * stage_pitch(K) : sa;
+    T* da = xs + c * P;
+    T* db = xs + (c + NW) * P;
     for (int64_t k0 = 0; k0 < K; k0 += 16 * 32) {
-      T x[16];
+      T x[16], y[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const int64_t k = k0 + lane + 32 * r;
-        if (k < K) x[r] = src[k];
+        if (k < K) {
+          x[r] = sa[k];
+          if (hb) y[r] = sb[k];
+        }
       }
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         const int64_t k = k0 + lane + 32 * r;
-        if (k < K) dst[k] = x[r];
+        if (k < K) {
+          da[k] = x[r];
+          if (hb) db[k] = y[r];
+        }
       }
     }
   }

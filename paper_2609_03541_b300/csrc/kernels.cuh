@@ -96,6 +96,12 @@ struct SciLoopParams {
 bool sci_loop_supported(int64_t K, int64_t n, double max_bytes);
 size_t sci_loop_level_bytes(int64_t K, int64_t n);
 mbar_status sci_loop_launch(const float* vT, const SciLoopParams& prm, cudaStream_t st);
+// The same loop over the whole GPU (one cooperative launch, one CTA per SM,
+// the level resident in shared memory): for one solve alone on the device.
+// scratch: sci_grid_scratch_bytes(K) bytes, 256-byte aligned.
+bool sci_grid_supported(int64_t K, int64_t n);
+size_t sci_grid_scratch_bytes(int64_t K);
+mbar_status sci_grid_launch(const float* vT, const SciLoopParams& prm, void* scratch, cudaStream_t st);
 // Algorithm 1's first loop for many problems in one persistent launch
 // (batch_loop.cu): a device queue of descriptors, one CTA per problem with its
 // level in shared memory; K <= 256.

@@ -431,9 +431,20 @@ __global__ void __launch_bounds__(32 * kEpiWarps) lse_epilogue_kernel(LseParams 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = blockIdx.x * kEpiWarps + warp;
   const bool sci = p.mode == kLseModeSci;
+  // the lane's partials b = lane, lane + 32, ... added in that order; eight
+  // loads are issued before their adds (past the end: exact zeros)
   auto rowsum = [&](int row) {
     double q = 0.0;
-    for (int b = lane; b < p.nparts; b += 32) q += p.partials[static_cast<size_t>(b) * K + row];
+    for (int b0 = lane; b0 < p.nparts; b0 += 32 * 8) {
+      double x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int b = b0 + 32 * j;
+        x[j] = b < p.nparts ? p.partials[static_cast<size_t>(b) * K + row] : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) q += x[j];
+    }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     return q;

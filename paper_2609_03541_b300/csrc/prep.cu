@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
   extern __shared__ __align__(1024) unsigned char st_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(st_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  __shared__ unsigned long long part[kStRows][kStCols];
-  __shared__ int okp[kStRows][kStCols];
+  __shared__ unsigned long long part[kStRows][kStCols + 1];  // padded: a warp reads one column
+  __shared__ int nonfinite[kStCols];                         // set by any thread that met one
   __shared__ double cmin[kStCols];
   __shared__ float mhs[kStCols], mls[kStCols];
   __shared__ int msp[kStCols];
@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
       tma_load_2d(xs + s * xb + static_cast<size_t>(b) * box_rows * 128, &tmap, &bars[s],
                   static_cast<int>(strip * kStCols), b * box_rows);
   };
+  if (tid < kStCols) nonfinite[tid] = 0;
   if (tid == 0) {
     prefetch_tmap(&tmap);
     mbar_init(&bars[0], 1);
@@ -280,26 +281,37 @@ __global__ void __launch_bounds__(kStThreads, 1) stage_tma_kernel(const __grid_c
       m = kx < m ? kx : m;
     }
     part[r0][jj] = m;
-    okp[r0][jj] = ok ? 1 : 0;
+    if (!ok) nonfinite[jj] = 1;
     // the bulk stores of two strips ago must have read their tile
     if (tid == 0) bulk_wait_read1();
     __syncthreads();
-    if (tid < ns) {
-      unsigned long long mm = part[0][tid];
-      int allok = okp[0][tid];
-#pragma unroll 8
-      for (int r = 1; r < kStRows; ++r) {
-        mm = part[r][tid] < mm ? part[r][tid] : mm;
-        allok &= okp[r][tid];
+    // warp w reduces the kStRows partials of column w: kStRows / 32 per
+    // lane, then the 64-bit minimum as the minimum of the high words and of
+    // the low words among the lanes that hold that high word (one redux each)
+    {
+      const int w = tid >> 5, l = tid & 31;
+      static_assert(kStRows % 32 == 0 && kStThreads / 32 >= kStCols, "one warp per column");
+      if (w < ns) {
+        unsigned long long pv = part[l][w];
+#pragma unroll
+        for (int q = l + 32; q < kStRows; q += 32) pv = part[q][w] < pv ? part[q][w] : pv;
+        const unsigned ph = static_cast<unsigned>(pv >> 32), pl = static_cast<unsigned>(pv);
+        const unsigned mh32 = __reduce_min_sync(0xffffffffu, ph);
+        const unsigned ml32 = __reduce_min_sync(0xffffffffu, ph == mh32 ? pl : 0xffffffffu);
+        if (l == 0) {
+          const unsigned long long mm = (static_cast<unsigned long long>(mh32) << 32) | ml32;
+          const bool allok = nonfinite[w] == 0;
+          nonfinite[w] = 0;  // read by this lane only; set again after the next barrier
+          if (!allok) atomicOr(bad, 1);
+          const double cm = allok ? from_ordered(mm) : 0.0;
+          c[n0 + w] = cm;
+          cmin[w] = cm;
+          float mh = 0.f, ml = 0.f;
+          msp[w] = (split_f64_trunc(cm, mh, ml) || cm == 0.0) ? 1 : 0;
+          mhs[w] = mh;
+          mls[w] = ml;
+        }
       }
-      if (!allok) atomicOr(bad, 1);
-      const double cm = allok ? from_ordered(mm) : 0.0;
-      c[n0 + tid] = cm;
-      cmin[tid] = cm;
-      float mh = 0.f, ml = 0.f;
-      msp[tid] = (split_f64_trunc(cm, mh, ml) || cm == 0.0) ? 1 : 0;
-      mhs[tid] = mh;
-      mls[tid] = ml;
     }
     __syncthreads();
     // pass 2: fl32(u - c) as (uh - ch) + (ul - cl), into the sample-major tile
@@ -433,7 +445,11 @@ mbar_status stage_samples(const double* u, int64_t K, int64_t N, int64_t ldu, do
           int dev = 0, optin = 0;
           cudaGetDevice(&dev);
           cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-          cudaFuncSetAttribute(stage_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 8 * 1024);
+          cudaFuncAttributes fa = {};
+          BUMBAR_CUDA(cudaFuncGetAttributes(&fa, stage_tma_kernel));
+          // the dynamic part may take what the static arrays leave
+          BUMBAR_CUDA(cudaFuncSetAttribute(stage_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           optin - static_cast<int>(fa.sharedSizeBytes)));
           init = true;
         }
       }

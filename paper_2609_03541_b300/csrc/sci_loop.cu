@@ -392,6 +392,333 @@ __global__ void __launch_bounds__(NT, 1) sci_loop_kernel(const float* __restrict
   loop_cluster_sync();
 }
 
+// ---------------------------------------------------------------------------
+// Grid-wide variant for levels that fit in the shared memory of all SMs
+// (up to ~25 MB: 148 x ~200 KB): one cooperative launch of one CTA per SM.
+// Each CTA loads its contiguous range of the level's bins once and keeps it
+// in shared memory for every step, so a step reads nothing from L2 but f
+// and the reduction scratch. A step:
+//   1. the CTA's row partials of Q_k (FP32, warps in order) -> scratch;
+//   2. grid barrier;
+//   3. CTA b reduces the states k = b, b + G, ... over the G CTAs in rank
+//      order (every CTA also reduces state 0 for the gauge), forms the
+//      update, the gauge, Eq. 2's relative step and max|df| for them, and
+//      writes f'_k and its per-CTA maxima to scratch;
+//   4. grid barrier;
+//   5. every CTA reads the G maxima and the new f, and takes the same
+//      decision (stop test, underflow, non-finite) as the cluster kernel.
+// The arithmetic is that of the cluster kernel, with the row partials
+// grouped by CTA instead of by the cluster's chunk order. Every barrier wait
+// is bounded (~1 s); a CTA that gives up raises a shared abort word, which
+// ends the other CTAs' waits, and the launch reports the timeout.
+struct GridShared {
+  double d_red[32];
+  float s_red[32];
+  int flags_red[32];
+  int decision;
+  int ok;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// arrive on the grid barrier and wait until `target` arrivals (all CTAs of
+// this and the earlier barriers); false on a timeout or an abort elsewhere
+__device__ bool grid_barrier(unsigned* bar, unsigned* abort_w, unsigned target, GridShared* sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    bool ok = true;
+    const uint64_t t0 = loop_ns();
+    for (uint32_t i = 0;; ++i) {
+      if (ld_acquire_gpu_u32(bar) >= target) break;
+      if ((i & 63u) == 63u) {
+        if (ld_acquire_gpu_u32(abort_w) != 0u || loop_ns() - t0 > kLoopWaitNs || i >= kLoopSpin) {
+          atomicExch(abort_w, 1u);
+          ok = false;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    sh->ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  return sh->ok != 0;
+}
+
+template <int LPS, int NK, int NT>
+__global__ void __launch_bounds__(NT, 1) sci_grid_kernel(const float* __restrict__ vT, int Kp, SciLoopParams q,
+                                                         unsigned char* __restrict__ scratch) {
+  constexpr int SPW = 32 / LPS;
+  constexpr int NW = NT / 32;
+  constexpr int E = 4 * NK;
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  __shared__ GridShared sh;
+  const int G = static_cast<int>(gridDim.x), b = static_cast<int>(blockIdx.x);
+  const int K = q.K, n = q.n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lig = lane % LPS, grp = lane / LPS;
+  const int p0 = static_cast<int>(static_cast<int64_t>(b) * n / G);
+  const int p1 = static_cast<int>(static_cast<int64_t>(b + 1) * n / G);
+  const int nb = p1 - p0;
+  float* lv = reinterpret_cast<float*>(gsm_raw);                 // [nb][Kp] this CTA's bins
+  float* part = lv + static_cast<size_t>(nb) * Kp;               // [NW][Kp] warp partials
+  double* f_s = reinterpret_cast<double*>(part + static_cast<size_t>(NW) * Kp);  // [Kp]
+  double* fn_s = f_s + Kp;                                       // [Kp] the step's new f
+  float* ah_s = reinterpret_cast<float*>(fn_s + Kp);             // [Kp] a_k log2(e), hi
+  float* al_s = ah_s + Kp;                                       // [Kp] and lo
+  // the states this CTA reduces: k = b + G i (i < nown), then state 0 for the
+  // gauge; red holds their G partials each, qs their sums
+  const int nown = b < K ? (K - b + G - 1) / G : 0;
+  const int nsr = nown + 1;
+  float* red = al_s + Kp;                                        // [nsr][G]
+  float* qs = red + static_cast<size_t>(nsr) * G;                // [nsr]
+  unsigned* bar = reinterpret_cast<unsigned*>(scratch);
+  unsigned* abort_w = bar + 1;
+  double* slots = reinterpret_cast<double*>(scratch + 256);      // [G][4]: s, d, flags
+  double* fnew = slots + 4 * static_cast<size_t>(G);              // [Kp]
+  float* gpart = reinterpret_cast<float*>(fnew + Kp);             // [G][Kp]
+
+  auto set_offset = [&](int k, double fk) {
+    if (k < K) {
+      const double a = (fk + q.logN[k]) * 1.4426950408889634;
+      const float hi = static_cast<float>(a);
+      ah_s[k] = hi;
+      al_s[k] = isfinite(hi) ? static_cast<float>(a - static_cast<double>(hi)) : 0.f;  // N_k = 0: -inf
+    } else {
+      ah_s[k] = -INFINITY;  // padding rows: weight 0
+      al_s[k] = 0.f;
+    }
+  };
+  {
+    const float4* src = reinterpret_cast<const float4*>(vT + static_cast<size_t>(p0) * Kp);
+    float4* dst = reinterpret_cast<float4*>(lv);
+    const int n4 = nb * (Kp / 4);
+    for (int i = tid; i < n4; i += NT) dst[i] = src[i];
+  }
+  for (int k = tid; k < Kp; k += NT) {
+    f_s[k] = k < K ? q.f[k] : 0.0;
+    set_offset(k, f_s[k]);
+  }
+  __syncthreads();
+
+  unsigned nbar = 0;
+  int applied = 0;
+  float last_s = INFINITY;
+  double last_d = 0.0;
+  bool aborted = false;
+  int dec = 0;
+  const int npairs = (nb + 2 * SPW - 1) / (2 * SPW);
+  for (int64_t step = 0; step < q.max_steps; ++step) {
+    float ahi[E], alo[E];
+#pragma unroll
+    for (int i = 0; i < NK; ++i) {
+      const int k4 = 4 * (lig + LPS * i);
+      float4 h = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY), l = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k4 < Kp) {
+        h = *reinterpret_cast<const float4*>(ah_s + k4);
+        l = *reinterpret_cast<const float4*>(al_s + k4);
+      }
+      ahi[4 * i] = h.x;
+      ahi[4 * i + 1] = h.y;
+      ahi[4 * i + 2] = h.z;
+      ahi[4 * i + 3] = h.w;
+      alo[4 * i] = l.x;
+      alo[4 * i + 1] = l.y;
+      alo[4 * i + 2] = l.z;
+      alo[4 * i + 3] = l.w;
+    }
+    float acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = 0.f;
+    for (int ps = warp; ps < npairs; ps += NW) {
+      const int j0 = (2 * ps) * SPW + grp, j1 = (2 * ps + 1) * SPW + grp;
+      const bool v0 = j0 < nb, v1 = j1 < nb;
+      const float* c0 = lv + static_cast<size_t>(v0 ? j0 : 0) * Kp;
+      const float* c1 = lv + static_cast<size_t>(v1 ? j1 : 0) * Kp;
+      float x0[E], x1[E], m0, m1, s0, s1;
+      smaj_pair<LPS, NK>(c0, c1, lig, Kp, ahi, alo, x0, x1, m0, m1, s0, s1);
+      const float w0 = v0 ? (q.H ? static_cast<float>(q.H[p0 + j0]) : 1.f) / s0 : 0.f;
+      const float w1 = v1 ? (q.H ? static_cast<float>(q.H[p0 + j1]) : 1.f) / s1 : 0.f;
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[e] = fmaf(x1[e], w1, fmaf(x0[e], w0, acc[e]));
+    }
+    float* mypart = part + static_cast<size_t>(warp) * Kp;
+#pragma unroll
+    for (int i = 0; i < NK; ++i)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float v = acc[4 * i + t];
+#pragma unroll
+        for (int o = LPS; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int k = 4 * (lig + LPS * i) + t;
+        if (grp == 0 && k < Kp) mypart[k] = v;
+      }
+    __syncthreads();
+    for (int k = tid; k < K; k += NT) {
+      float v = 0.f;
+      for (int w = 0; w < NW; ++w) v += part[static_cast<size_t>(w) * Kp + k];
+      gpart[static_cast<size_t>(b) * Kp + k] = v;
+    }
+    if (!grid_barrier(bar, abort_w, static_cast<unsigned>(G) * ++nbar, &sh)) {
+      aborted = true;
+      break;
+    }
+    // Q_k of this CTA's states and of state 0 over the G CTAs' partials: all
+    // loads at once into shared memory, then per state the lanes add
+    // r = lane, lane + 32, ... in order and a fixed shuffle tree combines
+    // them (the same bits for Q_0 in every CTA)
+    for (int i = tid; i < nsr * G; i += NT) {
+      const int sidx = i / G, r = i - sidx * G;
+      const int k = sidx < nown ? b + G * sidx : 0;
+      red[i] = __ldcg(gpart + static_cast<size_t>(r) * Kp + k);
+    }
+    __syncthreads();
+    for (int sidx = warp; sidx < nsr; sidx += NW) {
+      float v = 0.f;
+      for (int r = lane; r < G; r += 32) v += red[sidx * G + r];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) qs[sidx] = v;
+    }
+    __syncthreads();
+    // the update, the gauge f'_0 = 0, Eq. 2's step and max|df| of the states
+    const double f0n = f_s[0] + q.logN[0] - static_cast<double>(logf(qs[nown])), f0 = f_s[0];
+    float smax = -1.f;  // -1: no f_k != 0 seen
+    double dmax = 0.0;
+    int finite = 1, under = 0;
+    for (int sidx = tid; sidx < nown; sidx += NT) {
+      const int k = b + G * sidx;
+      const float Q = qs[sidx];
+      under |= !(static_cast<double>(Q) >= 1e-20 * q.Nk[k]);
+      const double fo = (f_s[k] + q.logN[k] - static_cast<double>(logf(Q))) - f0n, fi = f_s[k];
+      fnew[k] = fo;
+      if (!isfinite(fo)) finite = 0;
+      if (fi != 0.0) smax = fmaxf(smax, fabsf(static_cast<float>(fo - fi) / static_cast<float>(fi)));
+      dmax = fmax(dmax, fabs(fo - (fi - f0)));
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      finite &= __shfl_xor_sync(0xffffffffu, finite, o);
+      under |= __shfl_xor_sync(0xffffffffu, under, o);
+    }
+    if (lane == 0) {
+      sh.s_red[warp] = smax;
+      sh.d_red[warp] = dmax;
+      sh.flags_red[warp] = finite | (under << 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float sm = -1.f;
+      double dm = 0.0;
+      int fin = 1, un = 0;
+      for (int w = 0; w < NW; ++w) {
+        sm = fmaxf(sm, sh.s_red[w]);
+        dm = fmax(dm, sh.d_red[w]);
+        fin &= sh.flags_red[w] & 1;
+        un |= (sh.flags_red[w] >> 1) & 1;
+      }
+      double* sl = slots + 4 * static_cast<size_t>(b);
+      sl[0] = static_cast<double>(sm);
+      sl[1] = dm;
+      sl[2] = static_cast<double>(fin | (un << 1));
+    }
+    if (!grid_barrier(bar, abort_w, static_cast<unsigned>(G) * ++nbar, &sh)) {
+      aborted = true;
+      break;
+    }
+    // every CTA combines the G maxima (max and or/and do not depend on the
+    // order) and takes the same decision
+    float sm = -1.f;
+    double dm = 0.0;
+    int fin = 1, un = 0;
+    for (int r = tid; r < G; r += NT) {
+      const double* sl = slots + 4 * static_cast<size_t>(r);
+      sm = fmaxf(sm, static_cast<float>(__ldcg(sl)));
+      dm = fmax(dm, __ldcg(sl + 1));
+      const int fl = static_cast<int>(__ldcg(sl + 2));
+      fin &= fl & 1;
+      un |= (fl >> 1) & 1;
+    }
+    for (int k = tid; k < K; k += NT) fn_s[k] = __ldcg(fnew + k);  // with the maxima: one round trip
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      sm = fmaxf(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+      dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+      fin &= __shfl_xor_sync(0xffffffffu, fin, o);
+      un |= __shfl_xor_sync(0xffffffffu, un, o);
+    }
+    __syncthreads();  // the slice's use of sh.*_red is over
+    if (lane == 0) {
+      sh.s_red[warp] = sm;
+      sh.d_red[warp] = dm;
+      sh.flags_red[warp] = fin | (un << 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float smf = -1.f;
+      double dmf = 0.0;
+      int finf = 1, unf = 0;
+      for (int w = 0; w < NW; ++w) {
+        smf = fmaxf(smf, sh.s_red[w]);
+        dmf = fmax(dmf, sh.d_red[w]);
+        finf &= sh.flags_red[w] & 1;
+        unf |= (sh.flags_red[w] >> 1) & 1;
+      }
+      const float sv = smf < 0.f ? INFINITY : smf;
+      int d = 0;
+      if (unf) {
+        d = 1 | 2;  // keep f: the host redoes this step exactly
+      } else {
+        ++applied;
+        last_s = sv;
+        last_d = dmf;
+        if (!finf && b == 0) q.ctrl->nonfinite = 1;
+        if ((q.eps > 0.0 && sv < q.eps) || (q.noise > 0.0 && dmf < q.noise) || !finf) d = 1;
+      }
+      sh.decision = d;
+    }
+    __syncthreads();
+    dec = sh.decision;
+    if (!(dec & 2))
+      for (int k = tid; k < K; k += NT) {
+        f_s[k] = fn_s[k];
+        set_offset(k, f_s[k]);
+      }
+    __syncthreads();
+    if (dec & 1) break;
+  }
+  if (b == 0) {
+    if (tid == 0) {
+      if (aborted) {
+        atomicAdd(q.err, 1u);
+        dec = 1 | 8;
+      }
+      q.ctrl->iters += applied;
+      if (applied > 0) q.ctrl->last_s = static_cast<double>(last_s);
+      if ((dec & (1 | 2 | 8)) == 1 && applied > 0) {
+        // stopped by the test (not by an underflow or a timeout)
+        if ((q.eps > 0.0 && last_s < q.eps) || (q.noise > 0.0 && last_d < q.noise)) q.ctrl->done = 1;
+      }
+      if (dec & 2) {
+        q.ctrl->underflow = 1;
+        if (q.s_out) *q.s_out = INFINITY;
+      } else if (q.s_out && applied > 0) {
+        *q.s_out = static_cast<double>(last_s);
+      }
+      if (q.d_out && applied > 0) *q.d_out = last_d;
+    }
+    for (int k = tid; k < K; k += NT) q.f[k] = f_s[k];
+  }
+}
+
 namespace {
 
 template <int LPS, int NK, int NT>
@@ -454,7 +781,111 @@ LoopPlan loop_plan(int64_t K) {
   return pl;
 }
 
+struct GridPlan {
+  int lps, nk, nt, G;
+  size_t smem;
+};
+
+// the cluster kernel's lane shape; at least four bins per CTA (fewer CTAs
+// make cheaper barriers on small levels), at most one CTA per SM
+GridPlan grid_plan(int64_t K, int64_t n) {
+  const LoopPlan lp = loop_plan(K);
+  GridPlan g{};
+  g.lps = lp.lps;
+  g.nk = lp.nk;
+  g.nt = lp.nt;
+  g.G = static_cast<int>(std::min<int64_t>(num_sms(), std::max<int64_t>(1, n / 4)));
+  const int64_t Kp = stage_pitch(K);
+  const int64_t nb = ceil_div(n, static_cast<int64_t>(g.G));  // bins of the largest CTA range
+  const int64_t nsr = ceil_div(K, static_cast<int64_t>(g.G)) + 1;  // states a CTA reduces
+  g.smem = static_cast<size_t>(nb * Kp * 4 + (g.nt / 32) * Kp * 4 + 2 * Kp * 8 + 2 * Kp * 4 + nsr * (g.G + 1) * 4);
+  return g;
+}
+
+template <int LPS, int NK, int NT>
+mbar_status grid_run(const float* vT, int Kp, const GridPlan& pl, const SciLoopParams& prm, void* scratch,
+                     cudaStream_t st) {
+  static bool init = false;
+  {
+    std::lock_guard<std::recursive_mutex> lock(init_mutex());
+    if (!init) {
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      cudaFuncAttributes fa = {};
+      BUMBAR_CUDA(cudaFuncGetAttributes(&fa, sci_grid_kernel<LPS, NK, NT>));
+      BUMBAR_CUDA(cudaFuncSetAttribute(sci_grid_kernel<LPS, NK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       optin - static_cast<int>(fa.sharedSizeBytes)));
+      init = true;
+    }
+  }
+  BUMBAR_CUDA(cudaMemsetAsync(scratch, 0, 256, st));  // barrier counter and abort word
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(pl.G));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident at once: they wait on one another
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BUMBAR_CUDA(cudaLaunchKernelEx(&cfg, sci_grid_kernel<LPS, NK, NT>, vT, Kp, prm,
+                                 static_cast<unsigned char*>(scratch)));
+  count_launches(1);
+  return MBAR_OK;
+}
+
 }  // namespace
+
+bool sci_grid_supported(int64_t K, int64_t n) {
+  if (K < 1 || K > 1024 || n < 1 || n > (int64_t{1} << 30)) return false;
+  return grid_plan(K, n).smem <= 200 * 1024;
+}
+
+size_t sci_grid_scratch_bytes(int64_t K) {
+  const int64_t Kp = stage_pitch(K);
+  return static_cast<size_t>(256 + 4 * 8 * num_sms() + Kp * 8 + static_cast<int64_t>(num_sms()) * Kp * 4);
+}
+
+mbar_status sci_grid_launch(const float* vT, const SciLoopParams& prm, void* scratch, cudaStream_t st) {
+  if (!sci_grid_supported(prm.K, prm.n)) {
+    set_error("sci_grid_launch: unsupported level");
+    return MBAR_EUNSUPPORTED;
+  }
+  const GridPlan pl = grid_plan(prm.K, prm.n);
+  const int Kp = static_cast<int>(stage_pitch(prm.K));
+  if (pl.lps < 32) {
+    switch (pl.lps) {
+#define BUMBAR_GRID_SMALL(L)                                                              \
+  case L:                                                                                 \
+    if (pl.nk == 1) return grid_run<L, 1, 512>(vT, Kp, pl, prm, scratch, st);             \
+    if (pl.nk == 2) return grid_run<L, 2, 512>(vT, Kp, pl, prm, scratch, st);             \
+    return grid_run<L, 4, 256>(vT, Kp, pl, prm, scratch, st);
+      BUMBAR_GRID_SMALL(1)
+      BUMBAR_GRID_SMALL(2)
+      BUMBAR_GRID_SMALL(4)
+      BUMBAR_GRID_SMALL(8)
+      BUMBAR_GRID_SMALL(16)
+#undef BUMBAR_GRID_SMALL
+      default: break;
+    }
+  } else {
+    switch (pl.nk) {
+      case 1: return grid_run<32, 1, 512>(vT, Kp, pl, prm, scratch, st);
+      case 2: return grid_run<32, 2, 512>(vT, Kp, pl, prm, scratch, st);
+      case 3: return grid_run<32, 3, 512>(vT, Kp, pl, prm, scratch, st);
+      case 4: return grid_run<32, 4, 256>(vT, Kp, pl, prm, scratch, st);
+      case 5: return grid_run<32, 5, 256>(vT, Kp, pl, prm, scratch, st);
+      case 6: return grid_run<32, 6, 256>(vT, Kp, pl, prm, scratch, st);
+      case 7: return grid_run<32, 7, 256>(vT, Kp, pl, prm, scratch, st);
+      case 8: return grid_run<32, 8, 256>(vT, Kp, pl, prm, scratch, st);
+      default: break;
+    }
+  }
+  set_error("sci_grid_launch: unsupported shape");
+  return MBAR_EUNSUPPORTED;
+}
 
 bool sci_loop_supported(int64_t K, int64_t n, double max_bytes) {
   if (K < 1 || K > 1024 || n < 1) return false;

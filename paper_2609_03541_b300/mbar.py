@@ -134,6 +134,7 @@ _SIGNATURES = {
     "mbar_last_error": ([], ctypes.c_char_p),
     "mbar_device_bytes": ([_vp, _i64p], ctypes.c_int),
     "mbar_set_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "mbar_set_exclusive": ([_vp, ctypes.c_int32], ctypes.c_int),
     "mbar_get_timing": ([_vp, ctypes.c_int32, _i64p, _dp, _dp], ctypes.c_int),
     "mbar_kernel_launches": ([_i64p], ctypes.c_int),
     "mbar_get_trace": ([_vp, _i64p, _dp, ctypes.c_int64], ctypes.c_int),
@@ -371,6 +372,12 @@ class Context:
         b = ctypes.c_int64()
         _check(lib().mbar_device_bytes(self._h, ctypes.byref(b)))
         return b.value
+
+    def set_exclusive(self, exclusive: bool):
+        """``mbar_set_exclusive``: True (default) lets the solve use every SM
+        (graphs, the whole-GPU loop on small levels); False for contexts
+        that share the GPU with concurrent solves."""
+        _check(lib().mbar_set_exclusive(self._h, int(bool(exclusive))))
 
     def set_timing(self, enable: bool):
         _check(lib().mbar_set_timing(self._h, int(bool(enable))))

@@ -101,6 +101,10 @@ def test_destroy_null_is_ok(L):
     assert L.mbar_destroy(None) == 0
 
 
+def test_exclusive_needs_a_context(L):
+    assert M.STATUS[L.mbar_set_exclusive(None, 1)] == "MBAR_EINVAL"
+
+
 def test_footprint_estimate_grows_with_the_problem(L):
     small = M.footprint_bytes(8, 8000)
     big = M.footprint_bytes(500, 2_000_000)

@@ -101,6 +101,27 @@ def test_bench_shapes_match_the_oracle(name, prec):
     assert err < TOL[prec], (name, err, rep)
 
 
+@pytest.mark.parametrize("name", ["alchemical_K500", "tempering_K50"] + BATCH_TYPES[:4])
+def test_exclusive_and_shared_device_loops_match_the_oracle(name):
+    """MIXED solves with the device to themselves (the default: graphs, and
+    the binned SCI steps of small levels in one cooperative launch over all
+    SMs with the level in shared memory) and shared (mbar_set_exclusive(0):
+    one 8-SM cluster or separate launches): both at the oracle's root within
+    1e-4 kT."""
+    case = REFS[name]
+    p = _problem(case)
+    f_ref = np.asarray(case["f"])
+    for exclusive in (True, False):
+        with M.Context(p.u_kn, p.N_k, M.MBAR_MIXED) as ctx:
+            ctx.set_exclusive(exclusive)
+            if p.phi is not None:
+                ctx.set_coordinate(p.phi)
+            rep = ctx.solve().as_dict()
+            f = ctx.free_energies()
+        err = float(np.max(np.abs(f - f_ref)))
+        assert err < TOL[M.MBAR_MIXED], (name, exclusive, err, rep)
+
+
 @pytest.mark.parametrize("name", ["umbrella_K4_s0", "umbrella_K4_s4", "umbrella_K4_s7"])
 def test_mixed_gradient_keeps_small_weight_deficits(name):
     """At the oracle's root the exact gradient vanishes (~1e-12). A sample

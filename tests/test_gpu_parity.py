@@ -283,6 +283,19 @@ def test_single_state_and_two_sample_closed_form():
     assert abs(f[1] - 0.5 * (1.3 - 0.4)) < 1e-10
 
 
+@pytest.mark.parametrize("K,N,k,n,bad", [(500, 4133, 321, 2777, np.nan), (500, 4133, 499, 4132, -np.inf),
+                                          (37, 100, 0, 0, np.inf), (700, 300, 650, 17, np.nan)])
+def test_nonfinite_entry_anywhere_is_rejected(K, N, k, n, bad):
+    """One non-finite u_kn anywhere (any row residue of the staging's
+    per-sample minimum, the last entry, the row-major fallback above
+    K = 512) makes a mixed-precision context fail with MBAR_EINVAL."""
+    u, Nk = rand_problem(K, N, seed=3)
+    u[k, n] = bad
+    with pytest.raises(M.MbarError) as e:
+        M.Context(u, Nk, M.MBAR_MIXED)
+    assert e.value.name == "MBAR_EINVAL"
+
+
 def test_bad_inputs_are_rejected():
     u = np.ones((2, 4))
     u[1, 2] = np.nan

@@ -31,7 +31,10 @@ def _mix():
 
 
 def _alone(u, nk, phi, prec):
+    """The same solve alone, set up as a server worker sets up its contexts
+    (a device shared with other solves: no graphs, cluster-sized loops)."""
     ctx = M.Context(u, nk, prec, opts=M.default_opts(prec))
+    ctx.set_exclusive(False)
     if phi is not None:
         ctx.set_coordinate(phi)
     ctx.solve()
@@ -151,6 +154,7 @@ def test_server_factorised_requests_equal_the_same_solves_alone():
     alone = []
     for a, b, phi, nk in mix:
         with M.Context.factorised(a, b, phi, nk, prec) as ctx:
+            ctx.set_exclusive(False)  # as the server's workers run them
             ctx.solve()
             alone.append(ctx.free_energies())
     with M.Server(M.server_config(workers=4, hbm_budget_bytes=8 << 30, precision=prec)) as srv:
