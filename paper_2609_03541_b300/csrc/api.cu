@@ -53,6 +53,7 @@ struct Level {
   int64_t n_sched = 0;  // n used by Algorithm 1's break rule
   bool fact = false;    // unbinned data of a factorised context: generated from (a, b, phi), no store
   CUtensorMap tmap;
+  const float* vT = nullptr;  // binned FP32: a sample-major copy (n x stage_pitch(K)), not owned
 };
 
 }  // namespace
@@ -256,6 +257,11 @@ mbar_status run_lse(mbar_ctx* c, const Level& L, const double* f_in, int mode, d
     // phi's range from the sorted copy: its first and last element
     s = lse_fact_launch(c->fa, c->fb, c->fphi, lse_fact_plan(c->K, L.n), p, c->phi_sorted, c->phi_sorted + c->N - 1,
                         1, c->fref, c->st);
+  } else if (L.binned && L.vT && !logden_out) {
+    // a large binned FP32 level with a sample-major copy (the second loop's
+    // current level): the sample-major pass streams whole contiguous bins
+    p.exact_max = 0;
+    s = lse_smaj_launch(L.vT, lse_smaj_plan(c->K, L.n), p, c->st);
   } else if (!L.binned && c->smaj && c->vst) {
     // unbinned MIXED pass over the sample-major copy (original sample order);
     // logden comes back to the store's column order through perm
@@ -1253,8 +1259,9 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   // column's largest exponent lies between min_k a_k and max_k a_k (v >= 0),
   // so this only matters when some |a_k| is large: below 64 kT the FP32
   // spacing there is under 1e-5 kT per entry and the data stay as they are.
-  float* cur_vT = nullptr;  // owned: the current level sample-major, when small
+  float* cur_vT = nullptr;  // owned: the current level sample-major (small levels, large ones in exclusive mode)
   void* grid_scr = nullptr;  // owned: scratch of the grid-wide loop, when it runs the level
+  bool cur_loop = false;     // the current level's in-place steps run in one launch
   // Levels up to 4 MB take the one-launch loop (a cluster of 8 SMs streaming
   // the level from L2). Without CUDA graphs (server workers, with other
   // solves on the GPU beside them) a round on a larger level is 2 x 21
@@ -1262,6 +1269,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   // thread; there the cluster loop runs up to 32 MB: 8 SMs per solve leave
   // the rest of the GPU to the other solves.
   const double kFusedRoundBytes = (c->graphs ? 4.0 : 32.0) * (1 << 20);
+  const double kSmajLevelMaxBytes = 4.0 * (1 << 30);
   auto recenter_pair = [&]() -> mbar_status {
     if (c->dtype != 4) return MBAR_OK;
     BUMBAR_TRY(d2h(c, c->f_h.data(), c->f, K));
@@ -1278,13 +1286,22 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
     // on one cluster
     dfree(c, cur_vT);
     cur_vT = nullptr;
+    cur.vT = nullptr;
     dfree(c, grid_scr);
     grid_scr = nullptr;
     const bool grid = cur.binned && use_grid_loop(c, cur.n);
-    if (cur.binned && (grid || sci_loop_supported(K, cur.n, kFusedRoundBytes))) {
+    cur_loop = cur.binned && (grid || sci_loop_supported(K, cur.n, kFusedRoundBytes));
+    // a larger current level, in exclusive mode: a sample-major copy for its
+    // N_intermediate + 1 passes (one transpose; the copy is not in a
+    // server's memory budget, hence exclusive mode only)
+    const double lbytes = static_cast<double>(sci_loop_level_bytes(K, cur.n));
+    const bool smaj_copy = !cur_loop && cur.binned && c->graphs && c->dtype == 4 && lse_smaj_preferred(K) &&
+                           lbytes <= kSmajLevelMaxBytes;
+    if (cur_loop || smaj_copy) {
       BUMBAR_TRY(dalloc(c, reinterpret_cast<void**>(&cur_vT), sci_loop_level_bytes(K, cur.n)));
       BUMBAR_TRY(level_to_samples(static_cast<const float*>(cur.v), K, cur.n, cur.ld, cur_vT, c->st));
       if (grid) BUMBAR_TRY(dalloc(c, &grid_scr, sci_grid_scratch_bytes(K)));
+      if (smaj_copy) cur.vT = cur_vT;
     }
     return MBAR_OK;
   };
@@ -1301,7 +1318,7 @@ mbar_status algorithm1(mbar_ctx* c, mbar_report* rep) {
   // and the probe at n * inc (-> fts); the f buffers keep their addresses so
   // the captured round stays valid until the level pair changes
   auto round_body = [&]() -> mbar_status {
-    if (cur_vT) {
+    if (cur_loop) {
       SciLoopParams q{};
       q.K = static_cast<int>(K);
       q.n = static_cast<int>(cur.n);
