@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NT, 1) lse_fact_kernel(const double* __restric
       const float s = EXACT ? static_cast<float>(nt) + r : r;
       const float w = j < nloc ? hw * rcp_approx(s) : 0.f;
       // every lane of a group holds its sample's m and s: lane l takes the
-      // logden of sample l from the group that has it in this round
+      // logden of sample l from the group that holds it in this exchange step
       // logden_p = (x_rp + m + log2 s) ln 2, x_rp = c_r - b'_r phi_p (0 in the absolute form)
       const float xr = rel ? fmaf(-bhr, ph, chr) + lor : 0.f;
       const float lv = (xr + (m + __log2f(s))) * kLn2;
