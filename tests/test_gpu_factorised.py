@@ -150,6 +150,26 @@ def test_factorised_poorly_overlapping_windows_reach_the_oracle(N_k, seed):
     assert np.max(np.abs(f - f_ref)) < 1e-4, rep
 
 
+@pytest.mark.parametrize("M_,N_0,seed", [(12, 200, 4), (30, 100, 1)])
+def test_factorised_covariance_matches_the_oracle(M_, N_0, seed):
+    """mbar_covariance of a store-free context (its Hessian from FP16 P~
+    formed from phi at every K) on Sec. IV ladders: the asymptotic
+    covariance within 2e-3 of the oracle's weight-matrix form (scaled by
+    sd_i sd_j), so the 5-sigma checks against the analytic f divide by the
+    right standard deviations."""
+    a, b, phi, Nk = _gaussian(M_, N_0, seed)
+    with M.Context.factorised(a, b, phi, Nk, M.MBAR_MIXED) as ctx:
+        ctx.solve()
+        f = ctx.free_energies()
+        C = ctx.covariance()
+    u = O.factorised_u(a, b, phi)
+    f_ref = O.solve_mbar(u, Nk)
+    C_ref = O.mbar_covariance(u, f_ref, Nk)
+    scale = np.sqrt(np.outer(np.diag(C_ref), np.diag(C_ref)))[1:, 1:]
+    assert np.max(np.abs(f - f_ref)) < 1e-4
+    assert np.max(np.abs(C[1:, 1:] - C_ref[1:, 1:]) / scale) < 2e-3
+
+
 @pytest.mark.parametrize("M_,N_0", [(309, 396), (552, 760)])
 def test_factorised_long_replica_ladder_matches_the_analytic_free_energies(M_, N_0):
     """Sec. IV replicas (80 % neighbour overlap) up to beta ~ 280: u reaches
